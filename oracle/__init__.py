@@ -1,0 +1,275 @@
+"""FP64 CPU oracle for the multigrid V-cycle: TEST INFRASTRUCTURE ONLY.
+
+Only tests/, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package. The product path (the CUDA library in
+``paper_1406_5369_gb300``) never imports it, and it never imports the
+product path; the two share only the seeded input generators in ``synth``.
+
+The arithmetic lives in ``mg_oracle.c`` (plain C, FP64, natural loop order,
+built with ``-O2 -ffp-contract=off``); this module compiles it with gcc on
+first use and wraps it with ctypes. Arrays are numpy float64 of shape
+``(n,)*dim`` with x fastest, as in ``synth``. Local Fourier analysis lives in
+``oracle.lfa``.
+
+Parity status of each routine (what pins it is in tests/test_oracle_*.py):
+stencil apply, residual, RBGS, Jacobi, full weighting, prolongation, dense
+coarse solve, V-cycle, solve loop, defect correction (FP64 inner), face
+coefficients and their coarsening are all pinned. No routine is unpinned.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mg_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+RBGS = 0
+JACOBI = 1
+
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def build(force: bool = False) -> str:
+    """Compiles mg_oracle.c into oracle/_build/liboracle.so (gcc, FP64, no FMA)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-std=c11", "-shared", "-fPIC",
+                               _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+            sig = {
+                "or_apply": (None, [i, i, _D, _D, _D, _D, _D, _D]),
+                "or_diag": (None, [i, i, _D, _D, _D, _D, _D]),
+                "or_residual": (None, [i, i, _D, _D, _D, _D, _D, _D, _D]),
+                "or_rbgs": (None, [i, i, _D, _D, _D, _D, d, i, _D, _D]),
+                "or_jacobi": (None, [i, i, _D, _D, _D, _D, d, i, _D, _D]),
+                "or_restrict": (None, [i, i, _D, _D]),
+                "or_prolong_add": (None, [i, i, _D, _D]),
+                "or_node_faces": (None, [i, i, _D, _D, _D, _D, _D]),
+                "or_coarsen_faces": (None, [i, i, _D, _D, _D, _D, _D, _D]),
+                "or_norm": (d, [i, i, _D]),
+                "or_dense_solve": (i, [i, i, _D, _D, _D, _D, _D, _D]),
+                "or_create": (vp, [i, i, _D, _D, i, i, d, i, i]),
+                "or_destroy": (None, [vp]),
+                "or_levels": (i, [vp]),
+                "or_level_n": (i, [vp, i]),
+                "or_get_faces": (None, [vp, i, _D, _D, _D]),
+                "or_set_rhs": (None, [vp, _D]),
+                "or_set_u": (None, [vp, _D]),
+                "or_get_u": (None, [vp, _D]),
+                "or_vcycle": (None, [vp]),
+                "or_residual_norm": (d, [vp]),
+                "or_solve": (i, [vp, d, i, _D]),
+                "or_dc_solve": (i, [vp, d, i, _D]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_D)
+
+
+def _grid(a, dim=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if dim is not None and a.ndim != dim:
+        raise ValueError("array rank does not match dim")
+    return a
+
+
+def _c3(c):
+    return np.ascontiguousarray(np.array([1.0, 1.0, 1.0] if c is None else list(c) + [1.0] * (3 - len(c)),
+                                         dtype=np.float64))
+
+
+def _faces(faces, dim):
+    if faces is None:
+        return [None, None, None]
+    fs = [_grid(x) for x in faces] + [None] * (3 - len(faces))
+    return fs[:3]
+
+
+# ---------------- stateless level operators ----------------
+
+def apply(u, c=None, faces=None):
+    """A u at interior nodes (0 on the boundary)."""
+    u = _grid(u)
+    dim, n = u.ndim, u.shape[0]
+    out = np.empty_like(u)
+    c3, fs = _c3(c), _faces(faces, dim)
+    lib().or_apply(dim, n, _p(c3), _p(fs[0]), _p(fs[1]), _p(fs[2]), _p(u), _p(out))
+    return out
+
+
+def diag(dim, n, c=None, faces=None):
+    out = np.empty((n,) * dim)
+    c3, fs = _c3(c), _faces(faces, dim)
+    lib().or_diag(dim, n, _p(c3), _p(fs[0]), _p(fs[1]), _p(fs[2]), _p(out))
+    return out
+
+
+def residual(u, f, c=None, faces=None):
+    u, f = _grid(u), _grid(f)
+    dim, n = u.ndim, u.shape[0]
+    r = np.empty_like(u)
+    c3, fs = _c3(c), _faces(faces, dim)
+    lib().or_residual(dim, n, _p(c3), _p(fs[0]), _p(fs[1]), _p(fs[2]), _p(u), _p(f), _p(r))
+    return r
+
+
+def rbgs(u, f, sweeps=1, omega=1.0, c=None, faces=None):
+    """Returns u after ``sweeps`` omega red-black Gauss-Seidel sweeps."""
+    u, f = _grid(u).copy(), _grid(f)
+    dim, n = u.ndim, u.shape[0]
+    c3, fs = _c3(c), _faces(faces, dim)
+    lib().or_rbgs(dim, n, _p(c3), _p(fs[0]), _p(fs[1]), _p(fs[2]), omega, sweeps, _p(u), _p(f))
+    return u
+
+
+def jacobi(u, f, sweeps=1, omega=0.8, c=None, faces=None):
+    u, f = _grid(u).copy(), _grid(f)
+    dim, n = u.ndim, u.shape[0]
+    c3, fs = _c3(c), _faces(faces, dim)
+    lib().or_jacobi(dim, n, _p(c3), _p(fs[0]), _p(fs[1]), _p(fs[2]), omega, sweeps, _p(u), _p(f))
+    return u
+
+
+def restrict(r):
+    r = _grid(r)
+    dim, nf = r.ndim, r.shape[0]
+    nc = (nf - 1) // 2 + 1
+    fc = np.empty((nc,) * dim)
+    lib().or_restrict(dim, nf, _p(r), _p(fc))
+    return fc
+
+
+def prolong_add(e, u):
+    """Returns u + P e (u fine, e coarse)."""
+    e, u = _grid(e), _grid(u).copy()
+    lib().or_prolong_add(e.ndim, e.shape[0], _p(e), _p(u))
+    return u
+
+
+def node_faces(knode, c=None):
+    k = _grid(knode)
+    dim, n = k.ndim, k.shape[0]
+    out = [np.empty_like(k) for _ in range(dim)] + [None] * (3 - dim)
+    lib().or_node_faces(dim, n, _p(_c3(c)), _p(k), _p(out[0]), _p(out[1]), _p(out[2]))
+    return out[:dim]
+
+
+def coarsen_faces(faces):
+    dim = len(faces)
+    fs = [_grid(x) for x in faces] + [None] * (3 - dim)
+    nf = fs[0].shape[0]
+    nc = (nf - 1) // 2 + 1
+    out = [np.empty((nc,) * dim) for _ in range(dim)] + [None] * (3 - dim)
+    lib().or_coarsen_faces(dim, nf, _p(fs[0]), _p(fs[1]), _p(fs[2]), _p(out[0]), _p(out[1]), _p(out[2]))
+    return out[:dim]
+
+
+def norm(r):
+    r = _grid(r)
+    return lib().or_norm(r.ndim, r.shape[0], _p(r))
+
+
+def dense_solve(f, u_boundary=None, c=None, faces=None):
+    """Exact solve of the interior system (Gaussian elimination, partial pivoting)."""
+    f = _grid(f)
+    dim, n = f.ndim, f.shape[0]
+    u = np.zeros_like(f) if u_boundary is None else _grid(u_boundary).copy()
+    c3, fs = _c3(c), _faces(faces, dim)
+    rc = lib().or_dense_solve(dim, n, _p(c3), _p(fs[0]), _p(fs[1]), _p(fs[2]), _p(u), _p(f))
+    if rc != 0:
+        raise RuntimeError("singular system")
+    return u
+
+
+# ---------------- hierarchy ----------------
+
+class Hierarchy:
+    """A grid hierarchy with V-cycle, solve loop and FP64 defect correction."""
+
+    def __init__(self, dim, n, c=None, knode=None, coarsest_n=3, smoother=RBGS, omega=1.0,
+                 nu1=2, nu2=1):
+        self.dim, self.n = dim, n
+        self._k = None if knode is None else _grid(knode, dim)
+        self._c3 = _c3(c)
+        self.h = lib().or_create(dim, n, _p(self._c3), _p(self._k), coarsest_n, smoother,
+                                 float(omega), nu1, nu2)
+        if not self.h:
+            raise ValueError("invalid hierarchy parameters")
+        self.levels = lib().or_levels(self.h)
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            lib().or_destroy(h)
+            self.h = None
+
+    def level_n(self, l):
+        return lib().or_level_n(self.h, l)
+
+    def faces(self, l):
+        if self._k is None:
+            return None
+        nl = self.level_n(l)
+        out = [np.empty((nl,) * self.dim) for _ in range(self.dim)] + [None] * (3 - self.dim)
+        lib().or_get_faces(self.h, l, _p(out[0]), _p(out[1]), _p(out[2]))
+        return out[:self.dim]
+
+    def set_rhs(self, f):
+        f = _grid(f, self.dim)
+        lib().or_set_rhs(self.h, _p(f))
+
+    def set_u(self, u):
+        u = _grid(u, self.dim)
+        lib().or_set_u(self.h, _p(u))
+
+    def get_u(self):
+        u = np.empty((self.n,) * self.dim)
+        lib().or_get_u(self.h, _p(u))
+        return u
+
+    def vcycle(self):
+        lib().or_vcycle(self.h)
+
+    def residual_norm(self):
+        return lib().or_residual_norm(self.h)
+
+    def solve(self, tol, maxit):
+        """Returns the relative residual history rho[0..k] (rho[0] = 1)."""
+        rho = np.zeros(maxit + 1)
+        k = lib().or_solve(self.h, float(tol), int(maxit), _p(rho))
+        return rho[:k + 1]
+
+    def dc_solve(self, tol, maxit):
+        """Defect correction with an FP64 inner V-cycle; rho[0..k]."""
+        rho = np.zeros(maxit + 1)
+        k = lib().or_dc_solve(self.h, float(tol), int(maxit), _p(rho))
+        return rho[:k + 1]

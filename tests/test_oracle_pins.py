@@ -1,0 +1,496 @@
+"""Pins of the FP64 CPU oracle against facts fixed by the paper and by mathematics.
+
+None of these tests uses the CUDA library. Each pin is chosen so that a
+plausible slip in the oracle (a dropped stencil term, a wrong sign, an
+off-by-one in the coarse index map, a transposed colour) fails at least one:
+
+* closed forms: discrete sine/cosine eigenfunctions of A, the Jacobi
+  amplification factor, full weighting and interpolation of trig modes,
+  the config-1 discrete solution c_h * sin(pi x) sin(pi y);
+* independent constructions: A from Kronecker products or from a sum over
+  grid edges, red-black Gauss-Seidel as a sequential sweep over a permuted
+  dense matrix, numpy.linalg.solve for the dense coarse solve;
+* the two-grid matrix assembled column by column from the oracle against the
+  exact sine-basis LFA (oracle.lfa) and the classical infinite-grid values;
+* the paper's printed settings and convergence claim (tests/golden).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import lfa
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def interior_index(dim, n):
+    return [p for p in np.ndindex(*((n,) * dim)) if all(0 < x < n - 1 for x in p)]
+
+
+def kron_poisson(dim, n, c=(1.0, 1.0, 1.0)):
+    """Dense interior matrix of -sum_d c_d D2_d from Kronecker products (x fastest)."""
+    m = n - 2
+    h = 1.0 / (n - 1)
+    T = (np.diag(2.0 * np.ones(m)) - np.diag(np.ones(m - 1), 1) - np.diag(np.ones(m - 1), -1)) / h**2
+    I = np.eye(m)
+    if dim == 2:
+        return c[0] * np.kron(I, T) + c[1] * np.kron(T, I)
+    return (c[0] * np.kron(I, np.kron(I, T)) + c[1] * np.kron(I, np.kron(T, I))
+            + c[2] * np.kron(T, np.kron(I, I)))
+
+
+def edge_matrix(dim, n, faces):
+    """Dense interior matrix as a sum over grid edges: edge (p, p+e_d) with
+    coefficient k adds k/h^2 * (e_p - e_q)(e_p - e_q)^T restricted to interior."""
+    h = 1.0 / (n - 1)
+    idx = interior_index(dim, n)
+    pos = {p: q for q, p in enumerate(idx)}
+    A = np.zeros((len(idx), len(idx)))
+    for p in np.ndindex(*((n,) * dim)):
+        for d in range(dim):
+            ax = dim - 1 - d  # array axis of dimension d (x is the last axis)
+            if p[ax] == n - 1:
+                continue
+            q = list(p)
+            q[ax] += 1
+            q = tuple(q)
+            k = faces[d][p] / h**2
+            a, b = pos.get(p), pos.get(q)
+            if a is not None:
+                A[a, a] += k
+            if b is not None:
+                A[b, b] += k
+            if a is not None and b is not None:
+                A[a, b] -= k
+                A[b, a] -= k
+    return A
+
+
+def assembled(dim, n, c=None, faces=None):
+    idx = interior_index(dim, n)
+    A = np.zeros((len(idx), len(idx)))
+    for col, p in enumerate(idx):
+        e = np.zeros((n,) * dim)
+        e[p] = 1.0
+        Ae = oracle.apply(e, c=c, faces=faces)
+        A[:, col] = [Ae[q] for q in idx]
+    return A
+
+
+def trig(dim, n, k, beta):
+    """prod_d cos(k_d pi x_d + beta_d) on all nodes (x = last axis)."""
+    x = synth.coords(n)
+    g = [np.cos(k[d] * math.pi * x + beta[d]) for d in range(dim)]
+    if dim == 2:
+        return np.multiply.outer(g[1], g[0])
+    return np.multiply.outer(np.multiply.outer(g[2], g[1]), g[0])
+
+
+def interior(a):
+    return a[(slice(1, -1),) * a.ndim]
+
+
+# ---------------- inputs ----------------
+
+def test_splitmix64_reference_vectors():
+    # Published SplitMix64 outputs (Steele, Lea & Flood 2014 / Vigna's splitmix64.c).
+    assert list(synth.splitmix64(1234567, 5)) == [6457827717110365317, 3203168211198807973,
+                                                  9817491932198370423, 4593380528125082431,
+                                                  16408922859458223821]
+    assert int(synth.splitmix64(0, 1)[0]) == 0xE220A8397B1DCDAF
+
+
+def test_generators_are_deterministic_and_distributed():
+    a = synth.uniform(11, (300, 300))
+    assert np.array_equal(a, synth.uniform(11, (300, 300)))
+    assert abs(a.mean()) < 0.01 and abs(a.var() - 1 / 3) < 0.01
+    z = synth.normal(12, (400, 400))
+    assert abs(z.mean()) < 0.01 and abs(z.std() - 1) < 0.01
+    f = synth.uniform_rhs(2, 33, 5)
+    assert np.all(f[0] == 0) and np.all(f[:, -1] == 0) and np.abs(f).max() <= 1
+    with pytest.raises(ValueError):
+        synth.check_size(2, 10)
+
+
+# ---------------- stencil ----------------
+
+@pytest.mark.parametrize("dim,n,c", [(2, 9, (1, 1, 1)), (2, 9, (2.0, 0.5, 1)), (3, 5, (1, 1, 1)),
+                                     (3, 5, (1.0, 3.0, 0.25))])
+def test_stencil_matches_kronecker_matrix(dim, n, c):
+    assert np.array_equal(assembled(dim, n, c=c), assembled(dim, n, c=c).T)
+    np.testing.assert_allclose(assembled(dim, n, c=c), kron_poisson(dim, n, c), rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("dim,n", [(2, 17), (3, 9)])
+def test_trig_modes_are_eigenfunctions(dim, n):
+    # A phi = lambda phi at interior nodes for any phase: pins every stencil term
+    # and the handling of non-zero boundary values.
+    h = 1.0 / (n - 1)
+    rng = np.random.default_rng(0)
+    for _ in range(5):
+        k = rng.integers(1, n - 1, size=dim)
+        beta = rng.uniform(0, 2 * math.pi, size=dim)
+        c = rng.uniform(0.5, 2.0, size=dim)
+        phi = trig(dim, n, k, beta)
+        lam = sum(c[d] * 4.0 / h**2 * math.sin(k[d] * math.pi * h / 2) ** 2 for d in range(dim))
+        Aphi = oracle.apply(phi, c=list(c))
+        np.testing.assert_allclose(interior(Aphi), lam * interior(phi), rtol=0, atol=1e-9 * lam)
+
+
+def test_residual_is_f_minus_Au():
+    n = 17
+    rng = np.random.default_rng(1)
+    u, f = rng.standard_normal((n, n)), rng.standard_normal((n, n))
+    r = oracle.residual(u, f)
+    k, beta = (3, 5), (0.3, 1.1)
+    phi = trig(2, n, k, beta)
+    h = 1.0 / (n - 1)
+    lam = sum(4.0 / h**2 * math.sin(kk * math.pi * h / 2) ** 2 for kk in k)
+    r2 = oracle.residual(phi, f)
+    np.testing.assert_allclose(interior(r2), interior(f - lam * phi), atol=1e-9 * lam)
+    assert np.all(r[0] == 0) and np.all(r[:, 0] == 0)
+
+
+# ---------------- smoothers ----------------
+
+@pytest.mark.parametrize("dim,n,omega", [(2, 17, 0.8), (3, 9, 6 / 7)])
+def test_jacobi_amplification_factor(dim, n, omega):
+    h = 1.0 / (n - 1)
+    for k in [(1,) * dim, (2, 7, 5)[:dim], (n - 2,) * dim]:
+        phi = trig(dim, n, k, (-math.pi / 2,) * dim)  # sine modes: zero on the boundary
+        lam = sum(4.0 / h**2 * math.sin(kk * math.pi * h / 2) ** 2 for kk in k)
+        g = 1.0 - omega * lam / (2 * dim / h**2)
+        out = oracle.jacobi(phi, np.zeros_like(phi), sweeps=2, omega=omega)
+        np.testing.assert_allclose(out, g * g * phi, atol=1e-13)
+
+
+def _rb_dense_sor(A, idx, b, x, omega):
+    order = [q for q, p in enumerate(idx) if sum(p) % 2 == 0] + \
+            [q for q, p in enumerate(idx) if sum(p) % 2 == 1]
+    for q in order:
+        x[q] += omega * (b[q] - A[q] @ x) / A[q, q]
+    return x
+
+
+@pytest.mark.parametrize("dim,n,omega,var", [(2, 9, 1.0, False), (2, 9, 1.3, False), (3, 5, 1.0, False),
+                                             (2, 9, 1.0, True), (3, 5, 0.9, True)])
+def test_rbgs_equals_sequential_sweep_red_then_black(dim, n, omega, var):
+    rng = np.random.default_rng(2)
+    shape = (n,) * dim
+    idx = interior_index(dim, n)
+    faces = oracle.node_faces(np.exp(rng.standard_normal(shape))) if var else None
+    A = edge_matrix(dim, n, faces) if var else kron_poisson(dim, n)
+    u = np.zeros(shape)
+    for p in idx:
+        u[p] = rng.standard_normal()
+    f = rng.standard_normal(shape)
+    x = np.array([u[p] for p in idx])
+    b = np.array([f[p] for p in idx])
+    for _ in range(2):
+        x = _rb_dense_sor(A, idx, b, x, omega)
+    out = oracle.rbgs(u, f, sweeps=2, omega=omega, faces=faces)
+    np.testing.assert_allclose([out[p] for p in idx], x, rtol=1e-12, atol=1e-12)
+
+
+# ---------------- transfers ----------------
+
+@pytest.mark.parametrize("dim,nf", [(2, 17), (3, 9)])
+def test_full_weighting_of_trig_modes(dim, nf):
+    h = 1.0 / (nf - 1)
+    nc = (nf - 1) // 2 + 1
+    rng = np.random.default_rng(3)
+    for _ in range(4):
+        k = rng.integers(1, nf - 1, size=dim)
+        beta = rng.uniform(0, 2 * math.pi, size=dim)
+        fc = oracle.restrict(trig(dim, nf, k, beta))
+        expect = np.prod([math.cos(kk * math.pi * h / 2) ** 2 for kk in k]) * trig(dim, nc, k, beta)
+        np.testing.assert_allclose(interior(fc), interior(expect), atol=1e-14)
+        assert np.all(fc[0] == 0)
+
+
+@pytest.mark.parametrize("dim,nc", [(2, 9), (3, 5)])
+def test_interpolation_of_coarse_sine_modes(dim, nc):
+    nf = 2 * (nc - 1) + 1
+    h = 1.0 / (nf - 1)
+    for k in [(1,) * dim, (3, 2, 1)[:dim]]:
+        psi = trig(dim, nc, k, (-math.pi / 2,) * dim)
+        out = oracle.prolong_add(psi, np.zeros((nf,) * dim))
+        phi = trig(dim, nf, k, (-math.pi / 2,) * dim)
+        # even fine index: the fine sine mode; odd: cos(k pi h) times it, per dimension
+        fac = np.ones((nf,) * dim)
+        for d in range(dim):
+            ax = dim - 1 - d
+            shp = [1] * dim
+            shp[ax] = nf
+            v = np.where(np.arange(nf) % 2 == 1, math.cos(k[d] * math.pi * h), 1.0).reshape(shp)
+            fac = fac * v
+        np.testing.assert_allclose(interior(out), interior(fac * phi), atol=1e-14)
+
+
+@pytest.mark.parametrize("dim,nf", [(2, 17), (3, 9)])
+def test_restriction_is_scaled_adjoint_of_interpolation(dim, nf):
+    rng = np.random.default_rng(4)
+    nc = (nf - 1) // 2 + 1
+    r = rng.standard_normal((nf,) * dim)
+    r[...] = r * (np.pad(np.ones((nf - 2,) * dim), 1))
+    e = np.pad(rng.standard_normal((nc - 2,) * dim), 1)
+    lhs = 2**dim * np.sum(oracle.restrict(r) * e)
+    rhs = np.sum(r * oracle.prolong_add(e, np.zeros((nf,) * dim)))
+    assert abs(lhs - rhs) <= 1e-12 * abs(rhs)
+
+
+# ---------------- coarse solve, norm ----------------
+
+@pytest.mark.parametrize("dim,n", [(2, 9), (3, 5), (2, 17)])
+def test_dense_solve_matches_numpy(dim, n):
+    rng = np.random.default_rng(5)
+    f = rng.standard_normal((n,) * dim)
+    u = oracle.dense_solve(f)
+    idx = interior_index(dim, n)
+    x = np.linalg.solve(kron_poisson(dim, n), [f[p] for p in idx])
+    np.testing.assert_allclose([u[p] for p in idx], x, rtol=1e-11, atol=1e-13)
+
+
+def test_three_point_grid_single_unknown():
+    for dim in (2, 3):
+        f = np.zeros((3,) * dim)
+        f[(1,) * dim] = 7.0
+        u = oracle.dense_solve(f)
+        assert u[(1,) * dim] == pytest.approx(7.0 * 0.25 / (2 * dim), rel=1e-15)
+
+
+def test_norm_is_euclidean_over_interior():
+    rng = np.random.default_rng(6)
+    r = rng.standard_normal((65, 65))
+    assert oracle.norm(r) == pytest.approx(np.linalg.norm(interior(r)), rel=1e-14)
+
+
+# ---------------- two-grid factors (LFA) ----------------
+
+def dense_two_grid(dim, n, smoother, omega, nu1, nu2):
+    nc = (n - 1) // 2 + 1
+    H = oracle.Hierarchy(dim, n, coarsest_n=nc, smoother=smoother, omega=omega, nu1=nu1, nu2=nu2)
+    assert H.levels == 2
+    idx = interior_index(dim, n)
+    H.set_rhs(np.zeros((n,) * dim))
+    M = np.zeros((len(idx), len(idx)))
+    for col, p in enumerate(idx):
+        e = np.zeros((n,) * dim)
+        e[p] = 1.0
+        H.set_u(e)
+        H.vcycle()
+        u = H.get_u()
+        M[:, col] = [u[q] for q in idx]
+    return float(np.max(np.abs(np.linalg.eigvals(M))))
+
+
+@pytest.mark.parametrize("dim,n,smoother,omega,nu1,nu2", [
+    (2, 17, oracle.RBGS, 1.0, 2, 1), (2, 17, oracle.RBGS, 1.0, 1, 0), (2, 17, oracle.JACOBI, 0.8, 2, 2),
+    (2, 9, oracle.RBGS, 1.2, 1, 1), (3, 9, oracle.RBGS, 1.0, 2, 1), (3, 9, oracle.JACOBI, 6 / 7, 2, 2),
+])
+def test_two_grid_matrix_matches_discrete_lfa(dim, n, smoother, omega, nu1, nu2):
+    rho_dense = dense_two_grid(dim, n, smoother, omega, nu1, nu2)
+    rho_lfa = lfa.two_grid_discrete(dim, n, smoother, omega, nu1, nu2)
+    assert abs(rho_dense - rho_lfa) < 1e-12
+
+
+def test_lfa_classical_values():
+    # Jacobi smoothing factors (closed forms): 2D omega=4/5 -> 3/5, 3D omega=6/7 -> 5/7.
+    assert lfa.smoothing_factor(2, 0.8) == pytest.approx(3 / 5, abs=1e-12)
+    assert lfa.smoothing_factor(3, 6 / 7, m=8) == pytest.approx(5 / 7, abs=1e-12)
+    # Red-black GS with full weighting and bilinear interpolation, 2D Poisson:
+    # two-grid factors 0.250, 0.074, 0.053 for nu = 1, 2, 3 (standard LFA values).
+    for nu, val in [(1, 0.250), (2, 0.074), (3, 0.053)]:
+        assert lfa.two_grid_lfa(2, lfa.RBGS, 1.0, nu, 0, m=48) == pytest.approx(val, abs=1.5e-3)
+
+
+@pytest.mark.parametrize("smoother,omega,nu1,nu2", [(oracle.RBGS, 1.0, 2, 1), (oracle.JACOBI, 0.8, 2, 2)])
+def test_measured_two_grid_factor_within_lfa(smoother, omega, nu1, nu2):
+    n = 65
+    H = oracle.Hierarchy(2, n, coarsest_n=33, smoother=smoother, omega=omega, nu1=nu1, nu2=nu2)
+    H.set_rhs(np.zeros((n, n)))
+    H.set_u(synth.random_u0(2, n, 3))
+    prev = H.residual_norm()
+    for _ in range(20):
+        H.vcycle()
+        cur = H.residual_norm()
+        fac, prev = cur / prev, cur
+    assert fac <= 1.1 * lfa.two_grid_discrete(2, n, smoother, omega, nu1, nu2)
+
+
+# ---------------- whole solver ----------------
+
+def test_paper_settings_fixture():
+    g = json.load(open(os.path.join(GOLDEN, "paper_settings.json")))
+    p = g["layer3_mgparameter"]
+    # 129^2 nodes (127^2 unknowns) coarsened by 2 down to 3^2: the paper's 7 levels.
+    H = oracle.Hierarchy(2, 129, nu1=p["nprae"], nu2=p["npost"], omega=p["omega"])
+    assert H.levels == p["nlevels"]
+    assert [H.level_n(l) for l in range(H.levels)] == [129, 65, 33, 17, 9, 5, 3]
+    # Layer 2: 4096 intervals per direction = accuracy 2^-12; Table 2: 4095^2 unknowns.
+    d = g["layer2_domain"]
+    assert d["xsize"] == 2 ** d["accuracy_exponent"]
+    assert (d["xsize"] - 1) ** 2 == g["table2_workload"]["unknowns_2d_node_based"]
+    assert (2 ** 8 - 1) ** 3 == g["table2_workload"]["unknowns_3d"]
+
+
+def test_config1_converges_to_closed_form_discrete_solution():
+    # -Lap u = 2 pi^2 sin(pi x) sin(pi y): the discrete solution is c_h times the
+    # continuous one, c_h = (pi h/2)^2 / sin^2(pi h/2).
+    n = 129
+    h = 1.0 / (n - 1)
+    H = oracle.Hierarchy(2, n, nu1=2, nu2=1, omega=1.0)
+    H.set_rhs(synth.sine_rhs(2, n))
+    rho = H.solve(1e-12, 30)
+    assert rho[-1] <= 1e-12
+    u = H.get_u()
+    ch = (math.pi * h / 2) ** 2 / math.sin(math.pi * h / 2) ** 2
+    exact = synth.sine_solution(2, n)
+    assert np.abs(u - ch * exact).max() < 1e-12
+    assert np.abs(u - exact).max() == pytest.approx(ch - 1, rel=1e-6)
+    assert ch - 1 == pytest.approx(5.02e-5, rel=1e-3)
+
+
+def test_second_order_discretisation_error():
+    errs = []
+    for n in (17, 33, 65):
+        H = oracle.Hierarchy(3, n, smoother=oracle.JACOBI, omega=6 / 7, nu1=2, nu2=2)
+        H.set_rhs(synth.sine_rhs(3, n))
+        H.solve(1e-12, 40)
+        errs.append(np.abs(H.get_u() - synth.sine_solution(3, n)).max())
+    ratios = [errs[i] / errs[i + 1] for i in range(2)]
+    assert all(3.9 < r < 4.1 for r in ratios), ratios
+
+
+@pytest.mark.parametrize("dim,n,var", [(2, 17, False), (3, 9, False), (2, 17, True), (3, 9, True)])
+def test_vcycle_converges_to_dense_solution(dim, n, var):
+    rng = np.random.default_rng(7)
+    shape = (n,) * dim
+    k = np.exp(rng.standard_normal(shape)) if var else None
+    f = rng.uniform(-1, 1, shape)
+    ub = np.zeros(shape)
+    ub[0] = rng.uniform(-1, 1, shape[1:])  # non-zero Dirichlet values on one face
+    H = oracle.Hierarchy(dim, n, knode=k, nu1=2, nu2=1)
+    H.set_rhs(f)
+    H.set_u(ub)
+    H.solve(1e-14, 60)
+    faces = oracle.node_faces(k) if var else None
+    ref = oracle.dense_solve(f, u_boundary=ub, faces=faces)
+    idx = interior_index(dim, n)
+    A = edge_matrix(dim, n, faces) if var else kron_poisson(dim, n)
+    # independent check of the dense solve itself through the edge/Kronecker matrix
+    x = np.array([ref[p] for p in idx])
+    bnd = oracle.apply(ub, faces=faces)
+    b = np.array([f[p] - bnd[p] for p in idx])
+    np.testing.assert_allclose(A @ x, b, rtol=1e-10, atol=1e-10 * np.abs(b).max())
+    np.testing.assert_allclose(H.get_u(), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+def test_paper_poisson_convergence_claim():
+    # Sec. 4: for Poisson the L2 residual drops by more than 1e8 within 5 V(2,2) cycles.
+    g = json.load(open(os.path.join(GOLDEN, "paper_settings.json")))["poisson_convergence_claim"]
+    n = 513
+    H = oracle.Hierarchy(2, n, smoother=oracle.RBGS, omega=1.0, nu1=g["nu1"], nu2=g["nu2"])
+    H.set_rhs(np.zeros((n, n)))
+    H.set_u(synth.random_u0(2, n, 0x5EED0006))
+    r0 = H.residual_norm()
+    for _ in range(g["cycles"]):
+        H.vcycle()
+    assert r0 / H.residual_norm() > g["min_residual_reduction"]
+
+
+def test_defect_correction_reproduces_plain_iteration():
+    # The V-cycle is an affine iteration u <- u + B (f - A u) with B = V(0, .),
+    # so FP64 defect correction with one inner cycle gives the same history.
+    for dim, n, sm, om, nu in [(2, 65, oracle.RBGS, 1.0, (2, 1)), (3, 17, oracle.JACOBI, 6 / 7, (2, 2))]:
+        f = synth.uniform_rhs(dim, n, 9)
+        H1 = oracle.Hierarchy(dim, n, smoother=sm, omega=om, nu1=nu[0], nu2=nu[1])
+        H1.set_rhs(f)
+        rho1 = H1.solve(1e-11, 40)
+        H2 = oracle.Hierarchy(dim, n, smoother=sm, omega=om, nu1=nu[0], nu2=nu[1])
+        H2.set_rhs(f)
+        rho2 = H2.dc_solve(1e-11, 40)
+        assert len(rho1) == len(rho2)
+        np.testing.assert_allclose(rho2, rho1, rtol=1e-6, atol=1e-13)
+        np.testing.assert_allclose(H2.get_u(), H1.get_u(), atol=1e-12 * np.abs(H1.get_u()).max())
+
+
+# ---------------- variable coefficients ----------------
+
+def test_unit_coefficient_reduces_to_poisson_bitwise():
+    n = 33
+    f = synth.uniform_rhs(2, n, 1)
+    H1 = oracle.Hierarchy(2, n)
+    H1.set_rhs(f)
+    H2 = oracle.Hierarchy(2, n, knode=np.ones((n, n)))
+    H2.set_rhs(f)
+    assert np.array_equal(H1.solve(1e-12, 20), H2.solve(1e-12, 20))
+    assert np.array_equal(H1.get_u(), H2.get_u())
+
+
+def test_variable_operator_matches_edge_sum_and_is_spd():
+    for dim, n in [(2, 9), (3, 5)]:
+        rng = np.random.default_rng(8)
+        faces = oracle.node_faces(np.exp(rng.standard_normal((n,) * dim)))
+        A = assembled(dim, n, faces=faces)
+        np.testing.assert_allclose(A, edge_matrix(dim, n, faces), rtol=1e-13, atol=1e-9)
+        assert np.all(np.linalg.eigvalsh(0.5 * (A + A.T)) > 0)
+        np.testing.assert_allclose(A, A.T, rtol=0, atol=1e-9)
+
+
+def test_node_faces_are_harmonic_means():
+    rng = np.random.default_rng(9)
+    k = np.exp(rng.standard_normal((9, 9)))
+    kx, ky = oracle.node_faces(k)
+    assert kx[3, 4] == pytest.approx(2 * k[3, 4] * k[3, 5] / (k[3, 4] + k[3, 5]), rel=1e-15)
+    assert ky[3, 4] == pytest.approx(2 * k[3, 4] * k[4, 4] / (k[3, 4] + k[4, 4]), rel=1e-15)
+    assert np.all(kx[:, -1] == 0) and np.all(ky[-1, :] == 0)
+
+
+def test_coarse_faces_follow_series_rule():
+    # Layered medium k = k(x): a discrete A-harmonic function (constant flux q,
+    # u_{i+1} - u_i = q h / k_{i+1/2}) restricted by injection must be A_H-harmonic
+    # on the coarse grid iff coarse faces combine the two fine faces in series.
+    nf = 33
+    h = 1.0 / (nf - 1)
+    rng = np.random.default_rng(10)
+    kx1 = np.exp(rng.standard_normal(nf))
+    k = np.tile(kx1, (nf, 1))
+    faces = oracle.node_faces(k)
+    q = 0.7
+    u1 = np.concatenate([[0.0], np.cumsum(q * h / faces[0][0, :-1])])
+    u = np.tile(u1, (nf, 1))
+    assert np.abs(interior(oracle.apply(u, faces=faces))).max() < 1e-9
+    cf = oracle.coarsen_faces(faces)
+    uc = u[::2, ::2]
+    assert np.abs(interior(oracle.apply(uc, faces=cf))).max() < 1e-9
+    # the same check fails for the arithmetic mean of the two fine faces
+    bad = [cf[0].copy(), cf[1]]
+    bad[0][:, :-1] = 0.5 * (faces[0][::2, 0:-1:2] + faces[0][::2, 1::2])
+    assert np.abs(interior(oracle.apply(uc, faces=bad))).max() > 1e-3
+
+
+def test_variable_coefficient_second_order():
+    # k = 1 + sin(2 pi x) sin(2 pi y)/2, u = sin(pi x) sin(pi y), f = -div(k grad u).
+    errs = []
+    for n in (33, 65, 129):
+        x = synth.coords(n)
+        X, Y = np.meshgrid(x, x)  # X varies along the last axis
+        pi = math.pi
+        k = 1 + 0.5 * np.sin(2 * pi * X) * np.sin(2 * pi * Y)
+        kx_ = pi * np.cos(2 * pi * X) * np.sin(2 * pi * Y)
+        ky_ = pi * np.sin(2 * pi * X) * np.cos(2 * pi * Y)
+        u = np.sin(pi * X) * np.sin(pi * Y)
+        ux, uy = pi * np.cos(pi * X) * np.sin(pi * Y), pi * np.sin(pi * X) * np.cos(pi * Y)
+        f = -(kx_ * ux + ky_ * uy) + k * 2 * pi**2 * u
+        H = oracle.Hierarchy(2, n, knode=k)
+        H.set_rhs(f)
+        H.solve(1e-12, 40)
+        errs.append(np.abs(H.get_u() - u).max())
+    ratios = [errs[i] / errs[i + 1] for i in range(2)]
+    assert all(3.5 < r < 4.5 for r in ratios), (errs, ratios)
