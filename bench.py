@@ -1,0 +1,323 @@
+"""Benchmark of the GB300 multigrid solver (one JSON line on rank 0).
+
+Workload (default): 2D Poisson, 5-point FD, homogeneous Dirichlet,
+8193 x 8193 nodes, right-hand side i.i.d. U[-1, 1] from a seed; V(2,1) with
+red-black Gauss-Seidel (omega 1), full weighting, bilinear interpolation,
+coarsening to 3 x 3. One step = one solve from u = 0 to a relative residual
+of 1e-10 with FP32-stored inner V-cycles inside FP64 defect correction; the
+plain FP64 V-cycle solve of the same problem is timed beside it.
+
+value = solves per second over all ranks (1 / time-to-1e-10 per GPU; ranks
+run independent replicas). e2e = the same solve through the public API with
+the right-hand side uploaded from pinned host memory and the solution read
+back every step.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload on the host cores and prints the same line with impl=reference.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-10 rel. residual & V-cycles/s, HBM GB/s vs 8 TB/s; p50/p99 serve latency"
+WORKLOAD = {
+    "workload": "2D Poisson -Lap u = f, 5-point FD, Dirichlet, 8193x8193 nodes, f ~ U[-1,1] i.i.d. (seed 0x5EED0002); "
+                "V(2,1) RBGS omega=1, full weighting, bilinear, 13 levels to 3x3; FP32-stored inner cycles in FP64 "
+                "defect correction to 1e-10 (plain FP64 V-cycle timed beside it)",
+    "dim": 2, "n": 8193, "tol": 1e-10, "smoother": "rbgs", "omega": 1.0, "nu1": 2, "nu2": 1,
+    "precision": "fp32_dc", "seed": 0x5EED0002,
+    "l2": "inputs larger than L2 (each field 268-537 MB > 129 MB L2)",
+}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = sorted(float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit())
+        mx = max((float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 3 + i and s[3 + i].lower().startswith("active")})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1406_5369_gb300 import Solver, load
+    from paper_1406_5369_gb300 import build as b
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    b.build()
+    load()
+    W = WORKLOAD
+    dim, n = W["dim"], W["n"]
+    f = synth.uniform_rhs(dim, n, W["seed"])
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+
+    def make(prec):
+        return Solver(dim, n, smoother=W["smoother"], omega=W["omega"], nu1=W["nu1"], nu2=W["nu2"],
+                      maxit=60, precision=prec)
+
+    f_dev = torch.from_numpy(f).to(dev)
+    s = make(W["precision"])
+    s.set_rhs(f_dev)
+
+    def step():
+        s.set_solution(None)
+        it, rr, _ = s.solve(W["tol"])
+        return it, rr
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    iters = []
+    launches0 = s.kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            it, rr = step()
+            iters.append(it)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    launches = s.kernel_launches() - launches0
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    cycles = iters[-1]
+
+    # plain FP64 V-cycle solve of the same problem (beside the headline)
+    s64 = make("fp64")
+    s64.set_rhs(f_dev)
+    s64.set_solution(None)
+    it64, _, _ = s64.solve(W["tol"])
+    t64 = []
+    for _ in range(2):
+        s64.set_solution(None)
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        it64, _, _ = s64.solve(W["tol"])
+        torch.cuda.synchronize()
+        t64.append(time.perf_counter() - a)
+    fp64_ms = 1e3 * min(t64)
+    del s64
+
+    # e2e: public API with host buffers (pinned), H2D of f and D2H of u every step
+    f_pin = torch.from_numpy(f).pin_memory()
+    u_pin = torch.empty_like(f_pin).pin_memory()
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.set_rhs(f_pin)
+        s.set_solution(None)
+        s.solve(W["tol"])
+        s.get_solution(u_pin)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - e0) / args.steps
+    nbytes_field = f.nbytes
+
+    # dominant kernel, timed through its C-ABI call on the same stream and data:
+    # one FP32 RBGS sweep (two colour half-sweeps) of the finest inner level.
+    hbm_peak, peak_kind = peaks()
+    s.set_field(0, "u", np.zeros_like(f))
+    reps = 20
+    for _ in range(3):
+        s.smooth(0, 1)
+    torch.cuda.synchronize()
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    for _ in range(reps):
+        s.smooth(0, 1)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    sweep_ms = k0.elapsed_time(k1) / reps
+    w = 4  # FP32 words
+    sweep_bytes = 3 * n * n * w  # read u, f; write u (one word each per node)
+    achieved = sweep_bytes / (sweep_ms * 1e-3) / 1e9
+
+    rec = {
+        "metric": METRIC,
+        "value": world * 1e3 / ms,
+        "unit": "solves/s (to 1e-10 rel. residual; 1/time-to-1e-10 per GPU)",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 inner / f64 outer",
+        "data": "synthetic",
+        "config": {k: v for k, v in W.items()},
+        "time_to_tol_s": ms / 1e3,
+        "cycles_to_tol": cycles,
+        "vcycles_per_s": cycles / (ms / 1e3),
+        "fp64_plain": {"time_to_tol_s": fp64_ms / 1e3, "cycles": it64, "vcycles_per_s": it64 / (fp64_ms / 1e3)},
+        "e2e": {"value": world / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": nbytes_field,
+                "d2h_bytes_per_step": nbytes_field},
+        "roofline": {"bound": "hbm", "kernel": "FP32 RBGS sweep on the finest inner level (2 launches)",
+                     "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                     "peak_kind": peak_kind, "traffic": None,
+                     "bytes_per_launch_model": "3 words x n nodes per sweep",
+                     "timed": "alone through mg_smooth(0,1), 20 reps, CUDA events"},
+        "clocks": clk.summary(),
+        "gpu_launches": int(launches),
+    }
+    rec["config"]["parallelism"] = f"replicas x{world}"
+    if rank == 0 and not args.no_cpu_baseline:
+        rec["cpu_baseline"] = cpu_baseline(args, cycles)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(rec), flush=True)
+
+
+# ------------------------------------------------------------------ oracle timing
+
+def oracle_sample(cycles_to_tol, ncycles=2):
+    """Times ncycles oracle V-cycles on the full grid and extrapolates to a solve."""
+    import synth
+    import oracle
+    W = WORKLOAD
+    dim, n = W["dim"], W["n"]
+    f = synth.uniform_rhs(dim, n, W["seed"])
+    H = oracle.Hierarchy(dim, n, smoother=oracle.RBGS, omega=W["omega"], nu1=W["nu1"], nu2=W["nu2"])
+    H.set_rhs(f)
+    t0 = time.perf_counter()
+    r0 = H.residual_norm()
+    t_norm = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for _ in range(ncycles):
+        H.vcycle()
+    t_cyc = (time.perf_counter() - t0) / ncycles
+    t_solve = t_norm + cycles_to_tol * (t_cyc + t_norm)
+    return t_solve, t_cyc, t_norm, r0
+
+
+def cpu_baseline(args, cycles_to_tol):
+    t_solve, t_cyc, t_norm, _ = oracle_sample(cycles_to_tol)
+    return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"2 FP64 oracle V(2,1) cycles + 1 residual norm on the full 8193^2 grid "
+                      f"({t_cyc:.2f} s/cycle, {t_norm:.2f} s/norm), extrapolated to the "
+                      f"{cycles_to_tol} cycles the solve takes to 1e-10"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    cycles = 10  # the plain FP64 V(2,1) solve of this workload reaches 1e-10 in 10 cycles
+    times = []
+    for _ in range(args.warmup + args.steps):
+        t_solve, t_cyc, t_norm, _ = oracle_sample(cycles, ncycles=1)
+        times.append(t_solve)
+    t = sum(times[args.warmup:]) / max(1, args.steps)
+    rec = {
+        "metric": METRIC, "impl": "reference", "value": 1.0 / t,
+        "unit": "solves/s (to 1e-10 rel. residual; 1/time-to-1e-10 per GPU)",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": dict(WORKLOAD, parallelism="1 host core"),
+        "cpu_baseline": {"value": 1.0 / t, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": "per step: 1 FP64 oracle V(2,1) cycle + 1 residual norm on the full "
+                                   "8193^2 grid, extrapolated to the 10 cycles of the solve"},
+        "e2e": {"value": 1.0 / t, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(rec), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * mg.h - C ABI of the GB300 geometric multigrid library (libmg.so).
+ *
+ * The library solves the node-based finite-difference problems of
+ * Koestler et al., "A Scala Prototype to Generate Multigrid Solver
+ * Implementations for Different Problems and Target Multi-Core Platforms"
+ * (arXiv:1406.5369):
+ *
+ *   -sum_d c_d d^2u/dx_d^2 = f  in [0,1]^dim,  u = g on the boundary   (Eq. 1,
+ *   written there with the opposite sign; this library uses the SPD sign), or
+ *   -div(k grad u) = f with a node-wise diffusivity k (harmonic-mean faces),
+ *
+ * with the recursive V-cycle of Algorithm 1 (Sec. 2.3): red-black
+ * Gauss-Seidel or omega-Jacobi smoothing, residual, full-weighting
+ * restriction, bi-/trilinear interpolation with correction and a direct
+ * solve on the coarsest grid; coarse operators are rediscretised (Table 1).
+ *
+ * Grid layout seen by callers: a grid has n = 2^m + 1 nodes per dimension
+ * including boundary nodes (h = 1/(n-1)); arrays are dense FP64 with x
+ * fastest: element (i, j[, k]) at i + n*(j + n*k). Inside the arena each
+ * level is stored with rows padded to 128 bytes.
+ *
+ * Pointers: every `const double *` input and `double *` output may be host
+ * or device memory (the library copies with cudaMemcpyDefault); it is
+ * borrowed for the duration of the call only. The arena is device memory
+ * owned by the caller and must outlive the context. The library never
+ * allocates device memory; it allocates only the small host-side context.
+ *
+ * Errors: every call returns an mg_status; no call aborts or throws. The
+ * message of the last failure on the calling thread is mg_last_error().
+ *
+ * Streams: calls are asynchronous on options.stream (a cudaStream_t, NULL
+ * = the legacy default stream) except mg_residual_norm, mg_solve,
+ * mg_get_solution and mg_get_field, which synchronise that stream before
+ * returning.
+ */
+#ifndef MG_H
+#define MG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MG_OK = 0,
+  MG_EINVAL = 1,   /* bad argument: size not 2^m+1, level out of range, NULL ... */
+  MG_ENOMEM = 2,   /* arena smaller than mg_workspace_bytes() */
+  MG_ECUDA = 3,    /* a CUDA runtime call failed (message in mg_last_error) */
+  MG_ENOCONV = 4,  /* residual became NaN/Inf or maxit reached above tol */
+  MG_ETIMEOUT = 5  /* a bounded device-side wait gave up */
+} mg_status;
+
+/* Smoothers of the feature model (Table 1): omega red-black Gauss-Seidel
+ * (Sec. 2.4 GaussSeidel, "order rb": red = i+j[+k] even, updated first) and
+ * omega-Jacobi (Sec. 4, Table 2 uses omega = 0.8). */
+typedef enum { MG_RBGS = 0, MG_JACOBI = 1 } mg_smoother;
+
+/* Data type of the V-cycle (Table 1 "single/double accuracy"; Sec. 5).
+ * MG_FP64: every level stored and computed in FP64.
+ * MG_FP32_DC / MG_BF16_DC: defect correction - an FP64 outer loop
+ * (residual, solution update) around inner V-cycles stored in FP32 or BF16
+ * and computed in FP32; the coarsest direct solve stays FP64. */
+typedef enum { MG_FP64 = 0, MG_FP32_DC = 1, MG_BF16_DC = 2 } mg_precision;
+
+/* Per-level fields addressable by mg_set_field / mg_get_field. */
+typedef enum { MG_FIELD_U = 0, MG_FIELD_F = 1, MG_FIELD_R = 2 } mg_field;
+
+/* Constant stencil -sum_d c_d d^2/dx_d^2 (Sec. 2.2: a constant 5-/7-point
+ * stencil stored matrix-free). Poisson: cx = cy = cz = 1. cz is ignored in 2D. */
+typedef struct { double cx, cy, cz; } mg_const_stencil;
+
+/* Boundary condition (Eq. 1b). kind 0 = Dirichlet. dirichlet_values: NULL
+ * for homogeneous, else a dense n^dim FP64 array of which only boundary
+ * nodes are read. */
+typedef struct { int kind; const double *dirichlet_values; } mg_boundary;
+
+/* Layer-3 parameters (Sec. 2.3 mgparameter) plus implementation choices.
+ * smoother, omega       : smoother and its relaxation weight
+ * nu1, nu2              : pre- and post-smoothing sweeps (0..8)
+ * coarsest_n            : nodes per dimension of the coarsest grid; 3 (one
+ *                         unknown, solved exactly) is the only value accepted
+ * maxit                 : V-cycles (outer steps for *_DC) allowed in mg_solve
+ * precision             : see mg_precision
+ * stream                : cudaStream_t for every launch, NULL = default stream
+ * fuse                  : 1 = fused fine-level kernels where available,
+ *                         0 = one kernel per operator (same results up to
+ *                         rounding order of FMA contraction)
+ * use_graph             : 1 = replay each V-cycle from a captured CUDA graph */
+typedef struct {
+  mg_smoother smoother;
+  double omega;
+  int nu1, nu2;
+  int coarsest_n;
+  int maxit;
+  mg_precision precision;
+  void *stream;
+  int fuse;
+  int use_graph;
+} mg_options;
+
+typedef struct mg_ctx mg_ctx;
+
+/* Fills *opt with RBGS, omega 1, V(2,1), coarsest 3, maxit 50, FP64,
+ * default stream, fuse 1, use_graph 1 (the Layer-3 defaults of Sec. 2.3). */
+void mg_default_options(mg_options *opt);
+
+/* Bytes of device arena mg_create needs for this problem (0 if the
+ * arguments are invalid). variable_k != 0 reserves face coefficients. */
+size_t mg_workspace_bytes(int dim, int n, int variable_k, const mg_options *opt);
+
+/* Builds the grid hierarchy n, (n-1)/2+1, ..., coarsest_n inside the
+ * caller's arena (Sec. 2.2 Discrete_Domain ... levels, coarsefac = 2).
+ * stencil: NULL = Poisson. k: NULL for the constant stencil, else a dense
+ * n^dim FP64 array of node diffusivities (> 0); face coefficients are the
+ * harmonic means of the two nodes times c_d, and coarse faces combine the
+ * two collinear fine faces in series, 2/(1/k_a + 1/k_b) (rediscretisation,
+ * Table 1). bc: NULL = homogeneous Dirichlet. The solution starts at zero
+ * (plus boundary values), the right-hand side at zero.
+ * Returns MG_EINVAL for dim not 2/3, n not 2^m+1 with m >= 1, bad options;
+ * MG_ENOMEM if arena_bytes < mg_workspace_bytes. On success *out owns a
+ * host-side context released by mg_destroy. */
+mg_status mg_create(int dim, int n, const mg_const_stencil *stencil, const double *k,
+                    const mg_boundary *bc, const mg_options *opt, void *arena,
+                    size_t arena_bytes, mg_ctx **out);
+
+/* Releases the host context (the arena stays the caller's). NULL is a no-op. */
+mg_status mg_destroy(mg_ctx *ctx);
+
+/* Number of levels L (level 0 finest, L-1 coarsest) and nodes per dimension
+ * of a level (-1 if out of range). */
+int mg_num_levels(const mg_ctx *ctx);
+int mg_level_size(const mg_ctx *ctx, int level);
+
+/* Finest-level right-hand side f (dense n^dim FP64; boundary entries ignored). */
+mg_status mg_set_rhs(mg_ctx *ctx, const double *f);
+
+/* Finest-level initial guess (Sec. 2.1 "Unknown solution = init...");
+ * u0 == NULL sets zero. Boundary nodes always keep the Dirichlet values. */
+mg_status mg_set_solution(mg_ctx *ctx, const double *u0);
+
+/* Copies the finest-level solution (dense n^dim FP64, boundary included). */
+mg_status mg_get_solution(mg_ctx *ctx, double *u);
+
+/* Per-level access used by operator-level tests and tools: level ell's
+ * solution U, right-hand side F or residual R, as dense n_ell^dim FP64
+ * (converted from/to the level's storage type). In the *_DC precisions
+ * the levels are the inner hierarchy (U = correction e, F = defect d). */
+mg_status mg_set_field(mg_ctx *ctx, int level, mg_field field, const double *src);
+mg_status mg_get_field(mg_ctx *ctx, int level, mg_field field, double *dst);
+
+/* `sweeps` smoothing steps on `level` (Algorithm 1 presmoothing /
+ * postsmoothing; Sec. 2.4 GaussSeidel). MG_EINVAL if level is out of range
+ * or sweeps < 0. */
+mg_status mg_smooth(mg_ctx *ctx, int level, int sweeps);
+
+/* r_level = f_level - A_level u_level at interior nodes (Algorithm 1,
+ * "compute residual"; Sec. 2.4 Residual). */
+mg_status mg_residual(mg_ctx *ctx, int level);
+
+/* f_{level+1} = R r_level with full weighting (Algorithm 1 "restrict
+ * residual"; Sec. 2.4 Restrict, ToCoarse). MG_EINVAL on the coarsest level. */
+mg_status mg_restrict(mg_ctx *ctx, int level);
+
+/* u_level += P u_{level+1} with bi-/trilinear interpolation at interior
+ * nodes (Algorithm 1 "prolongate error and do coarse grid correction";
+ * Sec. 2.4 interpolatecorr, ToFine). MG_EINVAL on the coarsest level. */
+mg_status mg_prolongate(mg_ctx *ctx, int level);
+
+/* Exact solve on the coarsest level, in FP64 (Algorithm 1, coarsest level). */
+mg_status mg_coarse_solve(mg_ctx *ctx);
+
+/* One V(nu1,nu2)-cycle on the finest level (Algorithm 1; Sec. 2.4 VCycle).
+ * In the *_DC precisions: one defect-correction step - FP64 residual of
+ * the outer problem, one inner V-cycle from zero on it, FP64 update. */
+mg_status mg_vcycle(mg_ctx *ctx);
+
+/* Euclidean norm of f - A u over the interior of `level` (Sec. 2.4
+ * L2Residual), accumulated in FP64; synchronises the stream. In the *_DC
+ * precisions level 0 means the outer FP64 problem. */
+mg_status mg_residual_norm(mg_ctx *ctx, int level, double *out);
+
+/* Driver loop of the Layer-4 Application (Sec. 2.4): r0 = ||f - A u||,
+ * then V-cycles (defect-correction steps for *_DC) until
+ * ||r_k||/r0 <= tol or maxit. *iters = cycles done, *relres = last ratio;
+ * history (may be NULL) receives maxit+1 doubles, rho_0 = 1 .. rho_iters.
+ * Returns MG_ENOCONV if the residual is not finite or tol was not reached. */
+mg_status mg_solve(mg_ctx *ctx, double tol, int *iters, double *relres, double *history);
+
+/* Diagnostic with no counterpart in the paper: the number of CUDA kernels
+ * this context has launched so far, counting each kernel node of a
+ * replayed graph (memset/copy operations are not counted). */
+unsigned long long mg_kernel_launches(const mg_ctx *ctx);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *mg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MG_H */

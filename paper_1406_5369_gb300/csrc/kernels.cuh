@@ -1,0 +1,389 @@
+// Device kernels of the multigrid V-cycle (Algorithm 1 of the paper,
+// Sec. 2.3-2.4), templated on dimension, storage type and stencil kind.
+//
+// Storage types: double (FP64 levels), float, __nv_bfloat16 (inner levels of
+// defect correction). Arithmetic runs in double for double storage and in
+// float otherwise. Every kernel touches interior nodes only, so boundary
+// nodes keep their Dirichlet values (finest level) or zero (coarse levels).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "mg_internal.h"
+
+namespace mg {
+
+typedef __nv_bfloat16 bf16;
+
+template <typename T> struct CT { typedef float type; };
+template <> struct CT<double> { typedef double type; };
+
+__device__ __forceinline__ double ld(const double *p) { return *p; }
+__device__ __forceinline__ float ld(const float *p) { return *p; }
+__device__ __forceinline__ float ld(const bf16 *p) { return __bfloat162float(*p); }
+
+__device__ __forceinline__ void st(double *p, double v) { *p = v; }
+__device__ __forceinline__ void st(float *p, double v) { *p = (float)v; }
+__device__ __forceinline__ void st(bf16 *p, double v) { *p = __float2bfloat16_rn((float)v); }
+__device__ __forceinline__ void st(float *p, float v) { *p = v; }
+__device__ __forceinline__ void st(bf16 *p, float v) { *p = __float2bfloat16_rn(v); }
+__device__ __forceinline__ void st(double *p, float v) { *p = (double)v; }
+
+// Geometry of a level in kernel form.
+struct Geo {
+  int n;
+  long long sy;  // row stride (pitch)
+  long long sz;  // plane stride
+};
+
+__host__ __forceinline__ Geo geo_of(const Level &L) {
+  Geo g;
+  g.n = L.n;
+  g.sy = L.pitch;
+  g.sz = L.plane;
+  return g;
+}
+
+// Stencil coefficients in compute type C.
+template <typename C> struct Sten {
+  const C *kf0, *kf1, *kf2;  // faces (variable stencil)
+  C c0, c1, c2;              // constant coefficients
+  C inv_h2;
+  C diag;                    // constant stencil: 2 (c0+c1[+c2]) / h^2
+};
+
+template <typename C> __host__ Sten<C> sten_of(const Level &L) {
+  Sten<C> s;
+  s.kf0 = (const C *)L.kf[0];
+  s.kf1 = (const C *)L.kf[1];
+  s.kf2 = (const C *)L.kf[2];
+  s.c0 = (C)L.c[0];
+  s.c1 = (C)L.c[1];
+  s.c2 = (C)L.c[2];
+  s.inv_h2 = (C)L.inv_h2;
+  double d = 2.0 * (L.c[0] + L.c[1] + (L.dim == 3 ? L.c[2] : 0.0)) * L.inv_h2;
+  s.diag = (C)d;
+  return s;
+}
+
+// (A u)_p and diag_p at node p. Constant stencil:
+//   A u = h^-2 sum_d c_d (2 u_p - u_{p-e_d} - u_{p+e_d});
+// variable stencil (conservative form):
+//   A u = h^-2 sum_d [k_{p+e_d/2} (u_p - u_{p+e_d}) + k_{p-e_d/2} (u_p - u_{p-e_d})].
+template <int DIM, bool VAR, typename T, typename C>
+__device__ __forceinline__ void apply_at(const T *__restrict__ u, long long p, const Geo &g,
+                                         const Sten<C> &s, C &Au, C &diag) {
+  C u0 = ld(u + p);
+  C uw = ld(u + p - 1), ue = ld(u + p + 1);
+  C us = ld(u + p - g.sy), un = ld(u + p + g.sy);
+  if (!VAR) {
+    C acc = s.c0 * ((u0 + u0) - uw - ue) + s.c1 * ((u0 + u0) - us - un);
+    if (DIM == 3) {
+      C ud = ld(u + p - g.sz), uu = ld(u + p + g.sz);
+      acc += s.c2 * ((u0 + u0) - ud - uu);
+    }
+    Au = acc * s.inv_h2;
+    diag = s.diag;
+  } else {
+    C kxp = s.kf0[p], kxm = s.kf0[p - 1], kyp = s.kf1[p], kym = s.kf1[p - g.sy];
+    C acc = kxp * (u0 - ue) + kxm * (u0 - uw) + kyp * (u0 - un) + kym * (u0 - us);
+    C dg = kxp + kxm + kyp + kym;
+    if (DIM == 3) {
+      C ud = ld(u + p - g.sz), uu = ld(u + p + g.sz);
+      C kzp = s.kf2[p], kzm = s.kf2[p - g.sz];
+      acc += kzp * (u0 - uu) + kzm * (u0 - ud);
+      dg += kzp + kzm;
+    }
+    Au = acc * s.inv_h2;
+    diag = dg * s.inv_h2;
+  }
+}
+
+// Thread -> node map of the simple kernels: x from the block/thread x index,
+// y from blockIdx.y, z from blockIdx.z.
+struct Idx {
+  int i, j, k;
+  long long p;
+  bool interior;
+};
+
+template <int DIM> __device__ __forceinline__ Idx node_index(const Geo &g) {
+  Idx t;
+  t.i = blockIdx.x * blockDim.x + threadIdx.x;
+  t.j = blockIdx.y;
+  t.k = DIM == 3 ? (int)blockIdx.z : 0;
+  t.p = (long long)t.k * g.sz + (long long)t.j * g.sy + t.i;
+  t.interior = t.i >= 1 && t.i <= g.n - 2 && t.j >= 1 && t.j <= g.n - 2 &&
+               (DIM == 2 || (t.k >= 1 && t.k <= g.n - 2));
+  return t;
+}
+
+// ---------------------------------------------------------------- smoothers
+
+// Half-sweep of omega-RBGS (Sec. 2.4 GaussSeidel, order rb): nodes with
+// (i+j[+k]) % 2 == color get u += omega (f - A u) / diag. Same-colour nodes
+// do not couple in a 5-/7-point stencil, so all of them update at once.
+template <int DIM, typename T, bool VAR>
+__global__ void k_rbgs_half(T *__restrict__ u, const T *__restrict__ f, Geo g, Sten<typename CT<T>::type> s,
+                            int color, typename CT<T>::type omega) {
+  typedef typename CT<T>::type C;
+  Idx t = node_index<DIM>(g);
+  if (!t.interior || ((t.i + t.j + t.k) & 1) != color) return;
+  C Au, dg;
+  apply_at<DIM, VAR>(u, t.p, g, s, Au, dg);
+  C u0 = ld(u + t.p);
+  st(u + t.p, u0 + omega * (ld(f + t.p) - Au) / dg);
+}
+
+// omega-Jacobi: uout = uin + omega (f - A uin) / diag.
+template <int DIM, typename T, bool VAR>
+__global__ void k_jacobi(const T *__restrict__ uin, T *__restrict__ uout, const T *__restrict__ f, Geo g,
+                         Sten<typename CT<T>::type> s, typename CT<T>::type omega) {
+  typedef typename CT<T>::type C;
+  Idx t = node_index<DIM>(g);
+  if (!t.interior) return;
+  C Au, dg;
+  apply_at<DIM, VAR>(uin, t.p, g, s, Au, dg);
+  st(uout + t.p, ld(uin + t.p) + omega * (ld(f + t.p) - Au) / dg);
+}
+
+// ---------------------------------------------------------------- residual
+
+template <int DIM, typename T, bool VAR>
+__global__ void k_residual(const T *__restrict__ u, const T *__restrict__ f, T *__restrict__ r, Geo g,
+                           Sten<typename CT<T>::type> s) {
+  typedef typename CT<T>::type C;
+  Idx t = node_index<DIM>(g);
+  if (!t.interior) return;
+  C Au, dg;
+  apply_at<DIM, VAR>(u, t.p, g, s, Au, dg);
+  st(r + t.p, ld(f + t.p) - Au);
+}
+
+// ---------------------------------------------------------------- transfers
+
+// Full weighting at coarse interior node (I,J[,K]): tensor product of
+// (1,2,1)/4 over the fine neighbourhood of fine node (2I,2J[,2K]).
+template <int DIM, typename Tf, typename Tc>
+__global__ void k_restrict(const Tf *__restrict__ rf, Geo gf, Tc *__restrict__ fc, Geo gc) {
+  typedef typename CT<Tc>::type C;
+  Idx t = node_index<DIM>(gc);
+  if (!t.interior) return;
+  long long q = (long long)(2 * t.k) * gf.sz + (long long)(2 * t.j) * gf.sy + 2 * t.i;
+  C acc = 0;
+  if (DIM == 2) {
+    C a = ld(rf + q - gf.sy - 1) + ld(rf + q - gf.sy + 1) + ld(rf + q + gf.sy - 1) + ld(rf + q + gf.sy + 1);
+    C b = ld(rf + q - gf.sy) + ld(rf + q + gf.sy) + ld(rf + q - 1) + ld(rf + q + 1);
+    acc = (C)0.0625 * a + (C)0.125 * b + (C)0.25 * ld(rf + q);
+  } else {
+#pragma unroll
+    for (int dz = -1; dz <= 1; dz++) {
+      C wz = dz == 0 ? (C)0.5 : (C)0.25;
+#pragma unroll
+      for (int dy = -1; dy <= 1; dy++) {
+        C wy = dy == 0 ? (C)0.5 : (C)0.25;
+        const Tf *row = rf + q + dz * gf.sz + dy * gf.sy;
+        C line = (C)0.25 * (ld(row - 1) + ld(row + 1)) + (C)0.5 * ld(row);
+        acc += wz * wy * line;
+      }
+    }
+  }
+  st(fc + t.p, acc);
+}
+
+// Bi-/trilinear interpolation and correction at fine interior node (i,j[,k]).
+template <int DIM, typename Tc, typename Tf>
+__global__ void k_prolong(const Tc *__restrict__ ec, Geo gc, Tf *__restrict__ uf, Geo gf) {
+  typedef typename CT<Tf>::type C;
+  Idx t = node_index<DIM>(gf);
+  if (!t.interior) return;
+  int I = t.i >> 1, J = t.j >> 1, K = t.k >> 1;
+  int oi = t.i & 1, oj = t.j & 1, ok = DIM == 3 ? (t.k & 1) : 0;
+  C acc = 0;
+#pragma unroll
+  for (int a = 0; a <= 1; a++) {
+    if (a && !ok) break;
+#pragma unroll
+    for (int b = 0; b <= 1; b++) {
+      if (b && !oj) break;
+      const Tc *row = ec + (long long)(K + a) * gc.sz + (long long)(J + b) * gc.sy + I;
+      C v = oi ? (C)0.5 * ((C)ld(row) + (C)ld(row + 1)) : (C)ld(row);
+      acc += v;
+    }
+  }
+  C w = (oj ? (C)0.5 : (C)1) * (ok ? (C)0.5 : (C)1);
+  st(uf + t.p, (C)ld(uf + t.p) + w * acc);
+}
+
+// ---------------------------------------------------------------- norms
+
+// Block sum of a double with warp shuffles, then one value per warp in
+// shared memory; the result is valid in thread 0.
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double warp_part[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) warp_part[w] = v;
+  __syncthreads();
+  int nw = (blockDim.x + 31) >> 5;
+  v = threadIdx.x < nw ? warp_part[threadIdx.x] : 0.0;
+  if (w == 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  }
+  return v;
+}
+
+// Interior node t of a level with m = n-2 interior nodes per dimension.
+template <int DIM>
+__device__ __forceinline__ long long interior_node(long long t, int m, const Geo &g) {
+  long long i = 1 + t % m;
+  long long rest = t / m;
+  long long j = 1 + rest % m;
+  long long k = DIM == 3 ? 1 + rest / m : 0;
+  return k * g.sz + j * g.sy + i;
+}
+
+// Per-block partial sums of (f - A u)^2 in FP64 over a fixed grid-stride
+// partition, so the summation order depends only on the grid size.
+template <int DIM, typename T, bool VAR>
+__global__ void k_norm_partials(const T *__restrict__ u, const T *__restrict__ f, Geo g,
+                                Sten<typename CT<T>::type> s, double *__restrict__ partials) {
+  typedef typename CT<T>::type C;
+  int m = g.n - 2;
+  long long total = (long long)m * m * (DIM == 3 ? m : 1);
+  double acc = 0.0;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    long long p = interior_node<DIM>(t, m, g);
+    C Au, dg;
+    apply_at<DIM, VAR>(u, p, g, s, Au, dg);
+    double r = (double)(ld(f + p) - Au);
+    acc += r * r;
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+// ---------------------------------------------------------------- coarsest
+
+// One unknown (3^dim grid): u + (f - A u)/diag is the exact solution.
+template <int DIM, bool VAR>
+__global__ void k_coarse3(double *u, const double *f, Geo g, Sten<double> s) {
+  long long p = (DIM == 3 ? g.sz : 0) + g.sy + 1;
+  double Au, dg;
+  apply_at<DIM, VAR>(u, p, g, s, Au, dg);
+  u[p] = u[p] + (f[p] - Au) / dg;
+}
+
+// ---------------------------------------------------------------- defect correction
+
+// d_I = f_O - A_O u_O (FP64 arithmetic, cast to the inner storage type),
+// plus per-block partial sums of the FP64 residual squared.
+template <int DIM, typename Ti, bool VAR>
+__global__ void k_dc_residual(const double *__restrict__ u, const double *__restrict__ f, Geo go,
+                              Sten<double> s, Ti *__restrict__ d, Geo gi, double *__restrict__ partials) {
+  int m = go.n - 2;
+  long long total = (long long)m * m * (DIM == 3 ? m : 1);
+  double acc = 0.0;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    long long p = interior_node<DIM>(t, m, go);
+    long long q = interior_node<DIM>(t, m, gi);
+    double Au, dg;
+    apply_at<DIM, VAR>(u, p, go, s, Au, dg);
+    double r = f[p] - Au;
+    acc += r * r;
+    st(d + q, (float)r);
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+// u_O += e_I (FP64 update of the outer solution).
+template <int DIM, typename Ti>
+__global__ void k_dc_update(double *__restrict__ u, Geo go, const Ti *__restrict__ e, Geo gi) {
+  Idx t = node_index<DIM>(go);
+  if (!t.interior) return;
+  long long q = (long long)t.k * gi.sz + (long long)t.j * gi.sy + t.i;
+  u[t.p] += (double)ld(e + q);
+}
+
+// ---------------------------------------------------------------- layout helpers
+
+template <int DIM, typename T>
+__global__ void k_from_dense(const double *__restrict__ src, T *__restrict__ dst, Geo g) {
+  Idx t = node_index<DIM>(g);
+  if (t.i >= g.n) return;
+  long long q = ((long long)t.k * g.n + t.j) * g.n + t.i;
+  st(dst + t.p, src[q]);
+}
+
+template <int DIM, typename T>
+__global__ void k_to_dense(const T *__restrict__ src, double *__restrict__ dst, Geo g) {
+  Idx t = node_index<DIM>(g);
+  if (t.i >= g.n) return;
+  long long q = ((long long)t.k * g.n + t.j) * g.n + t.i;
+  dst[q] = (double)ld(src + t.p);
+}
+
+template <int DIM, typename T> __global__ void k_zero_interior(T *__restrict__ a, Geo g) {
+  Idx t = node_index<DIM>(g);
+  if (t.interior) st(a + t.p, 0.0f);
+}
+
+template <int DIM, typename T>
+__global__ void k_copy_boundary(const T *__restrict__ src, T *__restrict__ dst, Geo g) {
+  Idx t = node_index<DIM>(g);
+  if (t.i < g.n && !t.interior) dst[t.p] = src[t.p];
+}
+
+// Faces from node coefficients: c_d * 2 a b / (a + b); 0 past the last node.
+template <int DIM, typename C>
+__global__ void k_node_faces(const double *__restrict__ k, Geo gk, C *kx, C *ky, C *kz, Geo g, double c0,
+                             double c1, double c2) {
+  Idx t = node_index<DIM>(g);
+  if (t.i >= g.n) return;
+  long long pk = (long long)t.k * gk.sz + (long long)t.j * gk.sy + t.i;
+  double a = k[pk];
+  int n = g.n;
+  double fx = 0.0, fy = 0.0, fz = 0.0;
+  if (t.i < n - 1) { double b = k[pk + 1]; fx = c0 * (2.0 * a * b / (a + b)); }
+  if (t.j < n - 1) { double b = k[pk + gk.sy]; fy = c1 * (2.0 * a * b / (a + b)); }
+  if (DIM == 3 && t.k < n - 1) { double b = k[pk + gk.sz]; fz = c2 * (2.0 * a * b / (a + b)); }
+  kx[t.p] = (C)fx;
+  ky[t.p] = (C)fy;
+  if (DIM == 3) kz[t.p] = (C)fz;
+}
+
+// Coarse faces: two collinear fine faces in series, 2 a b / (a + b).
+template <int DIM, typename Cf, typename Cc>
+__global__ void k_coarsen_faces(const Cf *fx, const Cf *fy, const Cf *fz, Geo gf, Cc *cx, Cc *cy, Cc *cz,
+                                Geo gc) {
+  Idx t = node_index<DIM>(gc);
+  if (t.i >= gc.n) return;
+  int n = gc.n;
+  long long q = (long long)(2 * t.k) * gf.sz + (long long)(2 * t.j) * gf.sy + 2 * t.i;
+  double vx = 0.0, vy = 0.0, vz = 0.0;
+  if (t.i < n - 1) { double a = fx[q], b = fx[q + 1]; vx = 2.0 * a * b / (a + b); }
+  if (t.j < n - 1) { double a = fy[q], b = fy[q + gf.sy]; vy = 2.0 * a * b / (a + b); }
+  if (DIM == 3 && t.k < n - 1) { double a = fz[q], b = fz[q + gf.sz]; vz = 2.0 * a * b / (a + b); }
+  cx[t.p] = (Cc)vx;
+  cy[t.p] = (Cc)vy;
+  if (DIM == 3) cz[t.p] = (Cc)vz;
+}
+
+template <int DIM, typename Cs, typename Cd>
+__global__ void k_convert_faces(const Cs *sx, const Cs *sy, const Cs *sz, Geo gs, Cd *dx, Cd *dy, Cd *dz,
+                                Geo gd) {
+  Idx t = node_index<DIM>(gd);
+  if (t.i >= gd.n) return;
+  long long q = (long long)t.k * gs.sz + (long long)t.j * gs.sy + t.i;
+  dx[t.p] = (Cd)sx[q];
+  dy[t.p] = (Cd)sy[q];
+  if (DIM == 3) dz[t.p] = (Cd)sz[q];
+}
+
+}  // namespace mg

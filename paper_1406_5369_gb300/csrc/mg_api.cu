@@ -1,0 +1,693 @@
+// C ABI of libmg.so (declared in include/mg.h): context, arena layout,
+// V-cycle orchestration (Algorithm 1), solve loop (Layer-4 Application),
+// defect correction and CUDA-graph replay.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "mg.h"
+#include "mg_internal.h"
+
+using mg::Level;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+mg_status fail(mg_status st, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+#define CK(call)                                                                             \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess) return fail(MG_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                                       __FILE__, __LINE__);                                  \
+  } while (0)
+
+// Launches one kernel through a dispatcher and counts it.
+#define LAUNCH(c, call)                                                                       \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) return fail(MG_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                                       __FILE__, __LINE__);                                   \
+    (c)->launches++;                                                                          \
+  } while (0)
+
+constexpr int kMaxLevels = 31;
+constexpr int kGraphSlots = 4;
+
+// Dimension dispatch of the level kernels.
+#define DISPATCH(L, fn, ...) ((L).dim == 2 ? mg::d2::fn(__VA_ARGS__) : mg::d3::fn(__VA_ARGS__))
+
+}  // namespace
+
+struct GraphSlot {
+  bool valid;
+  int kind;           // 0 = cycle, 1 = solve step
+  unsigned key;       // live-buffer bitmask at capture
+  unsigned post;      // live-buffer bitmask after the captured work
+  unsigned long long kernels;  // kernel nodes in the graph
+  cudaGraphExec_t exec;
+};
+
+struct mg_ctx {
+  int dim, n, nl;
+  int variable;
+  bool dc;                // defect-correction precision
+  mg_options opt;
+  cudaStream_t stream;    // user stream
+  cudaStream_t cap;       // private stream used for graph capture
+  Level lv[kMaxLevels];   // working hierarchy (FP64, or the inner DC hierarchy)
+  Level outer;            // DC: outer FP64 finest level (u[0], f, r = FP64 staging, kf)
+  double *partials;       // kNormBlocks doubles
+  double *norm_out;       // [0] = norm, [1] = sum of squares
+  double *host_norm;      // pinned host copy of norm_out
+  size_t used_bytes;
+  GraphSlot graphs[kGraphSlots];
+  int next_slot;
+  unsigned long long launches;  // kernels launched (direct or inside replayed graphs)
+};
+
+namespace {
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Bump {
+  char *base;
+  size_t off;
+  void *take(size_t bytes) {
+    off = align_up(off, 256);
+    void *p = base ? base + off : nullptr;
+    off += bytes;
+    return p;
+  }
+};
+
+bool valid_n(int n, int *m_out) {
+  if (n < 3) return false;
+  int m = 0;
+  while ((1 << (m + 1)) + 1 <= n) m++;
+  if ((1 << m) + 1 != n) return false;
+  if (m_out) *m_out = m;
+  return true;
+}
+
+mg_status check_args(int dim, int n, const mg_options *opt) {
+  if (dim != 2 && dim != 3) return fail(MG_EINVAL, "dim must be 2 or 3 (got %d)", dim);
+  int m;
+  if (!valid_n(n, &m)) return fail(MG_EINVAL, "n must be 2^m+1 with m >= 1 (got %d)", n);
+  if (dim == 3 && n > 2049) return fail(MG_EINVAL, "3D grids are limited to n <= 2049");
+  if (!opt) return fail(MG_EINVAL, "options are NULL");
+  if (opt->smoother != MG_RBGS && opt->smoother != MG_JACOBI) return fail(MG_EINVAL, "unknown smoother");
+  if (!(opt->omega > 0.0 && opt->omega < 2.0)) return fail(MG_EINVAL, "omega must lie in (0, 2)");
+  if (opt->nu1 < 0 || opt->nu2 < 0 || opt->nu1 > 8 || opt->nu2 > 8) return fail(MG_EINVAL, "nu1, nu2 must lie in 0..8");
+  if (opt->nu1 + opt->nu2 == 0) return fail(MG_EINVAL, "nu1 + nu2 must be positive");
+  if (opt->coarsest_n != 3) return fail(MG_EINVAL, "coarsest_n must be 3");
+  if (opt->maxit < 0) return fail(MG_EINVAL, "maxit must be >= 0");
+  if (opt->precision != MG_FP64 && opt->precision != MG_FP32_DC && opt->precision != MG_BF16_DC)
+    return fail(MG_EINVAL, "unknown precision");
+  return MG_OK;
+}
+
+int level_count(int n) {
+  int L = 0;
+  for (int nn = n; nn >= 3; nn = (nn - 1) / 2 + 1) {
+    L++;
+    if (nn == 3) break;
+  }
+  return L;
+}
+
+void init_level(Level &L, int dim, int n, int dtype, const double c[3]) {
+  memset(&L, 0, sizeof L);
+  L.dim = dim;
+  L.n = n;
+  L.dtype = dtype;
+  int per128 = 128 / mg::dtype_size(dtype);
+  L.pitch = (int)align_up((size_t)n, (size_t)per128);
+  L.plane = (long long)L.pitch * n;
+  L.count = L.plane * (dim == 3 ? n : 1);
+  for (int d = 0; d < 3; d++) L.c[d] = c[d];
+  double h = 1.0 / (double)(n - 1);
+  L.inv_h2 = 1.0 / (h * h);
+}
+
+void take_level(Level &L, Bump &b, bool variable) {
+  size_t bytes = (size_t)L.count * mg::dtype_size(L.dtype);
+  L.u[0] = b.take(bytes);
+  L.u[1] = b.take(bytes);
+  L.f = b.take(bytes);
+  L.r = b.take(bytes);
+  if (variable) {
+    size_t fb = (size_t)L.count * mg::face_size(L.dtype);
+    for (int d = 0; d < L.dim; d++) L.kf[d] = b.take(fb);
+  }
+}
+
+// Lays out every buffer of the context in the arena (base == NULL: sizing).
+size_t layout(mg_ctx *c, char *base) {
+  Bump b{base, 0};
+  int inner = c->opt.precision == MG_FP32_DC ? mg::F32 : (c->opt.precision == MG_BF16_DC ? mg::BF16 : mg::F64);
+  double cc[3] = {c->lv[0].c[0], c->lv[0].c[1], c->lv[0].c[2]};
+  int nn = c->n;
+  for (int l = 0; l < c->nl; l++) {
+    int dt = (l == c->nl - 1) ? mg::F64 : inner;
+    init_level(c->lv[l], c->dim, nn, dt, cc);
+    take_level(c->lv[l], b, c->variable);
+    nn = (nn - 1) / 2 + 1;
+  }
+  if (c->dc) {
+    init_level(c->outer, c->dim, c->n, mg::F64, cc);
+    size_t bytes = (size_t)c->outer.count * 8;
+    c->outer.u[0] = b.take(bytes);
+    c->outer.u[1] = nullptr;
+    c->outer.f = b.take(bytes);
+    c->outer.r = b.take(bytes);
+    if (c->variable)
+      for (int d = 0; d < c->dim; d++) c->outer.kf[d] = b.take(bytes);
+  }
+  c->partials = (double *)b.take(sizeof(double) * mg::kNormBlocks);
+  c->norm_out = (double *)b.take(sizeof(double) * 4);
+  return align_up(b.off, 256);
+}
+
+// The FP64 level whose u/f the user's finest-level calls address.
+Level &user_level(mg_ctx *c) { return c->dc ? c->outer : c->lv[0]; }
+void *user_u(mg_ctx *c) { return c->dc ? c->outer.u[0] : c->lv[0].u[c->lv[0].cur]; }
+
+// Dense n^dim FP64 (host or device) <-> pitched FP64 field, whole array.
+cudaError_t copy_dense_to_pitched(const Level &L, const double *src, void *dst, cudaStream_t s) {
+  size_t rows = (size_t)L.n * (L.dim == 3 ? L.n : 1);
+  return cudaMemcpy2DAsync(dst, (size_t)L.pitch * 8, src, (size_t)L.n * 8, (size_t)L.n * 8, rows,
+                           cudaMemcpyDefault, s);
+}
+cudaError_t copy_pitched_to_dense(const Level &L, const void *src, double *dst, cudaStream_t s) {
+  size_t rows = (size_t)L.n * (L.dim == 3 ? L.n : 1);
+  return cudaMemcpy2DAsync(dst, (size_t)L.n * 8, src, (size_t)L.pitch * 8, (size_t)L.n * 8, rows,
+                           cudaMemcpyDefault, s);
+}
+// Interior box only (boundary of dst untouched).
+cudaError_t copy_dense_interior(const Level &L, const double *src, void *dst, cudaStream_t s) {
+  size_t n = (size_t)L.n, m = n - 2;
+  if (L.dim == 2) {
+    return cudaMemcpy2DAsync((char *)dst + ((size_t)L.pitch + 1) * 8, (size_t)L.pitch * 8, src + n + 1, n * 8,
+                             m * 8, m, cudaMemcpyDefault, s);
+  }
+  cudaMemcpy3DParms p;
+  memset(&p, 0, sizeof p);
+  p.srcPtr = make_cudaPitchedPtr((void *)src, n * 8, n, n);
+  p.srcPos = make_cudaPos(8, 1, 1);
+  p.dstPtr = make_cudaPitchedPtr(dst, (size_t)L.pitch * 8, n, n);
+  p.dstPos = make_cudaPos(8, 1, 1);
+  p.extent = make_cudaExtent(m * 8, m, m);
+  p.kind = cudaMemcpyDefault;
+  return cudaMemcpy3DAsync(&p, s);
+}
+
+// ---------------------------------------------------------------- level ops
+
+mg_status op_smooth(mg_ctx *c, int l, int sweeps, cudaStream_t s) {
+  Level &L = c->lv[l];
+  for (int k = 0; k < sweeps; k++) {
+    if (c->opt.smoother == MG_RBGS) {
+      LAUNCH(c, DISPATCH(L, rbgs_half, L, L.u[L.cur], L.f, 0, c->opt.omega, s));
+      LAUNCH(c, DISPATCH(L, rbgs_half, L, L.u[L.cur], L.f, 1, c->opt.omega, s));
+    } else {
+      LAUNCH(c, DISPATCH(L, jacobi, L, L.u[L.cur], L.u[L.cur ^ 1], L.f, c->opt.omega, s));
+      L.cur ^= 1;
+    }
+  }
+  return MG_OK;
+}
+
+mg_status op_residual(mg_ctx *c, int l, cudaStream_t s) {
+  Level &L = c->lv[l];
+  LAUNCH(c, DISPATCH(L, residual, L, L.u[L.cur], L.f, L.r, s));
+  return MG_OK;
+}
+
+mg_status op_restrict(mg_ctx *c, int l, cudaStream_t s) {
+  Level &F = c->lv[l], &C = c->lv[l + 1];
+  LAUNCH(c, DISPATCH(F, restrict_fw, F, F.r, C, C.f, s));
+  return MG_OK;
+}
+
+mg_status op_prolong(mg_ctx *c, int l, cudaStream_t s) {
+  Level &F = c->lv[l], &C = c->lv[l + 1];
+  LAUNCH(c, DISPATCH(F, prolong, C, C.u[C.cur], F, F.u[F.cur], s));
+  return MG_OK;
+}
+
+mg_status op_coarse(mg_ctx *c, cudaStream_t s) {
+  Level &L = c->lv[c->nl - 1];
+  LAUNCH(c, DISPATCH(L, coarse3, L, L.u[L.cur], L.f, s));
+  return MG_OK;
+}
+
+mg_status op_zero_u(mg_ctx *c, int l, cudaStream_t s) {
+  Level &L = c->lv[l];
+  CK(cudaMemsetAsync(L.u[L.cur], 0, (size_t)L.count * mg::dtype_size(L.dtype), s));
+  return MG_OK;
+}
+
+// Algorithm 1 from level l down: presmooth, residual, restrict, zero the
+// coarse solution, recurse, interpolate and correct, postsmooth.
+mg_status vcycle_rec(mg_ctx *c, int l, cudaStream_t s) {
+  mg_status st;
+  if (l == c->nl - 1) return op_coarse(c, s);
+  if ((st = op_smooth(c, l, c->opt.nu1, s))) return st;
+  if ((st = op_residual(c, l, s))) return st;
+  if ((st = op_restrict(c, l, s))) return st;
+  if ((st = op_zero_u(c, l + 1, s))) return st;
+  if ((st = vcycle_rec(c, l + 1, s))) return st;
+  if ((st = op_prolong(c, l, s))) return st;
+  return op_smooth(c, l, c->opt.nu2, s);
+}
+
+mg_status op_norm(mg_ctx *c, int l, cudaStream_t s) {
+  if (c->dc && l == 0) {
+    Level &O = c->outer, &I = c->lv[0];
+    LAUNCH(c, DISPATCH(O, dc_residual, O, O.u[0], O.f, I, I.f, c->partials, mg::kNormBlocks, s));
+  } else {
+    Level &L = c->lv[l];
+    LAUNCH(c, DISPATCH(L, norm_partials, L, L.u[L.cur], L.f, c->partials, mg::kNormBlocks, s));
+  }
+  LAUNCH(c, mg::norm_finalize(c->partials, mg::kNormBlocks, c->norm_out, s));
+  return MG_OK;
+}
+
+// One defect-correction step with the defect d already in lv[0].f:
+// e = V(0, d); u += e.
+mg_status dc_inner_and_update(mg_ctx *c, cudaStream_t s) {
+  mg_status st;
+  if ((st = op_zero_u(c, 0, s))) return st;
+  if ((st = vcycle_rec(c, 0, s))) return st;
+  Level &O = c->outer, &I = c->lv[0];
+  LAUNCH(c, DISPATCH(O, dc_update, O, O.u[0], I, I.u[I.cur], s));
+  return MG_OK;
+}
+
+// kind 0: one cycle as mg_vcycle defines it; kind 1: one solve step
+// (cycle followed by the finest-level residual norm into norm_out).
+mg_status record(mg_ctx *c, int kind, cudaStream_t s) {
+  mg_status st;
+  if (!c->dc) {
+    if ((st = vcycle_rec(c, 0, s))) return st;
+    if (kind == 1) return op_norm(c, 0, s);
+    return MG_OK;
+  }
+  if (kind == 0) {
+    Level &O = c->outer, &I = c->lv[0];
+    LAUNCH(c, DISPATCH(O, dc_residual, O, O.u[0], O.f, I, I.f, c->partials, mg::kNormBlocks, s));
+    return dc_inner_and_update(c, s);
+  }
+  if ((st = dc_inner_and_update(c, s))) return st;
+  return op_norm(c, 0, s);
+}
+
+unsigned cur_key(mg_ctx *c) {
+  unsigned k = 0;
+  for (int l = 0; l < c->nl; l++) k |= (unsigned)c->lv[l].cur << l;
+  return k;
+}
+void set_cur(mg_ctx *c, unsigned k) {
+  for (int l = 0; l < c->nl; l++) c->lv[l].cur = (k >> l) & 1u;
+}
+
+void drop_graphs(mg_ctx *c) {
+  for (int i = 0; i < kGraphSlots; i++) {
+    if (c->graphs[i].valid) cudaGraphExecDestroy(c->graphs[i].exec);
+    c->graphs[i].valid = false;
+  }
+}
+
+// Runs one cycle or solve step, replaying a captured graph when enabled.
+// A graph is keyed by the live-buffer state it was captured in and stores
+// the state it leaves behind (Jacobi sweeps flip a level's live buffer).
+mg_status run(mg_ctx *c, int kind) {
+  if (!c->opt.use_graph) return record(c, kind, c->stream);
+  unsigned key = cur_key(c);
+  for (int i = 0; i < kGraphSlots; i++) {
+    GraphSlot &g = c->graphs[i];
+    if (g.valid && g.kind == kind && g.key == key) {
+      CK(cudaGraphLaunch(g.exec, c->stream));
+      c->launches += g.kernels;
+      set_cur(c, g.post);
+      return MG_OK;
+    }
+  }
+  // Capture on the private stream, ordered after the user stream.
+  cudaEvent_t ev;
+  CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  CK(cudaEventRecord(ev, c->stream));
+  CK(cudaStreamWaitEvent(c->cap, ev, 0));
+  CK(cudaEventDestroy(ev));
+  CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+  unsigned long long before = c->launches;
+  mg_status st = record(c, kind, c->cap);
+  unsigned long long kernels = c->launches - before;
+  c->launches = before;
+  unsigned post = cur_key(c);
+  set_cur(c, key);
+  cudaGraph_t graph = nullptr;
+  cudaError_t ee = cudaStreamEndCapture(c->cap, &graph);
+  if (st) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (ee != cudaSuccess) return fail(MG_ECUDA, "graph capture: %s", cudaGetErrorString(ee));
+  GraphSlot &g = c->graphs[c->next_slot];
+  c->next_slot = (c->next_slot + 1) % kGraphSlots;
+  if (g.valid) cudaGraphExecDestroy(g.exec);
+  g.valid = false;
+  cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) return fail(MG_ECUDA, "graph instantiate: %s", cudaGetErrorString(ie));
+  g.valid = true;
+  g.kind = kind;
+  g.key = key;
+  g.post = post;
+  g.kernels = kernels;
+  CK(cudaGraphLaunch(g.exec, c->stream));
+  c->launches += kernels;
+  set_cur(c, post);
+  return MG_OK;
+}
+
+mg_status read_norm(mg_ctx *c, double *out) {
+  CK(cudaMemcpyAsync(c->host_norm, c->norm_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  *out = c->host_norm[0];
+  return MG_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- ABI
+
+extern "C" {
+
+void mg_default_options(mg_options *o) {
+  if (!o) return;
+  memset(o, 0, sizeof *o);
+  o->smoother = MG_RBGS;
+  o->omega = 1.0;
+  o->nu1 = 2;
+  o->nu2 = 1;
+  o->coarsest_n = 3;
+  o->maxit = 50;
+  o->precision = MG_FP64;
+  o->stream = nullptr;
+  o->fuse = 1;
+  o->use_graph = 1;
+}
+
+size_t mg_workspace_bytes(int dim, int n, int variable_k, const mg_options *opt) {
+  if (check_args(dim, n, opt) != MG_OK) return 0;
+  mg_ctx tmp;
+  memset(&tmp, 0, sizeof tmp);
+  tmp.dim = dim;
+  tmp.n = n;
+  tmp.nl = level_count(n);
+  tmp.variable = variable_k != 0;
+  tmp.opt = *opt;
+  tmp.dc = opt->precision != MG_FP64;
+  tmp.lv[0].c[0] = tmp.lv[0].c[1] = tmp.lv[0].c[2] = 1.0;
+  return layout(&tmp, nullptr);
+}
+
+mg_status mg_create(int dim, int n, const mg_const_stencil *stencil, const double *k, const mg_boundary *bc,
+                    const mg_options *opt, void *arena, size_t arena_bytes, mg_ctx **out) {
+  g_err[0] = 0;
+  if (!out) return fail(MG_EINVAL, "out is NULL");
+  *out = nullptr;
+  mg_status st = check_args(dim, n, opt);
+  if (st) return st;
+  if (!arena) return fail(MG_EINVAL, "arena is NULL");
+  if ((uintptr_t)arena % 256) return fail(MG_EINVAL, "arena must be 256-byte aligned");
+  if (bc && bc->kind != 0) return fail(MG_EINVAL, "only Dirichlet boundaries (kind 0) are supported");
+  double c3[3] = {1.0, 1.0, 1.0};
+  if (stencil) {
+    c3[0] = stencil->cx;
+    c3[1] = stencil->cy;
+    c3[2] = dim == 3 ? stencil->cz : 1.0;
+    if (!(c3[0] > 0 && c3[1] > 0 && c3[2] > 0)) return fail(MG_EINVAL, "stencil coefficients must be > 0");
+  }
+  mg_ctx *c = (mg_ctx *)calloc(1, sizeof(mg_ctx));
+  if (!c) return fail(MG_ENOMEM, "host allocation of the context failed");
+  c->dim = dim;
+  c->n = n;
+  c->nl = level_count(n);
+  c->variable = k != nullptr;
+  c->opt = *opt;
+  c->dc = opt->precision != MG_FP64;
+  c->stream = (cudaStream_t)opt->stream;
+  for (int d = 0; d < 3; d++) c->lv[0].c[d] = c3[d];
+  size_t need = layout(c, nullptr);
+  if (arena_bytes < need) {
+    free(c);
+    return fail(MG_ENOMEM, "arena has %zu bytes, %zu needed", arena_bytes, need);
+  }
+  layout(c, (char *)arena);
+  c->used_bytes = need;
+  cudaError_t e;
+#define CKC(call)                                                                  \
+  do {                                                                             \
+    e = (call);                                                                    \
+    if (e != cudaSuccess) {                                                        \
+      st = fail(MG_ECUDA, "%s: %s", #call, cudaGetErrorString(e));                 \
+      goto bad;                                                                    \
+    }                                                                              \
+  } while (0)
+  CKC(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+  CKC(cudaMallocHost((void **)&c->host_norm, 4 * sizeof(double)));
+  CKC(cudaMemsetAsync(arena, 0, need, c->stream));
+  if (c->variable) {
+    // Node coefficients -> FP64 staging with the finest FP64 layout -> faces.
+    Level &K = c->dc ? c->outer : c->lv[0];
+    void *stage = K.r;
+    CKC(copy_dense_to_pitched(K, k, stage, c->stream));
+    Level &F0 = c->dc ? c->outer : c->lv[0];
+    CKC(DISPATCH(F0, node_faces, K, (const double *)stage, F0, c->stream));
+    if (c->dc) {
+      CKC(DISPATCH(F0, convert_faces, c->outer, c->lv[0], c->stream));
+      if (c->nl > 1) CKC(DISPATCH(F0, coarsen_faces, c->outer, c->lv[1], c->stream));
+      for (int l = 2; l < c->nl; l++) CKC(DISPATCH(F0, coarsen_faces, c->lv[l - 1], c->lv[l], c->stream));
+    } else {
+      for (int l = 1; l < c->nl; l++) CKC(DISPATCH(F0, coarsen_faces, c->lv[l - 1], c->lv[l], c->stream));
+    }
+    CKC(cudaMemsetAsync(stage, 0, (size_t)K.count * 8, c->stream));
+  }
+  if (bc && bc->dirichlet_values) {
+    Level &U = user_level(c);
+    CKC(copy_dense_to_pitched(U, bc->dirichlet_values, U.u[0], c->stream));
+    CKC(DISPATCH(U, zero_interior, U, U.u[0], c->stream));
+    if (!c->dc) CKC(cudaMemcpyAsync(U.u[1], U.u[0], (size_t)U.count * 8, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  CKC(cudaStreamSynchronize(c->stream));
+#undef CKC
+  *out = c;
+  return MG_OK;
+bad:
+  if (c->cap) cudaStreamDestroy(c->cap);
+  if (c->host_norm) cudaFreeHost(c->host_norm);
+  free(c);
+  return st;
+}
+
+mg_status mg_destroy(mg_ctx *c) {
+  if (!c) return MG_OK;
+  drop_graphs(c);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  if (c->host_norm) cudaFreeHost(c->host_norm);
+  free(c);
+  return MG_OK;
+}
+
+int mg_num_levels(const mg_ctx *c) { return c ? c->nl : -1; }
+
+int mg_level_size(const mg_ctx *c, int level) {
+  if (!c || level < 0 || level >= c->nl) return -1;
+  return c->lv[level].n;
+}
+
+mg_status mg_set_rhs(mg_ctx *c, const double *f) {
+  if (!c || !f) return fail(MG_EINVAL, "NULL argument");
+  Level &U = user_level(c);
+  CK(copy_dense_to_pitched(U, f, U.f, c->stream));
+  return MG_OK;
+}
+
+mg_status mg_set_solution(mg_ctx *c, const double *u0) {
+  if (!c) return fail(MG_EINVAL, "NULL context");
+  Level &U = user_level(c);
+  void *dst = user_u(c);
+  if (!u0) {
+    LAUNCH(c, DISPATCH(U, zero_interior, U, dst, c->stream));
+  } else {
+    CK(copy_dense_interior(U, u0, dst, c->stream));
+  }
+  return MG_OK;
+}
+
+mg_status mg_get_solution(mg_ctx *c, double *u) {
+  if (!c || !u) return fail(MG_EINVAL, "NULL argument");
+  Level &U = user_level(c);
+  CK(copy_pitched_to_dense(U, user_u(c), u, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return MG_OK;
+}
+
+static void *field_ptr(Level &L, mg_field f) {
+  return f == MG_FIELD_U ? L.u[L.cur] : (f == MG_FIELD_F ? L.f : L.r);
+}
+
+mg_status mg_set_field(mg_ctx *c, int level, mg_field field, const double *src) {
+  if (!c || !src) return fail(MG_EINVAL, "NULL argument");
+  if (level < 0 || level >= c->nl) return fail(MG_EINVAL, "level %d out of range", level);
+  if (field < MG_FIELD_U || field > MG_FIELD_R) return fail(MG_EINVAL, "unknown field");
+  Level &L = c->lv[level];
+  void *dst = field_ptr(L, field);
+  if (L.dtype == mg::F64) {
+    CK(copy_dense_to_pitched(L, src, dst, c->stream));
+  } else {
+    double *stage = (double *)c->outer.r;  // DC contexts only have non-FP64 levels
+    size_t cnt = (size_t)L.n * L.n * (L.dim == 3 ? L.n : 1);
+    CK(cudaMemcpyAsync(stage, src, cnt * 8, cudaMemcpyDefault, c->stream));
+    LAUNCH(c, DISPATCH(L, from_dense, L, stage, dst, c->stream));
+  }
+  return MG_OK;
+}
+
+mg_status mg_get_field(mg_ctx *c, int level, mg_field field, double *dst) {
+  if (!c || !dst) return fail(MG_EINVAL, "NULL argument");
+  if (level < 0 || level >= c->nl) return fail(MG_EINVAL, "level %d out of range", level);
+  if (field < MG_FIELD_U || field > MG_FIELD_R) return fail(MG_EINVAL, "unknown field");
+  Level &L = c->lv[level];
+  void *src = field_ptr(L, field);
+  if (L.dtype == mg::F64) {
+    CK(copy_pitched_to_dense(L, src, dst, c->stream));
+  } else {
+    double *stage = (double *)c->outer.r;
+    size_t cnt = (size_t)L.n * L.n * (L.dim == 3 ? L.n : 1);
+    LAUNCH(c, DISPATCH(L, to_dense, L, src, stage, c->stream));
+    CK(cudaMemcpyAsync(dst, stage, cnt * 8, cudaMemcpyDefault, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return MG_OK;
+}
+
+mg_status mg_smooth(mg_ctx *c, int level, int sweeps) {
+  if (!c) return fail(MG_EINVAL, "NULL context");
+  if (level < 0 || level >= c->nl) return fail(MG_EINVAL, "level %d out of range", level);
+  if (sweeps < 0) return fail(MG_EINVAL, "sweeps must be >= 0");
+  return op_smooth(c, level, sweeps, c->stream);
+}
+
+mg_status mg_residual(mg_ctx *c, int level) {
+  if (!c) return fail(MG_EINVAL, "NULL context");
+  if (level < 0 || level >= c->nl) return fail(MG_EINVAL, "level %d out of range", level);
+  return op_residual(c, level, c->stream);
+}
+
+mg_status mg_restrict(mg_ctx *c, int level) {
+  if (!c) return fail(MG_EINVAL, "NULL context");
+  if (level < 0 || level >= c->nl - 1) return fail(MG_EINVAL, "level %d has no coarser level", level);
+  return op_restrict(c, level, c->stream);
+}
+
+mg_status mg_prolongate(mg_ctx *c, int level) {
+  if (!c) return fail(MG_EINVAL, "NULL context");
+  if (level < 0 || level >= c->nl - 1) return fail(MG_EINVAL, "level %d has no coarser level", level);
+  return op_prolong(c, level, c->stream);
+}
+
+mg_status mg_coarse_solve(mg_ctx *c) {
+  if (!c) return fail(MG_EINVAL, "NULL context");
+  return op_coarse(c, c->stream);
+}
+
+mg_status mg_vcycle(mg_ctx *c) {
+  if (!c) return fail(MG_EINVAL, "NULL context");
+  return run(c, 0);
+}
+
+mg_status mg_residual_norm(mg_ctx *c, int level, double *out) {
+  if (!c || !out) return fail(MG_EINVAL, "NULL argument");
+  if (level < 0 || level >= c->nl) return fail(MG_EINVAL, "level %d out of range", level);
+  mg_status st = op_norm(c, level, c->stream);
+  if (st) return st;
+  return read_norm(c, out);
+}
+
+mg_status mg_solve(mg_ctx *c, double tol, int *iters, double *relres, double *history) {
+  if (!c) return fail(MG_EINVAL, "NULL context");
+  if (!(tol >= 0.0)) return fail(MG_EINVAL, "tol must be >= 0");
+  double r0;
+  mg_status st = op_norm(c, 0, c->stream);
+  if (st) return st;
+  if ((st = read_norm(c, &r0))) return st;
+  if (history) history[0] = 1.0;
+  int k = 0;
+  double rho = r0 > 0 ? 1.0 : 0.0;
+  if (!isfinite(r0)) return fail(MG_ENOCONV, "initial residual is not finite");
+  while (r0 > 0.0 && rho > tol && k < c->opt.maxit) {
+    if ((st = run(c, 1))) return st;
+    double rk;
+    if ((st = read_norm(c, &rk))) return st;
+    k++;
+    rho = rk / r0;
+    if (history) history[k] = rho;
+    if (!isfinite(rho)) {
+      if (iters) *iters = k;
+      if (relres) *relres = rho;
+      return fail(MG_ENOCONV, "residual is not finite after %d cycles", k);
+    }
+  }
+  if (iters) *iters = k;
+  if (relres) *relres = rho;
+  if (rho > tol) return fail(MG_ENOCONV, "relative residual %.3e above tol %.3e after %d cycles", rho, tol, k);
+  return MG_OK;
+}
+
+unsigned long long mg_kernel_launches(const mg_ctx *c) { return c ? c->launches : 0ull; }
+
+const char *mg_last_error(void) { return g_err; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- norm finalize
+
+namespace mg {
+
+// Sums kNormBlocks partials in a fixed tree order (deterministic).
+__global__ void k_norm_finalize(const double *__restrict__ partials, int nb, double *__restrict__ out) {
+  __shared__ double buf[1024];
+  int t = threadIdx.x;
+  buf[t] = t < nb ? partials[t] : 0.0;
+  __syncthreads();
+  for (int s = 512; s > 0; s >>= 1) {
+    if (t < s) buf[t] += buf[t + s];
+    __syncthreads();
+  }
+  if (t == 0) {
+    out[0] = sqrt(buf[0]);
+    out[1] = buf[0];
+  }
+}
+
+cudaError_t norm_finalize(const double *partials, int nblocks, double *out, cudaStream_t s) {
+  if (nblocks > 1024) return cudaErrorInvalidValue;
+  k_norm_finalize<<<1, 1024, 0, s>>>(partials, nblocks, out);
+  return cudaGetLastError();
+}
+
+}  // namespace mg

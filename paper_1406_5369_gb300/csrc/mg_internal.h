@@ -1,0 +1,71 @@
+// Internal declarations shared by the translation units of libmg.so.
+// Nothing here is part of the public C ABI (include/mg.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mg {
+
+enum DType { F64 = 0, F32 = 1, BF16 = 2 };
+
+inline int dtype_size(int t) { return t == F64 ? 8 : (t == F32 ? 4 : 2); }
+// Face coefficients are stored in the compute type of the level.
+inline int face_size(int t) { return t == F64 ? 8 : 4; }
+
+// One grid level as the kernels see it. Sizes are in elements of the
+// level's storage type.
+struct Level {
+  int dim;          // 2 or 3
+  int n;            // nodes per dimension, boundary included
+  int pitch;        // row stride (elements); every row starts 128-byte aligned
+  long long plane;  // plane stride (elements) = pitch * n
+  long long count;  // elements per field = plane * (dim == 3 ? n : 1)
+  int dtype;        // DType of u, f, r
+  void *u[2];       // solution, ping-pong pair; cur selects the live one
+  void *f;          // right-hand side
+  void *r;          // residual / scratch
+  void *kf[3];      // face coefficients (NULL for the constant stencil); kf[d][p] is
+                    // the face between node p and p + e_d, same indexing as u
+  double c[3];      // constant stencil coefficients
+  double inv_h2;    // 1/h^2
+  int cur;          // index of the live solution buffer
+};
+
+constexpr int kNormBlocks = 1024;
+
+// Per-dimension kernel launchers; all asynchronous on `s`.
+#define MG_DIM_OPS                                                                                \
+  cudaError_t rbgs_half(const Level &L, void *u, const void *f, int color, double omega,         \
+                        cudaStream_t s);                                                          \
+  cudaError_t jacobi(const Level &L, const void *uin, void *uout, const void *f, double omega,   \
+                     cudaStream_t s);                                                             \
+  cudaError_t residual(const Level &L, const void *u, const void *f, void *r, cudaStream_t s);   \
+  cudaError_t restrict_fw(const Level &F, const void *rf, const Level &C, void *fc,              \
+                          cudaStream_t s);                                                        \
+  cudaError_t prolong(const Level &C, const void *ec, const Level &F, void *uf, cudaStream_t s); \
+  cudaError_t norm_partials(const Level &L, const void *u, const void *f, double *partials,       \
+                            int nblocks, cudaStream_t s);                                         \
+  cudaError_t coarse3(const Level &L, void *u, const void *f, cudaStream_t s);                   \
+  cudaError_t dc_residual(const Level &O, const void *u, const void *f, const Level &I, void *d, \
+                          double *partials, int nblocks, cudaStream_t s);                         \
+  cudaError_t dc_update(const Level &O, void *u, const Level &I, const void *e, cudaStream_t s); \
+  cudaError_t from_dense(const Level &L, const double *src, void *dst, cudaStream_t s);          \
+  cudaError_t to_dense(const Level &L, const void *src, double *dst, cudaStream_t s);            \
+  cudaError_t zero_interior(const Level &L, void *field, cudaStream_t s);                        \
+  cudaError_t copy_boundary(const Level &L, const void *src, void *dst, cudaStream_t s);         \
+  cudaError_t node_faces(const Level &K, const double *knode, const Level &Lout, cudaStream_t s); \
+  cudaError_t coarsen_faces(const Level &F, const Level &C, cudaStream_t s);                     \
+  cudaError_t convert_faces(const Level &src, const Level &dst, cudaStream_t s);
+
+namespace d2 {
+MG_DIM_OPS
+}
+namespace d3 {
+MG_DIM_OPS
+}
+
+// out[0] = sqrt(sum of partials), out[1] = the sum; fixed summation order.
+cudaError_t norm_finalize(const double *partials, int nblocks, double *out, cudaStream_t s);
+
+}  // namespace mg

@@ -1,0 +1,102 @@
+"""Host-side checks of the C ABI: the library builds, loads and exports every
+function include/mg.h declares; argument validation needs no GPU; the product
+package never reaches the oracle."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1406_5369_gb300 import build as b
+    b.build()
+    from paper_1406_5369_gb300 import _capi
+    return _capi.load()
+
+
+def declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names += re.findall(r"\b(mg_[a-z0-9_]+)\s*\(", txt)
+    return sorted(set(names))
+
+
+def test_every_declared_function_is_exported(lib):
+    from paper_1406_5369_gb300 import _capi
+    names = declared_functions()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(lib, name), name
+        assert name in _capi.SIGNATURES, f"binding lacks {name}"
+
+
+def test_binding_declares_only_header_functions():
+    from paper_1406_5369_gb300 import _capi
+    assert set(_capi.SIGNATURES) <= set(declared_functions())
+
+
+def test_default_options_and_workspace(lib):
+    from paper_1406_5369_gb300 import _capi as C
+    o = C.mg_options()
+    lib.mg_default_options(ctypes.byref(o))
+    assert (o.smoother, o.omega, o.nu1, o.nu2, o.coarsest_n, o.precision) == (C.MG_RBGS, 1.0, 2, 1, 3, C.MG_FP64)
+    b129 = lib.mg_workspace_bytes(2, 129, 0, ctypes.byref(o))
+    # four FP64 fields per level, rows padded to 16 doubles: 129 -> 144, ...
+    assert b129 >= 4 * 144 * 129 * 8
+    assert lib.mg_workspace_bytes(2, 129, 1, ctypes.byref(o)) > b129
+    assert lib.mg_workspace_bytes(2, 100, 0, ctypes.byref(o)) == 0
+    assert lib.mg_workspace_bytes(4, 129, 0, ctypes.byref(o)) == 0
+    o.precision = C.MG_FP32_DC
+    dc = lib.mg_workspace_bytes(2, 8193, 0, ctypes.byref(o))
+    o.precision = C.MG_FP64
+    fp = lib.mg_workspace_bytes(2, 8193, 0, ctypes.byref(o))
+    # outer FP64 u, f, staging plus the FP32 inner hierarchy
+    assert fp < dc < 2 * fp
+
+
+def test_invalid_arguments_are_rejected_before_any_device_work(lib):
+    from paper_1406_5369_gb300 import _capi as C
+    o = C.mg_options()
+    lib.mg_default_options(ctypes.byref(o))
+    ctx = ctypes.c_void_p()
+    buf = ctypes.c_void_p(256)
+    assert lib.mg_create(2, 10, None, None, None, ctypes.byref(o), buf, 1 << 20, ctypes.byref(ctx)) == C.MG_EINVAL
+    assert b"2^m+1" in lib.mg_last_error()
+    o.omega = 2.5
+    assert lib.mg_create(2, 9, None, None, None, ctypes.byref(o), buf, 1 << 20, ctypes.byref(ctx)) == C.MG_EINVAL
+    lib.mg_default_options(ctypes.byref(o))
+    o.coarsest_n = 5
+    assert lib.mg_create(2, 9, None, None, None, ctypes.byref(o), buf, 1 << 20, ctypes.byref(ctx)) == C.MG_EINVAL
+    lib.mg_default_options(ctypes.byref(o))
+    assert lib.mg_create(2, 9, None, None, None, ctypes.byref(o), buf, 16, ctypes.byref(ctx)) == C.MG_ENOMEM
+    assert lib.mg_create(2, 9, None, None, None, ctypes.byref(o), None, 1 << 20, ctypes.byref(ctx)) == C.MG_EINVAL
+    assert lib.mg_destroy(None) == C.MG_OK
+    assert lib.mg_num_levels(None) == -1
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    from paper_1406_5369_gb300 import _capi
+    saved = _capi._lib
+    _capi._lib = None
+    try:
+        with pytest.raises(ImportError):
+            _capi.load(str(tmp_path / "nope.so"))
+    finally:
+        _capi._lib = saved
+
+
+def test_product_path_does_not_reach_the_oracle():
+    pkg = os.path.join(ROOT, "paper_1406_5369_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for fn in files:
+            if fn.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                txt = open(os.path.join(dirpath, fn)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", txt, flags=re.M), fn
+                assert "mg_oracle" not in txt and "liboracle" not in txt, fn
