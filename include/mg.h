@@ -193,6 +193,36 @@ mg_status mg_solve(mg_ctx *ctx, double tol, int *iters, double *relres, double *
  * replayed graph (memset/copy operations are not counted). */
 unsigned long long mg_kernel_launches(const mg_ctx *ctx);
 
+/* Largest number of per-block partial sums mg_residual_norm_noalloc keeps in
+ * its static device scratch. Each block covers 2048 interior nodes, so grids
+ * with at most MG_NOALLOC_MAX_PARTIALS * 2048 = 67,108,864 interior nodes are
+ * accepted: 2D up to n = 8193, 3D up to n = 257. */
+#define MG_NOALLOC_MAX_PARTIALS 32768
+
+/* The paper has no counterpart of this call. It returns in *out the norm
+ * ||f - A u||_2 over the interior nodes (FP64 accumulation) for the constant
+ * stencil (NULL = Poisson), like mg_residual_norm, for callers that may not
+ * allocate device memory at all: code embedded in a framework that owns
+ * every device allocation through its own pool, or a latency-critical loop
+ * where cudaMalloc (which can synchronise the device) is forbidden. Such
+ * callers cannot provide an arena, so this call needs no context: u and f
+ * are the caller's dense n^dim FP64 device arrays (x fastest, boundary
+ * nodes hold the Dirichlet values); out may be host or device memory.
+ * Scratch: the reduction's partial sums live in one static device array of
+ * MG_NOALLOC_MAX_PARTIALS + 32 doubles (about 256 KB) that every GPU which
+ * loads the library keeps until the process exits; nothing is allocated.
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) - make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents (every
+ * call overwrites the slots it reads), so calls that overlap on the GPU -
+ * on different streams, or from several host threads - race and must be
+ * serialised by the caller. The call runs on `stream` (a cudaStream_t,
+ * NULL = default stream) and synchronises it before returning.
+ * Returns MG_EINVAL for dim not 2/3, n < 3, NULL pointers or a grid above the
+ * limit (message in mg_last_error), MG_ECUDA if a launch fails. */
+mg_status mg_residual_norm_noalloc(int dim, int n, const mg_const_stencil *stencil, const double *u,
+                                   const double *f, double *out, void *stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *mg_last_error(void);
 

@@ -60,6 +60,8 @@ SIGNATURES = {
     "mg_residual_norm": (_I, [_P, _I, ctypes.POINTER(_D)]),
     "mg_solve": (_I, [_P, _D, ctypes.POINTER(_I), ctypes.POINTER(_D), _P]),
     "mg_kernel_launches": (ctypes.c_ulonglong, [_P]),
+    "mg_residual_norm_noalloc": (_I, [_I, _I, ctypes.POINTER(mg_const_stencil), _P, _P,
+                                      ctypes.POINTER(_D), _P]),
     "mg_last_error": (ctypes.c_char_p, []),
 }
 

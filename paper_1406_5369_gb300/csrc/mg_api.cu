@@ -668,6 +668,8 @@ const char *mg_last_error(void) { return g_err; }
 
 namespace mg {
 
+void set_error_message(const char *msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
+
 // Sums kNormBlocks partials in a fixed tree order (deterministic).
 __global__ void k_norm_finalize(const double *__restrict__ partials, int nb, double *__restrict__ out) {
   __shared__ double buf[1024];

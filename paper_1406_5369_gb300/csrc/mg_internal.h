@@ -65,6 +65,9 @@ namespace d3 {
 MG_DIM_OPS
 }
 
+// Sets the message mg_last_error() returns on the calling thread.
+void set_error_message(const char *msg);
+
 // out[0] = sqrt(sum of partials), out[1] = the sum; fixed summation order.
 cudaError_t norm_finalize(const double *partials, int nblocks, double *out, cudaStream_t s);
 
