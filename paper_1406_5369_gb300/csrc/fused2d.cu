@@ -1,0 +1,140 @@
+// Launchers of the fused 2D fine-level kernels (fused2d.cuh).
+#include <string.h>
+
+#include "fused2d.cuh"
+
+namespace mg {
+namespace d2 {
+
+namespace {
+
+template <typename KernelT>
+cudaError_t prepare(KernelT kernel, size_t smem) {
+  // Opt in to more than 48 KB of dynamic shared memory once per kernel.
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+int sm_count() {
+  static int count = 0;
+  if (!count) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev);
+    if (count <= 0) count = 152;
+  }
+  return count;
+}
+
+// Rows per chunk: as many chunks as fill one wave of resident warps, at
+// least 64 rows each, rounded up to a multiple of 8.
+int pick_rows(int n, int nstrips, int blocks_per_sm, int R_override) {
+  if (R_override > 0) return (R_override + 7) / 8 * 8;
+  long long slots = (long long)sm_count() * blocks_per_sm * fz::kWarps;
+  long long nchunks = slots / nstrips;
+  if (nchunks < 1) nchunks = 1;
+  int R = (int)((n + nchunks - 1) / nchunks);
+  R = (R + 7) / 8 * 8;
+  if (R < 64) R = 64;
+  return R;
+}
+
+fz::Args2D make_args(const Level &L, const Level &Cl, double omega, int R_override, int blocks_per_sm) {
+  fz::Args2D a;
+  memset(&a, 0, sizeof a);
+  a.n = L.n;
+  a.pitch = L.pitch;
+  a.nc = Cl.n;
+  a.pitchc = Cl.pitch;
+  a.nstrips = (L.n + fz::kOut - 1) / fz::kOut;
+  a.R = pick_rows(L.n, a.nstrips, blocks_per_sm, R_override);
+  a.nchunks = (L.n + a.R - 1) / a.R;
+  double cx = L.c[0] * L.inv_h2, cy = L.c[1] * L.inv_h2;
+  double diag = 2.0 * (cx + cy);
+  a.alpha = omega / diag;
+  a.betax = omega * cx / diag;
+  a.betay = omega * cy / diag;
+  a.gamma = 1.0 - omega;
+  a.cx = cx;
+  a.cy = cy;
+  return a;
+}
+
+template <typename T, int NU, bool ZERO>
+cudaError_t launch_pre(fz::Args2D a, int R_override, const Level &L, cudaStream_t s) {
+  constexpr size_t smem = (size_t)fz::kWarps * fz::kSlots * 32 * fz::Lane<T>::bytes * 2;
+  static bool ready = false;
+  static int bps = 1;
+  if (!ready) {
+    cudaError_t e = prepare(fz::k_pre2d<T, NU, ZERO>, smem);
+    if (e != cudaSuccess) return e;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fz::k_pre2d<T, NU, ZERO>, 32 * fz::kWarps, smem);
+    if (bps < 1) bps = 1;
+    ready = true;
+  }
+  if (R_override <= 0) {
+    a.R = pick_rows(L.n, a.nstrips, bps, 0);
+    a.nchunks = (L.n + a.R - 1) / a.R;
+  }
+  long long warps = (long long)a.nstrips * a.nchunks;
+  unsigned blocks = (unsigned)((warps + fz::kWarps - 1) / fz::kWarps);
+  fz::k_pre2d<T, NU, ZERO><<<blocks, 32 * fz::kWarps, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, int NU>
+cudaError_t launch_post(fz::Args2D a, int R_override, const Level &L, cudaStream_t s) {
+  constexpr size_t smem = (size_t)fz::kWarps * fz::kSlots * 32 * (2 * fz::Lane<T>::bytes + 16);
+  static bool ready = false;
+  static int bps = 1;
+  if (!ready) {
+    cudaError_t e = prepare(fz::k_post2d<T, NU>, smem);
+    if (e != cudaSuccess) return e;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fz::k_post2d<T, NU>, 32 * fz::kWarps, smem);
+    if (bps < 1) bps = 1;
+    ready = true;
+  }
+  if (R_override <= 0) {
+    a.R = pick_rows(L.n, a.nstrips, bps, 0);
+    a.nchunks = (L.n + a.R - 1) / a.R;
+  }
+  long long warps = (long long)a.nstrips * a.nchunks;
+  unsigned blocks = (unsigned)((warps + fz::kWarps - 1) / fz::kWarps);
+  fz::k_post2d<T, NU><<<blocks, 32 * fz::kWarps, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool fused_ok(const Level &L, const Level &Cl, int nu) {
+  return L.dim == 2 && !L.kf[0] && (L.dtype == F64 || L.dtype == F32) && Cl.dtype == L.dtype &&
+         (nu == 1 || nu == 2) && L.n >= 33;
+}
+
+cudaError_t pre_fused(const Level &L, const void *uin, void *uout, const Level &Cl, void *fc, bool zero, int nu,
+                      double omega, int R, cudaStream_t s) {
+  fz::Args2D a = make_args(L, Cl, omega, R, 1);
+  a.uin = uin;
+  a.f = L.f;
+  a.uout = uout;
+  a.fc = fc;
+  if (L.dtype == F32) {
+    if (nu == 1) return zero ? launch_pre<float, 1, true>(a, R, L, s) : launch_pre<float, 1, false>(a, R, L, s);
+    return zero ? launch_pre<float, 2, true>(a, R, L, s) : launch_pre<float, 2, false>(a, R, L, s);
+  }
+  if (nu == 1) return zero ? launch_pre<double, 1, true>(a, R, L, s) : launch_pre<double, 1, false>(a, R, L, s);
+  return zero ? launch_pre<double, 2, true>(a, R, L, s) : launch_pre<double, 2, false>(a, R, L, s);
+}
+
+cudaError_t post_fused(const Level &L, const void *uin, void *uout, const Level &Cl, const void *ec, int nu,
+                       double omega, int R, cudaStream_t s) {
+  fz::Args2D a = make_args(L, Cl, omega, R, 1);
+  a.uin = uin;
+  a.f = L.f;
+  a.uout = uout;
+  a.ec = ec;
+  if (L.dtype == F32) return nu == 1 ? launch_post<float, 1>(a, R, L, s) : launch_post<float, 2>(a, R, L, s);
+  return nu == 1 ? launch_post<double, 1>(a, R, L, s) : launch_post<double, 2>(a, R, L, s);
+}
+
+}  // namespace d2
+}  // namespace mg

@@ -258,16 +258,36 @@ mg_status op_zero_u(mg_ctx *c, int l, cudaStream_t s) {
   return MG_OK;
 }
 
+// True when level l's pre- and post-smoothing run as fused 2D kernels.
+bool level_fused(mg_ctx *c, int l) {
+  if (!c->opt.fuse || c->opt.smoother != MG_RBGS || l + 1 >= c->nl) return false;
+  return mg::d2::fused_ok(c->lv[l], c->lv[l + 1], c->opt.nu1) && mg::d2::fused_ok(c->lv[l], c->lv[l + 1], c->opt.nu2);
+}
+
 // Algorithm 1 from level l down: presmooth, residual, restrict, zero the
-// coarse solution, recurse, interpolate and correct, postsmooth.
-mg_status vcycle_rec(mg_ctx *c, int l, cudaStream_t s) {
+// coarse solution, recurse, interpolate and correct, postsmooth. `zero`
+// says that u_l is zero on entry (every coarse level, and the finest level
+// of a defect-correction step), which lets the fused kernels skip reading it.
+mg_status vcycle_rec(mg_ctx *c, int l, bool zero, cudaStream_t s) {
   mg_status st;
-  if (l == c->nl - 1) return op_coarse(c, s);
+  if (l == c->nl - 1) {
+    if (zero && (st = op_zero_u(c, l, s))) return st;
+    return op_coarse(c, s);
+  }
+  Level &L = c->lv[l], &C = c->lv[l + 1];
+  if (level_fused(c, l)) {
+    LAUNCH(c, mg::d2::pre_fused(L, L.u[L.cur], L.u[L.cur ^ 1], C, C.f, zero, c->opt.nu1, c->opt.omega, 0, s));
+    L.cur ^= 1;
+    if ((st = vcycle_rec(c, l + 1, true, s))) return st;
+    LAUNCH(c, mg::d2::post_fused(L, L.u[L.cur], L.u[L.cur ^ 1], C, C.u[C.cur], c->opt.nu2, c->opt.omega, 0, s));
+    L.cur ^= 1;
+    return MG_OK;
+  }
+  if (zero && (st = op_zero_u(c, l, s))) return st;
   if ((st = op_smooth(c, l, c->opt.nu1, s))) return st;
   if ((st = op_residual(c, l, s))) return st;
   if ((st = op_restrict(c, l, s))) return st;
-  if ((st = op_zero_u(c, l + 1, s))) return st;
-  if ((st = vcycle_rec(c, l + 1, s))) return st;
+  if ((st = vcycle_rec(c, l + 1, true, s))) return st;
   if ((st = op_prolong(c, l, s))) return st;
   return op_smooth(c, l, c->opt.nu2, s);
 }
@@ -288,8 +308,7 @@ mg_status op_norm(mg_ctx *c, int l, cudaStream_t s) {
 // e = V(0, d); u += e.
 mg_status dc_inner_and_update(mg_ctx *c, cudaStream_t s) {
   mg_status st;
-  if ((st = op_zero_u(c, 0, s))) return st;
-  if ((st = vcycle_rec(c, 0, s))) return st;
+  if ((st = vcycle_rec(c, 0, true, s))) return st;
   Level &O = c->outer, &I = c->lv[0];
   LAUNCH(c, DISPATCH(O, dc_update, O, O.u[0], I, I.u[I.cur], s));
   return MG_OK;
@@ -300,7 +319,7 @@ mg_status dc_inner_and_update(mg_ctx *c, cudaStream_t s) {
 mg_status record(mg_ctx *c, int kind, cudaStream_t s) {
   mg_status st;
   if (!c->dc) {
-    if ((st = vcycle_rec(c, 0, s))) return st;
+    if ((st = vcycle_rec(c, 0, false, s))) return st;
     if (kind == 1) return op_norm(c, 0, s);
     return MG_OK;
   }

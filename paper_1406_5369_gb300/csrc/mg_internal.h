@@ -65,6 +65,17 @@ namespace d3 {
 MG_DIM_OPS
 }
 
+// Fused 2D fine-level kernels (constant stencil, RBGS): nu sweeps +
+// residual + restriction into fc, and interpolation/correction + nu sweeps.
+// R = rows per chunk (0 = automatic).
+namespace d2 {
+bool fused_ok(const Level &L, const Level &Cl, int nu);
+cudaError_t pre_fused(const Level &L, const void *uin, void *uout, const Level &Cl, void *fc, bool zero, int nu,
+                      double omega, int R, cudaStream_t s);
+cudaError_t post_fused(const Level &L, const void *uin, void *uout, const Level &Cl, const void *ec, int nu,
+                       double omega, int R, cudaStream_t s);
+}  // namespace d2
+
 // Sets the message mg_last_error() returns on the calling thread.
 void set_error_message(const char *msg);
 
