@@ -160,6 +160,9 @@ def run_gpu(args):
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1) / args.steps
     launches = s.kernel_launches() - launches0
+    # Every kernel of this process so far was launched by `s`, so this range
+    # locates the timed region in an ncu launch list (-s START -c COUNT).
+    print(f"[bench] timed-region kernel launches: start={launches0} count={launches}", file=sys.stderr, flush=True)
     if world > 1:
         t = torch.tensor([ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)

@@ -1,0 +1,288 @@
+// Single-block V-cycle on the small coarse levels (Algorithm 1 below a size
+// threshold): one block of 1024 threads loads the top level's right-hand
+// side (and solution, unless it starts from zero), runs presmoothing,
+// residual, full weighting, the exact 3^dim solve, interpolation and
+// postsmoothing on every level below in shared memory with block barriers
+// between the stages, and writes the top level's solution back. It replaces
+// some 10 kernel launches per level, whose latency dominates these levels.
+//
+// Arithmetic runs in C (double in FP64 contexts, float for the inner levels
+// of defect correction); the 3^dim solve runs in FP64 as everywhere else.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace mg {
+namespace cz {
+
+constexpr int kThreads = 1024;
+constexpr int kMaxLev = 8;
+
+struct CoarseArgs {
+  int dim, nlev;           // levels handled: top (index 0 here) .. coarsest
+  int n[kMaxLev];
+  double inv_h2[kMaxLev];
+  double c[3];
+  int var;                 // face coefficients present
+  const void *kf[kMaxLev][3];
+  int kf64[kMaxLev];       // faces stored as double (else float)
+  int pitch[kMaxLev];      // element pitch of each level's global arrays
+  long long plane[kMaxLev];
+  const void *f_top;       // top level right-hand side (global)
+  void *u_top;             // top level solution (global, read unless zero_top)
+  int top_dtype;           // DType of the top level's fields
+  int zero_top;
+  int smoother;            // 0 RBGS, 1 Jacobi
+  double omega;
+  int nu1, nu2;
+};
+
+__device__ __forceinline__ double ldg_any(const void *p, long long i, int dtype) {
+  if (dtype == F64) return ((const double *)p)[i];
+  if (dtype == F32) return (double)((const float *)p)[i];
+  return (double)__bfloat162float(((const bf16 *)p)[i]);
+}
+__device__ __forceinline__ void stg_any(void *p, long long i, int dtype, double v) {
+  if (dtype == F64) ((double *)p)[i] = v;
+  else if (dtype == F32) ((float *)p)[i] = (float)v;
+  else ((bf16 *)p)[i] = __float2bfloat16_rn((float)v);
+}
+
+template <int DIM> __device__ __forceinline__ int npts(int n) { return DIM == 3 ? n * n * n : n * n; }
+
+// Interior node t (0 <= t < (n-2)^DIM) of a dense n^DIM array.
+template <int DIM> __device__ __forceinline__ int inode(int t, int n, int &i, int &j, int &k) {
+  int m = n - 2;
+  i = 1 + t % m;
+  int rest = t / m;
+  j = 1 + (DIM == 3 ? rest % m : rest);
+  k = DIM == 3 ? 1 + rest / m : 0;
+  return (k * n + j) * n + i;
+}
+
+template <int DIM, typename C>
+struct Lev {
+  C *u, *f, *kx, *ky, *kz;
+  int n;
+  C ih2;
+};
+
+// A u and diag at dense node p.
+template <int DIM, bool VAR, typename C>
+__device__ __forceinline__ void dense_apply(const Lev<DIM, C> &L, const C *u, int p, const C (&c)[3], C &Au,
+                                            C &dg) {
+  int sy = L.n, sz = L.n * L.n;
+  C u0 = u[p];
+  if (!VAR) {
+    C acc = c[0] * ((u0 - u[p - 1]) + (u0 - u[p + 1])) + c[1] * ((u0 - u[p - sy]) + (u0 - u[p + sy]));
+    C d = c[0] + c[1];
+    if (DIM == 3) {
+      acc += c[2] * ((u0 - u[p - sz]) + (u0 - u[p + sz]));
+      d += c[2];
+    }
+    Au = acc * L.ih2;
+    dg = (C)2 * d * L.ih2;
+  } else {
+    C kxp = L.kx[p], kxm = L.kx[p - 1], kyp = L.ky[p], kym = L.ky[p - sy];
+    C acc = kxp * (u0 - u[p + 1]) + kxm * (u0 - u[p - 1]) + kyp * (u0 - u[p + sy]) + kym * (u0 - u[p - sy]);
+    C d = kxp + kxm + kyp + kym;
+    if (DIM == 3) {
+      C kzp = L.kz[p], kzm = L.kz[p - sz];
+      acc += kzp * (u0 - u[p + sz]) + kzm * (u0 - u[p - sz]);
+      d += kzp + kzm;
+    }
+    Au = acc * L.ih2;
+    dg = d * L.ih2;
+  }
+}
+
+template <int DIM, bool VAR, typename C>
+__device__ void smooth(const Lev<DIM, C> &L, C *tmp, const C (&c)[3], int smoother, C omega, int sweeps) {
+  int m = L.n - 2;
+  int cnt = DIM == 3 ? m * m * m : m * m;
+  // constant stencil: omega / diag once per level instead of a division per node
+  const C wconst = omega / ((C)2 * (c[0] + c[1] + (DIM == 3 ? c[2] : (C)0)) * L.ih2);
+  for (int s = 0; s < sweeps; s++) {
+    if (smoother == 0) {
+      for (int color = 0; color < 2; color++) {
+        for (int t = threadIdx.x; t < cnt; t += kThreads) {
+          int i, j, k;
+          int p = inode<DIM>(t, L.n, i, j, k);
+          if (((i + j + k) & 1) != color) continue;
+          C Au, dg;
+          dense_apply<DIM, VAR>(L, L.u, p, c, Au, dg);
+          L.u[p] = L.u[p] + (VAR ? omega / dg : wconst) * (L.f[p] - Au);
+        }
+        __syncthreads();
+      }
+    } else {
+      int N = npts<DIM>(L.n);
+      for (int p = threadIdx.x; p < N; p += kThreads) tmp[p] = L.u[p];
+      __syncthreads();
+      for (int t = threadIdx.x; t < cnt; t += kThreads) {
+        int i, j, k;
+        int p = inode<DIM>(t, L.n, i, j, k);
+        C Au, dg;
+        dense_apply<DIM, VAR>(L, tmp, p, c, Au, dg);
+        L.u[p] = tmp[p] + (VAR ? omega / dg : wconst) * (L.f[p] - Au);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <int DIM, bool VAR, typename C>
+__global__ void __launch_bounds__(kThreads) k_coarse_cycle(CoarseArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *sm = (C *)smem_raw;
+  const C c[3] = {(C)a.c[0], (C)a.c[1], (C)a.c[2]};
+  const C omega = (C)a.omega;
+  Lev<DIM, C> L[kMaxLev];
+  // carve: per level u, f (, faces); then one scratch array of the top size
+  int off = 0;
+  for (int l = 0; l < a.nlev; l++) {
+    int N = npts<DIM>(a.n[l]);
+    L[l].n = a.n[l];
+    L[l].ih2 = (C)a.inv_h2[l];
+    L[l].u = sm + off; off += N;
+    L[l].f = sm + off; off += N;
+    L[l].kx = L[l].ky = L[l].kz = nullptr;
+    if (VAR) {
+      L[l].kx = sm + off; off += N;
+      L[l].ky = sm + off; off += N;
+      if (DIM == 3) { L[l].kz = sm + off; off += N; }
+    }
+  }
+  C *tmp = sm + off;
+  int total = off + npts<DIM>(a.n[0]);
+  for (int p = threadIdx.x; p < total; p += kThreads) sm[p] = (C)0;
+  __syncthreads();
+  // load the top level (and the faces of every level)
+  {
+    int n = a.n[0], N = npts<DIM>(n);
+    for (int p = threadIdx.x; p < N; p += kThreads) {
+      int i = p % n, j = (p / n) % n, k = DIM == 3 ? p / (n * n) : 0;
+      long long g = (long long)k * a.plane[0] + (long long)j * a.pitch[0] + i;
+      L[0].f[p] = (C)ldg_any(a.f_top, g, a.top_dtype);
+      if (!a.zero_top) L[0].u[p] = (C)ldg_any(a.u_top, g, a.top_dtype);
+    }
+    if (VAR) {
+      for (int l = 0; l < a.nlev; l++) {
+        int nl = a.n[l], Nl = npts<DIM>(nl);
+        C *dst[3] = {L[l].kx, L[l].ky, L[l].kz};
+        for (int d = 0; d < DIM; d++) {
+          for (int p = threadIdx.x; p < Nl; p += kThreads) {
+            int i = p % nl, j = (p / nl) % nl, k = DIM == 3 ? p / (nl * nl) : 0;
+            long long g = (long long)k * a.plane[l] + (long long)j * a.pitch[l] + i;
+            dst[d][p] = a.kf64[l] ? (C)((const double *)a.kf[l][d])[g] : (C)((const float *)a.kf[l][d])[g];
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // descend
+  for (int l = 0; l + 1 < a.nlev; l++) {
+    const Lev<DIM, C> &F = L[l];
+    const Lev<DIM, C> &G = L[l + 1];
+    smooth<DIM, VAR, C>(F, tmp, c, a.smoother, omega, a.nu1);
+    // residual into tmp
+    int m = F.n - 2, cnt = DIM == 3 ? m * m * m : m * m;
+    int N = npts<DIM>(F.n);
+    for (int p = threadIdx.x; p < N; p += kThreads) tmp[p] = (C)0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < cnt; t += kThreads) {
+      int i, j, k;
+      int p = inode<DIM>(t, F.n, i, j, k);
+      C Au, dg;
+      dense_apply<DIM, VAR>(F, F.u, p, c, Au, dg);
+      tmp[p] = F.f[p] - Au;
+    }
+    __syncthreads();
+    // full weighting into the coarse right-hand side; coarse u stays 0
+    int mc = G.n - 2, cc = DIM == 3 ? mc * mc * mc : mc * mc;
+    for (int t = threadIdx.x; t < cc; t += kThreads) {
+      int I, J, K;
+      int P = inode<DIM>(t, G.n, I, J, K);
+      int nf = F.n;
+      C acc = 0;
+      for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); dz++)
+        for (int dy = -1; dy <= 1; dy++)
+          for (int dx = -1; dx <= 1; dx++) {
+            C w = (dx == 0 ? (C)0.5 : (C)0.25) * (dy == 0 ? (C)0.5 : (C)0.25) *
+                  (DIM == 3 ? (dz == 0 ? (C)0.5 : (C)0.25) : (C)1);
+            int q = ((DIM == 3 ? 2 * K + dz : 0) * nf + 2 * J + dy) * nf + 2 * I + dx;
+            acc += w * tmp[q];
+          }
+      G.f[P] = acc;
+      G.u[P] = (C)0;
+    }
+    __syncthreads();
+  }
+  // coarsest: 3^dim grid, one unknown, solved exactly in FP64
+  if (threadIdx.x == 0) {
+    const Lev<DIM, C> &Z = L[a.nlev - 1];
+    int p = DIM == 3 ? 13 : 4;
+    double ih2 = a.inv_h2[a.nlev - 1];
+    double dg, acc = 0.0;
+    int sy = 3, sz = 9;
+    double u0 = (double)Z.u[p];
+    if (!VAR) {
+      double d = a.c[0] + a.c[1] + (DIM == 3 ? a.c[2] : 0.0);
+      acc = a.c[0] * ((u0 - (double)Z.u[p - 1]) + (u0 - (double)Z.u[p + 1])) +
+            a.c[1] * ((u0 - (double)Z.u[p - sy]) + (u0 - (double)Z.u[p + sy]));
+      if (DIM == 3) acc += a.c[2] * ((u0 - (double)Z.u[p - sz]) + (u0 - (double)Z.u[p + sz]));
+      dg = 2.0 * d * ih2;
+    } else {
+      double kxp = Z.kx[p], kxm = Z.kx[p - 1], kyp = Z.ky[p], kym = Z.ky[p - sy];
+      acc = kxp * (u0 - (double)Z.u[p + 1]) + kxm * (u0 - (double)Z.u[p - 1]) + kyp * (u0 - (double)Z.u[p + sy]) +
+            kym * (u0 - (double)Z.u[p - sy]);
+      double d = kxp + kxm + kyp + kym;
+      if (DIM == 3) {
+        double kzp = Z.kz[p], kzm = Z.kz[p - sz];
+        acc += kzp * (u0 - (double)Z.u[p + sz]) + kzm * (u0 - (double)Z.u[p - sz]);
+        d += kzp + kzm;
+      }
+      dg = d * ih2;
+    }
+    Z.u[p] = (C)(u0 + ((double)Z.f[p] - acc * ih2) / dg);
+  }
+  __syncthreads();
+  // ascend: interpolation and correction, postsmoothing
+  for (int l = a.nlev - 2; l >= 0; l--) {
+    const Lev<DIM, C> &F = L[l];
+    const Lev<DIM, C> &G = L[l + 1];
+    int m = F.n - 2, cnt = DIM == 3 ? m * m * m : m * m;
+    int nc = G.n;
+    for (int t = threadIdx.x; t < cnt; t += kThreads) {
+      int i, j, k;
+      int p = inode<DIM>(t, F.n, i, j, k);
+      int I = i >> 1, J = j >> 1, K = k >> 1;
+      int oi = i & 1, oj = j & 1, ok = DIM == 3 ? (k & 1) : 0;
+      C acc = 0;
+      for (int a3 = 0; a3 <= ok; a3++)
+        for (int b = 0; b <= oj; b++) {
+          const C *row = G.u + ((K + a3) * nc + J + b) * nc + I;
+          acc += oi ? (C)0.5 * (row[0] + row[1]) : row[0];
+        }
+      C w = (oj ? (C)0.5 : (C)1) * (ok ? (C)0.5 : (C)1);
+      F.u[p] += w * acc;
+    }
+    __syncthreads();
+    smooth<DIM, VAR, C>(F, tmp, c, a.smoother, omega, a.nu2);
+  }
+  // write back the top level's solution
+  {
+    int n = a.n[0], N = npts<DIM>(n);
+    for (int p = threadIdx.x; p < N; p += kThreads) {
+      int i = p % n, j = (p / n) % n, k = DIM == 3 ? p / (n * n) : 0;
+      bool inter = i >= 1 && i <= n - 2 && j >= 1 && j <= n - 2 && (DIM == 2 || (k >= 1 && k <= n - 2));
+      if (!inter) continue;
+      long long g = (long long)k * a.plane[0] + (long long)j * a.pitch[0] + i;
+      stg_any(a.u_top, g, a.top_dtype, (double)L[0].u[p]);
+    }
+  }
+}
+
+}  // namespace cz
+}  // namespace mg

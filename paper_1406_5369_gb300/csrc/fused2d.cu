@@ -25,16 +25,17 @@ int sm_count() {
   return count;
 }
 
-// Rows per chunk: as many chunks as fill one wave of resident warps, at
-// least 64 rows each, rounded up to a multiple of 8.
-int pick_rows(int n, int nstrips, int blocks_per_sm, int R_override) {
+// Rows per chunk: as many chunks as fill one wave of resident warps,
+// rounded up to a multiple of 8. Small levels get 8-row chunks: each warp
+// then walks only 3 blocks of 8 rows, which keeps their latency short.
+int pick_rows(int n, int nstrips, int blocks_per_sm, int warps_per_block, int R_override) {
   if (R_override > 0) return (R_override + 7) / 8 * 8;
-  long long slots = (long long)sm_count() * blocks_per_sm * fz::kWarps;
+  long long slots = (long long)sm_count() * blocks_per_sm * warps_per_block;
   long long nchunks = slots / nstrips;
   if (nchunks < 1) nchunks = 1;
   int R = (int)((n + nchunks - 1) / nchunks);
   R = (R + 7) / 8 * 8;
-  if (R < 64) R = 64;
+  if (R < 8) R = 8;
   return R;
 }
 
@@ -46,7 +47,7 @@ fz::Args2D make_args(const Level &L, const Level &Cl, double omega, int R_overri
   a.nc = Cl.n;
   a.pitchc = Cl.pitch;
   a.nstrips = (L.n + fz::kOut - 1) / fz::kOut;
-  a.R = pick_rows(L.n, a.nstrips, blocks_per_sm, R_override);
+  a.R = pick_rows(L.n, a.nstrips, blocks_per_sm, 1, R_override);
   a.nchunks = (L.n + a.R - 1) / a.R;
   double cx = L.c[0] * L.inv_h2, cy = L.c[1] * L.inv_h2;
   double diag = 2.0 * (cx + cy);
@@ -61,45 +62,47 @@ fz::Args2D make_args(const Level &L, const Level &Cl, double omega, int R_overri
 
 template <typename T, int NU, bool ZERO>
 cudaError_t launch_pre(fz::Args2D a, int R_override, const Level &L, cudaStream_t s) {
-  constexpr size_t smem = (size_t)fz::kWarps * fz::kSlots * 32 * fz::Lane<T>::bytes * 2;
+  constexpr int W = fz::Warps<T>::value;
+  constexpr size_t smem = (size_t)W * fz::kRing * 32 * fz::Lane<T>::bytes * 2;
   static bool ready = false;
   static int bps = 1;
   if (!ready) {
     cudaError_t e = prepare(fz::k_pre2d<T, NU, ZERO>, smem);
     if (e != cudaSuccess) return e;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fz::k_pre2d<T, NU, ZERO>, 32 * fz::kWarps, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fz::k_pre2d<T, NU, ZERO>, 32 * W, smem);
     if (bps < 1) bps = 1;
     ready = true;
   }
   if (R_override <= 0) {
-    a.R = pick_rows(L.n, a.nstrips, bps, 0);
+    a.R = pick_rows(L.n, a.nstrips, bps, W, 0);
     a.nchunks = (L.n + a.R - 1) / a.R;
   }
   long long warps = (long long)a.nstrips * a.nchunks;
-  unsigned blocks = (unsigned)((warps + fz::kWarps - 1) / fz::kWarps);
-  fz::k_pre2d<T, NU, ZERO><<<blocks, 32 * fz::kWarps, smem, s>>>(a);
+  unsigned blocks = (unsigned)((warps + W - 1) / W);
+  fz::k_pre2d<T, NU, ZERO><<<blocks, 32 * W, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 template <typename T, int NU>
 cudaError_t launch_post(fz::Args2D a, int R_override, const Level &L, cudaStream_t s) {
-  constexpr size_t smem = (size_t)fz::kWarps * fz::kSlots * 32 * (2 * fz::Lane<T>::bytes + 16);
+  constexpr int W = fz::Warps<T>::value;
+  constexpr size_t smem = (size_t)W * fz::kRing * 32 * (2 * fz::Lane<T>::bytes + 16);
   static bool ready = false;
   static int bps = 1;
   if (!ready) {
     cudaError_t e = prepare(fz::k_post2d<T, NU>, smem);
     if (e != cudaSuccess) return e;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fz::k_post2d<T, NU>, 32 * fz::kWarps, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fz::k_post2d<T, NU>, 32 * W, smem);
     if (bps < 1) bps = 1;
     ready = true;
   }
   if (R_override <= 0) {
-    a.R = pick_rows(L.n, a.nstrips, bps, 0);
+    a.R = pick_rows(L.n, a.nstrips, bps, W, 0);
     a.nchunks = (L.n + a.R - 1) / a.R;
   }
   long long warps = (long long)a.nstrips * a.nchunks;
-  unsigned blocks = (unsigned)((warps + fz::kWarps - 1) / fz::kWarps);
-  fz::k_post2d<T, NU><<<blocks, 32 * fz::kWarps, smem, s>>>(a);
+  unsigned blocks = (unsigned)((warps + W - 1) / W);
+  fz::k_post2d<T, NU><<<blocks, 32 * W, smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -10,10 +10,12 @@
 // Work decomposition: one warp owns a strip of 128 columns (lane l holds the
 // 4 consecutive columns x0 + 4l .. x0 + 4l + 3) and a chunk of R rows. The
 // outer 8 columns on each side are a halo recomputed redundantly, so each
-// warp writes 112 columns and needs no barrier. Rows stream through an
-// 8-slot ring in shared memory filled by cp.async (each lane copies, and
-// later reads back, only its own 16-byte pieces, so a lane's own
-// wait_group is the only synchronisation). Half-sweep h of the stack runs
+// warp writes 112 columns and needs no barrier. Rows stream in blocks of 8
+// through a 16-row ring in shared memory filled by cp.async, one commit
+// group per block, issued one block ahead (each lane copies, and later reads
+// back, only its own 16-byte pieces, so a lane's own wait_group is the only
+// synchronisation). The 8 rows of a block are processed by straight-line
+// code, which lets the compiler overlap consecutive rows. Half-sweep h of the stack runs
 // on row t - h when row t arrives (red = i+j even first, as in the paper's
 // "order rb"), so every update sees exactly the neighbour values a
 // sequential red-then-black sweep would; the x-neighbours of a lane's edge
@@ -40,9 +42,10 @@ constexpr int kVec = 4;                  // columns per lane
 constexpr int kCols = 32 * kVec;         // columns per warp strip (loaded)
 constexpr int kHalo = 8;                 // halo columns on each side
 constexpr int kOut = kCols - 2 * kHalo;  // columns written per strip
-constexpr int kSlots = 8;                // row ring (registers and shared memory)
-constexpr int kPf = 6;                   // rows in flight ahead of the consumer
-constexpr int kWarps = 4;                // warps per block
+constexpr int kSlots = 8;                // row window in registers
+constexpr int kRing = 16;                // row ring in shared memory: two blocks of 8 rows
+// Warps per block: the shared-memory ring of FP64 rows is twice as large.
+template <typename T> struct Warps { static constexpr int value = sizeof(T) == 8 ? 2 : 4; };
 
 struct Args2D {
   const void *uin;  // level solution (ignored when starting from zero)
@@ -109,7 +112,7 @@ __device__ __forceinline__ void store_lane(T *dst, const C (&v)[kVec]) {
 }
 
 template <typename C> struct Coef {
-  C alpha, bx, by, gamma, cx, cy;
+  C alpha, bx, by, gamma, cx, cy, cd;
   bool has_gamma;
 };
 
@@ -138,7 +141,10 @@ __device__ __forceinline__ void half_sweep(C (&uc)[kVec], const C (&ua)[kVec], c
   }
 }
 
-// Residual of row r (difference form, as accurate as the operator allows).
+// Residual of row r. FP64 uses the difference form (u - u_nbr first), which
+// keeps the rounding error at the size of A u itself; FP32 inner cycles use
+// f - cd u + cx (uw + ue) + cy (us + un) (five operations), whose larger
+// rounding error the defect-correction outer loop absorbs.
 template <typename C>
 __device__ __forceinline__ void residual_row(C (&rr)[kVec], const C (&uc)[kVec], const C (&ua)[kVec],
                                              const C (&ub)[kVec], const C (&fr)[kVec], int r, int c0, int n,
@@ -150,20 +156,26 @@ __device__ __forceinline__ void residual_row(C (&rr)[kVec], const C (&uc)[kVec],
     C u = uc[q];
     C uw = q == 0 ? left : uc[q - 1];
     C ue = q == kVec - 1 ? right : uc[q + 1];
-    C t = k.cx * ((u - uw) + (u - ue)) + k.cy * ((u - ua[q]) + (u - ub[q]));
+    C res;
+    if (sizeof(C) == 8) {
+      C t = k.cx * ((u - uw) + (u - ue)) + k.cy * ((u - ua[q]) + (u - ub[q]));
+      res = fr[q] - t;
+    } else {
+      res = k.cy * (ua[q] + ub[q]) + (k.cx * (uw + ue) + (fr[q] - k.cd * u));
+    }
     int c = c0 + q;
-    rr[q] = (rowok && c >= 1 && c <= n - 2) ? fr[q] - t : (C)0;
+    rr[q] = (rowok && c >= 1 && c <= n - 2) ? res : (C)0;
   }
 }
 
 // ------------------------------------------------------------------------
 // Pre-smoothing + residual + restriction.
 template <typename T, int NU, bool ZERO>
-__global__ void __launch_bounds__(32 * kWarps) k_pre2d(Args2D a) {
+__global__ void __launch_bounds__(32 * Warps<T>::value) k_pre2d(Args2D a) {
   typedef typename CT<T>::type C;
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const long long gw = (long long)blockIdx.x * kWarps + wib;
+  const long long gw = (long long)blockIdx.x * Warps<T>::value + wib;
   if (gw >= (long long)a.nstrips * a.nchunks) return;
   const int s = (int)(gw % a.nstrips), ch = (int)(gw / a.nstrips);
   const int n = a.n;
@@ -179,11 +191,11 @@ __global__ void __launch_bounds__(32 * kWarps) k_pre2d(Args2D a) {
   T *uout = (T *)a.uout;
   T *fc = (T *)a.fc;
   constexpr int LB = Lane<T>::bytes;
-  unsigned char *su = smem + (size_t)wib * kSlots * 32 * LB * 2;
-  unsigned char *sf = su + kSlots * 32 * LB;
+  unsigned char *su = smem + (size_t)wib * kRing * 32 * LB * 2;
+  unsigned char *sf = su + kRing * 32 * LB;
   Coef<C> k;
   k.alpha = (C)a.alpha; k.bx = (C)a.betax; k.by = (C)a.betay; k.gamma = (C)a.gamma;
-  k.cx = (C)a.cx; k.cy = (C)a.cy; k.has_gamma = a.gamma != 0.0;
+  k.cx = (C)a.cx; k.cy = (C)a.cy; k.cd = (C)(2.0 * (a.cx + a.cy)); k.has_gamma = a.gamma != 0.0;
 
   C U[kSlots][kVec], F[kSlots][kVec], Rr[kSlots][kVec];
 #pragma unroll
@@ -191,32 +203,36 @@ __global__ void __launch_bounds__(32 * kWarps) k_pre2d(Args2D a) {
 #pragma unroll
     for (int q = 0; q < kVec; q++) { U[i][q] = 0; F[i][q] = 0; Rr[i][q] = 0; }
 
-  auto issue = [&](int row) {
-    int slot = row & (kSlots - 1);
-    bool ok = col_ok && row >= 0 && row < n && row <= tend;
-    long long off = (long long)row * a.pitch + c0;
-    if (!ZERO) stage_row<T>(su + (slot * 32 + lane) * LB, uin, off, ok);
-    stage_row<T>(sf + (slot * 32 + lane) * LB, f, off, ok);
+  // Stages the 8 rows starting at tb (one commit group).
+  auto issue_block = [&](int tb) {
+#pragma unroll
+    for (int K = 0; K < kSlots; K++) {
+      int row = tb + K;
+      int slot = row & (kRing - 1);
+      bool ok = col_ok && row >= 0 && row < n && row <= tend;
+      long long off = (long long)row * a.pitch + c0;
+      if (!ZERO) stage_row<T>(su + (slot * 32 + lane) * LB, uin, off, ok);
+      stage_row<T>(sf + (slot * 32 + lane) * LB, f, off, ok);
+    }
     cp_async_commit();
   };
 
-#pragma unroll
-  for (int d = 0; d < kPf; d++) issue(tstart + d);
-
+  issue_block(tstart);
   for (int tb = tstart; tb <= tend; tb += kSlots) {
+    issue_block(tb + kSlots);
+    cp_async_wait<1>();  // block tb has landed; block tb + 8 may be in flight
+    const int ring = tb & (kRing - 1);  // 0 or 8
     static_for<0, kSlots>([&](auto kc) {
       constexpr int K = decltype(kc)::value;
       const int t = tb + K;
-      if (t <= tend) {
-        cp_async_wait<kPf - 1>();
+      {
         if (!ZERO) {
-          load_lane<T, C>(su + (K * 32 + lane) * LB, U[K]);
+          load_lane<T, C>(su + ((ring + K) * 32 + lane) * LB, U[K]);
         } else {
 #pragma unroll
           for (int q = 0; q < kVec; q++) U[K][q] = (C)0;
         }
-        load_lane<T, C>(sf + (K * 32 + lane) * LB, F[K]);
-        issue(t + kPf);
+        load_lane<T, C>(sf + ((ring + K) * 32 + lane) * LB, F[K]);
         // half-sweeps h = 1 .. 2 NU on rows t - h (odd h red, even h black)
 #pragma unroll
         for (int h = 1; h <= 2 * NU; h++) {
@@ -262,11 +278,11 @@ __global__ void __launch_bounds__(32 * kWarps) k_pre2d(Args2D a) {
 // ------------------------------------------------------------------------
 // Interpolation + correction + post-smoothing.
 template <typename T, int NU>
-__global__ void __launch_bounds__(32 * kWarps) k_post2d(Args2D a) {
+__global__ void __launch_bounds__(32 * Warps<T>::value) k_post2d(Args2D a) {
   typedef typename CT<T>::type C;
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const long long gw = (long long)blockIdx.x * kWarps + wib;
+  const long long gw = (long long)blockIdx.x * Warps<T>::value + wib;
   if (gw >= (long long)a.nstrips * a.nchunks) return;
   const int s = (int)(gw % a.nstrips), ch = (int)(gw / a.nstrips);
   const int n = a.n;
@@ -285,12 +301,12 @@ __global__ void __launch_bounds__(32 * kWarps) k_post2d(Args2D a) {
   T *uout = (T *)a.uout;
   constexpr int LB = Lane<T>::bytes;
   constexpr int CB = 2 * (int)sizeof(T);  // two coarse values per lane
-  unsigned char *su = smem + (size_t)wib * kSlots * 32 * (2 * LB + 16);
-  unsigned char *sf = su + kSlots * 32 * LB;
-  unsigned char *se = sf + kSlots * 32 * LB;  // 16 bytes per lane and slot
+  unsigned char *su = smem + (size_t)wib * kRing * 32 * (2 * LB + 16);
+  unsigned char *sf = su + kRing * 32 * LB;
+  unsigned char *se = sf + kRing * 32 * LB;  // 16 bytes per lane and slot
   Coef<C> k;
   k.alpha = (C)a.alpha; k.bx = (C)a.betax; k.by = (C)a.betay; k.gamma = (C)a.gamma;
-  k.cx = (C)a.cx; k.cy = (C)a.cy; k.has_gamma = a.gamma != 0.0;
+  k.cx = (C)a.cx; k.cy = (C)a.cy; k.cd = (C)(2.0 * (a.cx + a.cy)); k.has_gamma = a.gamma != 0.0;
 
   C U[kSlots][kVec], F[kSlots][kVec];
   // Coarse rows by parity of the coarse row index (values at J0, J0+1). Chunks
@@ -304,23 +320,26 @@ __global__ void __launch_bounds__(32 * kWarps) k_post2d(Args2D a) {
 
   // With fine row `row` also stage coarse row I = (row + 1) / 2 when row is
   // odd, and coarse row 0 with fine row 0.
-  auto issue = [&](int row) {
-    int slot = row & (kSlots - 1);
-    bool ok = col_ok && row >= 0 && row < n && row <= tend;
-    long long off = (long long)row * a.pitch + c0;
-    stage_row<T>(su + (slot * 32 + lane) * LB, uin, off, ok);
-    stage_row<T>(sf + (slot * 32 + lane) * LB, f, off, ok);
-    int I = (row & 1) ? (row + 1) >> 1 : (row == 0 ? 0 : -1);
-    bool cok = ccol_ok && row >= 0 && row <= tend && I >= 0 && I < a.nc;
-    const T *csrc = cok ? ec + (long long)I * a.pitchc + J0 : ec;
-    unsigned char *cdst = se + (slot * 32 + lane) * 16;
-    if (CB == 16) cp_async16(cdst, csrc, cok);
-    else cp_async8(cdst, csrc, cok);
+  auto issue_block = [&](int tb) {
+#pragma unroll
+    for (int K = 0; K < kSlots; K++) {
+      int row = tb + K;
+      int slot = row & (kRing - 1);
+      bool ok = col_ok && row >= 0 && row < n && row <= tend;
+      long long off = (long long)row * a.pitch + c0;
+      stage_row<T>(su + (slot * 32 + lane) * LB, uin, off, ok);
+      stage_row<T>(sf + (slot * 32 + lane) * LB, f, off, ok);
+      int I = (row & 1) ? (row + 1) >> 1 : (row == 0 ? 0 : -1);
+      bool cok = ccol_ok && row >= 0 && row <= tend && I >= 0 && I < a.nc;
+      const T *csrc = cok ? ec + (long long)I * a.pitchc + J0 : ec;
+      unsigned char *cdst = se + (slot * 32 + lane) * 16;
+      if (CB == 16) cp_async16(cdst, csrc, cok);
+      else cp_async8(cdst, csrc, cok);
+    }
     cp_async_commit();
   };
 
-#pragma unroll
-  for (int d = 0; d < kPf; d++) issue(tstart + d);
+  issue_block(tstart);
 
   // Coarse row tstart/2 (even index) precedes the window when the chunk starts inside the grid.
   if (tstart > 0) {
@@ -332,16 +351,18 @@ __global__ void __launch_bounds__(32 * kWarps) k_post2d(Args2D a) {
   }
 
   for (int tb = tstart; tb <= tend; tb += kSlots) {
+    issue_block(tb + kSlots);
+    cp_async_wait<1>();
+    const int ring = tb & (kRing - 1);
     static_for<0, kSlots>([&](auto kc) {
       constexpr int K = decltype(kc)::value;
       const int t = tb + K;
-      if (t <= tend) {
-        cp_async_wait<kPf - 1>();
-        load_lane<T, C>(su + (K * 32 + lane) * LB, U[K]);
-        load_lane<T, C>(sf + (K * 32 + lane) * LB, F[K]);
+      {
+        load_lane<T, C>(su + ((ring + K) * 32 + lane) * LB, U[K]);
+        load_lane<T, C>(sf + ((ring + K) * 32 + lane) * LB, F[K]);
         if ((K & 1) || t == 0) {
           constexpr int PI = ((K + 1) >> 1) & 1;  // parity of I = (t + 1) / 2
-          const unsigned char *cs = se + (K * 32 + lane) * 16;
+          const unsigned char *cs = se + ((ring + K) * 32 + lane) * 16;
           if (sizeof(T) == 4) {
             float2 v = *(const float2 *)cs;
             E[PI][0] = (C)v.x; E[PI][1] = (C)v.y;
@@ -350,7 +371,6 @@ __global__ void __launch_bounds__(32 * kWarps) k_post2d(Args2D a) {
             E[PI][0] = (C)v.x; E[PI][1] = (C)v.y;
           }
         }
-        issue(t + kPf);
         // interpolation and correction of row t
         {
           C e0, e1;

@@ -66,9 +66,10 @@ struct mg_ctx {
   cudaStream_t stream;    // user stream
   cudaStream_t cap;       // private stream used for graph capture
   Level lv[kMaxLevels];   // working hierarchy (FP64, or the inner DC hierarchy)
-  Level outer;            // DC: outer FP64 finest level (u[0], f, r = FP64 staging, kf)
-  double *partials;       // kNormBlocks doubles
+  Level outer;            // DC: outer FP64 finest level (u[0..1] ping-pong, f, r = FP64 staging, kf)
+  double *partials;       // kMaxPartials doubles
   double *norm_out;       // [0] = norm, [1] = sum of squares
+  float *dc_scale;        // power of two applied before squaring in scaled norm passes
   double *host_norm;      // pinned host copy of norm_out
   size_t used_bytes;
   GraphSlot graphs[kGraphSlots];
@@ -168,20 +169,26 @@ size_t layout(mg_ctx *c, char *base) {
     init_level(c->outer, c->dim, c->n, mg::F64, cc);
     size_t bytes = (size_t)c->outer.count * 8;
     c->outer.u[0] = b.take(bytes);
-    c->outer.u[1] = nullptr;
+    c->outer.u[1] = b.take(bytes);
     c->outer.f = b.take(bytes);
     c->outer.r = b.take(bytes);
     if (c->variable)
       for (int d = 0; d < c->dim; d++) c->outer.kf[d] = b.take(bytes);
   }
-  c->partials = (double *)b.take(sizeof(double) * mg::kNormBlocks);
+  c->partials = (double *)b.take(sizeof(double) * mg::kMaxPartials);
   c->norm_out = (double *)b.take(sizeof(double) * 4);
+  c->dc_scale = (float *)b.take(sizeof(float) * 4);
   return align_up(b.off, 256);
 }
 
 // The FP64 level whose u/f the user's finest-level calls address.
 Level &user_level(mg_ctx *c) { return c->dc ? c->outer : c->lv[0]; }
-void *user_u(mg_ctx *c) { return c->dc ? c->outer.u[0] : c->lv[0].u[c->lv[0].cur]; }
+void *user_u(mg_ctx *c) { return c->dc ? c->outer.u[c->outer.cur] : c->lv[0].u[c->lv[0].cur]; }
+
+double interior_count(const Level &L) {
+  double m = (double)(L.n - 2);
+  return L.dim == 3 ? m * m * m : m * m;
+}
 
 // Dense n^dim FP64 (host or device) <-> pitched FP64 field, whole array.
 cudaError_t copy_dense_to_pitched(const Level &L, const double *src, void *dst, cudaStream_t s) {
@@ -210,6 +217,16 @@ cudaError_t copy_dense_interior(const Level &L, const double *src, void *dst, cu
   p.extent = make_cudaExtent(m * 8, m, m);
   p.kind = cudaMemcpyDefault;
   return cudaMemcpy3DAsync(&p, s);
+}
+
+// Zeroes the interior box of a pitched FP64 field (boundary untouched).
+cudaError_t zero_interior_box(const Level &L, void *dst, cudaStream_t s) {
+  size_t n = (size_t)L.n, m = n - 2, es = (size_t)mg::dtype_size(L.dtype);
+  if (L.dim == 2)
+    return cudaMemset2DAsync((char *)dst + ((size_t)L.pitch + 1) * es, (size_t)L.pitch * es, 0, m * es, m, s);
+  cudaPitchedPtr p = make_cudaPitchedPtr((char *)dst + ((size_t)L.plane + L.pitch + 1) * es, (size_t)L.pitch * es,
+                                         m, n);
+  return cudaMemset3DAsync(p, 0, make_cudaExtent(m * es, m, m), s);
 }
 
 // ---------------------------------------------------------------- level ops
@@ -270,6 +287,10 @@ bool level_fused(mg_ctx *c, int l) {
 // of a defect-correction step), which lets the fused kernels skip reading it.
 mg_status vcycle_rec(mg_ctx *c, int l, bool zero, cudaStream_t s) {
   mg_status st;
+  if (c->opt.fuse && c->lv[l].n <= mg::coarse_top_n(c->dim, !c->dc)) {
+    LAUNCH(c, mg::coarse_cycle(c->lv, l, c->nl, zero, c->opt.smoother, c->opt.omega, c->opt.nu1, c->opt.nu2, !c->dc, s));
+    return MG_OK;
+  }
   if (l == c->nl - 1) {
     if (zero && (st = op_zero_u(c, l, s))) return st;
     return op_coarse(c, s);
@@ -292,12 +313,27 @@ mg_status vcycle_rec(mg_ctx *c, int l, bool zero, cudaStream_t s) {
   return op_smooth(c, l, c->opt.nu2, s);
 }
 
+// Residual norm of level l into norm_out[0]. In defect-correction contexts
+// level 0 is the outer FP64 problem; that pass also leaves the defect in the
+// inner level 0's right-hand side and resets the norm scale.
 mg_status op_norm(mg_ctx *c, int l, cudaStream_t s) {
+  int np = 0;
   if (c->dc && l == 0) {
     Level &O = c->outer, &I = c->lv[0];
-    LAUNCH(c, DISPATCH(O, dc_residual, O, O.u[0], O.f, I, I.f, c->partials, mg::kNormBlocks, s));
+    if (mg::d2::outer_ok(O, I)) {
+      LAUNCH(c, mg::d2::dc_step(O, (const double *)O.u[O.cur], nullptr, I, nullptr, I.f, c->partials, &np,
+                                c->dc_scale, false, true, s));
+      LAUNCH(c, mg::norm_finalize_ex(c->partials, np, c->norm_out, nullptr, c->dc_scale, interior_count(O), s));
+      return MG_OK;
+    }
+    LAUNCH(c, DISPATCH(O, dc_residual, O, O.u[O.cur], O.f, I, I.f, c->partials, mg::kNormBlocks, s));
   } else {
     Level &L = c->lv[l];
+    if (mg::d2::norm_ok(L)) {
+      LAUNCH(c, mg::d2::norm_stream(L, L.u[L.cur], L.f, c->partials, &np, s));
+      LAUNCH(c, mg::norm_finalize_ex(c->partials, np, c->norm_out, nullptr, nullptr, interior_count(L), s));
+      return MG_OK;
+    }
     LAUNCH(c, DISPATCH(L, norm_partials, L, L.u[L.cur], L.f, c->partials, mg::kNormBlocks, s));
   }
   LAUNCH(c, mg::norm_finalize(c->partials, mg::kNormBlocks, c->norm_out, s));
@@ -305,12 +341,23 @@ mg_status op_norm(mg_ctx *c, int l, cudaStream_t s) {
 }
 
 // One defect-correction step with the defect d already in lv[0].f:
-// e = V(0, d); u += e.
-mg_status dc_inner_and_update(mg_ctx *c, cudaStream_t s) {
+// e = V(0, d); u += e. With `norm`, the residual of the updated u is
+// computed in the same pass (new defect in lv[0].f, norm in norm_out).
+mg_status dc_inner_and_update(mg_ctx *c, bool norm, cudaStream_t s) {
   mg_status st;
   if ((st = vcycle_rec(c, 0, true, s))) return st;
   Level &O = c->outer, &I = c->lv[0];
-  LAUNCH(c, DISPATCH(O, dc_update, O, O.u[0], I, I.u[I.cur], s));
+  if (mg::d2::outer_ok(O, I)) {
+    int np = 0;
+    LAUNCH(c, mg::d2::dc_step(O, (const double *)O.u[O.cur], (double *)O.u[O.cur ^ 1], I, I.u[I.cur],
+                              norm ? I.f : nullptr, c->partials, &np, c->dc_scale, true, false, s));
+    O.cur ^= 1;
+    if (norm) LAUNCH(c, mg::norm_finalize_ex(c->partials, np, c->norm_out, c->dc_scale, c->dc_scale,
+                                             interior_count(O), s));
+    return MG_OK;
+  }
+  LAUNCH(c, DISPATCH(O, dc_update, O, O.u[O.cur], I, I.u[I.cur], s));
+  if (norm) return op_norm(c, 0, s);
   return MG_OK;
 }
 
@@ -324,21 +371,20 @@ mg_status record(mg_ctx *c, int kind, cudaStream_t s) {
     return MG_OK;
   }
   if (kind == 0) {
-    Level &O = c->outer, &I = c->lv[0];
-    LAUNCH(c, DISPATCH(O, dc_residual, O, O.u[0], O.f, I, I.f, c->partials, mg::kNormBlocks, s));
-    return dc_inner_and_update(c, s);
+    if ((st = op_norm(c, 0, s))) return st;  // leaves the defect in lv[0].f
+    return dc_inner_and_update(c, false, s);
   }
-  if ((st = dc_inner_and_update(c, s))) return st;
-  return op_norm(c, 0, s);
+  return dc_inner_and_update(c, true, s);
 }
 
 unsigned cur_key(mg_ctx *c) {
   unsigned k = 0;
   for (int l = 0; l < c->nl; l++) k |= (unsigned)c->lv[l].cur << l;
-  return k;
+  return k | ((unsigned)c->outer.cur << 31);
 }
 void set_cur(mg_ctx *c, unsigned k) {
   for (int l = 0; l < c->nl; l++) c->lv[l].cur = (k >> l) & 1u;
+  c->outer.cur = (k >> 31) & 1u;
 }
 
 void drop_graphs(mg_ctx *c) {
@@ -496,12 +542,15 @@ mg_status mg_create(int dim, int n, const mg_const_stencil *stencil, const doubl
     CKC(copy_dense_to_pitched(K, k, stage, c->stream));
     Level &F0 = c->dc ? c->outer : c->lv[0];
     CKC(DISPATCH(F0, node_faces, K, (const double *)stage, F0, c->stream));
+    c->launches++;
     if (c->dc) {
       CKC(DISPATCH(F0, convert_faces, c->outer, c->lv[0], c->stream));
       if (c->nl > 1) CKC(DISPATCH(F0, coarsen_faces, c->outer, c->lv[1], c->stream));
       for (int l = 2; l < c->nl; l++) CKC(DISPATCH(F0, coarsen_faces, c->lv[l - 1], c->lv[l], c->stream));
+      c->launches += c->nl;
     } else {
       for (int l = 1; l < c->nl; l++) CKC(DISPATCH(F0, coarsen_faces, c->lv[l - 1], c->lv[l], c->stream));
+      c->launches += c->nl - 1;
     }
     CKC(cudaMemsetAsync(stage, 0, (size_t)K.count * 8, c->stream));
   }
@@ -509,7 +558,12 @@ mg_status mg_create(int dim, int n, const mg_const_stencil *stencil, const doubl
     Level &U = user_level(c);
     CKC(copy_dense_to_pitched(U, bc->dirichlet_values, U.u[0], c->stream));
     CKC(DISPATCH(U, zero_interior, U, U.u[0], c->stream));
-    if (!c->dc) CKC(cudaMemcpyAsync(U.u[1], U.u[0], (size_t)U.count * 8, cudaMemcpyDeviceToDevice, c->stream));
+    c->launches++;
+    CKC(cudaMemcpyAsync(U.u[1], U.u[0], (size_t)U.count * 8, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  {
+    static const float one[4] = {1.0f, 1.0f, 1.0f, 1.0f};
+    CKC(cudaMemcpyAsync(c->dc_scale, one, sizeof one, cudaMemcpyHostToDevice, c->stream));
   }
   CKC(cudaStreamSynchronize(c->stream));
 #undef CKC
@@ -550,7 +604,7 @@ mg_status mg_set_solution(mg_ctx *c, const double *u0) {
   Level &U = user_level(c);
   void *dst = user_u(c);
   if (!u0) {
-    LAUNCH(c, DISPATCH(U, zero_interior, U, dst, c->stream));
+    CK(zero_interior_box(U, dst, c->stream));
   } else {
     CK(copy_dense_interior(U, u0, dst, c->stream));
   }

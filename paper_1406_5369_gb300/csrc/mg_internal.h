@@ -33,6 +33,7 @@ struct Level {
 };
 
 constexpr int kNormBlocks = 1024;
+constexpr int kMaxPartials = 16384;  // per-warp partial sums of the streaming norms
 
 // Per-dimension kernel launchers; all asynchronous on `s`.
 #define MG_DIM_OPS                                                                                \
@@ -75,6 +76,30 @@ cudaError_t pre_fused(const Level &L, const void *uin, void *uout, const Level &
 cudaError_t post_fused(const Level &L, const void *uin, void *uout, const Level &Cl, const void *ec, int nu,
                        double omega, int R, cudaStream_t s);
 }  // namespace d2
+
+// Streaming 2D finest-level kernels (constant stencil). dc_step: FP64 outer
+// step of defect correction (optional update u_out = u_in + e, residual ->
+// defect d, per-warp partial sums); norm_stream: per-warp partial sums of
+// the level residual squared. *nparts receives the number of partials.
+namespace d2 {
+bool outer_ok(const Level &O, const Level &I);
+cudaError_t dc_step(const Level &O, const double *uin, double *uout, const Level &I, const void *e, void *d,
+                    double *partials, int *nparts, const float *scale, bool update, bool acc64, cudaStream_t s);
+bool norm_ok(const Level &L);
+cudaError_t norm_stream(const Level &L, const void *u, const void *f, double *partials, int *nparts, cudaStream_t s);
+}  // namespace d2
+
+// Deterministic sum of nb partials (any nb): out[0] = sqrt(sum) / *scale_in
+// (scale_in may be NULL), out[1] = sum; scale_out (may be NULL) receives the
+// power of two for the next scaled pass.
+cudaError_t norm_finalize_ex(const double *partials, int nb, double *out, const float *scale_in, float *scale_out,
+                             double nint, cudaStream_t s);
+
+// Single-block V-cycle of levels first..nl-1 (coarse.cuh); the levels below
+// `first` are not written back. coarse_top_n: largest level size it takes.
+int coarse_top_n(int dim, bool fp64);
+cudaError_t coarse_cycle(const Level *lv, int first, int nl, bool zero_top, int smoother, double omega, int nu1,
+                         int nu2, bool fp64, cudaStream_t s);
 
 // Sets the message mg_last_error() returns on the calling thread.
 void set_error_message(const char *msg);
