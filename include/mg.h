@@ -87,7 +87,10 @@ typedef struct { int kind; const double *dirichlet_values; } mg_boundary;
  * fuse                  : 1 = fused fine-level kernels where available,
  *                         0 = one kernel per operator (same results up to
  *                         rounding order of FMA contraction)
- * use_graph             : 1 = replay each V-cycle from a captured CUDA graph */
+ * use_graph             : 1 = replay each V-cycle from a captured CUDA graph
+ * inner_cycles          : *_DC only: inner V-cycles per outer FP64 step (1..8, 0 = 1);
+ *                         the first starts from e = 0, the others continue
+ *                         from the current e. 1 = classic defect correction. */
 typedef struct {
   mg_smoother smoother;
   double omega;
@@ -98,12 +101,14 @@ typedef struct {
   void *stream;
   int fuse;
   int use_graph;
+  int inner_cycles;
 } mg_options;
 
 typedef struct mg_ctx mg_ctx;
 
 /* Fills *opt with RBGS, omega 1, V(2,1), coarsest 3, maxit 50, FP64,
- * default stream, fuse 1, use_graph 1 (the Layer-3 defaults of Sec. 2.3). */
+ * default stream, fuse 1, use_graph 1, inner_cycles 1 (the Layer-3
+ * defaults of Sec. 2.3). */
 void mg_default_options(mg_options *opt);
 
 /* Bytes of device arena mg_create needs for this problem (0 if the
@@ -173,7 +178,8 @@ mg_status mg_coarse_solve(mg_ctx *ctx);
 
 /* One V(nu1,nu2)-cycle on the finest level (Algorithm 1; Sec. 2.4 VCycle).
  * In the *_DC precisions: one defect-correction step - FP64 residual of
- * the outer problem, one inner V-cycle from zero on it, FP64 update. */
+ * the outer problem, inner_cycles inner V-cycles (the first from zero) on
+ * it, FP64 update. */
 mg_status mg_vcycle(mg_ctx *ctx);
 
 /* Euclidean norm of f - A u over the interior of `level` (Sec. 2.4
@@ -192,6 +198,31 @@ mg_status mg_solve(mg_ctx *ctx, double tol, int *iters, double *relres, double *
  * this context has launched so far, counting each kernel node of a
  * replayed graph (memset/copy operations are not counted). */
 unsigned long long mg_kernel_launches(const mg_ctx *ctx);
+
+/* Kernel classes for mg_get_timing: presmoothing + residual + restriction,
+ * interpolation + postsmoothing, the coarse-level cycle / 3^d solve, the
+ * FP64 outer step of defect correction, residual norms, anything else. */
+typedef enum {
+  MG_KERNEL_PRESMOOTH = 0,
+  MG_KERNEL_POSTSMOOTH = 1,
+  MG_KERNEL_COARSE = 2,
+  MG_KERNEL_OUTER = 3,
+  MG_KERNEL_NORM = 4,
+  MG_KERNEL_OTHER = 5
+} mg_kernel_kind;
+
+/* Diagnostics with no counterpart in the paper. mg_set_timing(ctx, 1)
+ * brackets every kernel the context launches with CUDA events (inside
+ * captured graphs too; graphs are recaptured when the setting changes).
+ * Durations are added up at synchronising calls (mg_solve,
+ * mg_residual_norm, mg_get_timing); a graph replayed twice between two of
+ * them contributes its last replay only. mg_get_timing returns the total
+ * milliseconds and the number of timed launches of one kernel class on one
+ * level (level 0 for the outer step and the finest norm); it synchronises
+ * the stream. mg_reset_timing clears the totals. */
+mg_status mg_set_timing(mg_ctx *ctx, int on);
+mg_status mg_get_timing(mg_ctx *ctx, int kind, int level, double *total_ms, unsigned long long *count);
+mg_status mg_reset_timing(mg_ctx *ctx);
 
 /* Largest number of per-block partial sums mg_residual_norm_noalloc keeps in
  * its static device scratch. Each block covers 2048 interior nodes, so grids

@@ -17,6 +17,7 @@ STATUS_NAMES = {0: "MG_OK", 1: "MG_EINVAL", 2: "MG_ENOMEM", 3: "MG_ECUDA", 4: "M
 MG_RBGS, MG_JACOBI = 0, 1
 MG_FP64, MG_FP32_DC, MG_BF16_DC = 0, 1, 2
 MG_FIELD_U, MG_FIELD_F, MG_FIELD_R = 0, 1, 2
+MG_KERNEL_PRESMOOTH, MG_KERNEL_POSTSMOOTH, MG_KERNEL_COARSE, MG_KERNEL_OUTER, MG_KERNEL_NORM, MG_KERNEL_OTHER = range(6)
 
 
 class mg_const_stencil(ctypes.Structure):
@@ -31,7 +32,7 @@ class mg_options(ctypes.Structure):
     _fields_ = [("smoother", ctypes.c_int), ("omega", ctypes.c_double), ("nu1", ctypes.c_int),
                 ("nu2", ctypes.c_int), ("coarsest_n", ctypes.c_int), ("maxit", ctypes.c_int),
                 ("precision", ctypes.c_int), ("stream", ctypes.c_void_p), ("fuse", ctypes.c_int),
-                ("use_graph", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("inner_cycles", ctypes.c_int)]
 
 
 # name -> (restype, argtypes); every function declared in include/mg.h.
@@ -60,6 +61,9 @@ SIGNATURES = {
     "mg_residual_norm": (_I, [_P, _I, ctypes.POINTER(_D)]),
     "mg_solve": (_I, [_P, _D, ctypes.POINTER(_I), ctypes.POINTER(_D), _P]),
     "mg_kernel_launches": (ctypes.c_ulonglong, [_P]),
+    "mg_set_timing": (_I, [_P, _I]),
+    "mg_get_timing": (_I, [_P, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_ulonglong)]),
+    "mg_reset_timing": (_I, [_P]),
     "mg_residual_norm_noalloc": (_I, [_I, _I, ctypes.POINTER(mg_const_stencil), _P, _P,
                                       ctypes.POINTER(_D), _P]),
     "mg_last_error": (ctypes.c_char_p, []),

@@ -49,9 +49,14 @@ cudaError_t coarse_cycle(const Level *lv, int first, int nl, bool zero_top, int 
     a.kf64[i] = L.dtype == F64;
     for (int d = 0; d < 3; d++) a.kf[i][d] = L.kf[d];
     size_t N = (size_t)L.n * L.n * (L.dim == 3 ? L.n : 1);
+    a.off_u[i] = (int)elems;
+    a.off_f[i] = (int)(elems + N);
+    a.off_k[i] = (int)(elems + 2 * N);
     elems += N * (2 + (a.var ? L.dim : 0));
   }
+  a.off_tmp = (int)elems;
   elems += (size_t)T.n * T.n * (T.dim == 3 ? T.n : 1);
+  a.total = (int)elems;
   a.f_top = T.f;
   a.u_top = T.u[T.cur];
   a.top_dtype = T.dtype;

@@ -8,6 +8,9 @@
 //
 // Arithmetic runs in C (double in FP64 contexts, float for the inner levels
 // of defect correction); the 3^dim solve runs in FP64 as everywhere else.
+// In 2D (n <= 65) each stage maps thread t to row 1 + t/64 (+16 k) and
+// column 1 + t%64, or, for a red-black half-sweep, to row 1 + t/32 (+32 k)
+// and the (t%32)-th column of the sweep's colour in that row.
 #pragma once
 
 #include "kernels.cuh"
@@ -21,6 +24,8 @@ constexpr int kMaxLev = 8;
 struct CoarseArgs {
   int dim, nlev;           // levels handled: top (index 0 here) .. coarsest
   int n[kMaxLev];
+  int off_u[kMaxLev], off_f[kMaxLev], off_k[kMaxLev];  // element offsets in shared memory
+  int off_tmp, total;
   double inv_h2[kMaxLev];
   double c[3];
   int var;                 // face coefficients present
@@ -50,7 +55,7 @@ __device__ __forceinline__ void stg_any(void *p, long long i, int dtype, double 
 
 template <int DIM> __device__ __forceinline__ int npts(int n) { return DIM == 3 ? n * n * n : n * n; }
 
-// Interior node t (0 <= t < (n-2)^DIM) of a dense n^DIM array.
+// Interior node t (0 <= t < (n-2)^DIM) of a dense n^DIM array (3D loops).
 template <int DIM> __device__ __forceinline__ int inode(int t, int n, int &i, int &j, int &k) {
   int m = n - 2;
   i = 1 + t % m;
@@ -60,17 +65,29 @@ template <int DIM> __device__ __forceinline__ int inode(int t, int n, int &i, in
   return (k * n + j) * n + i;
 }
 
-template <int DIM, typename C>
-struct Lev {
+template <typename C> struct Lev {
   C *u, *f, *kx, *ky, *kz;
   int n;
   C ih2;
 };
 
+template <int DIM, bool VAR, typename C>
+__device__ __forceinline__ Lev<C> level(const CoarseArgs &a, C *sm, int l) {
+  Lev<C> L;
+  int N = npts<DIM>(a.n[l]);
+  L.n = a.n[l];
+  L.ih2 = (C)a.inv_h2[l];
+  L.u = sm + a.off_u[l];
+  L.f = sm + a.off_f[l];
+  L.kx = VAR ? sm + a.off_k[l] : nullptr;
+  L.ky = VAR ? sm + a.off_k[l] + N : nullptr;
+  L.kz = (VAR && DIM == 3) ? sm + a.off_k[l] + 2 * N : nullptr;
+  return L;
+}
+
 // A u and diag at dense node p.
 template <int DIM, bool VAR, typename C>
-__device__ __forceinline__ void dense_apply(const Lev<DIM, C> &L, const C *u, int p, const C (&c)[3], C &Au,
-                                            C &dg) {
+__device__ __forceinline__ void dense_apply(const Lev<C> &L, const C *u, int p, const C (&c)[3], C &Au, C &dg) {
   int sy = L.n, sz = L.n * L.n;
   C u0 = u[p];
   if (!VAR) {
@@ -96,36 +113,63 @@ __device__ __forceinline__ void dense_apply(const Lev<DIM, C> &L, const C *u, in
   }
 }
 
+// Calls body(p, i, j, k) for every interior node of an n^DIM level.
+template <int DIM, typename Fn> __device__ __forceinline__ void for_interior(int n, Fn &&body) {
+  if (DIM == 2) {
+    int i = 1 + (threadIdx.x & 63);
+    if (i <= n - 2)
+      for (int j = 1 + (threadIdx.x >> 6); j <= n - 2; j += kThreads / 64) body(j * n + i, i, j, 0);
+  } else {
+    int m = n - 2, cnt = m * m * m;
+    for (int t = threadIdx.x; t < cnt; t += kThreads) {
+      int i, j, k;
+      int p = inode<DIM>(t, n, i, j, k);
+      body(p, i, j, k);
+    }
+  }
+}
+
+// Calls body(p) for every interior node of colour `color` ((i+j[+k]) % 2).
+template <int DIM, typename Fn> __device__ __forceinline__ void for_colour(int n, int color, Fn &&body) {
+  if (DIM == 2) {
+    int lane = threadIdx.x & 31;
+    for (int j = 1 + (threadIdx.x >> 5); j <= n - 2; j += kThreads / 32) {
+      int i = 2 * lane + ((color + j) & 1);
+      if (i >= 1 && i <= n - 2) body(j * n + i);
+    }
+  } else {
+    int m = n - 2, cnt = m * m * m;
+    for (int t = threadIdx.x; t < cnt; t += kThreads) {
+      int i, j, k;
+      int p = inode<DIM>(t, n, i, j, k);
+      if (((i + j + k) & 1) == color) body(p);
+    }
+  }
+}
+
 template <int DIM, bool VAR, typename C>
-__device__ void smooth(const Lev<DIM, C> &L, C *tmp, const C (&c)[3], int smoother, C omega, int sweeps) {
-  int m = L.n - 2;
-  int cnt = DIM == 3 ? m * m * m : m * m;
+__device__ void smooth(const Lev<C> &L, C *tmp, const C (&c)[3], int smoother, C omega, int sweeps) {
   // constant stencil: omega / diag once per level instead of a division per node
   const C wconst = omega / ((C)2 * (c[0] + c[1] + (DIM == 3 ? c[2] : (C)0)) * L.ih2);
   for (int s = 0; s < sweeps; s++) {
     if (smoother == 0) {
       for (int color = 0; color < 2; color++) {
-        for (int t = threadIdx.x; t < cnt; t += kThreads) {
-          int i, j, k;
-          int p = inode<DIM>(t, L.n, i, j, k);
-          if (((i + j + k) & 1) != color) continue;
+        for_colour<DIM>(L.n, color, [&](int p) {
           C Au, dg;
           dense_apply<DIM, VAR>(L, L.u, p, c, Au, dg);
           L.u[p] = L.u[p] + (VAR ? omega / dg : wconst) * (L.f[p] - Au);
-        }
+        });
         __syncthreads();
       }
     } else {
       int N = npts<DIM>(L.n);
       for (int p = threadIdx.x; p < N; p += kThreads) tmp[p] = L.u[p];
       __syncthreads();
-      for (int t = threadIdx.x; t < cnt; t += kThreads) {
-        int i, j, k;
-        int p = inode<DIM>(t, L.n, i, j, k);
+      for_interior<DIM>(L.n, [&](int p, int, int, int) {
         C Au, dg;
         dense_apply<DIM, VAR>(L, tmp, p, c, Au, dg);
         L.u[p] = tmp[p] + (VAR ? omega / dg : wconst) * (L.f[p] - Au);
-      }
+      });
       __syncthreads();
     }
   }
@@ -137,44 +181,28 @@ __global__ void __launch_bounds__(kThreads) k_coarse_cycle(CoarseArgs a) {
   C *sm = (C *)smem_raw;
   const C c[3] = {(C)a.c[0], (C)a.c[1], (C)a.c[2]};
   const C omega = (C)a.omega;
-  Lev<DIM, C> L[kMaxLev];
-  // carve: per level u, f (, faces); then one scratch array of the top size
-  int off = 0;
-  for (int l = 0; l < a.nlev; l++) {
-    int N = npts<DIM>(a.n[l]);
-    L[l].n = a.n[l];
-    L[l].ih2 = (C)a.inv_h2[l];
-    L[l].u = sm + off; off += N;
-    L[l].f = sm + off; off += N;
-    L[l].kx = L[l].ky = L[l].kz = nullptr;
-    if (VAR) {
-      L[l].kx = sm + off; off += N;
-      L[l].ky = sm + off; off += N;
-      if (DIM == 3) { L[l].kz = sm + off; off += N; }
-    }
-  }
-  C *tmp = sm + off;
-  int total = off + npts<DIM>(a.n[0]);
-  for (int p = threadIdx.x; p < total; p += kThreads) sm[p] = (C)0;
+  C *tmp = sm + a.off_tmp;
+  for (int p = threadIdx.x; p < a.total; p += kThreads) sm[p] = (C)0;
   __syncthreads();
   // load the top level (and the faces of every level)
   {
+    Lev<C> T = level<DIM, VAR, C>(a, sm, 0);
     int n = a.n[0], N = npts<DIM>(n);
     for (int p = threadIdx.x; p < N; p += kThreads) {
       int i = p % n, j = (p / n) % n, k = DIM == 3 ? p / (n * n) : 0;
       long long g = (long long)k * a.plane[0] + (long long)j * a.pitch[0] + i;
-      L[0].f[p] = (C)ldg_any(a.f_top, g, a.top_dtype);
-      if (!a.zero_top) L[0].u[p] = (C)ldg_any(a.u_top, g, a.top_dtype);
+      T.f[p] = (C)ldg_any(a.f_top, g, a.top_dtype);
+      if (!a.zero_top) T.u[p] = (C)ldg_any(a.u_top, g, a.top_dtype);
     }
     if (VAR) {
       for (int l = 0; l < a.nlev; l++) {
         int nl = a.n[l], Nl = npts<DIM>(nl);
-        C *dst[3] = {L[l].kx, L[l].ky, L[l].kz};
+        C *dst = sm + a.off_k[l];
         for (int d = 0; d < DIM; d++) {
           for (int p = threadIdx.x; p < Nl; p += kThreads) {
             int i = p % nl, j = (p / nl) % nl, k = DIM == 3 ? p / (nl * nl) : 0;
             long long g = (long long)k * a.plane[l] + (long long)j * a.pitch[l] + i;
-            dst[d][p] = a.kf64[l] ? (C)((const double *)a.kf[l][d])[g] : (C)((const float *)a.kf[l][d])[g];
+            dst[d * Nl + p] = a.kf64[l] ? (C)((const double *)a.kf[l][d])[g] : (C)((const float *)a.kf[l][d])[g];
           }
         }
       }
@@ -183,45 +211,34 @@ __global__ void __launch_bounds__(kThreads) k_coarse_cycle(CoarseArgs a) {
   __syncthreads();
   // descend
   for (int l = 0; l + 1 < a.nlev; l++) {
-    const Lev<DIM, C> &F = L[l];
-    const Lev<DIM, C> &G = L[l + 1];
+    const Lev<C> F = level<DIM, VAR, C>(a, sm, l);
+    const Lev<C> G = level<DIM, VAR, C>(a, sm, l + 1);
     smooth<DIM, VAR, C>(F, tmp, c, a.smoother, omega, a.nu1);
-    // residual into tmp
-    int m = F.n - 2, cnt = DIM == 3 ? m * m * m : m * m;
-    int N = npts<DIM>(F.n);
-    for (int p = threadIdx.x; p < N; p += kThreads) tmp[p] = (C)0;
-    __syncthreads();
-    for (int t = threadIdx.x; t < cnt; t += kThreads) {
-      int i, j, k;
-      int p = inode<DIM>(t, F.n, i, j, k);
+    // residual into tmp at interior nodes (the restriction reads only those)
+    for_interior<DIM>(F.n, [&](int p, int, int, int) {
       C Au, dg;
       dense_apply<DIM, VAR>(F, F.u, p, c, Au, dg);
       tmp[p] = F.f[p] - Au;
-    }
+    });
     __syncthreads();
-    // full weighting into the coarse right-hand side; coarse u stays 0
-    int mc = G.n - 2, cc = DIM == 3 ? mc * mc * mc : mc * mc;
-    for (int t = threadIdx.x; t < cc; t += kThreads) {
-      int I, J, K;
-      int P = inode<DIM>(t, G.n, I, J, K);
-      int nf = F.n;
+    // full weighting into the coarse right-hand side; the coarse u is 0
+    const int nf = F.n;
+    for_interior<DIM>(G.n, [&](int P, int I, int J, int K) {
       C acc = 0;
       for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); dz++)
-        for (int dy = -1; dy <= 1; dy++)
-          for (int dx = -1; dx <= 1; dx++) {
-            C w = (dx == 0 ? (C)0.5 : (C)0.25) * (dy == 0 ? (C)0.5 : (C)0.25) *
-                  (DIM == 3 ? (dz == 0 ? (C)0.5 : (C)0.25) : (C)1);
-            int q = ((DIM == 3 ? 2 * K + dz : 0) * nf + 2 * J + dy) * nf + 2 * I + dx;
-            acc += w * tmp[q];
-          }
+        for (int dy = -1; dy <= 1; dy++) {
+          const C *row = tmp + ((DIM == 3 ? 2 * K + dz : 0) * nf + 2 * J + dy) * nf + 2 * I;
+          C line = (C)0.25 * (row[-1] + row[1]) + (C)0.5 * row[0];
+          C w = (dy == 0 ? (C)0.5 : (C)0.25) * (DIM == 3 ? (dz == 0 ? (C)0.5 : (C)0.25) : (C)1);
+          acc += w * line;
+        }
       G.f[P] = acc;
-      G.u[P] = (C)0;
-    }
+    });
     __syncthreads();
   }
   // coarsest: 3^dim grid, one unknown, solved exactly in FP64
   if (threadIdx.x == 0) {
-    const Lev<DIM, C> &Z = L[a.nlev - 1];
+    const Lev<C> Z = level<DIM, VAR, C>(a, sm, a.nlev - 1);
     int p = DIM == 3 ? 13 : 4;
     double ih2 = a.inv_h2[a.nlev - 1];
     double dg, acc = 0.0;
@@ -250,13 +267,10 @@ __global__ void __launch_bounds__(kThreads) k_coarse_cycle(CoarseArgs a) {
   __syncthreads();
   // ascend: interpolation and correction, postsmoothing
   for (int l = a.nlev - 2; l >= 0; l--) {
-    const Lev<DIM, C> &F = L[l];
-    const Lev<DIM, C> &G = L[l + 1];
-    int m = F.n - 2, cnt = DIM == 3 ? m * m * m : m * m;
-    int nc = G.n;
-    for (int t = threadIdx.x; t < cnt; t += kThreads) {
-      int i, j, k;
-      int p = inode<DIM>(t, F.n, i, j, k);
+    const Lev<C> F = level<DIM, VAR, C>(a, sm, l);
+    const Lev<C> G = level<DIM, VAR, C>(a, sm, l + 1);
+    const int nc = G.n;
+    for_interior<DIM>(F.n, [&](int p, int i, int j, int k) {
       int I = i >> 1, J = j >> 1, K = k >> 1;
       int oi = i & 1, oj = j & 1, ok = DIM == 3 ? (k & 1) : 0;
       C acc = 0;
@@ -267,20 +281,17 @@ __global__ void __launch_bounds__(kThreads) k_coarse_cycle(CoarseArgs a) {
         }
       C w = (oj ? (C)0.5 : (C)1) * (ok ? (C)0.5 : (C)1);
       F.u[p] += w * acc;
-    }
+    });
     __syncthreads();
     smooth<DIM, VAR, C>(F, tmp, c, a.smoother, omega, a.nu2);
   }
   // write back the top level's solution
   {
-    int n = a.n[0], N = npts<DIM>(n);
-    for (int p = threadIdx.x; p < N; p += kThreads) {
-      int i = p % n, j = (p / n) % n, k = DIM == 3 ? p / (n * n) : 0;
-      bool inter = i >= 1 && i <= n - 2 && j >= 1 && j <= n - 2 && (DIM == 2 || (k >= 1 && k <= n - 2));
-      if (!inter) continue;
+    Lev<C> T = level<DIM, VAR, C>(a, sm, 0);
+    for_interior<DIM>(a.n[0], [&](int p, int i, int j, int k) {
       long long g = (long long)k * a.plane[0] + (long long)j * a.pitch[0] + i;
-      stg_any(a.u_top, g, a.top_dtype, (double)L[0].u[p]);
-    }
+      stg_any(a.u_top, g, a.top_dtype, (double)T.u[p]);
+    });
   }
 }
 

@@ -32,14 +32,18 @@ mg_status fail(mg_status st, const char *fmt, ...) {
                                        __FILE__, __LINE__);                                  \
   } while (0)
 
-// Launches one kernel through a dispatcher and counts it.
-#define LAUNCH(c, call)                                                                       \
+// Launches one kernel through a dispatcher and counts it. With timing on,
+// CUDA events bracket the launch (kernel class `kind`, grid level `lvl`).
+#define TLAUNCH(c, kind, lvl, s, call)                                                        \
   do {                                                                                        \
+    int ev_ = timing_begin((c), (kind), (lvl), (s));                                          \
     cudaError_t e_ = (call);                                                                  \
     if (e_ != cudaSuccess) return fail(MG_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
                                        __FILE__, __LINE__);                                   \
     (c)->launches++;                                                                          \
+    timing_end((c), ev_, (s));                                                                \
   } while (0)
+#define LAUNCH(c, call) TLAUNCH(c, MG_KERNEL_OTHER, 0, s, call)
 
 constexpr int kMaxLevels = 31;
 constexpr int kGraphSlots = 4;
@@ -49,6 +53,17 @@ constexpr int kGraphSlots = 4;
 
 }  // namespace
 
+constexpr int kMaxPairs = 2048;       // event pairs for kernel timing
+constexpr int kSlotPairs = 256;       // timed kernels per captured graph
+constexpr int kKinds = 6;             // mg_kernel_kind values
+
+struct TimingPair {
+  cudaEvent_t a, b;
+  int kind, level;
+  int owner;     // -1: direct launch (recycled after harvest), else graph slot
+  bool pending;  // recorded, not yet harvested
+};
+
 struct GraphSlot {
   bool valid;
   int kind;           // 0 = cycle, 1 = solve step
@@ -56,6 +71,8 @@ struct GraphSlot {
   unsigned post;      // live-buffer bitmask after the captured work
   unsigned long long kernels;  // kernel nodes in the graph
   cudaGraphExec_t exec;
+  int npairs;                  // timed kernels inside the graph
+  int pairs[kSlotPairs];
 };
 
 struct mg_ctx {
@@ -75,9 +92,79 @@ struct mg_ctx {
   GraphSlot graphs[kGraphSlots];
   int next_slot;
   unsigned long long launches;  // kernels launched (direct or inside replayed graphs)
+  // kernel timing (mg_set_timing)
+  int timing;
+  int capturing_slot;          // graph slot being captured, -1 if none
+  TimingPair pairs[kMaxPairs];
+  int npairs;
+  int free_pairs[kMaxPairs];
+  int nfree;
+  double t_ms[kKinds][kMaxLevels];
+  unsigned long long t_n[kKinds][kMaxLevels];
 };
 
 namespace {
+
+int alloc_pair(mg_ctx *c) {
+  if (c->nfree > 0) return c->free_pairs[--c->nfree];
+  if (c->npairs >= kMaxPairs) return -1;
+  TimingPair &p = c->pairs[c->npairs];
+  if (cudaEventCreate(&p.a) != cudaSuccess) return -1;
+  if (cudaEventCreate(&p.b) != cudaSuccess) {
+    cudaEventDestroy(p.a);
+    return -1;
+  }
+  return c->npairs++;
+}
+
+// Records the start event of a timed launch; returns the pair or -1.
+int timing_begin(mg_ctx *c, int kind, int level, cudaStream_t s) {
+  if (!c->timing) return -1;
+  int slot = c->capturing_slot;
+  if (slot >= 0 && c->graphs[slot].npairs >= kSlotPairs) return -1;
+  int i = alloc_pair(c);
+  if (i < 0) return -1;
+  TimingPair &p = c->pairs[i];
+  p.kind = kind;
+  p.level = level;
+  p.owner = slot;
+  p.pending = false;
+  if (slot >= 0) {
+    cudaEventRecordWithFlags(p.a, s, cudaEventRecordExternal);
+    c->graphs[slot].pairs[c->graphs[slot].npairs++] = i;
+  } else {
+    cudaEventRecord(p.a, s);
+  }
+  return i;
+}
+
+void timing_end(mg_ctx *c, int i, cudaStream_t s) {
+  if (i < 0) return;
+  TimingPair &p = c->pairs[i];
+  if (p.owner >= 0) {
+    cudaEventRecordWithFlags(p.b, s, cudaEventRecordExternal);
+  } else {
+    cudaEventRecord(p.b, s);
+    p.pending = true;
+  }
+}
+
+// Adds the durations of every recorded pair (the stream has been synchronised).
+void timing_harvest(mg_ctx *c) {
+  for (int i = 0; i < c->npairs; i++) {
+    TimingPair &p = c->pairs[i];
+    if (!p.pending) continue;
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess && p.kind >= 0 && p.kind < kKinds &&
+        p.level >= 0 && p.level < kMaxLevels) {
+      c->t_ms[p.kind][p.level] += ms;
+      c->t_n[p.kind][p.level] += 1;
+    }
+    p.pending = false;
+    if (p.owner < 0) c->free_pairs[c->nfree++] = i;
+  }
+  cudaGetLastError();  // a pair whose events never completed is simply skipped
+}
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -113,6 +200,7 @@ mg_status check_args(int dim, int n, const mg_options *opt) {
   if (opt->nu1 + opt->nu2 == 0) return fail(MG_EINVAL, "nu1 + nu2 must be positive");
   if (opt->coarsest_n != 3) return fail(MG_EINVAL, "coarsest_n must be 3");
   if (opt->maxit < 0) return fail(MG_EINVAL, "maxit must be >= 0");
+  if (opt->inner_cycles < 0 || opt->inner_cycles > 8) return fail(MG_EINVAL, "inner_cycles must lie in 0..8 (0 = 1)");
   if (opt->precision != MG_FP64 && opt->precision != MG_FP32_DC && opt->precision != MG_BF16_DC)
     return fail(MG_EINVAL, "unknown precision");
   return MG_OK;
@@ -231,41 +319,41 @@ cudaError_t zero_interior_box(const Level &L, void *dst, cudaStream_t s) {
 
 // ---------------------------------------------------------------- level ops
 
-mg_status op_smooth(mg_ctx *c, int l, int sweeps, cudaStream_t s) {
+mg_status op_smooth(mg_ctx *c, int l, int sweeps, cudaStream_t s, int kind = MG_KERNEL_OTHER) {
   Level &L = c->lv[l];
   for (int k = 0; k < sweeps; k++) {
     if (c->opt.smoother == MG_RBGS) {
-      LAUNCH(c, DISPATCH(L, rbgs_half, L, L.u[L.cur], L.f, 0, c->opt.omega, s));
-      LAUNCH(c, DISPATCH(L, rbgs_half, L, L.u[L.cur], L.f, 1, c->opt.omega, s));
+      TLAUNCH(c, kind, l, s, DISPATCH(L, rbgs_half, L, L.u[L.cur], L.f, 0, c->opt.omega, s));
+      TLAUNCH(c, kind, l, s, DISPATCH(L, rbgs_half, L, L.u[L.cur], L.f, 1, c->opt.omega, s));
     } else {
-      LAUNCH(c, DISPATCH(L, jacobi, L, L.u[L.cur], L.u[L.cur ^ 1], L.f, c->opt.omega, s));
+      TLAUNCH(c, kind, l, s, DISPATCH(L, jacobi, L, L.u[L.cur], L.u[L.cur ^ 1], L.f, c->opt.omega, s));
       L.cur ^= 1;
     }
   }
   return MG_OK;
 }
 
-mg_status op_residual(mg_ctx *c, int l, cudaStream_t s) {
+mg_status op_residual(mg_ctx *c, int l, cudaStream_t s, int kind = MG_KERNEL_OTHER) {
   Level &L = c->lv[l];
-  LAUNCH(c, DISPATCH(L, residual, L, L.u[L.cur], L.f, L.r, s));
+  TLAUNCH(c, kind, l, s, DISPATCH(L, residual, L, L.u[L.cur], L.f, L.r, s));
   return MG_OK;
 }
 
-mg_status op_restrict(mg_ctx *c, int l, cudaStream_t s) {
+mg_status op_restrict(mg_ctx *c, int l, cudaStream_t s, int kind = MG_KERNEL_OTHER) {
   Level &F = c->lv[l], &C = c->lv[l + 1];
-  LAUNCH(c, DISPATCH(F, restrict_fw, F, F.r, C, C.f, s));
+  TLAUNCH(c, kind, l, s, DISPATCH(F, restrict_fw, F, F.r, C, C.f, s));
   return MG_OK;
 }
 
-mg_status op_prolong(mg_ctx *c, int l, cudaStream_t s) {
+mg_status op_prolong(mg_ctx *c, int l, cudaStream_t s, int kind = MG_KERNEL_OTHER) {
   Level &F = c->lv[l], &C = c->lv[l + 1];
-  LAUNCH(c, DISPATCH(F, prolong, C, C.u[C.cur], F, F.u[F.cur], s));
+  TLAUNCH(c, kind, l, s, DISPATCH(F, prolong, C, C.u[C.cur], F, F.u[F.cur], s));
   return MG_OK;
 }
 
-mg_status op_coarse(mg_ctx *c, cudaStream_t s) {
+mg_status op_coarse(mg_ctx *c, cudaStream_t s, int kind = MG_KERNEL_OTHER) {
   Level &L = c->lv[c->nl - 1];
-  LAUNCH(c, DISPATCH(L, coarse3, L, L.u[L.cur], L.f, s));
+  TLAUNCH(c, kind, c->nl - 1, s, DISPATCH(L, coarse3, L, L.u[L.cur], L.f, s));
   return MG_OK;
 }
 
@@ -288,29 +376,32 @@ bool level_fused(mg_ctx *c, int l) {
 mg_status vcycle_rec(mg_ctx *c, int l, bool zero, cudaStream_t s) {
   mg_status st;
   if (c->opt.fuse && c->lv[l].n <= mg::coarse_top_n(c->dim, !c->dc)) {
-    LAUNCH(c, mg::coarse_cycle(c->lv, l, c->nl, zero, c->opt.smoother, c->opt.omega, c->opt.nu1, c->opt.nu2, !c->dc, s));
+    TLAUNCH(c, MG_KERNEL_COARSE, l, s,
+            mg::coarse_cycle(c->lv, l, c->nl, zero, c->opt.smoother, c->opt.omega, c->opt.nu1, c->opt.nu2, !c->dc, s));
     return MG_OK;
   }
   if (l == c->nl - 1) {
     if (zero && (st = op_zero_u(c, l, s))) return st;
-    return op_coarse(c, s);
+    return op_coarse(c, s, MG_KERNEL_COARSE);
   }
   Level &L = c->lv[l], &C = c->lv[l + 1];
   if (level_fused(c, l)) {
-    LAUNCH(c, mg::d2::pre_fused(L, L.u[L.cur], L.u[L.cur ^ 1], C, C.f, zero, c->opt.nu1, c->opt.omega, 0, s));
+    TLAUNCH(c, MG_KERNEL_PRESMOOTH, l, s,
+            mg::d2::pre_fused(L, L.u[L.cur], L.u[L.cur ^ 1], C, C.f, zero, c->opt.nu1, c->opt.omega, 0, s));
     L.cur ^= 1;
     if ((st = vcycle_rec(c, l + 1, true, s))) return st;
-    LAUNCH(c, mg::d2::post_fused(L, L.u[L.cur], L.u[L.cur ^ 1], C, C.u[C.cur], c->opt.nu2, c->opt.omega, 0, s));
+    TLAUNCH(c, MG_KERNEL_POSTSMOOTH, l, s,
+            mg::d2::post_fused(L, L.u[L.cur], L.u[L.cur ^ 1], C, C.u[C.cur], c->opt.nu2, c->opt.omega, 0, s));
     L.cur ^= 1;
     return MG_OK;
   }
   if (zero && (st = op_zero_u(c, l, s))) return st;
-  if ((st = op_smooth(c, l, c->opt.nu1, s))) return st;
-  if ((st = op_residual(c, l, s))) return st;
-  if ((st = op_restrict(c, l, s))) return st;
+  if ((st = op_smooth(c, l, c->opt.nu1, s, MG_KERNEL_PRESMOOTH))) return st;
+  if ((st = op_residual(c, l, s, MG_KERNEL_PRESMOOTH))) return st;
+  if ((st = op_restrict(c, l, s, MG_KERNEL_PRESMOOTH))) return st;
   if ((st = vcycle_rec(c, l + 1, true, s))) return st;
-  if ((st = op_prolong(c, l, s))) return st;
-  return op_smooth(c, l, c->opt.nu2, s);
+  if ((st = op_prolong(c, l, s, MG_KERNEL_POSTSMOOTH))) return st;
+  return op_smooth(c, l, c->opt.nu2, s, MG_KERNEL_POSTSMOOTH);
 }
 
 // Residual norm of level l into norm_out[0]. In defect-correction contexts
@@ -321,42 +412,48 @@ mg_status op_norm(mg_ctx *c, int l, cudaStream_t s) {
   if (c->dc && l == 0) {
     Level &O = c->outer, &I = c->lv[0];
     if (mg::d2::outer_ok(O, I)) {
-      LAUNCH(c, mg::d2::dc_step(O, (const double *)O.u[O.cur], nullptr, I, nullptr, I.f, c->partials, &np,
-                                c->dc_scale, false, true, s));
-      LAUNCH(c, mg::norm_finalize_ex(c->partials, np, c->norm_out, nullptr, c->dc_scale, interior_count(O), s));
+      TLAUNCH(c, MG_KERNEL_OUTER, 0, s, mg::d2::dc_step(O, (const double *)O.u[O.cur], nullptr, I, nullptr, I.f,
+                                                        c->partials, &np, c->dc_scale, false, true, s));
+      TLAUNCH(c, MG_KERNEL_NORM, 0, s,
+              mg::norm_finalize_ex(c->partials, np, c->norm_out, nullptr, c->dc_scale, interior_count(O), s));
       return MG_OK;
     }
-    LAUNCH(c, DISPATCH(O, dc_residual, O, O.u[O.cur], O.f, I, I.f, c->partials, mg::kNormBlocks, s));
+    TLAUNCH(c, MG_KERNEL_OUTER, 0, s, DISPATCH(O, dc_residual, O, O.u[O.cur], O.f, I, I.f, c->partials, mg::kNormBlocks, s));
   } else {
     Level &L = c->lv[l];
     if (mg::d2::norm_ok(L)) {
-      LAUNCH(c, mg::d2::norm_stream(L, L.u[L.cur], L.f, c->partials, &np, s));
-      LAUNCH(c, mg::norm_finalize_ex(c->partials, np, c->norm_out, nullptr, nullptr, interior_count(L), s));
+      TLAUNCH(c, MG_KERNEL_NORM, l, s, mg::d2::norm_stream(L, L.u[L.cur], L.f, c->partials, &np, s));
+      TLAUNCH(c, MG_KERNEL_NORM, l, s,
+              mg::norm_finalize_ex(c->partials, np, c->norm_out, nullptr, nullptr, interior_count(L), s));
       return MG_OK;
     }
-    LAUNCH(c, DISPATCH(L, norm_partials, L, L.u[L.cur], L.f, c->partials, mg::kNormBlocks, s));
+    TLAUNCH(c, MG_KERNEL_NORM, l, s, DISPATCH(L, norm_partials, L, L.u[L.cur], L.f, c->partials, mg::kNormBlocks, s));
   }
-  LAUNCH(c, mg::norm_finalize(c->partials, mg::kNormBlocks, c->norm_out, s));
+  TLAUNCH(c, MG_KERNEL_NORM, l, s, mg::norm_finalize(c->partials, mg::kNormBlocks, c->norm_out, s));
   return MG_OK;
 }
 
 // One defect-correction step with the defect d already in lv[0].f:
-// e = V(0, d); u += e. With `norm`, the residual of the updated u is
+// e = V(0, d), then inner_cycles - 1 further cycles e = V(e, d); u += e. With `norm`, the residual of the updated u is
 // computed in the same pass (new defect in lv[0].f, norm in norm_out).
 mg_status dc_inner_and_update(mg_ctx *c, bool norm, cudaStream_t s) {
   mg_status st;
   if ((st = vcycle_rec(c, 0, true, s))) return st;
+  for (int k = 1; k < (c->opt.inner_cycles > 1 ? c->opt.inner_cycles : 1); k++)
+    if ((st = vcycle_rec(c, 0, false, s))) return st;
   Level &O = c->outer, &I = c->lv[0];
   if (mg::d2::outer_ok(O, I)) {
     int np = 0;
-    LAUNCH(c, mg::d2::dc_step(O, (const double *)O.u[O.cur], (double *)O.u[O.cur ^ 1], I, I.u[I.cur],
-                              norm ? I.f : nullptr, c->partials, &np, c->dc_scale, true, false, s));
+    TLAUNCH(c, MG_KERNEL_OUTER, 0, s,
+            mg::d2::dc_step(O, (const double *)O.u[O.cur], (double *)O.u[O.cur ^ 1], I, I.u[I.cur],
+                            norm ? I.f : nullptr, c->partials, &np, c->dc_scale, true, false, s));
     O.cur ^= 1;
-    if (norm) LAUNCH(c, mg::norm_finalize_ex(c->partials, np, c->norm_out, c->dc_scale, c->dc_scale,
-                                             interior_count(O), s));
+    if (norm)
+      TLAUNCH(c, MG_KERNEL_NORM, 0, s,
+              mg::norm_finalize_ex(c->partials, np, c->norm_out, c->dc_scale, c->dc_scale, interior_count(O), s));
     return MG_OK;
   }
-  LAUNCH(c, DISPATCH(O, dc_update, O, O.u[O.cur], I, I.u[I.cur], s));
+  TLAUNCH(c, MG_KERNEL_OUTER, 0, s, DISPATCH(O, dc_update, O, O.u[O.cur], I, I.u[I.cur], s));
   if (norm) return op_norm(c, 0, s);
   return MG_OK;
 }
@@ -387,10 +484,24 @@ void set_cur(mg_ctx *c, unsigned k) {
   c->outer.cur = (k >> 31) & 1u;
 }
 
+void release_slot_pairs(mg_ctx *c, GraphSlot &g) {
+  for (int i = 0; i < g.npairs; i++) {
+    c->pairs[g.pairs[i]].pending = false;
+    c->free_pairs[c->nfree++] = g.pairs[i];
+  }
+  g.npairs = 0;
+}
+
+// After a replay the graph's event pairs hold that replay's times.
+void mark_slot_pending(mg_ctx *c, GraphSlot &g) {
+  for (int i = 0; i < g.npairs; i++) c->pairs[g.pairs[i]].pending = true;
+}
+
 void drop_graphs(mg_ctx *c) {
   for (int i = 0; i < kGraphSlots; i++) {
     if (c->graphs[i].valid) cudaGraphExecDestroy(c->graphs[i].exec);
     c->graphs[i].valid = false;
+    release_slot_pairs(c, c->graphs[i]);
   }
 }
 
@@ -405,6 +516,7 @@ mg_status run(mg_ctx *c, int kind) {
     if (g.valid && g.kind == kind && g.key == key) {
       CK(cudaGraphLaunch(g.exec, c->stream));
       c->launches += g.kernels;
+      mark_slot_pending(c, g);
       set_cur(c, g.post);
       return MG_OK;
     }
@@ -415,9 +527,16 @@ mg_status run(mg_ctx *c, int kind) {
   CK(cudaEventRecord(ev, c->stream));
   CK(cudaStreamWaitEvent(c->cap, ev, 0));
   CK(cudaEventDestroy(ev));
+  GraphSlot &g = c->graphs[c->next_slot];
+  c->next_slot = (c->next_slot + 1) % kGraphSlots;
+  if (g.valid) cudaGraphExecDestroy(g.exec);
+  g.valid = false;
+  release_slot_pairs(c, g);
   CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
   unsigned long long before = c->launches;
+  c->capturing_slot = (int)(&g - c->graphs);
   mg_status st = record(c, kind, c->cap);
+  c->capturing_slot = -1;
   unsigned long long kernels = c->launches - before;
   c->launches = before;
   unsigned post = cur_key(c);
@@ -429,10 +548,6 @@ mg_status run(mg_ctx *c, int kind) {
     return st;
   }
   if (ee != cudaSuccess) return fail(MG_ECUDA, "graph capture: %s", cudaGetErrorString(ee));
-  GraphSlot &g = c->graphs[c->next_slot];
-  c->next_slot = (c->next_slot + 1) % kGraphSlots;
-  if (g.valid) cudaGraphExecDestroy(g.exec);
-  g.valid = false;
   cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
   cudaGraphDestroy(graph);
   if (ie != cudaSuccess) return fail(MG_ECUDA, "graph instantiate: %s", cudaGetErrorString(ie));
@@ -443,6 +558,7 @@ mg_status run(mg_ctx *c, int kind) {
   g.kernels = kernels;
   CK(cudaGraphLaunch(g.exec, c->stream));
   c->launches += kernels;
+  mark_slot_pending(c, g);
   set_cur(c, post);
   return MG_OK;
 }
@@ -450,6 +566,7 @@ mg_status run(mg_ctx *c, int kind) {
 mg_status read_norm(mg_ctx *c, double *out) {
   CK(cudaMemcpyAsync(c->host_norm, c->norm_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  if (c->timing) timing_harvest(c);
   *out = c->host_norm[0];
   return MG_OK;
 }
@@ -473,6 +590,7 @@ void mg_default_options(mg_options *o) {
   o->stream = nullptr;
   o->fuse = 1;
   o->use_graph = 1;
+  o->inner_cycles = 1;
 }
 
 size_t mg_workspace_bytes(int dim, int n, int variable_k, const mg_options *opt) {
@@ -515,6 +633,7 @@ mg_status mg_create(int dim, int n, const mg_const_stencil *stencil, const doubl
   c->opt = *opt;
   c->dc = opt->precision != MG_FP64;
   c->stream = (cudaStream_t)opt->stream;
+  c->capturing_slot = -1;
   for (int d = 0; d < 3; d++) c->lv[0].c[d] = c3[d];
   size_t need = layout(c, nullptr);
   if (arena_bytes < need) {
@@ -579,6 +698,10 @@ bad:
 mg_status mg_destroy(mg_ctx *c) {
   if (!c) return MG_OK;
   drop_graphs(c);
+  for (int i = 0; i < c->npairs; i++) {
+    cudaEventDestroy(c->pairs[i].a);
+    cudaEventDestroy(c->pairs[i].b);
+  }
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->host_norm) cudaFreeHost(c->host_norm);
   free(c);
@@ -635,7 +758,7 @@ mg_status mg_set_field(mg_ctx *c, int level, mg_field field, const double *src) 
     double *stage = (double *)c->outer.r;  // DC contexts only have non-FP64 levels
     size_t cnt = (size_t)L.n * L.n * (L.dim == 3 ? L.n : 1);
     CK(cudaMemcpyAsync(stage, src, cnt * 8, cudaMemcpyDefault, c->stream));
-    LAUNCH(c, DISPATCH(L, from_dense, L, stage, dst, c->stream));
+    TLAUNCH(c, MG_KERNEL_OTHER, level, c->stream, DISPATCH(L, from_dense, L, stage, dst, c->stream));
   }
   return MG_OK;
 }
@@ -651,7 +774,7 @@ mg_status mg_get_field(mg_ctx *c, int level, mg_field field, double *dst) {
   } else {
     double *stage = (double *)c->outer.r;
     size_t cnt = (size_t)L.n * L.n * (L.dim == 3 ? L.n : 1);
-    LAUNCH(c, DISPATCH(L, to_dense, L, src, stage, c->stream));
+    TLAUNCH(c, MG_KERNEL_OTHER, level, c->stream, DISPATCH(L, to_dense, L, src, stage, c->stream));
     CK(cudaMemcpyAsync(dst, stage, cnt * 8, cudaMemcpyDefault, c->stream));
   }
   CK(cudaStreamSynchronize(c->stream));
@@ -732,6 +855,36 @@ mg_status mg_solve(mg_ctx *c, double tol, int *iters, double *relres, double *hi
 }
 
 unsigned long long mg_kernel_launches(const mg_ctx *c) { return c ? c->launches : 0ull; }
+
+mg_status mg_set_timing(mg_ctx *c, int on) {
+  if (!c) return fail(MG_EINVAL, "NULL context");
+  if ((on != 0) != (c->timing != 0)) {
+    CK(cudaStreamSynchronize(c->stream));
+    if (c->timing) timing_harvest(c);
+    drop_graphs(c);  // graphs are recaptured with (or without) event nodes
+    c->timing = on != 0;
+  }
+  return MG_OK;
+}
+
+mg_status mg_get_timing(mg_ctx *c, int kind, int level, double *total_ms, unsigned long long *count) {
+  if (!c) return fail(MG_EINVAL, "NULL context");
+  if (kind < 0 || kind >= kKinds || level < 0 || level >= kMaxLevels) return fail(MG_EINVAL, "bad kind or level");
+  CK(cudaStreamSynchronize(c->stream));
+  if (c->timing) timing_harvest(c);
+  if (total_ms) *total_ms = c->t_ms[kind][level];
+  if (count) *count = c->t_n[kind][level];
+  return MG_OK;
+}
+
+mg_status mg_reset_timing(mg_ctx *c) {
+  if (!c) return fail(MG_EINVAL, "NULL context");
+  CK(cudaStreamSynchronize(c->stream));
+  if (c->timing) timing_harvest(c);
+  memset(c->t_ms, 0, sizeof c->t_ms);
+  memset(c->t_n, 0, sizeof c->t_n);
+  return MG_OK;
+}
 
 const char *mg_last_error(void) { return g_err; }
 

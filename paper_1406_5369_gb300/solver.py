@@ -48,7 +48,7 @@ class Solver:
 
     def __init__(self, dim, n, *, stencil=(1.0, 1.0, 1.0), k=None, dirichlet=None,
                  smoother="rbgs", omega=1.0, nu1=2, nu2=1, maxit=50, precision="fp64",
-                 fuse=True, use_graph=True, stream=None, device="cuda"):
+                 fuse=True, use_graph=True, inner_cycles=1, stream=None, device="cuda"):
         import torch
         self._lib = C.load()
         self.dim, self.n = dim, n
@@ -61,6 +61,7 @@ class Solver:
         opt.precision = _PRECISION[precision]
         opt.fuse = int(bool(fuse))
         opt.use_graph = int(bool(use_graph))
+        opt.inner_cycles = int(inner_cycles)
         opt.stream = default_stream_handle() if stream is None else stream
         self._tstream = torch.cuda.current_stream() if stream is None else torch.cuda.ExternalStream(stream)
         self.opt = opt
@@ -97,6 +98,21 @@ class Solver:
 
     def kernel_launches(self):
         return self._lib.mg_kernel_launches(self.ctx)
+
+    def set_timing(self, on=True):
+        C.check(self._lib.mg_set_timing(self.ctx, int(bool(on))))
+
+    def reset_timing(self):
+        C.check(self._lib.mg_reset_timing(self.ctx))
+
+    def timing(self, kind, level=0):
+        """(total milliseconds, launches) of one kernel class on one level."""
+        kinds = {"pre": C.MG_KERNEL_PRESMOOTH, "post": C.MG_KERNEL_POSTSMOOTH, "coarse": C.MG_KERNEL_COARSE,
+                 "outer": C.MG_KERNEL_OUTER, "norm": C.MG_KERNEL_NORM, "other": C.MG_KERNEL_OTHER}
+        ms = ctypes.c_double()
+        cnt = ctypes.c_ulonglong()
+        C.check(self._lib.mg_get_timing(self.ctx, kinds.get(kind, kind), level, ctypes.byref(ms), ctypes.byref(cnt)))
+        return ms.value, cnt.value
 
     def level_size(self, level):
         return self._lib.mg_level_size(self.ctx, level)

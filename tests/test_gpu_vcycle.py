@@ -208,3 +208,47 @@ def test_fp64_cycle_of_defect_correction_shape_matches_plain():
     rho = ref.dc_solve(0.0, 4)
     assert len(hist) == len(rho)
     assert np.all(np.abs(hist - rho) <= 1e-5 * rho + 1e-12)
+
+
+@pytest.mark.parametrize("prec", ["fp32_dc", "bf16_dc"])
+def test_defect_correction_several_inner_cycles(prec):
+    # inner_cycles = 2: e = V(V(0, d), d) per outer FP64 step; fewer outer
+    # steps to the same FP64 residual, which the oracle recomputes.
+    need_gpu()
+    from paper_1406_5369_gb300 import Solver
+    n = 1025
+    f = synth.uniform_rhs(2, n, 0x5EED0002)
+    its = {}
+    for ic in (1, 2):
+        s = Solver(2, n, precision=prec, inner_cycles=ic, maxit=60)
+        s.set_rhs(f)
+        it, rr, _ = s.solve(1e-10)
+        assert rr <= 1e-10
+        u = s.get_solution()
+        assert oracle.norm(oracle.residual(u, f)) / oracle.norm(f) <= 1.01e-10
+        its[ic] = it
+    assert its[2] < its[1]
+
+
+def test_kernel_timing_instrumentation():
+    # Events bracket every launch, inside replayed graphs too; totals are
+    # positive for the classes a DC solve runs and counts follow the launches.
+    need_gpu()
+    from paper_1406_5369_gb300 import Solver
+    n = 1025
+    f = synth.uniform_rhs(2, n, 7)
+    s = Solver(2, n, precision="fp32_dc", inner_cycles=2, maxit=30)
+    s.set_rhs(f)
+    s.set_timing(True)
+    it, rr, _ = s.solve(1e-10)
+    pre_ms, pre_n = s.timing("pre", 0)
+    post_ms, post_n = s.timing("post", 0)
+    out_ms, out_n = s.timing("outer", 0)
+    assert pre_n == post_n == 2 * it and pre_ms > 0 and post_ms > 0
+    assert out_n == it + 1 and out_ms > 0
+    s.reset_timing()
+    assert s.timing("pre", 0) == (0.0, 0)
+    s.set_timing(False)
+    s.set_solution(None)
+    s.solve(1e-10)
+    assert s.timing("pre", 0) == (0.0, 0)
