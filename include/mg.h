@@ -254,6 +254,50 @@ mg_status mg_reset_timing(mg_ctx *ctx);
 mg_status mg_residual_norm_noalloc(int dim, int n, const mg_const_stencil *stencil, const double *u,
                                    const double *f, double *out, void *stream);
 
+/* ---- Batches of independent problems (the task's batching and serving
+ * patterns; the paper solves one problem at a time). A batch holds contexts
+ * created with mg_create that share smoother, omega, nu1, nu2, precision and
+ * inner_cycles (and dim); each keeps its own arena, right-hand side,
+ * solution and tolerance. A batch step runs one solve step - a V-cycle, or
+ * a defect-correction step - for every listed problem at once: each fine
+ * level size is one launch per operator over all problems that have it,
+ * the small coarse levels of all problems run in one launch (one block per
+ * problem), and the outer step and the norms run once for all. A problem's
+ * arithmetic does not depend on the other problems in the batch, so its
+ * result is the same alone and in any mix. ---- */
+typedef struct mg_batch mg_batch;
+
+/* Device workspace (descriptor arrays, norm partial sums) for at most
+ * max_problems problems; 0 if max_problems < 1. */
+size_t mg_batch_workspace_bytes(int max_problems);
+
+/* Creates an empty batch using the caller's device workspace (256-byte
+ * aligned, at least mg_batch_workspace_bytes bytes) and stream (NULL =
+ * default). The batch allocates pinned host staging for descriptors. */
+mg_status mg_batch_create(int max_problems, void *workspace, size_t bytes, void *stream, mg_batch **out);
+mg_status mg_batch_destroy(mg_batch *batch);
+
+/* Adds a context (borrowed; it must outlive its membership) and returns its
+ * id. MG_EINVAL if its options differ from the batch's, or for Jacobi with
+ * an odd nu1 + nu2; MG_ENOMEM if the batch is full. The problem's initial
+ * residual is taken at its first step. */
+mg_status mg_batch_add(mg_batch *batch, mg_ctx *ctx, int *id);
+mg_status mg_batch_remove(mg_batch *batch, int id);
+
+/* One solve step for the `count` problems in ids (all constant or all
+ * variable stencil). rho (may be NULL) receives each problem's relative
+ * residual ||r|| / ||r_0|| after the step. Synchronises the batch stream. */
+mg_status mg_batch_step(mg_batch *batch, const int *ids, int count, double *rho);
+
+/* Steps every problem in the batch until its relative residual is at most
+ * tol[id] or maxit steps; iters[id] and relres[id] (arrays indexed by id,
+ * may be NULL) receive the steps taken and the final ratio. MG_ENOCONV if
+ * some problem did not reach its tolerance or a residual was not finite. */
+mg_status mg_batch_solve(mg_batch *batch, const double *tol, int maxit, int *iters, double *relres);
+
+/* Kernels the batch has launched so far (diagnostic). */
+unsigned long long mg_batch_launches(const mg_batch *batch);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *mg_last_error(void);
 

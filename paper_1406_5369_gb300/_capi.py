@@ -66,6 +66,14 @@ SIGNATURES = {
     "mg_reset_timing": (_I, [_P]),
     "mg_residual_norm_noalloc": (_I, [_I, _I, ctypes.POINTER(mg_const_stencil), _P, _P,
                                       ctypes.POINTER(_D), _P]),
+    "mg_batch_workspace_bytes": (ctypes.c_size_t, [_I]),
+    "mg_batch_create": (_I, [_I, _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)]),
+    "mg_batch_destroy": (_I, [_P]),
+    "mg_batch_add": (_I, [_P, _P, ctypes.POINTER(_I)]),
+    "mg_batch_remove": (_I, [_P, _I]),
+    "mg_batch_step": (_I, [_P, ctypes.POINTER(_I), _I, ctypes.POINTER(_D)]),
+    "mg_batch_solve": (_I, [_P, ctypes.POINTER(_D), _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "mg_batch_launches": (ctypes.c_ulonglong, [_P]),
     "mg_last_error": (ctypes.c_char_p, []),
 }
 

@@ -1,0 +1,76 @@
+"""BatchSolver: many independent problems stepped together (mg_batch_* in mg.h).
+
+Each problem is a Solver (its own arena, right-hand side, solution and
+tolerance); the batch steps all of them with level-grouped launches. Only
+argument marshalling happens here.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _capi as C
+from .solver import default_stream_handle
+
+
+class BatchSolver:
+    def __init__(self, max_problems, stream=None, device="cuda"):
+        import torch
+        self._lib = C.load()
+        nbytes = self._lib.mg_batch_workspace_bytes(int(max_problems))
+        if nbytes == 0:
+            raise C.MGError(C.MG_EINVAL, "max_problems must be positive")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        h = ctypes.c_void_p()
+        st = default_stream_handle() if stream is None else stream
+        C.check(self._lib.mg_batch_create(int(max_problems), ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
+                                          st, ctypes.byref(h)))
+        self.h = h
+        self.max_problems = int(max_problems)
+        self.members = {}
+
+    def add(self, solver):
+        i = ctypes.c_int()
+        C.check(self._lib.mg_batch_add(self.h, solver.ctx, ctypes.byref(i)))
+        self.members[i.value] = solver
+        return i.value
+
+    def remove(self, pid):
+        C.check(self._lib.mg_batch_remove(self.h, int(pid)))
+        self.members.pop(pid, None)
+
+    def step(self, ids):
+        ids = np.ascontiguousarray(ids, dtype=np.int32)
+        rho = np.zeros(len(ids))
+        C.check(self._lib.mg_batch_step(self.h, ids.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), len(ids),
+                                        rho.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return rho
+
+    def solve(self, tol, maxit=50, raise_on_noconv=True):
+        """tol: scalar or {id: tol}; returns (iters, relres) arrays indexed by id."""
+        tols = np.zeros(self.max_problems)
+        for pid in self.members:
+            tols[pid] = tol[pid] if isinstance(tol, dict) else float(tol)
+        iters = np.zeros(self.max_problems, dtype=np.int32)
+        rel = np.zeros(self.max_problems)
+        st = self._lib.mg_batch_solve(self.h, tols.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(maxit),
+                                      iters.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                      rel.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        if st != C.MG_OK and (raise_on_noconv or st != C.MG_ENOCONV):
+            C.check(st)
+        return iters, rel
+
+    def launches(self):
+        return self._lib.mg_batch_launches(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.mg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,804 @@
+// Batched multigrid over many independent problems (mg_batch_* in mg.h).
+//
+// A batch step runs one solve step (a V-cycle, or a defect-correction step:
+// inner_cycles inner V-cycles and the FP64 outer update + residual) for every
+// listed problem. Work is grouped by absolute level size across problems:
+// each fine level size is one launch per operator over all problems that
+// have a level of that size, the levels below the coarse threshold of every
+// problem run in one launch of the single-block coarse cycle (one block per
+// problem), and the outer step and the norms run once over all problems.
+// Kernels read per-problem descriptors from device arrays; each problem's
+// arithmetic (and the order of its norm sums) is the same whatever else is
+// in the batch, so a problem's result does not depend on its companions.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <map>
+#include <vector>
+
+#include "ctx.h"
+#include "kernels.cuh"
+
+namespace mg {
+namespace bz {
+
+constexpr int kPartBlocks = 128;  // norm partial sums per problem
+
+// One level of one problem.
+struct BOp {
+  void *u[2];
+  void *f;
+  void *r;
+  const void *kf[3];
+  Geo g;
+  double c[3];
+  double inv_h2;
+  int cur;  // live solution buffer at the start of the step
+};
+
+// Fine/coarse pair of one problem (restriction: fine r -> coarse f;
+// interpolation: coarse u -> fine u).
+struct BXfer {
+  const void *src;
+  void *dst;
+  Geo gf, gc;
+};
+
+// Outer (FP64) finest level and inner level 0 of one problem.
+struct BOuter {
+  double *u;
+  const double *f;
+  const void *kf[3];
+  Geo go;
+  double c[3];
+  double inv_h2;
+  void *d;        // inner defect (inner f)
+  const void *e;  // inner correction (live inner u)
+  Geo gi;
+};
+
+template <typename C> __device__ __forceinline__ Sten<C> sten_dev(const double (&c)[3], double inv_h2,
+                                                                   const void *const (&kf)[3], int dim) {
+  Sten<C> s;
+  s.kf0 = (const C *)kf[0];
+  s.kf1 = (const C *)kf[1];
+  s.kf2 = (const C *)kf[2];
+  s.c0 = (C)c[0];
+  s.c1 = (C)c[1];
+  s.c2 = (C)c[2];
+  s.inv_h2 = (C)inv_h2;
+  s.diag = (C)(2.0 * (c[0] + c[1] + (dim == 3 ? c[2] : 0.0)) * inv_h2);
+  return s;
+}
+
+// Grid: x covers columns, y rows, z = (problem * n + plane) in 3D or problem in 2D.
+template <int DIM> __device__ __forceinline__ Idx bnode(const Geo &g, int &p) {
+  Idx t;
+  t.i = blockIdx.x * blockDim.x + threadIdx.x;
+  t.j = blockIdx.y;
+  if (DIM == 3) {
+    p = blockIdx.z / g.n;
+    t.k = blockIdx.z % g.n;
+  } else {
+    p = blockIdx.z;
+    t.k = 0;
+  }
+  t.p = (long long)t.k * g.sz + (long long)t.j * g.sy + t.i;
+  t.interior = t.i >= 1 && t.i <= g.n - 2 && t.j >= 1 && t.j <= g.n - 2 &&
+               (DIM == 2 || (t.k >= 1 && t.k <= g.n - 2));
+  return t;
+}
+
+template <int DIM, typename T, bool VAR>
+__global__ void kb_rbgs_half(const BOp *__restrict__ ops, Geo g, int color, int flip, double omega) {
+  typedef typename CT<T>::type C;
+  int pi;
+  Idx t = bnode<DIM>(g, pi);
+  const BOp &o = ops[pi];
+  if (!t.interior || ((t.i + t.j + t.k) & 1) != color) return;
+  T *u = (T *)o.u[o.cur ^ flip];
+  const T *f = (const T *)o.f;
+  Sten<C> s = sten_dev<C>(o.c, o.inv_h2, o.kf, DIM);
+  C Au, dg;
+  apply_at<DIM, VAR>(u, t.p, g, s, Au, dg);
+  st(u + t.p, ld(u + t.p) + (C)omega * (ld(f + t.p) - Au) / dg);
+}
+
+template <int DIM, typename T, bool VAR>
+__global__ void kb_jacobi(const BOp *__restrict__ ops, Geo g, int flip, double omega) {
+  typedef typename CT<T>::type C;
+  int pi;
+  Idx t = bnode<DIM>(g, pi);
+  const BOp &o = ops[pi];
+  if (!t.interior) return;
+  const T *uin = (const T *)o.u[o.cur ^ flip];
+  T *uout = (T *)o.u[o.cur ^ flip ^ 1];
+  const T *f = (const T *)o.f;
+  Sten<C> s = sten_dev<C>(o.c, o.inv_h2, o.kf, DIM);
+  C Au, dg;
+  apply_at<DIM, VAR>(uin, t.p, g, s, Au, dg);
+  st(uout + t.p, ld(uin + t.p) + (C)omega * (ld(f + t.p) - Au) / dg);
+}
+
+template <int DIM, typename T, bool VAR>
+__global__ void kb_residual(const BOp *__restrict__ ops, Geo g, int flip) {
+  typedef typename CT<T>::type C;
+  int pi;
+  Idx t = bnode<DIM>(g, pi);
+  const BOp &o = ops[pi];
+  if (!t.interior) return;
+  const T *u = (const T *)o.u[o.cur ^ flip];
+  Sten<C> s = sten_dev<C>(o.c, o.inv_h2, o.kf, DIM);
+  C Au, dg;
+  apply_at<DIM, VAR>(u, t.p, g, s, Au, dg);
+  st((T *)o.r + t.p, ld((const T *)o.f + t.p) - Au);
+}
+
+template <int DIM, typename T> __global__ void kb_zero(const BOp *__restrict__ ops, Geo g, int flip) {
+  int pi;
+  Idx t = bnode<DIM>(g, pi);
+  const BOp &o = ops[pi];
+  if (t.i >= g.n) return;
+  st((T *)o.u[o.cur ^ flip] + t.p, 0.0f);
+}
+
+template <int DIM, typename Tf, typename Tc>
+__global__ void kb_restrict(const BXfer *__restrict__ xs, Geo gf, Geo gc) {
+  typedef typename CT<Tc>::type C;
+  int pi;
+  Idx t = bnode<DIM>(gc, pi);
+  if (!t.interior) return;
+  const Tf *rf = (const Tf *)xs[pi].src;
+  Tc *fc = (Tc *)xs[pi].dst;
+  long long q = (long long)(2 * t.k) * gf.sz + (long long)(2 * t.j) * gf.sy + 2 * t.i;
+  C acc = 0;
+#pragma unroll
+  for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); dz++) {
+    C wz = DIM == 3 ? (dz == 0 ? (C)0.5 : (C)0.25) : (C)1;
+#pragma unroll
+    for (int dy = -1; dy <= 1; dy++) {
+      C wy = dy == 0 ? (C)0.5 : (C)0.25;
+      const Tf *row = rf + q + dz * gf.sz + dy * gf.sy;
+      C line = (C)0.25 * ((C)ld(row - 1) + (C)ld(row + 1)) + (C)0.5 * (C)ld(row);
+      acc += wz * wy * line;
+    }
+  }
+  st(fc + t.p, acc);
+}
+
+template <int DIM, typename Tc, typename Tf>
+__global__ void kb_prolong(const BXfer *__restrict__ xs, Geo gc, Geo gf) {
+  typedef typename CT<Tf>::type C;
+  int pi;
+  Idx t = bnode<DIM>(gf, pi);
+  if (!t.interior) return;
+  const Tc *ec = (const Tc *)xs[pi].src;
+  Tf *uf = (Tf *)xs[pi].dst;
+  int I = t.i >> 1, J = t.j >> 1, K = t.k >> 1;
+  int oi = t.i & 1, oj = t.j & 1, ok = DIM == 3 ? (t.k & 1) : 0;
+  C acc = 0;
+  for (int a = 0; a <= ok; a++)
+    for (int b = 0; b <= oj; b++) {
+      const Tc *row = ec + (long long)(K + a) * gc.sz + (long long)(J + b) * gc.sy + I;
+      acc += oi ? (C)0.5 * ((C)ld(row) + (C)ld(row + 1)) : (C)ld(row);
+    }
+  C w = (oj ? (C)0.5 : (C)1) * (ok ? (C)0.5 : (C)1);
+  st(uf + t.p, (C)ld(uf + t.p) + w * acc);
+}
+
+// Per-problem partial sums of the FP64 outer residual squared (kPartBlocks
+// blocks per problem, fixed partition), writing the inner defect.
+template <int DIM, typename Ti, bool VAR>
+__global__ void kb_dc_residual(const BOuter *__restrict__ os, double *__restrict__ partials) {
+  const BOuter &o = os[blockIdx.y];
+  Sten<double> s = sten_dev<double>(o.c, o.inv_h2, o.kf, DIM);
+  int m = o.go.n - 2;
+  long long total = (long long)m * m * (DIM == 3 ? m : 1);
+  double acc = 0.0;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    long long p = interior_node<DIM>(t, m, o.go);
+    long long q = interior_node<DIM>(t, m, o.gi);
+    double Au, dg;
+    apply_at<DIM, VAR>(o.u, p, o.go, s, Au, dg);
+    double r = o.f[p] - Au;
+    acc += r * r;
+    if (o.d) st((Ti *)o.d + q, (float)r);
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = acc;
+}
+
+template <int DIM, typename Ti>
+__global__ void kb_dc_update(const BOuter *__restrict__ os) {
+  const BOuter &o = os[blockIdx.y];
+  int m = o.go.n - 2;
+  long long total = (long long)m * m * (DIM == 3 ? m : 1);
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    long long p = interior_node<DIM>(t, m, o.go);
+    long long q = interior_node<DIM>(t, m, o.gi);
+    o.u[p] += (double)ld((const Ti *)o.e + q);
+  }
+}
+
+// Norm partials of level 0 for plain FP64 problems.
+template <int DIM, bool VAR>
+__global__ void kb_norm(const BOp *__restrict__ ops, double *__restrict__ partials) {
+  const BOp &o = ops[blockIdx.y];
+  Sten<double> s = sten_dev<double>(o.c, o.inv_h2, o.kf, DIM);
+  const double *u = (const double *)o.u[o.cur];
+  const double *f = (const double *)o.f;
+  int m = o.g.n - 2;
+  long long total = (long long)m * m * (DIM == 3 ? m : 1);
+  double acc = 0.0;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    long long p = interior_node<DIM>(t, m, o.g);
+    double Au, dg;
+    apply_at<DIM, VAR>(u, p, o.g, s, Au, dg);
+    double r = f[p] - Au;
+    acc += r * r;
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = acc;
+}
+
+// One block per problem: fixed-order sum of its partials, norm out.
+__global__ void kb_finalize(const double *__restrict__ partials, int per, double *__restrict__ norms) {
+  __shared__ double buf[kPartBlocks];
+  int t = threadIdx.x;
+  buf[t] = partials[(long long)blockIdx.x * per + t];
+  __syncthreads();
+  for (int s = kPartBlocks / 2; s > 0; s >>= 1) {
+    if (t < s) buf[t] += buf[t + s];
+    __syncthreads();
+  }
+  if (t == 0) norms[blockIdx.x] = sqrt(buf[0]);
+}
+
+}  // namespace bz
+}  // namespace mg
+
+using namespace mg;
+using namespace mg::bz;
+
+namespace {
+
+thread_local char g_berr[256];
+
+mg_status bfail(mg_status st, const char *msg, cudaError_t e = cudaSuccess) {
+  if (e != cudaSuccess) snprintf(g_berr, sizeof g_berr, "%s: %s", msg, cudaGetErrorString(e));
+  else snprintf(g_berr, sizeof g_berr, "%s", msg);
+  set_error_message(g_berr);
+  return st;
+}
+
+#define BCK(msg, call)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return bfail(MG_ECUDA, msg, e_); \
+  } while (0)
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+}  // namespace
+
+struct mg_batch {
+  int maxp;
+  std::vector<mg_ctx *> probs;  // by id; nullptr when free
+  std::vector<double> r0;       // initial residual norm per id (< 0: not yet computed)
+  char *ws;
+  size_t ws_bytes;
+  size_t desc_bytes;            // descriptor area at the start of ws
+  double *partials;             // maxp * kPartBlocks
+  double *norms;                // maxp
+  cudaStream_t stream;
+  bool have_opts;
+  mg_options opt;
+  int dim;
+  bool dc, fp64;
+  // descriptors: staged in pinned host memory, copied right before the
+  // launch that reads them (stream order), reset after each step's sync
+  char *pinned;
+  size_t dev_off;
+  unsigned long long launches;
+};
+
+namespace {
+
+size_t desc_area_bytes(int maxp) {
+  // per problem and level: one BOp, one BXfer, plus a coarse record and an outer record
+  size_t per = (size_t)kMaxLevels * (sizeof(BOp) + 2 * sizeof(BXfer)) + coarse_args_bytes() + sizeof(BOuter) + 1024;
+  return align256((size_t)maxp * per * 2);
+}
+
+// Stages `bytes` of descriptors and copies them to the next device slot on
+// the batch stream (before any kernel launched after this call); returns
+// the device address, NULL if the area is exhausted or the copy failed.
+void *push(mg_batch *b, const void *src, size_t bytes) {
+  size_t off = align256(b->dev_off);
+  if (off + bytes > b->desc_bytes) return nullptr;
+  memcpy(b->pinned + off, src, bytes);
+  if (cudaMemcpyAsync(b->ws + off, b->pinned + off, bytes, cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+    return nullptr;
+  b->dev_off = off + bytes;
+  return b->ws + off;
+}
+
+template <typename D> struct Group {
+  int n = 0;
+  std::vector<D> items;
+};
+
+dim3 bgrid(int dim, int n, int count) {
+  return dim3((unsigned)((n + 127) / 128), (unsigned)n, (unsigned)(dim == 3 ? n * count : count));
+}
+
+// Largest count of problems per launch so that grid.z stays within 65535.
+int chunk_of(int dim, int n) { return dim == 3 ? std::max(1, 65535 / n) : 65535; }
+
+BOp make_op(const Level &L) {
+  BOp o;
+  memset(&o, 0, sizeof o);
+  o.u[0] = L.u[0];
+  o.u[1] = L.u[1];
+  o.f = L.f;
+  o.r = L.r;
+  for (int d = 0; d < 3; d++) o.kf[d] = L.kf[d];
+  o.g = geo_of(L);
+  for (int d = 0; d < 3; d++) o.c[d] = L.c[d];
+  o.inv_h2 = L.inv_h2;
+  o.cur = L.cur;
+  return o;
+}
+
+// ----- launch helpers: dispatch on dim / storage type / variable stencil
+
+#define DISPATCH_T(dtype, ...)                         \
+  switch (dtype) {                                     \
+    case F64: { typedef double T; __VA_ARGS__; } break; \
+    case F32: { typedef float T; __VA_ARGS__; } break;  \
+    default: { typedef bf16 T; __VA_ARGS__; } break;    \
+  }
+
+}  // namespace
+
+// The batched operator launches need each op's geometry; groups share n and
+// storage type, hence pitch and plane, so the group's first op supplies it.
+namespace {
+
+cudaError_t launch_group_op(int what, const std::vector<BOp> &items, mg_batch *b, int dim, int dtype, bool var,
+                            int color, int flip, double omega) {
+  if (items.empty()) return cudaSuccess;
+  Geo g = items[0].g;
+  int n = g.n;
+  int chunk = chunk_of(dim, n);
+  for (size_t base = 0; base < items.size(); base += chunk) {
+    int count = (int)std::min<size_t>(chunk, items.size() - base);
+    const BOp *dev = (const BOp *)push(b, items.data() + base, sizeof(BOp) * count);
+    if (!dev) return cudaErrorMemoryAllocation;
+    dim3 blk(128), gr = bgrid(dim, n, count);
+    cudaStream_t s = b->stream;
+#define OPK(K, ...)                                                                       \
+  if (dim == 2) {                                                                         \
+    DISPATCH_T(dtype, if (var) K<2, T, true><<<gr, blk, 0, s>>>(__VA_ARGS__);             \
+               else K<2, T, false><<<gr, blk, 0, s>>>(__VA_ARGS__));                      \
+  } else {                                                                                \
+    DISPATCH_T(dtype, if (var) K<3, T, true><<<gr, blk, 0, s>>>(__VA_ARGS__);             \
+               else K<3, T, false><<<gr, blk, 0, s>>>(__VA_ARGS__));                      \
+  }
+    if (what == 0) { OPK(kb_rbgs_half, dev, g, color, flip, omega) }
+    else if (what == 1) { OPK(kb_jacobi, dev, g, flip, omega) }
+    else if (what == 2) { OPK(kb_residual, dev, g, flip) }
+    else {
+      if (dim == 2) { DISPATCH_T(dtype, kb_zero<2, T><<<gr, blk, 0, s>>>(dev, g, flip)) }
+      else { DISPATCH_T(dtype, kb_zero<3, T><<<gr, blk, 0, s>>>(dev, g, flip)) }
+    }
+#undef OPK
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    b->launches++;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_group_xfer(bool restrict_, const std::vector<BXfer> &items, mg_batch *b, int dim, int tf, int tc) {
+  if (items.empty()) return cudaSuccess;
+  Geo gf = items[0].gf, gc = items[0].gc;
+  int n = restrict_ ? gc.n : gf.n;  // grid of the written level
+  int chunk = chunk_of(dim, n);
+  for (size_t base = 0; base < items.size(); base += chunk) {
+    int count = (int)std::min<size_t>(chunk, items.size() - base);
+    const BXfer *dev = (const BXfer *)push(b, items.data() + base, sizeof(BXfer) * count);
+    if (!dev) return cudaErrorMemoryAllocation;
+    dim3 blk(128), gr = bgrid(dim, n, count);
+    cudaStream_t s = b->stream;
+    // (fine type, coarse type): (T,T) or (T, double) for the FP64 coarsest
+    if (restrict_) {
+      if (dim == 2) {
+        if (tc == F64 && tf != F64) { DISPATCH_T(tf, kb_restrict<2, T, double><<<gr, blk, 0, s>>>(dev, gf, gc)) }
+        else { DISPATCH_T(tf, kb_restrict<2, T, T><<<gr, blk, 0, s>>>(dev, gf, gc)) }
+      } else {
+        if (tc == F64 && tf != F64) { DISPATCH_T(tf, kb_restrict<3, T, double><<<gr, blk, 0, s>>>(dev, gf, gc)) }
+        else { DISPATCH_T(tf, kb_restrict<3, T, T><<<gr, blk, 0, s>>>(dev, gf, gc)) }
+      }
+    } else {
+      if (dim == 2) {
+        if (tc == F64 && tf != F64) { DISPATCH_T(tf, kb_prolong<2, double, T><<<gr, blk, 0, s>>>(dev, gc, gf)) }
+        else { DISPATCH_T(tf, kb_prolong<2, T, T><<<gr, blk, 0, s>>>(dev, gc, gf)) }
+      } else {
+        if (tc == F64 && tf != F64) { DISPATCH_T(tf, kb_prolong<3, double, T><<<gr, blk, 0, s>>>(dev, gc, gf)) }
+        else { DISPATCH_T(tf, kb_prolong<3, T, T><<<gr, blk, 0, s>>>(dev, gc, gf)) }
+      }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    b->launches++;
+  }
+  return cudaSuccess;
+}
+
+#define BLAUNCH(msg, call)                                   \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return bfail(MG_ECUDA, msg, e_);  \
+  } while (0)
+
+// One V-cycle of every problem in `ps` (levels grouped by size). zero0:
+// level 0 starts from zero (first inner cycle of a defect-correction step).
+mg_status batched_vcycle(mg_batch *b, const std::vector<mg_ctx *> &ps, bool zero0) {
+  const int dim = b->dim;
+  const int top_n = coarse_top_n(dim, b->fp64);
+  const mg_options &o = b->opt;
+  // level -> list, for every fine level size (size above the coarse threshold)
+  std::map<int, std::vector<std::pair<mg_ctx *, int>>, std::greater<int>> fine;
+  for (mg_ctx *c : ps)
+    for (int l = 0; l < c->nl; l++)
+      if (c->lv[l].n > top_n) fine[c->lv[l].n].push_back({c, l});
+  // Jacobi sweeps flip the live buffer of a level; track the parity per size
+  std::map<int, int> flip;
+  auto ops_of = [&](const std::vector<std::pair<mg_ctx *, int>> &v, bool only_zero, bool &any) {
+    std::vector<BOp> out;
+    any = false;
+    for (auto &pl : v) {
+      bool z = pl.second > 0 || zero0;
+      if (only_zero && !z) continue;
+      out.push_back(make_op(pl.first->lv[pl.second]));
+      any = true;
+    }
+    return out;
+  };
+  auto smooth = [&](int n, const std::vector<std::pair<mg_ctx *, int>> &v, int sweeps) -> mg_status {
+    bool any;
+    std::vector<BOp> ops = ops_of(v, false, any);
+    if (ops.empty()) return MG_OK;
+    const Level &L0 = v[0].first->lv[v[0].second];
+    bool var = L0.kf[0] != nullptr;
+    for (int k = 0; k < sweeps; k++) {
+      if (o.smoother == MG_RBGS) {
+        BLAUNCH("batched RBGS", launch_group_op(0, ops, b, dim, L0.dtype, var, 0, flip[n], o.omega));
+        BLAUNCH("batched RBGS", launch_group_op(0, ops, b, dim, L0.dtype, var, 1, flip[n], o.omega));
+      } else {
+        BLAUNCH("batched Jacobi", launch_group_op(1, ops, b, dim, L0.dtype, var, 0, flip[n], o.omega));
+        flip[n] ^= 1;
+      }
+    }
+    return MG_OK;
+  };
+  mg_status st;
+  // descend over the fine sizes
+  for (auto &kv : fine) {
+    int n = kv.first;
+    auto &v = kv.second;
+    const Level &L0 = v[0].first->lv[v[0].second];
+    bool any;
+    std::vector<BOp> zops = ops_of(v, true, any);
+    if (any) BLAUNCH("batched zero", launch_group_op(3, zops, b, dim, L0.dtype, false, 0, flip[n], 0.0));
+    if ((st = smooth(n, v, o.nu1))) return st;
+    std::vector<BOp> ops = ops_of(v, false, any);
+    BLAUNCH("batched residual", launch_group_op(2, ops, b, dim, L0.dtype, L0.kf[0] != nullptr, 0, flip[n], 0.0));
+    std::vector<BXfer> xs;
+    int tc = F64;
+    for (auto &pl : v) {
+      const Level &F = pl.first->lv[pl.second];
+      const Level &C = pl.first->lv[pl.second + 1];
+      BXfer x;
+      x.src = F.r;
+      x.dst = C.f;
+      x.gf = geo_of(F);
+      x.gc = geo_of(C);
+      xs.push_back(x);
+      tc = C.dtype;
+    }
+    BLAUNCH("batched restriction", launch_group_xfer(true, xs, b, dim, L0.dtype, tc));
+  }
+  // coarse cycles: one block per problem
+  {
+    std::vector<char> recs;
+    size_t smem = 0, rb = coarse_args_bytes();
+    bool var = false;
+    for (mg_ctx *c : ps) {
+      int t = 0;
+      while (t < c->nl && c->lv[t].n > top_n) t++;
+      std::vector<char> rec(rb);
+      size_t sm = coarse_args(c->lv, t, c->nl, t > 0 || zero0, o.smoother, o.omega, o.nu1, o.nu2, b->fp64,
+                              rec.data());
+      if (!sm) return bfail(MG_EINVAL, "coarse levels do not fit in shared memory");
+      smem = std::max(smem, sm);
+      var = c->lv[0].kf[0] != nullptr;
+      recs.insert(recs.end(), rec.begin(), rec.end());
+    }
+    const void *dev = push(b, recs.data(), recs.size());
+    if (!dev) return bfail(MG_ENOMEM, "batch descriptor area exhausted");
+    BLAUNCH("batched coarse cycle", coarse_cycle_batched(dev, (int)ps.size(), dim, var, b->fp64, smem, b->stream));
+    b->launches++;
+  }
+  // ascend
+  std::vector<int> sizes;
+  for (auto &kv : fine) sizes.push_back(kv.first);
+  std::reverse(sizes.begin(), sizes.end());
+  for (int n : sizes) {
+    auto &v = fine[n];
+    const Level &L0 = v[0].first->lv[v[0].second];
+    std::vector<BXfer> xs;
+    int tc = F64;
+    for (auto &pl : v) {
+      Level &F = pl.first->lv[pl.second];
+      Level &C = pl.first->lv[pl.second + 1];
+      BXfer x;
+      int cflip = C.n > top_n ? flip[C.n] : 0;
+      x.src = C.u[C.cur ^ cflip];
+      x.dst = F.u[F.cur ^ flip[n]];
+      x.gf = geo_of(F);
+      x.gc = geo_of(C);
+      xs.push_back(x);
+      tc = C.dtype;
+    }
+    BLAUNCH("batched interpolation", launch_group_xfer(false, xs, b, dim, L0.dtype, tc));
+    if ((st = smooth(n, v, o.nu2))) return st;
+  }
+  // commit the live-buffer flips of Jacobi levels
+  for (auto &kv : fine)
+    if (flip[kv.first])
+      for (auto &pl : kv.second) pl.first->lv[pl.second].cur ^= 1;
+  return MG_OK;
+}
+
+BOuter make_outer(mg_ctx *c, bool with_d, bool with_e) {
+  BOuter o;
+  memset(&o, 0, sizeof o);
+  Level &O = c->dc ? c->outer : c->lv[0];
+  Level &I = c->lv[0];
+  o.u = (double *)O.u[O.cur];
+  o.f = (const double *)O.f;
+  for (int d = 0; d < 3; d++) o.kf[d] = O.kf[d];
+  o.go = geo_of(O);
+  for (int d = 0; d < 3; d++) o.c[d] = O.c[d];
+  o.inv_h2 = O.inv_h2;
+  o.d = with_d ? I.f : nullptr;
+  o.e = with_e ? I.u[I.cur] : nullptr;
+  o.gi = geo_of(I);
+  return o;
+}
+
+// Residual norms of every problem into b->norms[i] (i = position in ps); in
+// defect-correction batches this is the outer FP64 residual, which also
+// writes each problem's inner defect.
+mg_status batched_norms(mg_batch *b, const std::vector<mg_ctx *> &ps) {
+  int P = (int)ps.size();
+  const int dim = b->dim;
+  bool var = ps[0]->variable;
+  if (b->dc) {
+    std::vector<BOuter> os;
+    for (mg_ctx *c : ps) os.push_back(make_outer(c, true, false));
+    const BOuter *dev = (const BOuter *)push(b, os.data(), sizeof(BOuter) * P);
+    if (!dev) return bfail(MG_ENOMEM, "batch descriptor area exhausted");
+    dim3 gr(kPartBlocks, P);
+    int ti = ps[0]->lv[0].dtype;
+    if (dim == 2) {
+      if (ti == F32) { if (var) kb_dc_residual<2, float, true><<<gr, 256, 0, b->stream>>>(dev, b->partials); else kb_dc_residual<2, float, false><<<gr, 256, 0, b->stream>>>(dev, b->partials); }
+      else { if (var) kb_dc_residual<2, bf16, true><<<gr, 256, 0, b->stream>>>(dev, b->partials); else kb_dc_residual<2, bf16, false><<<gr, 256, 0, b->stream>>>(dev, b->partials); }
+    } else {
+      if (ti == F32) { if (var) kb_dc_residual<3, float, true><<<gr, 256, 0, b->stream>>>(dev, b->partials); else kb_dc_residual<3, float, false><<<gr, 256, 0, b->stream>>>(dev, b->partials); }
+      else { if (var) kb_dc_residual<3, bf16, true><<<gr, 256, 0, b->stream>>>(dev, b->partials); else kb_dc_residual<3, bf16, false><<<gr, 256, 0, b->stream>>>(dev, b->partials); }
+    }
+  } else {
+    std::vector<BOp> os;
+    for (mg_ctx *c : ps) os.push_back(make_op(c->lv[0]));
+    const BOp *dev = (const BOp *)push(b, os.data(), sizeof(BOp) * P);
+    if (!dev) return bfail(MG_ENOMEM, "batch descriptor area exhausted");
+    dim3 gr(kPartBlocks, P);
+    if (dim == 2) { if (var) kb_norm<2, true><<<gr, 256, 0, b->stream>>>(dev, b->partials); else kb_norm<2, false><<<gr, 256, 0, b->stream>>>(dev, b->partials); }
+    else { if (var) kb_norm<3, true><<<gr, 256, 0, b->stream>>>(dev, b->partials); else kb_norm<3, false><<<gr, 256, 0, b->stream>>>(dev, b->partials); }
+  }
+  BCK("batched norm partials", cudaGetLastError());
+  kb_finalize<<<P, kPartBlocks, 0, b->stream>>>(b->partials, kPartBlocks, b->norms);
+  BCK("batched norm finalize", cudaGetLastError());
+  b->launches += 2;
+  return MG_OK;
+}
+
+mg_status batched_update(mg_batch *b, const std::vector<mg_ctx *> &ps) {
+  int P = (int)ps.size();
+  std::vector<BOuter> os;
+  for (mg_ctx *c : ps) os.push_back(make_outer(c, false, true));
+  const BOuter *dev = (const BOuter *)push(b, os.data(), sizeof(BOuter) * P);
+  if (!dev) return bfail(MG_ENOMEM, "batch descriptor area exhausted");
+  dim3 gr(kPartBlocks, P);
+  int ti = ps[0]->lv[0].dtype;
+  if (b->dim == 2) {
+    if (ti == F32) kb_dc_update<2, float><<<gr, 256, 0, b->stream>>>(dev);
+    else kb_dc_update<2, bf16><<<gr, 256, 0, b->stream>>>(dev);
+  } else {
+    if (ti == F32) kb_dc_update<3, float><<<gr, 256, 0, b->stream>>>(dev);
+    else kb_dc_update<3, bf16><<<gr, 256, 0, b->stream>>>(dev);
+  }
+  BCK("batched update", cudaGetLastError());
+  b->launches++;
+  return MG_OK;
+}
+
+bool same_shape(const mg_options &a, const mg_options &b) {
+  return a.smoother == b.smoother && a.omega == b.omega && a.nu1 == b.nu1 && a.nu2 == b.nu2 &&
+         a.precision == b.precision && std::max(a.inner_cycles, 1) == std::max(b.inner_cycles, 1);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t mg_batch_workspace_bytes(int max_problems) {
+  if (max_problems < 1) return 0;
+  return desc_area_bytes(max_problems) + align256(sizeof(double) * (size_t)max_problems * kPartBlocks) +
+         align256(sizeof(double) * (size_t)max_problems);
+}
+
+mg_status mg_batch_create(int max_problems, void *workspace, size_t bytes, void *stream, mg_batch **out) {
+  if (!out || max_problems < 1 || !workspace) return bfail(MG_EINVAL, "bad batch arguments");
+  if ((uintptr_t)workspace % 256) return bfail(MG_EINVAL, "batch workspace must be 256-byte aligned");
+  if (bytes < mg_batch_workspace_bytes(max_problems)) return bfail(MG_ENOMEM, "batch workspace too small");
+  mg_batch *b = new (std::nothrow) mg_batch();
+  if (!b) return bfail(MG_ENOMEM, "host allocation of the batch failed");
+  b->maxp = max_problems;
+  b->probs.assign(max_problems, nullptr);
+  b->r0.assign(max_problems, -1.0);
+  b->ws = (char *)workspace;
+  b->ws_bytes = bytes;
+  b->desc_bytes = desc_area_bytes(max_problems);
+  b->partials = (double *)(b->ws + b->desc_bytes);
+  b->norms = (double *)(b->ws + b->desc_bytes + align256(sizeof(double) * (size_t)max_problems * kPartBlocks));
+  b->stream = (cudaStream_t)stream;
+  b->have_opts = false;
+  b->launches = 0;
+  b->dev_off = 0;
+  b->pinned = nullptr;
+  if (cudaMallocHost((void **)&b->pinned, b->desc_bytes) != cudaSuccess) {
+    delete b;
+    return bfail(MG_ENOMEM, "pinned host staging for batch descriptors failed");
+  }
+  *out = b;
+  return MG_OK;
+}
+
+mg_status mg_batch_destroy(mg_batch *b) {
+  if (!b) return MG_OK;
+  if (b->pinned) cudaFreeHost(b->pinned);
+  delete b;
+  return MG_OK;
+}
+
+mg_status mg_batch_add(mg_batch *b, mg_ctx *c, int *id) {
+  if (!b || !c || !id) return bfail(MG_EINVAL, "NULL argument");
+  if (c->opt.smoother == MG_JACOBI && ((c->opt.nu1 + c->opt.nu2) & 1))
+    return bfail(MG_EINVAL, "batched Jacobi needs an even number of sweeps per cycle");
+  if (b->have_opts && (!same_shape(b->opt, c->opt) || b->dim != c->dim))
+    return bfail(MG_EINVAL, "problem options differ from the batch's (smoother, omega, nu, precision, dim)");
+  for (int i = 0; i < b->maxp; i++) {
+    if (!b->probs[i]) {
+      if (!b->have_opts) {
+        b->opt = c->opt;
+        b->dim = c->dim;
+        b->dc = c->dc;
+        b->fp64 = !c->dc;
+        b->have_opts = true;
+      }
+      b->probs[i] = c;
+      b->r0[i] = -1.0;
+      *id = i;
+      return MG_OK;
+    }
+  }
+  return bfail(MG_ENOMEM, "batch is full");
+}
+
+mg_status mg_batch_remove(mg_batch *b, int id) {
+  if (!b || id < 0 || id >= b->maxp || !b->probs[id]) return bfail(MG_EINVAL, "unknown problem id");
+  b->probs[id] = nullptr;
+  b->r0[id] = -1.0;
+  return MG_OK;
+}
+
+mg_status mg_batch_step(mg_batch *b, const int *ids, int count, double *rho) {
+  if (!b || (count > 0 && !ids)) return bfail(MG_EINVAL, "NULL argument");
+  if (count == 0) return MG_OK;
+  std::vector<mg_ctx *> ps, fresh;
+  std::vector<int> fresh_ids;
+  for (int i = 0; i < count; i++) {
+    int id = ids[i];
+    if (id < 0 || id >= b->maxp || !b->probs[id]) return bfail(MG_EINVAL, "unknown problem id");
+    ps.push_back(b->probs[id]);
+    if (b->r0[id] < 0.0) {
+      fresh.push_back(b->probs[id]);
+      fresh_ids.push_back(id);
+    }
+  }
+  bool var = ps[0]->variable != 0;
+  for (mg_ctx *c : ps)
+    if ((c->variable != 0) != var) return bfail(MG_EINVAL, "a step mixes constant and variable stencils");
+  mg_status st;
+  b->dev_off = 0;
+  // initial residual (and, with defect correction, the first defect) of new problems
+  if (!fresh.empty()) {
+    std::vector<double> h(fresh.size());
+    if ((st = batched_norms(b, fresh))) return st;
+    BCK("read initial norms", cudaMemcpyAsync(h.data(), b->norms, sizeof(double) * fresh.size(),
+                                              cudaMemcpyDeviceToHost, b->stream));
+    BCK("synchronize", cudaStreamSynchronize(b->stream));
+    for (size_t i = 0; i < fresh.size(); i++) b->r0[fresh_ids[i]] = h[i];
+    b->dev_off = 0;
+  }
+  int inner = b->dc ? std::max(b->opt.inner_cycles, 1) : 1;
+  for (int k = 0; k < inner; k++)
+    if ((st = batched_vcycle(b, ps, b->dc && k == 0))) return st;
+  if (b->dc && (st = batched_update(b, ps))) return st;
+  if ((st = batched_norms(b, ps))) return st;
+  std::vector<double> h(count);
+  BCK("read norms", cudaMemcpyAsync(h.data(), b->norms, sizeof(double) * count, cudaMemcpyDeviceToHost, b->stream));
+  BCK("synchronize", cudaStreamSynchronize(b->stream));
+  b->dev_off = 0;
+  if (rho)
+    for (int i = 0; i < count; i++) {
+      double r0 = b->r0[ids[i]];
+      rho[i] = r0 > 0.0 ? h[i] / r0 : 0.0;
+    }
+  return MG_OK;
+}
+
+mg_status mg_batch_solve(mg_batch *b, const double *tol, int maxit, int *iters, double *relres) {
+  if (!b || !tol) return bfail(MG_EINVAL, "NULL argument");
+  std::vector<int> active;
+  for (int i = 0; i < b->maxp; i++)
+    if (b->probs[i]) {
+      active.push_back(i);
+      if (iters) iters[i] = 0;
+      if (relres) relres[i] = 1.0;
+    }
+  mg_status st;
+  bool bad = false;
+  for (int k = 1; k <= maxit && !active.empty(); k++) {
+    std::vector<double> rho(active.size());
+    if ((st = mg_batch_step(b, active.data(), (int)active.size(), rho.data()))) return st;
+    std::vector<int> next;
+    for (size_t i = 0; i < active.size(); i++) {
+      int id = active[i];
+      if (iters) iters[id] = k;
+      if (relres) relres[id] = rho[i];
+      if (!std::isfinite(rho[i])) bad = true;
+      else if (rho[i] > tol[id]) next.push_back(id);
+    }
+    active.swap(next);
+  }
+  if (bad) return bfail(MG_ENOCONV, "a residual became non-finite");
+  if (!active.empty()) return bfail(MG_ENOCONV, "some problems did not reach their tolerance");
+  return MG_OK;
+}
+
+unsigned long long mg_batch_launches(const mg_batch *b) { return b ? b->launches : 0ull; }
+
+}  // extern "C"

@@ -29,14 +29,14 @@ int coarse_top_n(int dim, bool fp64) {
   return fp64 ? 9 : 17;
 }
 
-cudaError_t coarse_cycle(const Level *lv, int first, int nl, bool zero_top, int smoother, double omega, int nu1,
-                         int nu2, bool fp64, cudaStream_t s) {
-  cz::CoarseArgs a;
+size_t coarse_args(const Level *lv, int first, int nl, bool zero_top, int smoother, double omega, int nu1, int nu2,
+                   bool fp64, void *args_out) {
+  cz::CoarseArgs &a = *(cz::CoarseArgs *)args_out;
   memset(&a, 0, sizeof a);
   const Level &T = lv[first];
   a.dim = T.dim;
   a.nlev = nl - first;
-  if (a.nlev > cz::kMaxLev || a.nlev < 1) return cudaErrorInvalidValue;
+  if (a.nlev > cz::kMaxLev || a.nlev < 1) return 0;
   a.var = T.kf[0] != nullptr;
   for (int d = 0; d < 3; d++) a.c[d] = T.c[d];
   size_t elems = 0;
@@ -66,13 +66,53 @@ cudaError_t coarse_cycle(const Level *lv, int first, int nl, bool zero_top, int 
   a.nu1 = nu1;
   a.nu2 = nu2;
   size_t smem = elems * (fp64 ? 8 : 4);
-  if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  if (T.dim == 2) {
+  if (smem > 227 * 1024) return 0;
+  return smem;
+}
+
+size_t coarse_args_bytes() { return sizeof(cz::CoarseArgs); }
+
+cudaError_t coarse_cycle(const Level *lv, int first, int nl, bool zero_top, int smoother, double omega, int nu1,
+                         int nu2, bool fp64, cudaStream_t s) {
+  cz::CoarseArgs a;
+  size_t smem = coarse_args(lv, first, nl, zero_top, smoother, omega, nu1, nu2, fp64, &a);
+  if (!smem) return cudaErrorInvalidValue;
+  if (a.dim == 2) {
     if (fp64) return a.var ? launch<2, true, double>(a, smem, s) : launch<2, false, double>(a, smem, s);
     return a.var ? launch<2, true, float>(a, smem, s) : launch<2, false, float>(a, smem, s);
   }
   if (fp64) return a.var ? launch<3, true, double>(a, smem, s) : launch<3, false, double>(a, smem, s);
   return a.var ? launch<3, true, float>(a, smem, s) : launch<3, false, float>(a, smem, s);
+}
+
+namespace {
+template <int DIM, bool VAR, typename C>
+cudaError_t launch_batched(const void *list, int count, size_t smem, cudaStream_t s) {
+  static size_t opted = 0;
+  if (smem > opted) {
+    cudaError_t e = cudaFuncSetAttribute(cz::k_coarse_cycle_batched<DIM, VAR, C>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    opted = smem;
+  }
+  cz::k_coarse_cycle_batched<DIM, VAR, C><<<count, cz::kThreads, smem, s>>>((const cz::CoarseArgs *)list);
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t coarse_cycle_batched(const void *list_dev, int count, int dim, bool var, bool fp64, size_t smem,
+                                 cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  if (dim == 2) {
+    if (fp64) return var ? launch_batched<2, true, double>(list_dev, count, smem, s)
+                         : launch_batched<2, false, double>(list_dev, count, smem, s);
+    return var ? launch_batched<2, true, float>(list_dev, count, smem, s)
+               : launch_batched<2, false, float>(list_dev, count, smem, s);
+  }
+  if (fp64) return var ? launch_batched<3, true, double>(list_dev, count, smem, s)
+                       : launch_batched<3, false, double>(list_dev, count, smem, s);
+  return var ? launch_batched<3, true, float>(list_dev, count, smem, s)
+             : launch_batched<3, false, float>(list_dev, count, smem, s);
 }
 
 }  // namespace mg

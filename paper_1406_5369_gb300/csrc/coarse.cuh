@@ -176,7 +176,7 @@ __device__ void smooth(const Lev<C> &L, C *tmp, const C (&c)[3], int smoother, C
 }
 
 template <int DIM, bool VAR, typename C>
-__global__ void __launch_bounds__(kThreads) k_coarse_cycle(CoarseArgs a) {
+__device__ __forceinline__ void coarse_cycle_body(const CoarseArgs &a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *sm = (C *)smem_raw;
   const C c[3] = {(C)a.c[0], (C)a.c[1], (C)a.c[2]};
@@ -293,6 +293,17 @@ __global__ void __launch_bounds__(kThreads) k_coarse_cycle(CoarseArgs a) {
       stg_any(a.u_top, g, a.top_dtype, (double)T.u[p]);
     });
   }
+}
+
+template <int DIM, bool VAR, typename C>
+__global__ void __launch_bounds__(kThreads) k_coarse_cycle(CoarseArgs a) {
+  coarse_cycle_body<DIM, VAR, C>(a);
+}
+
+// One block per problem: the coarse cycles of a batch of independent problems.
+template <int DIM, bool VAR, typename C>
+__global__ void __launch_bounds__(kThreads) k_coarse_cycle_batched(const CoarseArgs *__restrict__ list) {
+  coarse_cycle_body<DIM, VAR, C>(list[blockIdx.x]);
 }
 
 }  // namespace cz

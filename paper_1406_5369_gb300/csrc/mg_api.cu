@@ -45,63 +45,13 @@ mg_status fail(mg_status st, const char *fmt, ...) {
   } while (0)
 #define LAUNCH(c, call) TLAUNCH(c, MG_KERNEL_OTHER, 0, s, call)
 
-constexpr int kMaxLevels = 31;
-constexpr int kGraphSlots = 4;
 
 // Dimension dispatch of the level kernels.
 #define DISPATCH(L, fn, ...) ((L).dim == 2 ? mg::d2::fn(__VA_ARGS__) : mg::d3::fn(__VA_ARGS__))
 
 }  // namespace
 
-constexpr int kMaxPairs = 2048;       // event pairs for kernel timing
-constexpr int kSlotPairs = 256;       // timed kernels per captured graph
-constexpr int kKinds = 6;             // mg_kernel_kind values
-
-struct TimingPair {
-  cudaEvent_t a, b;
-  int kind, level;
-  int owner;     // -1: direct launch (recycled after harvest), else graph slot
-  bool pending;  // recorded, not yet harvested
-};
-
-struct GraphSlot {
-  bool valid;
-  int kind;           // 0 = cycle, 1 = solve step
-  unsigned key;       // live-buffer bitmask at capture
-  unsigned post;      // live-buffer bitmask after the captured work
-  unsigned long long kernels;  // kernel nodes in the graph
-  cudaGraphExec_t exec;
-  int npairs;                  // timed kernels inside the graph
-  int pairs[kSlotPairs];
-};
-
-struct mg_ctx {
-  int dim, n, nl;
-  int variable;
-  bool dc;                // defect-correction precision
-  mg_options opt;
-  cudaStream_t stream;    // user stream
-  cudaStream_t cap;       // private stream used for graph capture
-  Level lv[kMaxLevels];   // working hierarchy (FP64, or the inner DC hierarchy)
-  Level outer;            // DC: outer FP64 finest level (u[0..1] ping-pong, f, r = FP64 staging, kf)
-  double *partials;       // kMaxPartials doubles
-  double *norm_out;       // [0] = norm, [1] = sum of squares
-  float *dc_scale;        // power of two applied before squaring in scaled norm passes
-  double *host_norm;      // pinned host copy of norm_out
-  size_t used_bytes;
-  GraphSlot graphs[kGraphSlots];
-  int next_slot;
-  unsigned long long launches;  // kernels launched (direct or inside replayed graphs)
-  // kernel timing (mg_set_timing)
-  int timing;
-  int capturing_slot;          // graph slot being captured, -1 if none
-  TimingPair pairs[kMaxPairs];
-  int npairs;
-  int free_pairs[kMaxPairs];
-  int nfree;
-  double t_ms[kKinds][kMaxLevels];
-  unsigned long long t_n[kKinds][kMaxLevels];
-};
+#include "ctx.h"
 
 namespace {
 
@@ -702,6 +652,8 @@ mg_status mg_destroy(mg_ctx *c) {
     cudaEventDestroy(c->pairs[i].a);
     cudaEventDestroy(c->pairs[i].b);
   }
+  free(c->pairs);
+  free(c->free_pairs);
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->host_norm) cudaFreeHost(c->host_norm);
   free(c);
@@ -858,6 +810,17 @@ unsigned long long mg_kernel_launches(const mg_ctx *c) { return c ? c->launches 
 
 mg_status mg_set_timing(mg_ctx *c, int on) {
   if (!c) return fail(MG_EINVAL, "NULL context");
+  if (on && !c->pairs) {
+    c->pairs = (TimingPair *)calloc(kMaxPairs, sizeof(TimingPair));
+    c->free_pairs = (int *)calloc(kMaxPairs, sizeof(int));
+    if (!c->pairs || !c->free_pairs) {
+      free(c->pairs);
+      free(c->free_pairs);
+      c->pairs = nullptr;
+      c->free_pairs = nullptr;
+      return fail(MG_ENOMEM, "host allocation of timing events failed");
+    }
+  }
   if ((on != 0) != (c->timing != 0)) {
     CK(cudaStreamSynchronize(c->stream));
     if (c->timing) timing_harvest(c);

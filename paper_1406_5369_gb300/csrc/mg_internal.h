@@ -100,6 +100,15 @@ cudaError_t norm_finalize_ex(const double *partials, int nb, double *out, const 
 int coarse_top_n(int dim, bool fp64);
 cudaError_t coarse_cycle(const Level *lv, int first, int nl, bool zero_top, int smoother, double omega, int nu1,
                          int nu2, bool fp64, cudaStream_t s);
+// Fills the kernel arguments of one problem's coarse cycle into args_out
+// (coarse_args_bytes() bytes); returns the shared memory it needs, 0 if the
+// levels do not fit. coarse_cycle_batched runs `count` such argument
+// records (device memory) with one block each.
+size_t coarse_args(const Level *lv, int first, int nl, bool zero_top, int smoother, double omega, int nu1, int nu2,
+                   bool fp64, void *args_out);
+size_t coarse_args_bytes();
+cudaError_t coarse_cycle_batched(const void *list_dev, int count, int dim, bool var, bool fp64, size_t smem,
+                                 cudaStream_t s);
 
 // Sets the message mg_last_error() returns on the calling thread.
 void set_error_message(const char *msg);
