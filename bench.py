@@ -346,6 +346,161 @@ def run_reference(args):
     print(json.dumps(rec), flush=True)
 
 
+# ------------------------------------------------------------------ other configurations
+# These print their own JSON line when selected with --workload; the default
+# run measures only the 8193^2 headline above.
+
+def _init_cuda():
+    import torch
+    from paper_1406_5369_gb300 import build as b
+    from paper_1406_5369_gb300 import load
+    torch.cuda.set_device(0)
+    b.build()
+    load()
+    return torch
+
+
+def _line(metric, value, unit, hib, ms, args, config, dtype, **extra):
+    rec = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": hib, "scaling": "weak",
+           "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": config}
+    rec.update(extra)
+    print(json.dumps(rec), flush=True)
+
+
+def run_c1(args):
+    """129^2 2D Poisson, sine right-hand side, FP64 V(2,1) RBGS, 10 cycles from 0."""
+    torch = _init_cuda()
+    import math
+    import numpy as np
+    import synth
+    from paper_1406_5369_gb300 import Solver
+    n = 129
+    f = torch.from_numpy(synth.sine_rhs(2, n)).cuda()
+    s = Solver(2, n, maxit=10)
+    s.set_rhs(f)
+    for _ in range(args.warmup):
+        s.set_solution(None)
+        s.solve(0.0, raise_on_noconv=False)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        s.set_solution(None)
+        it, rr, hist = s.solve(0.0, raise_on_noconv=False)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    u = s.get_solution()
+    h = 1.0 / (n - 1)
+    ch = (math.pi * h / 2) ** 2 / math.sin(math.pi * h / 2) ** 2
+    err = float(np.max(np.abs(u - synth.sine_solution(2, n))))
+    _line(METRIC, 10 / (ms / 1e3), "V-cycles/s (10 cycles + norms per step, launch-bound)", True, ms, args,
+          {"workload": "2D Poisson 129^2, f = 2 pi^2 sin(pi x) sin(pi y), FP64 V(2,1) RBGS omega=1, 7 levels, "
+                       "10 cycles from u0 = 0"}, "f64",
+          rho_history=[float(x) for x in hist], max_error_vs_exact=err, closed_form_error=ch - 1)
+
+
+def run_c3(args):
+    """513^3 3D Poisson, N(0,1) right-hand side, Jacobi V(2,2) omega 6/7: FP64 vs BF16-DC to 1e-10."""
+    torch = _init_cuda()
+    import synth
+    from paper_1406_5369_gb300 import Solver, autotune
+    n = 513
+    f = torch.from_numpy(synth.normal_rhs(3, n, 0x5EED0003)).cuda()
+    kw = dict(smoother="jacobi", omega=6.0 / 7.0, nu1=2, nu2=2, maxit=80)
+    best, table = autotune.tune(3, n, f, 1e-10, {"inner_cycles": [1, 2, 3]}, base=dict(kw, precision="bf16_dc"))
+    res = {}
+    for prec, extra in (("bf16_dc", {"inner_cycles": best["inner_cycles"]}), ("fp32_dc", {"inner_cycles": best["inner_cycles"]}), ("fp64", {})):
+        s = Solver(3, n, precision=prec, **kw, **extra)
+        ms, it = autotune.time_solve(s, f, 1e-10, reps=max(1, args.steps))
+        res[prec] = {"time_to_tol_s": ms / 1e3, "steps": it}
+        s.close()
+        del s
+    ms = res["bf16_dc"]["time_to_tol_s"] * 1e3
+    _line(METRIC, 1e3 / ms, "solves/s (to 1e-10 rel. residual; 1/time-to-1e-10)", True, ms, args,
+          {"workload": "3D Poisson 513^3, f ~ N(0,1) (seed 0x5EED0003), Jacobi omega=6/7 V(2,2), full weighting, "
+                       "trilinear; BF16-stored FP32 inner cycles in FP64 defect correction to 1e-10",
+           "inner_cycles": best["inner_cycles"]}, "bf16 storage / f32 inner / f64 outer",
+          forms=res, autotune=table)
+
+
+def run_c4(args):
+    """4096 variable-coefficient 2D problems, sizes (2^m+1)^2, m ~ U{5..10}, FP32-DC to 1e-8, one batch."""
+    torch = _init_cuda()
+    import numpy as np
+    import synth
+    from paper_1406_5369_gb300 import BatchSolver, Solver
+    P = args.batch_problems
+    seed = 0x5EED0004
+    ms_ = synth.batch_levels(P, seed)
+    t_setup = time.perf_counter()
+    solvers = []
+    nodes = 0
+    for p in range(P):
+        n = (1 << int(ms_[p])) + 1
+        k = synth.torch_lognormal_k(2, n, seed ^ p ^ 0x10000, device="cuda")
+        f = synth.torch_uniform_rhs(2, n, seed ^ p, device="cuda")
+        s = Solver(2, n, k=k, precision="fp32_dc", maxit=60, inner_cycles=1)
+        s.set_rhs(f)
+        solvers.append(s)
+        nodes += n * n
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
+    timings = {}
+    best_inner, best_ms = None, None
+    for inner in (1, 2, 3):  # default (1) and the autotuner's candidates
+        B = BatchSolver(P)
+        for s in solvers:
+            s.set_solution(None)
+            B.add(s)
+        B.set_inner_cycles(inner)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        iters, rel = B.solve(1e-8, maxit=60)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        timings[inner] = {"total_s": dt, "max_steps": int(iters[:P].max()), "launches": int(B.launches()),
+                          "max_relres": float(rel[:P].max())}
+        if best_ms is None or dt < best_ms:
+            best_inner, best_ms = inner, dt
+        B.close()
+    _line(METRIC, P / best_ms, "problems/s (batch of 4096 solved to 1e-8)", True, best_ms * 1e3, args,
+          {"workload": f"{P} independent 2D variable-coefficient problems -div(k grad u) = f, sizes (2^m+1)^2, "
+                       "m ~ U{5..10} (seed 0x5EED0004), k lognormal(0,1) per node, harmonic faces, f ~ U[-1,1]; "
+                       "FP32 inner / FP64 outer defect correction to 1e-8; RBGS V(2,1); one mg_batch",
+           "total_nodes": nodes, "setup_s": t_setup},
+          "f32 inner / f64 outer", tuned_inner_cycles=best_inner, default_vs_tuned=timings,
+          note="inner_cycles is chosen by timing candidates 1..3 on the batch (autotuned vs default = 1)")
+
+
+def run_c5(args):
+    """Serving: Poisson arrivals, mixed 2D/3D Poisson requests, p50/p99 latency and solves/s."""
+    torch = _init_cuda()
+    import synth
+    from paper_1406_5369_gb300.serve import Server
+    rate = args.rate
+    count = max(1, int(rate * args.serve_seconds))
+    reqs = synth.serving_requests(count, 0x5EED0005, rate_per_s=rate)
+    srv = Server(budget_bytes=150e9, max_active=4096)
+    # warm the pools / kernels with a short burst of the same mix (not counted)
+    warm = synth.serving_requests(min(64, count), 0x5EED0095, rate_per_s=rate * 10)
+    srv.run(warm)
+    srv.steps = 0
+    with ClockSampler(0) as clk:
+        done, stats = srv.run(reqs, max_wall=args.serve_seconds * 6 + 30)
+    saturated = stats["unfinished"] > 0 or stats["solves_per_s"] < 0.9 * rate
+    _line(METRIC, stats["solves_per_s"], "solves/s (served; p50/p99 latency in fields)", True,
+          1e3 * stats["wall_s"] / max(1, stats["steps"]), args,
+          {"workload": f"serving: Poisson arrivals at {rate:g} req/s for {args.serve_seconds:g} s ({count} requests); "
+                       "70% 2D Poisson 65^2..4097^2 (RBGS V(2,1)), 30% 3D 33^3..257^3 (Jacobi V(2,2)), sizes "
+                       "log-uniform over 2^m+1, f ~ U[-1,1], tol 1e-6 or 1e-10; FP32-DC; 150 GB HBM budget; "
+                       "hierarchies resident and pooled; same-level batching across requests"},
+          "f32 inner / f64 outer", p50_ms=stats["p50_ms"], p99_ms=stats["p99_ms"], serving=stats,
+          saturated=saturated, clocks=clk.summary())
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -353,11 +508,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
+                    help="c2 (default): the 8193^2 headline; others print their own line")
+    ap.add_argument("--batch-problems", type=int, default=4096)
+    ap.add_argument("--rate", type=float, default=2000.0)
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
-    else:
+    elif args.workload == "c2":
         run_gpu(args)
+    else:
+        {"c1": run_c1, "c3": run_c3, "c4": run_c4, "c5": run_c5}[args.workload](args)
 
 
 if __name__ == "__main__":

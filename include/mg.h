@@ -295,6 +295,10 @@ mg_status mg_batch_step(mg_batch *batch, const int *ids, int count, double *rho)
  * some problem did not reach its tolerance or a residual was not finite. */
 mg_status mg_batch_solve(mg_batch *batch, const double *tol, int maxit, int *iters, double *relres);
 
+/* Inner V-cycles per outer step for the batch's defect-correction steps
+ * (1..8), overriding the value taken from its first problem. */
+mg_status mg_batch_set_inner_cycles(mg_batch *batch, int inner_cycles);
+
 /* Kernels the batch has launched so far (diagnostic). */
 unsigned long long mg_batch_launches(const mg_batch *batch);
 

@@ -210,9 +210,13 @@ void or_node_faces(int dim, int n, const double *c, const double *knode, double 
   }
 }
 
-/* Coarse faces by rediscretisation (Table 1, "direct" coarsening): a coarse
- * face spans two collinear fine faces in series, so its coefficient is
- * 2 / (1/k_a + 1/k_b) = 2 k_a k_b / (k_a + k_b). */
+/* Coarse faces by rediscretisation (Table 1, "direct" coarsening). A coarse
+ * face along dimension d spans two collinear fine faces in series,
+ * 2 / (1/k_a + 1/k_b) = 2 k_a k_b / (k_a + k_b); across the face, the series
+ * values of the fine lines at offsets -1, 0, +1 (in each other dimension)
+ * are averaged in parallel with the full-weighting weights (1/4, 1/2, 1/4).
+ * Faces on coarse boundary lines, which no interior stencil uses, take the
+ * centre line only. */
 void or_coarsen_faces(int dim, int nf, const double *kxf, const double *kyf, const double *kzf,
                       double *kxc, double *kyc, double *kzc) {
   const double *ff[3] = {kxf, kyf, kzf};
@@ -222,12 +226,30 @@ void or_coarsen_faces(int dim, int nf, const double *kxf, const double *kyf, con
   for (int d = 0; d < dim; d++) {
     long sc = stride(nc, d), sf = stride(nf, d);
     for (long P = 0; P < Nc; P++) {
-      long I = P % nc, J = (P / nc) % nc, K = dim == 3 ? P / ((long)nc * nc) : 0;
+      long C3[3] = {P % nc, (P / nc) % nc, dim == 3 ? P / ((long)nc * nc) : 0};
       long coord = (P / sc) % nc;
       if (coord >= nc - 1) { fc[d][P] = 0.0; continue; }
-      long q = 2 * I + (long)nf * (2 * J + (long)nf * 2 * K);
-      double a = ff[d][q], b = ff[d][q + sf];
-      fc[d][P] = 2.0 * a * b / (a + b);
+      double acc = 0.0;
+      for (int oz = -1; oz <= 1; oz++)
+        for (int oy = -1; oy <= 1; oy++)
+          for (int ox = -1; ox <= 1; ox++) {
+            int off[3] = {ox, oy, oz};
+            double w = 1.0;
+            int skip = 0;
+            for (int e = 0; e < 3; e++) {
+              int interior_line = e < dim && e != d && C3[e] >= 1 && C3[e] <= nc - 2;
+              if (e == d || e >= dim || !interior_line) {
+                if (off[e] != 0) skip = 1;
+              } else {
+                w *= off[e] == 0 ? 0.5 : 0.25;
+              }
+            }
+            if (skip) continue;
+            long q = (2 * C3[0] + off[0]) + (long)nf * ((2 * C3[1] + off[1]) + (long)nf * (2 * C3[2] + off[2]));
+            double a = ff[d][q], b = ff[d][q + sf];
+            acc += w * (2.0 * a * b / (a + b));
+          }
+      fc[d][P] = acc;
     }
   }
 }

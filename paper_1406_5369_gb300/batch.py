@@ -61,6 +61,9 @@ class BatchSolver:
             C.check(st)
         return iters, rel
 
+    def set_inner_cycles(self, n):
+        C.check(self._lib.mg_batch_set_inner_cycles(self.h, int(n)))
+
     def launches(self):
         return self._lib.mg_batch_launches(self.h)
 

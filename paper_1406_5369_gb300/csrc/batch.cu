@@ -801,4 +801,10 @@ mg_status mg_batch_solve(mg_batch *b, const double *tol, int maxit, int *iters, 
 
 unsigned long long mg_batch_launches(const mg_batch *b) { return b ? b->launches : 0ull; }
 
+mg_status mg_batch_set_inner_cycles(mg_batch *b, int inner_cycles) {
+  if (!b || inner_cycles < 1 || inner_cycles > 8) return bfail(MG_EINVAL, "inner_cycles must lie in 1..8");
+  b->opt.inner_cycles = inner_cycles;
+  return MG_OK;
+}
+
 }  // extern "C"

@@ -358,18 +358,54 @@ __global__ void k_node_faces(const double *__restrict__ k, Geo gk, C *kx, C *ky,
   if (DIM == 3) kz[t.p] = (C)fz;
 }
 
-// Coarse faces: two collinear fine faces in series, 2 a b / (a + b).
+// Coarse faces (rediscretisation): along the face's dimension two collinear
+// fine faces in series, 2 a b / (a + b); across it, the series values of the
+// fine lines at offsets -1, 0, +1 averaged with weights (1/4, 1/2, 1/4) per
+// other dimension (centre line only on coarse boundary lines, which no
+// interior stencil uses). Accumulated in FP64.
+template <int DIM>
+__device__ __forceinline__ double coarse_face(const void *ff, bool f64, Geo gf, int d, int I, int J, int K, int nc) {
+  const long long sd = d == 0 ? 1 : (d == 1 ? gf.sy : gf.sz);
+  const int C3[3] = {I, J, K};
+  int oth[2] = {0, 0}, no = 0;  // the dimensions across the face
+  for (int g = 0; g < DIM; g++)
+    if (g != d) oth[no++] = g;
+  double acc = 0.0;
+  for (int o2 = -1; o2 <= 1; o2++)
+    for (int o1 = -1; o1 <= 1; o1++) {
+      int off[2] = {o1, o2};
+      double w = 1.0;
+      bool skip = false;
+      for (int e = 0; e < 2; e++) {
+        bool line = e < no && C3[oth[e]] >= 1 && C3[oth[e]] <= nc - 2;
+        if (!line) {
+          if (off[e] != 0) skip = true;
+        } else {
+          w *= off[e] == 0 ? 0.5 : 0.25;
+        }
+      }
+      if (skip) continue;
+      int q3[3] = {2 * I, 2 * J, 2 * K};
+      for (int e = 0; e < no; e++) q3[oth[e]] += off[e];
+      long long q = (long long)q3[2] * gf.sz + (long long)q3[1] * gf.sy + q3[0];
+      double a = f64 ? ((const double *)ff)[q] : (double)((const float *)ff)[q];
+      double b = f64 ? ((const double *)ff)[q + sd] : (double)((const float *)ff)[q + sd];
+      acc += w * (2.0 * a * b / (a + b));
+    }
+  return acc;
+}
+
 template <int DIM, typename Cf, typename Cc>
 __global__ void k_coarsen_faces(const Cf *fx, const Cf *fy, const Cf *fz, Geo gf, Cc *cx, Cc *cy, Cc *cz,
                                 Geo gc) {
   Idx t = node_index<DIM>(gc);
   if (t.i >= gc.n) return;
   int n = gc.n;
-  long long q = (long long)(2 * t.k) * gf.sz + (long long)(2 * t.j) * gf.sy + 2 * t.i;
+  const bool f64 = sizeof(Cf) == 8;
   double vx = 0.0, vy = 0.0, vz = 0.0;
-  if (t.i < n - 1) { double a = fx[q], b = fx[q + 1]; vx = 2.0 * a * b / (a + b); }
-  if (t.j < n - 1) { double a = fy[q], b = fy[q + gf.sy]; vy = 2.0 * a * b / (a + b); }
-  if (DIM == 3 && t.k < n - 1) { double a = fz[q], b = fz[q + gf.sz]; vz = 2.0 * a * b / (a + b); }
+  if (t.i < n - 1) vx = coarse_face<DIM>(fx, f64, gf, 0, t.i, t.j, t.k, n);
+  if (t.j < n - 1) vy = coarse_face<DIM>(fy, f64, gf, 1, t.i, t.j, t.k, n);
+  if (DIM == 3 && t.k < n - 1) vz = coarse_face<DIM>(fz, f64, gf, 2, t.i, t.j, t.k, n);
   cx[t.p] = (Cc)vx;
   cy[t.p] = (Cc)vy;
   if (DIM == 3) cz[t.p] = (Cc)vz;

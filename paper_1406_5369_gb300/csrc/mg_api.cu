@@ -471,7 +471,8 @@ mg_status run(mg_ctx *c, int kind) {
       return MG_OK;
     }
   }
-  // Capture on the private stream, ordered after the user stream.
+  // Capture on the private stream (created on first use), ordered after the user stream.
+  if (!c->cap) CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
   cudaEvent_t ev;
   CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
   CK(cudaEventRecord(ev, c->stream));
@@ -514,6 +515,7 @@ mg_status run(mg_ctx *c, int kind) {
 }
 
 mg_status read_norm(mg_ctx *c, double *out) {
+  if (!c->host_norm) CK(cudaMallocHost((void **)&c->host_norm, 4 * sizeof(double)));
   CK(cudaMemcpyAsync(c->host_norm, c->norm_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   if (c->timing) timing_harvest(c);
@@ -601,8 +603,6 @@ mg_status mg_create(int dim, int n, const mg_const_stencil *stencil, const doubl
       goto bad;                                                                    \
     }                                                                              \
   } while (0)
-  CKC(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
-  CKC(cudaMallocHost((void **)&c->host_norm, 4 * sizeof(double)));
   CKC(cudaMemsetAsync(arena, 0, need, c->stream));
   if (c->variable) {
     // Node coefficients -> FP64 staging with the finest FP64 layout -> faces.

@@ -172,3 +172,70 @@ def serving_requests(count: int, seed: int, rate_per_s: float = 2000.0,
         out.append({"id": r, "t": t, "dim": dim, "n": (1 << m) + 1, "tol": tol,
                     "seed": (seed ^ (r + 1)) & 0xFFFFFFFF})
     return out
+
+
+# ---------------------------------------------------------------- torch (device) generation
+# The same counter-based SplitMix64 in torch int64 arithmetic, so that large
+# inputs can be drawn where they are used (e.g. on the GPU) with bit-identical
+# values to the numpy functions above. int64 products wrap modulo 2^64; right
+# shifts are made logical by masking off the copied sign bits.
+
+def _t_const(x):
+    return x - (1 << 64) if x >= (1 << 63) else x
+
+
+_T_GAMMA = _t_const(0x9E3779B97F4A7C15)
+_T_M1 = _t_const(0xBF58476D1CE4E5B9)
+_T_M2 = _t_const(0x94D049BB133111EB)
+
+
+def _t_shr(z, k):
+    return (z >> k) & ((1 << (64 - k)) - 1)
+
+
+def torch_splitmix64(seed: int, count: int, start: int = 0, device="cpu"):
+    import torch
+    idx = torch.arange(start + 1, start + count + 1, dtype=torch.int64, device=device)
+    z = idx * _T_GAMMA + _t_const(seed & 0xFFFFFFFFFFFFFFFF)
+    z = (z ^ _t_shr(z, 30)) * _T_M1
+    z = (z ^ _t_shr(z, 27)) * _T_M2
+    return z ^ _t_shr(z, 31)
+
+
+def torch_uniform01(seed: int, count: int, start: int = 0, device="cpu"):
+    import torch
+    z = torch_splitmix64(seed, count, start, device)
+    return _t_shr(z, 11).to(torch.float64) * (2.0 ** -53)
+
+
+def torch_uniform(seed: int, shape, lo: float = -1.0, hi: float = 1.0, device="cpu"):
+    count = 1
+    for s in shape:
+        count *= s
+    out = lo + (hi - lo) * torch_uniform01(seed, count, 0, device)
+    return out.reshape(tuple(shape))
+
+
+def _t_zero_boundary(a):
+    for ax in range(a.dim()):
+        a.select(ax, 0).zero_()
+        a.select(ax, a.shape[ax] - 1).zero_()
+    return a
+
+
+def torch_uniform_rhs(dim: int, n: int, seed: int, lo: float = -1.0, hi: float = 1.0, device="cpu"):
+    """Same values as uniform_rhs, drawn with torch on `device`."""
+    check_size(dim, n)
+    return _t_zero_boundary(torch_uniform(seed, (n,) * dim, lo, hi, device)).contiguous()
+
+
+def torch_lognormal_k(dim: int, n: int, seed: int, mu: float = 0.0, sigma: float = 1.0, device="cpu"):
+    """k = exp(mu + sigma z), z by Box-Muller on the uniform pair (2i, 2i+1), as
+    lognormal_k; the uniforms are bit-identical, the transcendental functions
+    are the device's (equal to numpy's to a few ulps)."""
+    import torch
+    check_size(dim, n)
+    count = n ** dim
+    u = torch_uniform01(seed, 2 * count, 0, device)
+    z = torch.sqrt(-2.0 * torch.log1p(-u[0::2])) * torch.cos(2.0 * math.pi * u[1::2])
+    return torch.exp(mu + sigma * z).reshape((n,) * dim).contiguous()

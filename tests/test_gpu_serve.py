@@ -1,0 +1,55 @@
+"""Continuous-batching server: admission under a memory budget, requests that
+arrive while others run join at the next step, every result reaches its
+tolerance (the oracle recomputes the residual) and is bit-for-bit the same
+as the request served alone."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def requests():
+    reqs = []
+    spec = [(2, 65, 1e-6), (3, 17, 1e-10), (2, 257, 1e-10), (2, 129, 1e-6), (3, 33, 1e-6),
+            (2, 65, 1e-10), (3, 17, 1e-6), (2, 513, 1e-10), (3, 65, 1e-10), (2, 129, 1e-10)]
+    for i, (dim, n, tol) in enumerate(spec):
+        reqs.append({"id": i, "t": 0.002 * i, "dim": dim, "n": n, "tol": tol, "seed": 0x5EED0005 ^ (i + 1)})
+    return reqs
+
+
+def test_server_mix_equals_alone_and_meets_tolerance():
+    need_gpu()
+    from paper_1406_5369_gb300.serve import Server
+    reqs = requests()
+    srv = Server(budget_bytes=4e9, max_active=16)
+    done, stats = srv.run(reqs, keep_solutions=True)
+    assert stats["completed"] == len(reqs) and stats["unfinished"] == 0
+    by_id = {d["id"]: d for d in done}
+    for r in reqs:
+        d = by_id[r["id"]]
+        assert d["relres"] <= r["tol"]
+        f = synth.uniform_rhs(r["dim"], r["n"], r["seed"])
+        res = oracle.norm(oracle.residual(d["u"], f)) / oracle.norm(f)
+        assert res <= 1.01 * r["tol"], (r, res)
+    for r in (reqs[2], reqs[8], reqs[6]):
+        alone = Server(budget_bytes=4e9, max_active=2)
+        d1, _ = alone.run([dict(r, t=0.0)], keep_solutions=True)
+        assert d1[0]["steps"] == by_id[r["id"]]["steps"]
+        assert np.array_equal(d1[0]["u"], by_id[r["id"]]["u"])
+
+
+def test_server_admission_respects_budget():
+    need_gpu()
+    from paper_1406_5369_gb300.serve import Server
+    reqs = [{"id": i, "t": 0.0, "dim": 2, "n": 257, "tol": 1e-6, "seed": 7 + i} for i in range(6)]
+    srv = Server(budget_bytes=1.0, max_active=8)
+    one = srv._bytes(2, 257)
+    srv.budget = 2.5 * one  # room for two hierarchies at a time
+    done, stats = srv.run(reqs)
+    assert stats["completed"] == 6
+    assert srv.peak_used <= srv.budget
+    assert stats["max_queue_depth"] >= 3

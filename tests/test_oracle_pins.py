@@ -494,3 +494,51 @@ def test_variable_coefficient_second_order():
         errs.append(np.abs(H.get_u() - u).max())
     ratios = [errs[i] / errs[i + 1] for i in range(2)]
     assert all(3.5 < r < 4.5 for r in ratios), (errs, ratios)
+
+
+def test_torch_generator_matches_numpy_bitwise():
+    torch = pytest.importorskip("torch")
+    for seed in (0, 1234567, 0x5EED0002):
+        a = synth.splitmix64(seed, 1000, 17)
+        b = synth.torch_splitmix64(seed, 1000, 17).numpy().astype(np.uint64)
+        assert np.array_equal(a, b)
+    for dim, n in ((2, 65), (3, 17)):
+        a = synth.uniform_rhs(dim, n, 99)
+        b = synth.torch_uniform_rhs(dim, n, 99).numpy()
+        assert np.array_equal(a, b)
+
+
+def test_coarse_faces_conserve_parallel_conductance():
+    # Stripes k = k(y) with flow along x: every x-face of a row carries that
+    # row's conductance, so the coarse faces (series along x = the value itself)
+    # averaged across rows with (1/4, 1/2, 1/4) must carry the same total
+    # conductance through any vertical line: sum_J K(J) * 2h = sum_j k(j) * h
+    # over the interior rows (odd fine rows are shared by two coarse rows).
+    nf = 33
+    rng = np.random.default_rng(11)
+    ky = np.exp(rng.standard_normal(nf))
+    k = np.tile(ky[:, None], (1, nf))
+    faces = oracle.node_faces(k)
+    cf = oracle.coarsen_faces(faces)
+    h = 1.0 / (nf - 1)
+    fine_rows = faces[0][1:nf - 1, 5]           # x-face values of the interior rows
+    coarse_rows = cf[0][1:(nf - 1) // 2, 2]     # interior coarse rows
+    lhs = coarse_rows.sum() * 2 * h
+    rhs = fine_rows.sum() * h - 0.5 * h * (fine_rows[0] + fine_rows[-1]) * 0.5  # rows 1, nf-2 enter once, at 1/4
+    rhs = h * (0.5 * fine_rows[1:-1].sum() + 0.25 * fine_rows[0] + 0.25 * fine_rows[-1]) * 2
+    assert lhs == pytest.approx(rhs, rel=1e-13)
+
+
+def test_lognormal_coefficient_cycle_converges():
+    # A lognormal(0,1) field (contrast ~1e4) on 513^2 on which coarse faces
+    # taken from the single collinear fine line stagnate near 1e-2: with the
+    # full-weighting average of series values the V(2,1) cycle reduces the
+    # residual by at least 0.45 per cycle (measured 0.12 rising to ~0.39).
+    n = 513
+    k = synth.lognormal_k(2, n, 0x5EED0004 ^ 1 ^ 0x10000)
+    f = synth.uniform_rhs(2, n, 0x5EED0004 ^ 1)
+    H = oracle.Hierarchy(2, n, knode=k)
+    H.set_rhs(f)
+    rho = H.solve(1e-8, 30)
+    assert rho[-1] <= 1e-8 and len(rho) - 1 <= 20
+    assert np.all(rho[1:] / rho[:-1] <= 0.45)
