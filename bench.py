@@ -106,6 +106,11 @@ def dist_env():
 
 # ------------------------------------------------------------------ GPU arm
 
+# DRAM bytes (read + write) of one k_dc2d<float,1,0> launch at 8193^2, from ncu
+# (profiles/k_dc2d_outer_8193.md); set to None whenever that kernel changes.
+K_DC2D_TRAFFIC = 2146.2e6
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -229,15 +234,25 @@ def run_gpu(args):
         a_outer = 6.0 * inner / (t_outer / c_outer * 1e-3) / 1e9
         lines.append({"kernel": "k_dc2d: FP64 outer step (update + residual -> FP32 defect + norm partials), 8193^2",
                       "bound": "alu", "achieved": a_outer, "peak": fp64_peak, "unit": "G FP64 instr/s",
-                      "frac": a_outer / fp64_peak, "traffic": None, "per_launch": "6 FP64 ops x 8191^2 interior nodes",
+                      "frac": a_outer / fp64_peak, "traffic": K_DC2D_TRAFFIC,
+                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_dc2d<float,1,0> launch "
+                                        "at 8193^2 (profiles/k_dc2d_outer_8193.md); algorithmic 32 B/node = 2148 MB",
+                      "per_launch": "6 FP64 ops x 8191^2 interior nodes",
                       "avg_launch_us": 1e3 * t_outer / c_outer, "launches": c_outer, "share": t_outer / (ms * args.steps),
                       "peak_source": "2 FP64 lanes/SM/clock (nominal 1.25 TFLOP/s at 2070 MHz, 152 SMs) x 152 SMs x median SM clock"})
     t_pre, c_pre = kinds["pre"]
     if c_pre:
-        a_pre = (2.25 * w) * nodes / (t_pre / c_pre * 1e-3) / 1e9
+        # The first inner cycle of an outer step starts from u = 0 and does not read u:
+        # 1 launch in inner_cycles reads f and writes u and the coarse f (2.25 words per
+        # node), the others also read u (3.25 words).
+        ic = best["inner_cycles"]
+        words_pre = 2.25 + (ic - 1) / ic
+        a_pre = (words_pre * w) * nodes / (t_pre / c_pre * 1e-3) / 1e9
         lines.append({"kernel": "k_pre2d<float,2,zero>: 2 RBGS sweeps + residual + full weighting, level 0",
                       "bound": "hbm", "achieved": a_pre, "peak": hbm_peak, "unit": "GB/s", "frac": a_pre / hbm_peak,
-                      "traffic": None, "per_launch": "read f, write u (1 word each) + coarse f (1/4 word) per node",
+                      "traffic": None,
+                      "per_launch": f"read f, write u (1 word each) + coarse f (1/4 word) per node, + read u in "
+                                    f"{ic - 1} of {ic} launches ({words_pre:.3f} words/node on average)",
                       "avg_launch_us": 1e3 * t_pre / c_pre, "launches": c_pre, "share": t_pre / (ms * args.steps)})
     t_post, c_post = kinds["post"]
     if c_post:

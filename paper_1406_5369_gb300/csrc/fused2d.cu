@@ -86,7 +86,7 @@ cudaError_t launch_pre(fz::Args2D a, int R_override, const Level &L, cudaStream_
 template <typename T, int NU>
 cudaError_t launch_post(fz::Args2D a, int R_override, const Level &L, cudaStream_t s) {
   constexpr int W = fz::Warps<T>::value;
-  constexpr size_t smem = (size_t)W * fz::kRing * 32 * (2 * fz::Lane<T>::bytes + 16);
+  constexpr size_t smem = (size_t)W * fz::kRing * 32 * (2 * fz::Lane<T>::bytes + 2 * sizeof(T));
   static bool ready = false;
   static int bps = 1;
   if (!ready) {

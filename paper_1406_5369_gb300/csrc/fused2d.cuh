@@ -10,12 +10,15 @@
 // Work decomposition: one warp owns a strip of 128 columns (lane l holds the
 // 4 consecutive columns x0 + 4l .. x0 + 4l + 3) and a chunk of R rows. The
 // outer 8 columns on each side are a halo recomputed redundantly, so each
-// warp writes 112 columns and needs no barrier. Rows stream in blocks of 8
-// through a 16-row ring in shared memory filled by cp.async, one commit
-// group per block, issued one block ahead (each lane copies, and later reads
-// back, only its own 16-byte pieces, so a lane's own wait_group is the only
-// synchronisation). The 8 rows of a block are processed by straight-line
-// code, which lets the compiler overlap consecutive rows. Half-sweep h of the stack runs
+// warp writes 112 columns and needs no barrier. Rows stream in groups of 4
+// through an 8-row ring in shared memory filled by cp.async, one commit
+// group per 4 rows, issued one group ahead (each lane copies, and later reads
+// back, only its own pieces, so a lane's own wait_group is the only
+// synchronisation); the small ring keeps 5 blocks of 4 warps resident per
+// SM. Rows are processed 8 at a time by straight-line code (the register
+// window), which lets the compiler overlap consecutive rows. Warps whose
+// rows and columns are all interior run a copy of that code without the
+// boundary predicates. Half-sweep h of the stack runs
 // on row t - h when row t arrives (red = i+j even first, as in the paper's
 // "order rb"), so every update sees exactly the neighbour values a
 // sequential red-then-black sweep would; the x-neighbours of a lane's edge
@@ -43,9 +46,14 @@ constexpr int kCols = 32 * kVec;         // columns per warp strip (loaded)
 constexpr int kHalo = 8;                 // halo columns on each side
 constexpr int kOut = kCols - 2 * kHalo;  // columns written per strip
 constexpr int kSlots = 8;                // row window in registers
-constexpr int kRing = 16;                // row ring in shared memory: two blocks of 8 rows
+constexpr int kGroup = 4;                // rows per cp.async commit group
+constexpr int kRing = 2 * kGroup;        // row ring in shared memory: two groups in flight
 // Warps per block: the shared-memory ring of FP64 rows is twice as large.
 template <typename T> struct Warps { static constexpr int value = sizeof(T) == 8 ? 2 : 4; };
+// Resident blocks asked of the register allocator: 5 blocks of 4 FP32 warps
+// (at most 96 registers per thread); FP64 kernels are bound by the FP64 pipe
+// and keep their natural register count.
+template <typename T> struct MinBlocks { static constexpr int value = sizeof(T) == 8 ? 1 : 5; };
 
 struct Args2D {
   const void *uin;  // level solution (ignored when starting from zero)
@@ -118,26 +126,38 @@ template <typename C> struct Coef {
 
 // Red-black half-sweep of colour `color` on row r held in uc, with rows r-1
 // (ua) and r+1 (ub). Columns c0 + q with (c0 + q + r) % 2 == color update.
-template <typename C>
+// CHECK = false is for warps whose rows and columns are all interior: no
+// boundary node can be touched, so the predicates are dropped.
+template <bool CHECK, typename C>
 __device__ __forceinline__ void half_sweep(C (&uc)[kVec], const C (&ua)[kVec], const C (&ub)[kVec],
                                            const C (&fr)[kVec], int r, int color, int c0, int n,
                                            const Coef<C> &k) {
-  bool rowok = r >= 1 && r <= n - 2;
+  bool rowok = !CHECK || (r >= 1 && r <= n - 2);
   int par = (color ^ r) & 1;  // c0 is even, so column parity is q's parity
   if (par == 0) {
     C left = shup(uc[3]);
     C n0 = k.alpha * fr[0] + k.bx * (left + uc[1]) + k.by * (ua[0] + ub[0]);
     C n2 = k.alpha * fr[2] + k.bx * (uc[1] + uc[3]) + k.by * (ua[2] + ub[2]);
     if (k.has_gamma) { n0 += k.gamma * uc[0]; n2 += k.gamma * uc[2]; }
-    if (rowok && c0 >= 1 && c0 <= n - 2) uc[0] = n0;
-    if (rowok && c0 + 2 >= 1 && c0 + 2 <= n - 2) uc[2] = n2;
+    if (!CHECK) {
+      uc[0] = n0;
+      uc[2] = n2;
+    } else {
+      if (rowok && c0 >= 1 && c0 <= n - 2) uc[0] = n0;
+      if (rowok && c0 + 2 >= 1 && c0 + 2 <= n - 2) uc[2] = n2;
+    }
   } else {
     C right = shdn(uc[0]);
     C n1 = k.alpha * fr[1] + k.bx * (uc[0] + uc[2]) + k.by * (ua[1] + ub[1]);
     C n3 = k.alpha * fr[3] + k.bx * (uc[2] + right) + k.by * (ua[3] + ub[3]);
     if (k.has_gamma) { n1 += k.gamma * uc[1]; n3 += k.gamma * uc[3]; }
-    if (rowok && c0 + 1 >= 1 && c0 + 1 <= n - 2) uc[1] = n1;
-    if (rowok && c0 + 3 >= 1 && c0 + 3 <= n - 2) uc[3] = n3;
+    if (!CHECK) {
+      uc[1] = n1;
+      uc[3] = n3;
+    } else {
+      if (rowok && c0 + 1 >= 1 && c0 + 1 <= n - 2) uc[1] = n1;
+      if (rowok && c0 + 3 >= 1 && c0 + 3 <= n - 2) uc[3] = n3;
+    }
   }
 }
 
@@ -145,12 +165,12 @@ __device__ __forceinline__ void half_sweep(C (&uc)[kVec], const C (&ua)[kVec], c
 // keeps the rounding error at the size of A u itself; FP32 inner cycles use
 // f - cd u + cx (uw + ue) + cy (us + un) (five operations), whose larger
 // rounding error the defect-correction outer loop absorbs.
-template <typename C>
+template <bool CHECK, typename C>
 __device__ __forceinline__ void residual_row(C (&rr)[kVec], const C (&uc)[kVec], const C (&ua)[kVec],
                                              const C (&ub)[kVec], const C (&fr)[kVec], int r, int c0, int n,
                                              const Coef<C> &k) {
   C left = shup(uc[3]), right = shdn(uc[0]);
-  bool rowok = r >= 1 && r <= n - 2;
+  bool rowok = !CHECK || (r >= 1 && r <= n - 2);
 #pragma unroll
   for (int q = 0; q < kVec; q++) {
     C u = uc[q];
@@ -164,14 +184,14 @@ __device__ __forceinline__ void residual_row(C (&rr)[kVec], const C (&uc)[kVec],
       res = k.cy * (ua[q] + ub[q]) + (k.cx * (uw + ue) + (fr[q] - k.cd * u));
     }
     int c = c0 + q;
-    rr[q] = (rowok && c >= 1 && c <= n - 2) ? res : (C)0;
+    rr[q] = (!CHECK || (rowok && c >= 1 && c <= n - 2)) ? res : (C)0;
   }
 }
 
 // ------------------------------------------------------------------------
 // Pre-smoothing + residual + restriction.
 template <typename T, int NU, bool ZERO>
-__global__ void __launch_bounds__(32 * Warps<T>::value) k_pre2d(Args2D a) {
+__global__ void __launch_bounds__(32 * Warps<T>::value, MinBlocks<T>::value) k_pre2d(Args2D a) {
   typedef typename CT<T>::type C;
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -203,11 +223,11 @@ __global__ void __launch_bounds__(32 * Warps<T>::value) k_pre2d(Args2D a) {
 #pragma unroll
     for (int q = 0; q < kVec; q++) { U[i][q] = 0; F[i][q] = 0; Rr[i][q] = 0; }
 
-  // Stages the 8 rows starting at tb (one commit group).
-  auto issue_block = [&](int tb) {
+  // Stages the kGroup rows starting at tg (one commit group).
+  auto issue_group = [&](int tg) {
 #pragma unroll
-    for (int K = 0; K < kSlots; K++) {
-      int row = tb + K;
+    for (int K = 0; K < kGroup; K++) {
+      int row = tg + K;
       int slot = row & (kRing - 1);
       bool ok = col_ok && row >= 0 && row < n && row <= tend;
       long long off = (long long)row * a.pitch + c0;
@@ -217,27 +237,39 @@ __global__ void __launch_bounds__(32 * Warps<T>::value) k_pre2d(Args2D a) {
     cp_async_commit();
   };
 
-  issue_block(tstart);
+  // Rows t of the loop run up to the end of the last block of 8; interior
+  // warps (every touched row and column inside the domain) skip predicates.
+  const int tlast = tstart + ((tend - tstart) / kSlots + 1) * kSlots - 1;
+  const bool interior_warp = x0 >= 1 && x0 + kCols - 1 <= n - 2 && tstart - 2 * NU - 2 >= 1 && tlast <= n - 2;
+
+  // Row t lives in ring slot t % kRing. Group t + kGroup is issued when row
+  // t is about to be read: its slots held rows t - kGroup .. t - 1, which are
+  // already in registers.
+  auto body = [&](auto chk) {
+  constexpr bool CHECK = decltype(chk)::value;
+  issue_group(tstart);
   for (int tb = tstart; tb <= tend; tb += kSlots) {
-    issue_block(tb + kSlots);
-    cp_async_wait<1>();  // block tb has landed; block tb + 8 may be in flight
-    const int ring = tb & (kRing - 1);  // 0 or 8
     static_for<0, kSlots>([&](auto kc) {
       constexpr int K = decltype(kc)::value;
       const int t = tb + K;
+      if constexpr (K % kGroup == 0) {
+        issue_group(t + kGroup);
+        cp_async_wait<1>();  // group t has landed; group t + kGroup may be in flight
+      }
       {
+        constexpr int slot = K % kRing;  // tb is a multiple of kRing
         if (!ZERO) {
-          load_lane<T, C>(su + ((ring + K) * 32 + lane) * LB, U[K]);
+          load_lane<T, C>(su + (slot * 32 + lane) * LB, U[K]);
         } else {
 #pragma unroll
           for (int q = 0; q < kVec; q++) U[K][q] = (C)0;
         }
-        load_lane<T, C>(sf + ((ring + K) * 32 + lane) * LB, F[K]);
+        load_lane<T, C>(sf + (slot * 32 + lane) * LB, F[K]);
         // half-sweeps h = 1 .. 2 NU on rows t - h (odd h red, even h black)
 #pragma unroll
         for (int h = 1; h <= 2 * NU; h++) {
           const int sc = (K - h) & (kSlots - 1), sa = (K - h - 1) & (kSlots - 1), sb = (K - h + 1) & (kSlots - 1);
-          half_sweep<C>(U[sc], U[sa], U[sb], F[sc], t - h, (h - 1) & 1, c0, n, k);
+          half_sweep<CHECK, C>(U[sc], U[sa], U[sb], F[sc], t - h, (h - 1) & 1, c0, n, k);
         }
         // final u of row t - 2 NU
         {
@@ -250,9 +282,10 @@ __global__ void __launch_bounds__(32 * Warps<T>::value) k_pre2d(Args2D a) {
           const int r = t - 2 * NU - 1;
           const int sc = (K - 2 * NU - 1) & (kSlots - 1), sa = (K - 2 * NU - 2) & (kSlots - 1),
                     sb = (K - 2 * NU) & (kSlots - 1);
-          residual_row<C>(Rr[sc], U[sc], U[sa], U[sb], F[sc], r, c0, n, k);
-          // restriction once the row below the coarse row is ready (r = 2I + 1)
-          if (r & 1) {
+          residual_row<CHECK, C>(Rr[sc], U[sc], U[sa], U[sb], F[sc], r, c0, n, k);
+          // restriction once the row below the coarse row is ready (r = 2I + 1);
+          // tb is a multiple of 8, so r's parity is known at compile time
+          if constexpr (((K - 2 * NU - 1) & 1) != 0) {
             const int I = (r - 1) >> 1;
             const int sA = (K - 2 * NU - 3) & (kSlots - 1), sB = (K - 2 * NU - 2) & (kSlots - 1);
             C lA = shup(Rr[sA][3]), lB = shup(Rr[sB][3]), lC = shup(Rr[sc][3]);
@@ -272,13 +305,16 @@ __global__ void __launch_bounds__(32 * Warps<T>::value) k_pre2d(Args2D a) {
       }
     });
   }
+  };
+  if (interior_warp) body(std::false_type{});
+  else body(std::true_type{});
   cp_async_wait<0>();
 }
 
 // ------------------------------------------------------------------------
 // Interpolation + correction + post-smoothing.
 template <typename T, int NU>
-__global__ void __launch_bounds__(32 * Warps<T>::value) k_post2d(Args2D a) {
+__global__ void __launch_bounds__(32 * Warps<T>::value, MinBlocks<T>::value) k_post2d(Args2D a) {
   typedef typename CT<T>::type C;
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -301,9 +337,9 @@ __global__ void __launch_bounds__(32 * Warps<T>::value) k_post2d(Args2D a) {
   T *uout = (T *)a.uout;
   constexpr int LB = Lane<T>::bytes;
   constexpr int CB = 2 * (int)sizeof(T);  // two coarse values per lane
-  unsigned char *su = smem + (size_t)wib * kRing * 32 * (2 * LB + 16);
+  unsigned char *su = smem + (size_t)wib * kRing * 32 * (2 * LB + CB);
   unsigned char *sf = su + kRing * 32 * LB;
-  unsigned char *se = sf + kRing * 32 * LB;  // 16 bytes per lane and slot
+  unsigned char *se = sf + kRing * 32 * LB;  // CB bytes per lane and slot
   Coef<C> k;
   k.alpha = (C)a.alpha; k.bx = (C)a.betax; k.by = (C)a.betay; k.gamma = (C)a.gamma;
   k.cx = (C)a.cx; k.cy = (C)a.cy; k.cd = (C)(2.0 * (a.cx + a.cy)); k.has_gamma = a.gamma != 0.0;
@@ -320,10 +356,10 @@ __global__ void __launch_bounds__(32 * Warps<T>::value) k_post2d(Args2D a) {
 
   // With fine row `row` also stage coarse row I = (row + 1) / 2 when row is
   // odd, and coarse row 0 with fine row 0.
-  auto issue_block = [&](int tb) {
+  auto issue_group = [&](int tg) {
 #pragma unroll
-    for (int K = 0; K < kSlots; K++) {
-      int row = tb + K;
+    for (int K = 0; K < kGroup; K++) {
+      int row = tg + K;
       int slot = row & (kRing - 1);
       bool ok = col_ok && row >= 0 && row < n && row <= tend;
       long long off = (long long)row * a.pitch + c0;
@@ -332,14 +368,15 @@ __global__ void __launch_bounds__(32 * Warps<T>::value) k_post2d(Args2D a) {
       int I = (row & 1) ? (row + 1) >> 1 : (row == 0 ? 0 : -1);
       bool cok = ccol_ok && row >= 0 && row <= tend && I >= 0 && I < a.nc;
       const T *csrc = cok ? ec + (long long)I * a.pitchc + J0 : ec;
-      unsigned char *cdst = se + (slot * 32 + lane) * 16;
+      unsigned char *cdst = se + (slot * 32 + lane) * CB;
       if (CB == 16) cp_async16(cdst, csrc, cok);
       else cp_async8(cdst, csrc, cok);
     }
     cp_async_commit();
   };
 
-  issue_block(tstart);
+  const int tlast = tstart + ((tend - tstart) / kSlots + 1) * kSlots - 1;
+  const bool interior_warp = x0 >= 1 && x0 + kCols - 1 <= n - 2 && tstart - 2 * NU >= 1 && tlast <= n - 2;
 
   // Coarse row tstart/2 (even index) precedes the window when the chunk starts inside the grid.
   if (tstart > 0) {
@@ -350,19 +387,24 @@ __global__ void __launch_bounds__(32 * Warps<T>::value) k_post2d(Args2D a) {
     }
   }
 
+  auto body = [&](auto chk) {
+  constexpr bool CHECK = decltype(chk)::value;
+  issue_group(tstart);
   for (int tb = tstart; tb <= tend; tb += kSlots) {
-    issue_block(tb + kSlots);
-    cp_async_wait<1>();
-    const int ring = tb & (kRing - 1);
     static_for<0, kSlots>([&](auto kc) {
       constexpr int K = decltype(kc)::value;
       const int t = tb + K;
+      if constexpr (K % kGroup == 0) {
+        issue_group(t + kGroup);
+        cp_async_wait<1>();
+      }
       {
-        load_lane<T, C>(su + ((ring + K) * 32 + lane) * LB, U[K]);
-        load_lane<T, C>(sf + ((ring + K) * 32 + lane) * LB, F[K]);
-        if ((K & 1) || t == 0) {
+        constexpr int slot = K % kRing;
+        load_lane<T, C>(su + (slot * 32 + lane) * LB, U[K]);
+        load_lane<T, C>(sf + (slot * 32 + lane) * LB, F[K]);
+        if ((K & 1) || (CHECK && t == 0)) {
           constexpr int PI = ((K + 1) >> 1) & 1;  // parity of I = (t + 1) / 2
-          const unsigned char *cs = se + ((ring + K) * 32 + lane) * 16;
+          const unsigned char *cs = se + (slot * 32 + lane) * CB;
           if (sizeof(T) == 4) {
             float2 v = *(const float2 *)cs;
             E[PI][0] = (C)v.x; E[PI][1] = (C)v.y;
@@ -384,17 +426,17 @@ __global__ void __launch_bounds__(32 * Warps<T>::value) k_post2d(Args2D a) {
           }
           C e2 = shdn(e0);
           C v[kVec] = {e0, (C)0.5 * (e0 + e1), e1, (C)0.5 * (e1 + e2)};
-          bool rowok = t >= 1 && t <= n - 2;
+          bool rowok = !CHECK || (t >= 1 && t <= n - 2);
 #pragma unroll
           for (int q = 0; q < kVec; q++) {
             int c = c0 + q;
-            if (rowok && c >= 1 && c <= n - 2) U[K][q] += v[q];
+            if (!CHECK || (rowok && c >= 1 && c <= n - 2)) U[K][q] += v[q];
           }
         }
 #pragma unroll
         for (int h = 1; h <= 2 * NU; h++) {
           const int sc = (K - h) & (kSlots - 1), sa = (K - h - 1) & (kSlots - 1), sb = (K - h + 1) & (kSlots - 1);
-          half_sweep<C>(U[sc], U[sa], U[sb], F[sc], t - h, (h - 1) & 1, c0, n, k);
+          half_sweep<CHECK, C>(U[sc], U[sa], U[sb], F[sc], t - h, (h - 1) & 1, c0, n, k);
         }
         {
           const int r = t - 2 * NU;
@@ -404,6 +446,9 @@ __global__ void __launch_bounds__(32 * Warps<T>::value) k_post2d(Args2D a) {
       }
     });
   }
+  };
+  if (interior_warp) body(std::false_type{});
+  else body(std::true_type{});
   cp_async_wait<0>();
 }
 
