@@ -354,6 +354,21 @@ mg_status vcycle_rec(mg_ctx *c, int l, bool zero, cudaStream_t s) {
   return op_smooth(c, l, c->opt.nu2, s, MG_KERNEL_POSTSMOOTH);
 }
 
+// Streaming finest-level kernels of either dimension (constant stencil).
+bool outer_fast(const Level &O, const Level &I) {
+  return O.dim == 2 ? mg::d2::outer_ok(O, I) : mg::d3::outer_ok(O, I);
+}
+cudaError_t outer_step(const Level &O, const double *uin, double *uout, const Level &I, const void *e, void *d,
+                       double *partials, int *nparts, const float *scale, bool update, bool acc64, cudaStream_t s) {
+  return O.dim == 2 ? mg::d2::dc_step(O, uin, uout, I, e, d, partials, nparts, scale, update, acc64, s)
+                    : mg::d3::dc_step(O, uin, uout, I, e, d, partials, nparts, scale, update, acc64, s);
+}
+bool norm_fast(const Level &L) { return L.dim == 2 ? mg::d2::norm_ok(L) : mg::d3::norm_ok(L); }
+cudaError_t norm_fast_partials(const Level &L, const void *u, const void *f, double *partials, int *nparts,
+                               cudaStream_t s) {
+  return L.dim == 2 ? mg::d2::norm_stream(L, u, f, partials, nparts, s) : mg::d3::norm_stream(L, u, f, partials, nparts, s);
+}
+
 // Residual norm of level l into norm_out[0]. In defect-correction contexts
 // level 0 is the outer FP64 problem; that pass also leaves the defect in the
 // inner level 0's right-hand side and resets the norm scale.
@@ -361,8 +376,8 @@ mg_status op_norm(mg_ctx *c, int l, cudaStream_t s) {
   int np = 0;
   if (c->dc && l == 0) {
     Level &O = c->outer, &I = c->lv[0];
-    if (mg::d2::outer_ok(O, I)) {
-      TLAUNCH(c, MG_KERNEL_OUTER, 0, s, mg::d2::dc_step(O, (const double *)O.u[O.cur], nullptr, I, nullptr, I.f,
+    if (outer_fast(O, I)) {
+      TLAUNCH(c, MG_KERNEL_OUTER, 0, s, outer_step(O, (const double *)O.u[O.cur], nullptr, I, nullptr, I.f,
                                                         c->partials, &np, c->dc_scale, false, true, s));
       TLAUNCH(c, MG_KERNEL_NORM, 0, s,
               mg::norm_finalize_ex(c->partials, np, c->norm_out, nullptr, c->dc_scale, interior_count(O), s));
@@ -371,8 +386,8 @@ mg_status op_norm(mg_ctx *c, int l, cudaStream_t s) {
     TLAUNCH(c, MG_KERNEL_OUTER, 0, s, DISPATCH(O, dc_residual, O, O.u[O.cur], O.f, I, I.f, c->partials, mg::kNormBlocks, s));
   } else {
     Level &L = c->lv[l];
-    if (mg::d2::norm_ok(L)) {
-      TLAUNCH(c, MG_KERNEL_NORM, l, s, mg::d2::norm_stream(L, L.u[L.cur], L.f, c->partials, &np, s));
+    if (norm_fast(L)) {
+      TLAUNCH(c, MG_KERNEL_NORM, l, s, norm_fast_partials(L, L.u[L.cur], L.f, c->partials, &np, s));
       TLAUNCH(c, MG_KERNEL_NORM, l, s,
               mg::norm_finalize_ex(c->partials, np, c->norm_out, nullptr, nullptr, interior_count(L), s));
       return MG_OK;
@@ -392,10 +407,10 @@ mg_status dc_inner_and_update(mg_ctx *c, bool norm, cudaStream_t s) {
   for (int k = 1; k < (c->opt.inner_cycles > 1 ? c->opt.inner_cycles : 1); k++)
     if ((st = vcycle_rec(c, 0, false, s))) return st;
   Level &O = c->outer, &I = c->lv[0];
-  if (mg::d2::outer_ok(O, I)) {
+  if (outer_fast(O, I)) {
     int np = 0;
     TLAUNCH(c, MG_KERNEL_OUTER, 0, s,
-            mg::d2::dc_step(O, (const double *)O.u[O.cur], (double *)O.u[O.cur ^ 1], I, I.u[I.cur],
+            outer_step(O, (const double *)O.u[O.cur], (double *)O.u[O.cur ^ 1], I, I.u[I.cur],
                             norm ? I.f : nullptr, c->partials, &np, c->dc_scale, true, false, s));
     O.cur ^= 1;
     if (norm)

@@ -89,6 +89,25 @@ bool norm_ok(const Level &L);
 cudaError_t norm_stream(const Level &L, const void *u, const void *f, double *partials, int *nparts, cudaStream_t s);
 }  // namespace d2
 
+// Plane-marching 3D kernels for constant-stencil levels (stencil3d.cuh):
+// z_ok says whether a level takes them; transfer_ok whether a fine/coarse
+// pair does (same storage type). dc_step, norm_ok and norm_stream have the
+// meaning of their 2D namespaces' counterparts; partial sums are per block.
+namespace d3 {
+bool z_ok(const Level &L);
+bool transfer_ok(const Level &F, const Level &C);
+cudaError_t z_sweep(const Level &L, const void *uin, void *uout, const void *f, int color, double omega,
+                    cudaStream_t s);
+cudaError_t z_residual(const Level &L, const void *u, const void *f, void *r, cudaStream_t s);
+cudaError_t z_restrict(const Level &F, const void *rf, const Level &C, void *fc, cudaStream_t s);
+cudaError_t z_prolong(const Level &C, const void *ec, const Level &F, void *uf, cudaStream_t s);
+bool outer_ok(const Level &O, const Level &I);
+cudaError_t dc_step(const Level &O, const double *uin, double *uout, const Level &I, const void *e, void *d,
+                    double *partials, int *nparts, const float *scale, bool update, bool acc64, cudaStream_t s);
+bool norm_ok(const Level &L);
+cudaError_t norm_stream(const Level &L, const void *u, const void *f, double *partials, int *nparts, cudaStream_t s);
+}  // namespace d3
+
 // Deterministic sum of nb partials (any nb): out[0] = sqrt(sum) / *scale_in
 // (scale_in may be NULL), out[1] = sum; scale_out (may be NULL) receives the
 // power of two for the next scaled pass.

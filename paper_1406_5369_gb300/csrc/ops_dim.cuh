@@ -19,6 +19,7 @@ static dim3 node_grid(int n, int bx) {
   }
 
 cudaError_t rbgs_half(const Level &L, void *u, const void *f, int color, double omega, cudaStream_t s) {
+  if (kDim == 3 && d3::z_ok(L)) return d3::z_sweep(L, u, u, f, color, omega, s);
   dim3 b(128), gr = node_grid(L.n, 128);
   bool var = L.kf[0] != nullptr;
   MG_DISPATCH_T(L.dtype, {
@@ -30,6 +31,7 @@ cudaError_t rbgs_half(const Level &L, void *u, const void *f, int color, double 
 }
 
 cudaError_t jacobi(const Level &L, const void *uin, void *uout, const void *f, double omega, cudaStream_t s) {
+  if (kDim == 3 && d3::z_ok(L)) return d3::z_sweep(L, uin, uout, f, -1, omega, s);
   dim3 b(128), gr = node_grid(L.n, 128);
   bool var = L.kf[0] != nullptr;
   MG_DISPATCH_T(L.dtype, {
@@ -41,6 +43,7 @@ cudaError_t jacobi(const Level &L, const void *uin, void *uout, const void *f, d
 }
 
 cudaError_t residual(const Level &L, const void *u, const void *f, void *r, cudaStream_t s) {
+  if (kDim == 3 && d3::z_ok(L)) return d3::z_residual(L, u, f, r, s);
   dim3 b(128), gr = node_grid(L.n, 128);
   bool var = L.kf[0] != nullptr;
   MG_DISPATCH_T(L.dtype, {
@@ -52,6 +55,7 @@ cudaError_t residual(const Level &L, const void *u, const void *f, void *r, cuda
 }
 
 cudaError_t restrict_fw(const Level &F, const void *rf, const Level &C, void *fc, cudaStream_t s) {
+  if (kDim == 3 && d3::transfer_ok(F, C)) return d3::z_restrict(F, rf, C, fc, s);
   dim3 b(128), gr = node_grid(C.n, 128);
   switch (F.dtype) {
     case F64:
@@ -70,6 +74,7 @@ cudaError_t restrict_fw(const Level &F, const void *rf, const Level &C, void *fc
 }
 
 cudaError_t prolong(const Level &C, const void *ec, const Level &F, void *uf, cudaStream_t s) {
+  if (kDim == 3 && d3::transfer_ok(F, C)) return d3::z_prolong(C, ec, F, uf, s);
   dim3 b(128), gr = node_grid(F.n, 128);
   switch (F.dtype) {
     case F64:

@@ -1,0 +1,504 @@
+// Plane-marching 3D kernels for the constant 7-point stencil (Algorithm 1's
+// level operators on 3D grids, Sec. 2.2-2.4):
+//
+//   k3_stencil<T, kSweep>: one omega-Jacobi sweep (u_out from u_in) or one
+//                          red-black half-sweep (in place, one colour);
+//   k3_stencil<T, kResid>: residual r = f - A u;
+//   k3_stencil<T, kNorm> : per-block partial sums of (f - A u)^2;
+//   k3_restrict<T>       : full weighting r_h -> f_H;
+//   k3_prolong<T>        : trilinear interpolation and correction u_h += P e_H;
+//   k3_dc<Ti, ...>       : the FP64 outer step of defect correction (update
+//                          u_out = u_in + e, residual of the updated u written
+//                          as the inner defect, partial sums of its square).
+//
+// Decomposition of the marching kernels: a block owns kTY = 8 consecutive
+// interior rows y0 .. y0+7 of one x-tile of 32 V columns (V = 16 bytes / element
+// size: 8 BF16, 4 FP32 or 2 FP64 values per lane, one 16-byte vector) and a
+// chunk of planes z0 .. z1-1, and walks the chunk plane by plane. Each plane
+// of the tile, with one halo row above and below and one 16-byte halo chunk
+// left and right, is staged by cp.async into a ring of kRingZ plane slots in
+// shared memory, kAhead planes ahead of the plane being computed; one
+// __syncthreads per plane publishes the staged plane and frees the oldest
+// slot. A warp keeps its own row at planes z-1, z, z+1 in registers and reads
+// rows y-1, y+1 and the x-halo values of plane z from the staged tile; the
+// x-neighbours inside the segment come from warp shuffles. Arithmetic runs in
+// float for BF16/FP32 storage and in double for FP64 storage.
+#pragma once
+
+#include "fused2d.cuh"
+#include "outer2d.cuh"
+
+namespace mg {
+namespace z3 {
+
+using fz::cp_async16;
+using fz::cp_async_commit;
+using fz::cp_async_wait;
+using fz::shdn;
+using fz::shup;
+
+constexpr int kTY = 8;                     // rows (warps) per block
+constexpr int kAhead = 3;                  // planes staged ahead of the computed plane
+constexpr int kRingZ = kAhead + 3;         // plane slots: z-1, z, z+1 and the planes in flight
+constexpr int kUChunks = 34;               // 16-byte chunks per staged u row: halo, 32 lanes, halo
+constexpr int kURowB = kUChunks * 16;
+constexpr int kFRowB = 32 * 16;
+constexpr int kSlotB = (kTY + 2) * kURowB + kTY * kFRowB;
+
+template <typename T> struct VW { static constexpr int V = 16 / (int)sizeof(T); };
+
+// 16-byte vectors <-> compute type.
+__device__ __forceinline__ void vld(const double *p, double (&v)[2]) {
+  double2 a = *(const double2 *)p;
+  v[0] = a.x; v[1] = a.y;
+}
+__device__ __forceinline__ void vld(const float *p, float (&v)[4]) {
+  float4 a = *(const float4 *)p;
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+// BF16 -> FP32 is exact: the 16 bits are the top half of the float.
+__device__ __forceinline__ void vld(const bf16 *p, float (&v)[8]) {
+  uint4 a = *(const uint4 *)p;
+  unsigned w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    v[2 * k] = __uint_as_float(w[k] << 16);
+    v[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+  }
+}
+__device__ __forceinline__ void vst(double *p, const double (&v)[2]) { *(double2 *)p = make_double2(v[0], v[1]); }
+__device__ __forceinline__ void vst(float *p, const float (&v)[4]) { *(float4 *)p = make_float4(v[0], v[1], v[2], v[3]); }
+__device__ __forceinline__ void vst(bf16 *p, const float (&v)[8]) {
+  unsigned w[4];
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+    w[k] = *(unsigned *)&b;
+  }
+  *(uint4 *)p = make_uint4(w[0], w[1], w[2], w[3]);
+}
+template <typename T> __device__ __forceinline__ typename CT<T>::type sld(const unsigned char *p) {
+  return (typename CT<T>::type)ld((const T *)p);
+}
+
+struct Args3 {
+  const void *u;      // solution read (in place for a red-black half-sweep)
+  void *out;          // sweep: solution written; residual: r
+  const void *f;      // right-hand side
+  double *partials;   // norm: one partial sum per block
+  int n, pitch;       // nodes per dimension, row stride (elements)
+  long long plane;    // plane stride (elements)
+  int ntx, nty, zc;   // x-tiles, y-tiles of kTY rows, planes per chunk
+  int color;          // sweep: red-black colour to update, -1 = Jacobi
+  double alpha, bx, by, bz, gamma;  // sweep: u' = gamma u + alpha f + bx (uw+ue) + by (us+un) + bz (ud+uu)
+  double cd, cx, cy, cz;            // residual: r = f - cd u + cx (uw+ue) + cy (us+un) + cz (ud+uu)
+};
+
+enum { kSweep = 0, kResid = 1, kNorm = 2 };
+
+// Stages plane p of the block's tile (u rows y0-1 .. y0+kTY with halo chunks,
+// f rows y0 .. y0+kTY-1) into `slot`; invalid pieces are zero-filled. One
+// commit group per call.
+template <typename T>
+__device__ __forceinline__ void stage_plane(unsigned char *slot, const T *u, const T *f, int p, int y0, int x0,
+                                            int n, int pitch, long long P, bool with_f) {
+  constexpr int V = VW<T>::V;
+  constexpr int NU = (kTY + 2) * kUChunks, NF = kTY * 32;
+  const bool pok = p >= 0 && p < n;
+  for (int i = threadIdx.x; i < NU + NF; i += blockDim.x) {
+    if (i < NU) {
+      const int rr = i / kUChunks, ch = i - rr * kUChunks;
+      const int y = y0 - 1 + rr, x = x0 + (ch - 1) * V;
+      const bool ok = pok && y >= 0 && y < n && x >= 0 && x + V <= pitch;
+      const T *src = ok ? u + (long long)p * P + (long long)y * pitch + x : u;
+      cp_async16(slot + rr * kURowB + ch * 16, src, ok);
+    } else if (with_f) {
+      const int j = i - NU, rr = j >> 5, ch = j & 31;
+      const int y = y0 + rr, x = x0 + ch * V;
+      const bool ok = pok && y < n && x + V <= pitch;
+      const T *src = ok ? f + (long long)p * P + (long long)y * pitch + x : f;
+      cp_async16(slot + (kTY + 2) * kURowB + rr * kFRowB + ch * 16, src, ok);
+    }
+  }
+  cp_async_commit();
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(32 * kTY, 3) k3_stencil(Args3 a) {
+  typedef typename CT<T>::type C;
+  constexpr int V = VW<T>::V;
+  constexpr int TX = 32 * V;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double wsum[kTY];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int tx = blockIdx.x % a.ntx, ty = blockIdx.x / a.ntx;
+  const int n = a.n, pitch = a.pitch;
+  const long long P = a.plane;
+  const int y0 = 1 + ty * kTY, y = y0 + w;
+  const int x0 = tx * TX, cl = x0 + V * lane;
+  const int z0 = 1 + blockIdx.y * a.zc, z1 = min(z0 + a.zc, n - 1);
+  const T *u = (const T *)a.u;
+  const T *f = (const T *)a.f;
+  const bool wact = y <= n - 2;  // warp-uniform
+  const C alpha = (C)a.alpha, bx = (C)a.bx, by = (C)a.by, bz = (C)a.bz, gamma = (C)a.gamma;
+  const C cd = (C)a.cd, cx = (C)a.cx, cy = (C)a.cy, cz = (C)a.cz;
+  const bool has_gamma = a.gamma != 0.0;
+  double acc = 0.0;
+
+  // Row offsets inside a slot: own row w + 1, rows w and w + 2 above/below.
+  auto urow = [&](int p, int rr) { return smem + (p % kRingZ) * kSlotB + rr * kURowB; };
+  auto frow = [&](int p) { return smem + (p % kRingZ) * kSlotB + (kTY + 2) * kURowB + w * kFRowB; };
+
+  // Planes z0 - 1 .. z0 + kAhead up front; step z then refills with z + kAhead + 1.
+  for (int k = 0; k <= kAhead + 1; k++) {
+    const int p = z0 - 1 + k;
+    stage_plane<T>(urow(p, 0), u, f, p <= z1 ? p : -1, y0, x0, n, pitch, P, true);
+  }
+
+  C um[V], uc[V], up[V];
+  for (int z = z0; z < z1; z++) {
+    cp_async_wait<kAhead - 1>();  // planes up to z + 1 have landed (own copies)
+    __syncthreads();              // ... everyone's, and nobody still reads plane z - 2
+    C ys[V], yn[V], fc[V];
+    C hx = 0;
+    if (wact) {
+      if (z == z0) {
+        vld((const T *)(urow(z - 1 + kRingZ, w + 1) + (lane + 1) * 16), um);
+        vld((const T *)(urow(z + kRingZ, w + 1) + (lane + 1) * 16), uc);
+      }
+      vld((const T *)(urow(z + 1, w + 1) + (lane + 1) * 16), up);
+      vld((const T *)(urow(z, w) + (lane + 1) * 16), ys);
+      vld((const T *)(urow(z, w + 2) + (lane + 1) * 16), yn);
+      vld((const T *)(frow(z) + lane * 16), fc);
+      if (lane == 0) hx = sld<T>(urow(z, w + 1) + 16 - sizeof(T));
+      if (lane == 31) hx = sld<T>(urow(z, w + 1) + 33 * 16);
+    }
+    // The slot of plane z + kAhead + 1 held plane z - 2 (z0 - 1 on the first
+    // step is read above, before this refill of a different slot).
+    stage_plane<T>(urow(z + kAhead + 1, 0), u, f, z + kAhead + 1 <= z1 ? z + kAhead + 1 : -1, y0, x0, n, pitch, P,
+                   true);
+    if (wact) {
+      C wl = shup(uc[V - 1]), er = shdn(uc[0]);
+      if (lane == 0) wl = hx;
+      if (lane == 31) er = hx;
+      C res[V];
+#pragma unroll
+      for (int q = 0; q < V; q++) {
+        const C wv = q == 0 ? wl : uc[q - 1];
+        const C ev = q == V - 1 ? er : uc[q + 1];
+        const int c = cl + q;
+        const bool in = c >= 1 && c <= n - 2;
+        if (MODE == kSweep) {
+          C nv = alpha * fc[q] + bx * (wv + ev) + by * (ys[q] + yn[q]) + bz * (um[q] + up[q]);
+          if (has_gamma) nv += gamma * uc[q];
+          const bool upd = in && (a.color < 0 || ((c + y + z) & 1) == a.color);
+          res[q] = upd ? nv : uc[q];
+        } else {
+          C rr = fc[q] - cd * uc[q] + cx * (wv + ev) + cy * (ys[q] + yn[q]) + cz * (um[q] + up[q]);
+          if (MODE == kResid) res[q] = in ? rr : (C)0;
+          if (MODE == kNorm && in) acc += (double)rr * (double)rr;
+        }
+      }
+      if (MODE != kNorm && cl < pitch) vst((T *)a.out + (long long)z * P + (long long)y * pitch + cl, res);
+#pragma unroll
+      for (int q = 0; q < V; q++) { um[q] = uc[q]; uc[q] = up[q]; }
+    }
+  }
+  cp_async_wait<0>();
+  if (MODE == kNorm) {
+    double s = oz::warp_sum(acc);
+    if (lane == 0) wsum[w] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int i = 0; i < kTY; i++) t += wsum[i];
+      a.partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = t;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- transfers
+
+struct ArgsT3 {
+  const void *src;    // restrict: fine residual; prolong: coarse correction
+  void *dst;          // restrict: coarse right-hand side; prolong: fine solution (in place)
+  int nf, pitchf;     // fine grid
+  long long planef;
+  int nc, pitchc;     // coarse grid
+  long long planec;
+  int ntx;            // x-tiles (of the grid the warps run over)
+};
+
+// Full weighting at coarse interior nodes: a warp covers 16 V coarse columns
+// (V / 2 per lane, from one 16-byte vector of V fine values per fine row),
+// for one coarse row J and plane K; blocks hold kTY consecutive rows.
+template <typename T>
+__global__ void __launch_bounds__(32 * kTY) k3_restrict(ArgsT3 a) {
+  typedef typename CT<T>::type C;
+  constexpr int V = VW<T>::V, VC = V / 2;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int tx = blockIdx.x % a.ntx, jt = blockIdx.x / a.ntx;
+  const int J = 1 + jt * kTY + w, K = 1 + blockIdx.y;
+  if (J > a.nc - 2) return;
+  const int X0 = tx * 16 * V, I0 = X0 + VC * lane;  // first coarse column of this lane
+  const int xf = 2 * I0;                              // its fine column
+  const bool lact = xf + V <= a.pitchf;
+  const T *rf = (const T *)a.src;
+  C acc[VC];
+#pragma unroll
+  for (int q = 0; q < VC; q++) acc[q] = 0;
+#pragma unroll
+  for (int dz = -1; dz <= 1; dz++) {
+#pragma unroll
+    for (int dy = -1; dy <= 1; dy++) {
+      const C wyz = (dz == 0 ? (C)0.5 : (C)0.25) * (dy == 0 ? (C)0.5 : (C)0.25);
+      const T *row = rf + (long long)(2 * K + dz) * a.planef + (long long)(2 * J + dy) * a.pitchf;
+      C v[V];
+      if (lact) vld(row + xf, v);
+      else {
+#pragma unroll
+        for (int q = 0; q < V; q++) v[q] = 0;
+      }
+      C left = shup(v[V - 1]);
+      if (lane == 0) left = xf >= 1 ? (C)ld(row + xf - 1) : (C)0;
+#pragma unroll
+      for (int q = 0; q < VC; q++) {
+        const C a0 = q == 0 ? left : v[2 * q - 1];
+        acc[q] += wyz * ((C)0.25 * (a0 + v[2 * q + 1]) + (C)0.5 * v[2 * q]);
+      }
+    }
+  }
+  T *fc = (T *)a.dst + (long long)K * a.planec + (long long)J * a.pitchc;
+#pragma unroll
+  for (int q = 0; q < VC; q++) {
+    const int I = I0 + q;
+    if (I >= 1 && I <= a.nc - 2) st(fc + I, acc[q]);
+  }
+}
+
+// Trilinear interpolation and correction at fine interior nodes: a warp
+// covers 32 V fine columns of one fine row j and plane k.
+template <typename T>
+__global__ void __launch_bounds__(32 * kTY) k3_prolong(ArgsT3 a) {
+  typedef typename CT<T>::type C;
+  constexpr int V = VW<T>::V, VC = V / 2;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int tx = blockIdx.x % a.ntx, jt = blockIdx.x / a.ntx;
+  const int j = 1 + jt * kTY + w, k = 1 + blockIdx.y;
+  if (j > a.nf - 2) return;
+  const int cl = tx * 32 * V + V * lane;  // first fine column (even)
+  if (cl >= a.pitchf) return;             // whole lane outside the row: no shuffles below read it
+  const int Ic = cl >> 1;
+  const int J = j >> 1, Kc = k >> 1, oj = j & 1, ok = k & 1;
+  const T *ec = (const T *)a.src;
+  C e[VC + 1];
+#pragma unroll
+  for (int q = 0; q <= VC; q++) e[q] = 0;
+  const C wgt = (oj ? (C)0.5 : (C)1) * (ok ? (C)0.5 : (C)1);
+#pragma unroll
+  for (int dk = 0; dk <= 1; dk++) {
+    if (dk && !ok) break;
+#pragma unroll
+    for (int dj = 0; dj <= 1; dj++) {
+      if (dj && !oj) break;
+      const T *row = ec + (long long)(Kc + dk) * a.planec + (long long)(J + dj) * a.pitchc + Ic;
+#pragma unroll
+      for (int q = 0; q <= VC; q++) {
+        const int I = Ic + q;
+        if (I < a.nc) e[q] += (C)ld(row + q);
+      }
+    }
+  }
+  T *uf = (T *)a.dst + (long long)k * a.planef + (long long)j * a.pitchf + cl;
+  C u[V];
+  vld(uf, u);
+#pragma unroll
+  for (int q = 0; q < V; q++) {
+    const int c = cl + q;
+    const C ev = (q & 1) ? (C)0.5 * (e[q >> 1] + e[(q >> 1) + 1]) : e[q >> 1];
+    if (c >= 1 && c <= a.nf - 2) u[q] += wgt * ev;
+  }
+  vst(uf, u);
+}
+
+// ---------------------------------------------------------------- FP64 outer step
+
+// Block of kTY + 2 warps: rows y0-1 .. y0+kTY (the first and last only update
+// their row so that the others see updated y-neighbours). Per plane, staged
+// by cp.async kAhead planes ahead: u_in and e for all kTY + 2 rows (with
+// 16-byte halo chunks), f for the kTY output rows. Step z updates plane z + 1
+// (u_new = u_in + e, FP64; written to u_out and to a 3-slot ring of updated
+// rows in shared memory) and, after a barrier, forms the residual of plane z
+// from updated values only: FP64 work per node is one add for the update and
+// seven operations for the residual f - cd u + cx (uw+ue) + cy (us+un) + cz (ud+uu).
+constexpr int kDCWarps = kTY + 2;
+constexpr int kDCRing = kAhead + 2;
+template <typename Ti> struct DCL {
+  static constexpr int ECH = 64 * (int)sizeof(Ti) / 16;  // 16-byte chunks of e per 64-column row
+  static constexpr int ERowB = (ECH + 2) * 16;
+  static constexpr int SlotB = kDCWarps * kURowB + kDCWarps * ERowB + kTY * kFRowB;
+  static constexpr int UNRowB = 64 * 8;
+  static constexpr int Smem = kDCRing * SlotB + 3 * kDCWarps * UNRowB;
+};
+
+struct ArgsDC3 {
+  const double *u;     // outer solution read
+  double *uout;        // updated outer solution (UPDATE)
+  const double *f;     // outer right-hand side
+  const void *e;       // inner correction (inner storage type)
+  void *d;             // inner defect (inner storage type), may be NULL
+  double *partials;    // one per block
+  const float *scale;  // power of two applied before the FP32 squares
+  int n, pitch, pitchi;
+  long long plane, planei;
+  int ntx, nty, zc;
+  double cd, cx, cy, cz;
+};
+
+template <typename Ti, bool UPDATE>
+__device__ __forceinline__ void stage_dc(unsigned char *slot, const ArgsDC3 &a, int p, int y0, int x0) {
+  typedef DCL<Ti> L;
+  constexpr int NU = kDCWarps * kUChunks, NE = UPDATE ? kDCWarps * (L::ECH + 2) : 0, NF = kTY * 32;
+  constexpr int EV = 16 / (int)sizeof(Ti);  // e values per chunk
+  const bool pok = p >= 0 && p < a.n;
+  const Ti *e = (const Ti *)a.e;
+  for (int i = threadIdx.x; i < NU + NE + NF; i += blockDim.x) {
+    if (i < NU) {
+      const int rr = i / kUChunks, ch = i - rr * kUChunks;
+      const int y = y0 - 1 + rr, x = x0 + (ch - 1) * 2;
+      const bool ok = pok && y >= 0 && y < a.n && x >= 0 && x + 2 <= a.pitch;
+      const double *src = ok ? a.u + (long long)p * a.plane + (long long)y * a.pitch + x : a.u;
+      cp_async16(slot + rr * kURowB + ch * 16, src, ok);
+    } else if (i < NU + NE) {
+      const int j = i - NU, rr = j / (L::ECH + 2), ch = j - rr * (L::ECH + 2);
+      const int y = y0 - 1 + rr, x = x0 + (ch - 1) * EV;
+      const bool ok = pok && y >= 0 && y < a.n && x >= 0 && x + EV <= a.pitchi;
+      const Ti *src = ok ? e + (long long)p * a.planei + (long long)y * a.pitchi + x : e;
+      cp_async16(slot + kDCWarps * kURowB + rr * L::ERowB + ch * 16, src, ok);
+    } else {
+      const int j = i - NU - NE, rr = j >> 5, ch = j & 31;
+      const int y = y0 + rr, x = x0 + ch * 2;
+      const bool ok = pok && y < a.n && x + 2 <= a.pitch;
+      const double *src = ok ? a.f + (long long)p * a.plane + (long long)y * a.pitch + x : a.f;
+      cp_async16(slot + kDCWarps * kURowB + kDCWarps * L::ERowB + rr * kFRowB + ch * 16, src, ok);
+    }
+  }
+  cp_async_commit();
+}
+
+template <typename Ti> __device__ __forceinline__ double e_at(const unsigned char *p) {
+  return oz::f2d_bits(sizeof(Ti) == 4 ? *(const float *)p : __bfloat162float(*(const bf16 *)p));
+}
+
+template <typename Ti, bool UPDATE, bool ACC64>
+__global__ void __launch_bounds__(32 * kDCWarps) k3_dc(ArgsDC3 a) {
+  typedef DCL<Ti> L;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double wsum[kDCWarps];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;  // w = 0 .. kTY + 1: row y0 - 1 + w
+  const int tx = blockIdx.x % a.ntx, ty = blockIdx.x / a.ntx;
+  const int n = a.n;
+  const int y0 = 1 + ty * kTY, y = y0 - 1 + w;
+  const int x0 = tx * 64, cl = x0 + 2 * lane;
+  const int z0 = 1 + blockIdx.y * a.zc, z1 = min(z0 + a.zc, n - 1);
+  const bool out_warp = w >= 1 && w <= kTY && y <= n - 2;  // residual rows (interior)
+  const bool row_ok = y <= n - 1;
+  unsigned char *un = smem + kDCRing * L::SlotB;  // 3 slots x kDCWarps rows of updated u
+  auto slot = [&](int p) { return smem + (p % kDCRing) * L::SlotB; };
+  const float scale = *a.scale;
+  const double cd = a.cd, cx = a.cx, cy = a.cy, cz = a.cz;
+  Ti *d = (Ti *)a.d;
+  float acc = 0.0f;
+  double acc64 = 0.0;
+
+  // Updated u of this warp's row at plane p: own two values and the x-halo
+  // value (lane 0: column x0 - 1, lane 31: column x0 + 64).
+  auto update_row = [&](int p, double (&v)[2], double &h) {
+    const unsigned char *s = slot(p + kDCRing);
+    const unsigned char *ur = s + w * kURowB;
+    vld((const double *)(ur + (lane + 1) * 16), v);
+    h = 0.0;
+    if (lane == 0) h = *(const double *)(ur + 8);
+    if (lane == 31) h = *(const double *)(ur + 33 * 16);
+    if (UPDATE) {
+      const unsigned char *er = s + kDCWarps * kURowB + w * L::ERowB;
+      const unsigned char *mine = er + 16 + lane * 2 * sizeof(Ti);
+      v[0] += e_at<Ti>(mine);
+      v[1] += e_at<Ti>(mine + sizeof(Ti));
+      if (lane == 0) h += e_at<Ti>(er + 16 - sizeof(Ti));
+      if (lane == 31) h += e_at<Ti>(er + 16 + 64 * sizeof(Ti));
+    }
+  };
+
+  const int zs = z0 - 2;  // first step: updates plane z0 - 1
+  for (int k = 1; k <= kAhead; k++) {
+    const int p = zs + k;
+    stage_dc<Ti, UPDATE>(slot(p + kDCRing), a, p <= z1 ? p : -1, y0, x0);
+  }
+
+  double um[2] = {0, 0}, uc[2] = {0, 0}, up[2] = {0, 0};
+  double hc = 0, hp = 0;
+  for (int z = zs; z < z1; z++) {
+    cp_async_wait<kAhead - 1>();  // plane z + 1 staged
+    __syncthreads();              // (A) for everyone; plane z - 1's slot is free
+    stage_dc<Ti, UPDATE>(slot(z + kAhead + 1 + kDCRing), a, z + kAhead + 1 <= z1 ? z + kAhead + 1 : -1, y0, x0);
+    double nv[2] = {0, 0}, nh = 0;
+    if (row_ok) {
+      update_row(z + 1, nv, nh);
+      *(double2 *)(un + (((z + 1) % 3 + 3) % 3 * kDCWarps + w) * L::UNRowB + lane * 16) = make_double2(nv[0], nv[1]);
+      if (UPDATE && out_warp && z + 1 >= z0 && z + 1 < z1 && cl < a.pitch)
+        *(double2 *)(a.uout + (long long)(z + 1) * a.plane + (long long)y * a.pitch + cl) = make_double2(nv[0], nv[1]);
+    }
+    __syncthreads();  // (B) updated rows of plane z + 1 visible
+    um[0] = uc[0]; um[1] = uc[1];
+    uc[0] = up[0]; uc[1] = up[1];
+    up[0] = nv[0]; up[1] = nv[1];
+    hc = hp; hp = nh;
+    if (z >= z0 && out_warp) {
+      const unsigned char *us = un + ((z % 3 + 3) % 3 * kDCWarps + (w - 1)) * L::UNRowB + lane * 16;
+      const unsigned char *un_ = un + ((z % 3 + 3) % 3 * kDCWarps + (w + 1)) * L::UNRowB + lane * 16;
+      const double2 s2 = *(const double2 *)us, n2 = *(const double2 *)un_;
+      const double2 f2 = *(const double2 *)(slot(z + kDCRing) + kDCWarps * kURowB + kDCWarps * L::ERowB +
+                                             (w - 1) * kFRowB + lane * 16);
+      double wl = shup(uc[1]), er = shdn(uc[0]);
+      if (lane == 0) wl = hc;
+      if (lane == 31) er = hc;
+      const double ysv[2] = {s2.x, s2.y}, ynv[2] = {n2.x, n2.y}, fv[2] = {f2.x, f2.y};
+      float rv[2];
+#pragma unroll
+      for (int q = 0; q < 2; q++) {
+        const double uw = q == 0 ? wl : uc[0], ue = q == 1 ? er : uc[1];
+        const double rr = fma(cz, um[q] + up[q], fma(cy, ysv[q] + ynv[q], fma(cx, uw + ue, fma(-cd, uc[q], fv[q]))));
+        const int c = cl + q;
+        const bool in = c >= 1 && c <= n - 2;
+        rv[q] = in ? oz::d2f_bits(rr) : 0.0f;
+        if (ACC64 && in) acc64 = fma(rr, rr, acc64);
+        if (!ACC64) {
+          const float sr = rv[q] * scale;
+          acc = fmaf(sr, sr, acc);
+        }
+      }
+      if (d && cl < a.pitchi) {
+        Ti *dp = d + (long long)z * a.planei + (long long)y * a.pitchi + cl;
+        if (sizeof(Ti) == 4) {
+          *(float2 *)dp = make_float2(rv[0], rv[1]);
+        } else {
+          __nv_bfloat162 b = __floats2bfloat162_rn(rv[0], rv[1]);
+          *(__nv_bfloat162 *)dp = b;
+        }
+      }
+    }
+  }
+  cp_async_wait<0>();
+  double s = oz::warp_sum(ACC64 ? acc64 : (double)acc);
+  if (lane == 0) wsum[w] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < kDCWarps; i++) t += wsum[i];
+    a.partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+}  // namespace z3
+}  // namespace mg
