@@ -38,12 +38,16 @@ size_t coarse_args(const Level *lv, int first, int nl, bool zero_top, int smooth
   a.nlev = nl - first;
   if (a.nlev > cz::kMaxLev || a.nlev < 1) return 0;
   a.var = T.kf[0] != nullptr;
-  for (int d = 0; d < 3; d++) a.c[d] = T.c[d];
+  for (int d = 0; d < 3; d++) {
+    a.c[d] = T.c[d];
+    a.cf[d] = (float)T.c[d];
+  }
   size_t elems = 0;
   for (int i = 0; i < a.nlev; i++) {
     const Level &L = lv[first + i];
     a.n[i] = L.n;
     a.inv_h2[i] = L.inv_h2;
+    a.inv_h2f[i] = (float)L.inv_h2;
     a.pitch[i] = L.pitch;
     a.plane[i] = L.plane;
     a.kf64[i] = L.dtype == F64;
@@ -63,6 +67,7 @@ size_t coarse_args(const Level *lv, int first, int nl, bool zero_top, int smooth
   a.zero_top = zero_top;
   a.smoother = smoother;
   a.omega = omega;
+  a.omegaf = (float)omega;
   a.nu1 = nu1;
   a.nu2 = nu2;
   size_t smem = elems * (fp64 ? 8 : 4);

@@ -40,17 +40,23 @@ struct CoarseArgs {
   int smoother;            // 0 RBGS, 1 Jacobi
   double omega;
   int nu1, nu2;
+  // inv_h2, c and omega rounded to FP32 on the host, for FP32 cycles
+  float inv_h2f[kMaxLev];
+  float cf[3];
+  float omegaf;
 };
 
-__device__ __forceinline__ double ldg_any(const void *p, long long i, int dtype) {
-  if (dtype == F64) return ((const double *)p)[i];
-  if (dtype == F32) return (double)((const float *)p)[i];
-  return (double)__bfloat162float(((const bf16 *)p)[i]);
+// Element i of a global field of type dtype, in the cycle's compute type C
+// (no round trip through double for float fields).
+template <typename C> __device__ __forceinline__ C ldg_as(const void *p, long long i, int dtype) {
+  if (dtype == F64) return (C)((const double *)p)[i];
+  if (dtype == F32) return (C)((const float *)p)[i];
+  return (C)__bfloat162float(((const bf16 *)p)[i]);
 }
-__device__ __forceinline__ void stg_any(void *p, long long i, int dtype, double v) {
-  if (dtype == F64) ((double *)p)[i] = v;
+template <typename C> __device__ __forceinline__ void stg_as(void *p, long long i, int dtype, C v) {
+  if (dtype == F64) ((double *)p)[i] = (double)v;
   else if (dtype == F32) ((float *)p)[i] = (float)v;
-  else ((bf16 *)p)[i] = __float2bfloat16_rn((float)v);
+  else ((bf16 *)p)[i] = bf16_rne((float)v);
 }
 
 template <int DIM> __device__ __forceinline__ int npts(int n) { return DIM == 3 ? n * n * n : n * n; }
@@ -76,7 +82,7 @@ __device__ __forceinline__ Lev<C> level(const CoarseArgs &a, C *sm, int l) {
   Lev<C> L;
   int N = npts<DIM>(a.n[l]);
   L.n = a.n[l];
-  L.ih2 = (C)a.inv_h2[l];
+  L.ih2 = pick<C>(a.inv_h2[l], a.inv_h2f[l]);
   L.u = sm + a.off_u[l];
   L.f = sm + a.off_f[l];
   L.kx = VAR ? sm + a.off_k[l] : nullptr;
@@ -179,8 +185,8 @@ template <int DIM, bool VAR, typename C>
 __device__ __forceinline__ void coarse_cycle_body(const CoarseArgs &a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *sm = (C *)smem_raw;
-  const C c[3] = {(C)a.c[0], (C)a.c[1], (C)a.c[2]};
-  const C omega = (C)a.omega;
+  const C c[3] = {pick<C>(a.c[0], a.cf[0]), pick<C>(a.c[1], a.cf[1]), pick<C>(a.c[2], a.cf[2])};
+  const C omega = pick<C>(a.omega, a.omegaf);
   C *tmp = sm + a.off_tmp;
   for (int p = threadIdx.x; p < a.total; p += kThreads) sm[p] = (C)0;
   __syncthreads();
@@ -191,8 +197,8 @@ __device__ __forceinline__ void coarse_cycle_body(const CoarseArgs &a) {
     for (int p = threadIdx.x; p < N; p += kThreads) {
       int i = p % n, j = (p / n) % n, k = DIM == 3 ? p / (n * n) : 0;
       long long g = (long long)k * a.plane[0] + (long long)j * a.pitch[0] + i;
-      T.f[p] = (C)ldg_any(a.f_top, g, a.top_dtype);
-      if (!a.zero_top) T.u[p] = (C)ldg_any(a.u_top, g, a.top_dtype);
+      T.f[p] = ldg_as<C>(a.f_top, g, a.top_dtype);
+      if (!a.zero_top) T.u[p] = ldg_as<C>(a.u_top, g, a.top_dtype);
     }
     if (VAR) {
       for (int l = 0; l < a.nlev; l++) {
@@ -290,7 +296,7 @@ __device__ __forceinline__ void coarse_cycle_body(const CoarseArgs &a) {
     Lev<C> T = level<DIM, VAR, C>(a, sm, 0);
     for_interior<DIM>(a.n[0], [&](int p, int i, int j, int k) {
       long long g = (long long)k * a.plane[0] + (long long)j * a.pitch[0] + i;
-      stg_any(a.u_top, g, a.top_dtype, (double)T.u[p]);
+      stg_as<C>(a.u_top, g, a.top_dtype, T.u[p]);
     });
   }
 }

@@ -57,6 +57,15 @@ fz::Args2D make_args(const Level &L, const Level &Cl, double omega, int R_overri
   a.gamma = 1.0 - omega;
   a.cx = cx;
   a.cy = cy;
+  a.cd = 2.0 * (cx + cy);
+  a.alphaf = (float)a.alpha;
+  a.betaxf = (float)a.betax;
+  a.betayf = (float)a.betay;
+  a.gammaf = (float)a.gamma;
+  a.cxf = (float)a.cx;
+  a.cyf = (float)a.cy;
+  a.cdf = (float)a.cd;
+  a.has_gamma = a.gamma != 0.0;
   return a;
 }
 

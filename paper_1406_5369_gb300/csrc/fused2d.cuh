@@ -66,7 +66,12 @@ struct Args2D {
   int R;            // rows per chunk (multiple of 8)
   int nstrips, nchunks;
   double alpha, betax, betay, gamma;  // u_new = gamma u + alpha f + betax (uw+ue) + betay (us+un)
-  double cx, cy;                      // residual: f - [cx((u-uw)+(u-ue)) + cy((u-us)+(u-un))]
+  double cx, cy, cd;                  // residual: f - [cx((u-uw)+(u-ue)) + cy((u-us)+(u-un))], cd = 2 (cx + cy)
+  // The same coefficients rounded to FP32 on the host: FP32 kernels read
+  // these, so that no FP64 -> FP32 conversion (a slow-pipe instruction the
+  // compiler may repeat inside loops) runs on the device.
+  float alphaf, betaxf, betayf, gammaf, cxf, cyf, cdf;
+  int has_gamma;  // gamma != 0 (omega != 1), decided on the host
 };
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool valid) {
@@ -123,6 +128,20 @@ template <typename C> struct Coef {
   C alpha, bx, by, gamma, cx, cy, cd;
   bool has_gamma;
 };
+
+
+template <typename C> __device__ __forceinline__ Coef<C> coef_of(const Args2D &a) {
+  Coef<C> k;
+  k.alpha = pick<C>(a.alpha, a.alphaf);
+  k.bx = pick<C>(a.betax, a.betaxf);
+  k.by = pick<C>(a.betay, a.betayf);
+  k.gamma = pick<C>(a.gamma, a.gammaf);
+  k.cx = pick<C>(a.cx, a.cxf);
+  k.cy = pick<C>(a.cy, a.cyf);
+  k.cd = pick<C>(a.cd, a.cdf);
+  k.has_gamma = a.has_gamma != 0;
+  return k;
+}
 
 // Red-black half-sweep of colour `color` on row r held in uc, with rows r-1
 // (ua) and r+1 (ub). Columns c0 + q with (c0 + q + r) % 2 == color update.
@@ -213,9 +232,7 @@ __global__ void __launch_bounds__(32 * Warps<T>::value, MinBlocks<T>::value) k_p
   constexpr int LB = Lane<T>::bytes;
   unsigned char *su = smem + (size_t)wib * kRing * 32 * LB * 2;
   unsigned char *sf = su + kRing * 32 * LB;
-  Coef<C> k;
-  k.alpha = (C)a.alpha; k.bx = (C)a.betax; k.by = (C)a.betay; k.gamma = (C)a.gamma;
-  k.cx = (C)a.cx; k.cy = (C)a.cy; k.cd = (C)(2.0 * (a.cx + a.cy)); k.has_gamma = a.gamma != 0.0;
+  const Coef<C> k = coef_of<C>(a);
 
   C U[kSlots][kVec], F[kSlots][kVec], Rr[kSlots][kVec];
 #pragma unroll
@@ -340,9 +357,7 @@ __global__ void __launch_bounds__(32 * Warps<T>::value, MinBlocks<T>::value) k_p
   unsigned char *su = smem + (size_t)wib * kRing * 32 * (2 * LB + CB);
   unsigned char *sf = su + kRing * 32 * LB;
   unsigned char *se = sf + kRing * 32 * LB;  // CB bytes per lane and slot
-  Coef<C> k;
-  k.alpha = (C)a.alpha; k.bx = (C)a.betax; k.by = (C)a.betay; k.gamma = (C)a.gamma;
-  k.cx = (C)a.cx; k.cy = (C)a.cy; k.cd = (C)(2.0 * (a.cx + a.cy)); k.has_gamma = a.gamma != 0.0;
+  const Coef<C> k = coef_of<C>(a);
 
   C U[kSlots][kVec], F[kSlots][kVec];
   // Coarse rows by parity of the coarse row index (values at J0, J0+1). Chunks

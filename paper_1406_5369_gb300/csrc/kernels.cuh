@@ -19,15 +19,39 @@ typedef __nv_bfloat16 bf16;
 template <typename T> struct CT { typedef float type; };
 template <> struct CT<double> { typedef double type; };
 
+// A coefficient in the compute type: the double, or its float rounded on the
+// host (so that no FP64 -> FP32 conversion, a slow-pipe instruction the
+// compiler may repeat inside loops, runs on the device).
+template <typename C> __device__ __forceinline__ C pick(double d, float f);
+template <> __device__ __forceinline__ double pick<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }
+
 __device__ __forceinline__ double ld(const double *p) { return *p; }
 __device__ __forceinline__ float ld(const float *p) { return *p; }
 __device__ __forceinline__ float ld(const bf16 *p) { return __bfloat162float(*p); }
 
+// FP32 -> BF16 with round to nearest, ties to even, on the integer pipe: add
+// 0x7fff plus the lowest kept bit to the float's bits and keep the top 16
+// (a carry into the exponent rounds up to the next binade or to infinity,
+// as IEEE-754 rounding requires); NaNs keep their sign and get the quiet bit.
+// The conversion instructions run on the same slow pipe as FP64 arithmetic
+// on this GPU, so the streaming kernels avoid them.
+__device__ __forceinline__ unsigned bf16_rne_bits(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned r = (b + 0x7fffu + ((b >> 16) & 1u)) >> 16;
+  return (b & 0x7fffffffu) > 0x7f800000u ? ((b >> 16) | 0x40u) : r;
+}
+// Two values packed as a bfloat162 word (a in the low half).
+__device__ __forceinline__ unsigned bf16x2_rne_bits(float a, float b) {
+  return bf16_rne_bits(a) | (bf16_rne_bits(b) << 16);
+}
+__device__ __forceinline__ bf16 bf16_rne(float x) { return __ushort_as_bfloat16((unsigned short)bf16_rne_bits(x)); }
+
 __device__ __forceinline__ void st(double *p, double v) { *p = v; }
 __device__ __forceinline__ void st(float *p, double v) { *p = (float)v; }
-__device__ __forceinline__ void st(bf16 *p, double v) { *p = __float2bfloat16_rn((float)v); }
+__device__ __forceinline__ void st(bf16 *p, double v) { *p = bf16_rne((float)v); }
 __device__ __forceinline__ void st(float *p, float v) { *p = v; }
-__device__ __forceinline__ void st(bf16 *p, float v) { *p = __float2bfloat16_rn(v); }
+__device__ __forceinline__ void st(bf16 *p, float v) { *p = bf16_rne(v); }
 __device__ __forceinline__ void st(double *p, float v) { *p = (double)v; }
 
 // Geometry of a level in kernel form.

@@ -108,11 +108,7 @@ template <typename Ti> __device__ __forceinline__ void store4i(Ti *dst, const fl
   if (sizeof(Ti) == 4) {
     *(float4 *)dst = make_float4(v[0], v[1], v[2], v[3]);
   } else {
-    __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]), b = __floats2bfloat162_rn(v[2], v[3]);
-    uint2 w;
-    w.x = *(unsigned *)&a;
-    w.y = *(unsigned *)&b;
-    *(uint2 *)dst = w;
+    *(uint2 *)dst = make_uint2(bf16x2_rne_bits(v[0], v[1]), bf16x2_rne_bits(v[2], v[3]));
   }
 }
 

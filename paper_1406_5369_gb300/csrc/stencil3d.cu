@@ -60,6 +60,16 @@ z3::Args3 stencil_args(const Level &L, double omega) {
   a.cx = cx;
   a.cy = cy;
   a.cz = cz;
+  a.alphaf = (float)a.alpha;
+  a.bxf = (float)a.bx;
+  a.byf = (float)a.by;
+  a.bzf = (float)a.bz;
+  a.gammaf = (float)a.gamma;
+  a.cdf = (float)a.cd;
+  a.cxf = (float)a.cx;
+  a.cyf = (float)a.cy;
+  a.czf = (float)a.cz;
+  a.has_gamma = a.gamma != 0.0;
   a.color = -1;
   return a;
 }
@@ -99,7 +109,11 @@ cudaError_t z_sweep(const Level &L, const void *uin, void *uout, const void *f, 
   a.f = f;
   a.color = color;
   cudaError_t e = cudaSuccess;
-  Z3_DISPATCH(L.dtype, e = (launch_stencil<T, z3::kSweep>(a, 1LL << 30, nullptr, s)));
+  if (color < 0) {
+    Z3_DISPATCH(L.dtype, e = (launch_stencil<T, z3::kJacobi>(a, 1LL << 30, nullptr, s)));
+  } else {
+    Z3_DISPATCH(L.dtype, e = (launch_stencil<T, z3::kRB>(a, 1LL << 30, nullptr, s)));
+  }
   return e;
 }
 

@@ -1,8 +1,8 @@
 // Plane-marching 3D kernels for the constant 7-point stencil (Algorithm 1's
 // level operators on 3D grids, Sec. 2.2-2.4):
 //
-//   k3_stencil<T, kSweep>: one omega-Jacobi sweep (u_out from u_in) or one
-//                          red-black half-sweep (in place, one colour);
+//   k3_stencil<T, kJacobi>: one omega-Jacobi sweep (u_out from u_in);
+//   k3_stencil<T, kRB>   : one red-black half-sweep (in place, one colour);
 //   k3_stencil<T, kResid>: residual r = f - A u;
 //   k3_stencil<T, kNorm> : per-block partial sums of (f - A u)^2;
 //   k3_restrict<T>       : full weighting r_h -> f_H;
@@ -69,13 +69,8 @@ __device__ __forceinline__ void vld(const bf16 *p, float (&v)[8]) {
 __device__ __forceinline__ void vst(double *p, const double (&v)[2]) { *(double2 *)p = make_double2(v[0], v[1]); }
 __device__ __forceinline__ void vst(float *p, const float (&v)[4]) { *(float4 *)p = make_float4(v[0], v[1], v[2], v[3]); }
 __device__ __forceinline__ void vst(bf16 *p, const float (&v)[8]) {
-  unsigned w[4];
-#pragma unroll
-  for (int k = 0; k < 4; k++) {
-    __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
-    w[k] = *(unsigned *)&b;
-  }
-  *(uint4 *)p = make_uint4(w[0], w[1], w[2], w[3]);
+  *(uint4 *)p = make_uint4(bf16x2_rne_bits(v[0], v[1]), bf16x2_rne_bits(v[2], v[3]), bf16x2_rne_bits(v[4], v[5]),
+                           bf16x2_rne_bits(v[6], v[7]));
 }
 template <typename T> __device__ __forceinline__ typename CT<T>::type sld(const unsigned char *p) {
   return (typename CT<T>::type)ld((const T *)p);
@@ -89,38 +84,76 @@ struct Args3 {
   int n, pitch;       // nodes per dimension, row stride (elements)
   long long plane;    // plane stride (elements)
   int ntx, nty, zc;   // x-tiles, y-tiles of kTY rows, planes per chunk
-  int color;          // sweep: red-black colour to update, -1 = Jacobi
+  int color;          // red-black half-sweep: colour to update
   double alpha, bx, by, bz, gamma;  // sweep: u' = gamma u + alpha f + bx (uw+ue) + by (us+un) + bz (ud+uu)
   double cd, cx, cy, cz;            // residual: r = f - cd u + cx (uw+ue) + cy (us+un) + cz (ud+uu)
+  // The same, rounded to FP32 on the host (read by the FP32-arithmetic kernels).
+  float alphaf, bxf, byf, bzf, gammaf, cdf, cxf, cyf, czf;
+  int has_gamma;  // gamma != 0 (omega != 1), decided on the host
 };
 
-enum { kSweep = 0, kResid = 1, kNorm = 2 };
+enum { kJacobi = 0, kRB = 1, kResid = 2, kNorm = 3 };
 
-// Stages plane p of the block's tile (u rows y0-1 .. y0+kTY with halo chunks,
-// f rows y0 .. y0+kTY-1) into `slot`; invalid pieces are zero-filled. One
-// commit group per call.
+// The 16-byte pieces a thread stages for every plane, fixed for the whole
+// march: source address at plane 0, byte stride between planes, shared-memory
+// offset inside a slot and whether the piece lies inside its array.
+// issue() stages consecutive planes: it is called first with plane `first`
+// (start()), then with each following plane, so the source addresses advance
+// by one plane stride per call instead of being recomputed.
+template <int K> struct Pieces {
+  const unsigned char *src[K];
+  const unsigned char *anchor;  // a valid address handed to zero-filled copies
+  long long pstep[K];
+  int soff[K];  // -1: no piece
+  bool ok[K];
+  __device__ __forceinline__ void start(int first) {
+#pragma unroll
+    for (int k = 0; k < K; k++) src[k] += (long long)first * pstep[k];
+  }
+  // Stages the current plane into `slot` (zero-fill unless `pok`), advances.
+  __device__ __forceinline__ void issue(unsigned char *slot, bool pok) {
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      if (soff[k] >= 0) {
+        const bool v = ok[k] && pok;
+        cp_async16(slot + soff[k], v ? src[k] : anchor, v);
+        src[k] += pstep[k];
+      }
+    }
+    cp_async_commit();
+  }
+};
+
+// Pieces of the stencil kernels' tile: u rows y0-1 .. y0+kTY (34 chunks each:
+// left halo, 32 lanes, right halo), f rows y0 .. y0+kTY-1 (32 chunks).
+constexpr int kStPieces = ((kTY + 2) * kUChunks + kTY * 32 + 32 * kTY - 1) / (32 * kTY);
 template <typename T>
-__device__ __forceinline__ void stage_plane(unsigned char *slot, const T *u, const T *f, int p, int y0, int x0,
-                                            int n, int pitch, long long P, bool with_f) {
+__device__ __forceinline__ void stencil_pieces(Pieces<kStPieces> &pc, const T *u, const T *f, int y0, int x0, int n,
+                                               int pitch, long long P) {
   constexpr int V = VW<T>::V;
   constexpr int NU = (kTY + 2) * kUChunks, NF = kTY * 32;
-  const bool pok = p >= 0 && p < n;
-  for (int i = threadIdx.x; i < NU + NF; i += blockDim.x) {
+  pc.anchor = (const unsigned char *)u;
+#pragma unroll
+  for (int k = 0; k < kStPieces; k++) {
+    const int i = threadIdx.x + k * 32 * kTY;
+    pc.soff[k] = -1;
+    pc.ok[k] = false;
+    pc.src[k] = (const unsigned char *)u;
+    pc.pstep[k] = P * (long long)sizeof(T);
     if (i < NU) {
       const int rr = i / kUChunks, ch = i - rr * kUChunks;
       const int y = y0 - 1 + rr, x = x0 + (ch - 1) * V;
-      const bool ok = pok && y >= 0 && y < n && x >= 0 && x + V <= pitch;
-      const T *src = ok ? u + (long long)p * P + (long long)y * pitch + x : u;
-      cp_async16(slot + rr * kURowB + ch * 16, src, ok);
-    } else if (with_f) {
+      pc.ok[k] = y >= 0 && y < n && x >= 0 && x + V <= pitch;
+      if (pc.ok[k]) pc.src[k] = (const unsigned char *)(u + (long long)y * pitch + x);
+      pc.soff[k] = rr * kURowB + ch * 16;
+    } else if (i < NU + NF) {
       const int j = i - NU, rr = j >> 5, ch = j & 31;
       const int y = y0 + rr, x = x0 + ch * V;
-      const bool ok = pok && y < n && x + V <= pitch;
-      const T *src = ok ? f + (long long)p * P + (long long)y * pitch + x : f;
-      cp_async16(slot + (kTY + 2) * kURowB + rr * kFRowB + ch * 16, src, ok);
+      pc.ok[k] = y < n && x + V <= pitch;
+      pc.src[k] = (const unsigned char *)(pc.ok[k] ? f + (long long)y * pitch + x : f);
+      pc.soff[k] = (kTY + 2) * kURowB + rr * kFRowB + ch * 16;
     }
   }
-  cp_async_commit();
 }
 
 template <typename T, int MODE>
@@ -137,23 +170,33 @@ __global__ void __launch_bounds__(32 * kTY, 3) k3_stencil(Args3 a) {
   const int y0 = 1 + ty * kTY, y = y0 + w;
   const int x0 = tx * TX, cl = x0 + V * lane;
   const int z0 = 1 + blockIdx.y * a.zc, z1 = min(z0 + a.zc, n - 1);
-  const T *u = (const T *)a.u;
-  const T *f = (const T *)a.f;
-  const bool wact = y <= n - 2;  // warp-uniform
-  const C alpha = (C)a.alpha, bx = (C)a.bx, by = (C)a.by, bz = (C)a.bz, gamma = (C)a.gamma;
-  const C cd = (C)a.cd, cx = (C)a.cx, cy = (C)a.cy, cz = (C)a.cz;
-  const bool has_gamma = a.gamma != 0.0;
+  const bool wact = y <= n - 2;                        // warp-uniform
+  const C alpha = pick<C>(a.alpha, a.alphaf), bx = pick<C>(a.bx, a.bxf), by = pick<C>(a.by, a.byf);
+  const C bz = pick<C>(a.bz, a.bzf), gamma = pick<C>(a.gamma, a.gammaf);
+  const C cd = pick<C>(a.cd, a.cdf), cx = pick<C>(a.cx, a.cxf), cy = pick<C>(a.cy, a.cyf), cz = pick<C>(a.cz, a.czf);
+  const bool has_gamma = a.has_gamma != 0;
   double acc = 0.0;
 
-  // Row offsets inside a slot: own row w + 1, rows w and w + 2 above/below.
-  auto urow = [&](int p, int rr) { return smem + (p % kRingZ) * kSlotB + rr * kURowB; };
-  auto frow = [&](int p) { return smem + (p % kRingZ) * kSlotB + (kTY + 2) * kURowB + w * kFRowB; };
+  auto slot = [&](int p) { return smem + (p % kRingZ) * kSlotB; };
+  const unsigned char *own = smem + (w + 1) * kURowB + (lane + 1) * 16;  // + slot offset
+  const unsigned char *above = smem + w * kURowB + (lane + 1) * 16;
+  const unsigned char *below = smem + (w + 2) * kURowB + (lane + 1) * 16;
+  const unsigned char *frw = smem + (kTY + 2) * kURowB + w * kFRowB + lane * 16;
+  const unsigned char *halo = smem + (w + 1) * kURowB + (lane == 0 ? 16 - (int)sizeof(T) : 33 * 16);
 
+  Pieces<kStPieces> pc;
+  stencil_pieces<T>(pc, (const T *)a.u, (const T *)a.f, y0, x0, n, pitch, P);
   // Planes z0 - 1 .. z0 + kAhead up front; step z then refills with z + kAhead + 1.
+  pc.start(z0 - 1);
   for (int k = 0; k <= kAhead + 1; k++) {
     const int p = z0 - 1 + k;
-    stage_plane<T>(urow(p, 0), u, f, p <= z1 ? p : -1, y0, x0, n, pitch, P, true);
+    pc.issue(slot(p), p <= z1);
   }
+  // Columns of this lane inside the domain (the same on every plane).
+  bool inq[V];
+#pragma unroll
+  for (int q = 0; q < V; q++) inq[q] = cl + q >= 1 && cl + q <= n - 2;
+  T *outp = (T *)a.out + (long long)z0 * P + (long long)y * pitch + cl;
 
   C um[V], uc[V], up[V];
   for (int z = z0; z < z1; z++) {
@@ -161,45 +204,48 @@ __global__ void __launch_bounds__(32 * kTY, 3) k3_stencil(Args3 a) {
     __syncthreads();              // ... everyone's, and nobody still reads plane z - 2
     C ys[V], yn[V], fc[V];
     C hx = 0;
+    const long long sz = (z % kRingZ) * kSlotB, szp = ((z + 1) % kRingZ) * kSlotB;
     if (wact) {
       if (z == z0) {
-        vld((const T *)(urow(z - 1 + kRingZ, w + 1) + (lane + 1) * 16), um);
-        vld((const T *)(urow(z + kRingZ, w + 1) + (lane + 1) * 16), uc);
+        vld((const T *)(own + ((z + kRingZ - 1) % kRingZ) * kSlotB), um);
+        vld((const T *)(own + sz), uc);
       }
-      vld((const T *)(urow(z + 1, w + 1) + (lane + 1) * 16), up);
-      vld((const T *)(urow(z, w) + (lane + 1) * 16), ys);
-      vld((const T *)(urow(z, w + 2) + (lane + 1) * 16), yn);
-      vld((const T *)(frow(z) + lane * 16), fc);
-      if (lane == 0) hx = sld<T>(urow(z, w + 1) + 16 - sizeof(T));
-      if (lane == 31) hx = sld<T>(urow(z, w + 1) + 33 * 16);
+      vld((const T *)(own + szp), up);
+      vld((const T *)(above + sz), ys);
+      vld((const T *)(below + sz), yn);
+      vld((const T *)(frw + sz), fc);
+      if (lane == 0 || lane == 31) hx = sld<T>(halo + sz);
     }
-    // The slot of plane z + kAhead + 1 held plane z - 2 (z0 - 1 on the first
-    // step is read above, before this refill of a different slot).
-    stage_plane<T>(urow(z + kAhead + 1, 0), u, f, z + kAhead + 1 <= z1 ? z + kAhead + 1 : -1, y0, x0, n, pitch, P,
-                   true);
+    // The slot of plane z + kAhead + 1 held plane z - 2 (on the first step
+    // plane z0 - 1 sits in another slot and was read above).
+    pc.issue(slot(z + kAhead + 1), z + kAhead + 1 <= z1);
     if (wact) {
       C wl = shup(uc[V - 1]), er = shdn(uc[0]);
       if (lane == 0) wl = hx;
       if (lane == 31) er = hx;
       C res[V];
+      C sq = 0;
+      const int rbpar = (y + z + a.color) & 1;  // node (cl + q, y, z) has colour a.color iff (q + rbpar) is even
 #pragma unroll
       for (int q = 0; q < V; q++) {
         const C wv = q == 0 ? wl : uc[q - 1];
         const C ev = q == V - 1 ? er : uc[q + 1];
-        const int c = cl + q;
-        const bool in = c >= 1 && c <= n - 2;
-        if (MODE == kSweep) {
+        const bool in = inq[q];
+        if (MODE == kJacobi || MODE == kRB) {
           C nv = alpha * fc[q] + bx * (wv + ev) + by * (ys[q] + yn[q]) + bz * (um[q] + up[q]);
           if (has_gamma) nv += gamma * uc[q];
-          const bool upd = in && (a.color < 0 || ((c + y + z) & 1) == a.color);
+          // cl is even (V is), so the colour of column cl + q alternates with q
+          const bool upd = MODE == kJacobi ? in : (in && ((q + rbpar) & 1) == 0);
           res[q] = upd ? nv : uc[q];
         } else {
-          C rr = fc[q] - cd * uc[q] + cx * (wv + ev) + cy * (ys[q] + yn[q]) + cz * (um[q] + up[q]);
+          const C rr = fc[q] - cd * uc[q] + cx * (wv + ev) + cy * (ys[q] + yn[q]) + cz * (um[q] + up[q]);
           if (MODE == kResid) res[q] = in ? rr : (C)0;
-          if (MODE == kNorm && in) acc += (double)rr * (double)rr;
+          if (MODE == kNorm && in) sq += rr * rr;
         }
       }
-      if (MODE != kNorm && cl < pitch) vst((T *)a.out + (long long)z * P + (long long)y * pitch + cl, res);
+      if (MODE == kNorm) acc += (double)sq;
+      if (MODE != kNorm && cl < pitch) vst(outp, res);
+      outp += P;
 #pragma unroll
       for (int q = 0; q < V; q++) { um[q] = uc[q]; uc[q] = up[q]; }
     }
@@ -355,35 +401,47 @@ struct ArgsDC3 {
   double cd, cx, cy, cz;
 };
 
+// Pieces of the outer step's tile: u and e rows y0-1 .. y0+kTY with halo
+// chunks, f rows y0 .. y0+kTY-1.
+template <typename Ti, bool UPDATE> struct DCP {
+  static constexpr int NU = kDCWarps * kUChunks, NE = UPDATE ? kDCWarps * (DCL<Ti>::ECH + 2) : 0, NF = kTY * 32;
+  static constexpr int K = (NU + NE + NF + 32 * kDCWarps - 1) / (32 * kDCWarps);
+};
 template <typename Ti, bool UPDATE>
-__device__ __forceinline__ void stage_dc(unsigned char *slot, const ArgsDC3 &a, int p, int y0, int x0) {
+__device__ __forceinline__ void dc_pieces(Pieces<DCP<Ti, UPDATE>::K> &pc, const ArgsDC3 &a, int y0, int x0) {
   typedef DCL<Ti> L;
-  constexpr int NU = kDCWarps * kUChunks, NE = UPDATE ? kDCWarps * (L::ECH + 2) : 0, NF = kTY * 32;
+  typedef DCP<Ti, UPDATE> Q;
   constexpr int EV = 16 / (int)sizeof(Ti);  // e values per chunk
-  const bool pok = p >= 0 && p < a.n;
   const Ti *e = (const Ti *)a.e;
-  for (int i = threadIdx.x; i < NU + NE + NF; i += blockDim.x) {
-    if (i < NU) {
+  pc.anchor = (const unsigned char *)a.u;
+#pragma unroll
+  for (int k = 0; k < Q::K; k++) {
+    const int i = threadIdx.x + k * 32 * kDCWarps;
+    pc.soff[k] = -1;
+    pc.ok[k] = false;
+    pc.src[k] = (const unsigned char *)a.u;
+    pc.pstep[k] = a.plane * 8;
+    if (i < Q::NU) {
       const int rr = i / kUChunks, ch = i - rr * kUChunks;
       const int y = y0 - 1 + rr, x = x0 + (ch - 1) * 2;
-      const bool ok = pok && y >= 0 && y < a.n && x >= 0 && x + 2 <= a.pitch;
-      const double *src = ok ? a.u + (long long)p * a.plane + (long long)y * a.pitch + x : a.u;
-      cp_async16(slot + rr * kURowB + ch * 16, src, ok);
-    } else if (i < NU + NE) {
-      const int j = i - NU, rr = j / (L::ECH + 2), ch = j - rr * (L::ECH + 2);
+      pc.ok[k] = y >= 0 && y < a.n && x >= 0 && x + 2 <= a.pitch;
+      if (pc.ok[k]) pc.src[k] = (const unsigned char *)(a.u + (long long)y * a.pitch + x);
+      pc.soff[k] = rr * kURowB + ch * 16;
+    } else if (i < Q::NU + Q::NE) {
+      const int j = i - Q::NU, rr = j / (L::ECH + 2), ch = j - rr * (L::ECH + 2);
       const int y = y0 - 1 + rr, x = x0 + (ch - 1) * EV;
-      const bool ok = pok && y >= 0 && y < a.n && x >= 0 && x + EV <= a.pitchi;
-      const Ti *src = ok ? e + (long long)p * a.planei + (long long)y * a.pitchi + x : e;
-      cp_async16(slot + kDCWarps * kURowB + rr * L::ERowB + ch * 16, src, ok);
-    } else {
-      const int j = i - NU - NE, rr = j >> 5, ch = j & 31;
+      pc.ok[k] = y >= 0 && y < a.n && x >= 0 && x + EV <= a.pitchi;
+      pc.src[k] = (const unsigned char *)(pc.ok[k] ? e + (long long)y * a.pitchi + x : e);
+      pc.pstep[k] = a.planei * (long long)sizeof(Ti);
+      pc.soff[k] = kDCWarps * kURowB + rr * L::ERowB + ch * 16;
+    } else if (i < Q::NU + Q::NE + Q::NF) {
+      const int j = i - Q::NU - Q::NE, rr = j >> 5, ch = j & 31;
       const int y = y0 + rr, x = x0 + ch * 2;
-      const bool ok = pok && y < a.n && x + 2 <= a.pitch;
-      const double *src = ok ? a.f + (long long)p * a.plane + (long long)y * a.pitch + x : a.f;
-      cp_async16(slot + kDCWarps * kURowB + kDCWarps * L::ERowB + rr * kFRowB + ch * 16, src, ok);
+      pc.ok[k] = y < a.n && x + 2 <= a.pitch;
+      pc.src[k] = (const unsigned char *)(pc.ok[k] ? a.f + (long long)y * a.pitch + x : a.f);
+      pc.soff[k] = kDCWarps * kURowB + kDCWarps * L::ERowB + rr * kFRowB + ch * 16;
     }
   }
-  cp_async_commit();
 }
 
 template <typename Ti> __device__ __forceinline__ double e_at(const unsigned char *p) {
@@ -430,10 +488,13 @@ __global__ void __launch_bounds__(32 * kDCWarps) k3_dc(ArgsDC3 a) {
     }
   };
 
+  Pieces<DCP<Ti, UPDATE>::K> pc;
+  dc_pieces<Ti, UPDATE>(pc, a, y0, x0);
   const int zs = z0 - 2;  // first step: updates plane z0 - 1
+  pc.start(zs + 1);
   for (int k = 1; k <= kAhead; k++) {
     const int p = zs + k;
-    stage_dc<Ti, UPDATE>(slot(p + kDCRing), a, p <= z1 ? p : -1, y0, x0);
+    pc.issue(slot(p + kDCRing), p <= z1);
   }
 
   double um[2] = {0, 0}, uc[2] = {0, 0}, up[2] = {0, 0};
@@ -441,7 +502,7 @@ __global__ void __launch_bounds__(32 * kDCWarps) k3_dc(ArgsDC3 a) {
   for (int z = zs; z < z1; z++) {
     cp_async_wait<kAhead - 1>();  // plane z + 1 staged
     __syncthreads();              // (A) for everyone; plane z - 1's slot is free
-    stage_dc<Ti, UPDATE>(slot(z + kAhead + 1 + kDCRing), a, z + kAhead + 1 <= z1 ? z + kAhead + 1 : -1, y0, x0);
+    pc.issue(slot(z + kAhead + 1 + kDCRing), z + kAhead + 1 <= z1);
     double nv[2] = {0, 0}, nh = 0;
     if (row_ok) {
       update_row(z + 1, nv, nh);
@@ -480,12 +541,8 @@ __global__ void __launch_bounds__(32 * kDCWarps) k3_dc(ArgsDC3 a) {
       }
       if (d && cl < a.pitchi) {
         Ti *dp = d + (long long)z * a.planei + (long long)y * a.pitchi + cl;
-        if (sizeof(Ti) == 4) {
-          *(float2 *)dp = make_float2(rv[0], rv[1]);
-        } else {
-          __nv_bfloat162 b = __floats2bfloat162_rn(rv[0], rv[1]);
-          *(__nv_bfloat162 *)dp = b;
-        }
+        if (sizeof(Ti) == 4) *(float2 *)dp = make_float2(rv[0], rv[1]);
+        else *(unsigned *)dp = bf16x2_rne_bits(rv[0], rv[1]);
       }
     }
   }

@@ -163,3 +163,30 @@ def test_invalid_level_arguments():
         s.prolongate(-1)
     with pytest.raises(ValueError):
         s.set_rhs(np.zeros((8, 8)))
+
+
+def test_bf16_storage_rounds_to_nearest_even():
+    # BF16 fields are written with an integer round-to-nearest-even; compare
+    # with torch's CPU float32 -> bfloat16 conversion on values that are
+    # exact floats: ties at every exponent, neighbours of ties, subnormals,
+    # the overflow edge and random values over the whole range.
+    torch = pytest.importorskip("torch")
+    need_gpu()
+    from paper_1406_5369_gb300 import Solver
+    n = 65
+    s = Solver(2, n, precision="bf16_dc")
+    rng = np.random.default_rng(7)
+    bits = rng.integers(0, 2 ** 32, size=n * n, dtype=np.uint64).astype(np.uint32)
+    e = np.arange(n * n, dtype=np.uint32) % 254 + 1
+    ties = (e << 23) | (rng.integers(0, 2 ** 7, size=n * n, dtype=np.uint32) << 16) | 0x8000
+    special = np.array([0x00000001, 0x00008000, 0x00018000, 0x007fffff, 0x7f7fffff, 0x7f7f8000, 0x7f7f7fff,
+                        0x80008000, 0x3f808000, 0x3f818000, 0x3f80ffff], dtype=np.uint32)
+    pool = np.concatenate([bits[: n * n // 3], ties[: n * n // 3], ties[: n * n // 3] + 1, ties[: n * n // 3] - 1])
+    pool = pool[(pool & 0x7f800000) != 0x7f800000]  # finite values only
+    vals = np.zeros(n * n, dtype=np.uint32)
+    vals[: special.size] = special
+    vals[special.size:] = pool[: n * n - special.size]
+    a = vals.view(np.float32).astype(np.float64).reshape(n, n)
+    got = upload(s, 0, "f", a)
+    want = torch.from_numpy(a.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(got, want)
