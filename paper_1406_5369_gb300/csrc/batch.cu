@@ -23,21 +23,23 @@
 
 #include "ctx.h"
 #include "kernels.cuh"
+#include "outer2d.cuh"
 
 namespace mg {
 namespace bz {
 
 constexpr int kPartBlocks = 128;  // norm partial sums per problem
 
-// One level of one problem.
+// One level of one problem. The stencil is stored in both compute types,
+// converted on the host: FP64 -> FP32 conversions run on the slow FP64 pipe
+// of this GPU, so kernels must not redo them per thread.
 struct BOp {
   void *u[2];
   void *f;
   void *r;
-  const void *kf[3];
+  Sten<double> sd;
+  Sten<float> sf;
   Geo g;
-  double c[3];
-  double inv_h2;
   int cur;  // live solution buffer at the start of the step
 };
 
@@ -53,28 +55,16 @@ struct BXfer {
 struct BOuter {
   double *u;
   const double *f;
-  const void *kf[3];
+  Sten<double> sd;
   Geo go;
-  double c[3];
-  double inv_h2;
   void *d;        // inner defect (inner f)
   const void *e;  // inner correction (live inner u)
   Geo gi;
 };
 
-template <typename C> __device__ __forceinline__ Sten<C> sten_dev(const double (&c)[3], double inv_h2,
-                                                                   const void *const (&kf)[3], int dim) {
-  Sten<C> s;
-  s.kf0 = (const C *)kf[0];
-  s.kf1 = (const C *)kf[1];
-  s.kf2 = (const C *)kf[2];
-  s.c0 = (C)c[0];
-  s.c1 = (C)c[1];
-  s.c2 = (C)c[2];
-  s.inv_h2 = (C)inv_h2;
-  s.diag = (C)(2.0 * (c[0] + c[1] + (dim == 3 ? c[2] : 0.0)) * inv_h2);
-  return s;
-}
+template <typename C> __device__ __forceinline__ const Sten<C> &sten_of_op(const BOp &o);
+template <> __device__ __forceinline__ const Sten<double> &sten_of_op<double>(const BOp &o) { return o.sd; }
+template <> __device__ __forceinline__ const Sten<float> &sten_of_op<float>(const BOp &o) { return o.sf; }
 
 // Grid: x covers columns, y rows, z = (problem * n + plane) in 3D or problem in 2D.
 template <int DIM> __device__ __forceinline__ Idx bnode(const Geo &g, int &p) {
@@ -95,7 +85,7 @@ template <int DIM> __device__ __forceinline__ Idx bnode(const Geo &g, int &p) {
 }
 
 template <int DIM, typename T, bool VAR>
-__global__ void kb_rbgs_half(const BOp *__restrict__ ops, Geo g, int color, int flip, double omega) {
+__global__ void kb_rbgs_half(const BOp *__restrict__ ops, Geo g, int color, int flip, double omega_d, float omega_f) {
   typedef typename CT<T>::type C;
   int pi;
   Idx t = bnode<DIM>(g, pi);
@@ -103,14 +93,14 @@ __global__ void kb_rbgs_half(const BOp *__restrict__ ops, Geo g, int color, int 
   if (!t.interior || ((t.i + t.j + t.k) & 1) != color) return;
   T *u = (T *)o.u[o.cur ^ flip];
   const T *f = (const T *)o.f;
-  Sten<C> s = sten_dev<C>(o.c, o.inv_h2, o.kf, DIM);
+  const Sten<C> s = sten_of_op<C>(o);
   C Au, dg;
   apply_at<DIM, VAR>(u, t.p, g, s, Au, dg);
-  st(u + t.p, ld(u + t.p) + (C)omega * (ld(f + t.p) - Au) / dg);
+  st(u + t.p, ld(u + t.p) + pick<C>(omega_d, omega_f) * (ld(f + t.p) - Au) / dg);
 }
 
 template <int DIM, typename T, bool VAR>
-__global__ void kb_jacobi(const BOp *__restrict__ ops, Geo g, int flip, double omega) {
+__global__ void kb_jacobi(const BOp *__restrict__ ops, Geo g, int flip, double omega_d, float omega_f) {
   typedef typename CT<T>::type C;
   int pi;
   Idx t = bnode<DIM>(g, pi);
@@ -119,10 +109,10 @@ __global__ void kb_jacobi(const BOp *__restrict__ ops, Geo g, int flip, double o
   const T *uin = (const T *)o.u[o.cur ^ flip];
   T *uout = (T *)o.u[o.cur ^ flip ^ 1];
   const T *f = (const T *)o.f;
-  Sten<C> s = sten_dev<C>(o.c, o.inv_h2, o.kf, DIM);
+  const Sten<C> s = sten_of_op<C>(o);
   C Au, dg;
   apply_at<DIM, VAR>(uin, t.p, g, s, Au, dg);
-  st(uout + t.p, ld(uin + t.p) + (C)omega * (ld(f + t.p) - Au) / dg);
+  st(uout + t.p, ld(uin + t.p) + pick<C>(omega_d, omega_f) * (ld(f + t.p) - Au) / dg);
 }
 
 template <int DIM, typename T, bool VAR>
@@ -133,7 +123,7 @@ __global__ void kb_residual(const BOp *__restrict__ ops, Geo g, int flip) {
   const BOp &o = ops[pi];
   if (!t.interior) return;
   const T *u = (const T *)o.u[o.cur ^ flip];
-  Sten<C> s = sten_dev<C>(o.c, o.inv_h2, o.kf, DIM);
+  const Sten<C> s = sten_of_op<C>(o);
   C Au, dg;
   apply_at<DIM, VAR>(u, t.p, g, s, Au, dg);
   st((T *)o.r + t.p, ld((const T *)o.f + t.p) - Au);
@@ -196,7 +186,7 @@ __global__ void kb_prolong(const BXfer *__restrict__ xs, Geo gc, Geo gf) {
 template <int DIM, typename Ti, bool VAR>
 __global__ void kb_dc_residual(const BOuter *__restrict__ os, double *__restrict__ partials) {
   const BOuter &o = os[blockIdx.y];
-  Sten<double> s = sten_dev<double>(o.c, o.inv_h2, o.kf, DIM);
+  const Sten<double> s = o.sd;
   int m = o.go.n - 2;
   long long total = (long long)m * m * (DIM == 3 ? m : 1);
   double acc = 0.0;
@@ -208,7 +198,7 @@ __global__ void kb_dc_residual(const BOuter *__restrict__ os, double *__restrict
     apply_at<DIM, VAR>(o.u, p, o.go, s, Au, dg);
     double r = o.f[p] - Au;
     acc += r * r;
-    if (o.d) st((Ti *)o.d + q, (float)r);
+    if (o.d) st((Ti *)o.d + q, oz::d2f_bits(r));  // truncation to FP32 without the FP64 pipe
   }
   acc = block_sum(acc);
   if (threadIdx.x == 0) partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = acc;
@@ -223,7 +213,7 @@ __global__ void kb_dc_update(const BOuter *__restrict__ os) {
        t += (long long)gridDim.x * blockDim.x) {
     long long p = interior_node<DIM>(t, m, o.go);
     long long q = interior_node<DIM>(t, m, o.gi);
-    o.u[p] += (double)ld((const Ti *)o.e + q);
+    o.u[p] += oz::f2d_bits(ld((const Ti *)o.e + q));
   }
 }
 
@@ -231,7 +221,7 @@ __global__ void kb_dc_update(const BOuter *__restrict__ os) {
 template <int DIM, bool VAR>
 __global__ void kb_norm(const BOp *__restrict__ ops, double *__restrict__ partials) {
   const BOp &o = ops[blockIdx.y];
-  Sten<double> s = sten_dev<double>(o.c, o.inv_h2, o.kf, DIM);
+  const Sten<double> s = o.sd;
   const double *u = (const double *)o.u[o.cur];
   const double *f = (const double *)o.f;
   int m = o.g.n - 2;
@@ -350,10 +340,9 @@ BOp make_op(const Level &L) {
   o.u[1] = L.u[1];
   o.f = L.f;
   o.r = L.r;
-  for (int d = 0; d < 3; d++) o.kf[d] = L.kf[d];
+  o.sd = sten_of<double>(L);
+  o.sf = sten_of<float>(L);
   o.g = geo_of(L);
-  for (int d = 0; d < 3; d++) o.c[d] = L.c[d];
-  o.inv_h2 = L.inv_h2;
   o.cur = L.cur;
   return o;
 }
@@ -393,8 +382,8 @@ cudaError_t launch_group_op(int what, const std::vector<BOp> &items, mg_batch *b
     DISPATCH_T(dtype, if (var) K<3, T, true><<<gr, blk, 0, s>>>(__VA_ARGS__);             \
                else K<3, T, false><<<gr, blk, 0, s>>>(__VA_ARGS__));                      \
   }
-    if (what == 0) { OPK(kb_rbgs_half, dev, g, color, flip, omega) }
-    else if (what == 1) { OPK(kb_jacobi, dev, g, flip, omega) }
+    if (what == 0) { OPK(kb_rbgs_half, dev, g, color, flip, omega, (float)omega) }
+    else if (what == 1) { OPK(kb_jacobi, dev, g, flip, omega, (float)omega) }
     else if (what == 2) { OPK(kb_residual, dev, g, flip) }
     else {
       if (dim == 2) { DISPATCH_T(dtype, kb_zero<2, T><<<gr, blk, 0, s>>>(dev, g, flip)) }
@@ -577,10 +566,8 @@ BOuter make_outer(mg_ctx *c, bool with_d, bool with_e) {
   Level &I = c->lv[0];
   o.u = (double *)O.u[O.cur];
   o.f = (const double *)O.f;
-  for (int d = 0; d < 3; d++) o.kf[d] = O.kf[d];
+  o.sd = sten_of<double>(O);
   o.go = geo_of(O);
-  for (int d = 0; d < 3; d++) o.c[d] = O.c[d];
-  o.inv_h2 = O.inv_h2;
   o.d = with_d ? I.f : nullptr;
   o.e = with_e ? I.u[I.cur] : nullptr;
   o.gi = geo_of(I);
