@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <functional>
 #include <new>
 #include <map>
 #include <vector>
@@ -24,11 +25,13 @@
 #include "ctx.h"
 #include "kernels.cuh"
 #include "outer2d.cuh"
+#include "stencil3d.cuh"
 
 namespace mg {
 namespace bz {
 
-constexpr int kPartBlocks = 128;  // norm partial sums per problem
+constexpr int kPartBlocks = 128;   // blocks (one partial sum each) of the generic norm kernels per problem
+constexpr int kSlots = 1024;       // partial-sum slots per problem (the streaming kernels write up to this many)
 
 // One level of one problem. The stencil is stored in both compute types,
 // converted on the host: FP64 -> FP32 conversions run on the slow FP64 pipe
@@ -60,6 +63,7 @@ struct BOuter {
   void *d;        // inner defect (inner f)
   const void *e;  // inner correction (live inner u)
   Geo gi;
+  double *partials;  // this problem's partial-sum slots
 };
 
 template <typename C> __device__ __forceinline__ const Sten<C> &sten_of_op(const BOp &o);
@@ -184,7 +188,7 @@ __global__ void kb_prolong(const BXfer *__restrict__ xs, Geo gc, Geo gf) {
 // Per-problem partial sums of the FP64 outer residual squared (kPartBlocks
 // blocks per problem, fixed partition), writing the inner defect.
 template <int DIM, typename Ti, bool VAR>
-__global__ void kb_dc_residual(const BOuter *__restrict__ os, double *__restrict__ partials) {
+__global__ void kb_dc_residual(const BOuter *__restrict__ os) {
   const BOuter &o = os[blockIdx.y];
   const Sten<double> s = o.sd;
   int m = o.go.n - 2;
@@ -201,7 +205,7 @@ __global__ void kb_dc_residual(const BOuter *__restrict__ os, double *__restrict
     if (o.d) st((Ti *)o.d + q, oz::d2f_bits(r));  // truncation to FP32 without the FP64 pipe
   }
   acc = block_sum(acc);
-  if (threadIdx.x == 0) partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = acc;
+  if (threadIdx.x == 0) o.partials[blockIdx.x] = acc;
 }
 
 template <int DIM, typename Ti>
@@ -236,16 +240,20 @@ __global__ void kb_norm(const BOp *__restrict__ ops, double *__restrict__ partia
     acc += r * r;
   }
   acc = block_sum(acc);
-  if (threadIdx.x == 0) partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = acc;
+  if (threadIdx.x == 0) partials[(long long)blockIdx.y * kSlots + blockIdx.x] = acc;
 }
 
-// One block per problem: fixed-order sum of its partials, norm out.
-__global__ void kb_finalize(const double *__restrict__ partials, int per, double *__restrict__ norms) {
-  __shared__ double buf[kPartBlocks];
+// One block per problem: fixed-order sum of its kSlots partial slots
+// (unused slots hold zero), norm out.
+__global__ void kb_finalize(const double *__restrict__ partials, double *__restrict__ norms) {
+  __shared__ double buf[256];
   int t = threadIdx.x;
-  buf[t] = partials[(long long)blockIdx.x * per + t];
+  const double *p = partials + (long long)blockIdx.x * kSlots;
+  double a = 0.0;
+  for (int i = t; i < kSlots; i += 256) a += p[i];
+  buf[t] = a;
   __syncthreads();
-  for (int s = kPartBlocks / 2; s > 0; s >>= 1) {
+  for (int s = 128; s > 0; s >>= 1) {
     if (t < s) buf[t] += buf[t + s];
     __syncthreads();
   }
@@ -286,7 +294,7 @@ struct mg_batch {
   char *ws;
   size_t ws_bytes;
   size_t desc_bytes;            // descriptor area at the start of ws
-  double *partials;             // maxp * kPartBlocks
+  double *partials;             // maxp * kSlots
   double *norms;                // maxp
   cudaStream_t stream;
   bool have_opts;
@@ -303,9 +311,12 @@ struct mg_batch {
 namespace {
 
 size_t desc_area_bytes(int maxp) {
-  // per problem and level: one BOp, one BXfer, plus a coarse record and an outer record
-  size_t per = (size_t)kMaxLevels * (sizeof(BOp) + 2 * sizeof(BXfer)) + coarse_args_bytes() + sizeof(BOuter) + 1024;
-  return align256((size_t)maxp * per * 2);
+  // Room for about one V-cycle's records of every problem (12 levels, a few
+  // records per level, the coarse record and the outer records); when a step
+  // needs more, push() waits for the queued kernels and reuses the area.
+  size_t rec = std::max(std::max(sizeof(BOp), sizeof(fz::Args2D)), std::max(sizeof(z3::Args3), sizeof(z3::ArgsDC3)));
+  size_t per = (size_t)12 * 6 * rec + coarse_args_bytes() + 2 * sizeof(BOuter) + 1024;
+  return align256((size_t)maxp * per);
 }
 
 // Stages `bytes` of descriptors and copies them to the next device slot on
@@ -313,7 +324,13 @@ size_t desc_area_bytes(int maxp) {
 // the device address, NULL if the area is exhausted or the copy failed.
 void *push(mg_batch *b, const void *src, size_t bytes) {
   size_t off = align256(b->dev_off);
-  if (off + bytes > b->desc_bytes) return nullptr;
+  if (bytes > b->desc_bytes) return nullptr;
+  if (off + bytes > b->desc_bytes) {
+    // area full: once the kernels queued so far have read their
+    // descriptors, the whole area (and its pinned staging) is free again
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return nullptr;
+    off = 0;
+  }
   memcpy(b->pinned + off, src, bytes);
   if (cudaMemcpyAsync(b->ws + off, b->pinned + off, bytes, cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
     return nullptr;
@@ -439,68 +456,233 @@ cudaError_t launch_group_xfer(bool restrict_, const std::vector<BXfer> &items, m
     if (e_ != cudaSuccess) return bfail(MG_ECUDA, msg, e_);  \
   } while (0)
 
+// One (problem, level) entry of a level-size group. `fast` is decided from
+// the problem alone (its stencil, smoother, storage type and sizes), so a
+// problem runs the same kernels - and gets the same result - whatever else
+// is in the batch. `flip` counts the live-buffer swaps in this cycle.
+struct Item {
+  mg_ctx *c;
+  int l;
+  bool fast;
+  int flip;
+};
+
+bool fast_level(const mg_ctx *c, int l) {
+  const Level &L = c->lv[l], &C = c->lv[l + 1];
+  const mg_options &o = c->opt;
+  if (!o.fuse) return false;
+  if (L.dim == 2) return o.smoother == MG_RBGS && d2::fused_ok(L, C, o.nu1) && d2::fused_ok(L, C, o.nu2);
+  return d3::z_ok(L) && d3::transfer_ok(L, C);
+}
+
+template <typename R> const R *push_list(mg_batch *b, const std::vector<R> &v) {
+  return (const R *)push(b, v.data(), sizeof(R) * v.size());
+}
+
+// Streaming / fused kernels of the fast items of one group: pre-smoothing,
+// residual and restriction (descend) or interpolation and post-smoothing.
+mg_status fast_descend(mg_batch *b, std::vector<Item *> &F, bool zero0) {
+  if (F.empty()) return MG_OK;
+  const mg_options &o = b->opt;
+  const Level &L0 = F[0]->c->lv[F[0]->l], &C0 = F[0]->c->lv[F[0]->l + 1];
+  cudaStream_t s = b->stream;
+  if (L0.dim == 2) {
+    for (int zero = 0; zero <= 1; zero++) {
+      std::vector<fz::Args2D> recs;
+      for (Item *it : F) {
+        bool z = it->l > 0 || zero0;
+        if (z != (zero != 0)) continue;
+        Level &L = it->c->lv[it->l], &C = it->c->lv[it->l + 1];
+        recs.push_back(d2::fused_record(L, C, o.omega, L.u[L.cur ^ it->flip], L.u[L.cur ^ it->flip ^ 1], nullptr, C.f));
+      }
+      if (recs.empty()) continue;
+      const fz::Args2D *dev = push_list(b, recs);
+      if (!dev) return bfail(MG_ENOMEM, "batch descriptor area exhausted");
+      BLAUNCH("batched fused pre-smoothing", d2::pre_fused_list(L0, C0, dev, (int)recs.size(), zero != 0, o.nu1, s));
+      b->launches++;
+    }
+    for (Item *it : F) it->flip ^= 1;
+    return MG_OK;
+  }
+  // 3D: zero the levels that start from zero, nu1 sweeps, residual, restriction
+  {
+    std::vector<BOp> zops;
+    for (Item *it : F)
+      if (it->l > 0 || zero0) {
+        BOp op = make_op(it->c->lv[it->l]);
+        op.cur ^= it->flip;
+        zops.push_back(op);
+      }
+    if (!zops.empty()) BLAUNCH("batched zero", launch_group_op(3, zops, b, 3, L0.dtype, false, 0, 0, 0.0));
+  }
+  auto sweeps = [&](int nu) -> mg_status {
+    for (int k = 0; k < nu; k++) {
+      std::vector<z3::Args3> recs;
+      for (Item *it : F) {
+        Level &L = it->c->lv[it->l];
+        void *in = L.u[L.cur ^ it->flip];
+        recs.push_back(d3::stencil_record(L, o.omega, in, o.smoother == MG_RBGS ? in : L.u[L.cur ^ it->flip ^ 1], L.f));
+      }
+      const z3::Args3 *dev = push_list(b, recs);
+      if (!dev) return bfail(MG_ENOMEM, "batch descriptor area exhausted");
+      if (o.smoother == MG_RBGS) {
+        BLAUNCH("batched 3D RBGS", d3::z_sweep_list(L0, dev, (int)recs.size(), 0, s));
+        BLAUNCH("batched 3D RBGS", d3::z_sweep_list(L0, dev, (int)recs.size(), 1, s));
+        b->launches += 2;
+      } else {
+        BLAUNCH("batched 3D Jacobi", d3::z_sweep_list(L0, dev, (int)recs.size(), -1, s));
+        b->launches++;
+        for (Item *it : F) it->flip ^= 1;
+      }
+    }
+    return MG_OK;
+  };
+  mg_status st;
+  if ((st = sweeps(o.nu1))) return st;
+  std::vector<z3::Args3> rrec;
+  std::vector<z3::ArgsT3> xrec;
+  for (Item *it : F) {
+    Level &L = it->c->lv[it->l], &C = it->c->lv[it->l + 1];
+    rrec.push_back(d3::stencil_record(L, o.omega, L.u[L.cur ^ it->flip], L.r, L.f));
+    z3::ArgsT3 x;
+    memset(&x, 0, sizeof x);
+    x.src = L.r;
+    x.dst = C.f;
+    xrec.push_back(x);
+  }
+  const z3::Args3 *dr = push_list(b, rrec);
+  if (!dr) return bfail(MG_ENOMEM, "batch descriptor area exhausted");
+  BLAUNCH("batched 3D residual", d3::z_residual_list(L0, dr, (int)rrec.size(), s));
+  const z3::ArgsT3 *dx = push_list(b, xrec);
+  if (!dx) return bfail(MG_ENOMEM, "batch descriptor area exhausted");
+  BLAUNCH("batched 3D restriction", d3::z_transfer_list(true, L0, C0, dx, (int)xrec.size(), s));
+  b->launches += 2;
+  return MG_OK;
+}
+
+mg_status fast_ascend(mg_batch *b, std::vector<Item *> &F, const std::function<int(mg_ctx *, int)> &flip_of) {
+  if (F.empty()) return MG_OK;
+  const mg_options &o = b->opt;
+  const Level &L0 = F[0]->c->lv[F[0]->l], &C0 = F[0]->c->lv[F[0]->l + 1];
+  cudaStream_t s = b->stream;
+  if (L0.dim == 2) {
+    std::vector<fz::Args2D> recs;
+    for (Item *it : F) {
+      Level &L = it->c->lv[it->l], &C = it->c->lv[it->l + 1];
+      const void *ec = C.u[C.cur ^ flip_of(it->c, it->l + 1)];
+      recs.push_back(d2::fused_record(L, C, o.omega, L.u[L.cur ^ it->flip], L.u[L.cur ^ it->flip ^ 1], ec, nullptr));
+    }
+    const fz::Args2D *dev = push_list(b, recs);
+    if (!dev) return bfail(MG_ENOMEM, "batch descriptor area exhausted");
+    BLAUNCH("batched fused post-smoothing", d2::post_fused_list(L0, C0, dev, (int)recs.size(), o.nu2, s));
+    b->launches++;
+    for (Item *it : F) it->flip ^= 1;
+    return MG_OK;
+  }
+  std::vector<z3::ArgsT3> xrec;
+  for (Item *it : F) {
+    Level &L = it->c->lv[it->l], &C = it->c->lv[it->l + 1];
+    z3::ArgsT3 x;
+    memset(&x, 0, sizeof x);
+    x.src = C.u[C.cur ^ flip_of(it->c, it->l + 1)];
+    x.dst = L.u[L.cur ^ it->flip];
+    xrec.push_back(x);
+  }
+  const z3::ArgsT3 *dx = push_list(b, xrec);
+  if (!dx) return bfail(MG_ENOMEM, "batch descriptor area exhausted");
+  BLAUNCH("batched 3D interpolation", d3::z_transfer_list(false, L0, C0, dx, (int)xrec.size(), s));
+  b->launches++;
+  for (int k = 0; k < o.nu2; k++) {
+    std::vector<z3::Args3> recs;
+    for (Item *it : F) {
+      Level &L = it->c->lv[it->l];
+      void *in = L.u[L.cur ^ it->flip];
+      recs.push_back(d3::stencil_record(L, o.omega, in, o.smoother == MG_RBGS ? in : L.u[L.cur ^ it->flip ^ 1], L.f));
+    }
+    const z3::Args3 *dev = push_list(b, recs);
+    if (!dev) return bfail(MG_ENOMEM, "batch descriptor area exhausted");
+    if (o.smoother == MG_RBGS) {
+      BLAUNCH("batched 3D RBGS", d3::z_sweep_list(L0, dev, (int)recs.size(), 0, s));
+      BLAUNCH("batched 3D RBGS", d3::z_sweep_list(L0, dev, (int)recs.size(), 1, s));
+      b->launches += 2;
+    } else {
+      BLAUNCH("batched 3D Jacobi", d3::z_sweep_list(L0, dev, (int)recs.size(), -1, s));
+      b->launches++;
+      for (Item *it : F) it->flip ^= 1;
+    }
+  }
+  return MG_OK;
+}
+
 // One V-cycle of every problem in `ps` (levels grouped by size). zero0:
 // level 0 starts from zero (first inner cycle of a defect-correction step).
 mg_status batched_vcycle(mg_batch *b, const std::vector<mg_ctx *> &ps, bool zero0) {
   const int dim = b->dim;
   const int top_n = coarse_top_n(dim, b->fp64);
   const mg_options &o = b->opt;
-  // level -> list, for every fine level size (size above the coarse threshold)
-  std::map<int, std::vector<std::pair<mg_ctx *, int>>, std::greater<int>> fine;
+  // level size -> items, for every fine level size (above the coarse threshold)
+  std::map<int, std::vector<Item>, std::greater<int>> fine;
   for (mg_ctx *c : ps)
     for (int l = 0; l < c->nl; l++)
-      if (c->lv[l].n > top_n) fine[c->lv[l].n].push_back({c, l});
-  // Jacobi sweeps flip the live buffer of a level; track the parity per size
-  std::map<int, int> flip;
-  auto ops_of = [&](const std::vector<std::pair<mg_ctx *, int>> &v, bool only_zero, bool &any) {
+      if (c->lv[l].n > top_n) fine[c->lv[l].n].push_back({c, l, fast_level(c, l), 0});
+  std::map<std::pair<const mg_ctx *, int>, const Item *> where;
+  for (auto &kv : fine)
+    for (const Item &it : kv.second) where[{it.c, it.l}] = &it;
+  auto flip_of = [&](mg_ctx *c, int l) {
+    auto f = where.find({c, l});
+    return f == where.end() ? 0 : f->second->flip;
+  };
+  // generic (one thread per node) kernels for the items that are not fast
+  auto ops_of = [&](const std::vector<Item *> &v, bool only_zero) {
     std::vector<BOp> out;
-    any = false;
-    for (auto &pl : v) {
-      bool z = pl.second > 0 || zero0;
+    for (Item *it : v) {
+      bool z = it->l > 0 || zero0;
       if (only_zero && !z) continue;
-      out.push_back(make_op(pl.first->lv[pl.second]));
-      any = true;
+      out.push_back(make_op(it->c->lv[it->l]));
     }
     return out;
   };
-  auto smooth = [&](int n, const std::vector<std::pair<mg_ctx *, int>> &v, int sweeps) -> mg_status {
-    bool any;
-    std::vector<BOp> ops = ops_of(v, false, any);
-    if (ops.empty()) return MG_OK;
-    const Level &L0 = v[0].first->lv[v[0].second];
+  auto smooth = [&](std::vector<Item *> &v, int sweeps) -> mg_status {
+    if (v.empty()) return MG_OK;
+    std::vector<BOp> ops = ops_of(v, false);
+    const Level &L0 = v[0]->c->lv[v[0]->l];
     bool var = L0.kf[0] != nullptr;
     for (int k = 0; k < sweeps; k++) {
+      int flip = v[0]->flip;  // equal across the generic items of a group
       if (o.smoother == MG_RBGS) {
-        BLAUNCH("batched RBGS", launch_group_op(0, ops, b, dim, L0.dtype, var, 0, flip[n], o.omega));
-        BLAUNCH("batched RBGS", launch_group_op(0, ops, b, dim, L0.dtype, var, 1, flip[n], o.omega));
+        BLAUNCH("batched RBGS", launch_group_op(0, ops, b, dim, L0.dtype, var, 0, flip, o.omega));
+        BLAUNCH("batched RBGS", launch_group_op(0, ops, b, dim, L0.dtype, var, 1, flip, o.omega));
       } else {
-        BLAUNCH("batched Jacobi", launch_group_op(1, ops, b, dim, L0.dtype, var, 0, flip[n], o.omega));
-        flip[n] ^= 1;
+        BLAUNCH("batched Jacobi", launch_group_op(1, ops, b, dim, L0.dtype, var, 0, flip, o.omega));
+        for (Item *it : v) it->flip ^= 1;
       }
     }
     return MG_OK;
   };
   mg_status st;
+  std::vector<int> sizes;
   // descend over the fine sizes
   for (auto &kv : fine) {
-    int n = kv.first;
-    auto &v = kv.second;
-    const Level &L0 = v[0].first->lv[v[0].second];
-    bool any;
-    std::vector<BOp> zops = ops_of(v, true, any);
-    if (any) BLAUNCH("batched zero", launch_group_op(3, zops, b, dim, L0.dtype, false, 0, flip[n], 0.0));
-    if ((st = smooth(n, v, o.nu1))) return st;
-    std::vector<BOp> ops = ops_of(v, false, any);
-    BLAUNCH("batched residual", launch_group_op(2, ops, b, dim, L0.dtype, L0.kf[0] != nullptr, 0, flip[n], 0.0));
+    sizes.push_back(kv.first);
+    std::vector<Item *> G, F;
+    for (Item &it : kv.second) (it.fast ? F : G).push_back(&it);
+    if ((st = fast_descend(b, F, zero0))) return st;
+    if (G.empty()) continue;
+    const Level &L0 = G[0]->c->lv[G[0]->l];
+    std::vector<BOp> zops = ops_of(G, true);
+    if (!zops.empty()) BLAUNCH("batched zero", launch_group_op(3, zops, b, dim, L0.dtype, false, 0, G[0]->flip, 0.0));
+    if ((st = smooth(G, o.nu1))) return st;
+    std::vector<BOp> ops = ops_of(G, false);
+    BLAUNCH("batched residual", launch_group_op(2, ops, b, dim, L0.dtype, L0.kf[0] != nullptr, 0, G[0]->flip, 0.0));
     std::vector<BXfer> xs;
     int tc = F64;
-    for (auto &pl : v) {
-      const Level &F = pl.first->lv[pl.second];
-      const Level &C = pl.first->lv[pl.second + 1];
+    for (Item *it : G) {
+      const Level &Fl = it->c->lv[it->l];
+      const Level &C = it->c->lv[it->l + 1];
       BXfer x;
-      x.src = F.r;
+      x.src = Fl.r;
       x.dst = C.f;
-      x.gf = geo_of(F);
+      x.gf = geo_of(Fl);
       x.gc = geo_of(C);
       xs.push_back(x);
       tc = C.dtype;
@@ -529,37 +711,37 @@ mg_status batched_vcycle(mg_batch *b, const std::vector<mg_ctx *> &ps, bool zero
     b->launches++;
   }
   // ascend
-  std::vector<int> sizes;
-  for (auto &kv : fine) sizes.push_back(kv.first);
   std::reverse(sizes.begin(), sizes.end());
   for (int n : sizes) {
-    auto &v = fine[n];
-    const Level &L0 = v[0].first->lv[v[0].second];
+    std::vector<Item *> G, F;
+    for (Item &it : fine[n]) (it.fast ? F : G).push_back(&it);
+    if ((st = fast_ascend(b, F, flip_of))) return st;
+    if (G.empty()) continue;
+    const Level &L0 = G[0]->c->lv[G[0]->l];
     std::vector<BXfer> xs;
     int tc = F64;
-    for (auto &pl : v) {
-      Level &F = pl.first->lv[pl.second];
-      Level &C = pl.first->lv[pl.second + 1];
+    for (Item *it : G) {
+      Level &Fl = it->c->lv[it->l];
+      Level &C = it->c->lv[it->l + 1];
       BXfer x;
-      int cflip = C.n > top_n ? flip[C.n] : 0;
-      x.src = C.u[C.cur ^ cflip];
-      x.dst = F.u[F.cur ^ flip[n]];
-      x.gf = geo_of(F);
+      x.src = C.u[C.cur ^ flip_of(it->c, it->l + 1)];
+      x.dst = Fl.u[Fl.cur ^ it->flip];
+      x.gf = geo_of(Fl);
       x.gc = geo_of(C);
       xs.push_back(x);
       tc = C.dtype;
     }
     BLAUNCH("batched interpolation", launch_group_xfer(false, xs, b, dim, L0.dtype, tc));
-    if ((st = smooth(n, v, o.nu2))) return st;
+    if ((st = smooth(G, o.nu2))) return st;
   }
-  // commit the live-buffer flips of Jacobi levels
+  // commit the live-buffer swaps
   for (auto &kv : fine)
-    if (flip[kv.first])
-      for (auto &pl : kv.second) pl.first->lv[pl.second].cur ^= 1;
+    for (Item &it : kv.second)
+      if (it.flip & 1) it.c->lv[it.l].cur ^= 1;
   return MG_OK;
 }
 
-BOuter make_outer(mg_ctx *c, bool with_d, bool with_e) {
+BOuter make_outer(mg_ctx *c, bool with_d, bool with_e, double *partials) {
   BOuter o;
   memset(&o, 0, sizeof o);
   Level &O = c->dc ? c->outer : c->lv[0];
@@ -571,63 +753,119 @@ BOuter make_outer(mg_ctx *c, bool with_d, bool with_e) {
   o.d = with_d ? I.f : nullptr;
   o.e = with_e ? I.u[I.cur] : nullptr;
   o.gi = geo_of(I);
+  o.partials = partials;
   return o;
+}
+
+bool fast_outer(const mg_ctx *c) {
+  return c->opt.fuse && (c->dim == 2 ? d2::outer_ok(c->outer, c->lv[0]) : d3::outer_ok(c->outer, c->lv[0]));
+}
+
+// Defect-correction outer step of every problem in `ps`: with `update`,
+// u += e (the live inner solution) first; then the FP64 residual, written as
+// the next inner defect, and its norm into b->norms[i] (i = position in ps).
+// Fast problems run the fused streaming step (out-of-place update, so their
+// outer live buffer swaps); the others the generic update and residual.
+mg_status batched_outer(mg_batch *b, const std::vector<mg_ctx *> &ps, bool update) {
+  int P = (int)ps.size();
+  const int dim = b->dim;
+  bool var = ps[0]->variable;
+  BCK("clear partials", cudaMemsetAsync(b->partials, 0, sizeof(double) * (size_t)P * kSlots, b->stream));
+  std::vector<BOuter> gen;
+  std::map<int, std::vector<std::pair<int, mg_ctx *>>> fast;  // outer size -> (position, problem)
+  for (int i = 0; i < P; i++) {
+    mg_ctx *c = ps[i];
+    if (fast_outer(c)) fast[c->outer.n].push_back({i, c});
+    else gen.push_back(make_outer(c, true, update, b->partials + (size_t)i * kSlots));
+  }
+  cudaStream_t s = b->stream;
+  int ti = ps[0]->lv[0].dtype;
+  if (!gen.empty()) {
+    const BOuter *dev = (const BOuter *)push(b, gen.data(), sizeof(BOuter) * gen.size());
+    if (!dev) return bfail(MG_ENOMEM, "batch descriptor area exhausted");
+    dim3 gr(kPartBlocks, (unsigned)gen.size());
+    if (update) {
+      if (dim == 2) {
+        if (ti == F32) kb_dc_update<2, float><<<gr, 256, 0, s>>>(dev);
+        else kb_dc_update<2, bf16><<<gr, 256, 0, s>>>(dev);
+      } else {
+        if (ti == F32) kb_dc_update<3, float><<<gr, 256, 0, s>>>(dev);
+        else kb_dc_update<3, bf16><<<gr, 256, 0, s>>>(dev);
+      }
+      BCK("batched update", cudaGetLastError());
+      b->launches++;
+    }
+    if (dim == 2) {
+      if (ti == F32) { if (var) kb_dc_residual<2, float, true><<<gr, 256, 0, s>>>(dev); else kb_dc_residual<2, float, false><<<gr, 256, 0, s>>>(dev); }
+      else { if (var) kb_dc_residual<2, bf16, true><<<gr, 256, 0, s>>>(dev); else kb_dc_residual<2, bf16, false><<<gr, 256, 0, s>>>(dev); }
+    } else {
+      if (ti == F32) { if (var) kb_dc_residual<3, float, true><<<gr, 256, 0, s>>>(dev); else kb_dc_residual<3, float, false><<<gr, 256, 0, s>>>(dev); }
+      else { if (var) kb_dc_residual<3, bf16, true><<<gr, 256, 0, s>>>(dev); else kb_dc_residual<3, bf16, false><<<gr, 256, 0, s>>>(dev); }
+    }
+    BCK("batched outer residual", cudaGetLastError());
+    b->launches++;
+  }
+  for (auto &kv : fast) {
+    auto &v = kv.second;
+    const Level &O0 = v[0].second->outer, &I0 = v[0].second->lv[0];
+    int np = 0;
+    if (dim == 2) {
+      std::vector<oz::ArgsOuter> recs;
+      for (auto &pc : v) {
+        mg_ctx *c = pc.second;
+        Level &O = c->outer, &I = c->lv[0];
+        oz::ArgsOuter r = d2::outer_record(O, (const double *)O.u[O.cur], (double *)O.u[O.cur ^ 1], I,
+                                           update ? I.u[I.cur] : nullptr, I.f);
+        r.partials = b->partials + (size_t)pc.first * kSlots;
+        recs.push_back(r);
+      }
+      const oz::ArgsOuter *dev = push_list(b, recs);
+      if (!dev) return bfail(MG_ENOMEM, "batch descriptor area exhausted");
+      BCK("batched outer step", d2::dc_step_list(O0, I0, dev, (int)recs.size(), nullptr, kSlots, &np, update, s));
+    } else {
+      std::vector<z3::ArgsDC3> recs;
+      for (auto &pc : v) {
+        mg_ctx *c = pc.second;
+        Level &O = c->outer, &I = c->lv[0];
+        z3::ArgsDC3 r = d3::outer_record(O, (const double *)O.u[O.cur], (double *)O.u[O.cur ^ 1], I,
+                                         update ? I.u[I.cur] : nullptr, I.f);
+        r.partials = b->partials + (size_t)pc.first * kSlots;
+        recs.push_back(r);
+      }
+      const z3::ArgsDC3 *dev = push_list(b, recs);
+      if (!dev) return bfail(MG_ENOMEM, "batch descriptor area exhausted");
+      BCK("batched outer step", d3::dc_step_list(O0, I0, dev, (int)recs.size(), nullptr, kSlots, &np, update, s));
+    }
+    b->launches++;
+    if (update)
+      for (auto &pc : v) pc.second->outer.cur ^= 1;
+  }
+  kb_finalize<<<P, 256, 0, s>>>(b->partials, b->norms);
+  BCK("batched norm finalize", cudaGetLastError());
+  b->launches++;
+  return MG_OK;
 }
 
 // Residual norms of every problem into b->norms[i] (i = position in ps); in
 // defect-correction batches this is the outer FP64 residual, which also
 // writes each problem's inner defect.
 mg_status batched_norms(mg_batch *b, const std::vector<mg_ctx *> &ps) {
+  if (b->dc) return batched_outer(b, ps, false);
   int P = (int)ps.size();
   const int dim = b->dim;
   bool var = ps[0]->variable;
-  if (b->dc) {
-    std::vector<BOuter> os;
-    for (mg_ctx *c : ps) os.push_back(make_outer(c, true, false));
-    const BOuter *dev = (const BOuter *)push(b, os.data(), sizeof(BOuter) * P);
-    if (!dev) return bfail(MG_ENOMEM, "batch descriptor area exhausted");
-    dim3 gr(kPartBlocks, P);
-    int ti = ps[0]->lv[0].dtype;
-    if (dim == 2) {
-      if (ti == F32) { if (var) kb_dc_residual<2, float, true><<<gr, 256, 0, b->stream>>>(dev, b->partials); else kb_dc_residual<2, float, false><<<gr, 256, 0, b->stream>>>(dev, b->partials); }
-      else { if (var) kb_dc_residual<2, bf16, true><<<gr, 256, 0, b->stream>>>(dev, b->partials); else kb_dc_residual<2, bf16, false><<<gr, 256, 0, b->stream>>>(dev, b->partials); }
-    } else {
-      if (ti == F32) { if (var) kb_dc_residual<3, float, true><<<gr, 256, 0, b->stream>>>(dev, b->partials); else kb_dc_residual<3, float, false><<<gr, 256, 0, b->stream>>>(dev, b->partials); }
-      else { if (var) kb_dc_residual<3, bf16, true><<<gr, 256, 0, b->stream>>>(dev, b->partials); else kb_dc_residual<3, bf16, false><<<gr, 256, 0, b->stream>>>(dev, b->partials); }
-    }
-  } else {
-    std::vector<BOp> os;
-    for (mg_ctx *c : ps) os.push_back(make_op(c->lv[0]));
-    const BOp *dev = (const BOp *)push(b, os.data(), sizeof(BOp) * P);
-    if (!dev) return bfail(MG_ENOMEM, "batch descriptor area exhausted");
-    dim3 gr(kPartBlocks, P);
-    if (dim == 2) { if (var) kb_norm<2, true><<<gr, 256, 0, b->stream>>>(dev, b->partials); else kb_norm<2, false><<<gr, 256, 0, b->stream>>>(dev, b->partials); }
-    else { if (var) kb_norm<3, true><<<gr, 256, 0, b->stream>>>(dev, b->partials); else kb_norm<3, false><<<gr, 256, 0, b->stream>>>(dev, b->partials); }
-  }
+  std::vector<BOp> os;
+  for (mg_ctx *c : ps) os.push_back(make_op(c->lv[0]));
+  const BOp *dev = (const BOp *)push(b, os.data(), sizeof(BOp) * P);
+  if (!dev) return bfail(MG_ENOMEM, "batch descriptor area exhausted");
+  BCK("clear partials", cudaMemsetAsync(b->partials, 0, sizeof(double) * (size_t)P * kSlots, b->stream));
+  dim3 gr(kPartBlocks, P);
+  if (dim == 2) { if (var) kb_norm<2, true><<<gr, 256, 0, b->stream>>>(dev, b->partials); else kb_norm<2, false><<<gr, 256, 0, b->stream>>>(dev, b->partials); }
+  else { if (var) kb_norm<3, true><<<gr, 256, 0, b->stream>>>(dev, b->partials); else kb_norm<3, false><<<gr, 256, 0, b->stream>>>(dev, b->partials); }
   BCK("batched norm partials", cudaGetLastError());
-  kb_finalize<<<P, kPartBlocks, 0, b->stream>>>(b->partials, kPartBlocks, b->norms);
+  kb_finalize<<<P, 256, 0, b->stream>>>(b->partials, b->norms);
   BCK("batched norm finalize", cudaGetLastError());
   b->launches += 2;
-  return MG_OK;
-}
-
-mg_status batched_update(mg_batch *b, const std::vector<mg_ctx *> &ps) {
-  int P = (int)ps.size();
-  std::vector<BOuter> os;
-  for (mg_ctx *c : ps) os.push_back(make_outer(c, false, true));
-  const BOuter *dev = (const BOuter *)push(b, os.data(), sizeof(BOuter) * P);
-  if (!dev) return bfail(MG_ENOMEM, "batch descriptor area exhausted");
-  dim3 gr(kPartBlocks, P);
-  int ti = ps[0]->lv[0].dtype;
-  if (b->dim == 2) {
-    if (ti == F32) kb_dc_update<2, float><<<gr, 256, 0, b->stream>>>(dev);
-    else kb_dc_update<2, bf16><<<gr, 256, 0, b->stream>>>(dev);
-  } else {
-    if (ti == F32) kb_dc_update<3, float><<<gr, 256, 0, b->stream>>>(dev);
-    else kb_dc_update<3, bf16><<<gr, 256, 0, b->stream>>>(dev);
-  }
-  BCK("batched update", cudaGetLastError());
-  b->launches++;
   return MG_OK;
 }
 
@@ -642,7 +880,7 @@ extern "C" {
 
 size_t mg_batch_workspace_bytes(int max_problems) {
   if (max_problems < 1) return 0;
-  return desc_area_bytes(max_problems) + align256(sizeof(double) * (size_t)max_problems * kPartBlocks) +
+  return desc_area_bytes(max_problems) + align256(sizeof(double) * (size_t)max_problems * kSlots) +
          align256(sizeof(double) * (size_t)max_problems);
 }
 
@@ -659,7 +897,7 @@ mg_status mg_batch_create(int max_problems, void *workspace, size_t bytes, void 
   b->ws_bytes = bytes;
   b->desc_bytes = desc_area_bytes(max_problems);
   b->partials = (double *)(b->ws + b->desc_bytes);
-  b->norms = (double *)(b->ws + b->desc_bytes + align256(sizeof(double) * (size_t)max_problems * kPartBlocks));
+  b->norms = (double *)(b->ws + b->desc_bytes + align256(sizeof(double) * (size_t)max_problems * kSlots));
   b->stream = (cudaStream_t)stream;
   b->have_opts = false;
   b->launches = 0;
@@ -743,8 +981,7 @@ mg_status mg_batch_step(mg_batch *b, const int *ids, int count, double *rho) {
   int inner = b->dc ? std::max(b->opt.inner_cycles, 1) : 1;
   for (int k = 0; k < inner; k++)
     if ((st = batched_vcycle(b, ps, b->dc && k == 0))) return st;
-  if (b->dc && (st = batched_update(b, ps))) return st;
-  if ((st = batched_norms(b, ps))) return st;
+  if ((st = b->dc ? batched_outer(b, ps, true) : batched_norms(b, ps))) return st;
   std::vector<double> h(count);
   BCK("read norms", cudaMemcpyAsync(h.data(), b->norms, sizeof(double) * count, cudaMemcpyDeviceToHost, b->stream));
   BCK("synchronize", cudaStreamSynchronize(b->stream));

@@ -70,7 +70,8 @@ fz::Args2D make_args(const Level &L, const Level &Cl, double omega, int R_overri
 }
 
 template <typename T, int NU, bool ZERO>
-cudaError_t launch_pre(fz::Args2D a, int R_override, const Level &L, cudaStream_t s) {
+cudaError_t launch_pre(fz::Args2D a, int R_override, const Level &L, cudaStream_t s, const fz::Args2D *list = nullptr,
+                       int count = 1) {
   constexpr int W = fz::Warps<T>::value;
   constexpr size_t smem = (size_t)W * fz::kRing * 32 * fz::Lane<T>::bytes * 2;
   static bool ready = false;
@@ -88,12 +89,13 @@ cudaError_t launch_pre(fz::Args2D a, int R_override, const Level &L, cudaStream_
   }
   long long warps = (long long)a.nstrips * a.nchunks;
   unsigned blocks = (unsigned)((warps + W - 1) / W);
-  fz::k_pre2d<T, NU, ZERO><<<blocks, 32 * W, smem, s>>>(a);
+  fz::k_pre2d<T, NU, ZERO><<<dim3(blocks, (unsigned)count), 32 * W, smem, s>>>(a, list);
   return cudaGetLastError();
 }
 
 template <typename T, int NU>
-cudaError_t launch_post(fz::Args2D a, int R_override, const Level &L, cudaStream_t s) {
+cudaError_t launch_post(fz::Args2D a, int R_override, const Level &L, cudaStream_t s, const fz::Args2D *list = nullptr,
+                        int count = 1) {
   constexpr int W = fz::Warps<T>::value;
   constexpr size_t smem = (size_t)W * fz::kRing * 32 * (2 * fz::Lane<T>::bytes + 2 * sizeof(T));
   static bool ready = false;
@@ -111,7 +113,7 @@ cudaError_t launch_post(fz::Args2D a, int R_override, const Level &L, cudaStream
   }
   long long warps = (long long)a.nstrips * a.nchunks;
   unsigned blocks = (unsigned)((warps + W - 1) / W);
-  fz::k_post2d<T, NU><<<blocks, 32 * W, smem, s>>>(a);
+  fz::k_post2d<T, NU><<<dim3(blocks, (unsigned)count), 32 * W, smem, s>>>(a, list);
   return cudaGetLastError();
 }
 
@@ -146,6 +148,44 @@ cudaError_t post_fused(const Level &L, const void *uin, void *uout, const Level 
   a.ec = ec;
   if (L.dtype == F32) return nu == 1 ? launch_post<float, 1>(a, R, L, s) : launch_post<float, 2>(a, R, L, s);
   return nu == 1 ? launch_post<double, 1>(a, R, L, s) : launch_post<double, 2>(a, R, L, s);
+}
+
+}  // namespace d2
+}  // namespace mg
+
+namespace mg {
+namespace d2 {
+
+fz::Args2D fused_record(const Level &L, const Level &Cl, double omega, const void *uin, void *uout, const void *ec,
+                        void *fc) {
+  fz::Args2D a = make_args(L, Cl, omega, 0, 1);
+  a.uin = uin;
+  a.f = L.f;
+  a.uout = uout;
+  a.ec = ec;
+  a.fc = fc;
+  return a;
+}
+
+cudaError_t pre_fused_list(const Level &L, const Level &Cl, const fz::Args2D *list, int count, bool zero, int nu,
+                           cudaStream_t s) {
+  fz::Args2D a = make_args(L, Cl, 1.0, 0, 1);
+  if (L.dtype == F32) {
+    if (nu == 1)
+      return zero ? launch_pre<float, 1, true>(a, 0, L, s, list, count) : launch_pre<float, 1, false>(a, 0, L, s, list, count);
+    return zero ? launch_pre<float, 2, true>(a, 0, L, s, list, count) : launch_pre<float, 2, false>(a, 0, L, s, list, count);
+  }
+  if (nu == 1)
+    return zero ? launch_pre<double, 1, true>(a, 0, L, s, list, count) : launch_pre<double, 1, false>(a, 0, L, s, list, count);
+  return zero ? launch_pre<double, 2, true>(a, 0, L, s, list, count) : launch_pre<double, 2, false>(a, 0, L, s, list, count);
+}
+
+cudaError_t post_fused_list(const Level &L, const Level &Cl, const fz::Args2D *list, int count, int nu,
+                            cudaStream_t s) {
+  fz::Args2D a = make_args(L, Cl, 1.0, 0, 1);
+  if (L.dtype == F32)
+    return nu == 1 ? launch_post<float, 1>(a, 0, L, s, list, count) : launch_post<float, 2>(a, 0, L, s, list, count);
+  return nu == 1 ? launch_post<double, 1>(a, 0, L, s, list, count) : launch_post<double, 2>(a, 0, L, s, list, count);
 }
 
 }  // namespace d2

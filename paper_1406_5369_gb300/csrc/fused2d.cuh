@@ -74,6 +74,18 @@ struct Args2D {
   int has_gamma;  // gamma != 0 (omega != 1), decided on the host
 };
 
+// Launches over many problems of one level size (the batch engine) pass a
+// device list with one record per problem and blockIdx.y as the problem
+// index: a block takes the record's fields and coefficients, while the grid
+// geometry (sizes, pitches, row chunks) stays that of the launch argument.
+__device__ __forceinline__ void take_problem(Args2D &a, const Args2D &p) {
+  a.uin = p.uin; a.f = p.f; a.uout = p.uout; a.ec = p.ec; a.fc = p.fc;
+  a.alpha = p.alpha; a.betax = p.betax; a.betay = p.betay; a.gamma = p.gamma;
+  a.cx = p.cx; a.cy = p.cy; a.cd = p.cd;
+  a.alphaf = p.alphaf; a.betaxf = p.betaxf; a.betayf = p.betayf; a.gammaf = p.gammaf;
+  a.cxf = p.cxf; a.cyf = p.cyf; a.cdf = p.cdf; a.has_gamma = p.has_gamma;
+}
+
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool valid) {
   unsigned saddr = (unsigned)__cvta_generic_to_shared(smem);
   int sz = valid ? 16 : 0;
@@ -210,9 +222,10 @@ __device__ __forceinline__ void residual_row(C (&rr)[kVec], const C (&uc)[kVec],
 // ------------------------------------------------------------------------
 // Pre-smoothing + residual + restriction.
 template <typename T, int NU, bool ZERO>
-__global__ void __launch_bounds__(32 * Warps<T>::value, MinBlocks<T>::value) k_pre2d(Args2D a) {
+__global__ void __launch_bounds__(32 * Warps<T>::value, MinBlocks<T>::value) k_pre2d(Args2D a, const Args2D *__restrict__ list) {
   typedef typename CT<T>::type C;
   extern __shared__ __align__(16) unsigned char smem[];
+  if (list) take_problem(a, list[blockIdx.y]);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const long long gw = (long long)blockIdx.x * Warps<T>::value + wib;
   if (gw >= (long long)a.nstrips * a.nchunks) return;
@@ -331,9 +344,10 @@ __global__ void __launch_bounds__(32 * Warps<T>::value, MinBlocks<T>::value) k_p
 // ------------------------------------------------------------------------
 // Interpolation + correction + post-smoothing.
 template <typename T, int NU>
-__global__ void __launch_bounds__(32 * Warps<T>::value, MinBlocks<T>::value) k_post2d(Args2D a) {
+__global__ void __launch_bounds__(32 * Warps<T>::value, MinBlocks<T>::value) k_post2d(Args2D a, const Args2D *__restrict__ list) {
   typedef typename CT<T>::type C;
   extern __shared__ __align__(16) unsigned char smem[];
+  if (list) take_problem(a, list[blockIdx.y]);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const long long gw = (long long)blockIdx.x * Warps<T>::value + wib;
   if (gw >= (long long)a.nstrips * a.nchunks) return;
@@ -468,4 +482,16 @@ __global__ void __launch_bounds__(32 * Warps<T>::value, MinBlocks<T>::value) k_p
 }
 
 }  // namespace fz
+
+namespace d2 {
+// One problem's record for the list launches (pointers and coefficients).
+fz::Args2D fused_record(const Level &L, const Level &Cl, double omega, const void *uin, void *uout, const void *ec,
+                        void *fc);
+// k_pre2d / k_post2d over `count` problems of level size L.n (coarse Cl.n),
+// records in device memory; the grid's y index is the problem.
+cudaError_t pre_fused_list(const Level &L, const Level &Cl, const fz::Args2D *list, int count, bool zero, int nu,
+                           cudaStream_t s);
+cudaError_t post_fused_list(const Level &L, const Level &Cl, const fz::Args2D *list, int count, int nu,
+                            cudaStream_t s);
+}  // namespace d2
 }  // namespace mg

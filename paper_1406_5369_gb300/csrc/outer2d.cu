@@ -20,7 +20,7 @@ int sm_count() {
   return count;
 }
 
-void chunking(oz::ArgsOuter &a, int n, int bps) {
+void chunking(oz::ArgsOuter &a, int n, int bps, int max_parts = kMaxPartials) {
   a.nstrips = (n + oz::kOut - 1) / oz::kOut;
   long long slots = (long long)sm_count() * bps * oz::kWarps;
   long long nchunks = slots / a.nstrips;
@@ -30,8 +30,8 @@ void chunking(oz::ArgsOuter &a, int n, int bps) {
   if (R < 8) R = 8;
   a.R = R;
   a.nchunks = (n + R - 1) / R;
-  if ((long long)a.nstrips * a.nchunks > kMaxPartials) {  // one partial sum per warp must fit
-    int nc = kMaxPartials / a.nstrips;
+  if ((long long)a.nstrips * a.nchunks > max_parts) {  // one partial sum per warp must fit
+    int nc = max_parts / a.nstrips;
     if (nc < 1) nc = 1;
     a.R = ((n + nc - 1) / nc + 7) / 8 * 8;
     a.nchunks = (n + a.R - 1) / a.R;
@@ -46,17 +46,19 @@ template <typename KernelT> int occupancy(KernelT k, int threads, size_t smem) {
 }
 
 template <typename Ti, bool UPDATE, bool ACC64>
-cudaError_t launch_dc(oz::ArgsOuter a, int n, int *nparts, cudaStream_t s) {
+cudaError_t launch_dc(oz::ArgsOuter a, int n, int *nparts, cudaStream_t s, const oz::ArgsOuter *list = nullptr,
+                      int count = 1, int max_parts = kMaxPartials) {
   constexpr int IB = oz::InnerLane<Ti>::bytes;
   constexpr int IBP = IB < 16 ? 16 : IB;
   constexpr size_t smem = (size_t)oz::kWarps * oz::kRing * 32 * (32 + 32 + IBP);
   static int bps = 0;
   if (!bps) bps = occupancy(oz::k_dc2d<Ti, UPDATE, ACC64>, 32 * oz::kWarps, smem);
-  chunking(a, n, bps);
+  chunking(a, n, bps, max_parts);
   long long warps = (long long)a.nstrips * a.nchunks;
   *nparts = (int)warps;
+  a.pstride = max_parts;
   unsigned blocks = (unsigned)((warps + oz::kWarps - 1) / oz::kWarps);
-  oz::k_dc2d<Ti, UPDATE, ACC64><<<blocks, 32 * oz::kWarps, smem, s>>>(a);
+  oz::k_dc2d<Ti, UPDATE, ACC64><<<dim3(blocks, (unsigned)count), 32 * oz::kWarps, smem, s>>>(a, list);
   return cudaGetLastError();
 }
 
@@ -141,6 +143,36 @@ cudaError_t dc_step(const Level &O, const double *uin, double *uout, const Level
   }
   if (update) return acc64 ? launch_dc<bf16, true, true>(a, O.n, nparts, s) : launch_dc<bf16, true, false>(a, O.n, nparts, s);
   return acc64 ? launch_dc<bf16, false, true>(a, O.n, nparts, s) : launch_dc<bf16, false, false>(a, O.n, nparts, s);
+}
+
+oz::ArgsOuter outer_record(const Level &O, const double *uin, double *uout, const Level &I, const void *e, void *d) {
+  oz::ArgsOuter a;
+  memset(&a, 0, sizeof a);
+  a.u = uin;
+  a.uout = uout;
+  a.f = (const double *)O.f;
+  a.e = e;
+  a.d = d;
+  a.cx = O.c[0] * O.inv_h2;
+  a.cy = O.c[1] * O.inv_h2;
+  a.cd = 2.0 * (a.cx + a.cy);
+  return a;
+}
+
+cudaError_t dc_step_list(const Level &O, const Level &I, const oz::ArgsOuter *list, int count, double *partials,
+                         int pstride, int *nparts, bool update, cudaStream_t s) {
+  oz::ArgsOuter a;
+  memset(&a, 0, sizeof a);
+  a.partials = partials;
+  a.n = O.n;
+  a.pitch = O.pitch;
+  a.pitchi = I.pitch;
+  if (I.dtype == F32) {
+    return update ? launch_dc<float, true, true>(a, O.n, nparts, s, list, count, pstride)
+                  : launch_dc<float, false, true>(a, O.n, nparts, s, list, count, pstride);
+  }
+  return update ? launch_dc<bf16, true, true>(a, O.n, nparts, s, list, count, pstride)
+                : launch_dc<bf16, false, true>(a, O.n, nparts, s, list, count, pstride);
 }
 
 bool norm_ok(const Level &L) { return L.dim == 2 && !L.kf[0] && (L.dtype == F64 || L.dtype == F32) && L.n >= 5; }

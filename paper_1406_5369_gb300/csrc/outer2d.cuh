@@ -58,7 +58,16 @@ struct ArgsOuter {
   int pitchi;           // inner grid pitch (elements)
   int R, nstrips, nchunks;
   double cx, cy, cd;    // stencil: cx = c0/h^2, cy = c1/h^2, cd = 2 (cx + cy)
+  int pstride;          // list launches: partial slots per problem
 };
+
+// List launches (many problems of one size): record fields of problem
+// blockIdx.y, including the address of its partial-sum slots.
+__device__ __forceinline__ void take_problem(ArgsOuter &a, const ArgsOuter &p) {
+  a.u = p.u; a.uout = p.uout; a.f = p.f; a.e = p.e; a.d = p.d;
+  a.cx = p.cx; a.cy = p.cy; a.cd = p.cd;
+  a.partials = p.partials;  // the problem's own slots (at most pstride of them)
+}
 
 template <typename Ti> struct InnerLane { static constexpr int bytes = kVec * (int)sizeof(Ti); };
 
@@ -120,8 +129,9 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // ---------------------------------------------------------------- outer step
 template <typename Ti, bool UPDATE, bool ACC64>
-__global__ void __launch_bounds__(32 * kWarps) k_dc2d(ArgsOuter a) {
+__global__ void __launch_bounds__(32 * kWarps) k_dc2d(ArgsOuter a, const ArgsOuter *__restrict__ list) {
   extern __shared__ __align__(16) unsigned char smem[];
+  if (list) take_problem(a, list[blockIdx.y]);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const long long gw = (long long)blockIdx.x * kWarps + wib;
   if (gw >= (long long)a.nstrips * a.nchunks) return;
@@ -141,7 +151,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_dc2d(ArgsOuter a) {
   unsigned char *se = sf + kRing * 32 * 32;
   const Ti *e = (const Ti *)a.e;
   Ti *d = (Ti *)a.d;
-  const float scale = *a.scale;
+  const float scale = ACC64 ? 1.0f : *a.scale;  // FP64 squares need no scale
   const double cx = a.cx, cy = a.cy, cd = a.cd;
 
   double U[kSlots][kVec], F[kSlots][kVec];
@@ -311,4 +321,15 @@ __global__ void __launch_bounds__(32 * kWarps) k_norm2d(ArgsOuter a) {
 }
 
 }  // namespace oz
+
+namespace d2 {
+// One problem's record for the outer-step list launch (FP64 squares, no scale).
+oz::ArgsOuter outer_record(const Level &O, const double *uin, double *uout, const Level &I, const void *e, void *d);
+// k_dc2d over `count` problems of outer size O.n (inner level I): problem i
+// writes its per-warp partial sums to partials[i * pstride ...] (at most
+// pstride of them; *nparts receives the count).
+cudaError_t dc_step_list(const Level &O, const Level &I, const oz::ArgsOuter *list, int count, double *partials,
+                         int pstride, int *nparts, bool update, cudaStream_t s);
+}  // namespace d2
 }  // namespace mg
+

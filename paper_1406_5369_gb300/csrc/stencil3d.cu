@@ -75,7 +75,8 @@ z3::Args3 stencil_args(const Level &L, double omega) {
 }
 
 template <typename T, int MODE>
-cudaError_t launch_stencil(z3::Args3 a, long long max_blocks, int *nblocks, cudaStream_t s) {
+cudaError_t launch_stencil(z3::Args3 a, long long max_blocks, int *nblocks, cudaStream_t s,
+                           const z3::Args3 *list = nullptr, int count = 1) {
   constexpr int V = z3::VW<T>::V;
   constexpr size_t smem = (size_t)z3::kRingZ * z3::kSlotB;
   static int per_sm = 0;
@@ -86,7 +87,7 @@ cudaError_t launch_stencil(z3::Args3 a, long long max_blocks, int *nblocks, cuda
   a.zc = pick_zc(a.n, base, r, max_blocks);
   int nz = (a.n - 2 + a.zc - 1) / a.zc;
   if (nblocks) *nblocks = (int)(base * nz);
-  z3::k3_stencil<T, MODE><<<dim3((unsigned)base, (unsigned)nz), 32 * z3::kTY, smem, s>>>(a);
+  z3::k3_stencil<T, MODE><<<dim3((unsigned)base, (unsigned)nz, (unsigned)count), 32 * z3::kTY, smem, s>>>(a, list);
   return cudaGetLastError();
 }
 
@@ -154,7 +155,7 @@ cudaError_t z_restrict(const Level &F, const void *rf, const Level &C, void *fc,
     constexpr int V = z3::VW<T>::V;
     a.ntx = (C.n - 1 + 16 * V - 1) / (16 * V);
     dim3 g((unsigned)(a.ntx * ((rows + z3::kTY - 1) / z3::kTY)), (unsigned)rows);
-    z3::k3_restrict<T><<<g, 32 * z3::kTY, 0, s>>>(a);
+    z3::k3_restrict<T><<<g, 32 * z3::kTY, 0, s>>>(a, nullptr);
   })
   return cudaGetLastError();
 }
@@ -171,7 +172,7 @@ cudaError_t z_prolong(const Level &C, const void *ec, const Level &F, void *uf, 
     constexpr int V = z3::VW<T>::V;
     a.ntx = (F.n - 1 + 32 * V - 1) / (32 * V);
     dim3 g((unsigned)(a.ntx * ((rows + z3::kTY - 1) / z3::kTY)), (unsigned)rows);
-    z3::k3_prolong<T><<<g, 32 * z3::kTY, 0, s>>>(a);
+    z3::k3_prolong<T><<<g, 32 * z3::kTY, 0, s>>>(a, nullptr);
   })
   return cudaGetLastError();
 }
@@ -183,17 +184,19 @@ bool outer_ok(const Level &O, const Level &I) {
 
 namespace {
 template <typename Ti, bool UPDATE, bool ACC64>
-cudaError_t launch_dc(z3::ArgsDC3 a, int *nparts, cudaStream_t s) {
+cudaError_t launch_dc(z3::ArgsDC3 a, int *nparts, cudaStream_t s, const z3::ArgsDC3 *list = nullptr, int count = 1,
+                      int max_parts = kMaxPartials) {
   constexpr size_t smem = (size_t)z3::DCL<Ti>::Smem;
   static int per_sm = 0;
   int r = resident(z3::k3_dc<Ti, UPDATE, ACC64>, 32 * z3::kDCWarps, smem, &per_sm);
   a.ntx = (a.n - 1 + 63) / 64;
   a.nty = (a.n - 2 + z3::kTY - 1) / z3::kTY;
   long long base = (long long)a.ntx * a.nty;
-  a.zc = pick_zc(a.n, base, r, kMaxPartials);
+  a.zc = pick_zc(a.n, base, r, max_parts);
   int nz = (a.n - 2 + a.zc - 1) / a.zc;
   *nparts = (int)(base * nz);
-  z3::k3_dc<Ti, UPDATE, ACC64><<<dim3((unsigned)base, (unsigned)nz), 32 * z3::kDCWarps, smem, s>>>(a);
+  a.pstride = max_parts;
+  z3::k3_dc<Ti, UPDATE, ACC64><<<dim3((unsigned)base, (unsigned)nz, (unsigned)count), 32 * z3::kDCWarps, smem, s>>>(a, list);
   return cudaGetLastError();
 }
 }  // namespace
@@ -225,6 +228,95 @@ cudaError_t dc_step(const Level &O, const double *uin, double *uout, const Level
   }
   if (update) return acc64 ? launch_dc<bf16, true, true>(a, nparts, s) : launch_dc<bf16, true, false>(a, nparts, s);
   return acc64 ? launch_dc<bf16, false, true>(a, nparts, s) : launch_dc<bf16, false, false>(a, nparts, s);
+}
+
+
+// ---------------------------------------------------------------- list launches (batch engine)
+
+z3::Args3 stencil_record(const Level &L, double omega, const void *u, void *out, const void *f) {
+  z3::Args3 a = stencil_args(L, omega);
+  a.u = u;
+  a.out = out;
+  a.f = f;
+  return a;
+}
+
+cudaError_t z_sweep_list(const Level &L, const z3::Args3 *list, int count, int color, cudaStream_t s) {
+  z3::Args3 a = stencil_args(L, 1.0);
+  a.color = color;
+  cudaError_t e = cudaSuccess;
+  if (color < 0) {
+    Z3_DISPATCH(L.dtype, e = (launch_stencil<T, z3::kJacobi>(a, 1LL << 30, nullptr, s, list, count)));
+  } else {
+    Z3_DISPATCH(L.dtype, e = (launch_stencil<T, z3::kRB>(a, 1LL << 30, nullptr, s, list, count)));
+  }
+  return e;
+}
+
+cudaError_t z_residual_list(const Level &L, const z3::Args3 *list, int count, cudaStream_t s) {
+  z3::Args3 a = stencil_args(L, 1.0);
+  cudaError_t e = cudaSuccess;
+  Z3_DISPATCH(L.dtype, e = (launch_stencil<T, z3::kResid>(a, 1LL << 30, nullptr, s, list, count)));
+  return e;
+}
+
+cudaError_t z_transfer_list(bool restrict_, const Level &F, const Level &C, const z3::ArgsT3 *list, int count,
+                            cudaStream_t s) {
+  z3::ArgsT3 a;
+  memset(&a, 0, sizeof a);
+  a.nf = F.n; a.pitchf = F.pitch; a.planef = F.plane;
+  a.nc = C.n; a.pitchc = C.pitch; a.planec = C.plane;
+  if (restrict_) {
+    const int rows = C.n - 2;
+    Z3_DISPATCH(F.dtype, {
+      constexpr int V = z3::VW<T>::V;
+      a.ntx = (C.n - 1 + 16 * V - 1) / (16 * V);
+      dim3 g((unsigned)(a.ntx * ((rows + z3::kTY - 1) / z3::kTY)), (unsigned)rows, (unsigned)count);
+      z3::k3_restrict<T><<<g, 32 * z3::kTY, 0, s>>>(a, list);
+    })
+  } else {
+    const int rows = F.n - 2;
+    Z3_DISPATCH(F.dtype, {
+      constexpr int V = z3::VW<T>::V;
+      a.ntx = (F.n - 1 + 32 * V - 1) / (32 * V);
+      dim3 g((unsigned)(a.ntx * ((rows + z3::kTY - 1) / z3::kTY)), (unsigned)rows, (unsigned)count);
+      z3::k3_prolong<T><<<g, 32 * z3::kTY, 0, s>>>(a, list);
+    })
+  }
+  return cudaGetLastError();
+}
+
+z3::ArgsDC3 outer_record(const Level &O, const double *uin, double *uout, const Level &I, const void *e, void *d) {
+  z3::ArgsDC3 a;
+  memset(&a, 0, sizeof a);
+  a.u = uin;
+  a.uout = uout;
+  a.f = (const double *)O.f;
+  a.e = e;
+  a.d = d;
+  double cx = O.c[0] * O.inv_h2, cy = O.c[1] * O.inv_h2, cz = O.c[2] * O.inv_h2;
+  a.cx = cx;
+  a.cy = cy;
+  a.cz = cz;
+  a.cd = 2.0 * (cx + cy + cz);
+  return a;
+}
+
+cudaError_t dc_step_list(const Level &O, const Level &I, const z3::ArgsDC3 *list, int count, double *partials,
+                         int pstride, int *nparts, bool update, cudaStream_t s) {
+  z3::ArgsDC3 a;
+  memset(&a, 0, sizeof a);
+  a.partials = partials;
+  a.n = O.n;
+  a.pitch = O.pitch;
+  a.pitchi = I.pitch;
+  a.plane = O.plane;
+  a.planei = I.plane;
+  if (I.dtype == F32)
+    return update ? launch_dc<float, true, true>(a, nparts, s, list, count, pstride)
+                  : launch_dc<float, false, true>(a, nparts, s, list, count, pstride);
+  return update ? launch_dc<bf16, true, true>(a, nparts, s, list, count, pstride)
+                : launch_dc<bf16, false, true>(a, nparts, s, list, count, pstride);
 }
 
 }  // namespace d3

@@ -92,6 +92,17 @@ struct Args3 {
   int has_gamma;  // gamma != 0 (omega != 1), decided on the host
 };
 
+// List launches (many problems of one size, the batch engine): blockIdx.z
+// is the problem; a block takes its record's fields and coefficients, the
+// grid geometry stays that of the launch argument.
+__device__ __forceinline__ void take_problem(Args3 &a, const Args3 &p) {
+  a.u = p.u; a.out = p.out; a.f = p.f;
+  a.alpha = p.alpha; a.bx = p.bx; a.by = p.by; a.bz = p.bz; a.gamma = p.gamma;
+  a.cd = p.cd; a.cx = p.cx; a.cy = p.cy; a.cz = p.cz;
+  a.alphaf = p.alphaf; a.bxf = p.bxf; a.byf = p.byf; a.bzf = p.bzf; a.gammaf = p.gammaf;
+  a.cdf = p.cdf; a.cxf = p.cxf; a.cyf = p.cyf; a.czf = p.czf; a.has_gamma = p.has_gamma;
+}
+
 enum { kJacobi = 0, kRB = 1, kResid = 2, kNorm = 3 };
 
 // The 16-byte pieces a thread stages for every plane, fixed for the whole
@@ -157,11 +168,12 @@ __device__ __forceinline__ void stencil_pieces(Pieces<kStPieces> &pc, const T *u
 }
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(32 * kTY, 3) k3_stencil(Args3 a) {
+__global__ void __launch_bounds__(32 * kTY, 3) k3_stencil(Args3 a, const Args3 *__restrict__ list) {
   typedef typename CT<T>::type C;
   constexpr int V = VW<T>::V;
   constexpr int TX = 32 * V;
   extern __shared__ __align__(16) unsigned char smem[];
+  if (list) take_problem(a, list[blockIdx.z]);
   __shared__ double wsum[kTY];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int tx = blockIdx.x % a.ntx, ty = blockIdx.x / a.ntx;
@@ -279,7 +291,11 @@ struct ArgsT3 {
 // (V / 2 per lane, from one 16-byte vector of V fine values per fine row),
 // for one coarse row J and plane K; blocks hold kTY consecutive rows.
 template <typename T>
-__global__ void __launch_bounds__(32 * kTY) k3_restrict(ArgsT3 a) {
+__global__ void __launch_bounds__(32 * kTY) k3_restrict(ArgsT3 a, const ArgsT3 *__restrict__ list) {
+  if (list) {
+    a.src = list[blockIdx.z].src;
+    a.dst = list[blockIdx.z].dst;
+  }
   typedef typename CT<T>::type C;
   constexpr int V = VW<T>::V, VC = V / 2;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -325,7 +341,11 @@ __global__ void __launch_bounds__(32 * kTY) k3_restrict(ArgsT3 a) {
 // Trilinear interpolation and correction at fine interior nodes: a warp
 // covers 32 V fine columns of one fine row j and plane k.
 template <typename T>
-__global__ void __launch_bounds__(32 * kTY) k3_prolong(ArgsT3 a) {
+__global__ void __launch_bounds__(32 * kTY) k3_prolong(ArgsT3 a, const ArgsT3 *__restrict__ list) {
+  if (list) {
+    a.src = list[blockIdx.z].src;
+    a.dst = list[blockIdx.z].dst;
+  }
   typedef typename CT<T>::type C;
   constexpr int V = VW<T>::V, VC = V / 2;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -399,6 +419,7 @@ struct ArgsDC3 {
   long long plane, planei;
   int ntx, nty, zc;
   double cd, cx, cy, cz;
+  int pstride;         // list launches: partial slots per problem
 };
 
 // Pieces of the outer step's tile: u and e rows y0-1 .. y0+kTY with halo
@@ -449,9 +470,15 @@ template <typename Ti> __device__ __forceinline__ double e_at(const unsigned cha
 }
 
 template <typename Ti, bool UPDATE, bool ACC64>
-__global__ void __launch_bounds__(32 * kDCWarps) k3_dc(ArgsDC3 a) {
+__global__ void __launch_bounds__(32 * kDCWarps) k3_dc(ArgsDC3 a, const ArgsDC3 *__restrict__ list) {
   typedef DCL<Ti> L;
   extern __shared__ __align__(16) unsigned char smem[];
+  if (list) {  // problem blockIdx.z of a list launch
+    const ArgsDC3 &p = list[blockIdx.z];
+    a.u = p.u; a.uout = p.uout; a.f = p.f; a.e = p.e; a.d = p.d;
+    a.cd = p.cd; a.cx = p.cx; a.cy = p.cy; a.cz = p.cz;
+    a.partials = p.partials;  // the problem's own slots (at most pstride of them)
+  }
   __shared__ double wsum[kDCWarps];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;  // w = 0 .. kTY + 1: row y0 - 1 + w
   const int tx = blockIdx.x % a.ntx, ty = blockIdx.x / a.ntx;
@@ -463,7 +490,7 @@ __global__ void __launch_bounds__(32 * kDCWarps) k3_dc(ArgsDC3 a) {
   const bool row_ok = y <= n - 1;
   unsigned char *un = smem + kDCRing * L::SlotB;  // 3 slots x kDCWarps rows of updated u
   auto slot = [&](int p) { return smem + (p % kDCRing) * L::SlotB; };
-  const float scale = *a.scale;
+  const float scale = ACC64 ? 1.0f : *a.scale;  // FP64 squares need no scale
   const double cd = a.cd, cx = a.cx, cy = a.cy, cz = a.cz;
   Ti *d = (Ti *)a.d;
   float acc = 0.0f;
@@ -558,4 +585,18 @@ __global__ void __launch_bounds__(32 * kDCWarps) k3_dc(ArgsDC3 a) {
 }
 
 }  // namespace z3
+
+// List launches of the 3D kernels over many problems of one level size (the
+// batch engine); records in device memory, the grid's z index is the problem.
+namespace d3 {
+z3::Args3 stencil_record(const Level &L, double omega, const void *u, void *out, const void *f);
+cudaError_t z_sweep_list(const Level &L, const z3::Args3 *list, int count, int color, cudaStream_t s);
+cudaError_t z_residual_list(const Level &L, const z3::Args3 *list, int count, cudaStream_t s);
+cudaError_t z_transfer_list(bool restrict_, const Level &F, const Level &C, const z3::ArgsT3 *list, int count,
+                            cudaStream_t s);
+z3::ArgsDC3 outer_record(const Level &O, const double *uin, double *uout, const Level &I, const void *e, void *d);
+cudaError_t dc_step_list(const Level &O, const Level &I, const z3::ArgsDC3 *list, int count, double *partials,
+                         int pstride, int *nparts, bool update, cudaStream_t s);
+}  // namespace d3
 }  // namespace mg
+
