@@ -70,119 +70,132 @@ template <typename C> __device__ __forceinline__ const Sten<C> &sten_of_op(const
 template <> __device__ __forceinline__ const Sten<double> &sten_of_op<double>(const BOp &o) { return o.sd; }
 template <> __device__ __forceinline__ const Sten<float> &sten_of_op<float>(const BOp &o) { return o.sf; }
 
-// Grid: x covers columns, y rows, z = (problem * n + plane) in 3D or problem in 2D.
-template <int DIM> __device__ __forceinline__ Idx bnode(const Geo &g, int &p) {
-  Idx t;
-  t.i = blockIdx.x * blockDim.x + threadIdx.x;
-  t.j = blockIdx.y;
-  if (DIM == 3) {
-    p = blockIdx.z / g.n;
-    t.k = blockIdx.z % g.n;
-  } else {
-    p = blockIdx.z;
-    t.k = 0;
-  }
-  t.p = (long long)t.k * g.sz + (long long)t.j * g.sy + t.i;
-  t.interior = t.i >= 1 && t.i <= g.n - 2 && t.j >= 1 && t.j <= g.n - 2 &&
-               (DIM == 2 || (t.k >= 1 && t.k <= g.n - 2));
-  return t;
+// Generic kernels: a block owns one row (blockIdx.x) of one plane (3D:
+// blockIdx.y) of one problem (blockIdx.y in 2D, blockIdx.z in 3D) and its
+// threads loop over the columns, so a launch has one block per row and
+// problem, not one per 128 nodes. `first` is the index of the first row and
+// plane covered (1 when only interior rows/planes are launched).
+template <int DIM> struct BRow {
+  int j, k, pi;
+  long long off;  // element offset of the row
+};
+template <int DIM> __device__ __forceinline__ BRow<DIM> brow(const Geo &g, int first) {
+  BRow<DIM> r;
+  r.j = first + (int)blockIdx.x;
+  r.k = DIM == 3 ? first + (int)blockIdx.y : 0;
+  r.pi = DIM == 3 ? (int)blockIdx.z : (int)blockIdx.y;
+  r.off = (long long)r.k * g.sz + (long long)r.j * g.sy;
+  return r;
 }
 
 template <int DIM, typename T, bool VAR>
 __global__ void kb_rbgs_half(const BOp *__restrict__ ops, Geo g, int color, int flip, double omega_d, float omega_f) {
   typedef typename CT<T>::type C;
-  int pi;
-  Idx t = bnode<DIM>(g, pi);
-  const BOp &o = ops[pi];
-  if (!t.interior || ((t.i + t.j + t.k) & 1) != color) return;
+  BRow<DIM> r = brow<DIM>(g, 1);
+  const BOp &o = ops[r.pi];
   T *u = (T *)o.u[o.cur ^ flip];
   const T *f = (const T *)o.f;
   const Sten<C> s = sten_of_op<C>(o);
-  C Au, dg;
-  apply_at<DIM, VAR>(u, t.p, g, s, Au, dg);
-  st(u + t.p, ld(u + t.p) + pick<C>(omega_d, omega_f) * (ld(f + t.p) - Au) / dg);
+  const C omega = pick<C>(omega_d, omega_f);
+  // columns i with (i + j + k) % 2 == color, from the first interior one
+  const int i0 = 1 + ((color + r.j + r.k + 1) & 1);
+  for (int i = i0 + 2 * (int)threadIdx.x; i <= g.n - 2; i += 2 * (int)blockDim.x) {
+    const long long p = r.off + i;
+    C Au, dg;
+    apply_at<DIM, VAR>(u, p, g, s, Au, dg);
+    st(u + p, ld(u + p) + omega * (ld(f + p) - Au) / dg);
+  }
 }
 
 template <int DIM, typename T, bool VAR>
 __global__ void kb_jacobi(const BOp *__restrict__ ops, Geo g, int flip, double omega_d, float omega_f) {
   typedef typename CT<T>::type C;
-  int pi;
-  Idx t = bnode<DIM>(g, pi);
-  const BOp &o = ops[pi];
-  if (!t.interior) return;
+  BRow<DIM> r = brow<DIM>(g, 1);
+  const BOp &o = ops[r.pi];
   const T *uin = (const T *)o.u[o.cur ^ flip];
   T *uout = (T *)o.u[o.cur ^ flip ^ 1];
   const T *f = (const T *)o.f;
   const Sten<C> s = sten_of_op<C>(o);
-  C Au, dg;
-  apply_at<DIM, VAR>(uin, t.p, g, s, Au, dg);
-  st(uout + t.p, ld(uin + t.p) + pick<C>(omega_d, omega_f) * (ld(f + t.p) - Au) / dg);
+  const C omega = pick<C>(omega_d, omega_f);
+  for (int i = 1 + (int)threadIdx.x; i <= g.n - 2; i += (int)blockDim.x) {
+    const long long p = r.off + i;
+    C Au, dg;
+    apply_at<DIM, VAR>(uin, p, g, s, Au, dg);
+    st(uout + p, ld(uin + p) + omega * (ld(f + p) - Au) / dg);
+  }
 }
 
 template <int DIM, typename T, bool VAR>
 __global__ void kb_residual(const BOp *__restrict__ ops, Geo g, int flip) {
   typedef typename CT<T>::type C;
-  int pi;
-  Idx t = bnode<DIM>(g, pi);
-  const BOp &o = ops[pi];
-  if (!t.interior) return;
+  BRow<DIM> r = brow<DIM>(g, 1);
+  const BOp &o = ops[r.pi];
   const T *u = (const T *)o.u[o.cur ^ flip];
+  const T *f = (const T *)o.f;
+  T *res = (T *)o.r;
   const Sten<C> s = sten_of_op<C>(o);
-  C Au, dg;
-  apply_at<DIM, VAR>(u, t.p, g, s, Au, dg);
-  st((T *)o.r + t.p, ld((const T *)o.f + t.p) - Au);
+  for (int i = 1 + (int)threadIdx.x; i <= g.n - 2; i += (int)blockDim.x) {
+    const long long p = r.off + i;
+    C Au, dg;
+    apply_at<DIM, VAR>(u, p, g, s, Au, dg);
+    st(res + p, ld(f + p) - Au);
+  }
 }
 
+// Zeroes every row (boundary included) of the live solution.
 template <int DIM, typename T> __global__ void kb_zero(const BOp *__restrict__ ops, Geo g, int flip) {
-  int pi;
-  Idx t = bnode<DIM>(g, pi);
-  const BOp &o = ops[pi];
-  if (t.i >= g.n) return;
-  st((T *)o.u[o.cur ^ flip] + t.p, 0.0f);
+  BRow<DIM> r = brow<DIM>(g, 0);
+  const BOp &o = ops[r.pi];
+  T *u = (T *)o.u[o.cur ^ flip] + r.off;
+  for (int i = threadIdx.x; i < g.n; i += blockDim.x) st(u + i, 0.0f);
 }
 
+// Full weighting: rows/planes of the coarse grid.
 template <int DIM, typename Tf, typename Tc>
 __global__ void kb_restrict(const BXfer *__restrict__ xs, Geo gf, Geo gc) {
   typedef typename CT<Tc>::type C;
-  int pi;
-  Idx t = bnode<DIM>(gc, pi);
-  if (!t.interior) return;
-  const Tf *rf = (const Tf *)xs[pi].src;
-  Tc *fc = (Tc *)xs[pi].dst;
-  long long q = (long long)(2 * t.k) * gf.sz + (long long)(2 * t.j) * gf.sy + 2 * t.i;
-  C acc = 0;
+  BRow<DIM> r = brow<DIM>(gc, 1);
+  const Tf *rf = (const Tf *)xs[r.pi].src;
+  Tc *fc = (Tc *)xs[r.pi].dst;
+  const long long qrow = (long long)(2 * r.k) * gf.sz + (long long)(2 * r.j) * gf.sy;
+  for (int I = 1 + (int)threadIdx.x; I <= gc.n - 2; I += (int)blockDim.x) {
+    const long long q = qrow + 2 * I;
+    C acc = 0;
 #pragma unroll
-  for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); dz++) {
-    C wz = DIM == 3 ? (dz == 0 ? (C)0.5 : (C)0.25) : (C)1;
+    for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); dz++) {
+      C wz = DIM == 3 ? (dz == 0 ? (C)0.5 : (C)0.25) : (C)1;
 #pragma unroll
-    for (int dy = -1; dy <= 1; dy++) {
-      C wy = dy == 0 ? (C)0.5 : (C)0.25;
-      const Tf *row = rf + q + dz * gf.sz + dy * gf.sy;
-      C line = (C)0.25 * ((C)ld(row - 1) + (C)ld(row + 1)) + (C)0.5 * (C)ld(row);
-      acc += wz * wy * line;
+      for (int dy = -1; dy <= 1; dy++) {
+        C wy = dy == 0 ? (C)0.5 : (C)0.25;
+        const Tf *row = rf + q + dz * gf.sz + dy * gf.sy;
+        C line = (C)0.25 * ((C)ld(row - 1) + (C)ld(row + 1)) + (C)0.5 * (C)ld(row);
+        acc += wz * wy * line;
+      }
     }
+    st(fc + r.off + I, acc);
   }
-  st(fc + t.p, acc);
 }
 
+// Interpolation and correction: rows/planes of the fine grid.
 template <int DIM, typename Tc, typename Tf>
 __global__ void kb_prolong(const BXfer *__restrict__ xs, Geo gc, Geo gf) {
   typedef typename CT<Tf>::type C;
-  int pi;
-  Idx t = bnode<DIM>(gf, pi);
-  if (!t.interior) return;
-  const Tc *ec = (const Tc *)xs[pi].src;
-  Tf *uf = (Tf *)xs[pi].dst;
-  int I = t.i >> 1, J = t.j >> 1, K = t.k >> 1;
-  int oi = t.i & 1, oj = t.j & 1, ok = DIM == 3 ? (t.k & 1) : 0;
-  C acc = 0;
-  for (int a = 0; a <= ok; a++)
-    for (int b = 0; b <= oj; b++) {
-      const Tc *row = ec + (long long)(K + a) * gc.sz + (long long)(J + b) * gc.sy + I;
-      acc += oi ? (C)0.5 * ((C)ld(row) + (C)ld(row + 1)) : (C)ld(row);
-    }
-  C w = (oj ? (C)0.5 : (C)1) * (ok ? (C)0.5 : (C)1);
-  st(uf + t.p, (C)ld(uf + t.p) + w * acc);
+  BRow<DIM> r = brow<DIM>(gf, 1);
+  const Tc *ec = (const Tc *)xs[r.pi].src;
+  Tf *uf = (Tf *)xs[r.pi].dst;
+  const int J = r.j >> 1, K = r.k >> 1, oj = r.j & 1, ok = DIM == 3 ? (r.k & 1) : 0;
+  const C w = (oj ? (C)0.5 : (C)1) * (ok ? (C)0.5 : (C)1);
+  for (int i = 1 + (int)threadIdx.x; i <= gf.n - 2; i += (int)blockDim.x) {
+    const int I = i >> 1, oi = i & 1;
+    C acc = 0;
+    for (int a = 0; a <= ok; a++)
+      for (int b = 0; b <= oj; b++) {
+        const Tc *row = ec + (long long)(K + a) * gc.sz + (long long)(J + b) * gc.sy + I;
+        acc += oi ? (C)0.5 * ((C)ld(row) + (C)ld(row + 1)) : (C)ld(row);
+      }
+    const long long p = r.off + i;
+    st(uf + p, (C)ld(uf + p) + w * acc);
+  }
 }
 
 // Per-problem partial sums of the FP64 outer residual squared (kPartBlocks
@@ -343,12 +356,15 @@ template <typename D> struct Group {
   std::vector<D> items;
 };
 
-dim3 bgrid(int dim, int n, int count) {
-  return dim3((unsigned)((n + 127) / 128), (unsigned)n, (unsigned)(dim == 3 ? n * count : count));
+// One block per row (and plane) of one problem: interior rows/planes only
+// (`all` = every row and plane, for zeroing).
+dim3 bgrid(int dim, int n, int count, bool all = false) {
+  unsigned rows = (unsigned)(all ? n : n - 2);
+  return dim3(rows, dim == 3 ? rows : (unsigned)count, dim == 3 ? (unsigned)count : 1u);
 }
+unsigned bthreads(int n) { return n > 129 ? 256u : 128u; }
 
-// Largest count of problems per launch so that grid.z stays within 65535.
-int chunk_of(int dim, int n) { return dim == 3 ? std::max(1, 65535 / n) : 65535; }
+int chunk_of(int, int) { return 65535; }
 
 BOp make_op(const Level &L) {
   BOp o;
@@ -389,7 +405,7 @@ cudaError_t launch_group_op(int what, const std::vector<BOp> &items, mg_batch *b
     int count = (int)std::min<size_t>(chunk, items.size() - base);
     const BOp *dev = (const BOp *)push(b, items.data() + base, sizeof(BOp) * count);
     if (!dev) return cudaErrorMemoryAllocation;
-    dim3 blk(128), gr = bgrid(dim, n, count);
+    dim3 blk(bthreads(n)), gr = bgrid(dim, n, count, what == 3);
     cudaStream_t s = b->stream;
 #define OPK(K, ...)                                                                       \
   if (dim == 2) {                                                                         \
@@ -423,7 +439,7 @@ cudaError_t launch_group_xfer(bool restrict_, const std::vector<BXfer> &items, m
     int count = (int)std::min<size_t>(chunk, items.size() - base);
     const BXfer *dev = (const BXfer *)push(b, items.data() + base, sizeof(BXfer) * count);
     if (!dev) return cudaErrorMemoryAllocation;
-    dim3 blk(128), gr = bgrid(dim, n, count);
+    dim3 blk(bthreads(n)), gr = bgrid(dim, n, count);
     cudaStream_t s = b->stream;
     // (fine type, coarse type): (T,T) or (T, double) for the FP64 coarsest
     if (restrict_) {
