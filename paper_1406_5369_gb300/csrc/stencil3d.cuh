@@ -110,7 +110,8 @@ enum { kJacobi = 0, kRB = 1, kResid = 2, kNorm = 3 };
 // offset inside a slot and whether the piece lies inside its array.
 // issue() stages consecutive planes: it is called first with plane `first`
 // (start()), then with each following plane, so the source addresses advance
-// by one plane stride per call instead of being recomputed.
+// by one plane stride per call instead of being recomputed. Pieces outside
+// their array keep a valid address and a zero stride and copy nothing.
 template <int K> struct Pieces {
   const unsigned char *src[K];
   const unsigned char *anchor;  // a valid address handed to zero-filled copies
@@ -121,15 +122,45 @@ template <int K> struct Pieces {
 #pragma unroll
     for (int k = 0; k < K; k++) src[k] += (long long)first * pstep[k];
   }
-  // Stages the current plane into `slot` (zero-fill unless `pok`), advances.
+  // Stages the current plane into `slot` (zero-fill unless `pok`, which is
+  // the same for the whole block), then advances.
+  __device__ __forceinline__ void issue(unsigned char *slot, bool pok) {
+    if (pok) {
+#pragma unroll
+      for (int k = 0; k < K; k++)
+        if (soff[k] >= 0) cp_async16(slot + soff[k], src[k], ok[k]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < K; k++)
+        if (soff[k] >= 0) cp_async16(slot + soff[k], anchor, false);
+    }
+#pragma unroll
+    for (int k = 0; k < K; k++) src[k] += pstep[k];
+    cp_async_commit();
+  }
+};
+
+// The stencil kernels' pieces all advance by the same plane stride, so they
+// share one; a piece outside its array issues a zero-filling copy of a valid
+// address instead (a per-piece branch, no 64-bit selects).
+template <int K> struct Pieces1 {
+  const unsigned char *src[K];
+  const unsigned char *anchor;
+  long long pstep;
+  int soff[K];  // -1: no piece
+  bool ok[K];
+  __device__ __forceinline__ void start(int first) {
+#pragma unroll
+    for (int k = 0; k < K; k++) src[k] += (long long)first * pstep;
+  }
   __device__ __forceinline__ void issue(unsigned char *slot, bool pok) {
 #pragma unroll
     for (int k = 0; k < K; k++) {
       if (soff[k] >= 0) {
-        const bool v = ok[k] && pok;
-        cp_async16(slot + soff[k], v ? src[k] : anchor, v);
-        src[k] += pstep[k];
+        if (ok[k] && pok) cp_async16(slot + soff[k], src[k], true);
+        else cp_async16(slot + soff[k], anchor, false);
       }
+      src[k] += pstep;
     }
     cp_async_commit();
   }
@@ -139,18 +170,18 @@ template <int K> struct Pieces {
 // left halo, 32 lanes, right halo), f rows y0 .. y0+kTY-1 (32 chunks).
 constexpr int kStPieces = ((kTY + 2) * kUChunks + kTY * 32 + 32 * kTY - 1) / (32 * kTY);
 template <typename T>
-__device__ __forceinline__ void stencil_pieces(Pieces<kStPieces> &pc, const T *u, const T *f, int y0, int x0, int n,
+__device__ __forceinline__ void stencil_pieces(Pieces1<kStPieces> &pc, const T *u, const T *f, int y0, int x0, int n,
                                                int pitch, long long P) {
   constexpr int V = VW<T>::V;
   constexpr int NU = (kTY + 2) * kUChunks, NF = kTY * 32;
   pc.anchor = (const unsigned char *)u;
+  pc.pstep = P * (long long)sizeof(T);
 #pragma unroll
   for (int k = 0; k < kStPieces; k++) {
     const int i = threadIdx.x + k * 32 * kTY;
     pc.soff[k] = -1;
     pc.ok[k] = false;
     pc.src[k] = (const unsigned char *)u;
-    pc.pstep[k] = P * (long long)sizeof(T);
     if (i < NU) {
       const int rr = i / kUChunks, ch = i - rr * kUChunks;
       const int y = y0 - 1 + rr, x = x0 + (ch - 1) * V;
@@ -168,10 +199,11 @@ __device__ __forceinline__ void stencil_pieces(Pieces<kStPieces> &pc, const T *u
 }
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(32 * kTY, 3) k3_stencil(Args3 a, const Args3 *__restrict__ list) {
+__global__ void __launch_bounds__(32 * kTY, MODE == kResid ? 2 : 3) k3_stencil(Args3 a, const Args3 *__restrict__ list) {
   typedef typename CT<T>::type C;
   constexpr int V = VW<T>::V;
   constexpr int TX = 32 * V;
+  constexpr int RB = kRingZ * kSlotB;  // ring bytes
   extern __shared__ __align__(16) unsigned char smem[];
   if (list) take_problem(a, list[blockIdx.z]);
   __shared__ double wsum[kTY];
@@ -182,85 +214,115 @@ __global__ void __launch_bounds__(32 * kTY, 3) k3_stencil(Args3 a, const Args3 *
   const int y0 = 1 + ty * kTY, y = y0 + w;
   const int x0 = tx * TX, cl = x0 + V * lane;
   const int z0 = 1 + blockIdx.y * a.zc, z1 = min(z0 + a.zc, n - 1);
-  const bool wact = y <= n - 2;                        // warp-uniform
+  const bool wact = y <= n - 2;  // warp-uniform
   const C alpha = pick<C>(a.alpha, a.alphaf), bx = pick<C>(a.bx, a.bxf), by = pick<C>(a.by, a.byf);
   const C bz = pick<C>(a.bz, a.bzf), gamma = pick<C>(a.gamma, a.gammaf);
   const C cd = pick<C>(a.cd, a.cdf), cx = pick<C>(a.cx, a.cxf), cy = pick<C>(a.cy, a.cyf), cz = pick<C>(a.cz, a.czf);
   const bool has_gamma = a.has_gamma != 0;
   double acc = 0.0;
 
-  auto slot = [&](int p) { return smem + (p % kRingZ) * kSlotB; };
-  const unsigned char *own = smem + (w + 1) * kURowB + (lane + 1) * 16;  // + slot offset
-  const unsigned char *above = smem + w * kURowB + (lane + 1) * 16;
-  const unsigned char *below = smem + (w + 2) * kURowB + (lane + 1) * 16;
-  const unsigned char *frw = smem + (kTY + 2) * kURowB + w * kFRowB + lane * 16;
-  const unsigned char *halo = smem + (w + 1) * kURowB + (lane == 0 ? 16 - (int)sizeof(T) : 33 * 16);
+  // shared-memory byte offsets inside a slot (32-bit)
+  const int own = (w + 1) * kURowB + (lane + 1) * 16;
+  const int above = own - kURowB, below = own + kURowB;
+  const int frw = (kTY + 2) * kURowB + w * kFRowB + lane * 16;
+  const int halo = (w + 1) * kURowB + (lane == 0 ? 16 - (int)sizeof(T) : 33 * 16);
 
-  Pieces<kStPieces> pc;
+  Pieces1<kStPieces> pc;
   stencil_pieces<T>(pc, (const T *)a.u, (const T *)a.f, y0, x0, n, pitch, P);
   // Planes z0 - 1 .. z0 + kAhead up front; step z then refills with z + kAhead + 1.
+  // Ring slot of plane p: p % kRingZ, tracked as byte offsets.
+  int so_fill = ((z0 - 1) % kRingZ) * kSlotB;
+  auto advance = [](int o) { return o + kSlotB == RB ? 0 : o + kSlotB; };
   pc.start(z0 - 1);
   for (int k = 0; k <= kAhead + 1; k++) {
-    const int p = z0 - 1 + k;
-    pc.issue(slot(p), p <= z1);
+    pc.issue(smem + so_fill, z0 - 1 + k <= z1);
+    so_fill = advance(so_fill);
   }
-  // Columns of this lane inside the domain (the same on every plane).
-  bool inq[V];
-#pragma unroll
-  for (int q = 0; q < V; q++) inq[q] = cl + q >= 1 && cl + q <= n - 2;
+  // Most lanes have all V columns inside the domain and skip the boundary
+  // fix-ups below (the same on every plane).
+  const bool lane_in = cl >= 1 && cl + V - 1 <= n - 2;
   T *outp = (T *)a.out + (long long)z0 * P + (long long)y * pitch + cl;
+  int so_cur = (z0 % kRingZ) * kSlotB, so_next = advance(so_cur);
 
+  // um, uc: planes z - 1 and z of the own row; up receives plane z + 1.
   C um[V], uc[V], up[V];
+  cp_async_wait<kAhead - 1>();
+  __syncthreads();
+  if (wact) {
+    vld((const T *)(smem + own + (so_cur == 0 ? RB - kSlotB : so_cur - kSlotB)), um);
+    vld((const T *)(smem + own + so_cur), uc);
+  }
   for (int z = z0; z < z1; z++) {
     cp_async_wait<kAhead - 1>();  // planes up to z + 1 have landed (own copies)
     __syncthreads();              // ... everyone's, and nobody still reads plane z - 2
     C ys[V], yn[V], fc[V];
     C hx = 0;
-    const long long sz = (z % kRingZ) * kSlotB, szp = ((z + 1) % kRingZ) * kSlotB;
     if (wact) {
-      if (z == z0) {
-        vld((const T *)(own + ((z + kRingZ - 1) % kRingZ) * kSlotB), um);
-        vld((const T *)(own + sz), uc);
-      }
-      vld((const T *)(own + szp), up);
-      vld((const T *)(above + sz), ys);
-      vld((const T *)(below + sz), yn);
-      vld((const T *)(frw + sz), fc);
-      if (lane == 0 || lane == 31) hx = sld<T>(halo + sz);
+      vld((const T *)(smem + own + so_next), up);
+      vld((const T *)(smem + above + so_cur), ys);
+      vld((const T *)(smem + below + so_cur), yn);
+      vld((const T *)(smem + frw + so_cur), fc);
+      if (lane == 0 || lane == 31) hx = sld<T>(smem + halo + so_cur);
     }
-    // The slot of plane z + kAhead + 1 held plane z - 2 (on the first step
-    // plane z0 - 1 sits in another slot and was read above).
-    pc.issue(slot(z + kAhead + 1), z + kAhead + 1 <= z1);
-    if (wact) {
-      C wl = shup(uc[V - 1]), er = shdn(uc[0]);
-      if (lane == 0) wl = hx;
-      if (lane == 31) er = hx;
-      C res[V];
-      C sq = 0;
-      const int rbpar = (y + z + a.color) & 1;  // node (cl + q, y, z) has colour a.color iff (q + rbpar) is even
+    // the slot of plane z + kAhead + 1 held plane z - 2
+    pc.issue(smem + so_fill, z + kAhead + 1 <= z1);
+    so_fill = advance(so_fill);
+    so_cur = so_next;
+    so_next = advance(so_next);
+    if (!wact) continue;
+    C wl = shup(uc[V - 1]), er = shdn(uc[0]);
+    if (lane == 0) wl = hx;
+    if (lane == 31) er = hx;
+    C res[V];
+    auto nbr = [&](int q, C &wv, C &ev) {
+      wv = q == 0 ? wl : uc[q - 1];
+      ev = q == V - 1 ? er : uc[q + 1];
+    };
+    if (MODE == kJacobi || MODE == kRB) {
+      auto relax = [&](int q) {
+        C wv, ev;
+        nbr(q, wv, ev);
+        C nv = alpha * fc[q] + bx * (wv + ev) + by * (ys[q] + yn[q]) + bz * (um[q] + up[q]);
+        if (has_gamma) nv += gamma * uc[q];
+        return nv;
+      };
+      if (MODE == kJacobi) {
 #pragma unroll
-      for (int q = 0; q < V; q++) {
-        const C wv = q == 0 ? wl : uc[q - 1];
-        const C ev = q == V - 1 ? er : uc[q + 1];
-        const bool in = inq[q];
-        if (MODE == kJacobi || MODE == kRB) {
-          C nv = alpha * fc[q] + bx * (wv + ev) + by * (ys[q] + yn[q]) + bz * (um[q] + up[q]);
-          if (has_gamma) nv += gamma * uc[q];
-          // cl is even (V is), so the colour of column cl + q alternates with q
-          const bool upd = MODE == kJacobi ? in : (in && ((q + rbpar) & 1) == 0);
-          res[q] = upd ? nv : uc[q];
+        for (int q = 0; q < V; q++) res[q] = relax(q);
+      } else {
+        // cl is even, so column cl + q has this half-sweep's colour iff q has
+        // the parity of rbpar (warp-uniform): only those columns are computed
+        const int rbpar = (y + z + a.color) & 1;
+        if (rbpar == 0) {
+#pragma unroll
+          for (int q = 0; q < V; q++) res[q] = (q & 1) ? uc[q] : relax(q);
         } else {
-          const C rr = fc[q] - cd * uc[q] + cx * (wv + ev) + cy * (ys[q] + yn[q]) + cz * (um[q] + up[q]);
-          if (MODE == kResid) res[q] = in ? rr : (C)0;
-          if (MODE == kNorm && in) sq += rr * rr;
+#pragma unroll
+          for (int q = 0; q < V; q++) res[q] = (q & 1) ? relax(q) : uc[q];
         }
       }
-      if (MODE == kNorm) acc += (double)sq;
-      if (MODE != kNorm && cl < pitch) vst(outp, res);
-      outp += P;
+      if (!lane_in) {
 #pragma unroll
-      for (int q = 0; q < V; q++) { um[q] = uc[q]; uc[q] = up[q]; }
+        for (int q = 0; q < V; q++)
+          if (cl + q < 1 || cl + q > n - 2) res[q] = uc[q];
+      }
+    } else {
+      C sq = 0;
+#pragma unroll
+      for (int q = 0; q < V; q++) {
+        C wv, ev;
+        nbr(q, wv, ev);
+        const C rr = fc[q] - cd * uc[q] + cx * (wv + ev) + cy * (ys[q] + yn[q]) + cz * (um[q] + up[q]);
+        const bool in = cl + q >= 1 && cl + q <= n - 2;
+        res[q] = in ? rr : (C)0;
+        if (MODE == kNorm) sq += res[q] * res[q];
+      }
+      if (MODE == kNorm) acc += (double)sq;
     }
+    if (MODE != kNorm && cl < pitch) vst(outp, res);
+    outp += P;
+#pragma unroll
+    for (int q = 0; q < V; q++) { um[q] = uc[q]; uc[q] = up[q]; }
   }
   cp_async_wait<0>();
   if (MODE == kNorm) {
@@ -441,7 +503,7 @@ __device__ __forceinline__ void dc_pieces(Pieces<DCP<Ti, UPDATE>::K> &pc, const 
     pc.soff[k] = -1;
     pc.ok[k] = false;
     pc.src[k] = (const unsigned char *)a.u;
-    pc.pstep[k] = a.plane * 8;
+    long long step = a.plane * 8;
     if (i < Q::NU) {
       const int rr = i / kUChunks, ch = i - rr * kUChunks;
       const int y = y0 - 1 + rr, x = x0 + (ch - 1) * 2;
@@ -453,7 +515,7 @@ __device__ __forceinline__ void dc_pieces(Pieces<DCP<Ti, UPDATE>::K> &pc, const 
       const int y = y0 - 1 + rr, x = x0 + (ch - 1) * EV;
       pc.ok[k] = y >= 0 && y < a.n && x >= 0 && x + EV <= a.pitchi;
       pc.src[k] = (const unsigned char *)(pc.ok[k] ? e + (long long)y * a.pitchi + x : e);
-      pc.pstep[k] = a.planei * (long long)sizeof(Ti);
+      step = a.planei * (long long)sizeof(Ti);
       pc.soff[k] = kDCWarps * kURowB + rr * L::ERowB + ch * 16;
     } else if (i < Q::NU + Q::NE + Q::NF) {
       const int j = i - Q::NU - Q::NE, rr = j >> 5, ch = j & 31;
@@ -462,6 +524,7 @@ __device__ __forceinline__ void dc_pieces(Pieces<DCP<Ti, UPDATE>::K> &pc, const 
       pc.src[k] = (const unsigned char *)(pc.ok[k] ? a.f + (long long)y * a.pitch + x : a.f);
       pc.soff[k] = kDCWarps * kURowB + kDCWarps * L::ERowB + rr * kFRowB + ch * 16;
     }
+    pc.pstep[k] = pc.ok[k] ? step : 0;
   }
 }
 
