@@ -52,13 +52,19 @@ cudaError_t launch_dc(oz::ArgsOuter a, int n, int *nparts, cudaStream_t s, const
   constexpr int IBP = IB < 16 ? 16 : IB;
   constexpr size_t smem = (size_t)oz::kWarps * oz::kRing * 32 * (32 + 32 + IBP);
   static int bps = 0;
-  if (!bps) bps = occupancy(oz::k_dc2d<Ti, UPDATE, ACC64>, 32 * oz::kWarps, smem);
+  if (!bps) {
+    bps = occupancy(oz::k_dc2d<Ti, UPDATE, ACC64, false>, 32 * oz::kWarps, smem);
+    occupancy(oz::k_dc2d<Ti, UPDATE, ACC64, true>, 32 * oz::kWarps, smem);  // sets its shared-memory limit
+  }
   chunking(a, n, bps, max_parts);
   long long warps = (long long)a.nstrips * a.nchunks;
   *nparts = (int)warps;
   a.pstride = max_parts;
   unsigned blocks = (unsigned)((warps + oz::kWarps - 1) / oz::kWarps);
-  oz::k_dc2d<Ti, UPDATE, ACC64><<<dim3(blocks, (unsigned)count), 32 * oz::kWarps, smem, s>>>(a, list);
+  if (list)
+    oz::k_dc2d<Ti, UPDATE, ACC64, true><<<dim3(blocks, (unsigned)count), 32 * oz::kWarps, smem, s>>>(a, list);
+  else
+    oz::k_dc2d<Ti, UPDATE, ACC64, false><<<blocks, 32 * oz::kWarps, smem, s>>>(a, nullptr);
   return cudaGetLastError();
 }
 

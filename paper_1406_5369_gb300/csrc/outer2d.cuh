@@ -128,10 +128,12 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // ---------------------------------------------------------------- outer step
-template <typename Ti, bool UPDATE, bool ACC64>
+// LIST: a launch over many problems (records in `list`); the single-problem
+// instance keeps its arguments untouched, as the compiler prefers.
+template <typename Ti, bool UPDATE, bool ACC64, bool LIST = false>
 __global__ void __launch_bounds__(32 * kWarps) k_dc2d(ArgsOuter a, const ArgsOuter *__restrict__ list) {
   extern __shared__ __align__(16) unsigned char smem[];
-  if (list) take_problem(a, list[blockIdx.y]);
+  if (LIST) take_problem(a, list[blockIdx.y]);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const long long gw = (long long)blockIdx.x * kWarps + wib;
   if (gw >= (long long)a.nstrips * a.nchunks) return;
