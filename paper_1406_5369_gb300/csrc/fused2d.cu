@@ -28,6 +28,11 @@ int sm_count() {
 // Rows per chunk: as many chunks as fill one wave of resident warps,
 // rounded up to a multiple of 8. Small levels get 8-row chunks: each warp
 // then walks only 3 blocks of 8 rows, which keeps their latency short.
+// Rows per chunk of a list launch (many problems): the problems supply the
+// parallelism, so chunks are long (little of the 8-row warm-up is repeated)
+// and depend on the level size alone.
+constexpr int kListRows = 256;
+
 int pick_rows(int n, int nstrips, int blocks_per_sm, int warps_per_block, int R_override) {
   if (R_override > 0) return (R_override + 7) / 8 * 8;
   long long slots = (long long)sm_count() * blocks_per_sm * warps_per_block;
@@ -66,61 +71,102 @@ fz::Args2D make_args(const Level &L, const Level &Cl, double omega, int R_overri
   a.cyf = (float)a.cy;
   a.cdf = (float)a.cd;
   a.has_gamma = a.gamma != 0.0;
+  a.kx = L.kf[0];
+  a.ky = L.kf[1];
+  a.omega = omega;
+  a.h2 = 1.0 / L.inv_h2;
+  a.ih2 = L.inv_h2;
+  a.omegaf = (float)a.omega;
+  a.h2f = (float)a.h2;
+  a.ih2f = (float)a.ih2;
   return a;
 }
 
-template <typename T, int NU, bool ZERO>
+template <typename T, int NU, bool ZERO, bool VAR = false>
 cudaError_t launch_pre(fz::Args2D a, int R_override, const Level &L, cudaStream_t s, const fz::Args2D *list = nullptr,
                        int count = 1) {
   constexpr int W = fz::Warps<T>::value;
-  constexpr size_t smem = (size_t)W * fz::kRing * 32 * fz::Lane<T>::bytes * 2;
+  constexpr size_t smem = (size_t)W * (fz::kRing * 32 * fz::Lane<T>::bytes * 2 +
+                                       (VAR ? (size_t)fz::kFaceRing * 32 * fz::Lane<T>::bytes * 2 : 0));
   static bool ready = false;
   static int bps = 1;
   if (!ready) {
-    cudaError_t e = prepare(fz::k_pre2d<T, NU, ZERO>, smem);
+    cudaError_t e = prepare(fz::k_pre2d<T, NU, ZERO, VAR>, smem);
     if (e != cudaSuccess) return e;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fz::k_pre2d<T, NU, ZERO>, 32 * W, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fz::k_pre2d<T, NU, ZERO, VAR>, 32 * W, smem);
     if (bps < 1) bps = 1;
     ready = true;
   }
   if (R_override <= 0) {
-    a.R = pick_rows(L.n, a.nstrips, bps, W, 0);
+    a.R = pick_rows(L.n, a.nstrips, bps, W, list ? kListRows : 0);
     a.nchunks = (L.n + a.R - 1) / a.R;
   }
   long long warps = (long long)a.nstrips * a.nchunks;
   unsigned blocks = (unsigned)((warps + W - 1) / W);
-  fz::k_pre2d<T, NU, ZERO><<<dim3(blocks, (unsigned)count), 32 * W, smem, s>>>(a, list);
+  fz::k_pre2d<T, NU, ZERO, VAR><<<dim3(blocks, (unsigned)count), 32 * W, smem, s>>>(a, list);
   return cudaGetLastError();
 }
 
-template <typename T, int NU>
+template <typename T, int NU, bool VAR = false>
 cudaError_t launch_post(fz::Args2D a, int R_override, const Level &L, cudaStream_t s, const fz::Args2D *list = nullptr,
                         int count = 1) {
   constexpr int W = fz::Warps<T>::value;
-  constexpr size_t smem = (size_t)W * fz::kRing * 32 * (2 * fz::Lane<T>::bytes + 2 * sizeof(T));
+  constexpr size_t smem = (size_t)W * (fz::kRing * 32 * (2 * fz::Lane<T>::bytes + 2 * sizeof(T)) +
+                                       (VAR ? (size_t)fz::kFaceRing * 32 * fz::Lane<T>::bytes * 2 : 0));
   static bool ready = false;
   static int bps = 1;
   if (!ready) {
-    cudaError_t e = prepare(fz::k_post2d<T, NU>, smem);
+    cudaError_t e = prepare(fz::k_post2d<T, NU, VAR>, smem);
     if (e != cudaSuccess) return e;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fz::k_post2d<T, NU>, 32 * W, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fz::k_post2d<T, NU, VAR>, 32 * W, smem);
     if (bps < 1) bps = 1;
     ready = true;
   }
   if (R_override <= 0) {
-    a.R = pick_rows(L.n, a.nstrips, bps, W, 0);
+    a.R = pick_rows(L.n, a.nstrips, bps, W, list ? kListRows : 0);
     a.nchunks = (L.n + a.R - 1) / a.R;
   }
   long long warps = (long long)a.nstrips * a.nchunks;
   unsigned blocks = (unsigned)((warps + W - 1) / W);
-  fz::k_post2d<T, NU><<<dim3(blocks, (unsigned)count), 32 * W, smem, s>>>(a, list);
+  fz::k_post2d<T, NU, VAR><<<dim3(blocks, (unsigned)count), 32 * W, smem, s>>>(a, list);
   return cudaGetLastError();
+}
+
+// Storage type, sweep count, zero start and stencil kind -> kernel instance.
+cudaError_t dispatch_pre(fz::Args2D a, int R, const Level &L, cudaStream_t s, const fz::Args2D *list, int count,
+                         bool zero, int nu) {
+  const bool var = L.kf[0] != nullptr;
+#define MG_PRE(T, NUv, Z)                                                                      \
+  return var ? launch_pre<T, NUv, Z, true>(a, R, L, s, list, count) : launch_pre<T, NUv, Z, false>(a, R, L, s, list, count)
+  if (L.dtype == F32) {
+    if (nu == 1) { if (zero) { MG_PRE(float, 1, true); } else { MG_PRE(float, 1, false); } }
+    if (zero) { MG_PRE(float, 2, true); } else { MG_PRE(float, 2, false); }
+  }
+#undef MG_PRE
+  if (nu == 1) return zero ? launch_pre<double, 1, true>(a, R, L, s, list, count) : launch_pre<double, 1, false>(a, R, L, s, list, count);
+  return zero ? launch_pre<double, 2, true>(a, R, L, s, list, count) : launch_pre<double, 2, false>(a, R, L, s, list, count);
+}
+
+cudaError_t dispatch_post(fz::Args2D a, int R, const Level &L, cudaStream_t s, const fz::Args2D *list, int count,
+                          int nu) {
+  const bool var = L.kf[0] != nullptr;
+#define MG_POST(T, NUv) \
+  return var ? launch_post<T, NUv, true>(a, R, L, s, list, count) : launch_post<T, NUv, false>(a, R, L, s, list, count)
+  if (L.dtype == F32) {
+    if (nu == 1) { MG_POST(float, 1); }
+    MG_POST(float, 2);
+  }
+#undef MG_POST
+  return nu == 1 ? launch_post<double, 1>(a, R, L, s, list, count) : launch_post<double, 2>(a, R, L, s, list, count);
 }
 
 }  // namespace
 
+// Constant stencil in FP64 or FP32; variable stencil in FP32 (faces stored in
+// the level's type; the FP64 variable-stencil instance would not fit in the
+// register file without spilling, so those levels keep the generic kernels).
 bool fused_ok(const Level &L, const Level &Cl, int nu) {
-  return L.dim == 2 && !L.kf[0] && (L.dtype == F64 || L.dtype == F32) && Cl.dtype == L.dtype &&
+  return L.dim == 2 && (L.dtype == F64 || L.dtype == F32) && (!L.kf[0] || L.dtype == F32) && Cl.dtype == L.dtype &&
          (nu == 1 || nu == 2) && L.n >= 33;
 }
 
@@ -131,12 +177,7 @@ cudaError_t pre_fused(const Level &L, const void *uin, void *uout, const Level &
   a.f = L.f;
   a.uout = uout;
   a.fc = fc;
-  if (L.dtype == F32) {
-    if (nu == 1) return zero ? launch_pre<float, 1, true>(a, R, L, s) : launch_pre<float, 1, false>(a, R, L, s);
-    return zero ? launch_pre<float, 2, true>(a, R, L, s) : launch_pre<float, 2, false>(a, R, L, s);
-  }
-  if (nu == 1) return zero ? launch_pre<double, 1, true>(a, R, L, s) : launch_pre<double, 1, false>(a, R, L, s);
-  return zero ? launch_pre<double, 2, true>(a, R, L, s) : launch_pre<double, 2, false>(a, R, L, s);
+  return dispatch_pre(a, R, L, s, nullptr, 1, zero, nu);
 }
 
 cudaError_t post_fused(const Level &L, const void *uin, void *uout, const Level &Cl, const void *ec, int nu,
@@ -146,8 +187,7 @@ cudaError_t post_fused(const Level &L, const void *uin, void *uout, const Level 
   a.f = L.f;
   a.uout = uout;
   a.ec = ec;
-  if (L.dtype == F32) return nu == 1 ? launch_post<float, 1>(a, R, L, s) : launch_post<float, 2>(a, R, L, s);
-  return nu == 1 ? launch_post<double, 1>(a, R, L, s) : launch_post<double, 2>(a, R, L, s);
+  return dispatch_post(a, R, L, s, nullptr, 1, nu);
 }
 
 }  // namespace d2
@@ -170,22 +210,13 @@ fz::Args2D fused_record(const Level &L, const Level &Cl, double omega, const voi
 cudaError_t pre_fused_list(const Level &L, const Level &Cl, const fz::Args2D *list, int count, bool zero, int nu,
                            cudaStream_t s) {
   fz::Args2D a = make_args(L, Cl, 1.0, 0, 1);
-  if (L.dtype == F32) {
-    if (nu == 1)
-      return zero ? launch_pre<float, 1, true>(a, 0, L, s, list, count) : launch_pre<float, 1, false>(a, 0, L, s, list, count);
-    return zero ? launch_pre<float, 2, true>(a, 0, L, s, list, count) : launch_pre<float, 2, false>(a, 0, L, s, list, count);
-  }
-  if (nu == 1)
-    return zero ? launch_pre<double, 1, true>(a, 0, L, s, list, count) : launch_pre<double, 1, false>(a, 0, L, s, list, count);
-  return zero ? launch_pre<double, 2, true>(a, 0, L, s, list, count) : launch_pre<double, 2, false>(a, 0, L, s, list, count);
+  return dispatch_pre(a, 0, L, s, list, count, zero, nu);
 }
 
 cudaError_t post_fused_list(const Level &L, const Level &Cl, const fz::Args2D *list, int count, int nu,
                             cudaStream_t s) {
   fz::Args2D a = make_args(L, Cl, 1.0, 0, 1);
-  if (L.dtype == F32)
-    return nu == 1 ? launch_post<float, 1>(a, 0, L, s, list, count) : launch_post<float, 2>(a, 0, L, s, list, count);
-  return nu == 1 ? launch_post<double, 1>(a, 0, L, s, list, count) : launch_post<double, 2>(a, 0, L, s, list, count);
+  return dispatch_post(a, 0, L, s, list, count, nu);
 }
 
 }  // namespace d2

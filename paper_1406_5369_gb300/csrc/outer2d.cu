@@ -20,10 +20,13 @@ int sm_count() {
   return count;
 }
 
-void chunking(oz::ArgsOuter &a, int n, int bps, int max_parts = kMaxPartials) {
+// list: a launch over many problems, which supply the parallelism: chunks of
+// 256 rows, a function of the size alone (so is each problem's partition of
+// its norm sum, whatever else is in the list).
+void chunking(oz::ArgsOuter &a, int n, int bps, int max_parts = kMaxPartials, bool list = false) {
   a.nstrips = (n + oz::kOut - 1) / oz::kOut;
   long long slots = (long long)sm_count() * bps * oz::kWarps;
-  long long nchunks = slots / a.nstrips;
+  long long nchunks = list ? (n + 255) / 256 : slots / a.nstrips;
   if (nchunks < 1) nchunks = 1;
   int R = (int)((n + nchunks - 1) / nchunks);
   R = (R + 7) / 8 * 8;
@@ -56,7 +59,7 @@ cudaError_t launch_dc(oz::ArgsOuter a, int n, int *nparts, cudaStream_t s, const
     bps = occupancy(oz::k_dc2d<Ti, UPDATE, ACC64, false>, 32 * oz::kWarps, smem);
     occupancy(oz::k_dc2d<Ti, UPDATE, ACC64, true>, 32 * oz::kWarps, smem);  // sets its shared-memory limit
   }
-  chunking(a, n, bps, max_parts);
+  chunking(a, n, bps, max_parts, list != nullptr);
   long long warps = (long long)a.nstrips * a.nchunks;
   *nparts = (int)warps;
   a.pstride = max_parts;

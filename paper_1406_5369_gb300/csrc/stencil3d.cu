@@ -33,10 +33,12 @@ template <typename K> int resident(K kernel, int threads, size_t smem, int *cach
 
 // Planes per z-chunk: enough chunks for about two waves of resident blocks,
 // at least 8 planes each, and no more than `max_blocks` blocks in total.
-int pick_zc(int n, long long base_blocks, int per_sm, long long max_blocks) {
+// list: a launch over many problems, which supply the parallelism: chunks of
+// about 64 planes, a function of the size alone.
+int pick_zc(int n, long long base_blocks, int per_sm, long long max_blocks, bool list = false) {
   const int planes = n - 2;
   long long want = 2LL * sm_count() * per_sm;
-  long long nz = (want + base_blocks - 1) / base_blocks;
+  long long nz = list ? (planes + 63) / 64 : (want + base_blocks - 1) / base_blocks;
   if (nz > planes / 8) nz = planes / 8;
   if (nz * base_blocks > max_blocks) nz = max_blocks / base_blocks;
   if (nz < 1) nz = 1;
@@ -84,7 +86,7 @@ cudaError_t launch_stencil(z3::Args3 a, long long max_blocks, int *nblocks, cuda
   a.ntx = (a.n - 1 + 32 * V - 1) / (32 * V);
   a.nty = (a.n - 2 + z3::kTY - 1) / z3::kTY;
   long long base = (long long)a.ntx * a.nty;
-  a.zc = pick_zc(a.n, base, r, max_blocks);
+  a.zc = pick_zc(a.n, base, r, max_blocks, list != nullptr);
   int nz = (a.n - 2 + a.zc - 1) / a.zc;
   if (nblocks) *nblocks = (int)(base * nz);
   z3::k3_stencil<T, MODE><<<dim3((unsigned)base, (unsigned)nz, (unsigned)count), 32 * z3::kTY, smem, s>>>(a, list);
@@ -192,7 +194,7 @@ cudaError_t launch_dc(z3::ArgsDC3 a, int *nparts, cudaStream_t s, const z3::Args
   a.ntx = (a.n - 1 + 63) / 64;
   a.nty = (a.n - 2 + z3::kTY - 1) / z3::kTY;
   long long base = (long long)a.ntx * a.nty;
-  a.zc = pick_zc(a.n, base, r, max_parts);
+  a.zc = pick_zc(a.n, base, r, max_parts, list != nullptr);
   int nz = (a.n - 2 + a.zc - 1) / a.zc;
   *nparts = (int)(base * nz);
   a.pstride = max_parts;

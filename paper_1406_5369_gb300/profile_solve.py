@@ -33,9 +33,12 @@ def main(argv=None) -> int:
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--warm", type=int, default=2)
     ap.add_argument("--inner-cycles", type=int, default=1)
+    ap.add_argument("--lognormal-k", action="store_true",
+                    help="variable coefficient k = exp(N(0,1)) per node (synth.lognormal_k)")
     a = ap.parse_args(argv)
     f = torch.from_numpy(synth.uniform_rhs(a.dim, a.n, synth.WORKLOAD_SEED_BASE + 2)).cuda()
-    s = Solver(a.dim, a.n, precision=a.precision, smoother=a.smoother, omega=a.omega, nu1=a.nu1, nu2=a.nu2,
+    k = synth.lognormal_k(a.dim, a.n, synth.WORKLOAD_SEED_BASE + 4) if a.lognormal_k else None
+    s = Solver(a.dim, a.n, k=k, precision=a.precision, smoother=a.smoother, omega=a.omega, nu1=a.nu1, nu2=a.nu2,
                inner_cycles=a.inner_cycles, maxit=80)
     s.set_rhs(f)
     for _ in range(a.warm):

@@ -112,3 +112,25 @@ def test_fullsize_config2_fp32_dc_reaches_tolerance():
     # the oracle recomputes the FP64 residual of the GPU solution
     rel = oracle.norm(oracle.residual(u, f)) / oracle.norm(f)
     assert rel <= 1.01e-10, rel
+
+
+@pytest.mark.parametrize("n,nu1,nu2,omega", [(65, 2, 1, 1.0), (257, 1, 2, 1.2), (1025, 2, 1, 1.0), (513, 2, 2, 0.9)])
+def test_fused_variable_coefficient_fp32_equals_unfused(n, nu1, nu2, omega):
+    # Lognormal k (harmonic faces), FP32 inner cycles of defect correction:
+    # the fused variable-stencil kernels against the one-kernel-per-operator
+    # path (both round in FP32, differently), then the oracle's residual of
+    # the fused path's answer after a solve to 1e-8.
+    need_gpu()
+    from paper_1406_5369_gb300 import Solver
+    k = synth.lognormal_k(2, n, 0x5EED0004 ^ n)
+    f = synth.uniform_rhs(2, n, 0x5EED0004 ^ (n + 1))
+    kw = dict(k=k, precision="fp32_dc", nu1=nu1, nu2=nu2, omega=omega)
+    a, ha = history(2, n, f, 4, fuse=True, **kw)
+    b, hb = history(2, n, f, 4, fuse=False, **kw)
+    assert np.all(np.abs(ha - hb) <= 1e-4 * hb + 1e-12), (ha, hb)
+    s = Solver(2, n, maxit=60, fuse=True, **kw)
+    s.set_rhs(f)
+    it, rr, _ = s.solve(1e-8)
+    u = s.get_solution()
+    faces = oracle.node_faces(k)
+    assert oracle.norm(oracle.residual(u, f, faces=faces)) / oracle.norm(f) <= 1.01e-8
