@@ -191,6 +191,9 @@ mg_status mg_residual_norm(mg_ctx *ctx, int level, double *out);
  * then V-cycles (defect-correction steps for *_DC) until
  * ||r_k||/r0 <= tol or maxit. *iters = cycles done, *relres = last ratio;
  * history (may be NULL) receives maxit+1 doubles, rho_0 = 1 .. rho_iters.
+ * When the solution was last set to zero (mg_set_solution(ctx, NULL), or
+ * the context is new) and the Dirichlet data are homogeneous, the initial
+ * residual is f itself and is formed without applying the stencil.
  * Returns MG_ENOCONV if the residual is not finite or tol was not reached. */
 mg_status mg_solve(mg_ctx *ctx, double tol, int *iters, double *relres, double *history);
 

@@ -37,6 +37,8 @@ struct mg_ctx {
   int dim, n, nl;
   int variable;
   bool dc;                // defect-correction precision
+  bool bc_zero;           // homogeneous Dirichlet data
+  bool u_zero;            // the finest (user-level) interior solution is known to be zero
   mg_options opt;
   cudaStream_t stream;    // user stream
   cudaStream_t cap;       // private stream used for graph capture

@@ -398,6 +398,17 @@ mg_status op_norm(mg_ctx *c, int l, cudaStream_t s) {
   return MG_OK;
 }
 
+// op_norm(c, 0) when the finest interior u is zero and the Dirichlet data
+// are homogeneous: the residual is f itself (same norm, same defect).
+mg_status op_first_norm(mg_ctx *c, cudaStream_t s) {
+  Level &O = c->dc ? c->outer : c->lv[0];
+  TLAUNCH(c, MG_KERNEL_NORM, 0, s, mg::first_defect(O, c->dc ? &c->lv[0] : nullptr, c->partials, s));
+  TLAUNCH(c, MG_KERNEL_NORM, 0, s,
+          mg::norm_finalize_ex(c->partials, mg::kNormBlocks, c->norm_out, nullptr, c->dc ? c->dc_scale : nullptr,
+                               interior_count(O), s));
+  return MG_OK;
+}
+
 // One defect-correction step with the defect d already in lv[0].f:
 // e = V(0, d), then inner_cycles - 1 further cycles e = V(e, d); u += e. With `norm`, the residual of the updated u is
 // computed in the same pass (new defect in lv[0].f, norm in norm_out).
@@ -598,6 +609,8 @@ mg_status mg_create(int dim, int n, const mg_const_stencil *stencil, const doubl
   c->nl = level_count(n);
   c->variable = k != nullptr;
   c->opt = *opt;
+  c->bc_zero = !(bc && bc->dirichlet_values);
+  c->u_zero = true;  // the arena is zeroed below
   c->dc = opt->precision != MG_FP64;
   c->stream = (cudaStream_t)opt->stream;
   c->capturing_slot = -1;
@@ -698,6 +711,7 @@ mg_status mg_set_solution(mg_ctx *c, const double *u0) {
   } else {
     CK(copy_dense_interior(U, u0, dst, c->stream));
   }
+  c->u_zero = u0 == nullptr;
   return MG_OK;
 }
 
@@ -719,6 +733,7 @@ mg_status mg_set_field(mg_ctx *c, int level, mg_field field, const double *src) 
   if (field < MG_FIELD_U || field > MG_FIELD_R) return fail(MG_EINVAL, "unknown field");
   Level &L = c->lv[level];
   void *dst = field_ptr(L, field);
+  if (field == MG_FIELD_U && level == 0 && !c->dc) c->u_zero = false;
   if (L.dtype == mg::F64) {
     CK(copy_dense_to_pitched(L, src, dst, c->stream));
   } else {
@@ -752,6 +767,7 @@ mg_status mg_smooth(mg_ctx *c, int level, int sweeps) {
   if (!c) return fail(MG_EINVAL, "NULL context");
   if (level < 0 || level >= c->nl) return fail(MG_EINVAL, "level %d out of range", level);
   if (sweeps < 0) return fail(MG_EINVAL, "sweeps must be >= 0");
+  if (level == 0 && !c->dc) c->u_zero = false;
   return op_smooth(c, level, sweeps, c->stream);
 }
 
@@ -770,16 +786,19 @@ mg_status mg_restrict(mg_ctx *c, int level) {
 mg_status mg_prolongate(mg_ctx *c, int level) {
   if (!c) return fail(MG_EINVAL, "NULL context");
   if (level < 0 || level >= c->nl - 1) return fail(MG_EINVAL, "level %d has no coarser level", level);
+  if (level == 0 && !c->dc) c->u_zero = false;
   return op_prolong(c, level, c->stream);
 }
 
 mg_status mg_coarse_solve(mg_ctx *c) {
   if (!c) return fail(MG_EINVAL, "NULL context");
+  if (c->nl == 1 && !c->dc) c->u_zero = false;
   return op_coarse(c, c->stream);
 }
 
 mg_status mg_vcycle(mg_ctx *c) {
   if (!c) return fail(MG_EINVAL, "NULL context");
+  c->u_zero = false;
   return run(c, 0);
 }
 
@@ -795,7 +814,7 @@ mg_status mg_solve(mg_ctx *c, double tol, int *iters, double *relres, double *hi
   if (!c) return fail(MG_EINVAL, "NULL context");
   if (!(tol >= 0.0)) return fail(MG_EINVAL, "tol must be >= 0");
   double r0;
-  mg_status st = op_norm(c, 0, c->stream);
+  mg_status st = c->u_zero && c->bc_zero ? op_first_norm(c, c->stream) : op_norm(c, 0, c->stream);
   if (st) return st;
   if ((st = read_norm(c, &r0))) return st;
   if (history) history[0] = 1.0;
@@ -803,6 +822,7 @@ mg_status mg_solve(mg_ctx *c, double tol, int *iters, double *relres, double *hi
   double rho = r0 > 0 ? 1.0 : 0.0;
   if (!isfinite(r0)) return fail(MG_ENOCONV, "initial residual is not finite");
   while (r0 > 0.0 && rho > tol && k < c->opt.maxit) {
+    c->u_zero = false;
     if ((st = run(c, 1))) return st;
     double rk;
     if ((st = read_norm(c, &rk))) return st;

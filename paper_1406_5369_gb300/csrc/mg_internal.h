@@ -108,6 +108,11 @@ bool norm_ok(const Level &L);
 cudaError_t norm_stream(const Level &L, const void *u, const void *f, double *partials, int *nparts, cudaStream_t s);
 }  // namespace d3
 
+// Residual of u = 0 under homogeneous Dirichlet data (= f, exactly) on the
+// FP64 level O: kNormBlocks partial sums of f^2 over the interior and, when
+// I is given (defect correction), f written as I's right-hand side.
+cudaError_t first_defect(const Level &O, const Level *I, double *partials, cudaStream_t s);
+
 // Deterministic sum of nb partials (any nb): out[0] = sqrt(sum) / *scale_in
 // (scale_in may be NULL), out[1] = sum; scale_out (may be NULL) receives the
 // power of two for the next scaled pass.
