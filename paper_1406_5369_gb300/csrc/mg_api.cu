@@ -69,7 +69,7 @@ int alloc_pair(mg_ctx *c) {
 
 // Records the start event of a timed launch; returns the pair or -1.
 int timing_begin(mg_ctx *c, int kind, int level, cudaStream_t s) {
-  if (!c->timing) return -1;
+  if (!c->timing || (c->timing == 2 && level != 0)) return -1;
   int slot = c->capturing_slot;
   if (slot >= 0 && c->graphs[slot].npairs >= kSlotPairs) return -1;
   int i = alloc_pair(c);
@@ -856,11 +856,12 @@ mg_status mg_set_timing(mg_ctx *c, int on) {
       return fail(MG_ENOMEM, "host allocation of timing events failed");
     }
   }
-  if ((on != 0) != (c->timing != 0)) {
+  if (on < 0 || on > 2) return fail(MG_EINVAL, "timing mode must be 0, 1 or 2");
+  if (on != c->timing) {
     CK(cudaStreamSynchronize(c->stream));
     if (c->timing) timing_harvest(c);
     drop_graphs(c);  // graphs are recaptured with (or without) event nodes
-    c->timing = on != 0;
+    c->timing = on;
   }
   return MG_OK;
 }

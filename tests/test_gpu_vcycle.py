@@ -245,10 +245,20 @@ def test_kernel_timing_instrumentation():
     post_ms, post_n = s.timing("post", 0)
     out_ms, out_n = s.timing("outer", 0)
     assert pre_n == post_n == 2 * it and pre_ms > 0 and post_ms > 0
-    assert out_n == it + 1 and out_ms > 0
+    # one outer step per iteration (the first residual of a zero start is f,
+    # formed by a norm pass)
+    assert out_n == it and out_ms > 0
+    assert s.timing("pre", 1)[1] == 2 * it
     s.reset_timing()
     assert s.timing("pre", 0) == (0.0, 0)
+    # level-0-only mode: the finest level and the outer step, nothing below
+    s.set_timing(True, level0_only=True)
+    s.set_solution(None)
+    it2, _, _ = s.solve(1e-10)
+    assert s.timing("pre", 0)[1] == 2 * it2 and s.timing("outer", 0)[1] == it2
+    assert s.timing("pre", 1) == (0.0, 0) and s.timing("coarse", s.levels - 1) == (0.0, 0)
     s.set_timing(False)
+    s.reset_timing()
     s.set_solution(None)
     s.solve(1e-10)
     assert s.timing("pre", 0) == (0.0, 0)
