@@ -140,9 +140,13 @@ def run_gpu(args):
         import torch.distributed as dist
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
+        # one rank builds (a no-op when the library is up to date), the others wait
+        if rank == 0:
+            b.build()
+        dist.barrier()
     else:
         torch.cuda.set_device(0)
-    b.build()
+        b.build()
     load()
     W = WORKLOAD
     dim, n = W["dim"], W["n"]
