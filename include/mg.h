@@ -261,8 +261,8 @@ mg_status mg_reset_timing(mg_ctx *ctx);
 mg_status mg_residual_norm_noalloc(int dim, int n, const mg_const_stencil *stencil, const double *u,
                                    const double *f, double *out, void *stream);
 
-/* ---- Batches of independent problems (the task's batching and serving
- * patterns; the paper solves one problem at a time). A batch holds contexts
+/* ---- Batches of independent problems (the batching and serving patterns;
+ * the paper solves one problem at a time). A batch holds contexts
  * created with mg_create that share smoother, omega, nu1, nu2, precision and
  * inner_cycles (and dim); each keeps its own arena, right-hand side,
  * solution and tolerance. A batch step runs one solve step - a V-cycle, or
