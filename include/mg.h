@@ -90,7 +90,14 @@ typedef struct { int kind; const double *dirichlet_values; } mg_boundary;
  * use_graph             : 1 = replay each V-cycle from a captured CUDA graph
  * inner_cycles          : *_DC only: inner V-cycles per outer FP64 step (1..8, 0 = 1);
  *                         the first starts from e = 0, the others continue
- *                         from the current e. 1 = classic defect correction. */
+ *                         from the current e. 1 = classic defect correction.
+ * exact_outer           : *_DC only: 1 = when every axis coefficient c_d/h^2 of
+ *                         the constant stencil is the same power of two
+ *                         (Poisson with n = 2^m+1), the outer residual is
+ *                         evaluated exactly in 64-bit fixed-point integers and
+ *                         rounded once (at least FP64 accuracy, no FP64
+ *                         instruction); 0 = FP64 arithmetic. The update
+ *                         u += e is an FP64 addition either way. */
 typedef struct {
   mg_smoother smoother;
   double omega;
@@ -102,13 +109,14 @@ typedef struct {
   int fuse;
   int use_graph;
   int inner_cycles;
+  int exact_outer;
 } mg_options;
 
 typedef struct mg_ctx mg_ctx;
 
 /* Fills *opt with RBGS, omega 1, V(2,1), coarsest 3, maxit 50, FP64,
- * default stream, fuse 1, use_graph 1, inner_cycles 1 (the Layer-3
- * defaults of Sec. 2.3). */
+ * default stream, fuse 1, use_graph 1, inner_cycles 1, exact_outer 1 (the
+ * Layer-3 defaults of Sec. 2.3). */
 void mg_default_options(mg_options *opt);
 
 /* Bytes of device arena mg_create needs for this problem (0 if the

@@ -153,6 +153,7 @@ mg_status check_args(int dim, int n, const mg_options *opt) {
   if (opt->inner_cycles < 0 || opt->inner_cycles > 8) return fail(MG_EINVAL, "inner_cycles must lie in 0..8 (0 = 1)");
   if (opt->precision != MG_FP64 && opt->precision != MG_FP32_DC && opt->precision != MG_BF16_DC)
     return fail(MG_EINVAL, "unknown precision");
+  if (opt->exact_outer != 0 && opt->exact_outer != 1) return fail(MG_EINVAL, "exact_outer must be 0 or 1");
   return MG_OK;
 }
 
@@ -359,9 +360,10 @@ bool outer_fast(const Level &O, const Level &I) {
   return O.dim == 2 ? mg::d2::outer_ok(O, I) : mg::d3::outer_ok(O, I);
 }
 cudaError_t outer_step(const Level &O, const double *uin, double *uout, const Level &I, const void *e, void *d,
-                       double *partials, int *nparts, const float *scale, bool update, bool acc64, cudaStream_t s) {
-  return O.dim == 2 ? mg::d2::dc_step(O, uin, uout, I, e, d, partials, nparts, scale, update, acc64, s)
-                    : mg::d3::dc_step(O, uin, uout, I, e, d, partials, nparts, scale, update, acc64, s);
+                       double *partials, int *nparts, const float *scale, bool update, bool acc64, bool exact,
+                       cudaStream_t s) {
+  return O.dim == 2 ? mg::d2::dc_step(O, uin, uout, I, e, d, partials, nparts, scale, update, acc64, exact, s)
+                    : mg::d3::dc_step(O, uin, uout, I, e, d, partials, nparts, scale, update, acc64, exact, s);
 }
 bool norm_fast(const Level &L) { return L.dim == 2 ? mg::d2::norm_ok(L) : mg::d3::norm_ok(L); }
 cudaError_t norm_fast_partials(const Level &L, const void *u, const void *f, double *partials, int *nparts,
@@ -378,7 +380,7 @@ mg_status op_norm(mg_ctx *c, int l, cudaStream_t s) {
     Level &O = c->outer, &I = c->lv[0];
     if (outer_fast(O, I)) {
       TLAUNCH(c, MG_KERNEL_OUTER, 0, s, outer_step(O, (const double *)O.u[O.cur], nullptr, I, nullptr, I.f,
-                                                        c->partials, &np, c->dc_scale, false, true, s));
+                                                        c->partials, &np, c->dc_scale, false, true, false, s));
       TLAUNCH(c, MG_KERNEL_NORM, 0, s,
               mg::norm_finalize_ex(c->partials, np, c->norm_out, nullptr, c->dc_scale, interior_count(O), s));
       return MG_OK;
@@ -422,7 +424,8 @@ mg_status dc_inner_and_update(mg_ctx *c, bool norm, cudaStream_t s) {
     int np = 0;
     TLAUNCH(c, MG_KERNEL_OUTER, 0, s,
             outer_step(O, (const double *)O.u[O.cur], (double *)O.u[O.cur ^ 1], I, I.u[I.cur],
-                            norm ? I.f : nullptr, c->partials, &np, c->dc_scale, true, false, s));
+                            norm ? I.f : nullptr, c->partials, &np, c->dc_scale, true, false,
+                            c->opt.exact_outer != 0, s));
     O.cur ^= 1;
     if (norm)
       TLAUNCH(c, MG_KERNEL_NORM, 0, s,
@@ -569,6 +572,7 @@ void mg_default_options(mg_options *o) {
   o->fuse = 1;
   o->use_graph = 1;
   o->inner_cycles = 1;
+  o->exact_outer = 1;
 }
 
 size_t mg_workspace_bytes(int dim, int n, int variable_k, const mg_options *opt) {
@@ -698,7 +702,11 @@ int mg_level_size(const mg_ctx *c, int level) {
 mg_status mg_set_rhs(mg_ctx *c, const double *f) {
   if (!c || !f) return fail(MG_EINVAL, "NULL argument");
   Level &U = user_level(c);
-  CK(copy_dense_to_pitched(U, f, U.f, c->stream));
+  // Defect correction: interior only, so the outer right-hand side stays
+  // zero on the boundary (the exact outer step takes every value of a row
+  // into its exponent).
+  if (c->dc) CK(copy_dense_interior(U, f, U.f, c->stream));
+  else CK(copy_dense_to_pitched(U, f, U.f, c->stream));
   return MG_OK;
 }
 
@@ -909,6 +917,16 @@ __global__ void k_norm_finalize(const double *__restrict__ partials, int nb, dou
     out[0] = sqrt(buf[0]);
     out[1] = buf[0];
   }
+}
+
+int pow2_stencil(const Level &L) {
+  if (L.kf[0]) return kNoPow2;
+  const double c = L.c[0] * L.inv_h2;
+  for (int d = 1; d < L.dim; d++)
+    if (L.c[d] * L.inv_h2 != c) return kNoPow2;
+  int e = 0;
+  if (!(c > 0.0) || frexp(c, &e) != 0.5) return kNoPow2;
+  return e - 1;  // c = 0.5 * 2^e
 }
 
 cudaError_t norm_finalize(const double *partials, int nblocks, double *out, cudaStream_t s) {

@@ -35,6 +35,12 @@ struct Level {
 constexpr int kNormBlocks = 1024;
 constexpr int kMaxPartials = 16384;  // per-warp partial sums of the streaming norms
 
+// Exponent k when every axis coefficient of L's constant stencil, c_d / h^2,
+// equals the same power of two 2^k (the exact fixed-point outer step needs
+// it, fixed.cuh); kNoPow2 otherwise (and for variable stencils).
+constexpr int kNoPow2 = -100000;
+int pow2_stencil(const Level &L);
+
 // Per-dimension kernel launchers; all asynchronous on `s`.
 #define MG_DIM_OPS                                                                                \
   cudaError_t rbgs_half(const Level &L, void *u, const void *f, int color, double omega,         \
@@ -82,9 +88,12 @@ cudaError_t post_fused(const Level &L, const void *uin, void *uout, const Level 
 // defect d, per-warp partial sums); norm_stream: per-warp partial sums of
 // the level residual squared. *nparts receives the number of partials.
 namespace d2 {
+// exact: take the fixed-point kernel (k_dcx2d) when the step updates and the
+// stencil is one power of two (pow2_stencil).
 bool outer_ok(const Level &O, const Level &I);
 cudaError_t dc_step(const Level &O, const double *uin, double *uout, const Level &I, const void *e, void *d,
-                    double *partials, int *nparts, const float *scale, bool update, bool acc64, cudaStream_t s);
+                    double *partials, int *nparts, const float *scale, bool update, bool acc64, bool exact,
+                    cudaStream_t s);
 bool norm_ok(const Level &L);
 cudaError_t norm_stream(const Level &L, const void *u, const void *f, double *partials, int *nparts, cudaStream_t s);
 }  // namespace d2
@@ -103,7 +112,8 @@ cudaError_t z_restrict(const Level &F, const void *rf, const Level &C, void *fc,
 cudaError_t z_prolong(const Level &C, const void *ec, const Level &F, void *uf, cudaStream_t s);
 bool outer_ok(const Level &O, const Level &I);
 cudaError_t dc_step(const Level &O, const double *uin, double *uout, const Level &I, const void *e, void *d,
-                    double *partials, int *nparts, const float *scale, bool update, bool acc64, cudaStream_t s);
+                    double *partials, int *nparts, const float *scale, bool update, bool acc64, bool exact,
+                    cudaStream_t s);
 bool norm_ok(const Level &L);
 cudaError_t norm_stream(const Level &L, const void *u, const void *f, double *partials, int *nparts, cudaStream_t s);
 }  // namespace d3

@@ -71,6 +71,29 @@ cudaError_t launch_dc(oz::ArgsOuter a, int n, int *nparts, cudaStream_t s, const
   return cudaGetLastError();
 }
 
+template <typename Ti, bool ACC64>
+cudaError_t launch_dcx(oz::ArgsOuter a, int n, int *nparts, cudaStream_t s, const oz::ArgsOuter *list = nullptr,
+                       int count = 1, int max_parts = kMaxPartials) {
+  constexpr int IB = oz::InnerLane<Ti>::bytes;
+  constexpr int IBP = IB < 16 ? 16 : IB;
+  constexpr size_t smem = (size_t)oz::kWarps * oz::kXRing * 32 * (32 + 32 + IBP);
+  static int bps = 0;
+  if (!bps) {
+    bps = occupancy(oz::k_dcx2d<Ti, ACC64, false>, 32 * oz::kWarps, smem);
+    occupancy(oz::k_dcx2d<Ti, ACC64, true>, 32 * oz::kWarps, smem);
+  }
+  chunking(a, n, bps, max_parts, list != nullptr);
+  long long warps = (long long)a.nstrips * a.nchunks;
+  *nparts = (int)warps;
+  a.pstride = max_parts;
+  unsigned blocks = (unsigned)((warps + oz::kWarps - 1) / oz::kWarps);
+  if (list)
+    oz::k_dcx2d<Ti, ACC64, true><<<dim3(blocks, (unsigned)count), 32 * oz::kWarps, smem, s>>>(a, list);
+  else
+    oz::k_dcx2d<Ti, ACC64, false><<<blocks, 32 * oz::kWarps, smem, s>>>(a, nullptr);
+  return cudaGetLastError();
+}
+
 template <typename T> cudaError_t launch_norm(oz::ArgsOuter a, int n, int *nparts, cudaStream_t s) {
   constexpr size_t smem = (size_t)oz::kWarps * oz::kRing * 32 * fz::Lane<T>::bytes * 2;
   static int bps = 0;
@@ -130,7 +153,8 @@ bool outer_ok(const Level &O, const Level &I) {
 }
 
 cudaError_t dc_step(const Level &O, const double *uin, double *uout, const Level &I, const void *e, void *d,
-                    double *partials, int *nparts, const float *scale, bool update, bool acc64, cudaStream_t s) {
+                    double *partials, int *nparts, const float *scale, bool update, bool acc64, bool exact,
+                    cudaStream_t s) {
   oz::ArgsOuter a;
   memset(&a, 0, sizeof a);
   a.u = uin;
@@ -146,6 +170,13 @@ cudaError_t dc_step(const Level &O, const double *uin, double *uout, const Level
   a.cx = O.c[0] * O.inv_h2;
   a.cy = O.c[1] * O.inv_h2;
   a.cd = 2.0 * (a.cx + a.cy);
+  const int k2 = pow2_stencil(O);
+  if (exact && update && k2 != kNoPow2) {
+    a.k2 = k2;
+    if (I.dtype == F32)
+      return acc64 ? launch_dcx<float, true>(a, O.n, nparts, s) : launch_dcx<float, false>(a, O.n, nparts, s);
+    return acc64 ? launch_dcx<bf16, true>(a, O.n, nparts, s) : launch_dcx<bf16, false>(a, O.n, nparts, s);
+  }
   if (I.dtype == F32) {
     if (update) return acc64 ? launch_dc<float, true, true>(a, O.n, nparts, s) : launch_dc<float, true, false>(a, O.n, nparts, s);
     return acc64 ? launch_dc<float, false, true>(a, O.n, nparts, s) : launch_dc<float, false, false>(a, O.n, nparts, s);

@@ -23,6 +23,7 @@
 // always comes from a norm of the right magnitude.
 #pragma once
 
+#include "fixed.cuh"
 #include "fused2d.cuh"
 
 namespace mg {
@@ -59,13 +60,14 @@ struct ArgsOuter {
   int R, nstrips, nchunks;
   double cx, cy, cd;    // stencil: cx = c0/h^2, cy = c1/h^2, cd = 2 (cx + cy)
   int pstride;          // list launches: partial slots per problem
+  int k2;               // k_dcx2d: cx = cy = 2^k2
 };
 
 // List launches (many problems of one size): record fields of problem
 // blockIdx.y, including the address of its partial-sum slots.
 __device__ __forceinline__ void take_problem(ArgsOuter &a, const ArgsOuter &p) {
   a.u = p.u; a.uout = p.uout; a.f = p.f; a.e = p.e; a.d = p.d;
-  a.cx = p.cx; a.cy = p.cy; a.cd = p.cd;
+  a.cx = p.cx; a.cy = p.cy; a.cd = p.cd; a.k2 = p.k2;
   a.partials = p.partials;  // the problem's own slots (at most pstride of them)
 }
 
@@ -225,6 +227,176 @@ __global__ void __launch_bounds__(32 * kWarps) k_dc2d(ArgsOuter a, const ArgsOut
           bool ok = rowok && c >= 1 && c <= n - 2;
           rv[q] = ok ? d2f_bits(rr) : 0.0f;
           if (ACC64 && ok && r >= r0 && r < r1 && out_lane) acc64 = fma(rr, rr, acc64);
+        }
+        if (r >= r0 && r < r1 && out_lane) {
+          if (!ACC64) {
+#pragma unroll
+            for (int q = 0; q < kVec; q++) {
+              float sr = rv[q] * scale;
+              acc = fmaf(sr, sr, acc);
+            }
+          }
+          if (d) store4i<Ti>(d + (long long)r * a.pitchi + c0, rv);
+        }
+      }
+    });
+  }
+  cp_async_wait<0>();
+  double w = warp_sum(ACC64 ? acc64 : (double)acc);
+  if (lane == 0) a.partials[gw] = w;
+}
+
+// ------------------------------------------------ exact outer step (c = 2^k)
+// The outer step of k_dc2d<Ti, true, ACC64> for a stencil with cx = cy = 2^k2,
+// with the residual evaluated exactly in 64-bit fixed point (fixed.cuh)
+// instead of five FP64 operations per node. The update u_out = u_in + e is
+// the one FP64 addition per node (IEEE rounding, as in k_dc2d). Each row
+// gets the warp-wide largest exponent of its updated u and of f / 2^k2 (the
+// outer right-hand side is zero on the boundary, so every f value counts);
+// the residual of row r uses the largest of rows r-1..r+1, and rows
+// converted at a smaller one are shifted down to it. Rows stream through a
+// 4-row ring in two-row cp.async groups (half the staging of k_dc2d, so more
+// warps stay resident to cover the integer pipeline's latency).
+constexpr int kXRing = 4;
+template <typename Ti, bool ACC64, bool LIST = false>
+__global__ void __launch_bounds__(32 * kWarps) k_dcx2d(ArgsOuter a, const ArgsOuter *__restrict__ list) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (LIST) take_problem(a, list[blockIdx.y]);
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const long long gw = (long long)blockIdx.x * kWarps + wib;
+  if (gw >= (long long)a.nstrips * a.nchunks) return;
+  const int s = (int)(gw % a.nstrips), ch = (int)(gw / a.nstrips);
+  const int n = a.n;
+  const int x0 = s * kOut - kVec;
+  const int c0 = x0 + kVec * lane;
+  const bool col_ok = c0 >= 0 && c0 < a.pitch;
+  const bool out_lane = lane >= 1 && lane <= 30 && col_ok;
+  const int r0 = ch * a.R, r1 = min(r0 + a.R, n);
+  const int tstart = max(r0 - 8, 0);
+  const int tend = r1;
+  constexpr int IB = InnerLane<Ti>::bytes;
+  constexpr int IBP = IB < 16 ? 16 : IB;
+  unsigned char *su = smem + (size_t)wib * kXRing * 32 * (32 + 32 + IBP);
+  unsigned char *sf = su + kXRing * 32 * 32;
+  unsigned char *se = sf + kXRing * 32 * 32;
+  const Ti *e = (const Ti *)a.e;
+  Ti *d = (Ti *)a.d;
+  const float scale = ACC64 ? 1.0f : *a.scale;
+  const int k2 = a.k2;
+  bool colin[kVec];  // interior column
+#pragma unroll
+  for (int q = 0; q < kVec; q++) colin[q] = c0 + q >= 1 && c0 + q <= n - 2;
+
+  double F[kXRing][kVec];
+  long long X[kXRing][kVec];
+  int Bu[kXRing], Bf[kXRing];
+#pragma unroll
+  for (int i = 0; i < kXRing; i++) {
+    Bu[i] = Bf[i] = fx::kHead;
+#pragma unroll
+    for (int q = 0; q < kVec; q++) { X[i][q] = 0; F[i][q] = 0.0; }
+  }
+  float acc = 0.0f;
+  double acc64 = 0.0;
+
+  auto issue_pair = [&](int hb) {
+#pragma unroll
+    for (int K = 0; K < 2; K++) {
+      int row = hb + K;
+      int slot = row & (kXRing - 1);
+      bool ok = col_ok && row >= 0 && row < n && row <= tend;
+      long long off = (long long)row * a.pitch + c0;
+      const double *us = ok ? a.u + off : a.u;
+      const double *fs = ok ? a.f + off : a.f;
+      cp_async16(su + (slot * 32 + lane) * 32, us, ok);
+      cp_async16(su + (slot * 32 + lane) * 32 + 16, us + 2, ok);
+      cp_async16(sf + (slot * 32 + lane) * 32, fs, ok);
+      cp_async16(sf + (slot * 32 + lane) * 32 + 16, fs + 2, ok);
+      long long offi = (long long)row * a.pitchi + c0;
+      const Ti *es = ok ? e + offi : e;
+      if (IB == 16) cp_async16(se + (slot * 32 + lane) * IBP, es, ok);
+      else cp_async8(se + (slot * 32 + lane) * IBP, es, ok);
+    }
+    cp_async_commit();
+  };
+
+  issue_pair(tstart);
+  for (int tb = tstart; tb <= tend; tb += kXRing) {
+    static_for<0, kXRing>([&](auto kc) {
+      constexpr int K = decltype(kc)::value;
+      const int t = tb + K;
+      if constexpr ((K & 1) == 0) {
+        issue_pair(t + 2);  // its slots held rows t - 2, t - 1, already in registers
+        cp_async_wait<1>();
+      }
+      double u[kVec], ev[kVec];
+      load4d(su + (K * 32 + lane) * 32, u);
+      load4d(sf + (K * 32 + lane) * 32, F[K]);
+      load4i<Ti>(se + (K * 32 + lane) * IBP, ev);
+#pragma unroll
+      for (int q = 0; q < kVec; q++) u[q] += ev[q];  // e is 0 on the boundary
+      if (t >= r0 && t < r1 && t < n && out_lane) {
+        double *dst = a.uout + (long long)t * a.pitch + c0;
+        *(double2 *)dst = make_double2(u[0], u[1]);
+        *(double2 *)(dst + 2) = make_double2(u[2], u[3]);
+      }
+      // exponents of row t (a maximum of 2047 flags Inf/NaN)
+      {
+        unsigned mu = 0, mf = 0;
+#pragma unroll
+        for (int q = 0; q < kVec; q++) {
+          mu = max(mu, (unsigned)fx::dexp(u[q]));
+          mf = max(mf, (unsigned)fx::dexp(F[K][q]));
+        }
+        mu = __reduce_max_sync(0xffffffffu, mu);
+        mf = __reduce_max_sync(0xffffffffu, mf);
+        const bool bad = mu == 0x7ffu || mf == 0x7ffu;
+        Bu[K] = (bad ? fx::kNonFinite : (int)mu) + fx::kHead;
+        Bf[K] = max((int)mf - k2, 0) + fx::kHead;
+#pragma unroll
+        for (int q = 0; q < kVec; q++) X[K][q] = fx::to_fixed(u[q], Bu[K]);
+      }
+      // residual of row t - 1
+      {
+        const int r = t - 1;
+        constexpr int sc = (K - 1) & (kXRing - 1), sa = (K - 2) & (kXRing - 1), sb = K;
+        const int B = max(max(Bu[sa], Bu[sb]), max(Bu[sc], Bf[sc]));
+        long long xa[kVec], xc[kVec], xb[kVec];
+        const int da = B - Bu[sa], dc = B - Bu[sc], db = B - Bu[sb];
+#pragma unroll
+        for (int q = 0; q < kVec; q++) { xa[q] = X[sa][q]; xc[q] = X[sc][q]; xb[q] = X[sb][q]; }
+        if (da) {
+#pragma unroll
+          for (int q = 0; q < kVec; q++) xa[q] = fx::align_down(xa[q], da);
+        }
+        if (dc) {
+#pragma unroll
+          for (int q = 0; q < kVec; q++) xc[q] = fx::align_down(xc[q], dc);
+        }
+        if (db) {
+#pragma unroll
+          for (int q = 0; q < kVec; q++) xb[q] = fx::align_down(xb[q], db);
+        }
+        const long long left = fx::shfl_up64(xc[3]), right = fx::shfl_dn64(xc[0]);
+        const bool rowok = r >= 1 && r <= n - 2;
+        const bool finite = B < fx::kNonFinite;
+        const int E0 = B - 1085 + k2;
+        const fx::Pow2f p2 = fx::pow2f(E0);
+        const double s64 = ACC64 ? __hiloint2double((min(max(E0, -1022), 1023) + 1023) << 20, 0) : 0.0;
+        float rv[kVec];
+#pragma unroll
+        for (int q = 0; q < kVec; q++) {
+          const long long xw = q == 0 ? left : xc[q - 1];
+          const long long xe = q == kVec - 1 ? right : xc[q + 1];
+          const long long S = 4 * xc[q] - (xw + xe) - (xa[q] + xb[q]);
+          const long long R = fx::to_fixed(F[sc][q], B + k2) - S;
+          const bool ok = rowok && colin[q];
+          const float rf = finite ? fx::fixed_to_float(R, p2) : __int_as_float(0x7fc00000);
+          rv[q] = ok ? rf : 0.0f;
+          if (ACC64 && ok && r >= r0 && r < r1 && out_lane) {
+            const double rr = finite ? fx::fixed_to_double(R, s64) : __longlong_as_double(0x7ff8000000000000ll);
+            acc64 = fma(rr, rr, acc64);
+          }
         }
         if (r >= r0 && r < r1 && out_lane) {
           if (!ACC64) {

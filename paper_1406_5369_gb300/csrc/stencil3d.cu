@@ -204,7 +204,9 @@ cudaError_t launch_dc(z3::ArgsDC3 a, int *nparts, cudaStream_t s, const z3::Args
 }  // namespace
 
 cudaError_t dc_step(const Level &O, const double *uin, double *uout, const Level &I, const void *e, void *d,
-                    double *partials, int *nparts, const float *scale, bool update, bool acc64, cudaStream_t s) {
+                    double *partials, int *nparts, const float *scale, bool update, bool acc64, bool exact,
+                    cudaStream_t s) {
+  (void)exact;
   z3::ArgsDC3 a;
   memset(&a, 0, sizeof a);
   a.u = uin;

@@ -48,7 +48,7 @@ class Solver:
 
     def __init__(self, dim, n, *, stencil=(1.0, 1.0, 1.0), k=None, dirichlet=None,
                  smoother="rbgs", omega=1.0, nu1=2, nu2=1, maxit=50, precision="fp64",
-                 fuse=True, use_graph=True, inner_cycles=1, stream=None, device="cuda"):
+                 fuse=True, use_graph=True, inner_cycles=1, exact_outer=True, stream=None, device="cuda"):
         import torch
         self._lib = C.load()
         self.dim, self.n = dim, n
@@ -62,6 +62,7 @@ class Solver:
         opt.fuse = int(bool(fuse))
         opt.use_graph = int(bool(use_graph))
         opt.inner_cycles = int(inner_cycles)
+        opt.exact_outer = int(bool(exact_outer))
         opt.stream = default_stream_handle() if stream is None else stream
         self._tstream = torch.cuda.current_stream() if stream is None else torch.cuda.ExternalStream(stream)
         self.opt = opt
