@@ -201,12 +201,28 @@ cudaError_t launch_dc(z3::ArgsDC3 a, int *nparts, cudaStream_t s, const z3::Args
   z3::k3_dc<Ti, UPDATE, ACC64><<<dim3((unsigned)base, (unsigned)nz, (unsigned)count), 32 * z3::kDCWarps, smem, s>>>(a, list);
   return cudaGetLastError();
 }
+// The exact outer step (k3_dcx): same tiling, partial-sum layout and chunks.
+template <typename Ti, bool ACC64>
+cudaError_t launch_dcx(z3::ArgsDC3 a, int *nparts, cudaStream_t s, const z3::ArgsDC3 *list = nullptr, int count = 1,
+                       int max_parts = kMaxPartials) {
+  constexpr size_t smem = (size_t)z3::DCL<Ti>::Smem;
+  static int per_sm = 0;
+  int r = resident(z3::k3_dcx<Ti, ACC64>, 32 * z3::kDCWarps, smem, &per_sm);
+  a.ntx = (a.n - 1 + 63) / 64;
+  a.nty = (a.n - 2 + z3::kTY - 1) / z3::kTY;
+  long long base = (long long)a.ntx * a.nty;
+  a.zc = pick_zc(a.n, base, r, max_parts, list != nullptr);
+  int nz = (a.n - 2 + a.zc - 1) / a.zc;
+  *nparts = (int)(base * nz);
+  a.pstride = max_parts;
+  z3::k3_dcx<Ti, ACC64><<<dim3((unsigned)base, (unsigned)nz, (unsigned)count), 32 * z3::kDCWarps, smem, s>>>(a, list);
+  return cudaGetLastError();
+}
 }  // namespace
 
 cudaError_t dc_step(const Level &O, const double *uin, double *uout, const Level &I, const void *e, void *d,
                     double *partials, int *nparts, const float *scale, bool update, bool acc64, bool exact,
                     cudaStream_t s) {
-  (void)exact;
   z3::ArgsDC3 a;
   memset(&a, 0, sizeof a);
   a.u = uin;
@@ -226,6 +242,12 @@ cudaError_t dc_step(const Level &O, const double *uin, double *uout, const Level
   a.cy = cy;
   a.cz = cz;
   a.cd = 2.0 * (cx + cy + cz);
+  const int k2 = pow2_stencil(O);
+  if (exact && update && k2 != kNoPow2) {
+    a.k2 = k2;
+    if (I.dtype == F32) return acc64 ? launch_dcx<float, true>(a, nparts, s) : launch_dcx<float, false>(a, nparts, s);
+    return acc64 ? launch_dcx<bf16, true>(a, nparts, s) : launch_dcx<bf16, false>(a, nparts, s);
+  }
   if (I.dtype == F32) {
     if (update) return acc64 ? launch_dc<float, true, true>(a, nparts, s) : launch_dc<float, true, false>(a, nparts, s);
     return acc64 ? launch_dc<float, false, true>(a, nparts, s) : launch_dc<float, false, false>(a, nparts, s);

@@ -25,6 +25,7 @@
 // float for BF16/FP32 storage and in double for FP64 storage.
 #pragma once
 
+#include "fixed.cuh"
 #include "fused2d.cuh"
 #include "outer2d.cuh"
 
@@ -482,6 +483,7 @@ struct ArgsDC3 {
   int ntx, nty, zc;
   double cd, cx, cy, cz;
   int pstride;         // list launches: partial slots per problem
+  int k2;              // k3_dcx: cx = cy = cz = 2^k2
 };
 
 // Pieces of the outer step's tile: u and e rows y0-1 .. y0+kTY with halo
@@ -624,6 +626,160 @@ __global__ void __launch_bounds__(32 * kDCWarps) k3_dc(ArgsDC3 a, const ArgsDC3 
         const bool in = c >= 1 && c <= n - 2;
         rv[q] = in ? oz::d2f_bits(rr) : 0.0f;
         if (ACC64 && in) acc64 = fma(rr, rr, acc64);
+        if (!ACC64) {
+          const float sr = rv[q] * scale;
+          acc = fmaf(sr, sr, acc);
+        }
+      }
+      if (d && cl < a.pitchi) {
+        Ti *dp = d + (long long)z * a.planei + (long long)y * a.pitchi + cl;
+        if (sizeof(Ti) == 4) *(float2 *)dp = make_float2(rv[0], rv[1]);
+        else *(unsigned *)dp = bf16x2_rne_bits(rv[0], rv[1]);
+      }
+    }
+  }
+  cp_async_wait<0>();
+  double s = oz::warp_sum(ACC64 ? acc64 : (double)acc);
+  if (lane == 0) wsum[w] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < kDCWarps; i++) t += wsum[i];
+    a.partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// ------------------------------------------------ exact outer step (c = 2^k)
+// k3_dc<Ti, true, ACC64> for cx = cy = cz = 2^k2, with the residual
+// evaluated exactly in 64-bit fixed point (fixed.cuh): the update is the one
+// FP64 addition per node. A warp converts everything its residual row reads
+// at one exponent B: the largest of its own row at planes z-1, z, z+1 (each
+// converted once, when it is updated, at that row's own exponent and shifted
+// down to B when B is larger), of the staged y-neighbour rows of plane z and
+// of f / 2^k2 (converted at B when read).
+template <typename Ti, bool ACC64>
+__global__ void __launch_bounds__(32 * kDCWarps) k3_dcx(ArgsDC3 a, const ArgsDC3 *__restrict__ list) {
+  typedef DCL<Ti> L;
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (list) {  // problem blockIdx.z of a list launch
+    const ArgsDC3 &p = list[blockIdx.z];
+    a.u = p.u; a.uout = p.uout; a.f = p.f; a.e = p.e; a.d = p.d;
+    a.cd = p.cd; a.cx = p.cx; a.cy = p.cy; a.cz = p.cz; a.k2 = p.k2;
+    a.partials = p.partials;
+  }
+  __shared__ double wsum[kDCWarps];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;  // w = 0 .. kTY + 1: row y0 - 1 + w
+  const int tx = blockIdx.x % a.ntx, ty = blockIdx.x / a.ntx;
+  const int n = a.n;
+  const int y0 = 1 + ty * kTY, y = y0 - 1 + w;
+  const int x0 = tx * 64, cl = x0 + 2 * lane;
+  const int z0 = 1 + blockIdx.y * a.zc, z1 = min(z0 + a.zc, n - 1);
+  const bool out_warp = w >= 1 && w <= kTY && y <= n - 2;
+  const bool row_ok = y <= n - 1;
+  unsigned char *un = smem + kDCRing * L::SlotB;
+  auto slot = [&](int p) { return smem + (p % kDCRing) * L::SlotB; };
+  const float scale = ACC64 ? 1.0f : *a.scale;
+  const int k2 = a.k2;
+  Ti *d = (Ti *)a.d;
+  float acc = 0.0f;
+  double acc64 = 0.0;
+
+  auto update_row = [&](int p, double (&v)[2], double &h) {
+    const unsigned char *s = slot(p + kDCRing);
+    const unsigned char *ur = s + w * kURowB;
+    vld((const double *)(ur + (lane + 1) * 16), v);
+    h = 0.0;
+    if (lane == 0) h = *(const double *)(ur + 8);
+    if (lane == 31) h = *(const double *)(ur + 33 * 16);
+    const unsigned char *er = s + kDCWarps * kURowB + w * L::ERowB;
+    const unsigned char *mine = er + 16 + lane * 2 * sizeof(Ti);
+    v[0] += e_at<Ti>(mine);
+    v[1] += e_at<Ti>(mine + sizeof(Ti));
+    if (lane == 0) h += e_at<Ti>(er + 16 - sizeof(Ti));
+    if (lane == 31) h += e_at<Ti>(er + 16 + 64 * sizeof(Ti));
+  };
+
+  Pieces<DCP<Ti, true>::K> pc;
+  dc_pieces<Ti, true>(pc, a, y0, x0);
+  const int zs = z0 - 2;
+  pc.start(zs + 1);
+  for (int k = 1; k <= kAhead; k++) {
+    const int p = zs + k;
+    pc.issue(slot(p + kDCRing), p <= z1);
+  }
+
+  // own row at planes z-1 (m), z (c), z+1 (p): fixed values, halo, exponent
+  long long xm[2] = {0, 0}, xc[2] = {0, 0}, xp[2] = {0, 0};
+  long long hc = 0, hp = 0;
+  int bm = fx::kHead, bc = fx::kHead, bp = fx::kHead;
+  for (int z = zs; z < z1; z++) {
+    cp_async_wait<kAhead - 1>();
+    __syncthreads();  // (A)
+    pc.issue(slot(z + kAhead + 1 + kDCRing), z + kAhead + 1 <= z1);
+    double nv[2] = {0, 0}, nh = 0;
+    if (row_ok) {
+      update_row(z + 1, nv, nh);
+      *(double2 *)(un + (((z + 1) % 3 + 3) % 3 * kDCWarps + w) * L::UNRowB + lane * 16) = make_double2(nv[0], nv[1]);
+      if (out_warp && z + 1 >= z0 && z + 1 < z1 && cl < a.pitch)
+        *(double2 *)(a.uout + (long long)(z + 1) * a.plane + (long long)y * a.pitch + cl) = make_double2(nv[0], nv[1]);
+    }
+    // this row at plane z + 1 in fixed point at its own exponent
+    {
+      unsigned m = max(max((unsigned)fx::dexp(nv[0]), (unsigned)fx::dexp(nv[1])), (unsigned)fx::dexp(nh));
+      m = __reduce_max_sync(0xffffffffu, m);
+      const int bn = (m == 0x7ffu ? fx::kNonFinite : (int)m) + fx::kHead;
+      xm[0] = xc[0]; xm[1] = xc[1]; xc[0] = xp[0]; xc[1] = xp[1];
+      hc = hp;
+      bm = bc; bc = bp; bp = bn;
+      xp[0] = fx::to_fixed(nv[0], bn);
+      xp[1] = fx::to_fixed(nv[1], bn);
+      hp = fx::to_fixed(nh, bn);
+    }
+    __syncthreads();  // (B) updated rows of plane z + 1 visible
+    if (z >= z0 && out_warp) {
+      const unsigned char *us = un + ((z % 3 + 3) % 3 * kDCWarps + (w - 1)) * L::UNRowB + lane * 16;
+      const unsigned char *un_ = un + ((z % 3 + 3) % 3 * kDCWarps + (w + 1)) * L::UNRowB + lane * 16;
+      const double2 s2 = *(const double2 *)us, n2 = *(const double2 *)un_;
+      const double2 f2 = *(const double2 *)(slot(z + kDCRing) + kDCWarps * kURowB + kDCWarps * L::ERowB +
+                                             (w - 1) * kFRowB + lane * 16);
+      const double ysv[2] = {s2.x, s2.y}, ynv[2] = {n2.x, n2.y}, fv[2] = {f2.x, f2.y};
+      unsigned my = 0, mf = 0;
+#pragma unroll
+      for (int q = 0; q < 2; q++) {
+        my = max(my, max((unsigned)fx::dexp(ysv[q]), (unsigned)fx::dexp(ynv[q])));
+        mf = max(mf, (unsigned)fx::dexp(fv[q]));
+      }
+      my = __reduce_max_sync(0xffffffffu, my);
+      mf = __reduce_max_sync(0xffffffffu, mf);
+      const bool bad = my == 0x7ffu || mf == 0x7ffu;
+      int B = max(max(bm, bc), max(bp, max((int)my, (int)mf - k2) + fx::kHead));
+      B = bad ? fx::kNonFinite + fx::kHead : B;
+      long long um_[2] = {xm[0], xm[1]}, uc_[2] = {xc[0], xc[1]}, up_[2] = {xp[0], xp[1]}, h = hc;
+      if (B != bm) { um_[0] = fx::align_down(um_[0], B - bm); um_[1] = fx::align_down(um_[1], B - bm); }
+      if (B != bc) { uc_[0] = fx::align_down(uc_[0], B - bc); uc_[1] = fx::align_down(uc_[1], B - bc); h = fx::align_down(h, B - bc); }
+      if (B != bp) { up_[0] = fx::align_down(up_[0], B - bp); up_[1] = fx::align_down(up_[1], B - bp); }
+      long long wl = fx::shfl_up64(uc_[1]), er = fx::shfl_dn64(uc_[0]);
+      if (lane == 0) wl = h;
+      if (lane == 31) er = h;
+      const bool finite = B < fx::kNonFinite;
+      const int E0 = B - 1085 + k2;
+      const fx::Pow2f p2 = fx::pow2f(E0);
+      const double s64 = ACC64 ? __hiloint2double((min(max(E0, -1022), 1023) + 1023) << 20, 0) : 0.0;
+      float rv[2];
+#pragma unroll
+      for (int q = 0; q < 2; q++) {
+        const long long xw = q == 0 ? wl : uc_[0], xe = q == 1 ? er : uc_[1];
+        const long long S = 6 * uc_[q] - (xw + xe) - (fx::to_fixed(ysv[q], B) + fx::to_fixed(ynv[q], B)) -
+                            (um_[q] + up_[q]);
+        const long long R = fx::to_fixed(fv[q], B + k2) - S;
+        const int c = cl + q;
+        const bool in = c >= 1 && c <= n - 2;
+        const float rf = finite ? fx::fixed_to_float(R, p2) : __int_as_float(0x7fc00000);
+        rv[q] = in ? rf : 0.0f;
+        if (ACC64 && in) {
+          const double rr = finite ? fx::fixed_to_double(R, s64) : __longlong_as_double(0x7ff8000000000000ll);
+          acc64 = fma(rr, rr, acc64);
+        }
         if (!ACC64) {
           const float sr = rv[q] * scale;
           acc = fmaf(sr, sr, acc);

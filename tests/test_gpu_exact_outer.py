@@ -130,3 +130,70 @@ def test_exact_outer_with_dirichlet_data():
     r0 = oracle.residual(g, f)
     rel = oracle.norm(oracle.residual(u, f)) / oracle.norm(r0)
     assert rel <= 1.01e-10, rel
+
+
+def exact_residual_3d(u, f, c):
+    """r = f - c (6u - sum of the six neighbours) at interior nodes, exact rationals."""
+    n = u.shape[0]
+    U = np.vectorize(lambda v: Fraction(float(v)), otypes=[object])(u)
+    C = Fraction(c)
+    r = np.zeros((n, n, n))
+    for k in range(1, n - 1):
+        for j in range(1, n - 1):
+            for i in range(1, n - 1):
+                s = (6 * U[k, j, i] - U[k, j, i - 1] - U[k, j, i + 1] - U[k, j - 1, i] - U[k, j + 1, i]
+                     - U[k - 1, j, i] - U[k + 1, j, i])
+                r[k, j, i] = float(Fraction(float(f[k, j, i])) - C * s)
+    return r
+
+
+@pytest.mark.parametrize("prec", ["fp32_dc", "bf16_dc"])
+def test_exact_defect_3d_is_truncated_exact_residual(prec):
+    need_gpu()
+    from paper_1406_5369_gb300 import Solver
+    n = 17
+    rng = np.random.default_rng(5)
+    f = synth.normal_rhs(3, n, 0x5EED0003)
+    x = np.linspace(0.0, 1.0, n)
+    u0 = np.einsum("i,j,k->kji", np.sin(np.pi * x), np.sin(2 * np.pi * x), np.sin(3 * np.pi * x)) * 1e-2
+    u0[1:-1, 1:-1, 1:-1] += 1e-6 * rng.standard_normal((n - 2,) * 3)
+    u0[0], u0[-1], u0[:, 0], u0[:, -1], u0[:, :, 0], u0[:, :, -1] = 0, 0, 0, 0, 0, 0
+    out = {}
+    for exact in (True, False):
+        s = Solver(3, n, precision=prec, smoother="jacobi", omega=6 / 7, nu1=2, nu2=2, maxit=1, exact_outer=exact)
+        s.set_rhs(f)
+        s.set_solution(u0)
+        s.solve(0.0, raise_on_noconv=False)
+        out[exact] = (s.get_solution(), s.get_field(0, "f"), s.get_field(0, "u"))
+    u, d, e = out[True]
+    inner = (slice(1, -1),) * 3
+    assert np.array_equal(u[inner], u0[inner] + e[inner])
+    assert np.array_equal(out[False][0], u)
+    c = float((n - 1) ** 2)
+    r = exact_residual_3d(u, f, c)
+    rel = 2.0 ** -23 if prec == "fp32_dc" else 2.0 ** -8 + 2.0 ** -22
+    abs_fix = 16 * c * np.max(np.abs(u)) * 2.0 ** -56 + np.max(np.abs(f)) * 2.0 ** -56
+    err = np.abs(d[inner] - r[inner])
+    assert np.all(err <= rel * np.abs(r[inner]) * 1.0000001 + abs_fix), float(np.max(err))
+    fp64_noise = 24 * c * np.max(np.abs(u)) * 2.0 ** -52
+    assert np.all(np.abs(out[False][1][inner] - d[inner]) <= 2 * rel * np.abs(r[inner]) * 1.0000001 + fp64_noise + abs_fix)
+
+
+@pytest.mark.parametrize("prec", ["fp32_dc", "bf16_dc"])
+def test_exact_outer_3d_solve_matches_fp64_outer(prec):
+    need_gpu()
+    from paper_1406_5369_gb300 import Solver
+    n = 129
+    f = synth.normal_rhs(3, n, 0x5EED0003)
+    res = {}
+    for exact in (True, False):
+        s = Solver(3, n, precision=prec, smoother="jacobi", omega=6 / 7, nu1=2, nu2=2, inner_cycles=3, maxit=40,
+                   exact_outer=exact)
+        s.set_rhs(f)
+        it, rr, hist = s.solve(1e-10)
+        u = s.get_solution()
+        rel = oracle.norm(oracle.residual(u, f)) / oracle.norm(f)
+        assert rel <= 1.01e-10, (exact, rel)
+        res[exact] = (it, u)
+    assert res[True][0] == res[False][0]
+    assert rel_err(res[True][1], res[False][1]) <= 1e-8
