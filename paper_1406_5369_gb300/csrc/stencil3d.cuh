@@ -652,11 +652,13 @@ __global__ void __launch_bounds__(32 * kDCWarps) k3_dc(ArgsDC3 a, const ArgsDC3 
 // ------------------------------------------------ exact outer step (c = 2^k)
 // k3_dc<Ti, true, ACC64> for cx = cy = cz = 2^k2, with the residual
 // evaluated exactly in 64-bit fixed point (fixed.cuh): the update is the one
-// FP64 addition per node. A warp converts everything its residual row reads
-// at one exponent B: the largest of its own row at planes z-1, z, z+1 (each
-// converted once, when it is updated, at that row's own exponent and shifted
-// down to B when B is larger), of the staged y-neighbour rows of plane z and
-// of f / 2^k2 (converted at B when read).
+// FP64 addition per node. The warp that updates a row converts it once, at
+// that row's warp-wide exponent, and publishes the fixed values and the
+// exponent in the 3-slot ring of updated rows (fixed values take the place
+// of the FP64 ones; the updated FP64 row goes to u_out only). A warp forms
+// the residual of its row at the largest exponent B of the values it reads
+// (its row at planes z-1, z, z+1, the neighbour rows of plane z, f / 2^k2),
+// shifting rows held at a smaller exponent down to B.
 template <typename Ti, bool ACC64>
 __global__ void __launch_bounds__(32 * kDCWarps) k3_dcx(ArgsDC3 a, const ArgsDC3 *__restrict__ list) {
   typedef DCL<Ti> L;
@@ -668,6 +670,7 @@ __global__ void __launch_bounds__(32 * kDCWarps) k3_dcx(ArgsDC3 a, const ArgsDC3
     a.partials = p.partials;
   }
   __shared__ double wsum[kDCWarps];
+  __shared__ int rexp[3][kDCWarps];  // exponent of each published row
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;  // w = 0 .. kTY + 1: row y0 - 1 + w
   const int tx = blockIdx.x % a.ntx, ty = blockIdx.x / a.ntx;
   const int n = a.n;
@@ -716,14 +719,14 @@ __global__ void __launch_bounds__(32 * kDCWarps) k3_dcx(ArgsDC3 a, const ArgsDC3
     cp_async_wait<kAhead - 1>();
     __syncthreads();  // (A)
     pc.issue(slot(z + kAhead + 1 + kDCRing), z + kAhead + 1 <= z1);
+    const int ring = ((z + 1) % 3 + 3) % 3;
     double nv[2] = {0, 0}, nh = 0;
     if (row_ok) {
       update_row(z + 1, nv, nh);
-      *(double2 *)(un + (((z + 1) % 3 + 3) % 3 * kDCWarps + w) * L::UNRowB + lane * 16) = make_double2(nv[0], nv[1]);
       if (out_warp && z + 1 >= z0 && z + 1 < z1 && cl < a.pitch)
         *(double2 *)(a.uout + (long long)(z + 1) * a.plane + (long long)y * a.pitch + cl) = make_double2(nv[0], nv[1]);
     }
-    // this row at plane z + 1 in fixed point at its own exponent
+    // this row at plane z + 1 in fixed point at its own exponent, published
     {
       unsigned m = max(max((unsigned)fx::dexp(nv[0]), (unsigned)fx::dexp(nv[1])), (unsigned)fx::dexp(nh));
       m = __reduce_max_sync(0xffffffffu, m);
@@ -734,30 +737,28 @@ __global__ void __launch_bounds__(32 * kDCWarps) k3_dcx(ArgsDC3 a, const ArgsDC3
       xp[0] = fx::to_fixed(nv[0], bn);
       xp[1] = fx::to_fixed(nv[1], bn);
       hp = fx::to_fixed(nh, bn);
+      *(longlong2 *)(un + (ring * kDCWarps + w) * L::UNRowB + lane * 16) = make_longlong2(xp[0], xp[1]);
+      if (lane == 0) rexp[ring][w] = bn;
     }
-    __syncthreads();  // (B) updated rows of plane z + 1 visible
+    __syncthreads();  // (B) published rows of plane z + 1 visible
     if (z >= z0 && out_warp) {
-      const unsigned char *us = un + ((z % 3 + 3) % 3 * kDCWarps + (w - 1)) * L::UNRowB + lane * 16;
-      const unsigned char *un_ = un + ((z % 3 + 3) % 3 * kDCWarps + (w + 1)) * L::UNRowB + lane * 16;
-      const double2 s2 = *(const double2 *)us, n2 = *(const double2 *)un_;
+      const int rc = (z % 3 + 3) % 3;
+      const longlong2 s2 = *(const longlong2 *)(un + (rc * kDCWarps + (w - 1)) * L::UNRowB + lane * 16);
+      const longlong2 n2 = *(const longlong2 *)(un + (rc * kDCWarps + (w + 1)) * L::UNRowB + lane * 16);
+      const int bs = rexp[rc][w - 1], bnn = rexp[rc][w + 1];
       const double2 f2 = *(const double2 *)(slot(z + kDCRing) + kDCWarps * kURowB + kDCWarps * L::ERowB +
                                              (w - 1) * kFRowB + lane * 16);
-      const double ysv[2] = {s2.x, s2.y}, ynv[2] = {n2.x, n2.y}, fv[2] = {f2.x, f2.y};
-      unsigned my = 0, mf = 0;
-#pragma unroll
-      for (int q = 0; q < 2; q++) {
-        my = max(my, max((unsigned)fx::dexp(ysv[q]), (unsigned)fx::dexp(ynv[q])));
-        mf = max(mf, (unsigned)fx::dexp(fv[q]));
-      }
-      my = __reduce_max_sync(0xffffffffu, my);
+      unsigned mf = max((unsigned)fx::dexp(f2.x), (unsigned)fx::dexp(f2.y));
       mf = __reduce_max_sync(0xffffffffu, mf);
-      const bool bad = my == 0x7ffu || mf == 0x7ffu;
-      int B = max(max(bm, bc), max(bp, max((int)my, (int)mf - k2) + fx::kHead));
-      B = bad ? fx::kNonFinite + fx::kHead : B;
+      int B = max(max(max(bm, bc), max(bp, bs)), max(bnn, max((int)mf - k2, 0) + fx::kHead));
+      B = mf == 0x7ffu ? fx::kNonFinite + fx::kHead : B;
       long long um_[2] = {xm[0], xm[1]}, uc_[2] = {xc[0], xc[1]}, up_[2] = {xp[0], xp[1]}, h = hc;
+      long long ys[2] = {s2.x, s2.y}, yn[2] = {n2.x, n2.y};
       if (B != bm) { um_[0] = fx::align_down(um_[0], B - bm); um_[1] = fx::align_down(um_[1], B - bm); }
       if (B != bc) { uc_[0] = fx::align_down(uc_[0], B - bc); uc_[1] = fx::align_down(uc_[1], B - bc); h = fx::align_down(h, B - bc); }
       if (B != bp) { up_[0] = fx::align_down(up_[0], B - bp); up_[1] = fx::align_down(up_[1], B - bp); }
+      if (B != bs) { ys[0] = fx::align_down(ys[0], B - bs); ys[1] = fx::align_down(ys[1], B - bs); }
+      if (B != bnn) { yn[0] = fx::align_down(yn[0], B - bnn); yn[1] = fx::align_down(yn[1], B - bnn); }
       long long wl = fx::shfl_up64(uc_[1]), er = fx::shfl_dn64(uc_[0]);
       if (lane == 0) wl = h;
       if (lane == 31) er = h;
@@ -765,12 +766,12 @@ __global__ void __launch_bounds__(32 * kDCWarps) k3_dcx(ArgsDC3 a, const ArgsDC3
       const int E0 = B - 1085 + k2;
       const fx::Pow2f p2 = fx::pow2f(E0);
       const double s64 = ACC64 ? __hiloint2double((min(max(E0, -1022), 1023) + 1023) << 20, 0) : 0.0;
+      const double fv[2] = {f2.x, f2.y};
       float rv[2];
 #pragma unroll
       for (int q = 0; q < 2; q++) {
         const long long xw = q == 0 ? wl : uc_[0], xe = q == 1 ? er : uc_[1];
-        const long long S = 6 * uc_[q] - (xw + xe) - (fx::to_fixed(ysv[q], B) + fx::to_fixed(ynv[q], B)) -
-                            (um_[q] + up_[q]);
+        const long long S = 6 * uc_[q] - (xw + xe) - (ys[q] + yn[q]) - (um_[q] + up_[q]);
         const long long R = fx::to_fixed(fv[q], B + k2) - S;
         const int c = cl + q;
         const bool in = c >= 1 && c <= n - 2;
