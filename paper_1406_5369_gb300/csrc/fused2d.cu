@@ -2,6 +2,7 @@
 #include <string.h>
 
 #include "fused2d.cuh"
+#include "tile2d.cuh"
 
 namespace mg {
 namespace d2 {
@@ -132,6 +133,53 @@ cudaError_t launch_post(fz::Args2D a, int R_override, const Level &L, cudaStream
   return cudaGetLastError();
 }
 
+// Block-tile kernels (tile2d.cuh) for constant-stencil levels up to this size:
+// below it the streaming kernels' warps walk too few rows in parallel for the
+// grid to be bandwidth-bound, and a tile pass costs a handful of barriers.
+constexpr int kTileMaxN = 1025;
+
+bool tile_ok(const Level &L, int R) { return R <= 0 && !L.kf[0] && L.n <= kTileMaxN; }
+
+template <typename T, int NU, bool ZERO> cudaError_t launch_tpre(const fz::Args2D &a, const Level &L, cudaStream_t s) {
+  constexpr size_t smem = sizeof(typename CT<T>::type) * tz::PreGeo<NU>::elems;
+  static bool ready = false;
+  if (!ready) {
+    cudaError_t e = prepare(tz::k_tpre2d<T, NU, ZERO>, smem);
+    if (e != cudaSuccess) return e;
+    ready = true;
+  }
+  const dim3 g((unsigned)((L.n + tz::kTW - 1) / tz::kTW), (unsigned)((L.n + tz::kTH - 1) / tz::kTH));
+  tz::k_tpre2d<T, NU, ZERO><<<g, tz::kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, int NU> cudaError_t launch_tpost(const fz::Args2D &a, const Level &L, cudaStream_t s) {
+  constexpr size_t smem = sizeof(typename CT<T>::type) * tz::PostGeo<NU>::elems;
+  static bool ready = false;
+  if (!ready) {
+    cudaError_t e = prepare(tz::k_tpost2d<T, NU>, smem);
+    if (e != cudaSuccess) return e;
+    ready = true;
+  }
+  const dim3 g((unsigned)((L.n + tz::kTW - 1) / tz::kTW), (unsigned)((L.n + tz::kTH - 1) / tz::kTH));
+  tz::k_tpost2d<T, NU><<<g, tz::kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t dispatch_tpre(const fz::Args2D &a, const Level &L, cudaStream_t s, bool zero, int nu) {
+  if (L.dtype == F32) {
+    if (nu == 1) return zero ? launch_tpre<float, 1, true>(a, L, s) : launch_tpre<float, 1, false>(a, L, s);
+    return zero ? launch_tpre<float, 2, true>(a, L, s) : launch_tpre<float, 2, false>(a, L, s);
+  }
+  if (nu == 1) return zero ? launch_tpre<double, 1, true>(a, L, s) : launch_tpre<double, 1, false>(a, L, s);
+  return zero ? launch_tpre<double, 2, true>(a, L, s) : launch_tpre<double, 2, false>(a, L, s);
+}
+
+cudaError_t dispatch_tpost(const fz::Args2D &a, const Level &L, cudaStream_t s, int nu) {
+  if (L.dtype == F32) return nu == 1 ? launch_tpost<float, 1>(a, L, s) : launch_tpost<float, 2>(a, L, s);
+  return nu == 1 ? launch_tpost<double, 1>(a, L, s) : launch_tpost<double, 2>(a, L, s);
+}
+
 // Storage type, sweep count, zero start and stencil kind -> kernel instance.
 cudaError_t dispatch_pre(fz::Args2D a, int R, const Level &L, cudaStream_t s, const fz::Args2D *list, int count,
                          bool zero, int nu) {
@@ -177,6 +225,7 @@ cudaError_t pre_fused(const Level &L, const void *uin, void *uout, const Level &
   a.f = L.f;
   a.uout = uout;
   a.fc = fc;
+  if (tile_ok(L, R)) return dispatch_tpre(a, L, s, zero, nu);
   return dispatch_pre(a, R, L, s, nullptr, 1, zero, nu);
 }
 
@@ -187,6 +236,7 @@ cudaError_t post_fused(const Level &L, const void *uin, void *uout, const Level 
   a.f = L.f;
   a.uout = uout;
   a.ec = ec;
+  if (tile_ok(L, R)) return dispatch_tpost(a, L, s, nu);
   return dispatch_post(a, R, L, s, nullptr, 1, nu);
 }
 
