@@ -2,6 +2,7 @@
 #include <string.h>
 
 #include "fused2d.cuh"
+#include "fused2d_x2.cuh"
 #include "tile2d.cuh"
 
 namespace mg {
@@ -180,12 +181,73 @@ cudaError_t dispatch_tpost(const fz::Args2D &a, const Level &L, cudaStream_t s, 
   return nu == 1 ? launch_tpost<double, 1>(a, L, s) : launch_tpost<double, 2>(a, L, s);
 }
 
+// The packed-FP32 pre-smoothing kernel (fused2d_x2.cuh), constant stencil.
+template <int NU, bool ZERO>
+cudaError_t launch_pre_x2(fz::Args2D a, int R_override, const Level &L, cudaStream_t s, const fz::Args2D *list,
+                          int count) {
+  constexpr int W = 4;
+  constexpr size_t smem = (size_t)W * fz::kRing * 32 * 16 * 2;
+  static bool ready = false;
+  static int bps = 1;
+  if (!ready) {
+    cudaError_t e = prepare(fz::k_pre2d_x2<NU, ZERO, false>, smem);
+    if (e == cudaSuccess) e = prepare(fz::k_pre2d_x2<NU, ZERO, true>, smem);
+    if (e != cudaSuccess) return e;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fz::k_pre2d_x2<NU, ZERO, false>, 32 * W, smem);
+    if (bps < 1) bps = 1;
+    ready = true;
+  }
+  if (R_override <= 0) {
+    a.R = pick_rows(L.n, a.nstrips, bps, W, list ? kListRows : 0);
+    a.nchunks = (L.n + a.R - 1) / a.R;
+  }
+  long long warps = (long long)a.nstrips * a.nchunks;
+  unsigned blocks = (unsigned)((warps + W - 1) / W);
+  if (list)
+    fz::k_pre2d_x2<NU, ZERO, true><<<dim3(blocks, (unsigned)count), 32 * W, smem, s>>>(a, list);
+  else
+    fz::k_pre2d_x2<NU, ZERO, false><<<blocks, 32 * W, smem, s>>>(a, nullptr);
+  return cudaGetLastError();
+}
+
+template <int NU>
+cudaError_t launch_post_x2(fz::Args2D a, int R_override, const Level &L, cudaStream_t s, const fz::Args2D *list,
+                           int count) {
+  constexpr int W = 4;
+  constexpr size_t smem = (size_t)W * fz::kRing * 32 * (16 + 16 + 8);
+  static bool ready = false;
+  static int bps = 1;
+  if (!ready) {
+    cudaError_t e = prepare(fz::k_post2d_x2<NU, false>, smem);
+    if (e == cudaSuccess) e = prepare(fz::k_post2d_x2<NU, true>, smem);
+    if (e != cudaSuccess) return e;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fz::k_post2d_x2<NU, false>, 32 * W, smem);
+    if (bps < 1) bps = 1;
+    ready = true;
+  }
+  if (R_override <= 0) {
+    a.R = pick_rows(L.n, a.nstrips, bps, W, list ? kListRows : 0);
+    a.nchunks = (L.n + a.R - 1) / a.R;
+  }
+  long long warps = (long long)a.nstrips * a.nchunks;
+  unsigned blocks = (unsigned)((warps + W - 1) / W);
+  if (list)
+    fz::k_post2d_x2<NU, true><<<dim3(blocks, (unsigned)count), 32 * W, smem, s>>>(a, list);
+  else
+    fz::k_post2d_x2<NU, false><<<blocks, 32 * W, smem, s>>>(a, nullptr);
+  return cudaGetLastError();
+}
+
 // Storage type, sweep count, zero start and stencil kind -> kernel instance.
 cudaError_t dispatch_pre(fz::Args2D a, int R, const Level &L, cudaStream_t s, const fz::Args2D *list, int count,
                          bool zero, int nu) {
   const bool var = L.kf[0] != nullptr;
 #define MG_PRE(T, NUv, Z)                                                                      \
   return var ? launch_pre<T, NUv, Z, true>(a, R, L, s, list, count) : launch_pre<T, NUv, Z, false>(a, R, L, s, list, count)
+  if (L.dtype == F32 && !var) {
+    if (nu == 1) return zero ? launch_pre_x2<1, true>(a, R, L, s, list, count) : launch_pre_x2<1, false>(a, R, L, s, list, count);
+    return zero ? launch_pre_x2<2, true>(a, R, L, s, list, count) : launch_pre_x2<2, false>(a, R, L, s, list, count);
+  }
   if (L.dtype == F32) {
     if (nu == 1) { if (zero) { MG_PRE(float, 1, true); } else { MG_PRE(float, 1, false); } }
     if (zero) { MG_PRE(float, 2, true); } else { MG_PRE(float, 2, false); }
@@ -200,6 +262,8 @@ cudaError_t dispatch_post(fz::Args2D a, int R, const Level &L, cudaStream_t s, c
   const bool var = L.kf[0] != nullptr;
 #define MG_POST(T, NUv) \
   return var ? launch_post<T, NUv, true>(a, R, L, s, list, count) : launch_post<T, NUv, false>(a, R, L, s, list, count)
+  if (L.dtype == F32 && !var)
+    return nu == 1 ? launch_post_x2<1>(a, R, L, s, list, count) : launch_post_x2<2>(a, R, L, s, list, count);
   if (L.dtype == F32) {
     if (nu == 1) { MG_POST(float, 1); }
     MG_POST(float, 2);
