@@ -122,9 +122,11 @@ def dist_env():
 
 # ------------------------------------------------------------------ GPU arm
 
-# DRAM bytes (read + write) of one k_dc2d<float,1,0> launch at 8193^2, from ncu
-# (profiles/k_dc2d_outer_8193.md); set to None whenever that kernel changes.
-K_DC2D_TRAFFIC = 2146.2e6
+# DRAM bytes (read + write) per launch of the level-0 kernels at 8193^2, from
+# ncu (profiles/k_*_8193.md); each is set to None whenever its kernel changes.
+K_DCX2D_TRAFFIC = 2185.6e6  # profiles/k_dcx2d_outer_4097.md (8193^2 capture quoted there)
+K_PRE2D_TRAFFIC = 875.7e6  # u-reading launch; profiles/k_pre2d_x2_level0_4097.md (8193^2 capture)
+K_POST2D_TRAFFIC = None
 
 
 def run_gpu(args):
@@ -251,24 +253,24 @@ def run_gpu(args):
     # rooflines from the live per-kernel times
     hbm_peak, peak_kind = peaks()
     clk_sum = clk.summary()
-    sm_mhz = clk_sum.get("sm_mhz") or 2070.0
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    fp64_peak = 2.0 * sms * sm_mhz * 1e6 / 1e9  # G FP64 instr/s: 2 FP64 lanes per SM per clock
     nodes = float(n) * n
     inner = float(n - 2) ** 2
     w = 4  # FP32 inner words
     lines = []
     t_outer, c_outer = kinds["outer"]
     if c_outer:
-        a_outer = 6.0 * inner / (t_outer / c_outer * 1e-3) / 1e9
-        lines.append({"kernel": "k_dc2d: FP64 outer step (update + residual -> FP32 defect + norm partials), 8193^2",
-                      "bound": "alu", "achieved": a_outer, "peak": fp64_peak, "unit": "G FP64 instr/s",
-                      "frac": a_outer / fp64_peak, "traffic": K_DC2D_TRAFFIC,
-                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_dc2d<float,1,0> launch "
-                                        "at 8193^2 (profiles/k_dc2d_outer_8193.md); algorithmic 32 B/node = 2148 MB",
-                      "per_launch": "6 FP64 ops x 8191^2 interior nodes",
-                      "avg_launch_us": 1e3 * t_outer / c_outer, "launches": c_outer, "share": t_outer / (ms * args.steps),
-                      "peak_source": "2 FP64 lanes/SM/clock (nominal 1.25 TFLOP/s at 2070 MHz, 152 SMs) x 152 SMs x median SM clock"})
+        # exact outer step: read u, f (FP64) and e (FP32), write u (FP64) and the
+        # FP32 defect: 32 bytes per node of the 8193^2 grid
+        a_outer = 32.0 * nodes / (t_outer / c_outer * 1e-3) / 1e9
+        lines.append({"kernel": "k_dcx2d: outer step of defect correction (FP64 update, exact fixed-point residual "
+                                "-> FP32 defect + norm partials), 8193^2",
+                      "bound": "hbm", "achieved": a_outer, "peak": hbm_peak, "unit": "GB/s",
+                      "frac": a_outer / hbm_peak, "traffic": K_DCX2D_TRAFFIC,
+                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_dcx2d launch at "
+                                        "8193^2 (algorithmic 32 B/node = 2148 MB)",
+                      "per_launch": "read u, f (8 B each) and e (4 B), write u (8 B) and the defect (4 B) per node "
+                                    "= 32 B x 8193^2 = 2148 MB",
+                      "avg_launch_us": 1e3 * t_outer / c_outer, "launches": c_outer, "share": t_outer / (ms * args.steps)})
     t_pre, c_pre = kinds["pre"]
     if c_pre:
         # The first inner cycle of an outer step starts from u = 0 and does not read u:
@@ -277,24 +279,26 @@ def run_gpu(args):
         ic = best["inner_cycles"]
         words_pre = 2.25 + (ic - 1) / ic
         a_pre = (words_pre * w) * nodes / (t_pre / c_pre * 1e-3) / 1e9
-        lines.append({"kernel": "k_pre2d<float,2,zero>: 2 RBGS sweeps + residual + full weighting, level 0",
+        lines.append({"kernel": "k_pre2d_x2<2,zero>: 2 RBGS sweeps + residual + full weighting, level 0 (packed FP32)",
                       "bound": "hbm", "achieved": a_pre, "peak": hbm_peak, "unit": "GB/s", "frac": a_pre / hbm_peak,
-                      "traffic": None,
+                      "traffic": K_PRE2D_TRAFFIC,
+                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one level-0 launch that "
+                                        "reads u (13 B/node algorithmic = 872.6 MB) at 8193^2",
                       "per_launch": f"read f, write u (1 word each) + coarse f (1/4 word) per node, + read u in "
                                     f"{ic - 1} of {ic} launches ({words_pre:.3f} words/node on average)",
                       "avg_launch_us": 1e3 * t_pre / c_pre, "launches": c_pre, "share": t_pre / (ms * args.steps)})
     t_post, c_post = kinds["post"]
     if c_post:
         a_post = (3.25 * w) * nodes / (t_post / c_post * 1e-3) / 1e9
-        lines.append({"kernel": "k_post2d<float,1>: bilinear correction + 1 RBGS sweep, level 0",
+        lines.append({"kernel": "k_post2d_x2<1>: bilinear correction + 1 RBGS sweep, level 0 (packed FP32)",
                       "bound": "hbm", "achieved": a_post, "peak": hbm_peak, "unit": "GB/s", "frac": a_post / hbm_peak,
-                      "traffic": None, "per_launch": "read u, f (1 word each) + coarse e (1/4 word), write u per node",
+                      "traffic": K_POST2D_TRAFFIC, "per_launch": "read u, f (1 word each) + coarse e (1/4 word), write u per node",
                       "avg_launch_us": 1e3 * t_post / c_post, "launches": c_post, "share": t_post / (ms * args.steps)})
     dominant = max(lines, key=lambda d: d["share"]) if lines else None
     roofline = None
     if dominant:
         roofline = {k: dominant[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
-        roofline.update({"kernel": dominant["kernel"], "peak_kind": peak_kind if dominant["bound"] == "hbm" else "derived",
+        roofline.update({"kernel": dominant["kernel"], "peak_kind": peak_kind,
                          "timed": "CUDA events around the kernel inside the timed region (graph event nodes)"})
 
     rec = {
