@@ -126,7 +126,7 @@ def dist_env():
 # ncu (profiles/k_*_8193.md); each is set to None whenever its kernel changes.
 K_DCX2D_TRAFFIC = 2185.6e6  # profiles/k_dcx2d_outer_4097.md (8193^2 capture quoted there)
 K_PRE2D_TRAFFIC = 875.7e6  # u-reading launch; profiles/k_pre2d_x2_level0_4097.md (8193^2 capture)
-K_POST2D_TRAFFIC = None
+K_POST2D_TRAFFIC = 877.8e6  # profiles/k_post2d_x2_level0_4097.md (8193^2 capture)
 
 
 def run_gpu(args):
@@ -292,7 +292,9 @@ def run_gpu(args):
         a_post = (3.25 * w) * nodes / (t_post / c_post * 1e-3) / 1e9
         lines.append({"kernel": "k_post2d_x2<1>: bilinear correction + 1 RBGS sweep, level 0 (packed FP32)",
                       "bound": "hbm", "achieved": a_post, "peak": hbm_peak, "unit": "GB/s", "frac": a_post / hbm_peak,
-                      "traffic": K_POST2D_TRAFFIC, "per_launch": "read u, f (1 word each) + coarse e (1/4 word), write u per node",
+                      "traffic": K_POST2D_TRAFFIC,
+                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one level-0 launch at "
+                                        "8193^2 (13 B/node algorithmic = 872.6 MB)", "per_launch": "read u, f (1 word each) + coarse e (1/4 word), write u per node",
                       "avg_launch_us": 1e3 * t_post / c_post, "launches": c_post, "share": t_post / (ms * args.steps)})
     dominant = max(lines, key=lambda d: d["share"]) if lines else None
     roofline = None
