@@ -825,6 +825,10 @@ mg_status batched_outer(mg_batch *b, const std::vector<mg_ctx *> &ps, bool updat
     auto &v = kv.second;
     const Level &O0 = v[0].second->outer, &I0 = v[0].second->lv[0];
     int np = 0;
+    // the exact fixed-point step when every problem of the group asks for it
+    // and has a one-power-of-two stencil
+    bool exact = update;
+    for (auto &pc : v) exact = exact && pc.second->opt.exact_outer && pow2_stencil(pc.second->outer) != kNoPow2;
     if (dim == 2) {
       std::vector<oz::ArgsOuter> recs;
       for (auto &pc : v) {
@@ -833,11 +837,12 @@ mg_status batched_outer(mg_batch *b, const std::vector<mg_ctx *> &ps, bool updat
         oz::ArgsOuter r = d2::outer_record(O, (const double *)O.u[O.cur], (double *)O.u[O.cur ^ 1], I,
                                            update ? I.u[I.cur] : nullptr, I.f);
         r.partials = b->partials + (size_t)pc.first * kSlots;
+        r.k2 = exact ? pow2_stencil(O) : 0;
         recs.push_back(r);
       }
       const oz::ArgsOuter *dev = push_list(b, recs);
       if (!dev) return bfail(MG_ENOMEM, "batch descriptor area exhausted");
-      BCK("batched outer step", d2::dc_step_list(O0, I0, dev, (int)recs.size(), nullptr, kSlots, &np, update, s));
+      BCK("batched outer step", d2::dc_step_list(O0, I0, dev, (int)recs.size(), nullptr, kSlots, &np, update, exact, s));
     } else {
       std::vector<z3::ArgsDC3> recs;
       for (auto &pc : v) {
@@ -846,11 +851,12 @@ mg_status batched_outer(mg_batch *b, const std::vector<mg_ctx *> &ps, bool updat
         z3::ArgsDC3 r = d3::outer_record(O, (const double *)O.u[O.cur], (double *)O.u[O.cur ^ 1], I,
                                          update ? I.u[I.cur] : nullptr, I.f);
         r.partials = b->partials + (size_t)pc.first * kSlots;
+        r.k2 = exact ? pow2_stencil(O) : 0;
         recs.push_back(r);
       }
       const z3::ArgsDC3 *dev = push_list(b, recs);
       if (!dev) return bfail(MG_ENOMEM, "batch descriptor area exhausted");
-      BCK("batched outer step", d3::dc_step_list(O0, I0, dev, (int)recs.size(), nullptr, kSlots, &np, update, s));
+      BCK("batched outer step", d3::dc_step_list(O0, I0, dev, (int)recs.size(), nullptr, kSlots, &np, update, exact, s));
     }
     b->launches++;
     if (update)

@@ -200,13 +200,17 @@ oz::ArgsOuter outer_record(const Level &O, const double *uin, double *uout, cons
 }
 
 cudaError_t dc_step_list(const Level &O, const Level &I, const oz::ArgsOuter *list, int count, double *partials,
-                         int pstride, int *nparts, bool update, cudaStream_t s) {
+                         int pstride, int *nparts, bool update, bool exact, cudaStream_t s) {
   oz::ArgsOuter a;
   memset(&a, 0, sizeof a);
   a.partials = partials;
   a.n = O.n;
   a.pitch = O.pitch;
   a.pitchi = I.pitch;
+  if (exact && update) {
+    return I.dtype == F32 ? launch_dcx<float, true>(a, O.n, nparts, s, list, count, pstride)
+                          : launch_dcx<bf16, true>(a, O.n, nparts, s, list, count, pstride);
+  }
   if (I.dtype == F32) {
     return update ? launch_dc<float, true, true>(a, O.n, nparts, s, list, count, pstride)
                   : launch_dc<float, false, true>(a, O.n, nparts, s, list, count, pstride);

@@ -501,9 +501,11 @@ namespace d2 {
 oz::ArgsOuter outer_record(const Level &O, const double *uin, double *uout, const Level &I, const void *e, void *d);
 // k_dc2d over `count` problems of outer size O.n (inner level I): problem i
 // writes its per-warp partial sums to partials[i * pstride ...] (at most
-// pstride of them; *nparts receives the count).
+// pstride of them; *nparts receives the count). exact (with update): the
+// exact fixed-point step k_dcx2d; every record's k2 must then hold its
+// stencil's power-of-two exponent.
 cudaError_t dc_step_list(const Level &O, const Level &I, const oz::ArgsOuter *list, int count, double *partials,
-                         int pstride, int *nparts, bool update, cudaStream_t s);
+                         int pstride, int *nparts, bool update, bool exact, cudaStream_t s);
 }  // namespace d2
 }  // namespace mg
 

@@ -329,7 +329,7 @@ z3::ArgsDC3 outer_record(const Level &O, const double *uin, double *uout, const 
 }
 
 cudaError_t dc_step_list(const Level &O, const Level &I, const z3::ArgsDC3 *list, int count, double *partials,
-                         int pstride, int *nparts, bool update, cudaStream_t s) {
+                         int pstride, int *nparts, bool update, bool exact, cudaStream_t s) {
   z3::ArgsDC3 a;
   memset(&a, 0, sizeof a);
   a.partials = partials;
@@ -338,6 +338,10 @@ cudaError_t dc_step_list(const Level &O, const Level &I, const z3::ArgsDC3 *list
   a.pitchi = I.pitch;
   a.plane = O.plane;
   a.planei = I.plane;
+  if (exact && update) {
+    return I.dtype == F32 ? launch_dcx<float, true>(a, nparts, s, list, count, pstride)
+                          : launch_dcx<bf16, true>(a, nparts, s, list, count, pstride);
+  }
   if (I.dtype == F32)
     return update ? launch_dc<float, true, true>(a, nparts, s, list, count, pstride)
                   : launch_dc<float, false, true>(a, nparts, s, list, count, pstride);

@@ -816,7 +816,7 @@ cudaError_t z_transfer_list(bool restrict_, const Level &F, const Level &C, cons
                             cudaStream_t s);
 z3::ArgsDC3 outer_record(const Level &O, const double *uin, double *uout, const Level &I, const void *e, void *d);
 cudaError_t dc_step_list(const Level &O, const Level &I, const z3::ArgsDC3 *list, int count, double *partials,
-                         int pstride, int *nparts, bool update, cudaStream_t s);
+                         int pstride, int *nparts, bool update, bool exact, cudaStream_t s);
 }  // namespace d3
 }  // namespace mg
 
