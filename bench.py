@@ -555,6 +555,80 @@ def run_c5(args):
           saturated=saturated, clocks=clk.summary())
 
 
+# The paper's Table 2 (Poisson rows), ms per V(2,2) cycle on an NVIDIA GTX 680 (CUDA 5.5):
+# only the first column of the garbled table is a time, the others read as speedups over
+# it; these are the derived GPU times, double / float.
+PAPER_TABLE2_GTX680_MS = {
+    ("2D", "jacobi"): (85.0, 60.0), ("2D", "rbgs"): (132.8, 96.0),
+    ("3D", "jacobi"): (89.0, 59.0), ("3D", "rbgs"): (144.1, 102.0),
+}
+
+
+def run_table2(args):
+    """The paper's Table 2 Poisson workloads: one V(2,2) cycle on 4097^2 (2D, 4095^2 unknowns)
+    and 257^3 (3D), Jacobi omega = 0.8 and red-black Gauss-Seidel omega = 1, coarsening to 3^d.
+    double: a plain FP64 V-cycle (mg_vcycle of an FP64 context); float: one FP32-stored,
+    FP32-arithmetic V-cycle (the inner cycle of FP32 defect correction, timed as the difference
+    between one defect-correction step with 8 and with 1 inner cycles, divided by 7).
+    Also the residual reduction of 5 FP64 V(2,2) cycles from u0 ~ U[0,1), f = 0 (Sec. 4 reports
+    more than 1e8 for every Poisson test)."""
+    torch = _init_cuda()
+    import synth
+    from paper_1406_5369_gb300 import Solver
+    stream = torch.cuda.current_stream()
+
+    def time_calls(fn, reps):
+        for _ in range(3):
+            fn()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(reps):
+            fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / reps
+
+    reps = max(3, args.steps)
+    rows = []
+    for dim, n in ((2, 4097), (3, 257)):
+        zero = torch.zeros((n,) * dim, dtype=torch.float64, device="cuda")
+        u0 = torch.from_numpy(synth.random_u0(dim, n, 0x5EED0006)).cuda()
+        for sm, om in (("jacobi", 0.8), ("rbgs", 1.0)):
+            kw = dict(smoother=sm, omega=om, nu1=2, nu2=2)
+            s = Solver(dim, n, precision="fp64", maxit=5, **kw)
+            s.set_rhs(zero)
+            s.set_solution(u0)
+            r0 = s.residual_norm()
+            for _ in range(5):
+                s.vcycle()
+            red = r0 / s.residual_norm()
+            ms64 = time_calls(s.vcycle, reps)
+            del s
+            t = {}
+            for ic in (1, 8):
+                s = Solver(dim, n, precision="fp32_dc", inner_cycles=ic, maxit=1, **kw)
+                s.set_rhs(zero)
+                s.set_solution(u0)
+                t[ic] = time_calls(s.vcycle, reps)
+                del s
+            ms32 = (t[8] - t[1]) / 7
+            paper = PAPER_TABLE2_GTX680_MS[(f"{dim}D", sm)]
+            rows.append({"grid": f"{n}^{dim}", "smoother": sm, "omega": om,
+                         "ms_per_vcycle_f64": ms64, "ms_per_vcycle_f32": ms32,
+                         "paper_gtx680_ms_f64": paper[0], "paper_gtx680_ms_f32": paper[1],
+                         "residual_reduction_5_cycles_f64": red})
+    head = rows[0]
+    _line("ms per V(2,2) cycle (paper Table 2 Poisson workloads)", head["ms_per_vcycle_f64"], "ms per V(2,2) cycle",
+          False, head["ms_per_vcycle_f64"], args,
+          {"workload": "paper Table 2 Poisson rows: 4097^2 (2D) and 257^3 (3D), V(2,2), Jacobi omega=0.8 / RBGS "
+                       "omega=1, full weighting, bi-/trilinear, coarsening to 3^d; u0 ~ U[0,1) (seed 0x5EED0006), "
+                       "f = 0; value = 2D Jacobi FP64"},
+          "f64 / f32", table2=rows,
+          context="paper numbers: GTX 680 (192.2 GB/s, 128.8 GFLOP/s DP), derived from Table 2 as first "
+                  "column / speedup; hardware and software differ, context only")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -562,7 +636,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "table2"],
                     help="c2 (default): the 8193^2 headline; others print their own line")
     ap.add_argument("--batch-problems", type=int, default=4096)
     ap.add_argument("--rate", type=float, default=2000.0)
@@ -573,7 +647,7 @@ def main():
     elif args.workload == "c2":
         run_gpu(args)
     else:
-        {"c1": run_c1, "c3": run_c3, "c4": run_c4, "c5": run_c5}[args.workload](args)
+        {"c1": run_c1, "c3": run_c3, "c4": run_c4, "c5": run_c5, "table2": run_table2}[args.workload](args)
 
 
 if __name__ == "__main__":
