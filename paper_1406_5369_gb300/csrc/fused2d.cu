@@ -181,8 +181,9 @@ cudaError_t dispatch_tpost(const fz::Args2D &a, const Level &L, cudaStream_t s, 
   return nu == 1 ? launch_tpost<double, 1>(a, L, s) : launch_tpost<double, 2>(a, L, s);
 }
 
-// The packed-FP32 pre-smoothing kernel (fused2d_x2.cuh), constant stencil.
-template <int NU, bool ZERO>
+// The packed-FP32 fused kernels (fused2d_x2.cuh), constant stencil; G: the
+// relaxation term (1 - omega) u is present (omega != 1).
+template <int NU, bool ZERO, bool G>
 cudaError_t launch_pre_x2(fz::Args2D a, int R_override, const Level &L, cudaStream_t s, const fz::Args2D *list,
                           int count) {
   constexpr int W = 4;
@@ -190,10 +191,10 @@ cudaError_t launch_pre_x2(fz::Args2D a, int R_override, const Level &L, cudaStre
   static bool ready = false;
   static int bps = 1;
   if (!ready) {
-    cudaError_t e = prepare(fz::k_pre2d_x2<NU, ZERO, false>, smem);
-    if (e == cudaSuccess) e = prepare(fz::k_pre2d_x2<NU, ZERO, true>, smem);
+    cudaError_t e = prepare(fz::k_pre2d_x2<NU, ZERO, false, G>, smem);
+    if (e == cudaSuccess) e = prepare(fz::k_pre2d_x2<NU, ZERO, true, G>, smem);
     if (e != cudaSuccess) return e;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fz::k_pre2d_x2<NU, ZERO, false>, 32 * W, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fz::k_pre2d_x2<NU, ZERO, false, G>, 32 * W, smem);
     if (bps < 1) bps = 1;
     ready = true;
   }
@@ -204,13 +205,13 @@ cudaError_t launch_pre_x2(fz::Args2D a, int R_override, const Level &L, cudaStre
   long long warps = (long long)a.nstrips * a.nchunks;
   unsigned blocks = (unsigned)((warps + W - 1) / W);
   if (list)
-    fz::k_pre2d_x2<NU, ZERO, true><<<dim3(blocks, (unsigned)count), 32 * W, smem, s>>>(a, list);
+    fz::k_pre2d_x2<NU, ZERO, true, G><<<dim3(blocks, (unsigned)count), 32 * W, smem, s>>>(a, list);
   else
-    fz::k_pre2d_x2<NU, ZERO, false><<<blocks, 32 * W, smem, s>>>(a, nullptr);
+    fz::k_pre2d_x2<NU, ZERO, false, G><<<blocks, 32 * W, smem, s>>>(a, nullptr);
   return cudaGetLastError();
 }
 
-template <int NU>
+template <int NU, bool G>
 cudaError_t launch_post_x2(fz::Args2D a, int R_override, const Level &L, cudaStream_t s, const fz::Args2D *list,
                            int count) {
   constexpr int W = 4;
@@ -218,10 +219,10 @@ cudaError_t launch_post_x2(fz::Args2D a, int R_override, const Level &L, cudaStr
   static bool ready = false;
   static int bps = 1;
   if (!ready) {
-    cudaError_t e = prepare(fz::k_post2d_x2<NU, false>, smem);
-    if (e == cudaSuccess) e = prepare(fz::k_post2d_x2<NU, true>, smem);
+    cudaError_t e = prepare(fz::k_post2d_x2<NU, false, G>, smem);
+    if (e == cudaSuccess) e = prepare(fz::k_post2d_x2<NU, true, G>, smem);
     if (e != cudaSuccess) return e;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fz::k_post2d_x2<NU, false>, 32 * W, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fz::k_post2d_x2<NU, false, G>, 32 * W, smem);
     if (bps < 1) bps = 1;
     ready = true;
   }
@@ -232,10 +233,21 @@ cudaError_t launch_post_x2(fz::Args2D a, int R_override, const Level &L, cudaStr
   long long warps = (long long)a.nstrips * a.nchunks;
   unsigned blocks = (unsigned)((warps + W - 1) / W);
   if (list)
-    fz::k_post2d_x2<NU, true><<<dim3(blocks, (unsigned)count), 32 * W, smem, s>>>(a, list);
+    fz::k_post2d_x2<NU, true, G><<<dim3(blocks, (unsigned)count), 32 * W, smem, s>>>(a, list);
   else
-    fz::k_post2d_x2<NU, false><<<blocks, 32 * W, smem, s>>>(a, nullptr);
+    fz::k_post2d_x2<NU, false, G><<<blocks, 32 * W, smem, s>>>(a, nullptr);
   return cudaGetLastError();
+}
+
+template <int NU, bool ZERO>
+cudaError_t pre_x2(const fz::Args2D &a, int R, const Level &L, cudaStream_t s, const fz::Args2D *list, int count) {
+  return a.has_gamma ? launch_pre_x2<NU, ZERO, true>(a, R, L, s, list, count)
+                     : launch_pre_x2<NU, ZERO, false>(a, R, L, s, list, count);
+}
+template <int NU>
+cudaError_t post_x2(const fz::Args2D &a, int R, const Level &L, cudaStream_t s, const fz::Args2D *list, int count) {
+  return a.has_gamma ? launch_post_x2<NU, true>(a, R, L, s, list, count)
+                     : launch_post_x2<NU, false>(a, R, L, s, list, count);
 }
 
 // Storage type, sweep count, zero start and stencil kind -> kernel instance.
@@ -245,8 +257,8 @@ cudaError_t dispatch_pre(fz::Args2D a, int R, const Level &L, cudaStream_t s, co
 #define MG_PRE(T, NUv, Z)                                                                      \
   return var ? launch_pre<T, NUv, Z, true>(a, R, L, s, list, count) : launch_pre<T, NUv, Z, false>(a, R, L, s, list, count)
   if (L.dtype == F32 && !var) {
-    if (nu == 1) return zero ? launch_pre_x2<1, true>(a, R, L, s, list, count) : launch_pre_x2<1, false>(a, R, L, s, list, count);
-    return zero ? launch_pre_x2<2, true>(a, R, L, s, list, count) : launch_pre_x2<2, false>(a, R, L, s, list, count);
+    if (nu == 1) return zero ? pre_x2<1, true>(a, R, L, s, list, count) : pre_x2<1, false>(a, R, L, s, list, count);
+    return zero ? pre_x2<2, true>(a, R, L, s, list, count) : pre_x2<2, false>(a, R, L, s, list, count);
   }
   if (L.dtype == F32) {
     if (nu == 1) { if (zero) { MG_PRE(float, 1, true); } else { MG_PRE(float, 1, false); } }
@@ -263,7 +275,7 @@ cudaError_t dispatch_post(fz::Args2D a, int R, const Level &L, cudaStream_t s, c
 #define MG_POST(T, NUv) \
   return var ? launch_post<T, NUv, true>(a, R, L, s, list, count) : launch_post<T, NUv, false>(a, R, L, s, list, count)
   if (L.dtype == F32 && !var)
-    return nu == 1 ? launch_post_x2<1>(a, R, L, s, list, count) : launch_post_x2<2>(a, R, L, s, list, count);
+    return nu == 1 ? post_x2<1>(a, R, L, s, list, count) : post_x2<2>(a, R, L, s, list, count);
   if (L.dtype == F32) {
     if (nu == 1) { MG_POST(float, 1); }
     MG_POST(float, 2);

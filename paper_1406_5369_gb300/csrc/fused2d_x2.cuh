@@ -53,14 +53,14 @@ __device__ __forceinline__ CoefX2 coef_x2(const Args2D &a) {
 // Half-sweep of row r (pairs E, O) with rows r-1 (A) and r+1 (B): PAR = 0
 // updates the even columns (E), PAR = 1 the odd ones (O). CHECK: the row and
 // the columns may touch the boundary (rowok, masks mE / mO per component).
-template <bool CHECK, int PAR>
+template <bool CHECK, int PAR, bool G>
 __device__ __forceinline__ void half_x2(float2 &E, float2 &O, const float2 &AE, const float2 &AO, const float2 &BE,
                                         const float2 &BO, const float2 &FE, const float2 &FO, bool rowok,
                                         const bool (&mE)[2], const bool (&mO)[2], const CoefX2 &k) {
   if constexpr (PAR == 0) {
     const float2 w = make_float2(shup(O.y), O.x);
     float2 v = fma2(k.bx, add2(w, O), fma2(k.by, add2(AE, BE), FE));
-    if (k.has_gamma) v = fma2(k.gam, E, v);
+    if (G) v = fma2(k.gam, E, v);
     if (CHECK) {
       E.x = rowok && mE[0] ? v.x : E.x;
       E.y = rowok && mE[1] ? v.y : E.y;
@@ -70,7 +70,7 @@ __device__ __forceinline__ void half_x2(float2 &E, float2 &O, const float2 &AE, 
   } else {
     const float2 e = make_float2(E.y, shdn(E.x));
     float2 v = fma2(k.bx, add2(E, e), fma2(k.by, add2(AO, BO), FO));
-    if (k.has_gamma) v = fma2(k.gam, O, v);
+    if (G) v = fma2(k.gam, O, v);
     if (CHECK) {
       O.x = rowok && mO[0] ? v.x : O.x;
       O.y = rowok && mO[1] ? v.y : O.y;
@@ -80,7 +80,7 @@ __device__ __forceinline__ void half_x2(float2 &E, float2 &O, const float2 &AE, 
   }
 }
 
-template <int NU, bool ZERO, bool LIST>
+template <int NU, bool ZERO, bool LIST, bool G>
 __global__ void __launch_bounds__(128, 4) k_pre2d_x2(Args2D a, const Args2D *__restrict__ list) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (LIST) take_problem(a, list[blockIdx.y]);
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(128, 4) k_pre2d_x2(Args2D a, const Args2D *__r
           constexpr int PAR = ((h - 1) ^ (K - h)) & 1;  // colour (h - 1) & 1 on row t - h, t = K mod 2
           const int r = t - h;
           const bool rowok = !CHECK || (r >= 1 && r <= n - 2);
-          half_x2<CHECK, PAR>(UE[sc], UO[sc], UE[sa], UO[sa], UE[sb], UO[sb], FE[sc], FO[sc], rowok, mE, mO, k);
+          half_x2<CHECK, PAR, G>(UE[sc], UO[sc], UE[sa], UO[sa], UE[sb], UO[sb], FE[sc], FO[sc], rowok, mE, mO, k);
         });
         // final u of row t - 2 NU
         {
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(128, 4) k_pre2d_x2(Args2D a, const Args2D *__r
 // stencil) with the same pair layout: a lane's coarse values at J0 = c0 / 2
 // and J0 + 1 form one pair, so the correction of a fine row is (e0, e1) on
 // the even columns and the averages (e0 + e1, e1 + e2) / 2 on the odd ones.
-template <int NU, bool LIST>
+template <int NU, bool LIST, bool G>
 __global__ void __launch_bounds__(128, 4) k_post2d_x2(Args2D a, const Args2D *__restrict__ list) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (LIST) take_problem(a, list[blockIdx.y]);
@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(128, 4) k_post2d_x2(Args2D a, const Args2D *__
           constexpr int PAR = ((h - 1) ^ (K - h)) & 1;
           const int r = t - h;
           const bool rowok = !CHECK || (r >= 1 && r <= n - 2);
-          half_x2<CHECK, PAR>(UE[sc], UO[sc], UE[sa], UO[sa], UE[sb], UO[sb], FE[sc], FO[sc], rowok, mE, mO, k);
+          half_x2<CHECK, PAR, G>(UE[sc], UO[sc], UE[sa], UO[sa], UE[sb], UO[sb], FE[sc], FO[sc], rowok, mE, mO, k);
         });
         {
           const int r = t - 2 * NU;
