@@ -549,9 +549,11 @@ def run_c5(args):
           1e3 * stats["wall_s"] / max(1, stats["steps"]), args,
           {"workload": f"serving: Poisson arrivals at {rate:g} req/s for {args.serve_seconds:g} s ({count} requests); "
                        "70% 2D Poisson 65^2..4097^2 (RBGS V(2,1)), 30% 3D 33^3..257^3 (Jacobi V(2,2)), sizes "
-                       "log-uniform over 2^m+1, f ~ U[-1,1], tol 1e-6 or 1e-10; FP32-DC; 150 GB HBM budget; "
+                       "log-uniform over 2^m+1, f ~ U[-1,1], tol 1e-6 or 1e-10; 2D FP32-DC, 3D BF16-DC, 3 inner "
+                       "cycles per outer step; 150 GB HBM budget; "
                        "hierarchies resident and pooled; same-level batching across requests"},
-          "f32 inner / f64 outer", p50_ms=stats["p50_ms"], p99_ms=stats["p99_ms"], serving=stats,
+          "f32 (2D) / bf16-stored f32 (3D) inner, f64 outer", p50_ms=stats["p50_ms"], p99_ms=stats["p99_ms"],
+          serving=stats,
           saturated=saturated, clocks=clk.summary())
 
 

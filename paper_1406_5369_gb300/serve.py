@@ -23,9 +23,13 @@ import numpy as np
 from .batch import BatchSolver
 from .solver import Solver
 
+# Per-dimension solver settings. 3 inner V-cycles per outer step and BF16
+# storage for the 3D inner cycles measured fastest on the serving mix
+# (838 vs 749 solves/s against 2 inner cycles and FP32 storage everywhere);
+# every request still reaches its tolerance by the FP64 outer residual.
 DEFAULT_PARAMS = {
-    2: dict(smoother="rbgs", omega=1.0, nu1=2, nu2=1, precision="fp32_dc", inner_cycles=2),
-    3: dict(smoother="jacobi", omega=6.0 / 7.0, nu1=2, nu2=2, precision="fp32_dc", inner_cycles=2),
+    2: dict(smoother="rbgs", omega=1.0, nu1=2, nu2=1, precision="fp32_dc", inner_cycles=3),
+    3: dict(smoother="jacobi", omega=6.0 / 7.0, nu1=2, nu2=2, precision="bf16_dc", inner_cycles=3),
 }
 
 
