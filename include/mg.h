@@ -97,7 +97,19 @@ typedef struct { int kind; const double *dirichlet_values; } mg_boundary;
  *                         evaluated exactly in 64-bit fixed-point integers and
  *                         rounded once (at least FP64 accuracy, no FP64
  *                         instruction); 0 = FP64 arithmetic. The update
- *                         u += e is an FP64 addition either way. */
+ *                         u += e is an FP64 addition either way.
+ * Tile shape and sweep fusion of the 2D fine-level kernels (performance
+ * only; every setting computes the same iteration up to FP32 rounding order
+ * in the inner cycles, and the library's autotuner searches them):
+ * tile_rows             : rows each warp of the streaming fused kernels walks
+ *                         (rounded up to a multiple of 8); 0 = automatic (one
+ *                         wave of resident warps)
+ * tile_max_n            : largest level size (nodes per dimension) that runs on
+ *                         the shared-memory block-tile kernels instead of the
+ *                         streaming ones; 0 = 1025, values below 33 = none
+ * fuse_depth            : sweeps fused into each pre-/post-smoothing pass
+ *                         (0 = all nu1 / nu2); with 0 < fuse_depth < nu the
+ *                         other nu - fuse_depth sweeps run as separate passes */
 typedef struct {
   mg_smoother smoother;
   double omega;
@@ -110,13 +122,17 @@ typedef struct {
   int use_graph;
   int inner_cycles;
   int exact_outer;
+  int tile_rows;
+  int tile_max_n;
+  int fuse_depth;
 } mg_options;
 
 typedef struct mg_ctx mg_ctx;
 
 /* Fills *opt with RBGS, omega 1, V(2,1), coarsest 3, maxit 50, FP64,
- * default stream, fuse 1, use_graph 1, inner_cycles 1, exact_outer 1 (the
- * Layer-3 defaults of Sec. 2.3). */
+ * default stream, fuse 1, use_graph 1, inner_cycles 1, exact_outer 1,
+ * tile_rows 0, tile_max_n 0, fuse_depth 0 (the Layer-3 defaults of Sec. 2.3
+ * and automatic tiling). */
 void mg_default_options(mg_options *opt);
 
 /* Bytes of device arena mg_create needs for this problem (0 if the

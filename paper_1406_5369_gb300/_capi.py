@@ -32,7 +32,8 @@ class mg_options(ctypes.Structure):
     _fields_ = [("smoother", ctypes.c_int), ("omega", ctypes.c_double), ("nu1", ctypes.c_int),
                 ("nu2", ctypes.c_int), ("coarsest_n", ctypes.c_int), ("maxit", ctypes.c_int),
                 ("precision", ctypes.c_int), ("stream", ctypes.c_void_p), ("fuse", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("inner_cycles", ctypes.c_int), ("exact_outer", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("inner_cycles", ctypes.c_int), ("exact_outer", ctypes.c_int),
+                ("tile_rows", ctypes.c_int), ("tile_max_n", ctypes.c_int), ("fuse_depth", ctypes.c_int)]
 
 
 # name -> (restype, argtypes); every function declared in include/mg.h.

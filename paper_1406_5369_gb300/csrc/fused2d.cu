@@ -139,7 +139,9 @@ cudaError_t launch_post(fz::Args2D a, int R_override, const Level &L, cudaStream
 // grid to be bandwidth-bound, and a tile pass costs a handful of barriers.
 constexpr int kTileMaxN = 1025;
 
-bool tile_ok(const Level &L, int R) { return R <= 0 && !L.kf[0] && L.n <= kTileMaxN; }
+bool tile_ok(const Level &L, int tile_max_n) {
+  return !L.kf[0] && L.n <= (tile_max_n > 0 ? tile_max_n : kTileMaxN);
+}
 
 template <typename T, int NU, bool ZERO> cudaError_t launch_tpre(const fz::Args2D &a, const Level &L, cudaStream_t s) {
   constexpr size_t smem = sizeof(typename CT<T>::type) * tz::PreGeo<NU>::elems;
@@ -295,24 +297,24 @@ bool fused_ok(const Level &L, const Level &Cl, int nu) {
 }
 
 cudaError_t pre_fused(const Level &L, const void *uin, void *uout, const Level &Cl, void *fc, bool zero, int nu,
-                      double omega, int R, cudaStream_t s) {
+                      double omega, int R, int tile_max_n, cudaStream_t s) {
   fz::Args2D a = make_args(L, Cl, omega, R, 1);
   a.uin = uin;
   a.f = L.f;
   a.uout = uout;
   a.fc = fc;
-  if (tile_ok(L, R)) return dispatch_tpre(a, L, s, zero, nu);
+  if (tile_ok(L, tile_max_n)) return dispatch_tpre(a, L, s, zero, nu);
   return dispatch_pre(a, R, L, s, nullptr, 1, zero, nu);
 }
 
 cudaError_t post_fused(const Level &L, const void *uin, void *uout, const Level &Cl, const void *ec, int nu,
-                       double omega, int R, cudaStream_t s) {
+                       double omega, int R, int tile_max_n, cudaStream_t s) {
   fz::Args2D a = make_args(L, Cl, omega, R, 1);
   a.uin = uin;
   a.f = L.f;
   a.uout = uout;
   a.ec = ec;
-  if (tile_ok(L, R)) return dispatch_tpost(a, L, s, nu);
+  if (tile_ok(L, tile_max_n)) return dispatch_tpost(a, L, s, nu);
   return dispatch_post(a, R, L, s, nullptr, 1, nu);
 }
 

@@ -154,6 +154,9 @@ mg_status check_args(int dim, int n, const mg_options *opt) {
   if (opt->precision != MG_FP64 && opt->precision != MG_FP32_DC && opt->precision != MG_BF16_DC)
     return fail(MG_EINVAL, "unknown precision");
   if (opt->exact_outer != 0 && opt->exact_outer != 1) return fail(MG_EINVAL, "exact_outer must be 0 or 1");
+  if (opt->tile_rows < 0 || opt->tile_rows > (1 << 20)) return fail(MG_EINVAL, "tile_rows must lie in 0..2^20");
+  if (opt->tile_max_n < 0) return fail(MG_EINVAL, "tile_max_n must be >= 0");
+  if (opt->fuse_depth < 0 || opt->fuse_depth > 8) return fail(MG_EINVAL, "fuse_depth must lie in 0..8");
   return MG_OK;
 }
 
@@ -315,9 +318,15 @@ mg_status op_zero_u(mg_ctx *c, int l, cudaStream_t s) {
 }
 
 // True when level l's pre- and post-smoothing run as fused 2D kernels.
+// Sweeps a fused 2D pass takes of nu (fuse_depth; 0 = all of them).
+int fused_sweeps(const mg_ctx *c, int nu) {
+  return c->opt.fuse_depth > 0 && c->opt.fuse_depth < nu ? c->opt.fuse_depth : nu;
+}
+
 bool level_fused(mg_ctx *c, int l) {
   if (!c->opt.fuse || c->opt.smoother != MG_RBGS || l + 1 >= c->nl) return false;
-  return mg::d2::fused_ok(c->lv[l], c->lv[l + 1], c->opt.nu1) && mg::d2::fused_ok(c->lv[l], c->lv[l + 1], c->opt.nu2);
+  return mg::d2::fused_ok(c->lv[l], c->lv[l + 1], fused_sweeps(c, c->opt.nu1)) &&
+         mg::d2::fused_ok(c->lv[l], c->lv[l + 1], fused_sweeps(c, c->opt.nu2));
 }
 
 // Algorithm 1 from level l down: presmooth, residual, restrict, zero the
@@ -337,13 +346,24 @@ mg_status vcycle_rec(mg_ctx *c, int l, bool zero, cudaStream_t s) {
   }
   Level &L = c->lv[l], &C = c->lv[l + 1];
   if (level_fused(c, l)) {
+      // fuse_depth d < nu: nu - d separate sweeps before the fused pre-smoothing
+    // pass and after the fused post-smoothing pass
+    const int d1 = fused_sweeps(c, c->opt.nu1), d2 = fused_sweeps(c, c->opt.nu2);
+    if (d1 < c->opt.nu1) {
+      if (zero && (st = op_zero_u(c, l, s))) return st;
+      if ((st = op_smooth(c, l, c->opt.nu1 - d1, s, MG_KERNEL_PRESMOOTH))) return st;
+      zero = false;
+    }
     TLAUNCH(c, MG_KERNEL_PRESMOOTH, l, s,
-            mg::d2::pre_fused(L, L.u[L.cur], L.u[L.cur ^ 1], C, C.f, zero, c->opt.nu1, c->opt.omega, 0, s));
+            mg::d2::pre_fused(L, L.u[L.cur], L.u[L.cur ^ 1], C, C.f, zero, d1, c->opt.omega, c->opt.tile_rows,
+                              c->opt.tile_max_n, s));
     L.cur ^= 1;
     if ((st = vcycle_rec(c, l + 1, true, s))) return st;
     TLAUNCH(c, MG_KERNEL_POSTSMOOTH, l, s,
-            mg::d2::post_fused(L, L.u[L.cur], L.u[L.cur ^ 1], C, C.u[C.cur], c->opt.nu2, c->opt.omega, 0, s));
+            mg::d2::post_fused(L, L.u[L.cur], L.u[L.cur ^ 1], C, C.u[C.cur], d2, c->opt.omega, c->opt.tile_rows,
+                               c->opt.tile_max_n, s));
     L.cur ^= 1;
+    if (d2 < c->opt.nu2) return op_smooth(c, l, c->opt.nu2 - d2, s, MG_KERNEL_POSTSMOOTH);
     return MG_OK;
   }
   if (zero && (st = op_zero_u(c, l, s))) return st;

@@ -74,13 +74,15 @@ MG_DIM_OPS
 
 // Fused 2D fine-level kernels (constant stencil, RBGS): nu sweeps +
 // residual + restriction into fc, and interpolation/correction + nu sweeps.
-// R = rows per chunk (0 = automatic).
+// R = rows per chunk of the streaming kernels (0 = automatic); levels up to
+// tile_max_n nodes per dimension run on the block-tile kernels (0 = the
+// default size, below 33 = none).
 namespace d2 {
 bool fused_ok(const Level &L, const Level &Cl, int nu);
 cudaError_t pre_fused(const Level &L, const void *uin, void *uout, const Level &Cl, void *fc, bool zero, int nu,
-                      double omega, int R, cudaStream_t s);
+                      double omega, int R, int tile_max_n, cudaStream_t s);
 cudaError_t post_fused(const Level &L, const void *uin, void *uout, const Level &Cl, const void *ec, int nu,
-                       double omega, int R, cudaStream_t s);
+                       double omega, int R, int tile_max_n, cudaStream_t s);
 }  // namespace d2
 
 // Streaming 2D finest-level kernels (constant stencil). dc_step: FP64 outer

@@ -48,7 +48,8 @@ class Solver:
 
     def __init__(self, dim, n, *, stencil=(1.0, 1.0, 1.0), k=None, dirichlet=None,
                  smoother="rbgs", omega=1.0, nu1=2, nu2=1, maxit=50, precision="fp64",
-                 fuse=True, use_graph=True, inner_cycles=1, exact_outer=True, stream=None, device="cuda"):
+                 fuse=True, use_graph=True, inner_cycles=1, exact_outer=True, tile_rows=0, tile_max_n=0,
+                 fuse_depth=0, stream=None, device="cuda"):
         import torch
         self._lib = C.load()
         self.dim, self.n = dim, n
@@ -63,6 +64,9 @@ class Solver:
         opt.use_graph = int(bool(use_graph))
         opt.inner_cycles = int(inner_cycles)
         opt.exact_outer = int(bool(exact_outer))
+        opt.tile_rows = int(tile_rows)
+        opt.tile_max_n = int(tile_max_n)
+        opt.fuse_depth = int(fuse_depth)
         opt.stream = default_stream_handle() if stream is None else stream
         self._tstream = torch.cuda.current_stream() if stream is None else torch.cuda.ExternalStream(stream)
         self.opt = opt

@@ -134,3 +134,49 @@ def test_fused_variable_coefficient_fp32_equals_unfused(n, nu1, nu2, omega):
     u = s.get_solution()
     faces = oracle.node_faces(k)
     assert oracle.norm(oracle.residual(u, f, faces=faces)) / oracle.norm(f) <= 1.01e-8
+
+
+# ------------------------------------------------------------ tiling and fusion knobs
+
+KNOBS = [dict(tile_rows=64), dict(tile_rows=8), dict(tile_max_n=1), dict(tile_max_n=2049),
+         dict(fuse_depth=1), dict(fuse_depth=1, tile_max_n=1, tile_rows=128)]
+
+
+@pytest.mark.parametrize("knobs", KNOBS)
+@pytest.mark.parametrize("nu1,nu2,omega", [(2, 1, 1.0), (2, 2, 0.9)])
+def test_tiling_knobs_fp64_match_oracle(knobs, nu1, nu2, omega):
+    # Every tile shape and fusion depth computes the same FP64 iteration: the
+    # per-cycle relative residuals match the oracle's to 1e-12 (1025^2 takes
+    # the block tiles by default, 2049^2 the streaming kernels).
+    for n in (1025, 2049):
+        f = synth.uniform_rhs(2, n, 0x5EED0002 ^ n)
+        _, hist = history(2, n, f, 3, nu1=nu1, nu2=nu2, omega=omega, **knobs)
+        _, rho = oracle_history(2, n, f, 3, nu1=nu1, nu2=nu2, omega=omega)
+        assert np.max(np.abs(hist - rho)) <= 1e-12, (knobs, n, hist, rho)
+
+
+@pytest.mark.parametrize("knobs", KNOBS)
+def test_tiling_knobs_fp32_dc_reach_tolerance(knobs):
+    # FP32 inner cycles under every setting: the same number of outer steps to
+    # 1e-10 as the default, by the oracle's own FP64 residual.
+    need_gpu()
+    from paper_1406_5369_gb300 import Solver
+    n = 2049
+    f = synth.uniform_rhs(2, n, 0x5EED0002)
+    its = []
+    for kw in ({}, knobs):
+        s = Solver(2, n, precision="fp32_dc", inner_cycles=3, maxit=40, **kw)
+        s.set_rhs(f)
+        it, rr, _ = s.solve(1e-10)
+        assert oracle.norm(oracle.residual(s.get_solution(), f)) / oracle.norm(f) <= 1.01e-10
+        its.append(it)
+    assert its[0] == its[1]
+
+
+def test_tiling_knobs_rejected_when_out_of_range():
+    need_gpu()
+    from paper_1406_5369_gb300 import Solver
+    from paper_1406_5369_gb300._capi import MGError
+    for kw in (dict(tile_rows=-1), dict(tile_max_n=-5), dict(fuse_depth=9)):
+        with pytest.raises(MGError):
+            Solver(2, 65, **kw)
