@@ -106,7 +106,7 @@ typedef struct { int kind; const double *dirichlet_values; } mg_boundary;
  *                         wave of resident warps)
  * tile_max_n            : largest level size (nodes per dimension) that runs on
  *                         the shared-memory block-tile kernels instead of the
- *                         streaming ones; 0 = 1025, values below 33 = none
+ *                         streaming ones; 0 = 257, values below 33 = none
  * fuse_depth            : sweeps fused into each pre-/post-smoothing pass
  *                         (0 = all nu1 / nu2); with 0 < fuse_depth < nu the
  *                         other nu - fuse_depth sweeps run as separate passes */

@@ -134,10 +134,12 @@ cudaError_t launch_post(fz::Args2D a, int R_override, const Level &L, cudaStream
   return cudaGetLastError();
 }
 
-// Block-tile kernels (tile2d.cuh) for constant-stencil levels up to this size:
-// below it the streaming kernels' warps walk too few rows in parallel for the
-// grid to be bandwidth-bound, and a tile pass costs a handful of barriers.
-constexpr int kTileMaxN = 1025;
+// Block-tile kernels (tile2d.cuh) for constant-stencil levels up to this size
+// (mg_options.tile_max_n overrides it): below it the streaming kernels' warps
+// walk too few rows in parallel for the grid to be bandwidth-bound, and a
+// tile pass costs a handful of barriers. 257 is what the autotuner picks on
+// the GB300 for the 8193^2 workload.
+constexpr int kTileMaxN = 257;
 
 bool tile_ok(const Level &L, int tile_max_n) {
   return !L.kf[0] && L.n <= (tile_max_n > 0 ? tile_max_n : kTileMaxN);
