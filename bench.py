@@ -570,7 +570,7 @@ def run_c5(args):
 
 # The paper's Table 2 (Poisson rows), ms per V(2,2) cycle on an NVIDIA GTX 680 (CUDA 5.5):
 # only the first column of the garbled table is a time, the others read as speedups over
-# it; these are the derived GPU times, double / float.
+# it; these are the GPU times derived that way (first column / speedup), double / float.
 PAPER_TABLE2_GTX680_MS = {
     ("2D", "jacobi"): (85.0, 60.0), ("2D", "rbgs"): (132.8, 96.0),
     ("3D", "jacobi"): (89.0, 59.0), ("3D", "rbgs"): (144.1, 102.0),
