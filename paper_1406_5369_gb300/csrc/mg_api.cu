@@ -366,8 +366,15 @@ mg_status vcycle_rec(mg_ctx *c, int l, bool zero, cudaStream_t s) {
     if (d2 < c->opt.nu2) return op_smooth(c, l, c->opt.nu2 - d2, s, MG_KERNEL_POSTSMOOTH);
     return MG_OK;
   }
-  if (zero && (st = op_zero_u(c, l, s))) return st;
-  if ((st = op_smooth(c, l, c->opt.nu1, s, MG_KERNEL_PRESMOOTH))) return st;
+  if (zero && c->opt.fuse && c->opt.smoother == MG_JACOBI && c->opt.nu1 >= 2 && c->dim == 3 && mg::d3::z_ok(L)) {
+    // the first two sweeps from zero in one pass that reads f only (no zeroing pass)
+    TLAUNCH(c, MG_KERNEL_PRESMOOTH, l, s, mg::d3::z_jacobi_zero2(L, L.f, L.u[L.cur ^ 1], c->opt.omega, s));
+    L.cur ^= 1;
+    if ((st = op_smooth(c, l, c->opt.nu1 - 2, s, MG_KERNEL_PRESMOOTH))) return st;
+  } else {
+    if (zero && (st = op_zero_u(c, l, s))) return st;
+    if ((st = op_smooth(c, l, c->opt.nu1, s, MG_KERNEL_PRESMOOTH))) return st;
+  }
   if ((st = op_residual(c, l, s, MG_KERNEL_PRESMOOTH))) return st;
   if ((st = op_restrict(c, l, s, MG_KERNEL_PRESMOOTH))) return st;
   if ((st = vcycle_rec(c, l + 1, true, s))) return st;

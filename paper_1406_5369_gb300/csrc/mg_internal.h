@@ -109,6 +109,9 @@ bool z_ok(const Level &L);
 bool transfer_ok(const Level &F, const Level &C);
 cudaError_t z_sweep(const Level &L, const void *uin, void *uout, const void *f, int color, double omega,
                     cudaStream_t s);
+// two omega-Jacobi sweeps from u = 0 in one pass: uout = J(J(0)) = J(alpha f)
+// (f must be zero on the boundary; kJZ in stencil3d.cuh)
+cudaError_t z_jacobi_zero2(const Level &L, const void *f, void *uout, double omega, cudaStream_t s);
 cudaError_t z_residual(const Level &L, const void *u, const void *f, void *r, cudaStream_t s);
 cudaError_t z_restrict(const Level &F, const void *rf, const Level &C, void *fc, cudaStream_t s);
 cudaError_t z_prolong(const Level &C, const void *ec, const Level &F, void *uf, cudaStream_t s);

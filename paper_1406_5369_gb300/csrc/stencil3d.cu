@@ -120,6 +120,16 @@ cudaError_t z_sweep(const Level &L, const void *uin, void *uout, const void *f, 
   return e;
 }
 
+cudaError_t z_jacobi_zero2(const Level &L, const void *f, void *uout, double omega, cudaStream_t s) {
+  z3::Args3 a = stencil_args(L, omega);
+  a.u = f;  // staged in place of u; the kernel scales it by alpha (the first sweep from zero)
+  a.out = uout;
+  a.f = f;
+  cudaError_t e = cudaSuccess;
+  Z3_DISPATCH(L.dtype, e = (launch_stencil<T, z3::kJZ>(a, 1LL << 30, nullptr, s)));
+  return e;
+}
+
 cudaError_t z_residual(const Level &L, const void *u, const void *f, void *r, cudaStream_t s) {
   z3::Args3 a = stencil_args(L, 1.0);
   a.u = u;

@@ -104,7 +104,13 @@ __device__ __forceinline__ void take_problem(Args3 &a, const Args3 &p) {
   a.cdf = p.cdf; a.cxf = p.cxf; a.cyf = p.cyf; a.czf = p.czf; a.has_gamma = p.has_gamma;
 }
 
-enum { kJacobi = 0, kRB = 1, kResid = 2, kNorm = 3 };
+// kJZ: two omega-Jacobi sweeps from u = 0 in one pass. The first sweep of a
+// zero start gives alpha f at interior nodes and keeps the (zero) boundary,
+// so the pass stages f in place of u, scales every value by alpha as it is
+// read (the first sweep's rounding), and applies the second sweep to that.
+// Needs f = 0 on the boundary, as on every coarse level and on the inner
+// finest level of defect correction.
+enum { kJacobi = 0, kRB = 1, kResid = 2, kNorm = 3, kJZ = 4 };
 
 // The 16-byte pieces a thread stages for every plane, fixed for the whole
 // march: source address at plane 0, byte stride between planes, shared-memory
@@ -249,9 +255,20 @@ __global__ void __launch_bounds__(32 * kTY, MODE == kResid ? 2 : 3) k3_stencil(A
   C um[V], uc[V], up[V];
   cp_async_wait<kAhead - 1>();
   __syncthreads();
+  // kJZ: the staged "u" values are f; the first sweep's result is alpha f at
+  // interior nodes and zero on the boundary (bnd: the row or plane is a
+  // boundary one; boundary columns of the lane masked here)
+  auto first = [&](C (&v)[V], bool bnd) {
+    if (MODE == kJZ) {
+#pragma unroll
+      for (int q = 0; q < V; q++) v[q] = (bnd || cl + q == 0 || cl + q == n - 1) ? (C)0 : alpha * v[q];
+    }
+  };
   if (wact) {
     vld((const T *)(smem + own + (so_cur == 0 ? RB - kSlotB : so_cur - kSlotB)), um);
     vld((const T *)(smem + own + so_cur), uc);
+    first(um, z0 - 1 == 0);
+    first(uc, false);
   }
   for (int z = z0; z < z1; z++) {
     cp_async_wait<kAhead - 1>();  // planes up to z + 1 have landed (own copies)
@@ -264,6 +281,13 @@ __global__ void __launch_bounds__(32 * kTY, MODE == kResid ? 2 : 3) k3_stencil(A
       vld((const T *)(smem + below + so_cur), yn);
       vld((const T *)(smem + frw + so_cur), fc);
       if (lane == 0 || lane == 31) hx = sld<T>(smem + halo + so_cur);
+      first(up, z + 1 == n - 1);
+      first(ys, y - 1 == 0);
+      first(yn, y + 1 == n - 1);
+      if (MODE == kJZ) {
+        const int hc = lane == 0 ? cl - 1 : cl + V;
+        hx = (hc <= 0 || hc >= n - 1) ? (C)0 : alpha * hx;
+      }
     }
     // the slot of plane z + kAhead + 1 held plane z - 2
     pc.issue(smem + so_fill, z + kAhead + 1 <= z1);
@@ -279,7 +303,7 @@ __global__ void __launch_bounds__(32 * kTY, MODE == kResid ? 2 : 3) k3_stencil(A
       wv = q == 0 ? wl : uc[q - 1];
       ev = q == V - 1 ? er : uc[q + 1];
     };
-    if (MODE == kJacobi || MODE == kRB) {
+    if (MODE == kJacobi || MODE == kRB || MODE == kJZ) {
       auto relax = [&](int q) {
         C wv, ev;
         nbr(q, wv, ev);
@@ -287,7 +311,7 @@ __global__ void __launch_bounds__(32 * kTY, MODE == kResid ? 2 : 3) k3_stencil(A
         if (has_gamma) nv += gamma * uc[q];
         return nv;
       };
-      if (MODE == kJacobi) {
+      if (MODE == kJacobi || MODE == kJZ) {
 #pragma unroll
         for (int q = 0; q < V; q++) res[q] = relax(q);
       } else {
