@@ -520,19 +520,35 @@ mg_status fast_descend(mg_batch *b, std::vector<Item *> &F, bool zero0) {
     for (Item *it : F) it->flip ^= 1;
     return MG_OK;
   }
-  // 3D: zero the levels that start from zero, nu1 sweeps, residual, restriction
-  {
+  // 3D: levels that start from zero take their first two Jacobi sweeps in one
+  // pass that reads f only (kJZ); otherwise they are zeroed first. Then the
+  // (remaining) sweeps, residual, restriction.
+  const bool jz = o.smoother == MG_JACOBI && o.nu1 >= 2;
+  std::vector<Item *> Zs, Ns;
+  for (Item *it : F) ((it->l > 0 || zero0) ? Zs : Ns).push_back(it);
+  if (jz && !Zs.empty()) {
+    std::vector<z3::Args3> recs;
+    for (Item *it : Zs) {
+      Level &L = it->c->lv[it->l];
+      recs.push_back(d3::stencil_record(L, o.omega, L.f, L.u[L.cur ^ it->flip ^ 1], L.f));
+    }
+    const z3::Args3 *dev = push_list(b, recs);
+    if (!dev) return bfail(MG_ENOMEM, "batch descriptor area exhausted");
+    BLAUNCH("batched 3D Jacobi from zero", d3::z_jacobi_zero2_list(L0, dev, (int)recs.size(), s));
+    b->launches++;
+    for (Item *it : Zs) it->flip ^= 1;
+  } else {
     std::vector<BOp> zops;
-    for (Item *it : F)
-      if (it->l > 0 || zero0) {
-        BOp op = make_op(it->c->lv[it->l]);
-        op.cur ^= it->flip;
-        zops.push_back(op);
-      }
+    for (Item *it : Zs) {
+      BOp op = make_op(it->c->lv[it->l]);
+      op.cur ^= it->flip;
+      zops.push_back(op);
+    }
     if (!zops.empty()) BLAUNCH("batched zero", launch_group_op(3, zops, b, 3, L0.dtype, false, 0, 0, 0.0));
   }
-  auto sweeps = [&](int nu) -> mg_status {
+  auto sweeps = [&](std::vector<Item *> &F, int nu) -> mg_status {
     for (int k = 0; k < nu; k++) {
+      if (F.empty()) break;
       std::vector<z3::Args3> recs;
       for (Item *it : F) {
         Level &L = it->c->lv[it->l];
@@ -554,7 +570,12 @@ mg_status fast_descend(mg_batch *b, std::vector<Item *> &F, bool zero0) {
     return MG_OK;
   };
   mg_status st;
-  if ((st = sweeps(o.nu1))) return st;
+  if (jz) {
+    if ((st = sweeps(Zs, o.nu1 - 2))) return st;
+    if ((st = sweeps(Ns, o.nu1))) return st;
+  } else {
+    if ((st = sweeps(F, o.nu1))) return st;
+  }
   std::vector<z3::Args3> rrec;
   std::vector<z3::ArgsT3> xrec;
   for (Item *it : F) {

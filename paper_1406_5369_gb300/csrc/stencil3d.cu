@@ -289,6 +289,13 @@ cudaError_t z_sweep_list(const Level &L, const z3::Args3 *list, int count, int c
   return e;
 }
 
+cudaError_t z_jacobi_zero2_list(const Level &L, const z3::Args3 *list, int count, cudaStream_t s) {
+  z3::Args3 a = stencil_args(L, 1.0);
+  cudaError_t e = cudaSuccess;
+  Z3_DISPATCH(L.dtype, e = (launch_stencil<T, z3::kJZ>(a, 1LL << 30, nullptr, s, list, count)));
+  return e;
+}
+
 cudaError_t z_residual_list(const Level &L, const z3::Args3 *list, int count, cudaStream_t s) {
   z3::Args3 a = stencil_args(L, 1.0);
   cudaError_t e = cudaSuccess;

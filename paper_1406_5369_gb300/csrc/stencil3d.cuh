@@ -835,6 +835,8 @@ __global__ void __launch_bounds__(32 * kDCWarps) k3_dcx(ArgsDC3 a, const ArgsDC3
 namespace d3 {
 z3::Args3 stencil_record(const Level &L, double omega, const void *u, void *out, const void *f);
 cudaError_t z_sweep_list(const Level &L, const z3::Args3 *list, int count, int color, cudaStream_t s);
+// kJZ over `count` problems (records as for z_sweep_list, u = f): two Jacobi sweeps from zero.
+cudaError_t z_jacobi_zero2_list(const Level &L, const z3::Args3 *list, int count, cudaStream_t s);
 cudaError_t z_residual_list(const Level &L, const z3::Args3 *list, int count, cudaStream_t s);
 cudaError_t z_transfer_list(bool restrict_, const Level &F, const Level &C, const z3::ArgsT3 *list, int count,
                             cudaStream_t s);
