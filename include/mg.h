@@ -79,8 +79,13 @@ typedef struct { int kind; const double *dirichlet_values; } mg_boundary;
 /* Layer-3 parameters (Sec. 2.3 mgparameter) plus implementation choices.
  * smoother, omega       : smoother and its relaxation weight
  * nu1, nu2              : pre- and post-smoothing sweeps (0..8)
- * coarsest_n            : nodes per dimension of the coarsest grid; 3 (one
- *                         unknown, solved exactly) is the only value accepted
+ * coarsest_n            : nodes per dimension of the coarsest grid: 3 (one
+ *                         unknown), 5 or 9 ((coarsest_n-2)^dim unknowns);
+ *                         n >= coarsest_n. The coarsest grid is solved
+ *                         exactly in FP64; for 5 and 9 mg_create forms the
+ *                         inverse of its operator (Gauss-Jordan, N x N FP64
+ *                         in the arena) and each solve applies it to the
+ *                         residual. MG_EINVAL for any other value
  * maxit                 : V-cycles (outer steps for *_DC) allowed in mg_solve
  * precision             : see mg_precision
  * stream                : cudaStream_t for every launch, NULL = default stream
@@ -197,7 +202,10 @@ mg_status mg_restrict(mg_ctx *ctx, int level);
  * Sec. 2.4 interpolatecorr, ToFine). MG_EINVAL on the coarsest level. */
 mg_status mg_prolongate(mg_ctx *ctx, int level);
 
-/* Exact solve on the coarsest level, in FP64 (Algorithm 1, coarsest level). */
+/* Exact solve on the coarsest level, in FP64 (Algorithm 1, coarsest level):
+ * u += A^{-1} (f - A u) over its interior unknowns, so the result does not
+ * depend on the starting u; A^{-1} is 1/diag for a 3^dim grid and the dense
+ * inverse formed at creation for 5^dim and 9^dim grids. */
 mg_status mg_coarse_solve(mg_ctx *ctx);
 
 /* One V(nu1,nu2)-cycle on the finest level (Algorithm 1; Sec. 2.4 VCycle).

@@ -60,6 +60,16 @@ size_t coarse_args(const Level *lv, int first, int nl, bool zero_top, int smooth
   }
   a.off_tmp = (int)elems;
   elems += (size_t)T.n * T.n * (T.dim == 3 ? T.n : 1);
+  const Level &Z = lv[nl - 1];
+  if (Z.dense) {
+    // N FP64 slots: 2N elements cover them for float cycles, at an even
+    // element offset so that they are 8-byte aligned
+    size_t m = (size_t)Z.n - 2, N = Z.dim == 3 ? m * m * m : m * m;
+    elems = (elems + 1) & ~(size_t)1;
+    a.dense = Z.dense;
+    a.off_rd = (int)elems;
+    elems += 2 * N;
+  }
   a.total = (int)elems;
   a.f_top = T.f;
   a.u_top = T.u[T.cur];

@@ -44,6 +44,11 @@ struct CoarseArgs {
   float inv_h2f[kMaxLev];
   float cf[3];
   float omegaf;
+  // coarsest grid of 5^dim or 9^dim nodes: FP64 inverse of its operator
+  // (global, N x N) and the element offset of N FP64 residual slots in
+  // shared memory; NULL for a 3^dim coarsest grid
+  const double *dense;
+  int off_rd;
 };
 
 // Element i of a global field of type dtype, in the cycle's compute type C
@@ -242,33 +247,61 @@ __device__ __forceinline__ void coarse_cycle_body(const CoarseArgs &a) {
     });
     __syncthreads();
   }
-  // coarsest: 3^dim grid, one unknown, solved exactly in FP64
-  if (threadIdx.x == 0) {
+  // coarsest level, solved exactly in FP64: the residual of the coarsest
+  // operator at its interior nodes, then one unknown (3^dim) divided by the
+  // diagonal or u += A^{-1} r with the dense inverse
+  {
     const Lev<C> Z = level<DIM, VAR, C>(a, sm, a.nlev - 1);
-    int p = DIM == 3 ? 13 : 4;
-    double ih2 = a.inv_h2[a.nlev - 1];
-    double dg, acc = 0.0;
-    int sy = 3, sz = 9;
-    double u0 = (double)Z.u[p];
-    if (!VAR) {
-      double d = a.c[0] + a.c[1] + (DIM == 3 ? a.c[2] : 0.0);
-      acc = a.c[0] * ((u0 - (double)Z.u[p - 1]) + (u0 - (double)Z.u[p + 1])) +
-            a.c[1] * ((u0 - (double)Z.u[p - sy]) + (u0 - (double)Z.u[p + sy]));
-      if (DIM == 3) acc += a.c[2] * ((u0 - (double)Z.u[p - sz]) + (u0 - (double)Z.u[p + sz]));
-      dg = 2.0 * d * ih2;
-    } else {
-      double kxp = Z.kx[p], kxm = Z.kx[p - 1], kyp = Z.ky[p], kym = Z.ky[p - sy];
-      acc = kxp * (u0 - (double)Z.u[p + 1]) + kxm * (u0 - (double)Z.u[p - 1]) + kyp * (u0 - (double)Z.u[p + sy]) +
-            kym * (u0 - (double)Z.u[p - sy]);
-      double d = kxp + kxm + kyp + kym;
-      if (DIM == 3) {
-        double kzp = Z.kz[p], kzm = Z.kz[p - sz];
-        acc += kzp * (u0 - (double)Z.u[p + sz]) + kzm * (u0 - (double)Z.u[p - sz]);
-        d += kzp + kzm;
+    const double ih2 = a.inv_h2[a.nlev - 1];
+    const int nz = Z.n, sy = nz, sz = nz * nz;
+    // (r_p, diag_p) in FP64 from the stored (C) values
+    auto resid = [&](int p, double &dg) {
+      double acc;
+      const double u0 = (double)Z.u[p];
+      if (!VAR) {
+        const double d = a.c[0] + a.c[1] + (DIM == 3 ? a.c[2] : 0.0);
+        acc = a.c[0] * ((u0 - (double)Z.u[p - 1]) + (u0 - (double)Z.u[p + 1])) +
+              a.c[1] * ((u0 - (double)Z.u[p - sy]) + (u0 - (double)Z.u[p + sy]));
+        if (DIM == 3) acc += a.c[2] * ((u0 - (double)Z.u[p - sz]) + (u0 - (double)Z.u[p + sz]));
+        dg = 2.0 * d * ih2;
+      } else {
+        const double kxp = Z.kx[p], kxm = Z.kx[p - 1], kyp = Z.ky[p], kym = Z.ky[p - sy];
+        acc = kxp * (u0 - (double)Z.u[p + 1]) + kxm * (u0 - (double)Z.u[p - 1]) + kyp * (u0 - (double)Z.u[p + sy]) +
+              kym * (u0 - (double)Z.u[p - sy]);
+        double d = kxp + kxm + kyp + kym;
+        if (DIM == 3) {
+          const double kzp = Z.kz[p], kzm = Z.kz[p - sz];
+          acc += kzp * (u0 - (double)Z.u[p + sz]) + kzm * (u0 - (double)Z.u[p - sz]);
+          d += kzp + kzm;
+        }
+        dg = d * ih2;
       }
-      dg = d * ih2;
+      return (double)Z.f[p] - acc * ih2;
+    };
+    if (!a.dense) {
+      if (threadIdx.x == 0) {
+        const int p = DIM == 3 ? 13 : 4;
+        double dg;
+        const double r = resid(p, dg);
+        Z.u[p] = (C)((double)Z.u[p] + r / dg);
+      }
+    } else {
+      double *rd = (double *)(sm + a.off_rd);
+      const int m = nz - 2, N = DIM == 3 ? m * m * m : m * m;
+      for (int t = threadIdx.x; t < N; t += kThreads) {
+        int i, j, k;
+        double dg;
+        rd[t] = resid(inode<DIM>(t, nz, i, j, k), dg);
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < N; t += kThreads) {
+        double acc = 0.0;
+        for (int q = 0; q < N; q++) acc += a.dense[(long long)q * N + t] * rd[q];
+        int i, j, k;
+        const int p = inode<DIM>(t, nz, i, j, k);
+        Z.u[p] = (C)((double)Z.u[p] + acc);
+      }
     }
-    Z.u[p] = (C)(u0 + ((double)Z.f[p] - acc * ih2) / dg);
   }
   __syncthreads();
   // ascend: interpolation and correction, postsmoothing

@@ -308,6 +308,89 @@ __global__ void k_coarse3(double *u, const double *f, Geo g, Sten<double> s) {
   u[p] = u[p] + (f[p] - Au) / dg;
 }
 
+// Coarsest grids of 5^dim or 9^dim nodes are solved directly: the FP64
+// inverse of the operator restricted to the interior unknowns is formed once
+// (k_dense_inverse) and applied to the residual, u += A^{-1} (f - A u), so a
+// nonzero start and Dirichlet values are handled like the 3^dim case.
+
+// Interior node t of the coarsest level, lexicographic order (x fastest).
+template <int DIM> __device__ __forceinline__ long long coarse_node(int t, const Geo &g) {
+  const int m = g.n - 2;
+  const int i = 1 + t % m, r = t / m;
+  const int j = 1 + (DIM == 3 ? r % m : r), k = DIM == 3 ? 1 + r / m : 0;
+  return (long long)k * g.sz + (long long)j * g.sy + i;
+}
+
+// One block. Assembles the interior matrix A (row t: diag at t, -k_f/h^2 at
+// each interior neighbour; neighbours on the boundary only enter the
+// diagonal) into `a` and inverts it in place by Gauss-Jordan elimination
+// without pivoting, which is stable for a symmetric positive definite A.
+// Step k divides row k by the pivot (1/a_kk on the diagonal) and subtracts
+// a_ik times the new row k from every other row i (-a_ik/a_kk in column k).
+template <int DIM, bool VAR>
+__global__ void __launch_bounds__(1024) k_dense_inverse(double *a, Geo g, Sten<double> s) {
+  __shared__ double colk[kDenseMax];
+  __shared__ double rpiv;
+  const int m = g.n - 2, N = DIM == 3 ? m * m * m : m * m;
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) a[e] = 0.0;
+  __syncthreads();
+  for (int t = threadIdx.x; t < N; t += blockDim.x) {
+    const long long p = coarse_node<DIM>(t, g);
+    const int i = t % m, j = (t / m) % m, k = DIM == 3 ? t / (m * m) : 0;
+    const int pos[3] = {i, j, k};
+    const long long gs[3] = {1, g.sy, g.sz};
+    const int ts[3] = {1, m, m * m};
+    const double cc[3] = {s.c0, s.c1, s.c2};
+    const double *kf[3] = {s.kf0, s.kf1, s.kf2};
+    double diag = 0.0;
+    for (int d = 0; d < DIM; d++) {
+      const double kp = VAR ? kf[d][p] : cc[d], km = VAR ? kf[d][p - gs[d]] : cc[d];
+      diag += kp + km;
+      if (pos[d] + 1 < m) a[(long long)t * N + t + ts[d]] = -kp * s.inv_h2;
+      if (pos[d] > 0) a[(long long)t * N + t - ts[d]] = -km * s.inv_h2;
+    }
+    a[(long long)t * N + t] = diag * s.inv_h2;
+  }
+  __syncthreads();
+  for (int k = 0; k < N; k++) {
+    if (threadIdx.x == 0) rpiv = 1.0 / a[(long long)k * N + k];
+    for (int i = threadIdx.x; i < N; i += blockDim.x) colk[i] = a[(long long)i * N + k];
+    __syncthreads();
+    for (int j = threadIdx.x; j < N; j += blockDim.x)
+      a[(long long)k * N + j] = (j == k ? 1.0 : a[(long long)k * N + j]) * rpiv;
+    __syncthreads();
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+      const int i = e / N, j = e % N;
+      if (i == k) continue;
+      a[e] = (j == k ? 0.0 : a[e]) - colk[i] * a[(long long)k * N + j];
+    }
+    __syncthreads();
+  }
+}
+
+// One block: r = f - A u at the N interior nodes (shared memory), then
+// u_t += sum_j (A^{-1})_{jt} r_j (A^{-1} is symmetric; reading its column t
+// keeps consecutive threads on consecutive addresses).
+template <int DIM, bool VAR>
+__global__ void __launch_bounds__(352) k_coarse_dense(double *u, const double *f, Geo g, Sten<double> s,
+                                                      const double *ainv) {
+  __shared__ double r[kDenseMax];
+  const int m = g.n - 2, N = DIM == 3 ? m * m * m : m * m;
+  for (int t = threadIdx.x; t < N; t += blockDim.x) {
+    const long long p = coarse_node<DIM>(t, g);
+    double Au, dg;
+    apply_at<DIM, VAR>(u, p, g, s, Au, dg);
+    r[t] = f[p] - Au;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < N; t += blockDim.x) {
+    double acc = 0.0;
+    for (int j = 0; j < N; j++) acc += ainv[(long long)j * N + t] * r[j];
+    const long long p = coarse_node<DIM>(t, g);
+    u[p] += acc;
+  }
+}
+
 // ---------------------------------------------------------------- defect correction
 
 // d_I = f_O - A_O u_O (FP64 arithmetic, cast to the inner storage type),

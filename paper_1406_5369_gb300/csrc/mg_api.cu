@@ -148,7 +148,9 @@ mg_status check_args(int dim, int n, const mg_options *opt) {
   if (!(opt->omega > 0.0 && opt->omega < 2.0)) return fail(MG_EINVAL, "omega must lie in (0, 2)");
   if (opt->nu1 < 0 || opt->nu2 < 0 || opt->nu1 > 8 || opt->nu2 > 8) return fail(MG_EINVAL, "nu1, nu2 must lie in 0..8");
   if (opt->nu1 + opt->nu2 == 0) return fail(MG_EINVAL, "nu1 + nu2 must be positive");
-  if (opt->coarsest_n != 3) return fail(MG_EINVAL, "coarsest_n must be 3");
+  if (opt->coarsest_n != 3 && opt->coarsest_n != 5 && opt->coarsest_n != 9)
+    return fail(MG_EINVAL, "coarsest_n must be 3, 5 or 9 (got %d)", opt->coarsest_n);
+  if (n < opt->coarsest_n) return fail(MG_EINVAL, "n (%d) is below coarsest_n (%d)", n, opt->coarsest_n);
   if (opt->maxit < 0) return fail(MG_EINVAL, "maxit must be >= 0");
   if (opt->inner_cycles < 0 || opt->inner_cycles > 8) return fail(MG_EINVAL, "inner_cycles must lie in 0..8 (0 = 1)");
   if (opt->precision != MG_FP64 && opt->precision != MG_FP32_DC && opt->precision != MG_BF16_DC)
@@ -160,11 +162,12 @@ mg_status check_args(int dim, int n, const mg_options *opt) {
   return MG_OK;
 }
 
-int level_count(int n) {
+// Levels n, (n-1)/2+1, ..., nc (both of the form 2^m+1, nc <= n).
+int level_count(int n, int nc) {
   int L = 0;
-  for (int nn = n; nn >= 3; nn = (nn - 1) / 2 + 1) {
+  for (int nn = n; nn >= nc; nn = (nn - 1) / 2 + 1) {
     L++;
-    if (nn == 3) break;
+    if (nn == nc) break;
   }
   return L;
 }
@@ -206,6 +209,13 @@ size_t layout(mg_ctx *c, char *base) {
     init_level(c->lv[l], c->dim, nn, dt, cc);
     take_level(c->lv[l], b, c->variable);
     nn = (nn - 1) / 2 + 1;
+  }
+  {
+    Level &Z = c->lv[c->nl - 1];
+    if (Z.n > 3) {
+      size_t m = (size_t)Z.n - 2, N = c->dim == 3 ? m * m * m : m * m;
+      Z.dense = (double *)b.take(N * N * sizeof(double));
+    }
   }
   if (c->dc) {
     init_level(c->outer, c->dim, c->n, mg::F64, cc);
@@ -307,7 +317,8 @@ mg_status op_prolong(mg_ctx *c, int l, cudaStream_t s, int kind = MG_KERNEL_OTHE
 
 mg_status op_coarse(mg_ctx *c, cudaStream_t s, int kind = MG_KERNEL_OTHER) {
   Level &L = c->lv[c->nl - 1];
-  TLAUNCH(c, kind, c->nl - 1, s, DISPATCH(L, coarse3, L, L.u[L.cur], L.f, s));
+  if (L.dense) TLAUNCH(c, kind, c->nl - 1, s, DISPATCH(L, coarse_dense, L, L.u[L.cur], L.f, s));
+  else TLAUNCH(c, kind, c->nl - 1, s, DISPATCH(L, coarse3, L, L.u[L.cur], L.f, s));
   return MG_OK;
 }
 
@@ -608,7 +619,7 @@ size_t mg_workspace_bytes(int dim, int n, int variable_k, const mg_options *opt)
   memset(&tmp, 0, sizeof tmp);
   tmp.dim = dim;
   tmp.n = n;
-  tmp.nl = level_count(n);
+  tmp.nl = level_count(n, opt->coarsest_n);
   tmp.variable = variable_k != 0;
   tmp.opt = *opt;
   tmp.dc = opt->precision != MG_FP64;
@@ -637,7 +648,7 @@ mg_status mg_create(int dim, int n, const mg_const_stencil *stencil, const doubl
   if (!c) return fail(MG_ENOMEM, "host allocation of the context failed");
   c->dim = dim;
   c->n = n;
-  c->nl = level_count(n);
+  c->nl = level_count(n, opt->coarsest_n);
   c->variable = k != nullptr;
   c->opt = *opt;
   c->bc_zero = !(bc && bc->dirichlet_values);
@@ -681,6 +692,12 @@ mg_status mg_create(int dim, int n, const mg_const_stencil *stencil, const doubl
       c->launches += c->nl - 1;
     }
     CKC(cudaMemsetAsync(stage, 0, (size_t)K.count * 8, c->stream));
+  }
+  if (c->lv[c->nl - 1].dense) {
+    // the coarsest operator's inverse (after its faces, for variable k)
+    Level &Z = c->lv[c->nl - 1];
+    CKC(DISPATCH(Z, dense_inverse, Z, c->stream));
+    c->launches++;
   }
   if (bc && bc->dirichlet_values) {
     Level &U = user_level(c);

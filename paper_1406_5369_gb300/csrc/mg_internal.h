@@ -30,7 +30,14 @@ struct Level {
   double c[3];      // constant stencil coefficients
   double inv_h2;    // 1/h^2
   int cur;          // index of the live solution buffer
+  double *dense;    // coarsest level with more than one unknown: the FP64
+                    // inverse of its operator, N x N row-major over the N
+                    // interior nodes in lexicographic order (x fastest);
+                    // NULL on every other level and for a 3^dim coarsest grid
 };
+
+// Interior unknowns of the largest coarsest grid with a dense solve (9^3).
+constexpr int kDenseMax = 343;
 
 constexpr int kNormBlocks = 1024;
 constexpr int kMaxPartials = 16384;  // per-warp partial sums of the streaming norms
@@ -54,6 +61,8 @@ int pow2_stencil(const Level &L);
   cudaError_t norm_partials(const Level &L, const void *u, const void *f, double *partials,       \
                             int nblocks, cudaStream_t s);                                         \
   cudaError_t coarse3(const Level &L, void *u, const void *f, cudaStream_t s);                   \
+  cudaError_t dense_inverse(const Level &L, cudaStream_t s);                                     \
+  cudaError_t coarse_dense(const Level &L, void *u, const void *f, cudaStream_t s);              \
   cudaError_t dc_residual(const Level &O, const void *u, const void *f, const Level &I, void *d, \
                           double *partials, int nblocks, cudaStream_t s);                         \
   cudaError_t dc_update(const Level &O, void *u, const Level &I, const void *e, cudaStream_t s); \

@@ -110,6 +110,26 @@ cudaError_t coarse3(const Level &L, void *u, const void *f, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Dense coarsest grids (n - 2)^dim <= kDenseMax unknowns, FP64 only.
+static bool dense_ok(const Level &L) {
+  long long m = L.n - 2, N = kDim == 3 ? m * m * m : m * m;
+  return L.dtype == F64 && L.dense && L.n >= 5 && N <= kDenseMax;
+}
+
+cudaError_t dense_inverse(const Level &L, cudaStream_t s) {
+  if (!dense_ok(L)) return cudaErrorInvalidValue;
+  if (L.kf[0]) k_dense_inverse<kDim, true><<<1, 1024, 0, s>>>(L.dense, geo_of(L), sten_of<double>(L));
+  else k_dense_inverse<kDim, false><<<1, 1024, 0, s>>>(L.dense, geo_of(L), sten_of<double>(L));
+  return cudaGetLastError();
+}
+
+cudaError_t coarse_dense(const Level &L, void *u, const void *f, cudaStream_t s) {
+  if (!dense_ok(L)) return cudaErrorInvalidValue;
+  if (L.kf[0]) k_coarse_dense<kDim, true><<<1, 352, 0, s>>>((double *)u, (const double *)f, geo_of(L), sten_of<double>(L), L.dense);
+  else k_coarse_dense<kDim, false><<<1, 352, 0, s>>>((double *)u, (const double *)f, geo_of(L), sten_of<double>(L), L.dense);
+  return cudaGetLastError();
+}
+
 cudaError_t dc_residual(const Level &O, const void *u, const void *f, const Level &I, void *d, double *partials,
                         int nblocks, cudaStream_t s) {
   bool var = O.kf[0] != nullptr;

@@ -49,7 +49,7 @@ class Solver:
     def __init__(self, dim, n, *, stencil=(1.0, 1.0, 1.0), k=None, dirichlet=None,
                  smoother="rbgs", omega=1.0, nu1=2, nu2=1, maxit=50, precision="fp64",
                  fuse=True, use_graph=True, inner_cycles=1, exact_outer=True, tile_rows=0, tile_max_n=0,
-                 fuse_depth=0, stream=None, device="cuda"):
+                 fuse_depth=0, coarsest_n=3, stream=None, device="cuda"):
         import torch
         self._lib = C.load()
         self.dim, self.n = dim, n
@@ -58,6 +58,7 @@ class Solver:
         opt.smoother = _SMOOTHER[smoother]
         opt.omega = float(omega)
         opt.nu1, opt.nu2 = int(nu1), int(nu2)
+        opt.coarsest_n = int(coarsest_n)
         opt.maxit = int(maxit)
         opt.precision = _PRECISION[precision]
         opt.fuse = int(bool(fuse))

@@ -72,8 +72,13 @@ def test_invalid_arguments_are_rejected_before_any_device_work(lib):
     o.omega = 2.5
     assert lib.mg_create(2, 9, None, None, None, ctypes.byref(o), buf, 1 << 20, ctypes.byref(ctx)) == C.MG_EINVAL
     lib.mg_default_options(ctypes.byref(o))
-    o.coarsest_n = 5
+    o.coarsest_n = 7  # not of the form 2^m+1
     assert lib.mg_create(2, 9, None, None, None, ctypes.byref(o), buf, 1 << 20, ctypes.byref(ctx)) == C.MG_EINVAL
+    o.coarsest_n = 17  # above n
+    assert lib.mg_create(2, 9, None, None, None, ctypes.byref(o), buf, 1 << 20, ctypes.byref(ctx)) == C.MG_EINVAL
+    assert b"coarsest_n" in lib.mg_last_error()
+    o.coarsest_n = 33  # 2^m+1, but no dense solve of that size
+    assert lib.mg_workspace_bytes(2, 65, 0, ctypes.byref(o)) == 0
     lib.mg_default_options(ctypes.byref(o))
     assert lib.mg_create(2, 9, None, None, None, ctypes.byref(o), buf, 16, ctypes.byref(ctx)) == C.MG_ENOMEM
     assert lib.mg_create(2, 9, None, None, None, ctypes.byref(o), None, 1 << 20, ctypes.byref(ctx)) == C.MG_EINVAL
@@ -100,3 +105,28 @@ def test_product_path_does_not_reach_the_oracle():
                 txt = open(os.path.join(dirpath, fn)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle\b", txt, flags=re.M), fn
                 assert "mg_oracle" not in txt and "liboracle" not in txt, fn
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_dense_coarsest_grid_adds_its_inverse_to_the_workspace(lib, dim):
+    # coarsest_n 5 or 9: the hierarchy stops at that size and the arena holds
+    # the FP64 inverse of the coarsest operator, N x N for N = (nc-2)^dim
+    from paper_1406_5369_gb300 import _capi as C
+    o = C.mg_options()
+    lib.mg_default_options(ctypes.byref(o))
+    n = 33 if dim == 3 else 65
+
+    def a256(b):  # every arena buffer starts 256-byte aligned
+        return -(-b // 256) * 256
+
+    def fields(m):  # u[2], f, r of an m^dim FP64 level, 128-byte rows
+        pitch = -(-m // 16) * 16
+        return 4 * a256(pitch * m ** (dim - 1) * 8)
+
+    base = lib.mg_workspace_bytes(dim, n, 0, ctypes.byref(o))
+    for nc, dropped in [(5, [3]), (9, [5, 3])]:
+        o.coarsest_n = nc
+        got = lib.mg_workspace_bytes(dim, n, 0, ctypes.byref(o))
+        N = (nc - 2) ** dim
+        want = base - sum(fields(m) for m in dropped) + a256(N * N * 8)
+        assert got == want, (nc, got, want)
