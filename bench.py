@@ -405,10 +405,98 @@ def run_reference(args):
         "data": "synthetic", "config": dict(WORKLOAD, parallelism="1 host core"),
         "cpu_baseline": {"value": 1.0 / t, "unit": "solves/s", "cores": 1, "kind": "oracle",
                          "sample": "per step: 1 FP64 oracle V(2,1) cycle + 1 residual norm on the full "
-                                   "8193^2 grid, extrapolated to the 10 cycles of the solve"},
+                                   "8193^2 grid, extrapolated to the 9 cycles of the solve"},
         "e2e": {"value": 1.0 / t, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(rec), flush=True)
+
+
+# Oracle baselines of the other configurations (serial, one host core; each
+# bounded to some 10-30 s of CPU work).
+
+def cpu_baseline_c1():
+    """The whole 129^2 workload: 10 FP64 oracle V(2,1) cycles + norms."""
+    import synth
+    import oracle
+    H = oracle.Hierarchy(2, 129, smoother=oracle.RBGS, omega=1.0, nu1=2, nu2=1)
+    H.set_rhs(synth.sine_rhs(2, 129))
+    t0 = time.perf_counter()
+    H.solve(0.0, 10)
+    t = time.perf_counter() - t0
+    return {"value": 10 / t, "unit": "V-cycles/s", "cores": 1, "kind": "oracle",
+            "sample": "the whole workload: 10 oracle V(2,1) cycles with their residual norms on 129^2"}
+
+
+def cpu_baseline_c3(cycles_to_tol):
+    """One FP64 oracle Jacobi V(2,2) cycle + one norm on 513^3, extrapolated."""
+    import synth
+    import oracle
+    H = oracle.Hierarchy(3, 513, smoother=oracle.JACOBI, omega=6.0 / 7.0, nu1=2, nu2=2)
+    H.set_rhs(synth.normal_rhs(3, 513, 0x5EED0003))
+    t0 = time.perf_counter()
+    H.residual_norm()
+    t_norm = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    H.vcycle()
+    t_cyc = time.perf_counter() - t0
+    t = t_norm + cycles_to_tol * (t_cyc + t_norm)
+    return {"value": 1.0 / t, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"1 FP64 oracle Jacobi V(2,2) cycle ({t_cyc:.1f} s) + 1 residual norm ({t_norm:.1f} s) on the "
+                      f"full 513^3 grid, extrapolated to the {cycles_to_tol} FP64 cycles of the solve to 1e-10"}
+
+
+def cpu_baseline_c4(ms_, seed, budget_s=25.0):
+    """Stratified sample of the batch: the first problem of each size, solved by
+    the oracle (FP64 V(2,1) cycles to 1e-8), extrapolated by the size counts."""
+    import numpy as np
+    import synth
+    import oracle
+    P = len(ms_)
+    per_m, t_all = {}, 0.0
+    for m in sorted(set(int(x) for x in ms_)):
+        p = int(np.nonzero(ms_ == m)[0][0])
+        n = (1 << m) + 1
+        H = oracle.Hierarchy(2, n, knode=synth.lognormal_k(2, n, seed ^ p ^ 0x10000), smoother=oracle.RBGS,
+                             omega=1.0, nu1=2, nu2=1)
+        H.set_rhs(synth.uniform_rhs(2, n, seed ^ p))
+        t0 = time.perf_counter()
+        rho = H.solve(1e-8, 60)
+        dt = time.perf_counter() - t0
+        per_m[m] = {"s": dt, "cycles": len(rho) - 1}
+        t_all += dt
+        if t_all > budget_s:
+            break
+    est = sum(per_m[m]["s"] * int((ms_ == m).sum()) for m in per_m)
+    done = sum(int((ms_ == m).sum()) for m in per_m)
+    return {"value": done / est, "unit": "problems/s", "cores": 1, "kind": "oracle",
+            "sample": f"one problem per size m in {sorted(per_m)} solved by the oracle (FP64 RBGS V(2,1) to 1e-8), "
+                      f"times weighted by the {done} of {P} problems of those sizes",
+            "per_size": {str(m): v for m, v in per_m.items()}}
+
+
+def cpu_baseline_c5(reqs, budget_s=25.0):
+    """Requests of the arrival stream solved one after another by the oracle,
+    in arrival order, until the time budget is spent."""
+    import synth
+    import oracle
+    done, t_all = 0, 0.0
+    for r in reqs[:200]:
+        dim, n = r["dim"], r["n"]
+        if dim == 2:
+            H = oracle.Hierarchy(2, n, smoother=oracle.RBGS, omega=1.0, nu1=2, nu2=1)
+        else:
+            H = oracle.Hierarchy(3, n, smoother=oracle.JACOBI, omega=6.0 / 7.0, nu1=2, nu2=2)
+        H.set_rhs(synth.uniform_rhs(dim, n, r["seed"]))
+        t0 = time.perf_counter()
+        H.solve(r["tol"], 100)
+        t_all += time.perf_counter() - t0
+        done += 1
+        del H
+        if t_all > budget_s:
+            break
+    return {"value": done / t_all, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"the first {done} requests of the same arrival stream, each solved alone by the oracle "
+                      "(FP64, 2D RBGS V(2,1) / 3D Jacobi V(2,2)) to its tolerance, one after another"}
 
 
 # ------------------------------------------------------------------ other configurations
@@ -461,10 +549,11 @@ def run_c1(args):
     h = 1.0 / (n - 1)
     ch = (math.pi * h / 2) ** 2 / math.sin(math.pi * h / 2) ** 2
     err = float(np.max(np.abs(u - synth.sine_solution(2, n))))
+    extra = {} if args.no_cpu_baseline else {"cpu_baseline": cpu_baseline_c1()}
     _line(METRIC, 10 / (ms / 1e3), "V-cycles/s (10 cycles + norms per step, launch-bound)", True, ms, args,
           {"workload": "2D Poisson 129^2, f = 2 pi^2 sin(pi x) sin(pi y), FP64 V(2,1) RBGS omega=1, 7 levels, "
                        "10 cycles from u0 = 0"}, "f64",
-          rho_history=[float(x) for x in hist], max_error_vs_exact=err, closed_form_error=ch - 1)
+          rho_history=[float(x) for x in hist], max_error_vs_exact=err, closed_form_error=ch - 1, **extra)
 
 
 def run_c3(args):
@@ -484,11 +573,12 @@ def run_c3(args):
         s.close()
         del s
     ms = res["bf16_dc"]["time_to_tol_s"] * 1e3
+    extra = {} if args.no_cpu_baseline else {"cpu_baseline": cpu_baseline_c3(res["fp64"]["steps"])}
     _line(METRIC, 1e3 / ms, "solves/s (to 1e-10 rel. residual; 1/time-to-1e-10)", True, ms, args,
           {"workload": "3D Poisson 513^3, f ~ N(0,1) (seed 0x5EED0003), Jacobi omega=6/7 V(2,2), full weighting, "
                        "trilinear; BF16-stored FP32 inner cycles in FP64 defect correction to 1e-10",
            "inner_cycles": best["inner_cycles"]}, "bf16 storage / f32 inner / f64 outer",
-          forms=res, autotune=table)
+          forms=res, autotune=table, **extra)
 
 
 def run_c4(args):
@@ -531,13 +621,14 @@ def run_c4(args):
         if best_ms is None or dt < best_ms:
             best_inner, best_ms = inner, dt
         B.close()
+    extra = {} if args.no_cpu_baseline else {"cpu_baseline": cpu_baseline_c4(ms_, seed)}
     _line(METRIC, P / best_ms, "problems/s (batch of 4096 solved to 1e-8)", True, best_ms * 1e3, args,
           {"workload": f"{P} independent 2D variable-coefficient problems -div(k grad u) = f, sizes (2^m+1)^2, "
                        "m ~ U{5..10} (seed 0x5EED0004), k lognormal(0,1) per node, harmonic faces, f ~ U[-1,1]; "
                        "FP32 inner / FP64 outer defect correction to 1e-8; RBGS V(2,1); one mg_batch",
            "total_nodes": nodes, "setup_s": t_setup},
           "f32 inner / f64 outer", tuned_inner_cycles=best_inner, default_vs_tuned=timings,
-          note="inner_cycles is chosen by timing candidates 1..3 on the batch (autotuned vs default = 1)")
+          note="inner_cycles is chosen by timing candidates 1..3 on the batch (autotuned vs default = 1)", **extra)
 
 
 def run_c5(args):
@@ -556,6 +647,7 @@ def run_c5(args):
     with ClockSampler(0) as clk:
         done, stats = srv.run(reqs, max_wall=args.serve_seconds * 6 + 30)
     saturated = stats["unfinished"] > 0 or stats["solves_per_s"] < 0.9 * rate
+    extra = {} if args.no_cpu_baseline else {"cpu_baseline": cpu_baseline_c5(reqs)}
     _line(METRIC, stats["solves_per_s"], "solves/s (served; p50/p99 latency in fields)", True,
           1e3 * stats["wall_s"] / max(1, stats["steps"]), args,
           {"workload": f"serving: Poisson arrivals at {rate:g} req/s for {args.serve_seconds:g} s ({count} requests); "
@@ -565,7 +657,7 @@ def run_c5(args):
                        "hierarchies resident and pooled; same-level batching across requests"},
           "f32 (2D) / bf16-stored f32 (3D) inner, f64 outer", p50_ms=stats["p50_ms"], p99_ms=stats["p99_ms"],
           serving=stats,
-          saturated=saturated, clocks=clk.summary())
+          saturated=saturated, clocks=clk.summary(), **extra)
 
 
 # The paper's Table 2 (Poisson rows), ms per V(2,2) cycle on an NVIDIA GTX 680 (CUDA 5.5):
