@@ -5,16 +5,19 @@ Only tests/, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``paper_1406_5369_gb300``) never imports it, and it never imports the
 product path; the two share only the seeded input generators in ``synth``.
 
-The arithmetic lives in ``mg_oracle.c`` (plain C, FP64, natural loop order,
-built with ``-O2 -ffp-contract=off``); this module compiles it with gcc on
-first use and wraps it with ctypes. Arrays are numpy float64 of shape
+The arithmetic lives in ``mg_oracle.c`` (node-based grids) and ``cc_oracle.c``
+(cell-centred grids with Neumann or Dirichlet boundaries), plain C, FP64,
+natural loop order, built with ``-O2 -ffp-contract=off``; this module compiles
+them with gcc on first use and wraps them with ctypes. Arrays are numpy float64 of shape
 ``(n,)*dim`` with x fastest, as in ``synth``. Local Fourier analysis lives in
 ``oracle.lfa``.
 
 Parity status of each routine (what pins it is in tests/test_oracle_*.py):
 stencil apply, residual, RBGS, Jacobi, full weighting, prolongation, dense
 coarse solve, V-cycle, solve loop, defect correction (FP64 inner), face
-coefficients and their coarsening are all pinned. No routine is unpinned.
+coefficients and their coarsening are all pinned; so are the cell-centred
+operator, smoothers, restriction, constant interpolation, dense solve,
+V-cycle and solve loop (tests/test_oracle_cc.py). No routine is unpinned.
 """
 from __future__ import annotations
 
@@ -26,7 +29,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "mg_oracle.c")
+_SRCS = [os.path.join(_HERE, "mg_oracle.c"), os.path.join(_HERE, "cc_oracle.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -39,12 +42,12 @@ _D = ctypes.POINTER(ctypes.c_double)
 
 
 def build(force: bool = False) -> str:
-    """Compiles mg_oracle.c into oracle/_build/liboracle.so (gcc, FP64, no FMA)."""
+    """Compiles the C sources into oracle/_build/liboracle.so (gcc, FP64, no FMA)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(os.path.getmtime(x) for x in _SRCS):
         tmp = _SO + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-std=c11", "-shared", "-fPIC",
-                               _SRC, "-o", tmp, "-lm"])
+                               *_SRCS, "-o", tmp, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -79,6 +82,24 @@ def lib():
                 "or_residual_norm": (d, [vp]),
                 "or_solve": (i, [vp, d, i, _D]),
                 "or_dc_solve": (i, [vp, d, i, _D]),
+                "cc_apply": (None, [i, i, _D, d, i, _D, _D]),
+                "cc_diag": (None, [i, i, _D, d, i, _D]),
+                "cc_residual": (None, [i, i, _D, d, i, _D, _D, _D]),
+                "cc_smooth": (None, [i, i, _D, d, i, i, d, i, _D, _D]),
+                "cc_restrict": (None, [i, i, _D, _D]),
+                "cc_prolong_add": (None, [i, i, _D, _D]),
+                "cc_norm": (d, [i, i, _D]),
+                "cc_dense_solve": (i, [i, i, _D, d, i, _D, _D]),
+                "cc_create": (vp, [i, i, _D, d, i, i, i, d, i, i]),
+                "cc_destroy": (None, [vp]),
+                "cc_levels": (i, [vp]),
+                "cc_level_n": (i, [vp, i]),
+                "cc_set_rhs": (None, [vp, _D]),
+                "cc_set_u": (None, [vp, _D]),
+                "cc_get_u": (None, [vp, _D]),
+                "cc_vcycle": (None, [vp]),
+                "cc_residual_norm": (d, [vp]),
+                "cc_solve": (i, [vp, d, i, _D]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -272,4 +293,115 @@ class Hierarchy:
         """Defect correction with an FP64 inner V-cycle; rho[0..k]."""
         rho = np.zeros(maxit + 1)
         k = lib().or_dc_solve(self.h, float(tol), int(maxit), _p(rho))
+        return rho[:k + 1]
+
+
+# ---------------- cell-centred grids (cc_oracle.c) ----------------
+# Arrays are (n,)*dim over the cells, x fastest; bc is "neumann" or "dirichlet"
+# (homogeneous, on every face of the unit square/cube).
+
+def _bc(bc):
+    if bc not in ("neumann", "dirichlet"):
+        raise ValueError("bc must be 'neumann' or 'dirichlet'")
+    return 1 if bc == "neumann" else 0
+
+
+def cc_apply(u, c=None, sigma=0.0, bc="neumann"):
+    u = _grid(u)
+    out = np.empty_like(u)
+    lib().cc_apply(u.ndim, u.shape[0], _p(_c3(c)), float(sigma), _bc(bc), _p(u), _p(out))
+    return out
+
+
+def cc_diag(dim, n, c=None, sigma=0.0, bc="neumann"):
+    out = np.empty((n,) * dim)
+    lib().cc_diag(dim, n, _p(_c3(c)), float(sigma), _bc(bc), _p(out))
+    return out
+
+
+def cc_residual(u, f, c=None, sigma=0.0, bc="neumann"):
+    u, f = _grid(u), _grid(f)
+    out = np.empty_like(u)
+    lib().cc_residual(u.ndim, u.shape[0], _p(_c3(c)), float(sigma), _bc(bc), _p(u), _p(f), _p(out))
+    return out
+
+
+def cc_smooth(u, f, sweeps, smoother=RBGS, omega=1.0, c=None, sigma=0.0, bc="neumann"):
+    u = _grid(u).copy()
+    f = _grid(f)
+    lib().cc_smooth(u.ndim, u.shape[0], _p(_c3(c)), float(sigma), _bc(bc), int(smoother), float(omega),
+                    int(sweeps), _p(u), _p(f))
+    return u
+
+
+def cc_restrict(r):
+    r = _grid(r)
+    dim, nf = r.ndim, r.shape[0]
+    out = np.empty((nf // 2,) * dim)
+    lib().cc_restrict(dim, nf, _p(r), _p(out))
+    return out
+
+
+def cc_prolong_add(e, u):
+    e = _grid(e)
+    u = _grid(u).copy()
+    lib().cc_prolong_add(e.ndim, e.shape[0], _p(e), _p(u))
+    return u
+
+
+def cc_norm(r):
+    r = _grid(r)
+    return lib().cc_norm(r.ndim, r.shape[0], _p(r))
+
+
+def cc_dense_solve(f, c=None, sigma=0.0, bc="neumann"):
+    f = _grid(f)
+    u = np.zeros_like(f)
+    if lib().cc_dense_solve(f.ndim, f.shape[0], _p(_c3(c)), float(sigma), _bc(bc), _p(f), _p(u)) != 0:
+        raise RuntimeError("singular system")
+    return u
+
+
+class CCHierarchy:
+    """A cell-centred grid hierarchy n, n/2, ..., coarsest_n with V-cycle and solve loop."""
+
+    def __init__(self, dim, n, c=None, sigma=0.0, bc="neumann", coarsest_n=1, smoother=RBGS, omega=1.0,
+                 nu1=2, nu2=1):
+        self.dim, self.n = dim, n
+        self.h = lib().cc_create(dim, n, _p(_c3(c)), float(sigma), _bc(bc), coarsest_n, smoother, float(omega),
+                                 nu1, nu2)
+        if not self.h:
+            raise ValueError("invalid hierarchy parameters")
+        self.levels = lib().cc_levels(self.h)
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            lib().cc_destroy(h)
+            self.h = None
+
+    def level_n(self, l):
+        return lib().cc_level_n(self.h, l)
+
+    def set_rhs(self, f):
+        lib().cc_set_rhs(self.h, _p(_grid(f, self.dim)))
+
+    def set_u(self, u):
+        lib().cc_set_u(self.h, _p(_grid(u, self.dim)))
+
+    def get_u(self):
+        u = np.empty((self.n,) * self.dim)
+        lib().cc_get_u(self.h, _p(u))
+        return u
+
+    def vcycle(self):
+        lib().cc_vcycle(self.h)
+
+    def residual_norm(self):
+        return lib().cc_residual_norm(self.h)
+
+    def solve(self, tol, maxit):
+        """Returns the relative residual history rho[0..k] (rho[0] = 1)."""
+        rho = np.zeros(maxit + 1)
+        k = lib().cc_solve(self.h, float(tol), int(maxit), _p(rho))
         return rho[:k + 1]
