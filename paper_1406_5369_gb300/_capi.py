@@ -1,4 +1,5 @@
-"""ctypes declarations of the C ABI in include/mg.h (argument marshalling only).
+"""ctypes declarations of the C ABI in include/mg.h and include/mg_cc.h
+(argument marshalling only).
 
 Loading fails loudly if libmg.so has not been built: there is no fallback
 implementation of any operation in Python.
@@ -36,7 +37,16 @@ class mg_options(ctypes.Structure):
                 ("tile_rows", ctypes.c_int), ("tile_max_n", ctypes.c_int), ("fuse_depth", ctypes.c_int)]
 
 
-# name -> (restype, argtypes); every function declared in include/mg.h.
+class mg_cc_params(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("c", ctypes.c_double * 3),
+                ("sigma", ctypes.c_double), ("bc", ctypes.c_int), ("smoother", ctypes.c_int),
+                ("omega", ctypes.c_double), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
+                ("coarsest_n", ctypes.c_int), ("maxit", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+MG_CC_NEUMANN, MG_CC_DIRICHLET = 0, 1
+
+# name -> (restype, argtypes); every function declared in include/mg.h and include/mg_cc.h.
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _D = ctypes.c_double
@@ -77,6 +87,22 @@ SIGNATURES = {
     "mg_batch_launches": (ctypes.c_ulonglong, [_P]),
     "mg_batch_set_inner_cycles": (_I, [_P, _I]),
     "mg_last_error": (ctypes.c_char_p, []),
+    "mg_cc_default_params": (None, [ctypes.POINTER(mg_cc_params)]),
+    "mg_cc_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(mg_cc_params)]),
+    "mg_cc_create": (_I, [ctypes.POINTER(mg_cc_params), _P, ctypes.c_size_t, ctypes.POINTER(_P)]),
+    "mg_cc_destroy": (_I, [_P]),
+    "mg_cc_num_levels": (_I, [_P]),
+    "mg_cc_level_size": (_I, [_P, _I]),
+    "mg_cc_set_field": (_I, [_P, _I, _I, _P]),
+    "mg_cc_get_field": (_I, [_P, _I, _I, _P]),
+    "mg_cc_smooth": (_I, [_P, _I, _I]),
+    "mg_cc_residual": (_I, [_P, _I]),
+    "mg_cc_restrict": (_I, [_P, _I]),
+    "mg_cc_prolongate": (_I, [_P, _I]),
+    "mg_cc_coarse_solve": (_I, [_P]),
+    "mg_cc_vcycle": (_I, [_P]),
+    "mg_cc_residual_norm": (_I, [_P, _I, ctypes.POINTER(_D)]),
+    "mg_cc_solve": (_I, [_P, _D, ctypes.POINTER(_I), ctypes.POINTER(_D), _P]),
 }
 
 _lib = None

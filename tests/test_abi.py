@@ -130,3 +130,33 @@ def test_dense_coarsest_grid_adds_its_inverse_to_the_workspace(lib, dim):
         N = (nc - 2) ** dim
         want = base - sum(fields(m) for m in dropped) + a256(N * N * 8)
         assert got == want, (nc, got, want)
+
+
+def test_cell_grid_params_are_validated_without_a_device(lib):
+    from paper_1406_5369_gb300 import _capi as C
+    p = C.mg_cc_params()
+    lib.mg_cc_default_params(ctypes.byref(p))
+    assert (p.dim, p.n, p.sigma, p.bc, p.coarsest_n) == (2, 2, 1.0, C.MG_CC_NEUMANN, 1)
+    p.n = 64
+    good = lib.mg_cc_workspace_bytes(ctypes.byref(p))
+    # levels 64..1: four FP64 fields each (rows padded to 16 doubles), the
+    # 1x1 coarsest inverse, norm partials and the norm slot, 256-byte aligned
+    a256 = lambda b: -(-b // 256) * 256
+    want = sum(4 * a256(-(-m // 16) * 16 * m * 8) for m in (64, 32, 16, 8, 4, 2, 1)) + a256(8) + a256(512 * 8) + 8
+    assert good == a256(want)
+    for field, bad in [("n", 48), ("n", 32768), ("dim", 4), ("sigma", -1.0), ("omega", 2.0), ("coarsest_n", 3),
+                       ("coarsest_n", 128), ("bc", 5), ("nu1", 9)]:
+        q = C.mg_cc_params()
+        ctypes.memmove(ctypes.byref(q), ctypes.byref(p), ctypes.sizeof(p))
+        setattr(q, field, bad)
+        assert lib.mg_cc_workspace_bytes(ctypes.byref(q)) == 0, (field, bad)
+    q = C.mg_cc_params()
+    ctypes.memmove(ctypes.byref(q), ctypes.byref(p), ctypes.sizeof(p))
+    q.sigma = 0.0  # singular with Neumann faces, fine with Dirichlet ones
+    assert lib.mg_cc_workspace_bytes(ctypes.byref(q)) == 0
+    assert b"Neumann" in lib.mg_last_error()
+    q.bc = C.MG_CC_DIRICHLET
+    assert lib.mg_cc_workspace_bytes(ctypes.byref(q)) == good
+    ctx = ctypes.c_void_p()
+    assert lib.mg_cc_create(ctypes.byref(p), ctypes.c_void_p(256), 16, ctypes.byref(ctx)) == C.MG_ENOMEM
+    assert lib.mg_cc_num_levels(None) == -1
