@@ -734,6 +734,62 @@ def run_table2(args):
                   "column / speedup; hardware and software differ, context only")
 
 
+def run_cc(args):
+    """Cell-centred grids (include/mg_cc.h) at the paper's cell-centred sizes, 4096^2 and 256^3
+    (Table 2 caption), V(2,2) with Jacobi omega 0.8 or RBGS, Neumann faces, sigma = 1, FP64."""
+    torch = _init_cuda()
+    import synth
+    from paper_1406_5369_gb300 import CCSolver
+    stream = torch.cuda.current_stream()
+    hbm, _ = peaks()
+    reps = max(3, args.steps)
+    rows = []
+    for dim, n in ((2, 4096), (3, 256)):
+        f = torch.from_numpy(2.0 * synth.uniform(0x5EED00CC, (n,) * dim) - 1.0).cuda()
+        for sm, om in (("jacobi", 0.8), ("rbgs", 1.0)):
+            s = CCSolver(dim, n, sigma=1.0, bc="neumann", smoother=sm, omega=om, nu1=2, nu2=2)
+            s.set_rhs(f)
+            s.set_solution(None)
+            r0 = s.residual_norm()
+            for _ in range(5):
+                s.vcycle()
+            red = r0 / s.residual_norm()
+            for _ in range(3):
+                s.vcycle()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(reps):
+                s.vcycle()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1) / reps
+            # operator model: V(2,2) moves 25 (2D) / 21 (3D) FP64 words per fine cell per cycle
+            gb = (25 if dim == 2 else 21) * n ** dim * 8 / 1e9
+            rows.append({"grid": f"{n}^{dim} cells", "smoother": sm, "omega": om, "ms_per_vcycle_f64": ms,
+                         "effective_gbs": gb / (ms / 1e3), "frac_of_measured_hbm": gb / (ms / 1e3) / hbm,
+                         "residual_reduction_5_cycles": red})
+            s.close()
+            del s
+    extra = {}
+    if not args.no_cpu_baseline:
+        import oracle
+        H = oracle.CCHierarchy(2, 4096, sigma=1.0, bc="neumann", smoother=oracle.JACOBI, omega=0.8, nu1=2, nu2=2)
+        H.set_rhs(2.0 * synth.uniform(0x5EED00CC, (4096, 4096)) - 1.0)
+        t0 = time.perf_counter()
+        H.vcycle()
+        t = time.perf_counter() - t0
+        extra["cpu_baseline"] = {"value": 1e3 * t, "unit": "ms per V(2,2) cycle", "cores": 1, "kind": "oracle",
+                                 "sample": "one oracle Jacobi V(2,2) cycle on the 4096^2 cell-centred grid"}
+    head = rows[0]
+    _line("ms per V(2,2) cycle (cell-centred grids)", head["ms_per_vcycle_f64"], "ms per V(2,2) cycle", False,
+          head["ms_per_vcycle_f64"], args,
+          {"workload": "cell-centred 4096^2 (2D) and 256^3 (3D) cells, sigma u - Laplace u = f, Neumann faces, "
+                       "sigma = 1, f ~ U[-1,1] (seed 0x5EED00CC), V(2,2) Jacobi omega=0.8 / RBGS, cell-centred "
+                       "restriction, constant interpolation, coarsening to 1 cell; value = 2D Jacobi"},
+          "f64", cc=rows, **extra)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -741,7 +797,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "table2"],
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "table2", "cc"],
                     help="c2 (default): the 8193^2 headline; others print their own line")
     ap.add_argument("--batch-problems", type=int, default=4096)
     ap.add_argument("--rate", type=float, default=2000.0)
@@ -752,7 +808,8 @@ def main():
     elif args.workload == "c2":
         run_gpu(args)
     else:
-        {"c1": run_c1, "c3": run_c3, "c4": run_c4, "c5": run_c5, "table2": run_table2}[args.workload](args)
+        {"c1": run_c1, "c3": run_c3, "c4": run_c4, "c5": run_c5, "table2": run_table2,
+         "cc": run_cc}[args.workload](args)
 
 
 if __name__ == "__main__":

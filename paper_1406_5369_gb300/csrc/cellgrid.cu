@@ -36,42 +36,41 @@ struct Geo {
   long long sy, sz;  // row and plane strides (elements)
 };
 
+// FP64 runs at 1/64 of the FP32 rate on this GPU, so the kernels are bound
+// by FP64 issue, not by memory: the operator is written to need few FP64
+// instructions per cell. A boundary face uses a ghost value (u_p for a
+// Neumann face, -u_p for a Dirichlet one), so every face is one subtraction
+// u_p - u_q (exactly 0 or 2 u_p at the boundary, as the operator defines),
+// and the smoothers multiply by omega / diag_p from a table instead of
+// dividing: diag_p depends only on which faces of the cell are boundary
+// faces, class a_d = [x_d == 0] + [x_d == n-1] per axis, 3^dim classes.
 struct Coef {
-  double c[3];
-  double sigma, ih2;  // ih2 = 1/h^2 = n^2 (exact: n is a power of two)
-  int neumann;
+  double k[3];        // c_d / h^2 = c_d n^2 (exact scaling: n is a power of two)
+  double sigma, ih2;  // ih2 = 1/h^2 = n^2
+  int neumann;        // ghost value u_p (Neumann) or -u_p (Dirichlet)
+  double wd[27];      // omega / diag by boundary class a_0 + 3 a_1 + 9 a_2
 };
 
-// (A u)_p and diag_p of cell (i, j, k) at index p (the operator of mg_cc.h).
+// (A u)_p of cell (i, j, k) at index p (the operator of mg_cc.h); cls gets
+// the cell's boundary class.
 template <int DIM>
 __device__ __forceinline__ double apply(const double *__restrict__ u, long long p, int i, int j, int k,
-                                        const Geo &g, const Coef &s, double &diag) {
-  const double u0 = u[p];
+                                        const Geo &g, const Coef &s, int &cls) {
+  const double u0 = u[p], gh = s.neumann ? u0 : -u0;
   const int x[3] = {i, j, k};
   const long long st[3] = {1, g.sy, g.sz};
-  double acc = 0.0, wsum = 0.0;
+  const int mul[3] = {1, 3, 9};
+  double acc = 0.0;
+  cls = 0;
 #pragma unroll
   for (int d = 0; d < DIM; d++) {
-    double fm, fp, wm, wp;
-    if (x[d] > 0) {
-      fm = u0 - u[p - st[d]];
-      wm = 1.0;
-    } else {
-      fm = s.neumann ? 0.0 : 2.0 * u0;
-      wm = s.neumann ? 0.0 : 2.0;
-    }
-    if (x[d] < g.n - 1) {
-      fp = u0 - u[p + st[d]];
-      wp = 1.0;
-    } else {
-      fp = s.neumann ? 0.0 : 2.0 * u0;
-      wp = s.neumann ? 0.0 : 2.0;
-    }
-    acc += s.c[d] * (fm + fp);
-    wsum += s.c[d] * (wm + wp);
+    const bool lo = x[d] == 0, hi = x[d] == g.n - 1;
+    const double um = lo ? gh : u[p - st[d]];
+    const double up = hi ? gh : u[p + st[d]];
+    acc += s.k[d] * ((u0 - um) + (u0 - up));
+    cls += mul[d] * ((int)lo + (int)hi);
   }
-  diag = s.sigma + wsum * s.ih2;
-  return s.sigma * u0 + acc * s.ih2;
+  return s.sigma * u0 + acc;
 }
 
 struct Cell {
@@ -93,25 +92,24 @@ template <int DIM> __device__ __forceinline__ Cell cell_of(const Geo &g, int i) 
 // Half-sweep of red-black Gauss-Seidel: thread t of a row takes the t-th
 // cell of the colour ((i + j + k) % 2 == color) in that row.
 template <int DIM>
-__global__ void k_rbgs_half(double *__restrict__ u, const double *__restrict__ f, Geo g, Coef s, double omega,
-                            int color) {
+__global__ void k_rbgs_half(double *__restrict__ u, const double *__restrict__ f, Geo g, Coef s, int color) {
   const int j = blockIdx.y, k = DIM == 3 ? (int)blockIdx.z : 0;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   Cell c = cell_of<DIM>(g, 2 * t + ((color + j + k) & 1));
   if (!c.ok) return;
-  double dg;
-  const double Au = apply<DIM>(u, c.p, c.i, c.j, c.k, g, s, dg);
-  u[c.p] = u[c.p] + omega * (f[c.p] - Au) / dg;
+  int cls;
+  const double Au = apply<DIM>(u, c.p, c.i, c.j, c.k, g, s, cls);
+  u[c.p] = u[c.p] + s.wd[cls] * (f[c.p] - Au);
 }
 
 template <int DIM>
 __global__ void k_jacobi(const double *__restrict__ uin, double *__restrict__ uout, const double *__restrict__ f,
-                         Geo g, Coef s, double omega) {
+                         Geo g, Coef s) {
   Cell c = cell_of<DIM>(g, blockIdx.x * blockDim.x + threadIdx.x);
   if (!c.ok) return;
-  double dg;
-  const double Au = apply<DIM>(uin, c.p, c.i, c.j, c.k, g, s, dg);
-  uout[c.p] = uin[c.p] + omega * (f[c.p] - Au) / dg;
+  int cls;
+  const double Au = apply<DIM>(uin, c.p, c.i, c.j, c.k, g, s, cls);
+  uout[c.p] = uin[c.p] + s.wd[cls] * (f[c.p] - Au);
 }
 
 template <int DIM>
@@ -119,8 +117,8 @@ __global__ void k_residual(const double *__restrict__ u, const double *__restric
                            Geo g, Coef s) {
   Cell c = cell_of<DIM>(g, blockIdx.x * blockDim.x + threadIdx.x);
   if (!c.ok) return;
-  double dg;
-  r[c.p] = f[c.p] - apply<DIM>(u, c.p, c.i, c.j, c.k, g, s, dg);
+  int cls;
+  r[c.p] = f[c.p] - apply<DIM>(u, c.p, c.i, c.j, c.k, g, s, cls);
 }
 
 // Coarse cell (I, J, K): mean of its 2^DIM fine cells (2I+a, 2J+b, 2K+e).
@@ -170,8 +168,8 @@ __global__ void k_norm_partials(const double *__restrict__ u, const double *__re
        t += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(t % n), j = (int)((t / n) % n), k = DIM == 3 ? (int)(t / (n * n)) : 0;
     const long long p = (long long)k * g.sz + (long long)j * g.sy + i;
-    double dg;
-    const double r = f[p] - apply<DIM>(u, p, i, j, k, g, s, dg);
+    int cls;
+    const double r = f[p] - apply<DIM>(u, p, i, j, k, g, s, cls);
     acc += r * r;
   }
   acc = block_sum(acc);
@@ -195,7 +193,8 @@ template <int DIM> __device__ __forceinline__ void coarse_cell(int t, int n, int
 // One block: assembles the coarsest operator over its N = n^DIM cells
 // (row t: diag_t, and -c_d/h^2 for each neighbour across an interior face)
 // and inverts it in place by Gauss-Jordan elimination without pivoting (A
-// is symmetric positive definite: sigma > 0 or Dirichlet faces).
+// is symmetric positive definite: sigma > 0 or Dirichlet faces). A
+// Dirichlet face adds 2 c_d/h^2 to the diagonal, a Neumann face nothing.
 template <int DIM>
 __global__ void k_dense_inverse(double *a, Geo g, Coef s) {
   __shared__ double colk[kCoarseMax];
@@ -210,19 +209,19 @@ __global__ void k_dense_inverse(double *a, Geo g, Coef s) {
     double w = 0.0;
     for (int d = 0; d < DIM; d++) {
       if (x[d] > 0) {
-        a[t * N + t - ts[d]] = -s.c[d] * s.ih2;
-        w += s.c[d];
+        a[t * N + t - ts[d]] = -s.k[d];
+        w += s.k[d];
       } else if (!s.neumann) {
-        w += 2.0 * s.c[d];
+        w += 2.0 * s.k[d];
       }
       if (x[d] < n - 1) {
-        a[t * N + t + ts[d]] = -s.c[d] * s.ih2;
-        w += s.c[d];
+        a[t * N + t + ts[d]] = -s.k[d];
+        w += s.k[d];
       } else if (!s.neumann) {
-        w += 2.0 * s.c[d];
+        w += 2.0 * s.k[d];
       }
     }
-    a[t * N + t] = s.sigma + w * s.ih2;
+    a[t * N + t] = s.sigma + w;
   }
   __syncthreads();
   for (int k = 0; k < N; k++) {
@@ -250,8 +249,8 @@ __global__ void k_coarse_solve(double *__restrict__ u, const double *__restrict_
     int i, j, k;
     coarse_cell<DIM>(t, n, i, j, k);
     const long long p = (long long)k * g.sz + (long long)j * g.sy + i;
-    double dg;
-    r[t] = f[p] - apply<DIM>(u, p, i, j, k, g, s, dg);
+    int cls;
+    r[t] = f[p] - apply<DIM>(u, p, i, j, k, g, s, cls);
   }
   __syncthreads();
   for (int t = threadIdx.x; t < N; t += blockDim.x) {
@@ -368,10 +367,29 @@ Geo geo_of(const Lev &L) { return Geo{L.n, (long long)L.pitch, L.plane}; }
 
 Coef coef_of(const mg_cc_ctx *c, const Lev &L) {
   Coef s;
-  for (int d = 0; d < 3; d++) s.c[d] = c->p.c[d];
+  memset(&s, 0, sizeof s);
   s.sigma = c->p.sigma;
   s.ih2 = (double)L.n * (double)L.n;
-  s.neumann = c->p.bc == MG_CC_NEUMANN;
+  for (int d = 0; d < 3; d++) s.k[d] = c->p.c[d] * s.ih2;
+  const bool neumann = c->p.bc == MG_CC_NEUMANN;
+  s.neumann = neumann;
+  // diag of each boundary class: per axis, a_d boundary faces (a_d = 2 only
+  // for a single cell) weigh 0 (Neumann) or 2 (Dirichlet), interior faces 1
+  const int dim = c->p.dim;
+  for (int cls = 0; cls < 27; cls++) {
+    int a[3] = {cls % 3, (cls / 3) % 3, cls / 9};
+    bool valid = true;
+    double w = 0.0;
+    for (int d = 0; d < 3; d++) {
+      if (d >= dim) {
+        valid = valid && a[d] == 0;
+        continue;
+      }
+      if (a[d] == 2 && L.n != 1) valid = false;
+      w += c->p.c[d] * ((2 - a[d]) + (neumann ? 0 : 2 * a[d]));
+    }
+    s.wd[cls] = valid ? c->p.omega / (s.sigma + w * s.ih2) : 0.0;
+  }
   return s;
 }
 
@@ -394,10 +412,9 @@ mg_status op_smooth(mg_cc_ctx *c, int l, int sweeps) {
   for (int it = 0; it < sweeps; it++) {
     if (c->p.smoother == MG_RBGS) {
       for (int color = 0; color < 2; color++)
-        DIMCALL(c->p.dim, k_rbgs_half, grid_of(L, (L.n + 1) / 2), kThreads, L.u[L.cur], L.f, g, s, c->p.omega,
-                color);
+        DIMCALL(c->p.dim, k_rbgs_half, grid_of(L, (L.n + 1) / 2), kThreads, L.u[L.cur], L.f, g, s, color);
     } else {
-      DIMCALL(c->p.dim, k_jacobi, grid_of(L, L.n), kThreads, L.u[L.cur], L.u[L.cur ^ 1], L.f, g, s, c->p.omega);
+      DIMCALL(c->p.dim, k_jacobi, grid_of(L, L.n), kThreads, L.u[L.cur], L.u[L.cur ^ 1], L.f, g, s);
       L.cur ^= 1;
     }
   }
