@@ -5,8 +5,9 @@ Only tests/, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``paper_1406_5369_gb300``) never imports it, and it never imports the
 product path; the two share only the seeded input generators in ``synth``.
 
-The arithmetic lives in ``mg_oracle.c`` (node-based grids) and ``cc_oracle.c``
-(cell-centred grids with Neumann or Dirichlet boundaries), plain C, FP64,
+The arithmetic lives in ``mg_oracle.c`` (node-based grids), ``cc_oracle.c``
+(cell-centred grids with Neumann or Dirichlet boundaries) and ``cd_oracle.c``
+(implicit Euler steps of complex diffusion on cell-centred grids), plain C, FP64,
 natural loop order, built with ``-O2 -ffp-contract=off``; this module compiles
 them with gcc on first use and wraps them with ctypes. Arrays are numpy float64 of shape
 ``(n,)*dim`` with x fastest, as in ``synth``. Local Fourier analysis lives in
@@ -17,7 +18,9 @@ stencil apply, residual, RBGS, Jacobi, full weighting, prolongation, dense
 coarse solve, V-cycle, solve loop, defect correction (FP64 inner), face
 coefficients and their coarsening are all pinned; so are the cell-centred
 operator, smoothers, restriction, constant interpolation, dense solve,
-V-cycle and solve loop (tests/test_oracle_cc.py). No routine is unpinned.
+V-cycle and solve loop (tests/test_oracle_cc.py), and the complex-diffusion
+diffusivity, face averaging and coarsening, operator, smoothers, transfers,
+V-cycle and time step (tests/test_oracle_cd.py). No routine is unpinned.
 """
 from __future__ import annotations
 
@@ -29,7 +32,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = [os.path.join(_HERE, "mg_oracle.c"), os.path.join(_HERE, "cc_oracle.c")]
+_SRCS = [os.path.join(_HERE, "mg_oracle.c"), os.path.join(_HERE, "cc_oracle.c"), os.path.join(_HERE, "cd_oracle.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -100,6 +103,24 @@ def lib():
                 "cc_vcycle": (None, [vp]),
                 "cc_residual_norm": (d, [vp]),
                 "cc_solve": (i, [vp, d, i, _D]),
+                "cd_diffusivity": (None, [i, _D, d, d, _D]),
+                "cd_faces": (None, [i, _D, _D, _D]),
+                "cd_coarsen_faces": (None, [i, _D, _D, _D, _D]),
+                "cd_apply": (None, [i, d, _D, _D, _D, _D]),
+                "cd_residual": (None, [i, d, _D, _D, _D, _D, _D]),
+                "cd_smooth": (None, [i, d, _D, _D, i, d, i, _D, _D]),
+                "cd_restrict": (None, [i, _D, _D]),
+                "cd_prolong_add": (None, [i, _D, _D]),
+                "cd_norm": (d, [i, _D]),
+                "cd_create": (vp, [i, d, d, d, i, d, i, i]),
+                "cd_destroy": (None, [vp]),
+                "cd_levels": (i, [vp]),
+                "cd_get_u": (None, [vp, _D]),
+                "cd_get_faces": (None, [vp, i, _D, _D]),
+                "cd_begin_step": (None, [vp, _D]),
+                "cd_vcycle": (None, [vp]),
+                "cd_residual_norm": (d, [vp]),
+                "cd_time_step": (i, [vp, _D, d, i, _D]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -405,3 +426,122 @@ class CCHierarchy:
         rho = np.zeros(maxit + 1)
         k = lib().cc_solve(self.h, float(tol), int(maxit), _p(rho))
         return rho[:k + 1]
+
+
+# ---------------- complex diffusion (cd_oracle.c) ----------------
+# Complex arrays are numpy complex128 of shape (n, n), x fastest.
+
+def _cgrid(a):
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def _pc(a):
+    assert a.dtype == np.complex128 and a.flags.c_contiguous
+    return a.ctypes.data_as(_D)
+
+
+def cd_diffusivity(u, theta, kappa):
+    u = _cgrid(u)
+    g = np.empty_like(u)
+    lib().cd_diffusivity(u.shape[0], _pc(u), float(theta), float(kappa), _pc(g))
+    return g
+
+
+def cd_faces(g):
+    g = _cgrid(g)
+    gx, gy = np.empty_like(g), np.empty_like(g)
+    lib().cd_faces(g.shape[0], _pc(g), _pc(gx), _pc(gy))
+    return gx, gy
+
+
+def cd_coarsen_faces(gx, gy):
+    gx, gy = _cgrid(gx), _cgrid(gy)
+    nf = gx.shape[0]
+    cx, cy = np.empty((nf // 2, nf // 2), np.complex128), np.empty((nf // 2, nf // 2), np.complex128)
+    lib().cd_coarsen_faces(nf, _pc(gx), _pc(gy), _pc(cx), _pc(cy))
+    return cx, cy
+
+
+def cd_apply(u, tau, gx, gy):
+    u, gx, gy = _cgrid(u), _cgrid(gx), _cgrid(gy)
+    out = np.empty_like(u)
+    lib().cd_apply(u.shape[0], float(tau), _pc(gx), _pc(gy), _pc(u), _pc(out))
+    return out
+
+
+def cd_residual(u, f, tau, gx, gy):
+    u, f, gx, gy = _cgrid(u), _cgrid(f), _cgrid(gx), _cgrid(gy)
+    out = np.empty_like(u)
+    lib().cd_residual(u.shape[0], float(tau), _pc(gx), _pc(gy), _pc(u), _pc(f), _pc(out))
+    return out
+
+
+def cd_smooth(u, f, tau, gx, gy, sweeps, smoother=RBGS, omega=1.0):
+    u = _cgrid(u).copy()
+    f, gx, gy = _cgrid(f), _cgrid(gx), _cgrid(gy)
+    lib().cd_smooth(u.shape[0], float(tau), _pc(gx), _pc(gy), int(smoother), float(omega), int(sweeps), _pc(u), _pc(f))
+    return u
+
+
+def cd_restrict(r):
+    r = _cgrid(r)
+    out = np.empty((r.shape[0] // 2,) * 2, np.complex128)
+    lib().cd_restrict(r.shape[0], _pc(r), _pc(out))
+    return out
+
+
+def cd_prolong_add(e, u):
+    e = _cgrid(e)
+    u = _cgrid(u).copy()
+    lib().cd_prolong_add(e.shape[0], _pc(e), _pc(u))
+    return u
+
+
+def cd_norm(r):
+    r = _cgrid(r)
+    return lib().cd_norm(r.shape[0], _pc(r))
+
+
+class CDHierarchy:
+    """Implicit Euler steps of complex diffusion on an n x n cell-centred grid."""
+
+    def __init__(self, n, tau, theta, kappa, smoother=RBGS, omega=1.0, nu1=2, nu2=2):
+        self.n = n
+        self.h = lib().cd_create(n, float(tau), float(theta), float(kappa), smoother, float(omega), nu1, nu2)
+        if not self.h:
+            raise ValueError("invalid parameters")
+        self.levels = lib().cd_levels(self.h)
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            lib().cd_destroy(h)
+            self.h = None
+
+    def begin_step(self, un):
+        un = _cgrid(un)
+        lib().cd_begin_step(self.h, _pc(un))
+
+    def faces(self, l):
+        nl = self.n >> l
+        gx, gy = np.empty((nl, nl), np.complex128), np.empty((nl, nl), np.complex128)
+        lib().cd_get_faces(self.h, l, _pc(gx), _pc(gy))
+        return gx, gy
+
+    def vcycle(self):
+        lib().cd_vcycle(self.h)
+
+    def residual_norm(self):
+        return lib().cd_residual_norm(self.h)
+
+    def get_u(self):
+        u = np.empty((self.n, self.n), np.complex128)
+        lib().cd_get_u(self.h, _pc(u))
+        return u
+
+    def time_step(self, un, tol, maxit):
+        """Solves one step from un; returns (u^{n+1}, rho history)."""
+        un = _cgrid(un)
+        rho = np.zeros(maxit + 1)
+        k = lib().cd_time_step(self.h, _pc(un), float(tol), int(maxit), rho.ctypes.data_as(_D))
+        return self.get_u(), rho[:k + 1]
