@@ -1,5 +1,5 @@
-"""ctypes declarations of the C ABI in include/mg.h and include/mg_cc.h
-(argument marshalling only).
+"""ctypes declarations of the C ABI in include/mg.h, include/mg_cc.h and
+include/mg_cd.h (argument marshalling only).
 
 Loading fails loudly if libmg.so has not been built: there is no fallback
 implementation of any operation in Python.
@@ -46,7 +46,16 @@ class mg_cc_params(ctypes.Structure):
 
 MG_CC_NEUMANN, MG_CC_DIRICHLET = 0, 1
 
-# name -> (restype, argtypes); every function declared in include/mg.h and include/mg_cc.h.
+
+class mg_cd_params(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("tau", ctypes.c_double), ("theta", ctypes.c_double),
+                ("kappa", ctypes.c_double), ("smoother", ctypes.c_int), ("omega", ctypes.c_double),
+                ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("maxit", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+MG_CD_U, MG_CD_F, MG_CD_R, MG_CD_GX, MG_CD_GY = range(5)
+
+# name -> (restype, argtypes); every function declared in include/mg.h, mg_cc.h and mg_cd.h.
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _D = ctypes.c_double
@@ -103,6 +112,24 @@ SIGNATURES = {
     "mg_cc_vcycle": (_I, [_P]),
     "mg_cc_residual_norm": (_I, [_P, _I, ctypes.POINTER(_D)]),
     "mg_cc_solve": (_I, [_P, _D, ctypes.POINTER(_I), ctypes.POINTER(_D), _P]),
+    "mg_cd_default_params": (None, [ctypes.POINTER(mg_cd_params)]),
+    "mg_cd_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(mg_cd_params)]),
+    "mg_cd_create": (_I, [ctypes.POINTER(mg_cd_params), _P, ctypes.c_size_t, ctypes.POINTER(_P)]),
+    "mg_cd_destroy": (_I, [_P]),
+    "mg_cd_num_levels": (_I, [_P]),
+    "mg_cd_level_size": (_I, [_P, _I]),
+    "mg_cd_set_field": (_I, [_P, _I, _I, _P]),
+    "mg_cd_get_field": (_I, [_P, _I, _I, _P]),
+    "mg_cd_begin_step": (_I, [_P, _P]),
+    "mg_cd_smooth": (_I, [_P, _I, _I]),
+    "mg_cd_residual": (_I, [_P, _I]),
+    "mg_cd_restrict": (_I, [_P, _I]),
+    "mg_cd_prolongate": (_I, [_P, _I]),
+    "mg_cd_coarse_solve": (_I, [_P]),
+    "mg_cd_vcycle": (_I, [_P]),
+    "mg_cd_residual_norm": (_I, [_P, _I, ctypes.POINTER(_D)]),
+    "mg_cd_solve": (_I, [_P, _D, ctypes.POINTER(_I), ctypes.POINTER(_D), _P]),
+    "mg_cd_time_step": (_I, [_P, _P, _D, ctypes.POINTER(_I), ctypes.POINTER(_D), _P]),
 }
 
 _lib = None

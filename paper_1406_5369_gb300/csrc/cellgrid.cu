@@ -146,8 +146,9 @@ __global__ void k_prolong(const double *__restrict__ ec, Geo gc, double *__restr
   uf[c.p] += ec[(long long)(c.k >> 1) * gc.sz + (long long)(c.j >> 1) * gc.sy + (c.i >> 1)];
 }
 
-// Fixed-order norm: block b sums r^2 over the cells t = b*256 + tid +
-// m*gridDim*256 (row-major cell index), then a fixed-shape tree.
+// Fixed-order norm: block b sums r^2 over rows b, b + gridDim, ... (thread t
+// over cells t, t + 256, ... of each row), then a fixed-shape tree; no 64-bit
+// index division per cell.
 __device__ __forceinline__ double block_sum(double v) {
   __shared__ double buf[kThreads];
   buf[threadIdx.x] = v;
@@ -162,15 +163,16 @@ __device__ __forceinline__ double block_sum(double v) {
 template <int DIM>
 __global__ void k_norm_partials(const double *__restrict__ u, const double *__restrict__ f, Geo g, Coef s,
                                 double *__restrict__ partials) {
-  const long long n = g.n, total = n * n * (DIM == 3 ? n : 1);
+  const int n = g.n, rows = DIM == 3 ? n * n : n;
   double acc = 0.0;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % n), j = (int)((t / n) % n), k = DIM == 3 ? (int)(t / (n * n)) : 0;
-    const long long p = (long long)k * g.sz + (long long)j * g.sy + i;
-    int cls;
-    const double r = f[p] - apply<DIM>(u, p, i, j, k, g, s, cls);
-    acc += r * r;
+  for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int j = row % n, k = DIM == 3 ? row / n : 0;
+    const long long base = (long long)k * g.sz + (long long)j * g.sy;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      int cls;
+      const double r = f[base + i] - apply<DIM>(u, base + i, i, j, k, g, s, cls);
+      acc += r * r;
+    }
   }
   acc = block_sum(acc);
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
