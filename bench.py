@@ -814,6 +814,71 @@ def run_cc(args):
           "f64", cc=rows, **extra)
 
 
+# The paper's Table 2 complex-diffusion rows (2D, 4096^2 cells, one V(2,2) cycle): the
+# first column is ms on one CPU core, the GPU columns speedups over it; these are the
+# derived GTX 680 times (first column / speedup), double / float.
+PAPER_TABLE2_CD_GTX680_MS = {"jacobi": (9235 / 23.99, 9235 / 33.58), "rbgs": (7504 / 11.62, 7504 / 16.42)}
+
+
+def run_cd(args):
+    """Complex diffusion (include/mg_cd.h) at the paper's size, 4096^2 cells: ms per V(2,2)
+    cycle of an implicit Euler step, Jacobi omega 0.8 and RBGS, complex FP64."""
+    torch = _init_cuda()
+    import math
+    import numpy as np
+    import synth
+    from paper_1406_5369_gb300 import CDSolver
+    stream = torch.cuda.current_stream()
+    n, tau, theta, kappa = 4096, 1e-4, math.pi / 30, 0.1
+    x = (np.arange(n) + 0.5) / n
+    noise = synth.uniform(0x5EED00CD, (2, n, n))
+    img = (np.exp(-((x[None, :] - 0.5) ** 2 + (x[:, None] - 0.4) ** 2) / 0.05) + 0.3 * (2 * noise[0] - 1)
+           + 0.02j * (2 * noise[1] - 1))
+    u0 = torch.from_numpy(np.ascontiguousarray(img)).cuda()
+    reps = max(3, args.steps)
+    rows = []
+    for sm, om in (("jacobi", 0.8), ("rbgs", 1.0)):
+        s = CDSolver(n, tau=tau, theta=theta, kappa=kappa, smoother=sm, omega=om, nu1=2, nu2=2, maxit=40)
+        it, rr, _ = s.time_step(u0, 1e-10)
+        s.begin_step(u0)
+        for _ in range(3):
+            s.vcycle()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(reps):
+            s.vcycle()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / reps
+        paper = PAPER_TABLE2_CD_GTX680_MS[sm]
+        rows.append({"smoother": sm, "omega": om, "ms_per_vcycle_c128": ms, "cycles_to_1e-10": it,
+                     "relres": rr, "paper_gtx680_ms_f64": paper[0], "paper_gtx680_ms_f32": paper[1]})
+        s.close()
+        del s
+    extra = {}
+    if not args.no_cpu_baseline:
+        import oracle
+        H = oracle.CDHierarchy(n, tau, theta, kappa, smoother=oracle.JACOBI, omega=0.8, nu1=2, nu2=2)
+        H.begin_step(img)
+        t0 = time.perf_counter()
+        H.vcycle()
+        t = time.perf_counter() - t0
+        extra["cpu_baseline"] = {"value": 1e3 * t, "unit": "ms per V(2,2) cycle", "cores": 1, "kind": "oracle",
+                                 "sample": "one oracle Jacobi V(2,2) cycle of a 4096^2 complex-diffusion step"}
+    head = rows[0]
+    _line("ms per V(2,2) cycle (complex diffusion, paper Table 2)", head["ms_per_vcycle_c128"],
+          "ms per V(2,2) cycle", False, head["ms_per_vcycle_c128"], args,
+          {"workload": "complex diffusion u_t = div(g(Im u) grad u), 4096^2 cells, Neumann, implicit Euler "
+                       "tau = 1e-4, g = e^{i theta}/(1 + (Im u/(kappa theta))^2), theta = pi/30, kappa = 0.1, "
+                       "lagged diffusivity; synthetic image (bump + U[-0.3,0.3] noise + 0.02i noise, seed "
+                       "0x5EED00CD); V(2,2) Jacobi omega=0.8 / RBGS, cell-centred restriction, constant "
+                       "interpolation; value = Jacobi"},
+          "c128 (complex f64)", cd=rows,
+          context="paper numbers: GTX 680, derived from Table 2 as first column / speedup; complex arithmetic "
+                  "in both, hardware and software differ, context only", **extra)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -821,7 +886,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "table2", "cc"],
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "table2", "cc", "cd"],
                     help="c2 (default): the 8193^2 headline; others print their own line")
     ap.add_argument("--batch-problems", type=int, default=4096)
     ap.add_argument("--rate", type=float, default=2000.0)
@@ -833,7 +898,7 @@ def main():
         run_gpu(args)
     else:
         {"c1": run_c1, "c3": run_c3, "c4": run_c4, "c5": run_c5, "table2": run_table2,
-         "cc": run_cc}[args.workload](args)
+         "cc": run_cc, "cd": run_cd}[args.workload](args)
 
 
 if __name__ == "__main__":
