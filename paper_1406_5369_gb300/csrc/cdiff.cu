@@ -24,7 +24,7 @@ namespace cd {
 
 constexpr int kMaxLev = 16;
 constexpr int kThreads = 256;
-constexpr int kNormBlocks = 512;
+constexpr int kNormBlocks = 4096;  // enough blocks to hide FP64 latency on every level
 
 struct Geo {
   int n;

@@ -29,7 +29,7 @@ namespace cc {
 constexpr int kMaxLev = 16;
 constexpr int kCoarseMax = 64;  // unknowns of the largest coarsest grid (4^3)
 constexpr int kThreads = 256;
-constexpr int kNormBlocks = 512;
+constexpr int kNormBlocks = 4096;  // enough blocks to hide FP64 latency on every level
 
 struct Geo {
   int n;

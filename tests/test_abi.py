@@ -140,9 +140,9 @@ def test_cell_grid_params_are_validated_without_a_device(lib):
     p.n = 64
     good = lib.mg_cc_workspace_bytes(ctypes.byref(p))
     # levels 64..1: four FP64 fields each (rows padded to 16 doubles), the
-    # 1x1 coarsest inverse, norm partials and the norm slot, 256-byte aligned
+    # 1x1 coarsest inverse, 4096 norm partials and the norm slot, 256-byte aligned
     a256 = lambda b: -(-b // 256) * 256
-    want = sum(4 * a256(-(-m // 16) * 16 * m * 8) for m in (64, 32, 16, 8, 4, 2, 1)) + a256(8) + a256(512 * 8) + 8
+    want = sum(4 * a256(-(-m // 16) * 16 * m * 8) for m in (64, 32, 16, 8, 4, 2, 1)) + a256(8) + a256(4096 * 8) + 8
     assert good == a256(want)
     for field, bad in [("n", 48), ("n", 32768), ("dim", 4), ("sigma", -1.0), ("omega", 2.0), ("coarsest_n", 3),
                        ("coarsest_n", 128), ("bc", 5), ("nu1", 9)]:
