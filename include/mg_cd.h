@@ -70,6 +70,7 @@ mg_status mg_cd_destroy(mg_cd_ctx *ctx);
 int mg_cd_num_levels(const mg_cd_ctx *ctx);
 int mg_cd_level_size(const mg_cd_ctx *ctx, int level);
 
+/* Setting gx or gy also re-forms the level's omega / diag, which the smoothers use. */
 mg_status mg_cd_set_field(mg_cd_ctx *ctx, int level, int field, const double *src);
 /* Synchronises the stream. */
 mg_status mg_cd_get_field(mg_cd_ctx *ctx, int level, int field, double *dst);

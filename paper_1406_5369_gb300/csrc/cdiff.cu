@@ -1,12 +1,14 @@
 // Implicit Euler steps of nonlinear complex diffusion (include/mg_cd.h):
 // Sec. 4's second test problem on cell-centred grids, complex FP64.
 //
-// Layout: level l has n_l = n / 2^l cells per dimension and six complex
-// fields (double2: real, imaginary) u[0], u[1] (Jacobi ping-pong), f, r and
-// the face coefficients gx, gy, rows padded to 128 bytes (pitch = n_l
-// rounded up to 8 complex values), x fastest, no ghost cells. One thread per
-// cell (per cell of the swept colour for red-black Gauss-Seidel), rows on
-// blockIdx.y. The arithmetic is FP64 throughout and bound by FP64 issue.
+// Layout: level l has n_l = n / 2^l cells per dimension and seven complex
+// fields (double2: real, imaginary) u[0], u[1] (Jacobi ping-pong), f, r, the
+// face coefficients gx, gy and wd = omega / diag per cell, rows padded to 128
+// bytes (pitch = n_l rounded up to 8 complex values), x fastest, no ghost
+// cells. One thread per cell (per cell of the swept colour for red-black
+// Gauss-Seidel), rows on blockIdx.y. The arithmetic is FP64 throughout and
+// bound by FP64 issue, so the smoothers take omega / diag from wd (formed
+// whenever the faces change) instead of summing faces and dividing per sweep.
 #include <math.h>
 #include <stdarg.h>
 #include <stdint.h>
@@ -110,26 +112,41 @@ __global__ void k_coarsen_faces(const double2 *__restrict__ gxf, const double2 *
   gyc[P] = fy;
 }
 
+// omega / diag_p of every cell (diag as in apply).
+__global__ void k_wdiag(const double2 *__restrict__ gx, const double2 *__restrict__ gy, double2 *__restrict__ wd,
+                        Geo g, double s, double omega) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (i >= g.n) return;
+  const long long p = (long long)j * g.sy + i;
+  double2 gs = make_double2(0.0, 0.0);
+  if (i > 0) gs = cadd(gs, gx[p - 1]);
+  if (i + 1 < g.n) gs = cadd(gs, gx[p]);
+  if (j > 0) gs = cadd(gs, gy[p - g.sy]);
+  if (j + 1 < g.n) gs = cadd(gs, gy[p]);
+  wd[p] = cdiv(make_double2(omega, 0.0), make_double2(1.0 + s * gs.x, s * gs.y));
+}
+
 __global__ void k_rbgs_half(double2 *__restrict__ u, const double2 *__restrict__ f, const double2 *__restrict__ gx,
-                            const double2 *__restrict__ gy, Geo g, double s, double omega, int color) {
+                            const double2 *__restrict__ gy, const double2 *__restrict__ wd, Geo g, double s,
+                            int color) {
   const int j = blockIdx.y;
   const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((color + j) & 1);
   if (i >= g.n) return;
   const long long p = (long long)j * g.sy + i;
   double2 dg;
   const double2 Au = apply(u, gx, gy, p, i, j, g, s, dg);
-  u[p] = cadd(u[p], cscale(omega, cdiv(csub(f[p], Au), dg)));
+  u[p] = cadd(u[p], cmul(wd[p], csub(f[p], Au)));
 }
 
 __global__ void k_jacobi(const double2 *__restrict__ uin, double2 *__restrict__ uout, const double2 *__restrict__ f,
-                         const double2 *__restrict__ gx, const double2 *__restrict__ gy, Geo g, double s,
-                         double omega) {
+                         const double2 *__restrict__ gx, const double2 *__restrict__ gy,
+                         const double2 *__restrict__ wd, Geo g, double s) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
   if (i >= g.n) return;
   const long long p = (long long)j * g.sy + i;
   double2 dg;
   const double2 Au = apply(uin, gx, gy, p, i, j, g, s, dg);
-  uout[p] = cadd(uin[p], cscale(omega, cdiv(csub(f[p], Au), dg)));
+  uout[p] = cadd(uin[p], cmul(wd[p], csub(f[p], Au)));
 }
 
 __global__ void k_residual(const double2 *__restrict__ u, const double2 *__restrict__ f, double2 *__restrict__ r,
@@ -201,7 +218,7 @@ __global__ void k_norm_final(const double *__restrict__ partials, int count, dou
 struct Lev {
   int n, pitch;
   long long count;
-  double2 *u[2], *f, *r, *gx, *gy;
+  double2 *u[2], *f, *r, *gx, *gy, *wd;
   int cur;
 };
 
@@ -276,6 +293,7 @@ size_t layout(mg_cd_ctx *c, char *base) {
     L.r = (double2 *)take(bytes);
     L.gx = (double2 *)take(bytes);
     L.gy = (double2 *)take(bytes);
+    L.wd = (double2 *)take(bytes);
     if (n == 1) break;
   }
   c->partials = (double *)take(kNormBlocks * sizeof(double));
@@ -300,9 +318,9 @@ mg_status op_smooth(mg_cd_ctx *c, int l, int sweeps) {
   for (int it = 0; it < sweeps; it++) {
     if (c->p.smoother == MG_RBGS) {
       for (int color = 0; color < 2; color++)
-        LAUNCH(k_rbgs_half, grid_of(L, (L.n + 1) / 2), L.u[L.cur], L.f, L.gx, L.gy, g, s, c->p.omega, color);
+        LAUNCH(k_rbgs_half, grid_of(L, (L.n + 1) / 2), L.u[L.cur], L.f, L.gx, L.gy, L.wd, g, s, color);
     } else {
-      LAUNCH(k_jacobi, grid_of(L, L.n), L.u[L.cur], L.u[L.cur ^ 1], L.f, L.gx, L.gy, g, s, c->p.omega);
+      LAUNCH(k_jacobi, grid_of(L, L.n), L.u[L.cur], L.u[L.cur ^ 1], L.f, L.gx, L.gy, L.wd, g, s);
       L.cur ^= 1;
     }
   }
@@ -378,6 +396,12 @@ double2 *field_ptr(Lev &L, int field) {
     case MG_CD_GY: return L.gy;
     default: return nullptr;
   }
+}
+
+mg_status op_wdiag(mg_cd_ctx *c, int l) {
+  Lev &L = c->lv[l];
+  LAUNCH(k_wdiag, grid_of(L, L.n), L.gx, L.gy, L.wd, geo_of(L), s_of(c, L), c->p.omega);
+  return MG_OK;
 }
 
 mg_status copy_in(mg_cd_ctx *c, Lev &L, double2 *dst, const double *src) {
@@ -457,7 +481,8 @@ mg_status mg_cd_set_field(mg_cd_ctx *c, int level, int field, const double *src)
   if (!src) return cdfail(MG_EINVAL, "src is NULL");
   double2 *dst = field_ptr(c->lv[level], field);
   if (!dst) return cdfail(MG_EINVAL, "unknown field %d", field);
-  return copy_in(c, c->lv[level], dst, src);
+  if ((st = copy_in(c, c->lv[level], dst, src))) return st;
+  return (field == MG_CD_GX || field == MG_CD_GY) ? op_wdiag(c, level) : MG_OK;
 }
 
 mg_status mg_cd_get_field(mg_cd_ctx *c, int level, int field, double *dst) {
@@ -486,6 +511,8 @@ mg_status mg_cd_begin_step(mg_cd_ctx *c, const double *un) {
     Lev &F = c->lv[l - 1], &C = c->lv[l];
     LAUNCH(k_coarsen_faces, grid_of(C, C.n), F.gx, F.gy, geo_of(F), C.gx, C.gy, geo_of(C));
   }
+  for (int l = 0; l < c->nl; l++)
+    if ((st = op_wdiag(c, l))) return st;
   return MG_OK;
 }
 
