@@ -160,3 +160,26 @@ def test_cell_grid_params_are_validated_without_a_device(lib):
     ctx = ctypes.c_void_p()
     assert lib.mg_cc_create(ctypes.byref(p), ctypes.c_void_p(256), 16, ctypes.byref(ctx)) == C.MG_ENOMEM
     assert lib.mg_cc_num_levels(None) == -1
+
+
+def test_complex_diffusion_params_are_validated_without_a_device(lib):
+    from paper_1406_5369_gb300 import _capi as C
+    p = C.mg_cd_params()
+    lib.mg_cd_default_params(ctypes.byref(p))
+    assert (p.n, p.nu1, p.nu2, p.smoother) == (2, 2, 2, C.MG_RBGS)
+    p.n = 64
+    good = lib.mg_cd_workspace_bytes(ctypes.byref(p))
+    # levels 64..1: seven complex fields each (rows padded to 8 complex values),
+    # 4096 norm partials and the norm slot, 256-byte aligned
+    a256 = lambda b: -(-b // 256) * 256
+    want = sum(7 * a256(-(-m // 8) * 8 * m * 16) for m in (64, 32, 16, 8, 4, 2, 1)) + a256(4096 * 8) + 8
+    assert good == a256(want)
+    for field, bad in [("n", 96), ("n", 16384), ("tau", 0.0), ("theta", 0.0), ("kappa", -1.0), ("omega", 0.0),
+                       ("nu1", -1), ("maxit", -1), ("smoother", 7)]:
+        q = C.mg_cd_params()
+        ctypes.memmove(ctypes.byref(q), ctypes.byref(p), ctypes.sizeof(p))
+        setattr(q, field, bad)
+        assert lib.mg_cd_workspace_bytes(ctypes.byref(q)) == 0, (field, bad)
+    ctx = ctypes.c_void_p()
+    assert lib.mg_cd_create(ctypes.byref(p), ctypes.c_void_p(256), 16, ctypes.byref(ctx)) == C.MG_ENOMEM
+    assert lib.mg_cd_num_levels(None) == -1
