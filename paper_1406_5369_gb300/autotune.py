@@ -99,14 +99,15 @@ def tune(dim, n, f, tol, knobs, base=None, reps=2, use_cache=True):
     return best, table
 
 
-def lfa_choice(dim, c=(1.0, 1.0, 1.0), tol=1e-10, smoothers=("rbgs", "jacobi"), omegas=None, nus=None):
+def lfa_choice(dim, c=(1.0, 1.0, 1.0), tol=1e-10, smoothers=("rbgs", "jacobi"), omegas=None, nus=None,
+               grid="node"):
     """The configuration (smoother, omega, nu1, nu2) that local Fourier
     analysis predicts to reach `tol` with the least operator-model traffic
     (lfa.choose); the rest of the ranking is returned under "ranking".
     Host-side only: the prediction replaces timing for the discrete choices
     the feature model leaves open (Sec. 2.3, Sec. 5)."""
     from . import lfa
-    ranked = lfa.choose(dim, c=c, tol=tol, smoothers=smoothers, omegas=omegas, nus=nus)
+    ranked = lfa.choose(dim, c=c, tol=tol, smoothers=smoothers, omegas=omegas, nus=nus, grid=grid)
     if not ranked:
         raise ValueError("no candidate converges according to LFA")
     best = dict(ranked[0])

@@ -84,6 +84,30 @@ def two_grid_operators(dim, smoother, omega, nu1, nu2, c=(1.0, 1.0, 1.0), m=32, 
     return th, np.linalg.matrix_power(S, nu2) @ K @ np.linalg.matrix_power(S, nu1)
 
 
+def cc_two_grid_operators(dim, smoother, omega, nu1, nu2, c=(1.0, 1.0, 1.0), m=32, th=None):
+    """Two-grid matrices for cell-centred grids (the mg_cc.h operator with
+    sigma h^2 -> 0): mean-of-children restriction and constant interpolation.
+    With the cell centres x_i = i + 1/2 and the coarse centres X = 2I + 1 (in
+    fine cells), the restriction maps the harmonic theta + pi*alpha to the
+    coarse frequency 2 theta with the factor prod_d cos(theta_d / 2)
+    (alpha_d = 0) or sin(theta_d / 2) (alpha_d = 1), and constant
+    interpolation has the same components, so p = r as for the node-based
+    transfers but one order lower (no square: the node-based factor is
+    prod_d cos^2)."""
+    c = np.asarray(list(c)[:dim], dtype=np.float64)
+    if th is None:
+        th = _thetas(dim, m)
+    H = 2 ** dim
+    _, A = _symbols(dim, th, c)
+    AH = np.sum(c * (2.0 - 2.0 * np.cos(2.0 * th)), axis=1) / 4.0
+    alphas = np.array(list(itertools.product((0, 1), repeat=dim)), dtype=np.float64)
+    half = th / 2.0
+    r = np.prod(np.where(alphas[None, :, :] == 0, np.cos(half)[:, None, :], np.sin(half)[:, None, :]), axis=2)
+    K = np.eye(H)[None] - (r[:, :, None] * r[:, None, :] * A[:, None, :]) / AH[:, None, None]
+    S = _smoother(dim, smoother, omega, A, c)
+    return th, np.linalg.matrix_power(S, nu2) @ K @ np.linalg.matrix_power(S, nu1)
+
+
 def smoothing_operators(dim, smoother, omega, nu, c=(1.0, 1.0, 1.0), m=32, th=None):
     """Ideal coarse-grid correction: Q S^nu, Q the projection onto the high
     harmonics (alpha != 0)."""
@@ -126,6 +150,16 @@ def two_grid_factor(dim, smoother, omega, nu1, nu2, c=(1.0, 1.0, 1.0), m=None, r
     return _sup(lambda th: two_grid_operators(dim, smoother, omega, nu1, nu2, c, th=th)[1], dim, m, refine)
 
 
+def cc_two_grid_factor(dim, smoother, omega, nu1, nu2, c=(1.0, 1.0, 1.0), m=None, refine=4):
+    """Predicted two-grid factor on cell-centred grids (cell-centred restriction,
+    constant interpolation). V-cycles with these transfers converge more slowly
+    than the two-grid cycle and degrade with the number of levels (transfer
+    orders 1 + 1 do not exceed the operator's 2); the prediction ranks
+    smoothers, it does not bound the V-cycle."""
+    m = m or (32 if dim == 2 else 12)
+    return _sup(lambda th: cc_two_grid_operators(dim, smoother, omega, nu1, nu2, c, th=th)[1], dim, m, refine)
+
+
 def smoothing_factor(dim, smoother, omega, nu=1, c=(1.0, 1.0, 1.0), m=None, refine=4):
     """Smoothing factor per sweep (ideal coarse-grid correction)."""
     m = m or (32 if dim == 2 else 12)
@@ -142,10 +176,12 @@ def cycle_words(dim, nu1, nu2):
     return (3.0 * (nu1 + nu2) + 3.0 + (1.0 + q) + q + (2.0 + q)) / (1.0 - q)
 
 
-def choose(dim, c=(1.0, 1.0, 1.0), tol=1e-10, smoothers=SMOOTHERS, omegas=None, nus=None):
+def choose(dim, c=(1.0, 1.0, 1.0), tol=1e-10, smoothers=SMOOTHERS, omegas=None, nus=None, grid="node"):
     """Ranks configurations by predicted cost to reduce the residual by `tol`:
-    cycles = ceil(log tol / log rho_TG) times cycle_words. Returns the ranked
-    list of dicts (smoother, omega, nu1, nu2, rho, cycles, words)."""
+    cycles = ceil(log tol / log rho_TG) times cycle_words. grid: "node"
+    (node-based transfers) or "cell" (cell-centred transfers). Returns the
+    ranked list of dicts (smoother, omega, nu1, nu2, rho, cycles, words)."""
+    factor = {"node": two_grid_factor, "cell": cc_two_grid_factor}[grid]
     if omegas is None:
         omegas = {"rbgs": [1.0, 1.05, 1.1, 1.15, 1.2, 1.25, 1.3],
                   "jacobi": [0.5, 0.6, 0.7, 0.75, 0.8, 0.85, 0.9, 1.0]}
@@ -155,7 +191,7 @@ def choose(dim, c=(1.0, 1.0, 1.0), tol=1e-10, smoothers=SMOOTHERS, omegas=None, 
     for sm in smoothers:
         for om in omegas[sm]:
             for nu1, nu2 in nus:
-                rho = two_grid_factor(dim, sm, om, nu1, nu2, c)
+                rho = factor(dim, sm, om, nu1, nu2, c)
                 if not rho < 1.0:
                     continue
                 cycles = max(1, math.ceil(math.log(tol) / math.log(max(rho, 1e-300))))
