@@ -1,5 +1,5 @@
 """LFA in the product (paper_1406_5369_gb300.lfa) and the autotuner's choice
-built on it (LFA-driven choice of omega / nu / smoother).
+built on it: the LFA-driven choice of smoother, omega and nu.
 
 Pins: the classical two-grid factors of red-black Gauss-Seidel with full
 weighting and bilinear interpolation, 0.250 / 0.074 / 0.053 for nu = 1, 2, 3
