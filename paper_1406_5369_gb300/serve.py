@@ -131,6 +131,7 @@ class Server:
         pending = collections.deque(sorted(requests, key=lambda r: r["t"]))
         waiting = collections.deque()
         done = []
+        rejected = []  # requests whose hierarchy alone exceeds the budget: they could never start
         t0 = time.perf_counter()
         now_fn = lambda: time.perf_counter() - t0  # noqa: E731
         queue_depth = []
@@ -139,7 +140,11 @@ class Server:
             if max_wall is not None and now > max_wall:
                 break
             while pending and pending[0]["t"] <= now:
-                waiting.append(pending.popleft())
+                req = pending.popleft()
+                if self._bytes(req["dim"], req["n"]) > self.budget:
+                    rejected.append(req["id"])
+                else:
+                    waiting.append(req)
             while waiting and self.admit(waiting[0]):
                 waiting.popleft()
             queue_depth.append(len(waiting))
@@ -155,5 +160,5 @@ class Server:
                  "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
                  "mean_ms": 1e3 * float(lat.mean()), "steps": self.steps,
                  "peak_hbm_gb": self.peak_used / 1e9, "max_queue_depth": int(max(queue_depth) if queue_depth else 0),
-                 "unfinished": len(self.active) + len(waiting) + len(pending)}
+                 "unfinished": len(self.active) + len(waiting) + len(pending), "rejected": len(rejected)}
         return done, stats
