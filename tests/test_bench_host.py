@@ -1,0 +1,73 @@
+"""Host-side checks of bench.py and the autotuner, without a GPU.
+
+- The reference arm (the oracle, timed on the host) prints one JSON line with
+  the contract's keys: impl = reference, the arm's metric and unit, a
+  cpu_baseline describing the run and an e2e object with zero copy bytes.
+  The workload is shrunk to 129^2 here so that the check takes a second.
+- The autotuner searches one knob at a time (each knob tuned with the others
+  at their best so far), keeps the fastest candidate, and serves a repeated
+  request for the same problem from its cache without timing again.
+"""
+import io
+import json
+import sys
+import types
+from contextlib import redirect_stdout
+
+import pytest
+
+import bench
+
+
+def test_reference_arm_prints_the_contract_line(monkeypatch):
+    monkeypatch.setattr(bench, "WORKLOAD", dict(bench.WORKLOAD, n=129))
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    args = types.SimpleNamespace(steps=2, warmup=1)
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        bench.run_reference(args)
+    lines = [l for l in buf.getvalue().splitlines() if l.strip()]
+    assert len(lines) == 1
+    rec = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in rec, key
+    assert rec["impl"] == "reference" and rec["metric"] == bench.METRIC and rec["higher_is_better"] is True
+    assert rec["value"] > 0 and abs(rec["value"] * rec["ms_per_step"] - 1e3) < 1e-6 * 1e3
+    assert rec["cpu_baseline"]["kind"] == "oracle" and rec["cpu_baseline"]["cores"] == 1
+    assert rec["e2e"]["h2d_bytes_per_step"] == 0 and rec["e2e"]["d2h_bytes_per_step"] == 0
+    assert (rec["steps"], rec["warmup"]) == (2, 1)
+
+
+def test_autotuner_coordinate_search_and_cache(monkeypatch, tmp_path):
+    from paper_1406_5369_gb300 import autotune
+    monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "autotune.json"))
+    monkeypatch.setattr(autotune, "_gpu_name", lambda: "test-gpu")
+    made = []
+
+    class FakeSolver:
+        def __init__(self, dim, n, **kw):
+            self.kw = kw
+            made.append(kw)
+
+        def close(self):
+            pass
+
+    # time = (a - 2)^2 + (b - 3)^2 + 1: the search should land on a = 2, b = 3
+    def fake_time(solver, f, tol, reps=2):
+        kw = solver.kw
+        return (kw["a"] - 2) ** 2 + (kw["b"] - 3) ** 2 + 1.0, 4
+
+    monkeypatch.setattr(autotune, "time_solve", fake_time)
+    import paper_1406_5369_gb300.solver as solver_mod
+    monkeypatch.setattr(solver_mod, "Solver", FakeSolver)
+    knobs = {"a": [0, 1, 2, 3], "b": [0, 3, 5]}
+    best, table = autotune.tune(2, 65, None, 1e-8, knobs, base={"precision": "fp32_dc"})
+    assert best == {"a": 2, "b": 3}
+    assert len(made) == 4 + 3
+    # b was searched with a at its best value
+    assert all(m["a"] == 2 for m in made[4:])
+    assert all(m["precision"] == "fp32_dc" for m in made)
+    again, _ = autotune.tune(2, 65, None, 1e-8, knobs, base={"precision": "fp32_dc"})
+    assert again == best and len(made) == 7  # served from the cache
