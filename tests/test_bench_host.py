@@ -71,3 +71,21 @@ def test_autotuner_coordinate_search_and_cache(monkeypatch, tmp_path):
     assert all(m["precision"] == "fp32_dc" for m in made)
     again, _ = autotune.tune(2, 65, None, 1e-8, knobs, base={"precision": "fp32_dc"})
     assert again == best and len(made) == 7  # served from the cache
+
+
+def test_paper_gpu_times_in_bench_are_derived_from_table2():
+    # bench.py quotes the paper's GPU times (context beside its own) as the
+    # first column of Table 2 divided by the GPU speedup columns
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_table2_runtimes.json")) as fh:
+        rows = json.load(fh)["rows"]
+    pairs = {("2D", "jacobi"): "laplacian_2d_jacobi", ("2D", "rbgs"): "laplacian_2d_gauss_seidel",
+             ("3D", "jacobi"): "laplacian_3d_jacobi", ("3D", "rbgs"): "laplacian_3d_gauss_seidel"}
+    for key, row in pairs.items():
+        r = rows[row]
+        d, f = bench.PAPER_TABLE2_GTX680_MS[key]
+        assert abs(d - r[0] / r[4]) <= 0.05 and abs(f - r[0] / r[5]) <= 0.05, key
+    for sm, row in (("jacobi", "complex_diffusion_2d_jacobi"), ("rbgs", "complex_diffusion_2d_gauss_seidel")):
+        r = rows[row]
+        d, f = bench.PAPER_TABLE2_CD_GTX680_MS[sm]
+        assert abs(d - r[0] / r[4]) <= 1e-9 and abs(f - r[0] / r[5]) <= 1e-9, sm
