@@ -140,6 +140,19 @@ def job_ms(ms, world, device="cpu"):
     return float(t.item())
 
 
+def lfa_summary(dim, smoother, omega, nu1, nu2):
+    """Host-side LFA of a workload's cycle: the predicted two-grid factor of
+    the configured weight and the weight LFA would choose for the same
+    smoother and sweeps (autotune.lfa_choice)."""
+    from paper_1406_5369_gb300 import autotune, lfa
+    grid = {"rbgs": [1.0, 1.05, 1.1, 1.15, 1.2, 1.25, 1.3], "jacobi": [0.5, 0.6, 0.7, 0.75, 0.8, 0.85, 0.9, 1.0]}
+    omegas = {smoother: sorted(set(grid[smoother] + [omega]))}  # the configured weight competes too
+    best = autotune.lfa_choice(dim, smoothers=(smoother,), nus=[(nu1, nu2)], omegas=omegas)
+    return {"rho_two_grid_configured": lfa.two_grid_factor(dim, smoother, omega, nu1, nu2),
+            "omega_lfa": best["omega"], "rho_two_grid_lfa": best["rho"],
+            "note": "infinite-grid two-grid prediction (host-side), not measured"}
+
+
 def partition(weights, world):
     """Splits independent problems over ranks, balancing the weights (bytes):
     heaviest first, each to the least-loaded rank (lowest rank on ties).
@@ -643,6 +656,7 @@ def run_c3(args):
         del s
     ms = res["bf16_dc"]["time_to_tol_s"] * 1e3
     extra = {} if args.no_cpu_baseline else {"cpu_baseline": cpu_baseline_c3(res["fp64"]["steps"])}
+    extra["lfa"] = lfa_summary(3, "jacobi", 6.0 / 7.0, 2, 2)
     _line(METRIC, 1e3 / ms, "solves/s (to 1e-10 rel. residual; 1/time-to-1e-10)", True, ms, args,
           {"workload": "3D Poisson 513^3, f ~ N(0,1) (seed 0x5EED0003), Jacobi omega=6/7 V(2,2), full weighting, "
                        "trilinear; BF16-stored FP32 inner cycles in FP64 defect correction to 1e-10",

@@ -89,3 +89,10 @@ def test_paper_gpu_times_in_bench_are_derived_from_table2():
         r = rows[row]
         d, f = bench.PAPER_TABLE2_CD_GTX680_MS[sm]
         assert abs(d - r[0] / r[4]) <= 1e-9 and abs(f - r[0] / r[5]) <= 1e-9, sm
+
+
+def test_lfa_summary_of_the_3d_jacobi_cycle():
+    out = bench.lfa_summary(3, "jacobi", 6.0 / 7.0, 2, 2)
+    assert 0.2 < out["rho_two_grid_configured"] < 0.3
+    assert out["rho_two_grid_lfa"] <= out["rho_two_grid_configured"] + 1e-12
+    assert 0.5 <= out["omega_lfa"] <= 1.0
