@@ -80,18 +80,18 @@ def test_full_ranking_prefers_red_black_and_costs_are_consistent():
     assert np.isclose(lfa.cycle_words(3, 2, 2), 21.0)
 
 
-def _cc_two_grid_matrix(n, smoother, omega, nu1, nu2, sigma=1e-3):
-    """The oracle's cell-centred two-grid error propagation on an n x n Neumann
+def _cc_two_grid_matrix(n, smoother, omega, nu1, nu2, sigma=1e-3, dim=2):
+    """The oracle's cell-centred two-grid error propagation on an n^dim Neumann
     grid, column by column (smooth, residual, restrict, exact coarse solve,
     interpolate, smooth, all with f = 0)."""
-    N = n * n
+    N = n ** dim
     M = np.zeros((N, N))
-    z = np.zeros((n, n))
+    z = np.zeros((n,) * dim)
     kw = dict(sigma=sigma, bc="neumann")
     for k in range(N):
         u = np.zeros(N)
         u[k] = 1.0
-        u = u.reshape(n, n)
+        u = u.reshape((n,) * dim)
         if nu1:
             u = oracle.cc_smooth(u, z, nu1, smoother=smoother, omega=omega, **kw)
         ec = oracle.cc_dense_solve(oracle.cc_restrict(oracle.cc_residual(u, z, **kw)), **kw)
@@ -112,6 +112,14 @@ def test_cell_centred_lfa_matches_the_oracle_two_grid_matrix(smoother, omega, nu
     measured = float(np.max(np.abs(np.linalg.eigvals(M))))
     pred = lfa.cc_two_grid_factor(2, smoother, omega, *nu)
     assert abs(measured - pred) <= tol * pred + 1e-3, (measured, pred)
+
+
+def test_cell_centred_lfa_in_3d():
+    # 8^3 cells: Jacobi omega 6/7 V(1,1) attains its supremum on this grid
+    M = _cc_two_grid_matrix(8, oracle.JACOBI, 6 / 7, 1, 1, dim=3)
+    measured = float(np.max(np.abs(np.linalg.eigvals(M))))
+    pred = lfa.cc_two_grid_factor(3, "jacobi", 6 / 7, 1, 1)
+    assert abs(measured - pred) <= 0.03 * pred, (measured, pred)
 
 
 def test_cell_centred_choice():
