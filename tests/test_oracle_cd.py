@@ -20,6 +20,8 @@ cell-centred restriction and constant interpolation).
   eigenvalue; V(2,2) cycles contract by <= 0.15 on a random image.
 - With unit faces the operator is tau times the cell-centred oracle's with
   sigma = 1/tau, and the smoothers' iterates agree (two separate sources).
+- For the lagged (linear) system one FAS two-grid cycle equals the
+  correction scheme's cycle.
 """
 import math
 
@@ -151,3 +153,34 @@ def test_real_unit_faces_reduce_to_the_cell_centred_oracle():
         b = oracle.cc_smooth(u, f / tau, 3, smoother=sm, omega=om, sigma=1.0 / tau, bc="neumann")
         assert np.max(np.abs(a.imag)) == 0.0
         assert np.max(np.abs(a.real - b)) <= 1e-12 * np.max(np.abs(b)), sm
+
+
+def test_fas_and_correction_scheme_coincide_for_the_lagged_system():
+    # With the diffusivity lagged, a step's system is linear; one FAS two-grid
+    # cycle (coarse problem A_H v = A_H(R u) + R(f - A u), correction
+    # u += P(v - R u)) then equals the correction scheme's cycle (A_H e = R r,
+    # u += P e) up to rounding, which is why the correction scheme is used.
+    n, tau = 16, 4e-3
+    g = oracle.cd_diffusivity(rand_c(n, 10, 0.02), 0.05, 0.1)
+    gx, gy = oracle.cd_faces(g)
+    cx, cy = oracle.cd_coarsen_faces(gx, gy)
+    nc = n // 2
+
+    def coarse_solve(rhs):
+        cols = []
+        for k in range(nc * nc):
+            e = np.zeros(nc * nc, complex)
+            e[k] = 1.0
+            cols.append(oracle.cd_apply(e.reshape(nc, nc), tau, cx, cy).reshape(-1))
+        return np.linalg.solve(np.array(cols).T, rhs.reshape(-1)).reshape(nc, nc)
+
+    f = rand_c(n, 11)
+    u0 = oracle.cd_smooth(rand_c(n, 12), f, tau, gx, gy, 2)
+    r = oracle.cd_residual(u0, f, tau, gx, gy)
+    # correction scheme
+    u_cs = oracle.cd_prolong_add(coarse_solve(oracle.cd_restrict(r)), u0)
+    # full approximation scheme
+    Ru = oracle.cd_restrict(u0)
+    v = coarse_solve(oracle.cd_apply(Ru, tau, cx, cy) + oracle.cd_restrict(r))
+    u_fas = oracle.cd_prolong_add(v - Ru, u0)
+    assert np.max(np.abs(u_fas - u_cs)) <= 1e-12 * np.max(np.abs(u_cs))
