@@ -184,3 +184,12 @@ def test_fas_and_correction_scheme_coincide_for_the_lagged_system():
     v = coarse_solve(oracle.cd_apply(Ru, tau, cx, cy) + oracle.cd_restrict(r))
     u_fas = oracle.cd_prolong_add(v - Ru, u0)
     assert np.max(np.abs(u_fas - u_cs)) <= 1e-12 * np.max(np.abs(u_cs))
+
+
+def test_norms_closed_form():
+    # |3 + 4i| = 5 in every one of n^2 cells: the norm is 5 n; likewise the
+    # cell-centred oracle's norm of a constant field
+    n = 16
+    assert oracle.cd_norm(np.full((n, n), 3 + 4j)) == 5.0 * n
+    assert oracle.cc_norm(np.full((n, n), -2.0)) == 2.0 * n
+    assert oracle.cc_norm(np.full((8, 8, 8), 0.5)) == 0.5 * math.sqrt(512)
