@@ -173,11 +173,18 @@ def job_value(world, ms):
 
 # ------------------------------------------------------------------ GPU arm
 
-# DRAM bytes (read + write) per launch of the level-0 kernels at 8193^2, from
-# ncu (profiles/k_*_8193.md); each is set to None whenever its kernel changes.
-K_DCX2D_TRAFFIC = 2185.6e6  # profiles/k_dcx2d_outer_4097.md (8193^2 capture quoted there)
-K_PRE2D_TRAFFIC = 875.7e6  # u-reading launch; profiles/k_pre2d_x2_level0_4097.md (8193^2 capture)
-K_POST2D_TRAFFIC = 877.8e6  # profiles/k_post2d_x2_level0_4097.md (8193^2 capture)
+# DRAM bytes (read + write) per launch of the level-0 kernels at 8193^2, as
+# ncu measured them (dram__bytes_read.sum + dram__bytes_write.sum, one launch)
+# on the kernel builds this file times; not measured inside a bench run (the
+# bench runs without a profiler). Each entry is set to None when its kernel
+# changes and comes back with the next capture.
+KERNEL_TRAFFIC = {
+    "k_dcx2d": 2185.6e6,   # algorithmic 32 B/node = 2148 MB
+    "k_pre2d_x2": 875.7e6,  # a launch that reads u: algorithmic 13 B/node = 872.6 MB
+    "k_post2d_x2": 877.8e6,  # algorithmic 13 B/node = 872.6 MB
+}
+TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of this kernel build at 8193^2, "
+                  "captured separately (not in this run)")
 
 
 def run_gpu(args):
@@ -284,6 +291,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         t64.append(time.perf_counter() - a)
     fp64_ms = 1e3 * min(t64)
+    u64 = s64.get_solution() if rank == 0 else None
     del s64
 
     # e2e: public API with host buffers (pinned), H2D of f and D2H of u every step
@@ -315,9 +323,8 @@ def run_gpu(args):
         lines.append({"kernel": "k_dcx2d: outer step of defect correction (FP64 update, exact fixed-point residual "
                                 "-> FP32 defect + norm partials), 8193^2",
                       "bound": "hbm", "achieved": a_outer, "peak": hbm_peak, "unit": "GB/s",
-                      "frac": a_outer / hbm_peak, "traffic": K_DCX2D_TRAFFIC,
-                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_dcx2d launch at "
-                                        "8193^2 (algorithmic 32 B/node = 2148 MB)",
+                      "frac": a_outer / hbm_peak, "traffic": KERNEL_TRAFFIC["k_dcx2d"],
+                      "traffic_source": TRAFFIC_SOURCE,
                       "per_launch": "read u, f (8 B each) and e (4 B), write u (8 B) and the defect (4 B) per node "
                                     "= 32 B x 8193^2 = 2148 MB",
                       "avg_launch_us": 1e3 * t_outer / c_outer, "launches": c_outer, "share": t_outer / (ms * args.steps)})
@@ -331,9 +338,8 @@ def run_gpu(args):
         a_pre = (words_pre * w) * nodes / (t_pre / c_pre * 1e-3) / 1e9
         lines.append({"kernel": "k_pre2d_x2<2,zero>: 2 RBGS sweeps + residual + full weighting, level 0 (packed FP32)",
                       "bound": "hbm", "achieved": a_pre, "peak": hbm_peak, "unit": "GB/s", "frac": a_pre / hbm_peak,
-                      "traffic": K_PRE2D_TRAFFIC,
-                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one level-0 launch that "
-                                        "reads u (13 B/node algorithmic = 872.6 MB) at 8193^2",
+                      "traffic": KERNEL_TRAFFIC["k_pre2d_x2"],
+                      "traffic_source": TRAFFIC_SOURCE + " (a launch that reads u)",
                       "per_launch": f"read f, write u (1 word each) + coarse f (1/4 word) per node, + read u in "
                                     f"{ic - 1} of {ic} launches ({words_pre:.3f} words/node on average)",
                       "avg_launch_us": 1e3 * t_pre / c_pre, "launches": c_pre, "share": t_pre / (ms * args.steps)})
@@ -342,9 +348,8 @@ def run_gpu(args):
         a_post = (3.25 * w) * nodes / (t_post / c_post * 1e-3) / 1e9
         lines.append({"kernel": "k_post2d_x2<1>: bilinear correction + 1 RBGS sweep, level 0 (packed FP32)",
                       "bound": "hbm", "achieved": a_post, "peak": hbm_peak, "unit": "GB/s", "frac": a_post / hbm_peak,
-                      "traffic": K_POST2D_TRAFFIC,
-                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one level-0 launch at "
-                                        "8193^2 (13 B/node algorithmic = 872.6 MB)", "per_launch": "read u, f (1 word each) + coarse e (1/4 word), write u per node",
+                      "traffic": KERNEL_TRAFFIC["k_post2d_x2"],
+                      "traffic_source": TRAFFIC_SOURCE, "per_launch": "read u, f (1 word each) + coarse e (1/4 word), write u per node",
                       "avg_launch_us": 1e3 * t_post / c_post, "launches": c_post, "share": t_post / (ms * args.steps)})
     dominant = max(lines, key=lambda d: d["share"]) if lines else None
     roofline = None
@@ -411,7 +416,14 @@ def run_gpu(args):
     }
     rec["config"]["parallelism"] = f"replicas x{world}"
     if rank == 0 and not args.no_cpu_baseline:
-        rec["cpu_baseline"] = cpu_baseline(args, it64)
+        # the oracle on the host cores: whole solves (cpu_baseline), then its
+        # converged solution as the reference for the GPU answers' error
+        H = oracle_hierarchy()
+        rec["cpu_baseline"] = cpu_baseline(args, H)
+        s.set_solution(None)
+        s.solve(W["tol"])
+        rec["final_error_vs_oracle"] = final_error_vs_oracle({W["precision"]: s.get_solution(), "fp64": u64}, H, f)
+        del H
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
@@ -421,80 +433,120 @@ def run_gpu(args):
 
 # ------------------------------------------------------------------ oracle timing
 
-def oracle_hierarchy():
+def oracle_cores():
+    """Runs the oracle's OpenMP timing build on every host core this process
+    may use; returns the thread count."""
+    import oracle
+    return oracle.set_threads(oracle.host_cores())
+
+
+def oracle_hierarchy(mt=True):
     """The oracle's hierarchy of the 8193^2 workload with its right-hand side set."""
     import synth
     import oracle
     W = WORKLOAD
     dim, n = W["dim"], W["n"]
-    H = oracle.Hierarchy(dim, n, smoother=oracle.RBGS, omega=W["omega"], nu1=W["nu1"], nu2=W["nu2"])
+    H = oracle.Hierarchy(dim, n, smoother=oracle.RBGS, omega=W["omega"], nu1=W["nu1"], nu2=W["nu2"], mt=mt)
     H.set_rhs(synth.uniform_rhs(dim, n, W["seed"]))
     return H
 
 
-def oracle_sample(cycles_to_tol, ncycles=2, H=None, zero=None):
-    """Times ncycles oracle V-cycles from u = 0 on the full grid and
-    extrapolates to a solve (H, zero: a prepared hierarchy and zero field)."""
+def oracle_solve_timed(H, zero, tol, maxit=60):
+    """One whole oracle solve from u = 0 to `tol` (plain FP64 V-cycles and a
+    residual norm after each, the Layer-4 driver loop); returns (seconds, cycles)."""
+    H.set_u(zero)
+    t0 = time.perf_counter()
+    rho = H.solve(tol, maxit)
+    return time.perf_counter() - t0, len(rho) - 1
+
+
+def cpu_baseline(args, H=None, budget_s=15.0):
+    """Whole FP64 oracle solves of the 8193^2 workload to 1e-10 on all host
+    cores (OpenMP build), repeated until ~budget_s is spent (at least one)."""
+    import numpy as np
+    cores = oracle_cores()
     if H is None:
         H = oracle_hierarchy()
-    elif zero is not None:
-        H.set_u(zero)
-    t0 = time.perf_counter()
-    r0 = H.residual_norm()
-    t_norm = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    for _ in range(ncycles):
-        H.vcycle()
-    t_cyc = (time.perf_counter() - t0) / ncycles
-    t_solve = t_norm + cycles_to_tol * (t_cyc + t_norm)
-    return t_solve, t_cyc, t_norm, r0
-
-
-def cpu_baseline(args, cycles_to_tol):
-    import numpy as np
-    H = oracle_hierarchy()
-    H.vcycle()  # untimed: touches every page of the hierarchy once
     zero = np.zeros((WORKLOAD["n"],) * WORKLOAD["dim"])
-    t_solve, t_cyc, t_norm, _ = oracle_sample(cycles_to_tol, H=H, zero=zero)
-    return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": f"2 FP64 oracle V(2,1) cycles from u = 0 + 1 residual norm on the full 8193^2 grid "
-                      f"after one untimed cycle ({t_cyc:.2f} s/cycle, {t_norm:.2f} s/norm), extrapolated "
-                      f"to the {cycles_to_tol} cycles the solve takes to 1e-10"}
+    oracle_solve_timed(H, zero, WORKLOAD["tol"])  # untimed: touches every page of the hierarchy
+    times, cycles = [], 0
+    while not times or (sum(times) < budget_s and len(times) < 10):
+        t, cycles = oracle_solve_timed(H, zero, WORKLOAD["tol"])
+        times.append(t)
+    t = sum(times) / len(times)
+    return {"value": 1.0 / t, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(times)} whole FP64 oracle solves of the full 8193^2 workload from u = 0 to 1e-10 "
+                      f"({cycles} V(2,1) cycles, a residual norm after each; {t:.2f} s each) on {cores} host "
+                      f"threads (OpenMP build, bitwise the serial oracle's result), after one untimed solve"}
+
+
+def final_error_vs_oracle(u_list, H, f, tol=1e-13, maxit=20):
+    """Relative error of GPU solutions against the oracle's FP64 solution of the
+    same discrete problem, converged from u = 0 to `tol` (or until maxit
+    cycles, when rounding stops the residual first). Also a guaranteed bound:
+    ||u - u*||_2 <= (||r(u)|| + ||r(u*)||) / lambda_min(A), with
+    lambda_min = d (4/h^2) sin^2(pi h/2), the smallest eigenvalue of the
+    d-dimensional Dirichlet 5-/7-point Laplacian."""
+    import numpy as np
+    import oracle
+    oracle_cores()
+    dim, n = H.dim, H.n
+    H.set_u(np.zeros((n,) * dim))
+    rho = H.solve(tol, maxit)
+    us = H.get_u()
+    h = 1.0 / (n - 1)
+    lam_min = dim * 4.0 / h ** 2 * math.sin(math.pi * h / 2) ** 2
+    nf = oracle.norm(f, mt=True)
+    r_star = oracle.norm(oracle.residual(us, f, mt=True), mt=True)
+    us_l2 = float(np.sqrt(np.sum(us * us)))
+    us_max = float(np.max(np.abs(us)))
+    out = {}
+    for name, u in u_list.items():
+        d = u - us
+        r_u = oracle.norm(oracle.residual(u, f, mt=True), mt=True)
+        out[name] = {"rel_l2": float(np.sqrt(np.sum(d * d))) / us_l2,
+                     "rel_max": float(np.max(np.abs(d))) / us_max,
+                     "relres_by_oracle": r_u / nf,
+                     "rel_l2_bound": (r_u + r_star) / lam_min / us_l2}
+    out["oracle"] = {"relres": float(rho[-1]), "cycles": len(rho) - 1, "target": tol,
+                     "note": "plain FP64 oracle V-cycles from u = 0 until ||r||/||f|| <= target or the cycle cap "
+                             "(FP64 rounding bounds how far the residual falls at this size)"}
+    return out
 
 
 def run_reference(args):
+    """The reference arm: whole FP64 oracle solves of the 8193^2 workload to
+    1e-10 (plain V(2,1) cycles), one per step, on all host cores."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    # The plain FP64 V(2,1) iteration of this workload reaches 1e-10 in 9 cycles
-    # (the oracle's iteration is the GPU's: the tests pin them cycle by cycle).
-    cycles = 9
-    times = []
-    # one hierarchy for the run (setup untimed); each step restarts from u = 0
     import numpy as np
-    H = oracle_hierarchy()
+    cores = oracle_cores()
+    H = oracle_hierarchy()  # set-up untimed; each step restarts from u = 0
     zero = np.zeros((WORKLOAD["n"],) * WORKLOAD["dim"])
+    times, cycles = [], 0
     for _ in range(args.warmup + args.steps):
-        t_solve, t_cyc, t_norm, _ = oracle_sample(cycles, ncycles=1, H=H, zero=zero)
-        times.append(t_solve)
+        t, cycles = oracle_solve_timed(H, zero, WORKLOAD["tol"])
+        times.append(t)
     t = sum(times[args.warmup:]) / max(1, args.steps)
     rec = {
         "metric": METRIC, "impl": "reference", "value": 1.0 / t,
         "unit": "solves/s (to 1e-10 rel. residual; 1/time-to-1e-10 per GPU)",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": dict(WORKLOAD, parallelism="1 host core"),
-        "cpu_baseline": {"value": 1.0 / t, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                         "sample": "per step (hierarchy built once, untimed; u reset to 0): 1 FP64 oracle "
-                                   "V(2,1) cycle + 1 residual norm on the full "
-                                   "8193^2 grid, extrapolated to the 9 cycles of the solve"},
+        "data": "synthetic", "config": dict(WORKLOAD, parallelism=f"{cores} host threads (OpenMP)"),
+        "cpu_baseline": {"value": 1.0 / t, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                         "sample": f"each step one whole FP64 oracle solve of the full 8193^2 grid from u = 0 to "
+                                   f"1e-10 ({cycles} V(2,1) cycles with a residual norm after each), hierarchy built "
+                                   f"once, untimed"},
         "e2e": {"value": 1.0 / t, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(rec), flush=True)
 
 
-# Oracle baselines of the other configurations (serial, one host core; each
-# bounded to some 10-30 s of CPU work).
+# Oracle baselines of the other configurations (each bounded to some 10-30 s of
+# CPU work): c1 on one core (its 129^2 grid is too small to share out), the
+# others on every host core through the oracle's OpenMP timing build.
 
 def cpu_baseline_c1():
     """The whole 129^2 workload: 10 FP64 oracle V(2,1) cycles + norms."""
@@ -509,22 +561,21 @@ def cpu_baseline_c1():
             "sample": "the whole workload: 10 oracle V(2,1) cycles with their residual norms on 129^2"}
 
 
-def cpu_baseline_c3(cycles_to_tol):
-    """One FP64 oracle Jacobi V(2,2) cycle + one norm on 513^3, extrapolated."""
-    import synth
-    import oracle
-    H = oracle.Hierarchy(3, 513, smoother=oracle.JACOBI, omega=6.0 / 7.0, nu1=2, nu2=2)
-    H.set_rhs(synth.normal_rhs(3, 513, 0x5EED0003))
-    t0 = time.perf_counter()
-    H.residual_norm()
-    t_norm = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    H.vcycle()
-    t_cyc = time.perf_counter() - t0
-    t = t_norm + cycles_to_tol * (t_cyc + t_norm)
-    return {"value": 1.0 / t, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": f"1 FP64 oracle Jacobi V(2,2) cycle ({t_cyc:.1f} s) + 1 residual norm ({t_norm:.1f} s) on the "
-                      f"full 513^3 grid, extrapolated to the {cycles_to_tol} FP64 cycles of the solve to 1e-10"}
+def cpu_baseline_c3(H, f, budget_s=30.0):
+    """Whole FP64 oracle solves of the 513^3 workload (Jacobi V(2,2), to 1e-10)
+    on all host cores; at least one, more while within budget_s."""
+    import numpy as np
+    cores = oracle_cores()
+    zero = np.zeros(f.shape)
+    times, cycles = [], 0
+    while not times or (sum(times) < budget_s and len(times) < 5):
+        t, cycles = oracle_solve_timed(H, zero, 1e-10, maxit=100)
+        times.append(t)
+    t = sum(times) / len(times)
+    return {"value": 1.0 / t, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(times)} whole FP64 oracle solves of the full 513^3 grid from u = 0 to 1e-10 ({cycles} "
+                      f"Jacobi V(2,2) cycles, a residual norm after each; {t:.1f} s each) on {cores} host threads "
+                      f"(OpenMP build)"}
 
 
 def cpu_baseline_c4(ms_, seed, budget_s=25.0):
@@ -534,12 +585,13 @@ def cpu_baseline_c4(ms_, seed, budget_s=25.0):
     import synth
     import oracle
     P = len(ms_)
+    cores = oracle_cores()
     per_m, t_all = {}, 0.0
     for m in sorted(set(int(x) for x in ms_)):
         p = int(np.nonzero(ms_ == m)[0][0])
         n = (1 << m) + 1
         H = oracle.Hierarchy(2, n, knode=synth.lognormal_k(2, n, seed ^ p ^ 0x10000), smoother=oracle.RBGS,
-                             omega=1.0, nu1=2, nu2=1)
+                             omega=1.0, nu1=2, nu2=1, mt=True)
         H.set_rhs(synth.uniform_rhs(2, n, seed ^ p))
         t0 = time.perf_counter()
         rho = H.solve(1e-8, 60)
@@ -550,7 +602,7 @@ def cpu_baseline_c4(ms_, seed, budget_s=25.0):
             break
     est = sum(per_m[m]["s"] * int((ms_ == m).sum()) for m in per_m)
     done = sum(int((ms_ == m).sum()) for m in per_m)
-    return {"value": done / est, "unit": "problems/s", "cores": 1, "kind": "oracle",
+    return {"value": done / est, "unit": "problems/s", "cores": cores, "kind": "oracle",
             "sample": f"one problem per size m in {sorted(per_m)} solved by the oracle (FP64 RBGS V(2,1) to 1e-8), "
                       f"times weighted by the {done} of {P} problems of those sizes",
             "per_size": {str(m): v for m, v in per_m.items()}}
@@ -561,13 +613,14 @@ def cpu_baseline_c5(reqs, budget_s=25.0):
     in arrival order, until the time budget is spent."""
     import synth
     import oracle
+    cores = oracle_cores()
     done, t_all = 0, 0.0
     for r in reqs[:200]:
         dim, n = r["dim"], r["n"]
         if dim == 2:
-            H = oracle.Hierarchy(2, n, smoother=oracle.RBGS, omega=1.0, nu1=2, nu2=1)
+            H = oracle.Hierarchy(2, n, smoother=oracle.RBGS, omega=1.0, nu1=2, nu2=1, mt=True)
         else:
-            H = oracle.Hierarchy(3, n, smoother=oracle.JACOBI, omega=6.0 / 7.0, nu1=2, nu2=2)
+            H = oracle.Hierarchy(3, n, smoother=oracle.JACOBI, omega=6.0 / 7.0, nu1=2, nu2=2, mt=True)
         H.set_rhs(synth.uniform_rhs(dim, n, r["seed"]))
         t0 = time.perf_counter()
         H.solve(r["tol"], 100)
@@ -576,9 +629,10 @@ def cpu_baseline_c5(reqs, budget_s=25.0):
         del H
         if t_all > budget_s:
             break
-    return {"value": done / t_all, "unit": "solves/s", "cores": 1, "kind": "oracle",
+    return {"value": done / t_all, "unit": "solves/s", "cores": cores, "kind": "oracle",
             "sample": f"the first {done} requests of the same arrival stream, each solved alone by the oracle "
-                      "(FP64, 2D RBGS V(2,1) / 3D Jacobi V(2,2)) to its tolerance, one after another"}
+                      f"(FP64, 2D RBGS V(2,1) / 3D Jacobi V(2,2)) to its tolerance, one after another, each on {cores} "
+                      "host threads (OpenMP build)"}
 
 
 # ------------------------------------------------------------------ other configurations
@@ -647,15 +701,26 @@ def run_c3(args):
     f = torch.from_numpy(synth.normal_rhs(3, n, 0x5EED0003)).cuda()
     kw = dict(smoother="jacobi", omega=6.0 / 7.0, nu1=2, nu2=2, maxit=80)
     best, table = autotune.tune(3, n, f, 1e-10, {"inner_cycles": [1, 2, 3]}, base=dict(kw, precision="bf16_dc"))
-    res = {}
+    res, sols = {}, {}
     for prec, extra in (("bf16_dc", {"inner_cycles": best["inner_cycles"]}), ("fp32_dc", {"inner_cycles": best["inner_cycles"]}), ("fp64", {})):
         s = Solver(3, n, precision=prec, **kw, **extra)
         ms, it = autotune.time_solve(s, f, 1e-10, reps=max(1, args.steps))
         res[prec] = {"time_to_tol_s": ms / 1e3, "steps": it}
+        sols[prec] = s.get_solution()
         s.close()
         del s
     ms = res["bf16_dc"]["time_to_tol_s"] * 1e3
-    extra = {} if args.no_cpu_baseline else {"cpu_baseline": cpu_baseline_c3(res["fp64"]["steps"])}
+    extra = {}
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle_cores()
+        fh = synth.normal_rhs(3, n, 0x5EED0003)
+        H = oracle.Hierarchy(3, n, smoother=oracle.JACOBI, omega=6.0 / 7.0, nu1=2, nu2=2, mt=True)
+        H.set_rhs(fh)
+        extra["cpu_baseline"] = cpu_baseline_c3(H, fh)
+        extra["final_error_vs_oracle"] = final_error_vs_oracle(sols, H, fh, maxit=40)
+        del H
+    del sols
     extra["lfa"] = lfa_summary(3, "jacobi", 6.0 / 7.0, 2, 2)
     _line(METRIC, 1e3 / ms, "solves/s (to 1e-10 rel. residual; 1/time-to-1e-10)", True, ms, args,
           {"workload": "3D Poisson 513^3, f ~ N(0,1) (seed 0x5EED0003), Jacobi omega=6/7 V(2,2), full weighting, "

@@ -35,8 +35,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRCS = [os.path.join(_HERE, "mg_oracle.c"), os.path.join(_HERE, "cc_oracle.c"), os.path.join(_HERE, "cd_oracle.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
+_SO_MT = os.path.join(_BUILD, "liboracle_mt.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 RBGS = 0
 JACOBI = 1
@@ -44,22 +45,27 @@ JACOBI = 1
 _D = ctypes.POINTER(ctypes.c_double)
 
 
-def build(force: bool = False) -> str:
-    """Compiles the C sources into oracle/_build/liboracle.so (gcc, FP64, no FMA)."""
+def build(force: bool = False, mt: bool = False) -> str:
+    """Compiles the C sources into oracle/_build/liboracle.so (gcc, FP64, no
+    FMA); mt=True builds the timing variant liboracle_mt.so with -fopenmp
+    (the same loops, independent ones shared out over the host cores; the
+    same numbers bit for bit)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(os.path.getmtime(x) for x in _SRCS):
-        tmp = _SO + f".tmp{os.getpid()}"
+    so = _SO_MT if mt else _SO
+    if force or not os.path.exists(so) or os.path.getmtime(so) < max(os.path.getmtime(x) for x in _SRCS):
+        tmp = so + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-std=c11", "-shared", "-fPIC",
-                               *_SRCS, "-o", tmp, "-lm"])
-        os.replace(tmp, _SO)
-    return _SO
+                               *(["-fopenmp"] if mt else []), *_SRCS, "-o", tmp, "-lm"])
+        os.replace(tmp, so)
+    return so
 
 
-def lib():
-    global _lib
+def lib(mt: bool = False):
+    """The serial oracle library (mt=False, the parity oracle) or its OpenMP
+    timing build (mt=True)."""
     with _lock:
-        if _lib is None:
-            L = ctypes.CDLL(build())
+        if mt not in _libs:
+            L = ctypes.CDLL(build(mt=mt))
             vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
             sig = {
                 "or_apply": (None, [i, i, _D, _D, _D, _D, _D, _D]),
@@ -121,13 +127,30 @@ def lib():
                 "cd_vcycle": (None, [vp]),
                 "cd_residual_norm": (d, [vp]),
                 "cd_time_step": (i, [vp, _D, d, i, _D]),
+                "or_set_threads": (None, [i]),
+                "or_threads": (i, []),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
                 fn.restype = res
                 fn.argtypes = args
-            _lib = L
-    return _lib
+            _libs[mt] = L
+    return _libs[mt]
+
+
+def set_threads(n: int) -> int:
+    """Threads of the OpenMP timing build; returns the count it will use."""
+    L = lib(mt=True)
+    L.or_set_threads(int(n))
+    return int(L.or_threads())
+
+
+def host_cores() -> int:
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 def _p(a):
@@ -175,12 +198,12 @@ def diag(dim, n, c=None, faces=None):
     return out
 
 
-def residual(u, f, c=None, faces=None):
+def residual(u, f, c=None, faces=None, mt=False):
     u, f = _grid(u), _grid(f)
     dim, n = u.ndim, u.shape[0]
     r = np.empty_like(u)
     c3, fs = _c3(c), _faces(faces, dim)
-    lib().or_residual(dim, n, _p(c3), _p(fs[0]), _p(fs[1]), _p(fs[2]), _p(u), _p(f), _p(r))
+    lib(mt).or_residual(dim, n, _p(c3), _p(fs[0]), _p(fs[1]), _p(fs[2]), _p(u), _p(f), _p(r))
     return r
 
 
@@ -235,9 +258,9 @@ def coarsen_faces(faces):
     return out[:dim]
 
 
-def norm(r):
+def norm(r, mt=False):
     r = _grid(r)
-    return lib().or_norm(r.ndim, r.shape[0], _p(r))
+    return lib(mt).or_norm(r.ndim, r.shape[0], _p(r))
 
 
 def dense_solve(f, u_boundary=None, c=None, faces=None):
@@ -255,65 +278,67 @@ def dense_solve(f, u_boundary=None, c=None, faces=None):
 # ---------------- hierarchy ----------------
 
 class Hierarchy:
-    """A grid hierarchy with V-cycle, solve loop and FP64 defect correction."""
+    """A grid hierarchy with V-cycle, solve loop and FP64 defect correction.
+    mt=True runs it on the OpenMP timing build (bitwise the same results)."""
 
     def __init__(self, dim, n, c=None, knode=None, coarsest_n=3, smoother=RBGS, omega=1.0,
-                 nu1=2, nu2=1):
+                 nu1=2, nu2=1, mt=False):
         self.dim, self.n = dim, n
+        self._L = lib(mt)
         self._k = None if knode is None else _grid(knode, dim)
         self._c3 = _c3(c)
-        self.h = lib().or_create(dim, n, _p(self._c3), _p(self._k), coarsest_n, smoother,
-                                 float(omega), nu1, nu2)
+        self.h = self._L.or_create(dim, n, _p(self._c3), _p(self._k), coarsest_n, smoother,
+                                   float(omega), nu1, nu2)
         if not self.h:
             raise ValueError("invalid hierarchy parameters")
-        self.levels = lib().or_levels(self.h)
+        self.levels = self._L.or_levels(self.h)
 
     def __del__(self):
         h = getattr(self, "h", None)
         if h:
-            lib().or_destroy(h)
+            self._L.or_destroy(h)
             self.h = None
 
     def level_n(self, l):
-        return lib().or_level_n(self.h, l)
+        return self._L.or_level_n(self.h, l)
 
     def faces(self, l):
         if self._k is None:
             return None
         nl = self.level_n(l)
         out = [np.empty((nl,) * self.dim) for _ in range(self.dim)] + [None] * (3 - self.dim)
-        lib().or_get_faces(self.h, l, _p(out[0]), _p(out[1]), _p(out[2]))
+        self._L.or_get_faces(self.h, l, _p(out[0]), _p(out[1]), _p(out[2]))
         return out[:self.dim]
 
     def set_rhs(self, f):
         f = _grid(f, self.dim)
-        lib().or_set_rhs(self.h, _p(f))
+        self._L.or_set_rhs(self.h, _p(f))
 
     def set_u(self, u):
         u = _grid(u, self.dim)
-        lib().or_set_u(self.h, _p(u))
+        self._L.or_set_u(self.h, _p(u))
 
     def get_u(self):
         u = np.empty((self.n,) * self.dim)
-        lib().or_get_u(self.h, _p(u))
+        self._L.or_get_u(self.h, _p(u))
         return u
 
     def vcycle(self):
-        lib().or_vcycle(self.h)
+        self._L.or_vcycle(self.h)
 
     def residual_norm(self):
-        return lib().or_residual_norm(self.h)
+        return self._L.or_residual_norm(self.h)
 
     def solve(self, tol, maxit):
         """Returns the relative residual history rho[0..k] (rho[0] = 1)."""
         rho = np.zeros(maxit + 1)
-        k = lib().or_solve(self.h, float(tol), int(maxit), _p(rho))
+        k = self._L.or_solve(self.h, float(tol), int(maxit), _p(rho))
         return rho[:k + 1]
 
     def dc_solve(self, tol, maxit):
         """Defect correction with an FP64 inner V-cycle; rho[0..k]."""
         rho = np.zeros(maxit + 1)
-        k = lib().or_dc_solve(self.h, float(tol), int(maxit), _p(rho))
+        k = self._L.or_dc_solve(self.h, float(tol), int(maxit), _p(rho))
         return rho[:k + 1]
 
 

@@ -22,10 +22,22 @@
  * definitions of Sec. 2.3 (Algorithm 1 and the component list beneath it)
  * and the Layer-4 pseudo code of Sec. 2.4 (VCycle, GaussSeidel, Restrict,
  * interpolatecorr). Parity pins for each routine live in tests/.
+ *
+ * Timing build. Compiled a second time with -fopenmp (liboracle_mt.so), the
+ * loops marked PAR_FOR_INTERIOR run over all host cores: only loops whose
+ * points are independent (one colour of a red-black sweep - a 5-/7-point
+ * stencil couples a node only to the other colour -, a Jacobi sweep, the
+ * residual, the transfers, fills), and the pairwise norm sum evaluates the
+ * same tree with its subtrees as tasks. So both builds compute bitwise the
+ * same numbers (tests/ checks this); without -fopenmp the pragmas are
+ * ignored and every loop is the plain serial loop.
  */
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef struct {
   int dim, n;
@@ -84,13 +96,46 @@ static double diag_at(const Op *op, long p) {
         __VA_ARGS__                                                   \
       }
 
+/* The same loop, its (k, j) iterations shared out over threads in the
+ * OpenMP build; only for loops whose iterations are independent. */
+#define PAR_FOR_INTERIOR(dim, n, ...)                        \
+  _Pragma("omp parallel for collapse(2) schedule(static)") \
+  FOR_INTERIOR(dim, n, __VA_ARGS__)
+
+static void fill0(double *a, long N) {
+#pragma omp parallel for schedule(static)
+  for (long q = 0; q < N; q++) a[q] = 0.0;
+}
+
+static void copy_to(double *dst, const double *src, long N) {
+#pragma omp parallel for schedule(static)
+  for (long q = 0; q < N; q++) dst[q] = src[q];
+}
+
+/* Threads of the OpenMP build (1 in the serial build). */
+void or_set_threads(int nt) {
+#ifdef _OPENMP
+  if (nt > 0) omp_set_num_threads(nt);
+#else
+  (void)nt;
+#endif
+}
+
+int or_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
 /* ---------------- stateless level operators ---------------- */
 
 void or_apply(int dim, int n, const double *c, const double *kx, const double *ky,
               const double *kz, const double *u, double *out) {
   Op op = make_op(dim, n, c, kx, ky, kz);
-  memset(out, 0, sizeof(double) * npts(dim, n));
-  FOR_INTERIOR(dim, n, { out[p] = apply_at(&op, u, p); })
+  fill0(out, npts(dim, n));
+  PAR_FOR_INTERIOR(dim, n, { out[p] = apply_at(&op, u, p); })
 }
 
 void or_diag(int dim, int n, const double *c, const double *kx, const double *ky,
@@ -104,8 +149,8 @@ void or_diag(int dim, int n, const double *c, const double *kx, const double *ky
 void or_residual(int dim, int n, const double *c, const double *kx, const double *ky,
                  const double *kz, const double *u, const double *f, double *r) {
   Op op = make_op(dim, n, c, kx, ky, kz);
-  memset(r, 0, sizeof(double) * npts(dim, n));
-  FOR_INTERIOR(dim, n, { r[p] = f[p] - apply_at(&op, u, p); })
+  fill0(r, npts(dim, n));
+  PAR_FOR_INTERIOR(dim, n, { r[p] = f[p] - apply_at(&op, u, p); })
 }
 
 /* One omega red-black Gauss-Seidel sweep (Sec. 2.4 GaussSeidel, "order rb"):
@@ -113,7 +158,7 @@ void or_residual(int dim, int n, const double *c, const double *kx, const double
  * (i+j[+k] even), then over black nodes. */
 static void rbgs_sweep(const Op *op, double omega, double *u, const double *f) {
   for (int color = 0; color < 2; color++) {
-    FOR_INTERIOR(op->dim, op->n, {
+    PAR_FOR_INTERIOR(op->dim, op->n, {
       if (((i + j + k) & 1) == color)
         u[p] += omega * (f[p] - apply_at(op, u, p)) / diag_at(op, p);
     })
@@ -122,8 +167,8 @@ static void rbgs_sweep(const Op *op, double omega, double *u, const double *f) {
 
 /* One omega-Jacobi sweep: every interior node is updated from the old iterate. */
 static void jacobi_sweep(const Op *op, double omega, double *u, const double *f, double *tmp) {
-  memcpy(tmp, u, sizeof(double) * npts(op->dim, op->n));
-  FOR_INTERIOR(op->dim, op->n, {
+  copy_to(tmp, u, npts(op->dim, op->n));
+  PAR_FOR_INTERIOR(op->dim, op->n, {
     u[p] = tmp[p] + omega * (f[p] - apply_at(op, tmp, p)) / diag_at(op, p);
   })
 }
@@ -151,8 +196,8 @@ static double fw_w(int a) { return a == 0 ? 0.5 : 0.25; }
  * coarse boundary is 0. */
 void or_restrict(int dim, int nf, const double *r, double *fc) {
   int nc = (nf - 1) / 2 + 1;
-  memset(fc, 0, sizeof(double) * npts(dim, nc));
-  FOR_INTERIOR(dim, nc, {
+  fill0(fc, npts(dim, nc));
+  PAR_FOR_INTERIOR(dim, nc, {
     double acc = 0.0;
     int cmin = dim == 3 ? -1 : 0, cmax = dim == 3 ? 1 : 0;
     for (int cz = cmin; cz <= cmax; cz++)
@@ -173,7 +218,7 @@ void or_restrict(int dim, int nf, const double *r, double *fc) {
  * dimensions. */
 void or_prolong_add(int dim, int nc, const double *e, double *u) {
   int nf = 2 * (nc - 1) + 1;
-  FOR_INTERIOR(dim, nf, {
+  PAR_FOR_INTERIOR(dim, nf, {
     int idx[3] = {i, j, k};
     int lo[3], cnt[3];
     for (int d = 0; d < 3; d++) {
@@ -265,11 +310,41 @@ static double pairwise(const double *x, long m) {
   return pairwise(x, h) + pairwise(x + h, m - h);
 }
 
+#ifdef _OPENMP
+/* The pairwise tree of pairwise(), its upper `depth` levels split into tasks. */
+static double pairwise_tasks(const double *x, long m, int depth) {
+  if (depth <= 0 || m <= 8) return pairwise(x, m);
+  long h = m / 2;
+  double a = 0.0, b;
+#pragma omp task shared(a)
+  a = pairwise_tasks(x, h, depth - 1);
+  b = pairwise_tasks(x + h, m - h, depth - 1);
+#pragma omp taskwait
+  return a + b;
+}
+#endif
+
+static double sum_pairwise(const double *x, long m) {
+#ifdef _OPENMP
+  double s = 0.0;
+#pragma omp parallel
+#pragma omp single
+  s = pairwise_tasks(x, m, 8);
+  return s;
+#else
+  return pairwise(x, m);
+#endif
+}
+
 double or_norm(int dim, int n, const double *r) {
-  long m = (long)(n - 2) * (n - 2) * (dim == 3 ? (n - 2) : 1), q = 0;
+  long m = (long)(n - 2) * (n - 2) * (dim == 3 ? (n - 2) : 1);
   double *sq = (double *)malloc(sizeof(double) * (m > 0 ? m : 1));
-  FOR_INTERIOR(dim, n, { sq[q++] = r[p] * r[p]; })
-  double s = pairwise(sq, m);
+  /* sq in natural order: interior node (i, j, k) at its lexicographic index */
+  PAR_FOR_INTERIOR(dim, n, {
+    long q = (i - 1) + (long)(n - 2) * ((j - 1) + (long)(n - 2) * (dim == 3 ? k - 1 : 0));
+    sq[q] = r[p] * r[p];
+  })
+  double s = sum_pairwise(sq, m);
   free(sq);
   return sqrt(s);
 }
@@ -496,10 +571,10 @@ static void vcycle(Hier *H, int l) {
   Level *C = &H->lv[l + 1];
   Op op = level_op(H, l);
   smooth(H, l, H->nu1);
-  memset(L->r, 0, sizeof(double) * npts(H->dim, L->n));
-  FOR_INTERIOR(H->dim, L->n, { L->r[p] = L->f[p] - apply_at(&op, L->u, p); })
+  fill0(L->r, npts(H->dim, L->n));
+  PAR_FOR_INTERIOR(H->dim, L->n, { L->r[p] = L->f[p] - apply_at(&op, L->u, p); })
   or_restrict(H->dim, L->n, L->r, C->f);
-  memset(C->u, 0, sizeof(double) * npts(H->dim, C->n));
+  fill0(C->u, npts(H->dim, C->n));
   vcycle(H, l + 1);
   or_prolong_add(H->dim, C->n, C->u, L->u);
   smooth(H, l, H->nu2);
@@ -511,8 +586,8 @@ double or_residual_norm(void *h) {
   Hier *H = (Hier *)h;
   Level *L = &H->lv[0];
   Op op = level_op(H, 0);
-  memset(L->r, 0, sizeof(double) * npts(H->dim, L->n));
-  FOR_INTERIOR(H->dim, L->n, { L->r[p] = L->f[p] - apply_at(&op, L->u, p); })
+  fill0(L->r, npts(H->dim, L->n));
+  PAR_FOR_INTERIOR(H->dim, L->n, { L->r[p] = L->f[p] - apply_at(&op, L->u, p); })
   return or_norm(H->dim, L->n, L->r);
 }
 
@@ -547,17 +622,17 @@ int or_dc_solve(void *h, double tol, int maxit, double *rho) {
   double r0 = -1.0;
   int it = 0;
   for (;; it++) {
-    memset(L->r, 0, sizeof(double) * N);
-    FOR_INTERIOR(dim, n, { L->r[p] = H->fo[p] - apply_at(&op, H->uo, p); })
+    fill0(L->r, N);
+    PAR_FOR_INTERIOR(dim, n, { L->r[p] = H->fo[p] - apply_at(&op, H->uo, p); })
     double s = or_norm(dim, n, L->r);
     if (r0 < 0.0) r0 = s;
     rho[it] = r0 > 0.0 ? s / r0 : 0.0;
     if (it >= maxit || !(rho[it] > tol) || s == 0.0) break;
-    memset(L->f, 0, sizeof(double) * N);
-    FOR_INTERIOR(dim, n, { L->f[p] = L->r[p] / s; })
-    memset(L->u, 0, sizeof(double) * N);
+    fill0(L->f, N);
+    PAR_FOR_INTERIOR(dim, n, { L->f[p] = L->r[p] / s; })
+    fill0(L->u, N);
     vcycle(H, 0);
-    FOR_INTERIOR(dim, n, { H->uo[p] += s * L->u[p]; })
+    PAR_FOR_INTERIOR(dim, n, { H->uo[p] += s * L->u[p]; })
   }
   memcpy(L->u, H->uo, sizeof(double) * N);
   memcpy(L->f, H->fo, sizeof(double) * N);

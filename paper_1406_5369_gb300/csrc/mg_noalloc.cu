@@ -30,25 +30,6 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 double *g_scratch[kMaxDevices] = {};
 
-
-template <int DIM>
-__global__ void k_partials_dense(const double *__restrict__ u, const double *__restrict__ f, mg::Geo g,
-                                 mg::Sten<double> s, double *__restrict__ partials) {
-  int m = g.n - 2;
-  long long total = (long long)m * m * (DIM == 3 ? m : 1);
-  double acc = 0.0;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    long long p = mg::interior_node<DIM>(t, m, g);
-    double Au, dg;
-    mg::apply_at<DIM, false>(u, p, g, s, Au, dg);
-    double r = f[p] - Au;
-    acc += r * r;
-  }
-  acc = mg::block_sum(acc);
-  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
-}
-
 // One block: strided sequential sums per thread, then a fixed tree.
 __global__ void k_finalize_dense(const double *__restrict__ partials, int nb, double *__restrict__ result) {
   __shared__ double buf[1024];
@@ -94,6 +75,7 @@ mg_status scratch_ptr(double **out) {
 
 extern "C" mg_status mg_residual_norm_noalloc(int dim, int n, const mg_const_stencil *stencil, const double *u,
                                               const double *f, double *out, void *stream) {
+  mg::set_error_message("");
   if (dim != 2 && dim != 3) return nfail(MG_EINVAL, "dim must be 2 or 3");
   if (n < 3) return nfail(MG_EINVAL, "n must be at least 3");
   if (!u || !f || !out) return nfail(MG_EINVAL, "NULL argument");
@@ -109,6 +91,7 @@ extern "C" mg_status mg_residual_norm_noalloc(int dim, int n, const mg_const_ste
     c[0] = stencil->cx;
     c[1] = stencil->cy;
     c[2] = dim == 3 ? stencil->cz : 1.0;
+    if (!(c[0] > 0 && c[1] > 0 && c[2] > 0)) return nfail(MG_EINVAL, "stencil coefficients must be > 0");
   }
   double *scratch = nullptr;
   mg_status st = scratch_ptr(&scratch);
@@ -128,8 +111,10 @@ extern "C" mg_status mg_residual_norm_noalloc(int dim, int n, const mg_const_ste
   sten.diag = 2.0 * (c[0] + c[1] + (dim == 3 ? c[2] : 0.0)) * sten.inv_h2;
   double *partials = scratch;
   double *result = scratch + kMaxPartials;
-  if (dim == 2) k_partials_dense<2><<<(unsigned)nb, kThreads, 0, s>>>(u, f, g, sten, partials);
-  else k_partials_dense<3><<<(unsigned)nb, kThreads, 0, s>>>(u, f, g, sten, partials);
+  // the library's own partial-sum kernel (one partial per block, fixed
+  // per-block order), pointed at the static scratch
+  if (dim == 2) mg::k_norm_partials<2, double, false><<<(unsigned)nb, kThreads, 0, s>>>(u, f, g, sten, partials);
+  else mg::k_norm_partials<3, double, false><<<(unsigned)nb, kThreads, 0, s>>>(u, f, g, sten, partials);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return nfail(MG_ECUDA, "partial-sum kernel launch", e);
   k_finalize_dense<<<1, 1024, 0, s>>>(partials, (int)nb, result);

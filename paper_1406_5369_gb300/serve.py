@@ -39,7 +39,8 @@ class Server:
         self.params = {d: dict(DEFAULT_PARAMS[d], **((params or {}).get(d, {}))) for d in (2, 3)}
         self.maxit = maxit
         self.device = device
-        self.batches = {d: BatchSolver(max_active) for d in (2, 3)}
+        self.max_active = int(max_active)
+        self.batches = {d: BatchSolver(self.max_active) for d in (2, 3)}
         self.pool = collections.defaultdict(list)  # (dim, n) -> idle Solvers
         self.used = 0.0                            # bytes of every live hierarchy (active + pooled)
         self.active = {}                           # request id -> dict
@@ -84,17 +85,30 @@ class Server:
         return s, True
 
     # ---- requests
+    def _members(self, dim):
+        return sum(1 for a in self.active.values() if a["req"]["dim"] == dim)
+
     def admit(self, req):
-        """Returns True if the request got a hierarchy and joined its batch."""
+        """Returns True if the request got a hierarchy and joined its batch;
+        False (the request keeps waiting) while its batch has no free slot or
+        its hierarchy does not fit the memory budget."""
         import synth
-        s, _ = self._acquire(req["dim"], req["n"])
+        dim = req["dim"]
+        if self._members(dim) >= self.max_active:
+            return False
+        s, _ = self._acquire(dim, req["n"])
         if s is None:
             return False
-        f = synth.torch_uniform_rhs(req["dim"], req["n"], req["seed"], device=self.device)
-        s.set_rhs(f)
-        s.set_solution(None)
-        del f
-        pid = self.batches[req["dim"]].add(s)
+        try:
+            f = synth.torch_uniform_rhs(dim, req["n"], req["seed"], device=self.device)
+            s.set_rhs(f)
+            s.set_solution(None)
+            del f
+            pid = self.batches[dim].add(s)
+        except Exception:
+            # the hierarchy goes back to the pool (still counted in self.used)
+            self.pool[(dim, req["n"])].append(s)
+            return False
         self.active[req["id"]] = {"req": req, "solver": s, "pid": pid, "steps": 0}
         return True
 

@@ -2,8 +2,9 @@
 
 - The reference arm (the oracle, timed on the host) prints one JSON line with
   the contract's keys: impl = reference, the arm's metric and unit, a
-  cpu_baseline describing the run and an e2e object with zero copy bytes.
-  The workload is shrunk to 129^2 here so that the check takes a second.
+  cpu_baseline describing the run (whole solves on every host core) and an
+  e2e object with zero copy bytes. The workload is shrunk to 129^2 here so
+  that the check takes a second.
 - The autotuner searches one knob at a time (each knob tuned with the others
   at their best so far), keeps the fastest candidate, and serves a repeated
   request for the same problem from its cache without timing again.
@@ -35,7 +36,9 @@ def test_reference_arm_prints_the_contract_line(monkeypatch):
         assert key in rec, key
     assert rec["impl"] == "reference" and rec["metric"] == bench.METRIC and rec["higher_is_better"] is True
     assert rec["value"] > 0 and abs(rec["value"] * rec["ms_per_step"] - 1e3) < 1e-6 * 1e3
-    assert rec["cpu_baseline"]["kind"] == "oracle" and rec["cpu_baseline"]["cores"] == 1
+    import oracle
+    assert rec["cpu_baseline"]["kind"] == "oracle" and rec["cpu_baseline"]["cores"] == oracle.host_cores()
+    assert "whole FP64 oracle solve" in rec["cpu_baseline"]["sample"]
     assert rec["e2e"]["h2d_bytes_per_step"] == 0 and rec["e2e"]["d2h_bytes_per_step"] == 0
     assert (rec["steps"], rec["warmup"]) == (2, 1)
 
@@ -96,3 +99,25 @@ def test_lfa_summary_of_the_3d_jacobi_cycle():
     assert 0.2 < out["rho_two_grid_configured"] < 0.3
     assert out["rho_two_grid_lfa"] <= out["rho_two_grid_configured"] + 1e-12
     assert 0.5 <= out["omega_lfa"] <= 1.0
+
+
+def test_final_error_against_the_converged_oracle():
+    # a solution perturbed by a known vector: the reported relative error is
+    # that vector's size, and the guaranteed bound from the residual covers it
+    import numpy as np
+    import oracle
+    import synth
+    n = 129
+    f = synth.uniform_rhs(2, n, 5)
+    H = oracle.Hierarchy(2, n, mt=True)
+    H.set_rhs(f)
+    H.solve(1e-13, 30)
+    us = H.get_u()
+    d = np.zeros_like(us)
+    d[1:-1, 1:-1] = 1e-9 * np.max(np.abs(us)) * np.sin(np.arange(n - 2))[None, :]
+    out = bench.final_error_vs_oracle({"x": us + d, "same": us.copy()}, H, f)
+    assert out["same"]["rel_l2"] <= 1e-15 and out["same"]["rel_max"] <= 1e-15
+    want = np.sqrt(np.sum(d * d)) / np.sqrt(np.sum(us * us))
+    assert abs(out["x"]["rel_l2"] - want) <= 1e-3 * want
+    assert out["x"]["rel_l2"] <= out["x"]["rel_l2_bound"]
+    assert out["oracle"]["relres"] <= 1e-12

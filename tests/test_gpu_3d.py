@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import OP_TOL, interior, need_gpu, rel_err, zero_boundary
+from gpu_util import OP_TOL, error_vs_converged_oracle, interior, need_gpu, rel_err, zero_boundary
 
 pytestmark = pytest.mark.gpu
 
@@ -103,5 +103,13 @@ def test_fullsize_config3_bf16_dc_reaches_tolerance():
     it, rr, _ = s.solve(1e-10)
     assert rr <= 1e-10
     u = s.get_solution()
-    rel = oracle.norm(oracle.residual(u, f)) / oracle.norm(f)
+    del s
+    rel = oracle.norm(oracle.residual(u, f, mt=True), mt=True) / oracle.norm(f, mt=True)
     assert rel <= 1.01e-10, rel
+    # final error against the oracle's FP64 solution converged from zero,
+    # within the guaranteed bound (residuals of both over lambda_min(A))
+    err, bound, orr = error_vs_converged_oracle(u, f, maxit=40, smoother=oracle.JACOBI, omega=6.0 / 7.0,
+                                                nu1=2, nu2=2)
+    print(f"513^3 BF16-DC: rel l2 error vs oracle {err:.3e} (bound {bound:.3e}, oracle relres {orr:.2e})")
+    assert orr <= 1e-12
+    assert err <= bound, (err, bound)

@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import need_gpu, rel_err
+from gpu_util import error_vs_converged_oracle, need_gpu, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -112,6 +112,13 @@ def test_fullsize_config2_fp32_dc_reaches_tolerance():
     # the oracle recomputes the FP64 residual of the GPU solution
     rel = oracle.norm(oracle.residual(u, f)) / oracle.norm(f)
     assert rel <= 1.01e-10, rel
+    # final error against the oracle's FP64 solution converged from zero (to
+    # 1e-13, or as far as FP64 rounding lets the residual fall at this size):
+    # within the guaranteed bound (residuals of both over lambda_min(A))
+    err, bound, orr = error_vs_converged_oracle(u, f, maxit=20)
+    print(f"8193^2 FP32-DC: rel l2 error vs oracle {err:.3e} (bound {bound:.3e}, oracle relres {orr:.2e})")
+    assert orr <= 1e-12
+    assert err <= bound, (err, bound)
 
 
 @pytest.mark.parametrize("n,nu1,nu2,omega", [(65, 2, 1, 1.0), (257, 1, 2, 1.2), (1025, 2, 1, 1.0), (513, 2, 2, 0.9)])

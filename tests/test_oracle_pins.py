@@ -524,7 +524,6 @@ def test_coarse_faces_conserve_parallel_conductance():
     fine_rows = faces[0][1:nf - 1, 5]           # x-face values of the interior rows
     coarse_rows = cf[0][1:(nf - 1) // 2, 2]     # interior coarse rows
     lhs = coarse_rows.sum() * 2 * h
-    rhs = fine_rows.sum() * h - 0.5 * h * (fine_rows[0] + fine_rows[-1]) * 0.5  # rows 1, nf-2 enter once, at 1/4
     rhs = h * (0.5 * fine_rows[1:-1].sum() + 0.25 * fine_rows[0] + 0.25 * fine_rows[-1]) * 2
     assert lhs == pytest.approx(rhs, rel=1e-13)
 

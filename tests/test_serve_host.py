@@ -33,11 +33,18 @@ class FakeSolver:
 
 
 class FakeBatch:
+    fail_next_add = False
+
     def __init__(self, max_active):
+        self.max_active = max_active
         self.live = {}
         self.next = 0
 
     def add(self, s):
+        # like mg_batch_add: MG_ENOMEM (raised by the binding) when every slot is taken
+        if len(self.live) >= self.max_active or FakeBatch.fail_next_add:
+            FakeBatch.fail_next_add = False
+            raise RuntimeError("batch is full")
         self.next += 1
         self.live[self.next] = [s, 0]
         return self.next
@@ -62,8 +69,8 @@ def server(monkeypatch):
     monkeypatch.setattr(synth, "torch_uniform_rhs", lambda dim, n, seed, device=None: None)
     FakeSolver.created = []
 
-    def make(budget):
-        srv = serve.Server(budget_bytes=budget, device="cpu")
+    def make(budget, max_active=2048):
+        srv = serve.Server(budget_bytes=budget, max_active=max_active, device="cpu")
         FakeSolver.bytes_of = srv._bytes
         return srv
     return make
@@ -107,3 +114,29 @@ def test_run_serves_everything_and_rejects_what_can_never_fit(server):
     assert sorted(d["id"] for d in done) == list(range(12))
     assert all(d["latency"] >= 0 and d["relres"] <= d["tol"] for d in done)
     assert stats["peak_hbm_gb"] * 1e9 <= srv.budget
+
+
+def test_admission_waits_for_a_free_slot(server):
+    """More requests than batch slots: the surplus waits (no exception, no
+    leaked hierarchy) and is admitted as retiring requests free their slots."""
+    srv = server(1e15, max_active=3)
+    assert all(srv.admit(req(i, 2, 65)) for i in range(3))
+    n_created, used = len(FakeSolver.created), srv.used
+    assert not srv.admit(req(3, 2, 65))  # batch full: waits, takes no hierarchy
+    assert len(FakeSolver.created) == n_created and srv.used == used
+    assert srv.admit(req(4, 3, 33))  # the other dimension's batch has room
+    reqs = [req(10 + i, 2, 65 if i % 2 else 129, t=0.0) for i in range(20)]
+    srv2 = server(1e15, max_active=4)
+    done, stats = srv2.run(reqs, max_wall=30.0)
+    assert stats["completed"] == 20 and stats["unfinished"] == 0
+    assert sorted(d["id"] for d in done) == [10 + i for i in range(20)]
+
+
+def test_failed_batch_add_returns_the_hierarchy_to_the_pool(server):
+    srv = server(1e15, max_active=8)
+    FakeBatch.fail_next_add = True
+    assert not srv.admit(req(0, 2, 65))
+    assert srv.pool[(2, 65)] and not srv.active
+    n_created = len(FakeSolver.created)
+    assert srv.admit(req(0, 2, 65))  # retried: reuses the pooled hierarchy
+    assert len(FakeSolver.created) == n_created and srv.used == srv._bytes(2, 65)

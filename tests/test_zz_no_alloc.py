@@ -68,6 +68,37 @@ def test_noalloc_norm_result_into_device_memory_and_stencil():
         assert abs(float(out.item()) - want) <= NORM_RTOL * want
 
 
+@pytest.mark.parametrize("dim,n,sten", [(3, 65, (1.0, 0.5, 2.0)), (3, 257, None), (2, 8193, None)])
+def test_noalloc_norm_3d_anisotropic_and_largest_grids(dim, n, sten):
+    """The cz term of the 3D stencil, and the largest accepted grids: 3D n = 257
+    (8,097 partial sums) and 2D n = 8193 (32,761 of the 32,768 slots, so the
+    finalize loop reads to the end of the static array, next to the result slot)."""
+    torch = need_gpu()
+    from paper_1406_5369_gb300 import Solver, _capi
+    lib = _capi.load()
+    cs = None if sten is None else _capi.mg_const_stencil(*sten)
+    s = Solver(dim, n, **({} if sten is None else {"stencil": sten}))
+    gen = torch.Generator(device="cuda").manual_seed(77 + n)
+    ud = torch.rand((n,) * dim, dtype=torch.float64, device="cuda", generator=gen)
+    if dim == 2:
+        ud[0, :] = ud[-1, :] = ud[:, 0] = ud[:, -1] = 0
+    else:
+        ud[0], ud[-1], ud[:, 0], ud[:, -1], ud[:, :, 0], ud[:, :, -1] = 0, 0, 0, 0, 0, 0
+    fd = 2 * torch.rand((n,) * dim, dtype=torch.float64, device="cuda", generator=gen) - 1
+    s.set_rhs(fd)
+    s.set_solution(ud)
+    want = s.residual_norm(0)
+    for _ in range(2):
+        out = ctypes.c_double(-1.0)
+        st = lib.mg_residual_norm_noalloc(dim, n, None if cs is None else ctypes.byref(cs),
+                                          ctypes.c_void_p(ud.data_ptr()), ctypes.c_void_p(fd.data_ptr()),
+                                          ctypes.byref(out), None)
+        assert st == _capi.MG_OK, lib.mg_last_error()
+        assert lib.mg_last_error() == b""
+        assert abs(out.value - want) <= NORM_RTOL * want, (dim, n, out.value, want)
+    s.close()
+
+
 def test_noalloc_norm_rejects_grids_above_the_static_limit():
     torch = need_gpu()
     from paper_1406_5369_gb300 import _capi
@@ -80,3 +111,7 @@ def test_noalloc_norm_rejects_grids_above_the_static_limit():
     assert lib.mg_residual_norm_noalloc(3, 513, None, p, p, ctypes.byref(out), None) == _capi.MG_EINVAL
     assert b"static scratch" in lib.mg_last_error()
     assert lib.mg_residual_norm_noalloc(2, 2, None, p, p, ctypes.byref(out), None) == _capi.MG_EINVAL
+    # coefficients that mg_create refuses are refused here too
+    bad = _capi.mg_const_stencil(1.0, -1.0, 1.0)
+    assert lib.mg_residual_norm_noalloc(2, 3, ctypes.byref(bad), p, p, ctypes.byref(out), None) == _capi.MG_EINVAL
+    assert b"stencil" in lib.mg_last_error()
