@@ -306,13 +306,15 @@ mg_status mg_residual_norm_noalloc(int dim, int n, const mg_const_stencil *stenc
  * result is the same alone and in any mix. ---- */
 typedef struct mg_batch mg_batch;
 
-/* Device workspace (descriptor arrays, norm partial sums) for at most
- * max_problems problems; 0 if max_problems < 1. */
+/* Device workspace (descriptor arrays, norm partial sums, the state and
+ * descriptors of captured solve steps) for at most max_problems problems;
+ * 0 if max_problems < 1. */
 size_t mg_batch_workspace_bytes(int max_problems);
 
 /* Creates an empty batch using the caller's device workspace (256-byte
  * aligned, at least mg_batch_workspace_bytes bytes) and stream (NULL =
- * default). The batch allocates pinned host staging for descriptors. */
+ * default). The batch allocates pinned host staging for descriptors, a
+ * private stream to capture steps on and two events. */
 mg_status mg_batch_create(int max_problems, void *workspace, size_t bytes, void *stream, mg_batch **out);
 mg_status mg_batch_destroy(mg_batch *batch);
 
@@ -331,8 +333,23 @@ mg_status mg_batch_step(mg_batch *batch, const int *ids, int count, double *rho)
 /* Steps every problem in the batch until its relative residual is at most
  * tol[id] or maxit steps; iters[id] and relres[id] (arrays indexed by id,
  * may be NULL) receive the steps taken and the final ratio. MG_ENOCONV if
- * some problem did not reach its tolerance or a residual was not finite. */
+ * some problem did not reach its tolerance or a residual was not finite.
+ * By default (mg_batch_set_capture on) two solve steps of all problems are
+ * captured once into a CUDA graph and replayed: the stopping test runs on
+ * the device after every step (a problem that has reached its tolerance, or
+ * maxit, is skipped by every later kernel), and the host reads only a count
+ * of the problems still stepping, one replay behind, so the steps run back
+ * to back without waiting for the host. The iterates are the same as with
+ * mg_batch_step (each problem still stops after the step that meets its
+ * tolerance). Synchronises the batch stream. */
 mg_status mg_batch_solve(mg_batch *batch, const double *tol, int maxit, int *iters, double *relres);
+
+/* on = 1 (the default): mg_batch_solve replays captured steps as described
+ * there; on = 0: it calls mg_batch_step once per step (the host reads every
+ * problem's norm after each step). Batches whose steps do not fit the
+ * captured-descriptor area of mg_batch_workspace_bytes fall back to the
+ * latter by themselves. MG_EINVAL for other values. */
+mg_status mg_batch_set_capture(mg_batch *batch, int on);
 
 /* Inner V-cycles per outer step for the batch's defect-correction steps
  * (1..8), overriding the value taken from its first problem. */

@@ -64,6 +64,11 @@ class BatchSolver:
     def set_inner_cycles(self, n):
         C.check(self._lib.mg_batch_set_inner_cycles(self.h, int(n)))
 
+    def set_capture(self, on):
+        """True (default): solve() replays captured steps with the stopping
+        test on the device; False: one mg_batch_step per step."""
+        C.check(self._lib.mg_batch_set_capture(self.h, 1 if on else 0))
+
     def launches(self):
         return self._lib.mg_batch_launches(self.h)
 

@@ -20,6 +20,7 @@
 #include <functional>
 #include <new>
 #include <map>
+#include <unordered_map>
 #include <vector>
 
 #include "ctx.h"
@@ -44,6 +45,7 @@ struct BOp {
   Sten<float> sf;
   Geo g;
   int cur;  // live solution buffer at the start of the step
+  const int *live;  // captured steps: the problem's live flag (NULL = always live)
 };
 
 // Fine/coarse pair of one problem (restriction: fine r -> coarse f;
@@ -52,6 +54,7 @@ struct BXfer {
   const void *src;
   void *dst;
   Geo gf, gc;
+  const int *live;
 };
 
 // Outer (FP64) finest level and inner level 0 of one problem.
@@ -64,7 +67,11 @@ struct BOuter {
   const void *e;  // inner correction (live inner u)
   Geo gi;
   double *partials;  // this problem's partial-sum slots
+  const int *live;
 };
+
+// A block of a captured batch step whose problem has converged does nothing.
+template <typename R> __device__ __forceinline__ bool gone(const R &r) { return r.live && !*r.live; }
 
 template <typename C> __device__ __forceinline__ const Sten<C> &sten_of_op(const BOp &o);
 template <> __device__ __forceinline__ const Sten<double> &sten_of_op<double>(const BOp &o) { return o.sd; }
@@ -93,6 +100,7 @@ __global__ void kb_rbgs_half(const BOp *__restrict__ ops, Geo g, int color, int 
   typedef typename CT<T>::type C;
   BRow<DIM> r = brow<DIM>(g, 1);
   const BOp &o = ops[r.pi];
+  if (gone(o)) return;
   T *u = (T *)o.u[o.cur ^ flip];
   const T *f = (const T *)o.f;
   const Sten<C> s = sten_of_op<C>(o);
@@ -112,6 +120,7 @@ __global__ void kb_jacobi(const BOp *__restrict__ ops, Geo g, int flip, double o
   typedef typename CT<T>::type C;
   BRow<DIM> r = brow<DIM>(g, 1);
   const BOp &o = ops[r.pi];
+  if (gone(o)) return;
   const T *uin = (const T *)o.u[o.cur ^ flip];
   T *uout = (T *)o.u[o.cur ^ flip ^ 1];
   const T *f = (const T *)o.f;
@@ -130,6 +139,7 @@ __global__ void kb_residual(const BOp *__restrict__ ops, Geo g, int flip) {
   typedef typename CT<T>::type C;
   BRow<DIM> r = brow<DIM>(g, 1);
   const BOp &o = ops[r.pi];
+  if (gone(o)) return;
   const T *u = (const T *)o.u[o.cur ^ flip];
   const T *f = (const T *)o.f;
   T *res = (T *)o.r;
@@ -146,6 +156,7 @@ __global__ void kb_residual(const BOp *__restrict__ ops, Geo g, int flip) {
 template <int DIM, typename T> __global__ void kb_zero(const BOp *__restrict__ ops, Geo g, int flip) {
   BRow<DIM> r = brow<DIM>(g, 0);
   const BOp &o = ops[r.pi];
+  if (gone(o)) return;
   T *u = (T *)o.u[o.cur ^ flip] + r.off;
   for (int i = threadIdx.x; i < g.n; i += blockDim.x) st(u + i, 0.0f);
 }
@@ -155,6 +166,7 @@ template <int DIM, typename Tf, typename Tc>
 __global__ void kb_restrict(const BXfer *__restrict__ xs, Geo gf, Geo gc) {
   typedef typename CT<Tc>::type C;
   BRow<DIM> r = brow<DIM>(gc, 1);
+  if (gone(xs[r.pi])) return;
   const Tf *rf = (const Tf *)xs[r.pi].src;
   Tc *fc = (Tc *)xs[r.pi].dst;
   const long long qrow = (long long)(2 * r.k) * gf.sz + (long long)(2 * r.j) * gf.sy;
@@ -181,6 +193,7 @@ template <int DIM, typename Tc, typename Tf>
 __global__ void kb_prolong(const BXfer *__restrict__ xs, Geo gc, Geo gf) {
   typedef typename CT<Tf>::type C;
   BRow<DIM> r = brow<DIM>(gf, 1);
+  if (gone(xs[r.pi])) return;
   const Tc *ec = (const Tc *)xs[r.pi].src;
   Tf *uf = (Tf *)xs[r.pi].dst;
   const int J = r.j >> 1, K = r.k >> 1, oj = r.j & 1, ok = DIM == 3 ? (r.k & 1) : 0;
@@ -203,6 +216,7 @@ __global__ void kb_prolong(const BXfer *__restrict__ xs, Geo gc, Geo gf) {
 template <int DIM, typename Ti, bool VAR>
 __global__ void kb_dc_residual(const BOuter *__restrict__ os) {
   const BOuter &o = os[blockIdx.y];
+  if (gone(o)) return;
   const Sten<double> s = o.sd;
   int m = o.go.n - 2;
   long long total = (long long)m * m * (DIM == 3 ? m : 1);
@@ -224,6 +238,7 @@ __global__ void kb_dc_residual(const BOuter *__restrict__ os) {
 template <int DIM, typename Ti>
 __global__ void kb_dc_update(const BOuter *__restrict__ os) {
   const BOuter &o = os[blockIdx.y];
+  if (gone(o)) return;
   int m = o.go.n - 2;
   long long total = (long long)m * m * (DIM == 3 ? m : 1);
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
@@ -238,6 +253,7 @@ __global__ void kb_dc_update(const BOuter *__restrict__ os) {
 template <int DIM, bool VAR>
 __global__ void kb_norm(const BOp *__restrict__ ops, double *__restrict__ partials) {
   const BOp &o = ops[blockIdx.y];
+  if (gone(o)) return;
   const Sten<double> s = o.sd;
   const double *u = (const double *)o.u[o.cur];
   const double *f = (const double *)o.f;
@@ -271,6 +287,42 @@ __global__ void kb_finalize(const double *__restrict__ partials, double *__restr
     __syncthreads();
   }
   if (t == 0) norms[blockIdx.x] = sqrt(buf[0]);
+}
+
+// Stopping test of a captured batch step (one block): for every problem
+// still live, count the step, form rho = ||r|| / ||r_0|| and retire it when
+// rho <= tol, rho is not finite or maxit steps are done; *remaining = the
+// problems still live. Retired problems' kernels skip them from then on.
+__global__ void kb_check(const double *__restrict__ norms, const double *__restrict__ r0,
+                         const double *__restrict__ tol, int *__restrict__ live, int *__restrict__ iters,
+                         double *__restrict__ rho, int count, int maxit, int *__restrict__ remaining) {
+  __shared__ int left;
+  if (threadIdx.x == 0) left = 0;
+  __syncthreads();
+  int mine = 0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    if (!live[i]) continue;
+    const int it = iters[i] + 1;
+    iters[i] = it;
+    const double a = r0[i];
+    const double r = a > 0.0 ? norms[i] / a : (a == 0.0 ? 0.0 : (double)NAN);
+    rho[i] = r;
+    const int go = (r > tol[i]) && it < maxit;  // a NaN rho fails the comparison and retires
+    live[i] = go;
+    mine += go;
+  }
+  atomicAdd(&left, mine);
+  __syncthreads();
+  if (threadIdx.x == 0) *remaining = left;
+}
+
+// Start of a captured solve: every listed problem live, no steps, rho = 1.
+__global__ void kb_arm(int *__restrict__ live, int *__restrict__ iters, double *__restrict__ rho, int count) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+    live[i] = 1;
+    iters[i] = 0;
+    rho[i] = 1.0;
+  }
 }
 
 }  // namespace bz
@@ -319,6 +371,22 @@ struct mg_batch {
   char *pinned;
   size_t dev_off;
   unsigned long long launches;
+  // Captured solve (mg_batch_solve): per-position device state of the
+  // problems being solved, the descriptor area of the two captured steps and
+  // a private stream to capture on.
+  int capture;                 // 1: mg_batch_solve replays captured steps
+  int *live;                   // maxp flags: problem still stepping
+  int *iters_dev;              // maxp steps taken
+  double *rho_dev, *r0_dev, *tol_dev;  // maxp each
+  int *remaining;              // problems still live after the last check
+  char *gdesc;                 // descriptor area of the captured steps (device)
+  size_t gdesc_bytes, goff;
+  bool gmode;                  // push() stages into gstage for one upload after capture
+  std::vector<char> gstage;
+  std::unordered_map<const mg_ctx *, int> pos;  // position of each problem in the captured solve
+  cudaStream_t cap;
+  char *hstage;                // pinned: r0 and tol uploads, remaining-counter reads
+  cudaEvent_t ev[2];
 };
 
 namespace {
@@ -332,10 +400,33 @@ size_t desc_area_bytes(int maxp) {
   return align256((size_t)maxp * per);
 }
 
+// Device bytes of the captured steps' descriptors per problem: two solve
+// steps of up to four inner V-cycles over ten fine levels, the coarse-cycle
+// and outer records (a solve whose records need more runs uncaptured).
+constexpr size_t kGraphDescPerProblem = 48 * 1024;
+
+size_t graph_area_bytes(int maxp) { return align256((size_t)maxp * kGraphDescPerProblem); }
+
+// Device state of a captured solve: live flags, step counts, rho, r0, tol
+// (one each per problem) and the remaining-problems counter.
+size_t solve_state_bytes(int maxp) {
+  return 2 * align256(sizeof(int) * (size_t)maxp) + 3 * align256(sizeof(double) * (size_t)maxp) + 256;
+}
+
 // Stages `bytes` of descriptors and copies them to the next device slot on
 // the batch stream (before any kernel launched after this call); returns
 // the device address, NULL if the area is exhausted or the copy failed.
+// While a solve step is being captured (gmode) the records go to a host
+// buffer instead, uploaded once to the captured steps' own area.
 void *push(mg_batch *b, const void *src, size_t bytes) {
+  if (b->gmode) {
+    size_t off = align256(b->goff);
+    if (off + bytes > b->gdesc_bytes) return nullptr;
+    if (b->gstage.size() < off + bytes) b->gstage.resize(off + bytes);
+    memcpy(b->gstage.data() + off, src, bytes);
+    b->goff = off + bytes;
+    return b->gdesc + off;
+  }
   size_t off = align256(b->dev_off);
   if (bytes > b->desc_bytes) return nullptr;
   if (off + bytes > b->desc_bytes) {
@@ -349,6 +440,14 @@ void *push(mg_batch *b, const void *src, size_t bytes) {
     return nullptr;
   b->dev_off = off + bytes;
   return b->ws + off;
+}
+
+// The live flag a record of problem c points at: its slot while a solve is
+// captured, NULL (always live) otherwise.
+const int *live_of(const mg_batch *b, const mg_ctx *c) {
+  if (!b->gmode) return nullptr;
+  auto it = b->pos.find(c);
+  return it == b->pos.end() ? nullptr : b->live + it->second;
 }
 
 template <typename D> struct Group {
@@ -510,6 +609,7 @@ mg_status fast_descend(mg_batch *b, std::vector<Item *> &F, bool zero0) {
         if (z != (zero != 0)) continue;
         Level &L = it->c->lv[it->l], &C = it->c->lv[it->l + 1];
         recs.push_back(d2::fused_record(L, C, o.omega, L.u[L.cur ^ it->flip], L.u[L.cur ^ it->flip ^ 1], nullptr, C.f));
+        recs.back().live = live_of(b, it->c);
       }
       if (recs.empty()) continue;
       const fz::Args2D *dev = push_list(b, recs);
@@ -531,6 +631,7 @@ mg_status fast_descend(mg_batch *b, std::vector<Item *> &F, bool zero0) {
     for (Item *it : Zs) {
       Level &L = it->c->lv[it->l];
       recs.push_back(d3::stencil_record(L, o.omega, L.f, L.u[L.cur ^ it->flip ^ 1], L.f));
+      recs.back().live = live_of(b, it->c);
     }
     const z3::Args3 *dev = push_list(b, recs);
     if (!dev) return bfail(MG_ENOMEM, "batch descriptor area exhausted");
@@ -542,6 +643,7 @@ mg_status fast_descend(mg_batch *b, std::vector<Item *> &F, bool zero0) {
     for (Item *it : Zs) {
       BOp op = make_op(it->c->lv[it->l]);
       op.cur ^= it->flip;
+      op.live = live_of(b, it->c);
       zops.push_back(op);
     }
     if (!zops.empty()) BLAUNCH("batched zero", launch_group_op(3, zops, b, 3, L0.dtype, false, 0, 0, 0.0));
@@ -554,6 +656,7 @@ mg_status fast_descend(mg_batch *b, std::vector<Item *> &F, bool zero0) {
         Level &L = it->c->lv[it->l];
         void *in = L.u[L.cur ^ it->flip];
         recs.push_back(d3::stencil_record(L, o.omega, in, o.smoother == MG_RBGS ? in : L.u[L.cur ^ it->flip ^ 1], L.f));
+        recs.back().live = live_of(b, it->c);
       }
       const z3::Args3 *dev = push_list(b, recs);
       if (!dev) return bfail(MG_ENOMEM, "batch descriptor area exhausted");
@@ -581,10 +684,12 @@ mg_status fast_descend(mg_batch *b, std::vector<Item *> &F, bool zero0) {
   for (Item *it : F) {
     Level &L = it->c->lv[it->l], &C = it->c->lv[it->l + 1];
     rrec.push_back(d3::stencil_record(L, o.omega, L.u[L.cur ^ it->flip], L.r, L.f));
+    rrec.back().live = live_of(b, it->c);
     z3::ArgsT3 x;
     memset(&x, 0, sizeof x);
     x.src = L.r;
     x.dst = C.f;
+    x.live = live_of(b, it->c);
     xrec.push_back(x);
   }
   const z3::Args3 *dr = push_list(b, rrec);
@@ -608,6 +713,7 @@ mg_status fast_ascend(mg_batch *b, std::vector<Item *> &F, const std::function<i
       Level &L = it->c->lv[it->l], &C = it->c->lv[it->l + 1];
       const void *ec = C.u[C.cur ^ flip_of(it->c, it->l + 1)];
       recs.push_back(d2::fused_record(L, C, o.omega, L.u[L.cur ^ it->flip], L.u[L.cur ^ it->flip ^ 1], ec, nullptr));
+      recs.back().live = live_of(b, it->c);
     }
     const fz::Args2D *dev = push_list(b, recs);
     if (!dev) return bfail(MG_ENOMEM, "batch descriptor area exhausted");
@@ -623,6 +729,7 @@ mg_status fast_ascend(mg_batch *b, std::vector<Item *> &F, const std::function<i
     memset(&x, 0, sizeof x);
     x.src = C.u[C.cur ^ flip_of(it->c, it->l + 1)];
     x.dst = L.u[L.cur ^ it->flip];
+    x.live = live_of(b, it->c);
     xrec.push_back(x);
   }
   const z3::ArgsT3 *dx = push_list(b, xrec);
@@ -635,6 +742,7 @@ mg_status fast_ascend(mg_batch *b, std::vector<Item *> &F, const std::function<i
       Level &L = it->c->lv[it->l];
       void *in = L.u[L.cur ^ it->flip];
       recs.push_back(d3::stencil_record(L, o.omega, in, o.smoother == MG_RBGS ? in : L.u[L.cur ^ it->flip ^ 1], L.f));
+      recs.back().live = live_of(b, it->c);
     }
     const z3::Args3 *dev = push_list(b, recs);
     if (!dev) return bfail(MG_ENOMEM, "batch descriptor area exhausted");
@@ -676,6 +784,7 @@ mg_status batched_vcycle(mg_batch *b, const std::vector<mg_ctx *> &ps, bool zero
       bool z = it->l > 0 || zero0;
       if (only_zero && !z) continue;
       out.push_back(make_op(it->c->lv[it->l]));
+      out.back().live = live_of(b, it->c);
     }
     return out;
   };
@@ -721,6 +830,7 @@ mg_status batched_vcycle(mg_batch *b, const std::vector<mg_ctx *> &ps, bool zero
       x.dst = C.f;
       x.gf = geo_of(Fl);
       x.gc = geo_of(C);
+      x.live = live_of(b, it->c);
       xs.push_back(x);
       tc = C.dtype;
     }
@@ -738,6 +848,7 @@ mg_status batched_vcycle(mg_batch *b, const std::vector<mg_ctx *> &ps, bool zero
       size_t sm = coarse_args(c->lv, t, c->nl, t > 0 || zero0, o.smoother, o.omega, o.nu1, o.nu2, b->fp64,
                               rec.data());
       if (!sm) return bfail(MG_EINVAL, "coarse levels do not fit in shared memory");
+      coarse_args_set_live(rec.data(), live_of(b, c));
       smem = std::max(smem, sm);
       var = c->lv[0].kf[0] != nullptr;
       recs.insert(recs.end(), rec.begin(), rec.end());
@@ -765,6 +876,7 @@ mg_status batched_vcycle(mg_batch *b, const std::vector<mg_ctx *> &ps, bool zero
       x.dst = Fl.u[Fl.cur ^ it->flip];
       x.gf = geo_of(Fl);
       x.gc = geo_of(C);
+      x.live = live_of(b, it->c);
       xs.push_back(x);
       tc = C.dtype;
     }
@@ -813,7 +925,10 @@ mg_status batched_outer(mg_batch *b, const std::vector<mg_ctx *> &ps, bool updat
   for (int i = 0; i < P; i++) {
     mg_ctx *c = ps[i];
     if (fast_outer(c)) fast[c->outer.n].push_back({i, c});
-    else gen.push_back(make_outer(c, true, update, b->partials + (size_t)i * kSlots));
+    else {
+      gen.push_back(make_outer(c, true, update, b->partials + (size_t)i * kSlots));
+      gen.back().live = live_of(b, c);
+    }
   }
   cudaStream_t s = b->stream;
   int ti = ps[0]->lv[0].dtype;
@@ -859,6 +974,7 @@ mg_status batched_outer(mg_batch *b, const std::vector<mg_ctx *> &ps, bool updat
                                            update ? I.u[I.cur] : nullptr, I.f);
         r.partials = b->partials + (size_t)pc.first * kSlots;
         r.k2 = exact ? pow2_stencil(O) : 0;
+        r.live = live_of(b, c);
         recs.push_back(r);
       }
       const oz::ArgsOuter *dev = push_list(b, recs);
@@ -873,6 +989,7 @@ mg_status batched_outer(mg_batch *b, const std::vector<mg_ctx *> &ps, bool updat
                                          update ? I.u[I.cur] : nullptr, I.f);
         r.partials = b->partials + (size_t)pc.first * kSlots;
         r.k2 = exact ? pow2_stencil(O) : 0;
+        r.live = live_of(b, c);
         recs.push_back(r);
       }
       const z3::ArgsDC3 *dev = push_list(b, recs);
@@ -898,7 +1015,10 @@ mg_status batched_norms(mg_batch *b, const std::vector<mg_ctx *> &ps) {
   const int dim = b->dim;
   bool var = ps[0]->variable;
   std::vector<BOp> os;
-  for (mg_ctx *c : ps) os.push_back(make_op(c->lv[0]));
+  for (mg_ctx *c : ps) {
+    os.push_back(make_op(c->lv[0]));
+    os.back().live = live_of(b, c);
+  }
   const BOp *dev = (const BOp *)push(b, os.data(), sizeof(BOp) * P);
   if (!dev) return bfail(MG_ENOMEM, "batch descriptor area exhausted");
   BCK("clear partials", cudaMemsetAsync(b->partials, 0, sizeof(double) * (size_t)P * kSlots, b->stream));
@@ -909,6 +1029,186 @@ mg_status batched_norms(mg_batch *b, const std::vector<mg_ctx *> &ps) {
   kb_finalize<<<P, 256, 0, b->stream>>>(b->partials, b->norms);
   BCK("batched norm finalize", cudaGetLastError());
   b->launches += 2;
+  return MG_OK;
+}
+
+// Live-buffer state of one problem: every level's live solution buffer and
+// the outer one.
+struct CurSnap {
+  int lv[kMaxLevels];
+  int outer;
+  bool operator==(const CurSnap &o) const { return outer == o.outer && !memcmp(lv, o.lv, sizeof lv); }
+};
+
+CurSnap snap(const mg_ctx *c) {
+  CurSnap s;
+  memset(&s, 0, sizeof s);
+  for (int l = 0; l < c->nl; l++) s.lv[l] = c->lv[l].cur;
+  s.outer = c->outer.cur;
+  return s;
+}
+
+void restore(mg_ctx *c, const CurSnap &s) {
+  for (int l = 0; l < c->nl; l++) c->lv[l].cur = s.lv[l];
+  c->outer.cur = s.outer;
+}
+
+// Captures two solve steps of the problems `ps` (positions 0..P-1 of the
+// live flags) into one graph: each step's inner V-cycles and outer step (or
+// norms), then the stopping test. Two steps, because each step swaps some
+// ping-pong buffers (the outer update, Jacobi sweeps) and its records name
+// buffers: after two steps every buffer is back where it started, so the
+// graph can be replayed. s1 receives each problem's buffer state after one
+// step (the state of a problem that stops after an odd number of steps).
+// On failure every problem's state is restored and the graph discarded.
+mg_status capture_steps(mg_batch *b, const std::vector<mg_ctx *> &ps, int maxit, const std::vector<CurSnap> &s0,
+                        std::vector<CurSnap> &s1, cudaGraphExec_t *exec, unsigned long long *kernels) {
+  const int P = (int)ps.size();
+  b->pos.clear();
+  for (int i = 0; i < P; i++) b->pos[ps[i]] = i;
+  b->gmode = true;
+  b->goff = 0;
+  const unsigned long long l0 = b->launches;
+  cudaStream_t user = b->stream;
+  mg_status st = MG_OK;
+  cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    st = bfail(MG_ECUDA, "begin capture of the batch steps", e);
+  } else {
+    b->stream = b->cap;
+    const int inner = b->dc ? std::max(b->opt.inner_cycles, 1) : 1;
+    for (int step = 0; step < 2 && st == MG_OK; step++) {
+      for (int k = 0; k < inner && st == MG_OK; k++) st = batched_vcycle(b, ps, b->dc && k == 0);
+      if (st == MG_OK) st = b->dc ? batched_outer(b, ps, true) : batched_norms(b, ps);
+      if (st == MG_OK) {
+        kb_check<<<1, 1024, 0, b->cap>>>(b->norms, b->r0_dev, b->tol_dev, b->live, b->iters_dev, b->rho_dev, P,
+                                         maxit, b->remaining);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) st = bfail(MG_ECUDA, "stopping-test kernel", e);
+        b->launches++;
+      }
+      if (step == 0)
+        for (int i = 0; i < P; i++) s1[i] = snap(ps[i]);
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(b->cap, &g);  // ends the capture whatever happened inside it
+    b->stream = user;
+    if (st == MG_OK && e != cudaSuccess) st = bfail(MG_ECUDA, "end capture of the batch steps", e);
+    if (st == MG_OK) {
+      e = cudaGraphInstantiate(exec, g, 0);
+      if (e != cudaSuccess) st = bfail(MG_ECUDA, "instantiate the batch steps", e);
+    }
+    if (g) cudaGraphDestroy(g);
+  }
+  b->gmode = false;
+  b->pos.clear();
+  *kernels = b->launches - l0;
+  b->launches = l0;
+  for (int i = 0; i < P && st == MG_OK; i++)
+    if (!(snap(ps[i]) == s0[i])) st = bfail(MG_EINVAL, "two captured steps do not return the buffers to their start");
+  if (st != MG_OK) {
+    for (int i = 0; i < P; i++) restore(ps[i], s0[i]);
+    return st;
+  }
+  // the records of both steps, once, to the captured steps' own area
+  e = cudaMemcpyAsync(b->gdesc, b->gstage.data(), b->goff, cudaMemcpyHostToDevice, b->stream);
+  if (e != cudaSuccess) {
+    cudaGraphExecDestroy(*exec);
+    return bfail(MG_ECUDA, "upload of the captured steps' descriptors", e);
+  }
+  return MG_OK;
+}
+
+// mg_batch_solve by replayed captured steps: the stopping test runs on the
+// device, converged problems drop out of every later launch, and the host
+// reads one counter per replay (two steps) with one replay queued ahead, so
+// no step waits for the host. *used = false (nothing done, states intact)
+// when the steps cannot be captured - too many descriptors for the captured
+// area, mixed stencil kinds - and the caller steps the batch instead.
+mg_status captured_solve(mg_batch *b, const std::vector<int> &ids, const double *tol, int maxit, int *iters,
+                         double *relres, bool *used) {
+  *used = false;
+  const int P = (int)ids.size();
+  std::vector<mg_ctx *> ps;
+  for (int id : ids) ps.push_back(b->probs[id]);
+  for (mg_ctx *c : ps)
+    if ((c->variable != 0) != (ps[0]->variable != 0)) return MG_OK;
+  mg_status st;
+  cudaStream_t s = b->stream;
+  // initial residual norms of problems not stepped before (one synchronisation)
+  std::vector<mg_ctx *> fresh;
+  std::vector<int> fresh_ids;
+  for (int id : ids)
+    if (b->r0[id] < 0.0) {
+      fresh.push_back(b->probs[id]);
+      fresh_ids.push_back(id);
+    }
+  if (!fresh.empty()) {
+    b->dev_off = 0;
+    if ((st = batched_norms(b, fresh))) return st;
+    std::vector<double> h(fresh.size());
+    BCK("read initial norms", cudaMemcpyAsync(h.data(), b->norms, sizeof(double) * fresh.size(),
+                                              cudaMemcpyDeviceToHost, s));
+    BCK("synchronize", cudaStreamSynchronize(s));
+    for (size_t i = 0; i < fresh.size(); i++) b->r0[fresh_ids[i]] = h[i];
+    b->dev_off = 0;
+  }
+  double *h_r0 = (double *)b->hstage, *h_tol = h_r0 + b->maxp;
+  int *h_rem = (int *)(h_tol + b->maxp);
+  for (int i = 0; i < P; i++) {
+    h_r0[i] = b->r0[ids[i]];
+    h_tol[i] = tol[ids[i]];
+  }
+  std::vector<CurSnap> s0(P), s1(P);
+  for (int i = 0; i < P; i++) s0[i] = snap(ps[i]);
+  cudaGraphExec_t exec = nullptr;
+  unsigned long long kernels = 0;
+  if (capture_steps(b, ps, maxit, s0, s1, &exec, &kernels) != MG_OK) {
+    set_error_message("");
+    return MG_OK;  // not captured: the caller steps the batch
+  }
+  *used = true;
+  BCK("upload r0", cudaMemcpyAsync(b->r0_dev, h_r0, sizeof(double) * P, cudaMemcpyHostToDevice, s));
+  BCK("upload tolerances", cudaMemcpyAsync(b->tol_dev, h_tol, sizeof(double) * P, cudaMemcpyHostToDevice, s));
+  kb_arm<<<(P + 255) / 256, 256, 0, s>>>(b->live, b->iters_dev, b->rho_dev, P);
+  BCK("arm kernel", cudaGetLastError());
+  b->launches++;
+  const int replays = (maxit + 1) / 2;
+  cudaError_t e = cudaSuccess;
+  for (int r = 0; r < replays && e == cudaSuccess; r++) {
+    e = cudaGraphLaunch(exec, s);
+    if (e != cudaSuccess) break;
+    b->launches += kernels;
+    e = cudaMemcpyAsync(&h_rem[r & 1], b->remaining, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev[r & 1], s);
+    if (e == cudaSuccess && r >= 1) {
+      // the previous replay's count, while this one runs
+      e = cudaEventSynchronize(b->ev[(r - 1) & 1]);
+      if (e == cudaSuccess && h_rem[(r - 1) & 1] == 0) break;
+    }
+  }
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  cudaGraphExecDestroy(exec);
+  if (e == cudaSuccess) e = e2;
+  std::vector<int> it(P);
+  std::vector<double> rho(P);
+  if (e == cudaSuccess) e = cudaMemcpy(it.data(), b->iters_dev, sizeof(int) * P, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(rho.data(), b->rho_dev, sizeof(double) * P, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    for (int i = 0; i < P; i++) restore(ps[i], s0[i]);
+    return bfail(MG_ECUDA, "captured batch steps", e);
+  }
+  bool bad = false, open = false;
+  for (int i = 0; i < P; i++) {
+    restore(ps[i], (it[i] & 1) ? s1[i] : s0[i]);  // buffers after an odd / even number of steps
+    const int id = ids[i];
+    if (iters) iters[id] = it[i];
+    if (relres) relres[id] = rho[i];
+    if (!std::isfinite(rho[i])) bad = true;
+    else if (rho[i] > tol[id]) open = true;
+  }
+  if (bad) return bfail(MG_ENOCONV, "a residual became non-finite");
+  if (open) return bfail(MG_ENOCONV, "some problems did not reach their tolerance");
   return MG_OK;
 }
 
@@ -924,7 +1224,8 @@ extern "C" {
 size_t mg_batch_workspace_bytes(int max_problems) {
   if (max_problems < 1) return 0;
   return desc_area_bytes(max_problems) + align256(sizeof(double) * (size_t)max_problems * kSlots) +
-         align256(sizeof(double) * (size_t)max_problems);
+         align256(sizeof(double) * (size_t)max_problems) + solve_state_bytes(max_problems) +
+         graph_area_bytes(max_problems);
 }
 
 mg_status mg_batch_create(int max_problems, void *workspace, size_t bytes, void *stream, mg_batch **out) {
@@ -941,14 +1242,35 @@ mg_status mg_batch_create(int max_problems, void *workspace, size_t bytes, void 
   b->desc_bytes = desc_area_bytes(max_problems);
   b->partials = (double *)(b->ws + b->desc_bytes);
   b->norms = (double *)(b->ws + b->desc_bytes + align256(sizeof(double) * (size_t)max_problems * kSlots));
+  // captured-solve state, then the captured steps' descriptor area
+  char *st = (char *)b->norms + align256(sizeof(double) * (size_t)max_problems);
+  size_t ib = align256(sizeof(int) * (size_t)max_problems), db = align256(sizeof(double) * (size_t)max_problems);
+  b->live = (int *)st;
+  b->iters_dev = (int *)(st + ib);
+  b->rho_dev = (double *)(st + 2 * ib);
+  b->r0_dev = (double *)(st + 2 * ib + db);
+  b->tol_dev = (double *)(st + 2 * ib + 2 * db);
+  b->remaining = (int *)(st + 2 * ib + 3 * db);
+  b->gdesc = st + solve_state_bytes(max_problems);
+  b->gdesc_bytes = graph_area_bytes(max_problems);
+  b->goff = 0;
+  b->gmode = false;
+  b->capture = 1;
   b->stream = (cudaStream_t)stream;
   b->have_opts = false;
   b->launches = 0;
   b->dev_off = 0;
   b->pinned = nullptr;
-  if (cudaMallocHost((void **)&b->pinned, b->desc_bytes) != cudaSuccess) {
-    delete b;
-    return bfail(MG_ENOMEM, "pinned host staging for batch descriptors failed");
+  b->hstage = nullptr;
+  b->cap = nullptr;
+  b->ev[0] = b->ev[1] = nullptr;
+  if (cudaMallocHost((void **)&b->pinned, b->desc_bytes) != cudaSuccess ||
+      cudaMallocHost((void **)&b->hstage, 2 * sizeof(double) * (size_t)max_problems + 64) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev[1], cudaEventDisableTiming) != cudaSuccess) {
+    mg_batch_destroy(b);
+    return bfail(MG_ENOMEM, "pinned host staging, capture stream or events of the batch failed");
   }
   *out = b;
   return MG_OK;
@@ -957,6 +1279,10 @@ mg_status mg_batch_create(int max_problems, void *workspace, size_t bytes, void 
 mg_status mg_batch_destroy(mg_batch *b) {
   if (!b) return MG_OK;
   if (b->pinned) cudaFreeHost(b->pinned);
+  if (b->hstage) cudaFreeHost(b->hstage);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  for (int i = 0; i < 2; i++)
+    if (b->ev[i]) cudaEventDestroy(b->ev[i]);
   delete b;
   return MG_OK;
 }
@@ -1047,6 +1373,11 @@ mg_status mg_batch_solve(mg_batch *b, const double *tol, int maxit, int *iters, 
       if (relres) relres[i] = 1.0;
     }
   mg_status st;
+  if (b->capture && maxit >= 1 && !active.empty()) {
+    bool used = false;
+    st = captured_solve(b, active, tol, maxit, iters, relres, &used);
+    if (used || st != MG_OK) return st;
+  }
   bool bad = false;
   for (int k = 1; k <= maxit && !active.empty(); k++) {
     std::vector<double> rho(active.size());
@@ -1067,6 +1398,12 @@ mg_status mg_batch_solve(mg_batch *b, const double *tol, int maxit, int *iters, 
 }
 
 unsigned long long mg_batch_launches(const mg_batch *b) { return b ? b->launches : 0ull; }
+
+mg_status mg_batch_set_capture(mg_batch *b, int on) {
+  if (!b || (on != 0 && on != 1)) return bfail(MG_EINVAL, "capture must be 0 or 1");
+  b->capture = on;
+  return MG_OK;
+}
 
 mg_status mg_batch_set_inner_cycles(mg_batch *b, int inner_cycles) {
   if (!b || inner_cycles < 1 || inner_cycles > 8) return bfail(MG_EINVAL, "inner_cycles must lie in 1..8");

@@ -87,6 +87,8 @@ size_t coarse_args(const Level *lv, int first, int nl, bool zero_top, int smooth
 
 size_t coarse_args_bytes() { return sizeof(cz::CoarseArgs); }
 
+void coarse_args_set_live(void *args, const int *live) { ((cz::CoarseArgs *)args)->live = live; }
+
 cudaError_t coarse_cycle(const Level *lv, int first, int nl, bool zero_top, int smoother, double omega, int nu1,
                          int nu2, bool fp64, cudaStream_t s) {
   cz::CoarseArgs a;

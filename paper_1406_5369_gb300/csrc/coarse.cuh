@@ -49,6 +49,9 @@ struct CoarseArgs {
   // shared memory; NULL for a 3^dim coarsest grid
   const double *dense;
   int off_rd;
+  // batched cycles of a captured batch step: the problem's live flag in
+  // device memory; the block returns at once when it is 0 (NULL: always live)
+  const int *live;
 };
 
 // Element i of a global field of type dtype, in the cycle's compute type C
@@ -342,6 +345,7 @@ __global__ void __launch_bounds__(kThreads) k_coarse_cycle(CoarseArgs a) {
 // One block per problem: the coarse cycles of a batch of independent problems.
 template <int DIM, bool VAR, typename C>
 __global__ void __launch_bounds__(kThreads) k_coarse_cycle_batched(const CoarseArgs *__restrict__ list) {
+  if (list[blockIdx.x].live && !*list[blockIdx.x].live) return;
   coarse_cycle_body<DIM, VAR, C>(list[blockIdx.x]);
 }
 

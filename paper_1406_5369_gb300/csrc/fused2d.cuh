@@ -77,7 +77,14 @@ struct Args2D {
   const void *kx, *ky;
   double omega, h2, ih2;
   float omegaf, h2f, ih2f;
+  // List launches of a captured batch step: the problem's live flag in
+  // device memory; a block whose problem is no longer live returns at once
+  // (NULL: always live).
+  const int *live;
 };
+
+// True when a list launch's problem has converged (its blocks do nothing).
+template <typename R> __device__ __forceinline__ bool retired(const R &p) { return p.live && !*p.live; }
 
 // Launches over many problems of one level size (the batch engine) pass a
 // device list with one record per problem and blockIdx.y as the problem
@@ -326,7 +333,10 @@ template <typename T, int NU, bool ZERO, bool VAR = false>
 __global__ void __launch_bounds__(32 * Warps<T>::value, VAR ? 2 : MinBlocks<T>::value) k_pre2d(Args2D a, const Args2D *__restrict__ list) {
   typedef typename CT<T>::type C;
   extern __shared__ __align__(16) unsigned char smem[];
-  if (list) take_problem(a, list[blockIdx.y]);
+  if (list) {
+    if (retired(list[blockIdx.y])) return;
+    take_problem(a, list[blockIdx.y]);
+  }
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const long long gw = (long long)blockIdx.x * Warps<T>::value + wib;
   if (gw >= (long long)a.nstrips * a.nchunks) return;
@@ -492,7 +502,10 @@ template <typename T, int NU, bool VAR = false>
 __global__ void __launch_bounds__(32 * Warps<T>::value, VAR ? 2 : MinBlocks<T>::value) k_post2d(Args2D a, const Args2D *__restrict__ list) {
   typedef typename CT<T>::type C;
   extern __shared__ __align__(16) unsigned char smem[];
-  if (list) take_problem(a, list[blockIdx.y]);
+  if (list) {
+    if (retired(list[blockIdx.y])) return;
+    take_problem(a, list[blockIdx.y]);
+  }
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const long long gw = (long long)blockIdx.x * Warps<T>::value + wib;
   if (gw >= (long long)a.nstrips * a.nchunks) return;

@@ -83,7 +83,10 @@ __device__ __forceinline__ void half_x2(float2 &E, float2 &O, const float2 &AE, 
 template <int NU, bool ZERO, bool LIST, bool G>
 __global__ void __launch_bounds__(128, 4) k_pre2d_x2(Args2D a, const Args2D *__restrict__ list) {
   extern __shared__ __align__(16) unsigned char smem[];
-  if (LIST) take_problem(a, list[blockIdx.y]);
+  if (LIST) {
+    if (retired(list[blockIdx.y])) return;
+    take_problem(a, list[blockIdx.y]);
+  }
   constexpr int W = 4;  // warps per block
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const long long gw = (long long)blockIdx.x * W + wib;
@@ -232,7 +235,10 @@ __global__ void __launch_bounds__(128, 4) k_pre2d_x2(Args2D a, const Args2D *__r
 template <int NU, bool LIST, bool G>
 __global__ void __launch_bounds__(128, 4) k_post2d_x2(Args2D a, const Args2D *__restrict__ list) {
   extern __shared__ __align__(16) unsigned char smem[];
-  if (LIST) take_problem(a, list[blockIdx.y]);
+  if (LIST) {
+    if (retired(list[blockIdx.y])) return;
+    take_problem(a, list[blockIdx.y]);
+  }
   constexpr int W = 4;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const long long gw = (long long)blockIdx.x * W + wib;

@@ -155,6 +155,8 @@ cudaError_t coarse_cycle(const Level *lv, int first, int nl, bool zero_top, int 
 size_t coarse_args(const Level *lv, int first, int nl, bool zero_top, int smoother, double omega, int nu1, int nu2,
                    bool fp64, void *args_out);
 size_t coarse_args_bytes();
+// Points a filled argument record at its problem's live flag (captured batch steps).
+void coarse_args_set_live(void *args, const int *live);
 cudaError_t coarse_cycle_batched(const void *list_dev, int count, int dim, bool var, bool fp64, size_t smem,
                                  cudaStream_t s);
 

@@ -61,6 +61,10 @@ struct ArgsOuter {
   double cx, cy, cd;    // stencil: cx = c0/h^2, cy = c1/h^2, cd = 2 (cx + cy)
   int pstride;          // list launches: partial slots per problem
   int k2;               // k_dcx2d: cx = cy = 2^k2
+  // List launches of a captured batch step: the problem's live flag in
+  // device memory; a block whose problem is no longer live returns at once
+  // (NULL: always live).
+  const int *live;
 };
 
 // List launches (many problems of one size): record fields of problem
@@ -135,7 +139,10 @@ __device__ __forceinline__ double warp_sum(double v) {
 template <typename Ti, bool UPDATE, bool ACC64, bool LIST = false>
 __global__ void __launch_bounds__(32 * kWarps) k_dc2d(ArgsOuter a, const ArgsOuter *__restrict__ list) {
   extern __shared__ __align__(16) unsigned char smem[];
-  if (LIST) take_problem(a, list[blockIdx.y]);
+  if (LIST) {
+    if (list[blockIdx.y].live && !*list[blockIdx.y].live) return;
+    take_problem(a, list[blockIdx.y]);
+  }
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const long long gw = (long long)blockIdx.x * kWarps + wib;
   if (gw >= (long long)a.nstrips * a.nchunks) return;
@@ -261,7 +268,10 @@ constexpr int kXRing = 4;
 template <typename Ti, bool ACC64, bool LIST = false>
 __global__ void __launch_bounds__(32 * kWarps) k_dcx2d(ArgsOuter a, const ArgsOuter *__restrict__ list) {
   extern __shared__ __align__(16) unsigned char smem[];
-  if (LIST) take_problem(a, list[blockIdx.y]);
+  if (LIST) {
+    if (list[blockIdx.y].live && !*list[blockIdx.y].live) return;
+    take_problem(a, list[blockIdx.y]);
+  }
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const long long gw = (long long)blockIdx.x * kWarps + wib;
   if (gw >= (long long)a.nstrips * a.nchunks) return;

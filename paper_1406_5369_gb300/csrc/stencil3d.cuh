@@ -91,6 +91,10 @@ struct Args3 {
   // The same, rounded to FP32 on the host (read by the FP32-arithmetic kernels).
   float alphaf, bxf, byf, bzf, gammaf, cdf, cxf, cyf, czf;
   int has_gamma;  // gamma != 0 (omega != 1), decided on the host
+  // List launches of a captured batch step: the problem's live flag in
+  // device memory; a block whose problem is no longer live returns at once
+  // (NULL: always live).
+  const int *live;
 };
 
 // List launches (many problems of one size, the batch engine): blockIdx.z
@@ -212,7 +216,10 @@ __global__ void __launch_bounds__(32 * kTY, MODE == kResid ? 2 : 3) k3_stencil(A
   constexpr int TX = 32 * V;
   constexpr int RB = kRingZ * kSlotB;  // ring bytes
   extern __shared__ __align__(16) unsigned char smem[];
-  if (list) take_problem(a, list[blockIdx.z]);
+  if (list) {
+    if (list[blockIdx.z].live && !*list[blockIdx.z].live) return;
+    take_problem(a, list[blockIdx.z]);
+  }
   __shared__ double wsum[kTY];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int tx = blockIdx.x % a.ntx, ty = blockIdx.x / a.ntx;
@@ -372,6 +379,10 @@ struct ArgsT3 {
   int nc, pitchc;     // coarse grid
   long long planec;
   int ntx;            // x-tiles (of the grid the warps run over)
+  // List launches of a captured batch step: the problem's live flag in
+  // device memory; a block whose problem is no longer live returns at once
+  // (NULL: always live).
+  const int *live;
 };
 
 // Full weighting at coarse interior nodes: a warp covers 16 V coarse columns
@@ -380,6 +391,7 @@ struct ArgsT3 {
 template <typename T>
 __global__ void __launch_bounds__(32 * kTY) k3_restrict(ArgsT3 a, const ArgsT3 *__restrict__ list) {
   if (list) {
+    if (list[blockIdx.z].live && !*list[blockIdx.z].live) return;
     a.src = list[blockIdx.z].src;
     a.dst = list[blockIdx.z].dst;
   }
@@ -430,6 +442,7 @@ __global__ void __launch_bounds__(32 * kTY) k3_restrict(ArgsT3 a, const ArgsT3 *
 template <typename T>
 __global__ void __launch_bounds__(32 * kTY) k3_prolong(ArgsT3 a, const ArgsT3 *__restrict__ list) {
   if (list) {
+    if (list[blockIdx.z].live && !*list[blockIdx.z].live) return;
     a.src = list[blockIdx.z].src;
     a.dst = list[blockIdx.z].dst;
   }
@@ -508,6 +521,10 @@ struct ArgsDC3 {
   double cd, cx, cy, cz;
   int pstride;         // list launches: partial slots per problem
   int k2;              // k3_dcx: cx = cy = cz = 2^k2
+  // List launches of a captured batch step: the problem's live flag in
+  // device memory; a block whose problem is no longer live returns at once
+  // (NULL: always live).
+  const int *live;
 };
 
 // Pieces of the outer step's tile: u and e rows y0-1 .. y0+kTY with halo
@@ -564,6 +581,7 @@ __global__ void __launch_bounds__(32 * kDCWarps) k3_dc(ArgsDC3 a, const ArgsDC3 
   extern __shared__ __align__(16) unsigned char smem[];
   if (list) {  // problem blockIdx.z of a list launch
     const ArgsDC3 &p = list[blockIdx.z];
+    if (p.live && !*p.live) return;
     a.u = p.u; a.uout = p.uout; a.f = p.f; a.e = p.e; a.d = p.d;
     a.cd = p.cd; a.cx = p.cx; a.cy = p.cy; a.cz = p.cz;
     a.partials = p.partials;  // the problem's own slots (at most pstride of them)
@@ -689,6 +707,7 @@ __global__ void __launch_bounds__(32 * kDCWarps) k3_dcx(ArgsDC3 a, const ArgsDC3
   extern __shared__ __align__(16) unsigned char smem[];
   if (list) {  // problem blockIdx.z of a list launch
     const ArgsDC3 &p = list[blockIdx.z];
+    if (p.live && !*p.live) return;
     a.u = p.u; a.uout = p.uout; a.f = p.f; a.e = p.e; a.d = p.d;
     a.cd = p.cd; a.cx = p.cx; a.cy = p.cy; a.cz = p.cz; a.k2 = p.k2;
     a.partials = p.partials;

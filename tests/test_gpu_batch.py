@@ -109,3 +109,78 @@ def test_batch_argument_errors():
         BatchSolver(2).add(c)  # odd Jacobi sweeps
     with pytest.raises(MGError):
         B.step([5])
+
+
+def _solve_batch(probs, tol, maxit, capture, inner=None):
+    from paper_1406_5369_gb300 import BatchSolver
+    B = BatchSolver(len(probs) + 1)
+    for p in probs:
+        p[0].set_solution(None)
+        B.add(p[0])
+    if inner:
+        B.set_inner_cycles(inner)
+    B.set_capture(capture)
+    iters, rel = B.solve(tol, maxit=maxit, raise_on_noconv=False)
+    sols = [p[0].get_solution() for p in probs]
+    launches = B.launches()
+    B.close()
+    return iters, rel, sols, launches
+
+
+@pytest.mark.parametrize("case", ["2d_var_fp32", "2d_fp64", "3d_jacobi_bf16", "3d_rbgs_fp32"])
+def test_captured_solve_equals_stepped_solve(case):
+    """mg_batch_solve replaying two captured steps (stopping test on the
+    device, converged problems skipped by every later launch) gives the same
+    steps, ratios and solutions, bit for bit, as one mg_batch_step per step.
+    Tolerances are mixed so that problems stop after odd and even step counts
+    while others go on (the buffer state after an odd count is the one of the
+    first captured step)."""
+    need_gpu()
+    if case == "2d_var_fp32":
+        ms, mk = [5, 7, 6, 8, 5, 9], dict(var=True)
+    elif case == "2d_fp64":
+        ms, mk = [5, 6, 7, 6], dict(prec="fp64")
+    elif case == "3d_jacobi_bf16":
+        ms, mk = [4, 5, 6, 5], dict(prec="bf16_dc", smoother="jacobi", omega=6 / 7, nu=(2, 2), inner=2)
+    else:
+        ms, mk = [4, 5, 5], dict(prec="fp32_dc")
+    dim = 3 if case.startswith("3d") else 2
+    tols = [1e-6, 1e-10, 1e-8, 1e-4, 1e-10, 1e-7]
+    tol = {i: tols[i % len(tols)] for i in range(len(ms))}
+    out = {}
+    for capture in (False, True):
+        probs = [make_problem(dim, m, 500 + i, **mk) for i, m in enumerate(ms)]
+        out[capture] = _solve_batch(probs, tol, 60, capture)
+    (i0, r0, s0, l0), (i1, r1, s1, l1) = out[False], out[True]
+    n = len(ms)
+    assert np.array_equal(i0[:n], i1[:n]), (i0[:n], i1[:n])
+    assert np.array_equal(r0[:n], r1[:n])
+    if case == "2d_var_fp32":  # odd and even step counts both occur in this mix
+        assert len(set(int(x) % 2 for x in i1[:n])) == 2, i1[:n]
+    for a, b in zip(s0, s1):
+        assert np.array_equal(a, b)
+    assert all(r1[i] <= tol[i] for i in range(n))
+    assert l1 > 0
+
+
+def test_captured_solve_stops_at_maxit_and_reports_noconv():
+    need_gpu()
+    from paper_1406_5369_gb300 import MGError
+    probs = [make_problem(2, m, 600 + i, var=True) for i, m in enumerate([6, 7, 5])]
+    for maxit in (3, 4):
+        outs = []
+        for capture in (False, True):
+            for p in probs:
+                p[0].set_solution(None)
+            outs.append(_solve_batch(probs, 1e-14, maxit, capture))
+        (i0, r0, s0, _), (i1, r1, s1, _) = outs
+        assert np.all(i1[:3] == maxit) and np.array_equal(i0[:3], i1[:3]) and np.array_equal(r0[:3], r1[:3])
+        for a, b in zip(s0, s1):
+            assert np.array_equal(a, b)
+    from paper_1406_5369_gb300 import BatchSolver
+    B = BatchSolver(2)
+    for p in probs[:2]:
+        p[0].set_solution(None)
+        B.add(p[0])
+    with pytest.raises(MGError):
+        B.solve(1e-14, maxit=2)
