@@ -358,6 +358,14 @@ mg_status mg_batch_set_inner_cycles(mg_batch *batch, int inner_cycles);
 /* Kernels the batch has launched so far (diagnostic). */
 unsigned long long mg_batch_launches(const mg_batch *batch);
 
+/* Diagnostic of the last mg_batch_solve that replayed captured steps: out[0]
+ * = host milliseconds of its set-up (initial norms, state snapshots), out[1]
+ * = capturing and instantiating the two-step graph, out[2] = the replays
+ * until the last problem stopped (with the final synchronisation), out[3] =
+ * the replays launched, out[4] = kernel nodes per replay. Zeros before any
+ * such solve. */
+mg_status mg_batch_solve_profile(const mg_batch *batch, double *out);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *mg_last_error(void);
 

@@ -96,6 +96,7 @@ SIGNATURES = {
     "mg_batch_launches": (ctypes.c_ulonglong, [_P]),
     "mg_batch_set_inner_cycles": (_I, [_P, _I]),
     "mg_batch_set_capture": (_I, [_P, _I]),
+    "mg_batch_solve_profile": (_I, [_P, ctypes.POINTER(_D)]),
     "mg_last_error": (ctypes.c_char_p, []),
     "mg_cc_default_params": (None, [ctypes.POINTER(mg_cc_params)]),
     "mg_cc_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(mg_cc_params)]),

@@ -72,6 +72,14 @@ class BatchSolver:
     def launches(self):
         return self._lib.mg_batch_launches(self.h)
 
+    def solve_profile(self):
+        """Host milliseconds of the last captured solve's phases (set-up,
+        capture + instantiate, replays), replays launched, kernels per replay."""
+        out = (ctypes.c_double * 5)()
+        C.check(self._lib.mg_batch_solve_profile(self.h, out))
+        return {"setup_ms": out[0], "capture_ms": out[1], "replays_ms": out[2], "replays": int(out[3]),
+                "kernels_per_replay": int(out[4])}
+
     def close(self):
         if getattr(self, "h", None):
             self._lib.mg_batch_destroy(self.h)

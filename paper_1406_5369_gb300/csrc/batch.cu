@@ -16,6 +16,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <functional>
 #include <new>
@@ -387,6 +388,7 @@ struct mg_batch {
   cudaStream_t cap;
   char *hstage;                // pinned: r0 and tol uploads, remaining-counter reads
   cudaEvent_t ev[2];
+  double phase_ms[5];          // last mg_batch_solve: host wall time of its phases
 };
 
 namespace {
@@ -1128,6 +1130,9 @@ mg_status capture_steps(mg_batch *b, const std::vector<mg_ctx *> &ps, int maxit,
 mg_status captured_solve(mg_batch *b, const std::vector<int> &ids, const double *tol, int maxit, int *iters,
                          double *relres, bool *used) {
   *used = false;
+  typedef std::chrono::steady_clock clk;
+  auto ms_since = [](clk::time_point t) { return std::chrono::duration<double, std::milli>(clk::now() - t).count(); };
+  clk::time_point t0 = clk::now();
   const int P = (int)ids.size();
   std::vector<mg_ctx *> ps;
   for (int id : ids) ps.push_back(b->probs[id]);
@@ -1163,11 +1168,15 @@ mg_status captured_solve(mg_batch *b, const std::vector<int> &ids, const double 
   for (int i = 0; i < P; i++) s0[i] = snap(ps[i]);
   cudaGraphExec_t exec = nullptr;
   unsigned long long kernels = 0;
+  b->phase_ms[0] = ms_since(t0);
+  t0 = clk::now();
   if (capture_steps(b, ps, maxit, s0, s1, &exec, &kernels) != MG_OK) {
     set_error_message("");
     return MG_OK;  // not captured: the caller steps the batch
   }
   *used = true;
+  b->phase_ms[1] = ms_since(t0);
+  t0 = clk::now();
   BCK("upload r0", cudaMemcpyAsync(b->r0_dev, h_r0, sizeof(double) * P, cudaMemcpyHostToDevice, s));
   BCK("upload tolerances", cudaMemcpyAsync(b->tol_dev, h_tol, sizeof(double) * P, cudaMemcpyHostToDevice, s));
   kb_arm<<<(P + 255) / 256, 256, 0, s>>>(b->live, b->iters_dev, b->rho_dev, P);
@@ -1175,10 +1184,12 @@ mg_status captured_solve(mg_batch *b, const std::vector<int> &ids, const double 
   b->launches++;
   const int replays = (maxit + 1) / 2;
   cudaError_t e = cudaSuccess;
+  int done_replays = 0;
   for (int r = 0; r < replays && e == cudaSuccess; r++) {
     e = cudaGraphLaunch(exec, s);
     if (e != cudaSuccess) break;
     b->launches += kernels;
+    done_replays++;
     e = cudaMemcpyAsync(&h_rem[r & 1], b->remaining, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaEventRecord(b->ev[r & 1], s);
     if (e == cudaSuccess && r >= 1) {
@@ -1188,6 +1199,9 @@ mg_status captured_solve(mg_batch *b, const std::vector<int> &ids, const double 
     }
   }
   cudaError_t e2 = cudaStreamSynchronize(s);
+  b->phase_ms[2] = ms_since(t0);
+  b->phase_ms[3] = (double)done_replays;
+  b->phase_ms[4] = (double)kernels;
   cudaGraphExecDestroy(exec);
   if (e == cudaSuccess) e = e2;
   std::vector<int> it(P);
@@ -1264,6 +1278,7 @@ mg_status mg_batch_create(int max_problems, void *workspace, size_t bytes, void 
   b->hstage = nullptr;
   b->cap = nullptr;
   b->ev[0] = b->ev[1] = nullptr;
+  for (int i = 0; i < 5; i++) b->phase_ms[i] = 0.0;
   if (cudaMallocHost((void **)&b->pinned, b->desc_bytes) != cudaSuccess ||
       cudaMallocHost((void **)&b->hstage, 2 * sizeof(double) * (size_t)max_problems + 64) != cudaSuccess ||
       cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
@@ -1398,6 +1413,12 @@ mg_status mg_batch_solve(mg_batch *b, const double *tol, int maxit, int *iters, 
 }
 
 unsigned long long mg_batch_launches(const mg_batch *b) { return b ? b->launches : 0ull; }
+
+mg_status mg_batch_solve_profile(const mg_batch *b, double *out) {
+  if (!b || !out) return bfail(MG_EINVAL, "NULL argument");
+  for (int i = 0; i < 5; i++) out[i] = b->phase_ms[i];
+  return MG_OK;
+}
 
 mg_status mg_batch_set_capture(mg_batch *b, int on) {
   if (!b || (on != 0 && on != 1)) return bfail(MG_EINVAL, "capture must be 0 or 1");
