@@ -763,13 +763,14 @@ def run_c4(args):
     best_inner, best_ms = None, None
     Pm = len(mine)
 
-    def run_batch(inner, capture):
+    def run_batch(inner, capture, timing=False):
         B = BatchSolver(Pm)
         for s in solvers:
             s.set_solution(None)
             B.add(s)
         B.set_inner_cycles(inner)
         B.set_capture(capture)
+        B.set_timing(timing)
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
@@ -781,6 +782,8 @@ def run_c4(args):
                "max_relres": float(rel[:Pm].max())}
         if capture:
             rec["phases"] = B.solve_profile()
+        if timing:
+            rec["kinds"] = {k: B.timing(k) for k in ("pre", "post", "coarse", "outer", "update")}
         B.close()
         return dt, rec
 
@@ -791,6 +794,32 @@ def run_c4(args):
             best_inner, best_ms = inner, dt
     # the same batch stepped from the host (mg_batch_step per step, norms read back every step)
     _, stepped = run_batch(best_inner, False)
+    # per-kernel-kind CUDA-event times and algorithmic bytes: one more stepped
+    # solve with its launch groups timed (outside the timed runs above)
+    _, timed = run_batch(best_inner, False, timing=True)
+    hbm_peak, peak_kind = peaks()
+    kinds = timed.pop("kinds")
+    total_k = sum(v[0] for v in kinds.values())
+    names = {"pre": "fused variable-stencil pre-smoothing + residual + restriction list launches (k_pre2d<float,2,Z,VAR>)",
+             "post": "fused variable-stencil interpolation + post-smoothing list launches (k_post2d<float,1,VAR>)",
+             "coarse": "single-block coarse cycles, one block per problem (latency-bound, time only)",
+             "outer": "FP64 outer residual with FP64 harmonic faces (kb_dc_residual<2,float,VAR>; FP64-issue bound)",
+             "update": "FP64 outer update u += e (kb_dc_update)"}
+    klines = []
+    for k, (ms_k, n_k, by_k) in kinds.items():
+        if not n_k:
+            continue
+        ach = by_k / (ms_k * 1e-3) / 1e9 if ms_k > 0 else 0.0
+        klines.append({"kernel": names[k], "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                       "frac": ach / hbm_peak, "traffic": None, "algorithmic_bytes": by_k, "ms": ms_k,
+                       "launch_groups": n_k, "share": ms_k / total_k if total_k else None})
+    dom = max(klines, key=lambda d: d["ms"]) if klines else None
+    roofline = None
+    if dom:
+        roofline = {k: dom[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
+        roofline.update({"kernel": dom["kernel"], "peak_kind": peak_kind,
+                         "timed": "CUDA events around each launch group of a host-stepped solve of the same batch "
+                                  "(bytes: operator model, each array read or written once per pass)"})
     if world > 1:
         torch.distributed.destroy_process_group()
     if rank != 0:
@@ -803,7 +832,8 @@ def run_c4(args):
            "total_nodes_rank0": nodes, "setup_s": t_setup,
            "parallelism": f"{world} rank(s), problems split by size, no collective on the data path"},
           "f32 inner / f64 outer", tuned_inner_cycles=best_inner, default_vs_tuned=timings,
-          host_stepped=stepped,
+          host_stepped=stepped, roofline=roofline, roofline_kernels=klines,
+          kernel_timed_solve_s=timed["total_s"],
           note="one captured CUDA graph of two solve steps replayed, the stopping test on the device (converged "
                "problems skipped by every later launch); inner_cycles is chosen by timing candidates 1..3 "
                "(autotuned vs default = 1); host_stepped: the same batch with one host-synchronised "

@@ -358,6 +358,30 @@ mg_status mg_batch_set_inner_cycles(mg_batch *batch, int inner_cycles);
 /* Kernels the batch has launched so far (diagnostic). */
 unsigned long long mg_batch_launches(const mg_batch *batch);
 
+/* Diagnostics with no counterpart in the paper: CUDA-event timing of the
+ * batch's launch groups by kind - presmoothing + residual + restriction of
+ * one level size, interpolation + postsmoothing, the coarse cycles, the outer
+ * step of defect correction (its residual, or the whole fused step), the
+ * separate FP64 update of the generic outer path, norms. mg_batch_set_timing
+ * (1 on, 0 off; others MG_EINVAL) applies to steps run by mg_batch_step (and
+ * mg_batch_solve with capture off); captured steps are not timed.
+ * mg_batch_get_timing returns a kind's total milliseconds, its timed launch
+ * groups and their algorithmic bytes (the compulsory traffic of the kernels'
+ * operator model: each array read or written once per pass); it synchronises
+ * the batch stream. mg_batch_reset_timing clears the totals. */
+typedef enum {
+  MG_BATCH_PRE = 0,
+  MG_BATCH_POST = 1,
+  MG_BATCH_COARSE = 2,
+  MG_BATCH_OUTER = 3,
+  MG_BATCH_UPDATE = 4,
+  MG_BATCH_NORM = 5
+} mg_batch_kernel;
+mg_status mg_batch_set_timing(mg_batch *batch, int on);
+mg_status mg_batch_get_timing(mg_batch *batch, int kind, double *total_ms, unsigned long long *launches,
+                              double *bytes);
+mg_status mg_batch_reset_timing(mg_batch *batch);
+
 /* Diagnostic of the last mg_batch_solve that replayed captured steps: out[0]
  * = host milliseconds of its set-up (initial norms, state snapshots), out[1]
  * = capturing and instantiating the two-step graph, out[2] = the replays

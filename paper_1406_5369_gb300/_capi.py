@@ -97,6 +97,9 @@ SIGNATURES = {
     "mg_batch_set_inner_cycles": (_I, [_P, _I]),
     "mg_batch_set_capture": (_I, [_P, _I]),
     "mg_batch_solve_profile": (_I, [_P, ctypes.POINTER(_D)]),
+    "mg_batch_set_timing": (_I, [_P, _I]),
+    "mg_batch_get_timing": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(_D)]),
+    "mg_batch_reset_timing": (_I, [_P]),
     "mg_last_error": (ctypes.c_char_p, []),
     "mg_cc_default_params": (None, [ctypes.POINTER(mg_cc_params)]),
     "mg_cc_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(mg_cc_params)]),

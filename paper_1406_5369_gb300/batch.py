@@ -72,6 +72,22 @@ class BatchSolver:
     def launches(self):
         return self._lib.mg_batch_launches(self.h)
 
+    KINDS = {"pre": 0, "post": 1, "coarse": 2, "outer": 3, "update": 4, "norm": 5}
+
+    def set_timing(self, on):
+        """CUDA-event timing of the launch groups of uncaptured steps."""
+        C.check(self._lib.mg_batch_set_timing(self.h, 1 if on else 0))
+
+    def timing(self, kind):
+        """(total ms, timed launch groups, algorithmic bytes) of one kernel kind."""
+        ms, n, by = ctypes.c_double(), ctypes.c_ulonglong(), ctypes.c_double()
+        C.check(self._lib.mg_batch_get_timing(self.h, self.KINDS[kind], ctypes.byref(ms), ctypes.byref(n),
+                                              ctypes.byref(by)))
+        return ms.value, n.value, by.value
+
+    def reset_timing(self):
+        C.check(self._lib.mg_batch_reset_timing(self.h))
+
     def solve_profile(self):
         """Host milliseconds of the last captured solve's phases (set-up,
         capture + instantiate, replays), replays launched, kernels per replay."""

@@ -389,6 +389,14 @@ struct mg_batch {
   char *hstage;                // pinned: r0 and tol uploads, remaining-counter reads
   cudaEvent_t ev[2];
   double phase_ms[5];          // last mg_batch_solve: host wall time of its phases
+  // kernel timing (mg_batch_set_timing): event pairs around launch groups
+  // of uncaptured steps, harvested at the step's synchronisation
+  int timing;
+  struct Pending { cudaEvent_t a, e; int kind; double bytes; };
+  std::vector<Pending> tpend;
+  std::vector<cudaEvent_t> tpool;
+  double t_ms[8], t_bytes[8];
+  unsigned long long t_n[8];
 };
 
 namespace {
@@ -443,6 +451,57 @@ void *push(mg_batch *b, const void *src, size_t bytes) {
   b->dev_off = off + bytes;
   return b->ws + off;
 }
+
+// Times the launches issued during its lifetime (one launch group of one
+// kernel kind) with a pair of events on the batch stream, when timing is on
+// and the step is not being captured; `bytes` = the group's algorithmic
+// bytes (compulsory traffic of the kernels' operator model).
+struct BTimer {
+  mg_batch *b;
+  int kind;
+  double bytes;
+  cudaEvent_t a = nullptr;
+  static cudaEvent_t take(mg_batch *b) {
+    if (!b->tpool.empty()) {
+      cudaEvent_t e = b->tpool.back();
+      b->tpool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    return cudaEventCreate(&e) == cudaSuccess ? e : nullptr;
+  }
+  BTimer(mg_batch *b_, int kind_, double bytes_) : b(b_), kind(kind_), bytes(bytes_) {
+    if (b->timing && !b->gmode && (a = take(b))) cudaEventRecord(a, b->stream);
+  }
+  ~BTimer() {
+    if (!a) return;
+    cudaEvent_t e = take(b);
+    if (!e) {
+      b->tpool.push_back(a);
+      return;
+    }
+    cudaEventRecord(e, b->stream);
+    b->tpend.push_back({a, e, kind, bytes});
+  }
+};
+
+// Adds the finished event pairs to the totals (after a synchronisation).
+void harvest(mg_batch *b) {
+  for (auto &p : b->tpend) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.e) == cudaSuccess) {
+      b->t_ms[p.kind] += ms;
+      b->t_bytes[p.kind] += p.bytes;
+      b->t_n[p.kind]++;
+    }
+    b->tpool.push_back(p.a);
+    b->tpool.push_back(p.e);
+  }
+  b->tpend.clear();
+}
+
+// Nodes of a level (boundary included) and its word size.
+double nodes_of(const Level &L) { return (double)L.n * L.n * (L.dim == 3 ? L.n : 1); }
 
 // The live flag a record of problem c points at: its slot while a solve is
 // captured, NULL (always live) otherwise.
@@ -616,6 +675,9 @@ mg_status fast_descend(mg_batch *b, std::vector<Item *> &F, bool zero0) {
       if (recs.empty()) continue;
       const fz::Args2D *dev = push_list(b, recs);
       if (!dev) return bfail(MG_ENOMEM, "batch descriptor area exhausted");
+      // read f (and u), write u and the coarse f; faces (FP32) when variable
+      const double w = dtype_size(L0.dtype);
+      BTimer tm(b, MG_BATCH_PRE, recs.size() * nodes_of(L0) * ((zero ? 2.25 : 3.25) * w + (L0.kf[0] ? 8.0 : 0.0)));
       BLAUNCH("batched fused pre-smoothing", d2::pre_fused_list(L0, C0, dev, (int)recs.size(), zero != 0, o.nu1, s));
       b->launches++;
     }
@@ -626,6 +688,9 @@ mg_status fast_descend(mg_batch *b, std::vector<Item *> &F, bool zero0) {
   // pass that reads f only (kJZ); otherwise they are zeroed first. Then the
   // (remaining) sweeps, residual, restriction.
   const bool jz = o.smoother == MG_JACOBI && o.nu1 >= 2;
+  // operator model: nu1 sweeps of 3 words (2 for the f-only first pair),
+  // residual 3 words, full weighting 1 + 1/8 words per fine node
+  BTimer tm(b, MG_BATCH_PRE, F.size() * nodes_of(L0) * dtype_size(L0.dtype) * (3.0 * o.nu1 + 3.0 + 1.125 - (jz ? 4.0 : 0.0)));
   std::vector<Item *> Zs, Ns;
   for (Item *it : F) ((it->l > 0 || zero0) ? Zs : Ns).push_back(it);
   if (jz && !Zs.empty()) {
@@ -719,11 +784,15 @@ mg_status fast_ascend(mg_batch *b, std::vector<Item *> &F, const std::function<i
     }
     const fz::Args2D *dev = push_list(b, recs);
     if (!dev) return bfail(MG_ENOMEM, "batch descriptor area exhausted");
+    // read u, f and the coarse e, write u; faces (FP32) when variable
+    BTimer tm(b, MG_BATCH_POST, recs.size() * nodes_of(L0) * (3.25 * dtype_size(L0.dtype) + (L0.kf[0] ? 8.0 : 0.0)));
     BLAUNCH("batched fused post-smoothing", d2::post_fused_list(L0, C0, dev, (int)recs.size(), o.nu2, s));
     b->launches++;
     for (Item *it : F) it->flip ^= 1;
     return MG_OK;
   }
+  // operator model: trilinear correction 2 + 1/8 words, nu2 sweeps of 3 words
+  BTimer tm(b, MG_BATCH_POST, F.size() * nodes_of(L0) * dtype_size(L0.dtype) * (2.125 + 3.0 * o.nu2));
   std::vector<z3::ArgsT3> xrec;
   for (Item *it : F) {
     Level &L = it->c->lv[it->l], &C = it->c->lv[it->l + 1];
@@ -817,6 +886,10 @@ mg_status batched_vcycle(mg_batch *b, const std::vector<mg_ctx *> &ps, bool zero
     if ((st = fast_descend(b, F, zero0))) return st;
     if (G.empty()) continue;
     const Level &L0 = G[0]->c->lv[G[0]->l];
+    // operator model: nu1 sweeps and the residual of 3 words (+ faces), full
+    // weighting 1 + 2^-d words per fine node
+    BTimer tm(b, MG_BATCH_PRE, G.size() * nodes_of(L0) * ((3.0 * (o.nu1 + 1) + 1.0 + 1.0 / (1 << dim)) * dtype_size(L0.dtype) +
+                                                       (L0.kf[0] ? (o.nu1 + 1) * dim * face_size(L0.dtype) : 0)));
     std::vector<BOp> zops = ops_of(G, true);
     if (!zops.empty()) BLAUNCH("batched zero", launch_group_op(3, zops, b, dim, L0.dtype, false, 0, G[0]->flip, 0.0));
     if ((st = smooth(G, o.nu1))) return st;
@@ -857,6 +930,7 @@ mg_status batched_vcycle(mg_batch *b, const std::vector<mg_ctx *> &ps, bool zero
     }
     const void *dev = push(b, recs.data(), recs.size());
     if (!dev) return bfail(MG_ENOMEM, "batch descriptor area exhausted");
+    BTimer tm(b, MG_BATCH_COARSE, 0.0);  // latency-bound: time only
     BLAUNCH("batched coarse cycle", coarse_cycle_batched(dev, (int)ps.size(), dim, var, b->fp64, smem, b->stream));
     b->launches++;
   }
@@ -868,6 +942,8 @@ mg_status batched_vcycle(mg_batch *b, const std::vector<mg_ctx *> &ps, bool zero
     if ((st = fast_ascend(b, F, flip_of))) return st;
     if (G.empty()) continue;
     const Level &L0 = G[0]->c->lv[G[0]->l];
+    BTimer tm(b, MG_BATCH_POST, G.size() * nodes_of(L0) * ((2.0 + 1.0 / (1 << dim) + 3.0 * o.nu2) * dtype_size(L0.dtype) +
+                                                        (L0.kf[0] ? o.nu2 * dim * face_size(L0.dtype) : 0)));
     std::vector<BXfer> xs;
     int tc = F64;
     for (Item *it : G) {
@@ -938,7 +1014,11 @@ mg_status batched_outer(mg_batch *b, const std::vector<mg_ctx *> &ps, bool updat
     const BOuter *dev = (const BOuter *)push(b, gen.data(), sizeof(BOuter) * gen.size());
     if (!dev) return bfail(MG_ENOMEM, "batch descriptor area exhausted");
     dim3 gr(kPartBlocks, (unsigned)gen.size());
+    double gnodes = 0.0;
+    for (const BOuter &g : gen) gnodes += (double)g.go.n * g.go.n * (dim == 3 ? g.go.n : 1);
+    const double wi = dtype_size(ti);
     if (update) {
+      BTimer tm(b, MG_BATCH_UPDATE, gnodes * (16.0 + wi));  // read u, e; write u
       if (dim == 2) {
         if (ti == F32) kb_dc_update<2, float><<<gr, 256, 0, s>>>(dev);
         else kb_dc_update<2, bf16><<<gr, 256, 0, s>>>(dev);
@@ -949,6 +1029,8 @@ mg_status batched_outer(mg_batch *b, const std::vector<mg_ctx *> &ps, bool updat
       BCK("batched update", cudaGetLastError());
       b->launches++;
     }
+    // read u and f (FP64) and the FP64 faces, write the defect
+    BTimer tm(b, MG_BATCH_OUTER, gnodes * (16.0 + wi + (var ? 8.0 * dim : 0.0)));
     if (dim == 2) {
       if (ti == F32) { if (var) kb_dc_residual<2, float, true><<<gr, 256, 0, s>>>(dev); else kb_dc_residual<2, float, false><<<gr, 256, 0, s>>>(dev); }
       else { if (var) kb_dc_residual<2, bf16, true><<<gr, 256, 0, s>>>(dev); else kb_dc_residual<2, bf16, false><<<gr, 256, 0, s>>>(dev); }
@@ -981,6 +1063,8 @@ mg_status batched_outer(mg_batch *b, const std::vector<mg_ctx *> &ps, bool updat
       }
       const oz::ArgsOuter *dev = push_list(b, recs);
       if (!dev) return bfail(MG_ENOMEM, "batch descriptor area exhausted");
+      // read u, f (FP64) and e, write u (FP64) and the defect (no e, no u written without the update)
+      BTimer tm(b, MG_BATCH_OUTER, recs.size() * nodes_of(O0) * (update ? 24.0 + 2.0 * dtype_size(I0.dtype) : 16.0 + dtype_size(I0.dtype)));
       BCK("batched outer step", d2::dc_step_list(O0, I0, dev, (int)recs.size(), nullptr, kSlots, &np, update, exact, s));
     } else {
       std::vector<z3::ArgsDC3> recs;
@@ -996,6 +1080,7 @@ mg_status batched_outer(mg_batch *b, const std::vector<mg_ctx *> &ps, bool updat
       }
       const z3::ArgsDC3 *dev = push_list(b, recs);
       if (!dev) return bfail(MG_ENOMEM, "batch descriptor area exhausted");
+      BTimer tm(b, MG_BATCH_OUTER, recs.size() * nodes_of(O0) * (update ? 24.0 + 2.0 * dtype_size(I0.dtype) : 16.0 + dtype_size(I0.dtype)));
       BCK("batched outer step", d3::dc_step_list(O0, I0, dev, (int)recs.size(), nullptr, kSlots, &np, update, exact, s));
     }
     b->launches++;
@@ -1279,6 +1364,8 @@ mg_status mg_batch_create(int max_problems, void *workspace, size_t bytes, void 
   b->cap = nullptr;
   b->ev[0] = b->ev[1] = nullptr;
   for (int i = 0; i < 5; i++) b->phase_ms[i] = 0.0;
+  b->timing = 0;
+  for (int i = 0; i < 8; i++) b->t_ms[i] = b->t_bytes[i] = 0.0, b->t_n[i] = 0;
   if (cudaMallocHost((void **)&b->pinned, b->desc_bytes) != cudaSuccess ||
       cudaMallocHost((void **)&b->hstage, 2 * sizeof(double) * (size_t)max_problems + 64) != cudaSuccess ||
       cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
@@ -1298,6 +1385,11 @@ mg_status mg_batch_destroy(mg_batch *b) {
   if (b->cap) cudaStreamDestroy(b->cap);
   for (int i = 0; i < 2; i++)
     if (b->ev[i]) cudaEventDestroy(b->ev[i]);
+  for (auto &p : b->tpend) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.e);
+  }
+  for (cudaEvent_t e : b->tpool) cudaEventDestroy(e);
   delete b;
   return MG_OK;
 }
@@ -1370,6 +1462,7 @@ mg_status mg_batch_step(mg_batch *b, const int *ids, int count, double *rho) {
   BCK("read norms", cudaMemcpyAsync(h.data(), b->norms, sizeof(double) * count, cudaMemcpyDeviceToHost, b->stream));
   BCK("synchronize", cudaStreamSynchronize(b->stream));
   b->dev_off = 0;
+  harvest(b);
   if (rho)
     for (int i = 0; i < count; i++) {
       double r0 = b->r0[ids[i]];
@@ -1413,6 +1506,30 @@ mg_status mg_batch_solve(mg_batch *b, const double *tol, int maxit, int *iters, 
 }
 
 unsigned long long mg_batch_launches(const mg_batch *b) { return b ? b->launches : 0ull; }
+
+mg_status mg_batch_set_timing(mg_batch *b, int on) {
+  if (!b || (on != 0 && on != 1)) return bfail(MG_EINVAL, "timing must be 0 or 1");
+  b->timing = on;
+  return MG_OK;
+}
+
+mg_status mg_batch_get_timing(mg_batch *b, int kind, double *total_ms, unsigned long long *launches, double *bytes) {
+  if (!b || kind < 0 || kind > MG_BATCH_NORM) return bfail(MG_EINVAL, "bad batch timing request");
+  BCK("synchronize", cudaStreamSynchronize(b->stream));
+  harvest(b);
+  if (total_ms) *total_ms = b->t_ms[kind];
+  if (launches) *launches = b->t_n[kind];
+  if (bytes) *bytes = b->t_bytes[kind];
+  return MG_OK;
+}
+
+mg_status mg_batch_reset_timing(mg_batch *b) {
+  if (!b) return bfail(MG_EINVAL, "NULL batch");
+  BCK("synchronize", cudaStreamSynchronize(b->stream));
+  harvest(b);
+  for (int i = 0; i < 8; i++) b->t_ms[i] = b->t_bytes[i] = 0.0, b->t_n[i] = 0;
+  return MG_OK;
+}
 
 mg_status mg_batch_solve_profile(const mg_batch *b, double *out) {
   if (!b || !out) return bfail(MG_EINVAL, "NULL argument");

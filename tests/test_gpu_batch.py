@@ -184,3 +184,34 @@ def test_captured_solve_stops_at_maxit_and_reports_noconv():
         B.add(p[0])
     with pytest.raises(MGError):
         B.solve(1e-14, maxit=2)
+
+
+def test_batch_kernel_timing_counts_groups_and_bytes_without_changing_results():
+    """mg_batch_set_timing brackets each launch group with CUDA events: the
+    solve with timing on gives the same bits as with it off, every kind that
+    ran reports launch groups, positive time and the operator-model bytes
+    (for one 2D FP32 constant-stencil problem: the level-0 pre-smoothing pass
+    from zero moves 2.25 words per node)."""
+    need_gpu()
+    outs = []
+    for timing in (False, True):
+        from paper_1406_5369_gb300 import BatchSolver
+        s, f, _ = make_problem(2, 9, 700)
+        B = BatchSolver(2)
+        B.add(s)
+        B.set_capture(False)
+        B.set_timing(timing)
+        it, rel = B.solve(1e-8, maxit=30)
+        outs.append((it[0], s.get_solution()))
+        if timing:
+            for kind in ("pre", "post", "coarse", "outer"):
+                ms, n, by = B.timing(kind)
+                assert n > 0 and ms > 0, kind
+            ms, n, by = B.timing("pre")
+            n0 = 513 * 513
+            # levels 513, 257, 129 run the fused kernels from zero in each inner cycle (inner = 1 here)
+            per_cycle = 2.25 * 4 * (513 ** 2 + 257 ** 2 + 129 ** 2)
+            assert by == pytest.approx(per_cycle * it[0], rel=1e-12), (by, per_cycle * it[0])
+            B.reset_timing()
+            assert B.timing("pre") == (0.0, 0, 0.0)
+    assert outs[0][0] == outs[1][0] and np.array_equal(outs[0][1], outs[1][1])
