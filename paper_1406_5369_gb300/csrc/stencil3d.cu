@@ -2,6 +2,8 @@
 // constant-stencil levels.
 #include <string.h>
 
+#include <algorithm>
+
 #include "stencil3d.cuh"
 
 namespace mg {
@@ -29,6 +31,34 @@ template <typename K> int resident(K kernel, int threads, size_t smem, int *cach
     *cache = b > 0 ? b : 1;
   }
   return *cache;
+}
+
+// Planes per z-chunk of a single-problem launch, for kernels whose blocks
+// walk their chunk plus two extra planes: the chunk count that minimises
+// (waves of resident blocks) x (planes per block), waves rounded up, so that
+// the last wave is not a nearly empty one; chunks of at least 8 planes and no
+// more than `max_blocks` blocks.
+int pick_zc_waves(int n, long long base_blocks, int per_sm, long long max_blocks) {
+  const int planes = n - 2;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long slots = (long long)std::max(sms, 1) * std::max(per_sm, 1);
+  long long best_cost = -1;
+  int best = planes;
+  for (int nz = 1; nz <= 64; nz++) {
+    const int zc = (planes + nz - 1) / nz;
+    if (nz > 1 && zc < 8) break;
+    const int nzr = (planes + zc - 1) / zc;
+    if (base_blocks * nzr > max_blocks) break;
+    const long long waves = (base_blocks * nzr + slots - 1) / slots;
+    const long long cost = waves * (zc + 2);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = zc;
+    }
+  }
+  return best;
 }
 
 // Planes per z-chunk: enough chunks for about two waves of resident blocks,
@@ -211,21 +241,21 @@ cudaError_t launch_dc(z3::ArgsDC3 a, int *nparts, cudaStream_t s, const z3::Args
   z3::k3_dc<Ti, UPDATE, ACC64><<<dim3((unsigned)base, (unsigned)nz, (unsigned)count), 32 * z3::kDCWarps, smem, s>>>(a, list);
   return cudaGetLastError();
 }
-// The exact outer step (k3_dcx): same tiling, partial-sum layout and chunks.
+// The exact outer step (k3_dcx): 8 rows x 128 columns per block, no dynamic
+// shared memory; per-block partial sums in the same layout.
 template <typename Ti, bool ACC64>
 cudaError_t launch_dcx(z3::ArgsDC3 a, int *nparts, cudaStream_t s, const z3::ArgsDC3 *list = nullptr, int count = 1,
                        int max_parts = kMaxPartials) {
-  constexpr size_t smem = (size_t)z3::DCL<Ti>::Smem;
   static int per_sm = 0;
-  int r = resident(z3::k3_dcx<Ti, ACC64>, 32 * z3::kDCWarps, smem, &per_sm);
-  a.ntx = (a.n - 1 + 63) / 64;
-  a.nty = (a.n - 2 + z3::kTY - 1) / z3::kTY;
+  int r = resident(z3::k3_dcx<Ti, ACC64>, 32 * z3::kXW, 0, &per_sm);
+  a.ntx = (a.n - 1 + z3::kXC - 1) / z3::kXC;
+  a.nty = (a.n - 2 + z3::kXW - 1) / z3::kXW;
   long long base = (long long)a.ntx * a.nty;
-  a.zc = pick_zc(a.n, base, r, max_parts, list != nullptr);
+  a.zc = list ? pick_zc(a.n, base, r, max_parts, true) : pick_zc_waves(a.n, base, r, max_parts);
   int nz = (a.n - 2 + a.zc - 1) / a.zc;
   *nparts = (int)(base * nz);
   a.pstride = max_parts;
-  z3::k3_dcx<Ti, ACC64><<<dim3((unsigned)base, (unsigned)nz, (unsigned)count), 32 * z3::kDCWarps, smem, s>>>(a, list);
+  z3::k3_dcx<Ti, ACC64><<<dim3((unsigned)base, (unsigned)nz, (unsigned)count), 32 * z3::kXW, 0, s>>>(a, list);
   return cudaGetLastError();
 }
 }  // namespace

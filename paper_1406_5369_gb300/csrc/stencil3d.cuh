@@ -693,18 +693,82 @@ __global__ void __launch_bounds__(32 * kDCWarps) k3_dc(ArgsDC3 a, const ArgsDC3 
 
 // ------------------------------------------------ exact outer step (c = 2^k)
 // k3_dc<Ti, true, ACC64> for cx = cy = cz = 2^k2, with the residual
-// evaluated exactly in 64-bit fixed point (fixed.cuh): the update is the one
-// FP64 addition per node. The warp that updates a row converts it once, at
-// that row's warp-wide exponent, and publishes the fixed values and the
-// exponent in the 3-slot ring of updated rows (fixed values take the place
-// of the FP64 ones; the updated FP64 row goes to u_out only). A warp forms
-// the residual of its row at the largest exponent B of the values it reads
-// (its row at planes z-1, z, z+1, the neighbour rows of plane z, f / 2^k2),
-// shifting rows held at a smaller exponent down to B.
+// evaluated exactly in 64-bit fixed point (fixed.cuh); the update is the one
+// FP64 addition per node.
+//
+// A block of kXW = 8 warps owns rows y0 .. y0+7 of a 128-column x-tile (four
+// columns per lane) and a chunk of planes; warp w owns row y0 + w. At plane
+// step z every warp takes its row of u and e at plane z+1 (and of f at plane
+// z) from registers that were loaded straight from global memory one step
+// earlier, forms u + e (FP64), writes it to u_out, converts it once to fixed
+// point at the row's warp-wide exponent and publishes the fixed values and
+// that exponent in a 3-slot ring in shared memory. The two halo rows y0-1 and
+// y0+8 are updated one value per thread (all 256 threads of the block); their
+// row-wide exponent is the largest of four warp maxima, read after the
+// plane's one barrier, and their fixed values are published then (they are
+// read one step later, after the next barrier). The residual of plane z uses
+// the warp's own row at planes z-1, z, z+1 (registers), the neighbour rows of
+// plane z from the ring and f/2^k2, all on the grid of the largest exponent B
+// among them (rows held at a smaller exponent are shifted down to B).
+constexpr int kXW = 8;           // warps (own rows) per block
+constexpr int kXC = 128;         // columns per x-tile (four per lane)
+constexpr int kXRows = kXW + 2;  // published rows: top halo, the own rows, bottom halo
+
+// Four inner-type values of a lane as FP64 (bit conversions, no FP64 instruction).
+__device__ __forceinline__ void e4_to_d(const uint4 &b, double (&v)[4]) {  // float
+  v[0] = oz::f2d_bits(__uint_as_float(b.x));
+  v[1] = oz::f2d_bits(__uint_as_float(b.y));
+  v[2] = oz::f2d_bits(__uint_as_float(b.z));
+  v[3] = oz::f2d_bits(__uint_as_float(b.w));
+}
+__device__ __forceinline__ void e4_to_d(const uint2 &b, double (&v)[4]) {  // bf16 pairs
+  v[0] = oz::f2d_bits(__uint_as_float(b.x << 16));
+  v[1] = oz::f2d_bits(__uint_as_float(b.x & 0xffff0000u));
+  v[2] = oz::f2d_bits(__uint_as_float(b.y << 16));
+  v[3] = oz::f2d_bits(__uint_as_float(b.y & 0xffff0000u));
+}
+template <typename Ti> struct E4 { typedef uint4 V; };
+template <> struct E4<bf16> { typedef uint2 V; };
+
+// Non-coherent global loads kept where they are written: the plane step's
+// loads for the next plane are issued at its start, ahead of the step's
+// arithmetic, so that their latency overlaps it.
+__device__ __forceinline__ double2 ldv_d2(const double *p) {
+  double2 v;
+  asm volatile("ld.global.nc.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint4 ldv_e4(const float *p) {
+  uint4 v;
+  asm volatile("ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint2 ldv_e4(const bf16 *p) {
+  uint2 v;
+  asm volatile("ld.global.nc.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ double ldv_d(const double *p) {
+  double v;
+  asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ double e1_to_d(const float *p) { return oz::f2d_bits(__ldg(p)); }
+__device__ __forceinline__ double e1_to_d(const bf16 *p) {
+  return oz::f2d_bits(__uint_as_float((unsigned)__ldg((const unsigned short *)p) << 16));
+}
+
+// What one plane step reads from global memory: the lane's four columns of u
+// and e at plane p, of f at plane p - 1, its halo-row value (u, e) and, for
+// lanes 0 and 31, the x-halo column (u, e) of the row.
+template <typename Ti> struct XPlane {
+  double u[4], f[4];
+  typename E4<Ti>::V e;
+  double hu, he, xu, xe;
+};
+
 template <typename Ti, bool ACC64>
-__global__ void __launch_bounds__(32 * kDCWarps) k3_dcx(ArgsDC3 a, const ArgsDC3 *__restrict__ list) {
-  typedef DCL<Ti> L;
-  extern __shared__ __align__(16) unsigned char smem[];
+__global__ void __launch_bounds__(32 * kXW, 2) k3_dcx(ArgsDC3 a, const ArgsDC3 *__restrict__ list) {
   if (list) {  // problem blockIdx.z of a list launch
     const ArgsDC3 &p = list[blockIdx.z];
     if (p.live && !*p.live) return;
@@ -712,111 +776,175 @@ __global__ void __launch_bounds__(32 * kDCWarps) k3_dcx(ArgsDC3 a, const ArgsDC3
     a.cd = p.cd; a.cx = p.cx; a.cy = p.cy; a.cz = p.cz; a.k2 = p.k2;
     a.partials = p.partials;
   }
-  __shared__ double wsum[kDCWarps];
-  __shared__ int rexp[3][kDCWarps];  // exponent of each published row
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;  // w = 0 .. kTY + 1: row y0 - 1 + w
+  __shared__ __align__(16) long long pub[3][kXRows][kXC];  // published fixed rows
+  __shared__ int pexp[3][kXRows];                           // their exponents
+  __shared__ unsigned hmax[3][kXW];                         // halo-row pieces' largest biased exponent
+  __shared__ double wsum[kXW];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int tx = blockIdx.x % a.ntx, ty = blockIdx.x / a.ntx;
   const int n = a.n;
-  const int y0 = 1 + ty * kTY, y = y0 - 1 + w;
-  const int x0 = tx * 64, cl = x0 + 2 * lane;
+  const long long P = a.plane, Pi = a.planei;
+  const int y0 = 1 + ty * kXW, y = y0 + w;
+  const int x0 = tx * kXC, c0 = x0 + 4 * lane;
   const int z0 = 1 + blockIdx.y * a.zc, z1 = min(z0 + a.zc, n - 1);
-  const bool out_warp = w >= 1 && w <= kTY && y <= n - 2;
-  const bool row_ok = y <= n - 1;
-  unsigned char *un = smem + kDCRing * L::SlotB;
-  auto slot = [&](int p) { return smem + (p % kDCRing) * L::SlotB; };
-  const float scale = ACC64 ? 1.0f : *a.scale;
+  const bool row_live = y <= n - 1;     // the row exists: updated and published
+  const bool out_row = y <= n - 2;      // interior row: written and its residual formed
+  const bool cols = c0 < a.pitch;       // the lane's four columns lie inside the row's storage
+  const bool lv = row_live && cols;
+  // halo: thread t updates column x0 + t % 128 of row y0 - 1 (t < 128) or y0 + 8
+  const int t = threadIdx.x, hrow = t >> 7, hcol = x0 + (t & 127);
+  const int hy = hrow ? y0 + kXW : y0 - 1;
+  const bool hok = hy <= n - 1 && hcol <= n - 1;
+  // x-halo columns of the own row: x0 - 1 (lane 0) and x0 + 128 (lane 31)
+  const int hx = lane == 0 ? x0 - 1 : x0 + kXC;
+  const bool xok = row_live && ((lane == 0 && x0 >= 1) || (lane == 31 && x0 + kXC <= n - 1));
   const int k2 = a.k2;
+  const float scale = ACC64 ? 1.0f : *a.scale;
+  const Ti *e = (const Ti *)a.e;
   Ti *d = (Ti *)a.d;
-  float acc = 0.0f;
-  double acc64 = 0.0;
+  typedef typename E4<Ti>::V EV;
 
-  auto update_row = [&](int p, double (&v)[2], double &h) {
-    const unsigned char *s = slot(p + kDCRing);
-    const unsigned char *ur = s + w * kURowB;
-    vld((const double *)(ur + (lane + 1) * 16), v);
-    h = 0.0;
-    if (lane == 0) h = *(const double *)(ur + 8);
-    if (lane == 31) h = *(const double *)(ur + 33 * 16);
-    const unsigned char *er = s + kDCWarps * kURowB + w * L::ERowB;
-    const unsigned char *mine = er + 16 + lane * 2 * sizeof(Ti);
-    v[0] += e_at<Ti>(mine);
-    v[1] += e_at<Ti>(mine + sizeof(Ti));
-    if (lane == 0) h += e_at<Ti>(er + 16 - sizeof(Ti));
-    if (lane == 31) h += e_at<Ti>(er + 16 + 64 * sizeof(Ti));
+  auto load = [&](int p, XPlane<Ti> &q) {
+    if (lv) {
+      const double *up = a.u + p * P + (long long)y * a.pitch + c0;
+      const double2 u0 = ldv_d2(up), u1 = ldv_d2(up + 2);
+      q.u[0] = u0.x; q.u[1] = u0.y; q.u[2] = u1.x; q.u[3] = u1.y;
+      q.e = ldv_e4(e + p * Pi + (long long)y * a.pitchi + c0);
+    } else {
+      q.u[0] = q.u[1] = q.u[2] = q.u[3] = 0.0;
+      q.e = EV();
+    }
+    if (out_row && cols && p - 1 >= z0 && p - 1 < z1) {
+      const double *fp = a.f + (p - 1) * P + (long long)y * a.pitch + c0;
+      const double2 f0 = ldv_d2(fp), f1 = ldv_d2(fp + 2);
+      q.f[0] = f0.x; q.f[1] = f0.y; q.f[2] = f1.x; q.f[3] = f1.y;
+    } else {
+      q.f[0] = q.f[1] = q.f[2] = q.f[3] = 0.0;
+    }
+    q.hu = hok ? ldv_d(a.u + p * P + (long long)hy * a.pitch + hcol) : 0.0;
+    q.he = hok ? e1_to_d(e + p * Pi + (long long)hy * a.pitchi + hcol) : 0.0;
+    q.xu = xok ? ldv_d(a.u + p * P + (long long)y * a.pitch + hx) : 0.0;
+    q.xe = xok ? e1_to_d(e + p * Pi + (long long)y * a.pitchi + hx) : 0.0;
   };
 
-  Pieces<DCP<Ti, true>::K> pc;
-  dc_pieces<Ti, true>(pc, a, y0, x0);
-  const int zs = z0 - 2;
-  pc.start(zs + 1);
-  for (int k = 1; k <= kAhead; k++) {
-    const int p = zs + k;
-    pc.issue(slot(p + kDCRing), p <= z1);
-  }
-
-  // own row at planes z-1 (m), z (c), z+1 (p): fixed values, halo, exponent
-  long long xm[2] = {0, 0}, xc[2] = {0, 0}, xp[2] = {0, 0};
-  long long hc = 0, hp = 0;
+  XPlane<Ti> cur, nxt;
+  load(z0 - 1, cur);
+  long long xm[4] = {0, 0, 0, 0}, xc[4] = {0, 0, 0, 0}, xp[4] = {0, 0, 0, 0};
+  long long hxc = 0, hxp = 0;  // x-halo value of the own row (lanes 0 and 31)
   int bm = fx::kHead, bc = fx::kHead, bp = fx::kHead;
-  for (int z = zs; z < z1; z++) {
-    cp_async_wait<kAhead - 1>();
-    __syncthreads();  // (A)
-    pc.issue(slot(z + kAhead + 1 + kDCRing), z + kAhead + 1 <= z1);
-    const int ring = ((z + 1) % 3 + 3) % 3;
-    double nv[2] = {0, 0}, nh = 0;
-    if (row_ok) {
-      update_row(z + 1, nv, nh);
-      if (out_warp && z + 1 >= z0 && z + 1 < z1 && cl < a.pitch)
-        *(double2 *)(a.uout + (long long)(z + 1) * a.plane + (long long)y * a.pitch + cl) = make_double2(nv[0], nv[1]);
+  float acc = 0.0f;
+  double acc64 = 0.0;
+  // step z updates plane z + 1 and, from z0 on, forms the residual of plane z
+  for (int z = z0 - 2; z < z1; z++) {
+    if (z + 2 <= z1) load(z + 2, nxt);
+    const int zp = z + 1, ring = zp % 3;
+    // own row at plane z + 1: u + e, written, converted, published
+    double ev[4], v[4];
+    e4_to_d(cur.e, ev);
+#pragma unroll
+    for (int q = 0; q < 4; q++) v[q] = cur.u[q] + ev[q];
+    const double xv = cur.xu + cur.xe;
+    if (out_row && cols && zp >= z0 && zp < z1) {
+      double *op = a.uout + zp * P + (long long)y * a.pitch + c0;
+      *(double2 *)op = make_double2(v[0], v[1]);
+      *(double2 *)(op + 2) = make_double2(v[2], v[3]);
     }
-    // this row at plane z + 1 in fixed point at its own exponent, published
     {
-      unsigned m = max(max((unsigned)fx::dexp(nv[0]), (unsigned)fx::dexp(nv[1])), (unsigned)fx::dexp(nh));
+      unsigned m = max(max((unsigned)fx::dexp(v[0]), (unsigned)fx::dexp(v[1])),
+                       max((unsigned)fx::dexp(v[2]), (unsigned)fx::dexp(v[3])));
+      m = max(m, xok ? (unsigned)fx::dexp(xv) : 0u);
       m = __reduce_max_sync(0xffffffffu, m);
       const int bn = (m == 0x7ffu ? fx::kNonFinite : (int)m) + fx::kHead;
-      xm[0] = xc[0]; xm[1] = xc[1]; xc[0] = xp[0]; xc[1] = xp[1];
-      hc = hp;
-      bm = bc; bc = bp; bp = bn;
-      xp[0] = fx::to_fixed(nv[0], bn);
-      xp[1] = fx::to_fixed(nv[1], bn);
-      hp = fx::to_fixed(nh, bn);
-      *(longlong2 *)(un + (ring * kDCWarps + w) * L::UNRowB + lane * 16) = make_longlong2(xp[0], xp[1]);
-      if (lane == 0) rexp[ring][w] = bn;
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        xm[q] = xc[q];
+        xc[q] = xp[q];
+        xp[q] = fx::to_fixed(v[q], bn);
+      }
+      hxc = hxp;
+      hxp = fx::to_fixed(xv, bn);
+      bm = bc;
+      bc = bp;
+      bp = bn;
+      if (row_live) {
+        *(longlong2 *)&pub[ring][w + 1][4 * lane] = make_longlong2(xp[0], xp[1]);
+        *(longlong2 *)&pub[ring][w + 1][4 * lane + 2] = make_longlong2(xp[2], xp[3]);
+        if (lane == 0) pexp[ring][w + 1] = bn;
+      }
     }
-    __syncthreads();  // (B) published rows of plane z + 1 visible
-    if (z >= z0 && out_warp) {
-      const int rc = (z % 3 + 3) % 3;
-      const longlong2 s2 = *(const longlong2 *)(un + (rc * kDCWarps + (w - 1)) * L::UNRowB + lane * 16);
-      const longlong2 n2 = *(const longlong2 *)(un + (rc * kDCWarps + (w + 1)) * L::UNRowB + lane * 16);
-      const int bs = rexp[rc][w - 1], bnn = rexp[rc][w + 1];
-      const double2 f2 = *(const double2 *)(slot(z + kDCRing) + kDCWarps * kURowB + kDCWarps * L::ERowB +
-                                             (w - 1) * kFRowB + lane * 16);
-      unsigned mf = max((unsigned)fx::dexp(f2.x), (unsigned)fx::dexp(f2.y));
+    // halo rows at plane z + 1, first half: u + e and the pieces' exponents
+    const double hv = cur.hu + cur.he;
+    {
+      unsigned hm = hok ? (unsigned)fx::dexp(hv) : 0u;
+      hm = __reduce_max_sync(0xffffffffu, hm);
+      if (lane == 0) hmax[ring][w] = hm;
+    }
+    __syncthreads();  // the only barrier of the step
+    // halo rows, second half: the row's exponent and its fixed values
+    {
+      const unsigned *hp = &hmax[ring][hrow * (kXW / 2)];
+      const unsigned mm = max(max(hp[0], hp[1]), max(hp[2], hp[3]));
+      const int bh = (mm == 0x7ffu ? fx::kNonFinite : (int)mm) + fx::kHead;
+      const int hr = hrow ? kXRows - 1 : 0;
+      pub[ring][hr][t & 127] = fx::to_fixed(hv, bh);
+      if ((t & 127) == 0) pexp[ring][hr] = bh;
+    }
+    // residual of plane z
+    if (z >= z0 && out_row) {
+      const int rc = z % 3;
+      const longlong2 s01 = *(const longlong2 *)&pub[rc][w][4 * lane];
+      const longlong2 s23 = *(const longlong2 *)&pub[rc][w][4 * lane + 2];
+      const longlong2 n01 = *(const longlong2 *)&pub[rc][w + 2][4 * lane];
+      const longlong2 n23 = *(const longlong2 *)&pub[rc][w + 2][4 * lane + 2];
+      const int bs = pexp[rc][w], bnn = pexp[rc][w + 2];
+      unsigned mf = max(max((unsigned)fx::dexp(cur.f[0]), (unsigned)fx::dexp(cur.f[1])),
+                        max((unsigned)fx::dexp(cur.f[2]), (unsigned)fx::dexp(cur.f[3])));
       mf = __reduce_max_sync(0xffffffffu, mf);
       int B = max(max(max(bm, bc), max(bp, bs)), max(bnn, max((int)mf - k2, 0) + fx::kHead));
       B = mf == 0x7ffu ? fx::kNonFinite + fx::kHead : B;
-      long long um_[2] = {xm[0], xm[1]}, uc_[2] = {xc[0], xc[1]}, up_[2] = {xp[0], xp[1]}, h = hc;
-      long long ys[2] = {s2.x, s2.y}, yn[2] = {n2.x, n2.y};
-      if (B != bm) { um_[0] = fx::align_down(um_[0], B - bm); um_[1] = fx::align_down(um_[1], B - bm); }
-      if (B != bc) { uc_[0] = fx::align_down(uc_[0], B - bc); uc_[1] = fx::align_down(uc_[1], B - bc); h = fx::align_down(h, B - bc); }
-      if (B != bp) { up_[0] = fx::align_down(up_[0], B - bp); up_[1] = fx::align_down(up_[1], B - bp); }
-      if (B != bs) { ys[0] = fx::align_down(ys[0], B - bs); ys[1] = fx::align_down(ys[1], B - bs); }
-      if (B != bnn) { yn[0] = fx::align_down(yn[0], B - bnn); yn[1] = fx::align_down(yn[1], B - bnn); }
-      long long wl = fx::shfl_up64(uc_[1]), er = fx::shfl_dn64(uc_[0]);
-      if (lane == 0) wl = h;
-      if (lane == 31) er = h;
+      long long um_[4], uc_[4], up_[4], ys[4] = {s01.x, s01.y, s23.x, s23.y}, yn[4] = {n01.x, n01.y, n23.x, n23.y};
+      long long h = hxc;
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        um_[q] = xm[q];
+        uc_[q] = xc[q];
+        up_[q] = xp[q];
+      }
+      if (B != bm) {
+#pragma unroll
+        for (int q = 0; q < 4; q++) um_[q] = fx::align_down(um_[q], B - bm);
+      }
+      if (B != bc) {
+#pragma unroll
+        for (int q = 0; q < 4; q++) uc_[q] = fx::align_down(uc_[q], B - bc);
+        h = fx::align_down(h, B - bc);
+      }
+      if (B != bp) {
+#pragma unroll
+        for (int q = 0; q < 4; q++) up_[q] = fx::align_down(up_[q], B - bp);
+      }
+      if (B != bs) {
+#pragma unroll
+        for (int q = 0; q < 4; q++) ys[q] = fx::align_down(ys[q], B - bs);
+      }
+      if (B != bnn) {
+#pragma unroll
+        for (int q = 0; q < 4; q++) yn[q] = fx::align_down(yn[q], B - bnn);
+      }
+      long long west = fx::shfl_up64(uc_[3]), east = fx::shfl_dn64(uc_[0]);
+      if (lane == 0) west = h;
+      if (lane == 31) east = h;
       const bool finite = B < fx::kNonFinite;
       const int E0 = B - 1085 + k2;
       const fx::Pow2f p2 = fx::pow2f(E0);
       const double s64 = ACC64 ? __hiloint2double((min(max(E0, -1022), 1023) + 1023) << 20, 0) : 0.0;
-      const double fv[2] = {f2.x, f2.y};
-      float rv[2];
+      float rv[4];
 #pragma unroll
-      for (int q = 0; q < 2; q++) {
-        const long long xw = q == 0 ? wl : uc_[0], xe = q == 1 ? er : uc_[1];
+      for (int q = 0; q < 4; q++) {
+        const long long xw = q == 0 ? west : uc_[q - 1], xe = q == 3 ? east : uc_[q + 1];
         const long long S = 6 * uc_[q] - (xw + xe) - (ys[q] + yn[q]) - (um_[q] + up_[q]);
-        const long long R = fx::to_fixed(fv[q], B + k2) - S;
-        const int c = cl + q;
+        const long long R = fx::to_fixed(cur.f[q], B + k2) - S;
+        const int c = c0 + q;
         const bool in = c >= 1 && c <= n - 2;
         const float rf = finite ? fx::fixed_to_float(R, p2) : __int_as_float(0x7fc00000);
         rv[q] = in ? rf : 0.0f;
@@ -829,21 +957,21 @@ __global__ void __launch_bounds__(32 * kDCWarps) k3_dcx(ArgsDC3 a, const ArgsDC3
           acc = fmaf(sr, sr, acc);
         }
       }
-      if (d && cl < a.pitchi) {
-        Ti *dp = d + (long long)z * a.planei + (long long)y * a.pitchi + cl;
-        if (sizeof(Ti) == 4) *(float2 *)dp = make_float2(rv[0], rv[1]);
-        else *(unsigned *)dp = bf16x2_rne_bits(rv[0], rv[1]);
+      if (d && cols) {
+        Ti *dp = d + z * Pi + (long long)y * a.pitchi + c0;
+        if (sizeof(Ti) == 4) *(float4 *)dp = make_float4(rv[0], rv[1], rv[2], rv[3]);
+        else *(uint2 *)dp = make_uint2(bf16x2_rne_bits(rv[0], rv[1]), bf16x2_rne_bits(rv[2], rv[3]));
       }
     }
+    cur = nxt;
   }
-  cp_async_wait<0>();
   double s = oz::warp_sum(ACC64 ? acc64 : (double)acc);
   if (lane == 0) wsum[w] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int i = 0; i < kDCWarps; i++) t += wsum[i];
-    a.partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = t;
+    double tsum = 0.0;
+    for (int i = 0; i < kXW; i++) tsum += wsum[i];
+    a.partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = tsum;
   }
 }
 

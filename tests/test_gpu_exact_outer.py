@@ -197,3 +197,41 @@ def test_exact_outer_3d_solve_matches_fp64_outer(prec):
         res[exact] = (it, u)
     assert res[True][0] == res[False][0]
     assert rel_err(res[True][1], res[False][1]) <= 1e-8
+
+
+@pytest.mark.parametrize("prec", ["fp32_dc", "bf16_dc"])
+def test_exact_defect_3d_multi_tile_matches_fp64_outer(prec):
+    # 257^3: two 128-column x-tiles, 32 y-tiles with a ragged last one, several
+    # z-chunks. One outer step from a structured u0: the exact kernel's update
+    # is the FP64 kernel's bit for bit, and the two defects differ by at most
+    # the inner-type truncation of each, the FP64 kernel's own rounding and
+    # the fixed-point truncation bound (global max |u| scale).
+    need_gpu()
+    from paper_1406_5369_gb300 import Solver
+    n = 257
+    rng = np.random.default_rng(7)
+    f = synth.normal_rhs(3, n, 0x5EED0103)
+    x = np.linspace(0.0, 1.0, n)
+    u0 = np.einsum("i,j,k->kji", np.sin(np.pi * x), np.sin(2 * np.pi * x), np.sin(3 * np.pi * x)) * 1e-2
+    u0[1:-1, 1:-1, 1:-1] += 1e-6 * rng.standard_normal((n - 2,) * 3)
+    u0[0], u0[-1], u0[:, 0], u0[:, -1], u0[:, :, 0], u0[:, :, -1] = 0, 0, 0, 0, 0, 0
+    out = {}
+    for exact in (True, False):
+        s = Solver(3, n, precision=prec, smoother="jacobi", omega=6 / 7, nu1=2, nu2=2, maxit=1, exact_outer=exact)
+        s.set_rhs(f)
+        s.set_solution(u0)
+        s.solve(0.0, raise_on_noconv=False)
+        out[exact] = (s.get_solution(), s.get_field(0, "f"))
+        del s
+    inner = (slice(1, -1),) * 3
+    u, d = out[True]
+    u64, d64 = out[False]
+    assert np.array_equal(u, u64)
+    c = float((n - 1) ** 2)
+    rel = 2.0 ** -23 if prec == "fp32_dc" else 2.0 ** -8 + 2.0 ** -22
+    abs_fix = 16 * c * np.max(np.abs(u)) * 2.0 ** -56 + np.max(np.abs(f)) * 2.0 ** -56
+    fp64_noise = 24 * c * np.max(np.abs(u)) * 2.0 ** -52
+    ref = np.abs(d64[inner])
+    err = np.abs(d[inner] - d64[inner])
+    assert np.all(err <= 2.01 * rel * ref + fp64_noise + abs_fix), float(np.max(err - 2.01 * rel * ref))
+    assert np.all(d[0] == 0) and np.all(d[:, :, -1] == 0)
