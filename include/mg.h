@@ -229,6 +229,27 @@ mg_status mg_residual_norm(mg_ctx *ctx, int level, double *out);
  * Returns MG_ENOCONV if the residual is not finite or tol was not reached. */
 mg_status mg_solve(mg_ctx *ctx, double tol, int *iters, double *relres, double *history);
 
+/* A stream of independent problems with the same operator (the paper solves
+ * one problem per program run; this call keeps the GPU busy while data moves
+ * between host and device). Solves count right-hand sides f[i] (dense n^dim
+ * FP64, host or device memory; pinned host memory lets the copies overlap
+ * the solves), each from u = 0 with mg_solve to tol, and writes solution i to
+ * u[i] (dense n^dim FP64, host or device). Contexts a and b must share dim,
+ * n, precision and stencil kind and should have been created with the same
+ * stencil, coefficients, boundary data and options; each needs its own
+ * stream (options.stream), and copy_stream a third one. They take the
+ * problems in turn: while one solves problem i, the other receives f[i+1]
+ * on its stream and solution i-1 returns on copy_stream, so that every
+ * problem's host-to-device and device-to-host copies run beside another
+ * problem's solve. iters[i] and relres[i] (may be NULL) receive each solve's
+ * cycles and final ratio. All three streams are synchronised before the
+ * call returns; f[i] and u[i] are borrowed until then. Returns MG_EINVAL for
+ * mismatched contexts, shared streams or NULL arrays, MG_ENOCONV if some
+ * problem did not reach tol (the others are still solved and copied), and
+ * the first other error of a solve or copy (the sequence stops there). */
+mg_status mg_solve_sequence(mg_ctx *a, mg_ctx *b, void *copy_stream, int count, const double *const *f,
+                            double *const *u, double tol, int *iters, double *relres);
+
 /* Diagnostic with no counterpart in the paper: the number of CUDA kernels
  * this context has launched so far, counting each kernel node of a
  * replayed graph (memset/copy operations are not counted). */

@@ -8,10 +8,10 @@ library's kernels.
 """
 from ._capi import (MG_BF16_DC, MG_FIELD_F, MG_FIELD_R, MG_FIELD_U, MG_FP32_DC, MG_FP64,
                     MG_JACOBI, MG_RBGS, MGError, load)
-from .solver import Solver
+from .solver import Solver, solve_sequence
 from .batch import BatchSolver
 from .cellgrid import CCSolver
 from .cdiff import CDSolver
 
-__all__ = ["Solver", "BatchSolver", "CCSolver", "CDSolver", "MGError", "load", "MG_RBGS", "MG_JACOBI", "MG_FP64", "MG_FP32_DC",
+__all__ = ["Solver", "solve_sequence", "BatchSolver", "CCSolver", "CDSolver", "MGError", "load", "MG_RBGS", "MG_JACOBI", "MG_FP64", "MG_FP32_DC",
            "MG_BF16_DC", "MG_FIELD_U", "MG_FIELD_F", "MG_FIELD_R"]

@@ -86,6 +86,8 @@ SIGNATURES = {
     "mg_reset_timing": (_I, [_P]),
     "mg_residual_norm_noalloc": (_I, [_I, _I, ctypes.POINTER(mg_const_stencil), _P, _P,
                                       ctypes.POINTER(_D), _P]),
+    "mg_solve_sequence": (_I, [_P, _P, _P, _I, ctypes.POINTER(_P), ctypes.POINTER(_P), _D, ctypes.POINTER(_I),
+                               ctypes.POINTER(_D)]),
     "mg_batch_workspace_bytes": (ctypes.c_size_t, [_I]),
     "mg_batch_create": (_I, [_I, _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)]),
     "mg_batch_destroy": (_I, [_P]),

@@ -893,6 +893,78 @@ mg_status mg_solve(mg_ctx *c, double tol, int *iters, double *relres, double *hi
   return MG_OK;
 }
 
+mg_status mg_solve_sequence(mg_ctx *a, mg_ctx *b, void *copy_stream, int count, const double *const *f,
+                            double *const *u, double tol, int *iters, double *relres) {
+  g_err[0] = 0;
+  if (!a || !b || a == b) return fail(MG_EINVAL, "two distinct contexts are needed");
+  if (count < 0 || (count > 0 && (!f || !u))) return fail(MG_EINVAL, "bad count or NULL arrays");
+  if (a->dim != b->dim || a->n != b->n || a->dc != b->dc || a->variable != b->variable)
+    return fail(MG_EINVAL, "the two contexts differ in dimension, size, precision or stencil kind");
+  if (a->stream == b->stream || (cudaStream_t)copy_stream == a->stream || (cudaStream_t)copy_stream == b->stream)
+    return fail(MG_EINVAL, "the two contexts and the copy stream need three different streams");
+  if (!(tol >= 0.0)) return fail(MG_EINVAL, "tol must be >= 0");
+  for (int i = 0; i < count; i++)
+    if (!f[i] || !u[i]) return fail(MG_EINVAL, "NULL right-hand side or solution %d", i);
+  if (count == 0) return MG_OK;
+  cudaStream_t cs = (cudaStream_t)copy_stream;
+  mg_ctx *cx[2] = {a, b};
+  cudaEvent_t solved[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr};
+  bool pending[2] = {false, false};  // a copy-back of the context's solution is queued
+  mg_status st = MG_OK, worst = MG_OK;
+  for (int k = 0; k < 2 && st == MG_OK; k++) {
+    if (cudaEventCreateWithFlags(&solved[k], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&copied[k], cudaEventDisableTiming) != cudaSuccess)
+      st = fail(MG_ECUDA, "event creation failed");
+  }
+  auto load = [&](int i) -> mg_status {
+    mg_ctx *X = cx[i & 1];
+    // f travels at once (the copy-back of the context's previous solution
+    // reads u only); u is reset once that copy-back has finished
+    mg_status s1 = mg_set_rhs(X, f[i]);
+    if (s1) return s1;
+    if (pending[i & 1] && cudaStreamWaitEvent(X->stream, copied[i & 1], 0) != cudaSuccess)
+      return fail(MG_ECUDA, "stream wait");
+    return mg_set_solution(X, nullptr);
+  };
+  if (st == MG_OK) st = load(0);
+  for (int i = 0; i < count && st == MG_OK; i++) {
+    mg_ctx *X = cx[i & 1];
+    // the next problem's right-hand side travels while this one is solved
+    if (i + 1 < count && (st = load(i + 1))) break;
+    int it = 0;
+    double rr = 0.0;
+    mg_status s1 = mg_solve(X, tol, &it, &rr, nullptr);
+    if (iters) iters[i] = it;
+    if (relres) relres[i] = rr;
+    if (s1 == MG_ENOCONV) worst = MG_ENOCONV;
+    else if (s1) {
+      st = s1;
+      break;
+    }
+    // this solution travels back on the copy stream while the next one is solved
+    Level &U = user_level(X);
+    if (cudaEventRecord(solved[i & 1], X->stream) != cudaSuccess ||
+        cudaStreamWaitEvent(cs, solved[i & 1], 0) != cudaSuccess ||
+        copy_pitched_to_dense(U, user_u(X), u[i], cs) != cudaSuccess ||
+        cudaEventRecord(copied[i & 1], cs) != cudaSuccess) {
+      st = fail(MG_ECUDA, "copy of solution %d", i);
+      break;
+    }
+    pending[i & 1] = true;
+  }
+  cudaError_t e = cudaStreamSynchronize(cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(a->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  for (int k = 0; k < 2; k++) {
+    if (solved[k]) cudaEventDestroy(solved[k]);
+    if (copied[k]) cudaEventDestroy(copied[k]);
+  }
+  if (st == MG_OK && e != cudaSuccess) st = fail(MG_ECUDA, "synchronize: %s", cudaGetErrorString(e));
+  if (st) return st;
+  if (worst) return fail(MG_ENOCONV, "some problems did not reach tol");
+  return MG_OK;
+}
+
 unsigned long long mg_kernel_launches(const mg_ctx *c) { return c ? c->launches : 0ull; }
 
 mg_status mg_set_timing(mg_ctx *c, int on) {

@@ -195,3 +195,30 @@ class Solver:
         if st != C.MG_OK and (raise_on_noconv or st != C.MG_ENOCONV):
             C.check(st)
         return it.value, rr.value, hist[:it.value + 1]
+
+
+def solve_sequence(a, b, fs, us, tol, copy_stream):
+    """Solves right-hand sides fs[i] into us[i] (mg_solve_sequence): Solvers
+    a and b (same problem settings, each on its own stream) take the
+    problems in turn, and each problem's host copies run on `copy_stream`
+    (a third stream handle) beside the other Solver's solve. fs / us: float64
+    arrays or tensors of n^dim elements, host (pinned for overlap) or device.
+    Returns (iters, relres) as numpy arrays."""
+    lib = C.load()
+    count = len(fs)
+    if len(us) != count:
+        raise ValueError("fs and us differ in length")
+    keep = []
+    fp = (ctypes.c_void_p * max(count, 1))()
+    up = (ctypes.c_void_p * max(count, 1))()
+    for i in range(count):
+        p, k = _ptr(fs[i], a.dim, a.n)
+        q, k2 = _ptr(us[i], a.dim, a.n)
+        fp[i], up[i] = p, q
+        keep += [k, k2]
+    iters = np.zeros(max(count, 1), dtype=np.int32)
+    rel = np.zeros(max(count, 1))
+    C.check(lib.mg_solve_sequence(a.ctx, b.ctx, ctypes.c_void_p(copy_stream), count, fp, up, float(tol),
+                                  iters.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                  rel.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return iters[:count], rel[:count]

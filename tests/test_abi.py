@@ -184,3 +184,11 @@ def test_complex_diffusion_params_are_validated_without_a_device(lib):
     ctx = ctypes.c_void_p()
     assert lib.mg_cd_create(ctypes.byref(p), ctypes.c_void_p(256), 16, ctypes.byref(ctx)) == C.MG_ENOMEM
     assert lib.mg_cd_num_levels(None) == -1
+
+
+def test_solve_sequence_refuses_bad_arguments_without_a_device(lib):
+    from paper_1406_5369_gb300 import _capi as C
+    import ctypes
+    st = lib.mg_solve_sequence(None, None, None, 1, None, None, 1e-8, None, None)
+    assert st == C.MG_EINVAL
+    assert b"contexts" in lib.mg_last_error()
