@@ -174,7 +174,9 @@ mg_status mg_set_rhs(mg_ctx *ctx, const double *f);
  * u0 == NULL sets zero. Boundary nodes always keep the Dirichlet values. */
 mg_status mg_set_solution(mg_ctx *ctx, const double *u0);
 
-/* Copies the finest-level solution (dense n^dim FP64, boundary included). */
+/* Copies the finest-level solution (dense n^dim FP64, boundary included).
+ * A host destination is staged through the context's FP64 scratch field
+ * (the level-0 residual field R of an MG_FP64 context is overwritten). */
 mg_status mg_get_solution(mg_ctx *ctx, double *u);
 
 /* Per-level access used by operator-level tests and tools: level ell's

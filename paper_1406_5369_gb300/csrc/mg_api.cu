@@ -767,10 +767,54 @@ mg_status mg_set_solution(mg_ctx *c, const double *u0) {
   return MG_OK;
 }
 
+// Rows of a pitched FP64 field written to a dense array that the device
+// reaches directly (pinned host memory): each block takes rows in turn, its
+// threads stream one row with 8-byte loads and stores.
+__global__ void __launch_bounds__(1024) k_rows_out(const double *__restrict__ src, long long pitch, double *__restrict__ dst, int n,
+                           long long rows) {
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+    const double *a = src + r * pitch;
+    double *b = dst + r * n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) b[i] = __ldg(a + i);
+  }
+}
+
+// Copies the finest (user-level) solution to the dense array dst on stream
+// s. Pinned host memory is written by a small kernel through its device
+// mapping (the copy engines' device-to-host reads measured slow while the
+// other context's kernels kept HBM busy); other host memory goes through the
+// context's FP64 staging field - the outer level's r in defect-correction
+// contexts, level 0's r (scratch of the residual passes) otherwise: a
+// device-side 2D copy into dense layout, then one contiguous copy.
+static cudaError_t copy_solution_out(mg_ctx *c, double *dst, cudaStream_t s) {
+  Level &U = user_level(c);
+  cudaPointerAttributes at;
+  bool device = false, pinned = false;
+  if (cudaPointerGetAttributes(&at, dst) == cudaSuccess) {
+    device = at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    pinned = at.type == cudaMemoryTypeHost && at.devicePointer != nullptr;
+  } else {
+    cudaGetLastError();  // an unknown host pointer: clear the error
+  }
+  if (device) return copy_pitched_to_dense(U, user_u(c), dst, s);
+  if (pinned) {
+    const long long rows = (long long)U.n * (U.dim == 3 ? U.n : 1);
+    // 16 blocks of 1024 threads: fast enough to hide behind a concurrent
+    // solve, few enough not to slow it (measured over 16..152 blocks)
+    k_rows_out<<<16, 1024, 0, s>>>((const double *)user_u(c), U.pitch, (double *)at.devicePointer, U.n, rows);
+    c->launches++;
+    return cudaGetLastError();
+  }
+  double *stage = (double *)(c->dc ? c->outer.r : c->lv[0].r);
+  const size_t cnt = (size_t)U.n * U.n * (U.dim == 3 ? U.n : 1);
+  cudaError_t e = copy_pitched_to_dense(U, user_u(c), stage, s);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyAsync(dst, stage, cnt * 8, cudaMemcpyDeviceToHost, s);
+}
+
 mg_status mg_get_solution(mg_ctx *c, double *u) {
   if (!c || !u) return fail(MG_EINVAL, "NULL argument");
-  Level &U = user_level(c);
-  CK(copy_pitched_to_dense(U, user_u(c), u, c->stream));
+  CK(copy_solution_out(c, u, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return MG_OK;
 }
@@ -942,10 +986,9 @@ mg_status mg_solve_sequence(mg_ctx *a, mg_ctx *b, void *copy_stream, int count, 
       break;
     }
     // this solution travels back on the copy stream while the next one is solved
-    Level &U = user_level(X);
     if (cudaEventRecord(solved[i & 1], X->stream) != cudaSuccess ||
         cudaStreamWaitEvent(cs, solved[i & 1], 0) != cudaSuccess ||
-        copy_pitched_to_dense(U, user_u(X), u[i], cs) != cudaSuccess ||
+        copy_solution_out(X, u[i], cs) != cudaSuccess ||
         cudaEventRecord(copied[i & 1], cs) != cudaSuccess) {
       st = fail(MG_ECUDA, "copy of solution %d", i);
       break;
