@@ -182,6 +182,7 @@ KERNEL_TRAFFIC = {
     "k_dcx2d": 2185.6e6,   # algorithmic 32 B/node = 2148 MB
     "k_pre2d_x2": 875.7e6,  # a launch that reads u: algorithmic 13 B/node = 872.6 MB
     "k_post2d_x2": 877.8e6,  # algorithmic 13 B/node = 872.6 MB
+    "k_postpre2d_x2": None,  # not captured yet
 }
 TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of this kernel build at 8193^2, "
                   "captured separately (not in this run)")
@@ -264,7 +265,7 @@ def run_gpu(args):
     ms = job_ms(ms, world, dev)
     cycles = iters[-1]
     # per-kernel times of the timed region (CUDA events on the solver's stream)
-    kinds = {k: s.timing(k, 0) for k in ("pre", "post", "outer", "norm")}
+    kinds = {k: s.timing(k, 0) for k in ("pre", "post", "postpre", "outer", "norm")}
     # all-level split: two further solves with every kernel timed (outside the
     # timed region; the event nodes add a few us per kernel to these solves)
     s.set_timing(True)
@@ -346,20 +347,35 @@ def run_gpu(args):
                       "per_launch": "read u, f (8 B each) and e (4 B), write u (8 B) and the defect (4 B) per node "
                                     "= 32 B x 8193^2 = 2148 MB",
                       "avg_launch_us": 1e3 * t_outer / c_outer, "launches": c_outer, "share": t_outer / (ms * args.steps)})
+    t_pp, c_pp = kinds["postpre"]
+    if c_pp:
+        # post-smoothing of one inner cycle joined with the next cycle's pre-smoothing:
+        # read u, f and the coarse e (1/4 word), write u and the coarse f (1/4 word)
+        a_pp = (3.5 * w) * nodes / (t_pp / c_pp * 1e-3) / 1e9
+        lines.append({"kernel": "k_postpre2d_x2<1,2>: bilinear correction + 1 + 2 RBGS sweeps + residual + full "
+                                "weighting, level 0 (packed FP32; post-smoothing of one inner cycle joined with the "
+                                "pre-smoothing of the next)",
+                      "bound": "hbm", "achieved": a_pp, "peak": hbm_peak, "unit": "GB/s", "frac": a_pp / hbm_peak,
+                      "traffic": KERNEL_TRAFFIC.get("k_postpre2d_x2"), "traffic_source": TRAFFIC_SOURCE,
+                      "per_launch": "read u, f (1 word each) + coarse e (1/4 word), write u (1 word) + coarse f "
+                                    "(1/4 word) per node",
+                      "avg_launch_us": 1e3 * t_pp / c_pp, "launches": c_pp, "share": t_pp / (ms * args.steps)})
     t_pre, c_pre = kinds["pre"]
     if c_pre:
-        # The first inner cycle of an outer step starts from u = 0 and does not read u:
-        # 1 launch in inner_cycles reads f and writes u and the coarse f (2.25 words per
-        # node), the others also read u (3.25 words).
+        # The first inner cycle of an outer step starts from u = 0 and does not read u
+        # (2.25 words per node: read f, write u and the coarse f); with joined cycles
+        # that is the only separate pre-smoothing pass, otherwise the other inner
+        # cycles' passes also read u (3.25 words).
         ic = best["inner_cycles"]
-        words_pre = 2.25 + (ic - 1) / ic
+        words_pre = 2.25 if c_pp else 2.25 + (ic - 1) / ic
         a_pre = (words_pre * w) * nodes / (t_pre / c_pre * 1e-3) / 1e9
         lines.append({"kernel": "k_pre2d_x2<2,zero>: 2 RBGS sweeps + residual + full weighting, level 0 (packed FP32)",
                       "bound": "hbm", "achieved": a_pre, "peak": hbm_peak, "unit": "GB/s", "frac": a_pre / hbm_peak,
-                      "traffic": KERNEL_TRAFFIC["k_pre2d_x2"],
+                      "traffic": None if c_pp else KERNEL_TRAFFIC["k_pre2d_x2"],
                       "traffic_source": TRAFFIC_SOURCE + " (a launch that reads u)",
-                      "per_launch": f"read f, write u (1 word each) + coarse f (1/4 word) per node, + read u in "
-                                    f"{ic - 1} of {ic} launches ({words_pre:.3f} words/node on average)",
+                      "per_launch": f"read f, write u (1 word each) + coarse f (1/4 word) per node"
+                                    + ("" if c_pp else f", + read u in {ic - 1} of {ic} launches "
+                                                       f"({words_pre:.3f} words/node on average)"),
                       "avg_launch_us": 1e3 * t_pre / c_pre, "launches": c_pre, "share": t_pre / (ms * args.steps)})
     t_post, c_post = kinds["post"]
     if c_post:

@@ -114,7 +114,13 @@ typedef struct { int kind; const double *dirichlet_values; } mg_boundary;
  *                         streaming ones; 0 = 257, values below 33 = none
  * fuse_depth            : sweeps fused into each pre-/post-smoothing pass
  *                         (0 = all nu1 / nu2); with 0 < fuse_depth < nu the
- *                         other nu - fuse_depth sweeps run as separate passes */
+ *                         other nu - fuse_depth sweeps run as separate passes
+ * join_cycles           : *_DC with inner_cycles > 1 only: 1 = between two inner
+ *                         V-cycles, the finest inner level's post-smoothing
+ *                         pass and the next cycle's pre-smoothing pass run as
+ *                         one pass (packed FP32 2D streaming levels,
+ *                         nu1 + nu2 <= 3; the same operations in the same
+ *                         order, so the same results), 0 = two passes */
 typedef struct {
   mg_smoother smoother;
   double omega;
@@ -130,14 +136,15 @@ typedef struct {
   int tile_rows;
   int tile_max_n;
   int fuse_depth;
+  int join_cycles;
 } mg_options;
 
 typedef struct mg_ctx mg_ctx;
 
 /* Fills *opt with RBGS, omega 1, V(2,1), coarsest 3, maxit 50, FP64,
  * default stream, fuse 1, use_graph 1, inner_cycles 1, exact_outer 1,
- * tile_rows 0, tile_max_n 0, fuse_depth 0 (the Layer-3 defaults of Sec. 2.3
- * and automatic tiling). */
+ * tile_rows 0, tile_max_n 0, fuse_depth 0, join_cycles 1 (the Layer-3
+ * defaults of Sec. 2.3 and automatic tiling). */
 void mg_default_options(mg_options *opt);
 
 /* Bytes of device arena mg_create needs for this problem (0 if the
@@ -259,14 +266,17 @@ unsigned long long mg_kernel_launches(const mg_ctx *ctx);
 
 /* Kernel classes for mg_get_timing: presmoothing + residual + restriction,
  * interpolation + postsmoothing, the coarse-level cycle / 3^d solve, the
- * FP64 outer step of defect correction, residual norms, anything else. */
+ * FP64 outer step of defect correction, residual norms, anything else, and
+ * the joined postsmoothing + presmoothing pass of two inner cycles
+ * (join_cycles). */
 typedef enum {
   MG_KERNEL_PRESMOOTH = 0,
   MG_KERNEL_POSTSMOOTH = 1,
   MG_KERNEL_COARSE = 2,
   MG_KERNEL_OUTER = 3,
   MG_KERNEL_NORM = 4,
-  MG_KERNEL_OTHER = 5
+  MG_KERNEL_OTHER = 5,
+  MG_KERNEL_POSTPRE = 6
 } mg_kernel_kind;
 
 /* Diagnostics with no counterpart in the paper. mg_set_timing(ctx, 1)

@@ -18,7 +18,8 @@ STATUS_NAMES = {0: "MG_OK", 1: "MG_EINVAL", 2: "MG_ENOMEM", 3: "MG_ECUDA", 4: "M
 MG_RBGS, MG_JACOBI = 0, 1
 MG_FP64, MG_FP32_DC, MG_BF16_DC = 0, 1, 2
 MG_FIELD_U, MG_FIELD_F, MG_FIELD_R = 0, 1, 2
-MG_KERNEL_PRESMOOTH, MG_KERNEL_POSTSMOOTH, MG_KERNEL_COARSE, MG_KERNEL_OUTER, MG_KERNEL_NORM, MG_KERNEL_OTHER = range(6)
+(MG_KERNEL_PRESMOOTH, MG_KERNEL_POSTSMOOTH, MG_KERNEL_COARSE, MG_KERNEL_OUTER, MG_KERNEL_NORM, MG_KERNEL_OTHER,
+ MG_KERNEL_POSTPRE) = range(7)
 
 
 class mg_const_stencil(ctypes.Structure):
@@ -34,7 +35,8 @@ class mg_options(ctypes.Structure):
                 ("nu2", ctypes.c_int), ("coarsest_n", ctypes.c_int), ("maxit", ctypes.c_int),
                 ("precision", ctypes.c_int), ("stream", ctypes.c_void_p), ("fuse", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("inner_cycles", ctypes.c_int), ("exact_outer", ctypes.c_int),
-                ("tile_rows", ctypes.c_int), ("tile_max_n", ctypes.c_int), ("fuse_depth", ctypes.c_int)]
+                ("tile_rows", ctypes.c_int), ("tile_max_n", ctypes.c_int), ("fuse_depth", ctypes.c_int),
+                ("join_cycles", ctypes.c_int)]
 
 
 class mg_cc_params(ctypes.Structure):

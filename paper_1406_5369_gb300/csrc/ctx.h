@@ -13,7 +13,7 @@ constexpr int kMaxLevels = 31;
 constexpr int kGraphSlots = 4;
 constexpr int kMaxPairs = 2048;       // event pairs for kernel timing
 constexpr int kSlotPairs = 256;       // timed kernels per captured graph
-constexpr int kKinds = 6;             // mg_kernel_kind values
+constexpr int kKinds = 7;             // mg_kernel_kind values
 
 struct TimingPair {
   cudaEvent_t a, b;

@@ -243,6 +243,36 @@ cudaError_t launch_post_x2(fz::Args2D a, int R_override, const Level &L, cudaStr
   return cudaGetLastError();
 }
 
+// Post-smoothing of one cycle fused with the pre-smoothing of the next
+// (k_postpre2d_x2), single problem.
+template <int NUA, int NUB, bool G>
+cudaError_t launch_postpre_x2(fz::Args2D a, int R_override, const Level &L, cudaStream_t s) {
+  constexpr int W = 4;
+  constexpr size_t smem = (size_t)W * fz::kPS * 32 * (16 + 16 + 8);
+  static bool ready = false;
+  static int bps = 1;
+  if (!ready) {
+    cudaError_t e = prepare(fz::k_postpre2d_x2<NUA, NUB, G>, smem);
+    if (e != cudaSuccess) return e;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fz::k_postpre2d_x2<NUA, NUB, G>, 32 * W, smem);
+    if (bps < 1) bps = 1;
+    ready = true;
+  }
+  if (R_override <= 0) {
+    a.R = pick_rows(L.n, a.nstrips, bps, W, 0);
+    a.nchunks = (L.n + a.R - 1) / a.R;
+  }
+  long long warps = (long long)a.nstrips * a.nchunks;
+  unsigned blocks = (unsigned)((warps + W - 1) / W);
+  fz::k_postpre2d_x2<NUA, NUB, G><<<blocks, 32 * W, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int NUA, int NUB>
+cudaError_t postpre_x2(const fz::Args2D &a, int R, const Level &L, cudaStream_t s) {
+  return a.has_gamma ? launch_postpre_x2<NUA, NUB, true>(a, R, L, s) : launch_postpre_x2<NUA, NUB, false>(a, R, L, s);
+}
+
 template <int NU, bool ZERO>
 cudaError_t pre_x2(const fz::Args2D &a, int R, const Level &L, cudaStream_t s, const fz::Args2D *list, int count) {
   return a.has_gamma ? launch_pre_x2<NU, ZERO, true>(a, R, L, s, list, count)
@@ -307,6 +337,25 @@ cudaError_t pre_fused(const Level &L, const void *uin, void *uout, const Level &
   a.fc = fc;
   if (tile_ok(L, tile_max_n)) return dispatch_tpre(a, L, s, zero, nu);
   return dispatch_pre(a, R, L, s, nullptr, 1, zero, nu);
+}
+
+bool postpre_ok(const Level &L, const Level &Cl, int nu2, int nu1, int tile_max_n) {
+  return L.dim == 2 && L.dtype == F32 && !L.kf[0] && Cl.dtype == F32 && nu2 >= 1 && nu1 >= 1 && nu2 + nu1 <= 3 &&
+         L.n >= 33 && !tile_ok(L, tile_max_n);
+}
+
+cudaError_t postpre_fused(const Level &L, const void *uin, void *uout, const Level &Cl, const void *ec, void *fc,
+                          int nu2, int nu1, double omega, int R, int tile_max_n, cudaStream_t s) {
+  if (!postpre_ok(L, Cl, nu2, nu1, tile_max_n)) return cudaErrorInvalidValue;
+  fz::Args2D a = make_args(L, Cl, omega, R, 1);
+  a.uin = uin;
+  a.f = L.f;
+  a.uout = uout;
+  a.ec = ec;
+  a.fc = fc;
+  if (nu2 == 1 && nu1 == 2) return postpre_x2<1, 2>(a, R, L, s);
+  if (nu2 == 2 && nu1 == 1) return postpre_x2<2, 1>(a, R, L, s);
+  return postpre_x2<1, 1>(a, R, L, s);
 }
 
 cudaError_t post_fused(const Level &L, const void *uin, void *uout, const Level &Cl, const void *ec, int nu,

@@ -159,6 +159,7 @@ mg_status check_args(int dim, int n, const mg_options *opt) {
   if (opt->tile_rows < 0 || opt->tile_rows > (1 << 20)) return fail(MG_EINVAL, "tile_rows must lie in 0..2^20");
   if (opt->tile_max_n < 0) return fail(MG_EINVAL, "tile_max_n must be >= 0");
   if (opt->fuse_depth < 0 || opt->fuse_depth > 8) return fail(MG_EINVAL, "fuse_depth must lie in 0..8");
+  if (opt->join_cycles != 0 && opt->join_cycles != 1) return fail(MG_EINVAL, "join_cycles must be 0 or 1");
   return MG_OK;
 }
 
@@ -452,11 +453,45 @@ mg_status op_first_norm(mg_ctx *c, cudaStream_t s) {
 // One defect-correction step with the defect d already in lv[0].f:
 // e = V(0, d), then inner_cycles - 1 further cycles e = V(e, d); u += e. With `norm`, the residual of the updated u is
 // computed in the same pass (new defect in lv[0].f, norm in norm_out).
+// True when level 0 of the inner hierarchy joins the post-smoothing pass of
+// one inner cycle with the pre-smoothing pass of the next (join_cycles).
+bool can_join(mg_ctx *c) {
+  if (!c->opt.join_cycles || c->nl < 2 || !level_fused(c, 0)) return false;
+  if (fused_sweeps(c, c->opt.nu1) != c->opt.nu1 || fused_sweeps(c, c->opt.nu2) != c->opt.nu2) return false;
+  if (c->lv[0].n <= mg::coarse_top_n(c->dim, !c->dc)) return false;
+  return mg::d2::postpre_ok(c->lv[0], c->lv[1], c->opt.nu2, c->opt.nu1, c->opt.tile_max_n);
+}
+
 mg_status dc_inner_and_update(mg_ctx *c, bool norm, cudaStream_t s) {
   mg_status st;
-  if ((st = vcycle_rec(c, 0, true, s))) return st;
-  for (int k = 1; k < (c->opt.inner_cycles > 1 ? c->opt.inner_cycles : 1); k++)
-    if ((st = vcycle_rec(c, 0, false, s))) return st;
+  const int inner = c->opt.inner_cycles > 1 ? c->opt.inner_cycles : 1;
+  if (inner > 1 && can_join(c)) {
+    // level 0: pre-smoothing from zero, then between consecutive cycles one
+    // pass of post-smoothing + the next pre-smoothing, post-smoothing last;
+    // levels 1.. as in vcycle_rec
+    Level &L = c->lv[0], &C = c->lv[1];
+    const double om = c->opt.omega;
+    TLAUNCH(c, MG_KERNEL_PRESMOOTH, 0, s,
+            mg::d2::pre_fused(L, L.u[L.cur], L.u[L.cur ^ 1], C, C.f, true, c->opt.nu1, om, c->opt.tile_rows,
+                              c->opt.tile_max_n, s));
+    L.cur ^= 1;
+    if ((st = vcycle_rec(c, 1, true, s))) return st;
+    for (int k = 1; k < inner; k++) {
+      TLAUNCH(c, MG_KERNEL_POSTPRE, 0, s,
+              mg::d2::postpre_fused(L, L.u[L.cur], L.u[L.cur ^ 1], C, C.u[C.cur], C.f, c->opt.nu2, c->opt.nu1, om,
+                                    c->opt.tile_rows, c->opt.tile_max_n, s));
+      L.cur ^= 1;
+      if ((st = vcycle_rec(c, 1, true, s))) return st;
+    }
+    TLAUNCH(c, MG_KERNEL_POSTSMOOTH, 0, s,
+            mg::d2::post_fused(L, L.u[L.cur], L.u[L.cur ^ 1], C, C.u[C.cur], c->opt.nu2, om, c->opt.tile_rows,
+                               c->opt.tile_max_n, s));
+    L.cur ^= 1;
+  } else {
+    if ((st = vcycle_rec(c, 0, true, s))) return st;
+    for (int k = 1; k < inner; k++)
+      if ((st = vcycle_rec(c, 0, false, s))) return st;
+  }
   Level &O = c->outer, &I = c->lv[0];
   if (outer_fast(O, I)) {
     int np = 0;
@@ -611,6 +646,7 @@ void mg_default_options(mg_options *o) {
   o->use_graph = 1;
   o->inner_cycles = 1;
   o->exact_outer = 1;
+  o->join_cycles = 1;
 }
 
 size_t mg_workspace_bytes(int dim, int n, int variable_k, const mg_options *opt) {

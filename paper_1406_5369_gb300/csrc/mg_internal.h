@@ -92,6 +92,13 @@ cudaError_t pre_fused(const Level &L, const void *uin, void *uout, const Level &
                       double omega, int R, int tile_max_n, cudaStream_t s);
 cudaError_t post_fused(const Level &L, const void *uin, void *uout, const Level &Cl, const void *ec, int nu,
                        double omega, int R, int tile_max_n, cudaStream_t s);
+// Post-smoothing (nu2 sweeps) of one V-cycle and pre-smoothing (nu1 sweeps,
+// residual, restriction into fc) of the next in one pass, on a packed-FP32
+// constant-stencil streaming level (postpre_ok): u_out = the u the two
+// separate passes would leave, fc = their restricted residual.
+bool postpre_ok(const Level &L, const Level &Cl, int nu2, int nu1, int tile_max_n);
+cudaError_t postpre_fused(const Level &L, const void *uin, void *uout, const Level &Cl, const void *ec, void *fc,
+                          int nu2, int nu1, double omega, int R, int tile_max_n, cudaStream_t s);
 }  // namespace d2
 
 // Streaming 2D finest-level kernels (constant stencil). dc_step: FP64 outer

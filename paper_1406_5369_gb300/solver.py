@@ -49,7 +49,7 @@ class Solver:
     def __init__(self, dim, n, *, stencil=(1.0, 1.0, 1.0), k=None, dirichlet=None,
                  smoother="rbgs", omega=1.0, nu1=2, nu2=1, maxit=50, precision="fp64",
                  fuse=True, use_graph=True, inner_cycles=1, exact_outer=True, tile_rows=0, tile_max_n=0,
-                 fuse_depth=0, coarsest_n=3, stream=None, device="cuda"):
+                 fuse_depth=0, join_cycles=True, coarsest_n=3, stream=None, device="cuda"):
         import torch
         self._lib = C.load()
         self.dim, self.n = dim, n
@@ -68,6 +68,7 @@ class Solver:
         opt.tile_rows = int(tile_rows)
         opt.tile_max_n = int(tile_max_n)
         opt.fuse_depth = int(fuse_depth)
+        opt.join_cycles = int(bool(join_cycles))
         opt.stream = default_stream_handle() if stream is None else stream
         self._tstream = torch.cuda.current_stream() if stream is None else torch.cuda.ExternalStream(stream)
         self.opt = opt
@@ -116,7 +117,8 @@ class Solver:
     def timing(self, kind, level=0):
         """(total milliseconds, launches) of one kernel class on one level."""
         kinds = {"pre": C.MG_KERNEL_PRESMOOTH, "post": C.MG_KERNEL_POSTSMOOTH, "coarse": C.MG_KERNEL_COARSE,
-                 "outer": C.MG_KERNEL_OUTER, "norm": C.MG_KERNEL_NORM, "other": C.MG_KERNEL_OTHER}
+                 "outer": C.MG_KERNEL_OUTER, "norm": C.MG_KERNEL_NORM, "other": C.MG_KERNEL_OTHER,
+                 "postpre": C.MG_KERNEL_POSTPRE}
         ms = ctypes.c_double()
         cnt = ctypes.c_ulonglong()
         C.check(self._lib.mg_get_timing(self.ctx, kinds.get(kind, kind), level, ctypes.byref(ms), ctypes.byref(cnt)))

@@ -187,3 +187,28 @@ def test_tiling_knobs_rejected_when_out_of_range():
     for kw in (dict(tile_rows=-1), dict(tile_max_n=-5), dict(fuse_depth=9)):
         with pytest.raises(MGError):
             Solver(2, 65, **kw)
+
+
+@pytest.mark.parametrize("n,nu1,nu2,omega,inner", [(513, 2, 1, 1.0, 3), (1025, 2, 1, 1.15, 2), (513, 1, 1, 1.0, 3),
+                                                   (1025, 1, 2, 0.9, 3), (2049, 2, 1, 1.0, 4)])
+def test_joined_inner_cycles_equal_separate_passes(n, nu1, nu2, omega, inner):
+    # Between two inner cycles of a defect-correction step the finest inner
+    # level runs post-smoothing + the next pre-smoothing as one pass
+    # (join_cycles): the same FP32 operations in the same order as the two
+    # separate passes, so histories and solutions agree bit for bit; the
+    # oracle recomputes the final residual.
+    need_gpu()
+    from paper_1406_5369_gb300 import Solver
+    f = synth.uniform_rhs(2, n, 0x5EED0002 ^ n)
+    out = {}
+    for join in (True, False):
+        s = Solver(2, n, precision="fp32_dc", nu1=nu1, nu2=nu2, omega=omega, inner_cycles=inner, maxit=30,
+                   join_cycles=join)
+        s.set_rhs(f)
+        it, rr, hist = s.solve(1e-10)
+        out[join] = (hist[: it + 1], s.get_solution(), s.kernel_launches())
+    assert np.array_equal(out[True][0], out[False][0])
+    assert np.array_equal(out[True][1], out[False][1])
+    assert out[True][2] < out[False][2]  # fewer launches with the joined passes
+    u = out[True][1]
+    assert oracle.norm(oracle.residual(u, f)) / oracle.norm(f) <= 1.01e-10

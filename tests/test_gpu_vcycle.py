@@ -243,8 +243,11 @@ def test_kernel_timing_instrumentation():
     it, rr, _ = s.solve(1e-10)
     pre_ms, pre_n = s.timing("pre", 0)
     post_ms, post_n = s.timing("post", 0)
+    pp_ms, pp_n = s.timing("postpre", 0)
     out_ms, out_n = s.timing("outer", 0)
-    assert pre_n == post_n == 2 * it and pre_ms > 0 and post_ms > 0
+    # with 2 inner cycles per step, level 0 runs a pre-smoothing pass, one
+    # joined post + pre pass and a post-smoothing pass per step
+    assert pre_n == post_n == pp_n == it and pre_ms > 0 and post_ms > 0 and pp_ms > 0
     # one outer step per iteration (the first residual of a zero start is f,
     # formed by a norm pass)
     assert out_n == it and out_ms > 0
@@ -255,7 +258,7 @@ def test_kernel_timing_instrumentation():
     s.set_timing(True, level0_only=True)
     s.set_solution(None)
     it2, _, _ = s.solve(1e-10)
-    assert s.timing("pre", 0)[1] == 2 * it2 and s.timing("outer", 0)[1] == it2
+    assert s.timing("pre", 0)[1] == it2 and s.timing("postpre", 0)[1] == it2 and s.timing("outer", 0)[1] == it2
     assert s.timing("pre", 1) == (0.0, 0) and s.timing("coarse", s.levels - 1) == (0.0, 0)
     s.set_timing(False)
     s.reset_timing()
