@@ -877,32 +877,64 @@ def run_c4(args):
                "mg_batch_step per step", **extra)
 
 
+def serve_step_bytes(dim, n, inner=3):
+    """Operator-model bytes of one serving solve step of a (dim, n) request
+    (compulsory traffic, each array read or written once per pass, summed
+    over the levels: 4/3 (2D) or 8/7 (3D) of the finest level's).
+    2D FP32-DC, RBGS V(2,1): per inner cycle the fused pre-smoothing pass
+    (2.25 words from zero, 3.25 otherwise) and post-smoothing pass (3.25
+    words), w = 4 B; the exact outer step reads u, f (FP64) and e and writes
+    u (FP64) and the defect: 24 + 2 w B per node.
+    3D BF16-DC, Jacobi V(2,2), w = 2 B: per cycle two sweeps (the first pair
+    from zero reads f only: 2 words, else 6), residual 3, restriction 1 1/8,
+    interpolation 2 1/8 and two post-sweeps 6 words; outer step 24 + 2 w B."""
+    nodes = float(n) ** dim
+    if dim == 2:
+        w = 4.0
+        per_cycle = [(2.25 + 3.25) * w] + [(3.25 + 3.25) * w] * (inner - 1)
+        return nodes * (sum(per_cycle) * 4.0 / 3.0 + 24.0 + 2 * w)
+    w = 2.0
+    per_cycle = [(2.0 + 3.0 + 1.125 + 2.125 + 6.0) * w] + [(6.0 + 3.0 + 1.125 + 2.125 + 6.0) * w] * (inner - 1)
+    return nodes * (sum(per_cycle) * 8.0 / 7.0 + 24.0 + 2 * w)
+
+
 def run_c5(args):
-    """Serving: Poisson arrivals, mixed 2D/3D Poisson requests, p50/p99 latency and solves/s."""
+    """Serving: Poisson arrivals, mixed 2D/3D Poisson requests, p50/p99 latency and solves/s.
+    One arrival stream of warm-up + measured seconds; the statistics cover the
+    requests arriving, and the completions falling, in the measured window."""
     torch = _init_cuda()
     import synth
     from paper_1406_5369_gb300.serve import Server
     rate = args.rate
-    count = max(1, int(rate * args.serve_seconds))
+    warm_s, meas_s = args.serve_warmup, args.serve_seconds
+    count = max(1, int(rate * (warm_s + meas_s)))
     reqs = synth.serving_requests(count, 0x5EED0005, rate_per_s=rate)
     srv = Server(budget_bytes=150e9, max_active=4096)
-    # warm the pools / kernels with a short burst of the same mix (not counted)
-    warm = synth.serving_requests(min(64, count), 0x5EED0095, rate_per_s=rate * 10)
-    srv.run(warm)
+    # first launches of every kernel of the mix (not counted)
+    srv.run(synth.serving_requests(64, 0x5EED0095, rate_per_s=rate * 10))
     srv.steps = 0
+    window = (warm_s, warm_s + meas_s)
     with ClockSampler(0) as clk:
-        done, stats = srv.run(reqs, max_wall=args.serve_seconds * 6 + 30)
+        done, stats = srv.run(reqs, max_wall=warm_s + meas_s + 60.0, window=window)
+    inner = srv.params[2]["inner_cycles"]
+    moved = sum(d["steps"] * serve_step_bytes(d["dim"], d["n"], inner) for d in done
+                if window[0] <= d["done_at"] < window[1])
+    hbm_peak, peak_kind = peaks()
+    gbs = moved / meas_s / 1e9
     saturated = stats["unfinished"] > 0 or stats["solves_per_s"] < 0.9 * rate
     extra = {} if args.no_cpu_baseline else {"cpu_baseline": cpu_baseline_c5(reqs)}
     _line(METRIC, stats["solves_per_s"], "solves/s (served; p50/p99 latency in fields)", True,
           1e3 * stats["wall_s"] / max(1, stats["steps"]), args,
-          {"workload": f"serving: Poisson arrivals at {rate:g} req/s for {args.serve_seconds:g} s ({count} requests); "
-                       "70% 2D Poisson 65^2..4097^2 (RBGS V(2,1)), 30% 3D 33^3..257^3 (Jacobi V(2,2)), sizes "
-                       "log-uniform over 2^m+1, f ~ U[-1,1], tol 1e-6 or 1e-10; 2D FP32-DC, 3D BF16-DC, 3 inner "
-                       "cycles per outer step; 150 GB HBM budget; "
-                       "hierarchies resident and pooled; same-level batching across requests"},
+          {"workload": f"serving: Poisson arrivals at {rate:g} req/s, {warm_s:g} s warm-up then {meas_s:g} s measured "
+                       f"({count} requests); 70% 2D Poisson 65^2..4097^2 (RBGS V(2,1)), 30% 3D 33^3..257^3 (Jacobi "
+                       "V(2,2)), sizes log-uniform over 2^m+1, f ~ U[-1,1], tol 1e-6 or 1e-10; 2D FP32-DC, 3D BF16-DC, "
+                       "3 inner cycles per outer step; 150 GB HBM budget; hierarchies resident and pooled; "
+                       "same-level batching across requests; 2D and 3D batches on two streams"},
           "f32 (2D) / bf16-stored f32 (3D) inner, f64 outer", p50_ms=stats["p50_ms"], p99_ms=stats["p99_ms"],
           serving=stats,
+          achieved_gbs={"value": gbs, "frac_of_peak": gbs / hbm_peak, "peak": hbm_peak, "peak_kind": peak_kind,
+                        "how": "operator-model bytes (serve_step_bytes) of every step of the requests completed in "
+                               "the measured window / its length"},
           saturated=saturated, clocks=clk.summary(), **extra)
 
 
@@ -1112,7 +1144,8 @@ def main():
                     help="c2 (default): the 8193^2 headline; others print their own line")
     ap.add_argument("--batch-problems", type=int, default=4096)
     ap.add_argument("--rate", type=float, default=2000.0)
-    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0, help="c5: measured seconds of arrivals")
+    ap.add_argument("--serve-warmup", type=float, default=5.0, help="c5: warm-up seconds of arrivals before them")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

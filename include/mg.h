@@ -161,7 +161,9 @@ size_t mg_workspace_bytes(int dim, int n, int variable_k, const mg_options *opt)
  * (plus boundary values), the right-hand side at zero.
  * Returns MG_EINVAL for dim not 2/3, n not 2^m+1 with m >= 1, bad options;
  * MG_ENOMEM if arena_bytes < mg_workspace_bytes. On success *out owns a
- * host-side context released by mg_destroy. */
+ * host-side context released by mg_destroy. The set-up is queued on
+ * options.stream; the call waits for it only when k or boundary values are
+ * given (those arrays may be released when it returns). */
 mg_status mg_create(int dim, int n, const mg_const_stencil *stencil, const double *k,
                     const mg_boundary *bc, const mg_options *opt, void *arena,
                     size_t arena_bytes, mg_ctx **out);
@@ -354,7 +356,9 @@ mg_status mg_batch_destroy(mg_batch *batch);
 /* Adds a context (borrowed; it must outlive its membership) and returns its
  * id. MG_EINVAL if its options differ from the batch's, or for Jacobi with
  * an odd nu1 + nu2; MG_ENOMEM if the batch is full. The problem's initial
- * residual is taken at its first step. */
+ * residual is taken at its first step. Work already queued on the context's
+ * own stream (mg_set_rhs, mg_set_solution) is ordered before the batch's
+ * later steps through an event, without waiting on the host. */
 mg_status mg_batch_add(mg_batch *batch, mg_ctx *ctx, int *id);
 mg_status mg_batch_remove(mg_batch *batch, int id);
 
@@ -362,6 +366,19 @@ mg_status mg_batch_remove(mg_batch *batch, int id);
  * variable stencil). rho (may be NULL) receives each problem's relative
  * residual ||r|| / ||r_0|| after the step. Synchronises the batch stream. */
 mg_status mg_batch_step(mg_batch *batch, const int *ids, int count, double *rho);
+
+/* The same step in two halves, so that the host can work (and another
+ * batch's step run on its own stream) while it runs: mg_batch_step_async
+ * enqueues the step on the batch stream, with copies of the norms into
+ * pinned host memory and an event after them, and returns; ids is copied.
+ * mg_batch_step_wait waits for that event and fills rho (count entries, in
+ * the order of ids; may be NULL). One step may be in flight per batch:
+ * mg_batch_step_async, mg_batch_step and mg_batch_solve refuse with
+ * MG_EINVAL while one is, and mg_batch_step_wait refuses when none is.
+ * Problems may be added while a step is in flight (they join the next one);
+ * contexts must not be removed or destroyed until it has been waited for. */
+mg_status mg_batch_step_async(mg_batch *batch, const int *ids, int count);
+mg_status mg_batch_step_wait(mg_batch *batch, double *rho);
 
 /* Steps every problem in the batch until its relative residual is at most
  * tol[id] or maxit steps; iters[id] and relres[id] (arrays indexed by id,

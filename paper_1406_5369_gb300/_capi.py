@@ -96,6 +96,8 @@ SIGNATURES = {
     "mg_batch_add": (_I, [_P, _P, ctypes.POINTER(_I)]),
     "mg_batch_remove": (_I, [_P, _I]),
     "mg_batch_step": (_I, [_P, ctypes.POINTER(_I), _I, ctypes.POINTER(_D)]),
+    "mg_batch_step_async": (_I, [_P, ctypes.POINTER(_I), _I]),
+    "mg_batch_step_wait": (_I, [_P, ctypes.POINTER(_D)]),
     "mg_batch_solve": (_I, [_P, ctypes.POINTER(_D), _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "mg_batch_launches": (ctypes.c_ulonglong, [_P]),
     "mg_batch_set_inner_cycles": (_I, [_P, _I]),

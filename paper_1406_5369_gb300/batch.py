@@ -47,6 +47,18 @@ class BatchSolver:
                                         rho.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return rho
 
+    def step_async(self, ids):
+        """Enqueues one step (mg_batch_step_async); step_wait() completes it."""
+        ids = np.ascontiguousarray(ids, dtype=np.int32)
+        self._pending = len(ids)
+        C.check(self._lib.mg_batch_step_async(self.h, ids.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), len(ids)))
+
+    def step_wait(self):
+        """Waits for the step in flight; returns rho in the order of its ids."""
+        rho = np.zeros(max(getattr(self, "_pending", 0), 1))
+        C.check(self._lib.mg_batch_step_wait(self.h, rho.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return rho[: self._pending]
+
     def solve(self, tol, maxit=50, raise_on_noconv=True):
         """tol: scalar or {id: tol}; returns (iters, relres) arrays indexed by id."""
         tols = np.zeros(self.max_problems)

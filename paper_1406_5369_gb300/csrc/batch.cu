@@ -389,6 +389,12 @@ struct mg_batch {
   char *hstage;                // pinned: r0 and tol uploads, remaining-counter reads
   cudaEvent_t ev[2];
   double phase_ms[5];          // last mg_batch_solve: host wall time of its phases
+  // a step in flight (mg_batch_step_async): its problems, the fresh ones,
+  // the pinned copies of their norms and the event that completes them
+  bool step_pending;
+  std::vector<int> step_ids, step_fresh;
+  double *hstep;               // pinned: maxp step norms, then maxp initial norms
+  cudaEvent_t step_ev, add_ev;
   // kernel timing (mg_batch_set_timing): event pairs around launch groups
   // of uncaptured steps, harvested at the step's synchronisation
   int timing;
@@ -1363,6 +1369,9 @@ mg_status mg_batch_create(int max_problems, void *workspace, size_t bytes, void 
   b->hstage = nullptr;
   b->cap = nullptr;
   b->ev[0] = b->ev[1] = nullptr;
+  b->step_pending = false;
+  b->hstep = nullptr;
+  b->step_ev = b->add_ev = nullptr;
   for (int i = 0; i < 5; i++) b->phase_ms[i] = 0.0;
   b->timing = 0;
   for (int i = 0; i < 8; i++) b->t_ms[i] = b->t_bytes[i] = 0.0, b->t_n[i] = 0;
@@ -1370,7 +1379,10 @@ mg_status mg_batch_create(int max_problems, void *workspace, size_t bytes, void 
       cudaMallocHost((void **)&b->hstage, 2 * sizeof(double) * (size_t)max_problems + 64) != cudaSuccess ||
       cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev[0], cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->ev[1], cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&b->ev[1], cudaEventDisableTiming) != cudaSuccess ||
+      cudaMallocHost((void **)&b->hstep, 2 * sizeof(double) * (size_t)max_problems) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->step_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->add_ev, cudaEventDisableTiming) != cudaSuccess) {
     mg_batch_destroy(b);
     return bfail(MG_ENOMEM, "pinned host staging, capture stream or events of the batch failed");
   }
@@ -1382,6 +1394,9 @@ mg_status mg_batch_destroy(mg_batch *b) {
   if (!b) return MG_OK;
   if (b->pinned) cudaFreeHost(b->pinned);
   if (b->hstage) cudaFreeHost(b->hstage);
+  if (b->hstep) cudaFreeHost(b->hstep);
+  if (b->step_ev) cudaEventDestroy(b->step_ev);
+  if (b->add_ev) cudaEventDestroy(b->add_ev);
   if (b->cap) cudaStreamDestroy(b->cap);
   for (int i = 0; i < 2; i++)
     if (b->ev[i]) cudaEventDestroy(b->ev[i]);
@@ -1409,6 +1424,12 @@ mg_status mg_batch_add(mg_batch *b, mg_ctx *c, int *id) {
         b->fp64 = !c->dc;
         b->have_opts = true;
       }
+      // the batch's kernels read what the context's stream wrote (its
+      // right-hand side, a reset solution): order them after it
+      if (c->stream != b->stream &&
+          (cudaEventRecord(b->add_ev, c->stream) != cudaSuccess ||
+           cudaStreamWaitEvent(b->stream, b->add_ev, 0) != cudaSuccess))
+        return bfail(MG_ECUDA, "ordering the problem's stream before the batch's");
       b->probs[i] = c;
       b->r0[i] = -1.0;
       *id = i;
@@ -1425,9 +1446,10 @@ mg_status mg_batch_remove(mg_batch *b, int id) {
   return MG_OK;
 }
 
-mg_status mg_batch_step(mg_batch *b, const int *ids, int count, double *rho) {
-  if (!b || (count > 0 && !ids)) return bfail(MG_EINVAL, "NULL argument");
-  if (count == 0) return MG_OK;
+// Builds and enqueues one step of the `count` problems in ids on the batch
+// stream: the initial norms of new problems, the step, copies of both into
+// pinned host memory and an event after them. step_finish completes it.
+static mg_status step_enqueue(mg_batch *b, const int *ids, int count) {
   std::vector<mg_ctx *> ps, fresh;
   std::vector<int> fresh_ids;
   for (int i = 0; i < count; i++) {
@@ -1444,35 +1466,75 @@ mg_status mg_batch_step(mg_batch *b, const int *ids, int count, double *rho) {
     if ((c->variable != 0) != var) return bfail(MG_EINVAL, "a step mixes constant and variable stencils");
   mg_status st;
   b->dev_off = 0;
-  // initial residual (and, with defect correction, the first defect) of new problems
+  // initial residual (and, with defect correction, the first defect) of new
+  // problems; its norms are copied out before the step overwrites them
   if (!fresh.empty()) {
-    std::vector<double> h(fresh.size());
     if ((st = batched_norms(b, fresh))) return st;
-    BCK("read initial norms", cudaMemcpyAsync(h.data(), b->norms, sizeof(double) * fresh.size(),
+    BCK("copy initial norms", cudaMemcpyAsync(b->hstep + b->maxp, b->norms, sizeof(double) * fresh.size(),
                                               cudaMemcpyDeviceToHost, b->stream));
-    BCK("synchronize", cudaStreamSynchronize(b->stream));
-    for (size_t i = 0; i < fresh.size(); i++) b->r0[fresh_ids[i]] = h[i];
-    b->dev_off = 0;
   }
   int inner = b->dc ? std::max(b->opt.inner_cycles, 1) : 1;
   for (int k = 0; k < inner; k++)
     if ((st = batched_vcycle(b, ps, b->dc && k == 0))) return st;
   if ((st = b->dc ? batched_outer(b, ps, true) : batched_norms(b, ps))) return st;
-  std::vector<double> h(count);
-  BCK("read norms", cudaMemcpyAsync(h.data(), b->norms, sizeof(double) * count, cudaMemcpyDeviceToHost, b->stream));
-  BCK("synchronize", cudaStreamSynchronize(b->stream));
+  BCK("copy norms", cudaMemcpyAsync(b->hstep, b->norms, sizeof(double) * count, cudaMemcpyDeviceToHost, b->stream));
+  BCK("step event", cudaEventRecord(b->step_ev, b->stream));
+  b->step_ids.assign(ids, ids + count);
+  b->step_fresh = fresh_ids;
+  b->step_pending = true;
+  return MG_OK;
+}
+
+// Waits for the step in flight and forms each problem's rho = ||r|| / ||r_0||.
+static mg_status step_finish(mg_batch *b, double *rho) {
+  b->step_pending = false;
+  BCK("synchronize", cudaEventSynchronize(b->step_ev));
+  for (size_t i = 0; i < b->step_fresh.size(); i++) b->r0[b->step_fresh[i]] = b->hstep[b->maxp + i];
   b->dev_off = 0;
   harvest(b);
   if (rho)
-    for (int i = 0; i < count; i++) {
-      double r0 = b->r0[ids[i]];
-      rho[i] = r0 > 0.0 ? h[i] / r0 : 0.0;
+    for (size_t i = 0; i < b->step_ids.size(); i++) {
+      double r0 = b->r0[b->step_ids[i]];
+      rho[i] = r0 > 0.0 ? b->hstep[i] / r0 : 0.0;
     }
   return MG_OK;
 }
 
+mg_status mg_batch_step(mg_batch *b, const int *ids, int count, double *rho) {
+  if (!b || (count > 0 && !ids)) return bfail(MG_EINVAL, "NULL argument");
+  if (b->step_pending) return bfail(MG_EINVAL, "a step started by mg_batch_step_async is still in flight");
+  if (count == 0) return MG_OK;
+  mg_status st = step_enqueue(b, ids, count);
+  if (st) {
+    b->step_pending = false;
+    return st;
+  }
+  return step_finish(b, rho);
+}
+
+mg_status mg_batch_step_async(mg_batch *b, const int *ids, int count) {
+  if (!b || (count > 0 && !ids)) return bfail(MG_EINVAL, "NULL argument");
+  if (b->step_pending) return bfail(MG_EINVAL, "a step started by mg_batch_step_async is still in flight");
+  if (count == 0) {
+    b->step_ids.clear();
+    b->step_fresh.clear();
+    b->step_pending = true;  // a step of no problems: step_wait returns at once
+    return cudaEventRecord(b->step_ev, b->stream) == cudaSuccess ? MG_OK : bfail(MG_ECUDA, "step event");
+  }
+  mg_status st = step_enqueue(b, ids, count);
+  if (st) b->step_pending = false;
+  return st;
+}
+
+mg_status mg_batch_step_wait(mg_batch *b, double *rho) {
+  if (!b) return bfail(MG_EINVAL, "NULL batch");
+  if (!b->step_pending) return bfail(MG_EINVAL, "no step in flight");
+  return step_finish(b, rho);
+}
+
 mg_status mg_batch_solve(mg_batch *b, const double *tol, int maxit, int *iters, double *relres) {
   if (!b || !tol) return bfail(MG_EINVAL, "NULL argument");
+  if (b->step_pending) return bfail(MG_EINVAL, "a step started by mg_batch_step_async is still in flight");
   std::vector<int> active;
   for (int i = 0; i < b->maxp; i++)
     if (b->probs[i]) {

@@ -272,15 +272,6 @@ cudaError_t copy_dense_interior(const Level &L, const double *src, void *dst, cu
   return cudaMemcpy3DAsync(&p, s);
 }
 
-// Zeroes the interior box of a pitched FP64 field (boundary untouched).
-cudaError_t zero_interior_box(const Level &L, void *dst, cudaStream_t s) {
-  size_t n = (size_t)L.n, m = n - 2, es = (size_t)mg::dtype_size(L.dtype);
-  if (L.dim == 2)
-    return cudaMemset2DAsync((char *)dst + ((size_t)L.pitch + 1) * es, (size_t)L.pitch * es, 0, m * es, m, s);
-  cudaPitchedPtr p = make_cudaPitchedPtr((char *)dst + ((size_t)L.plane + L.pitch + 1) * es, (size_t)L.pitch * es,
-                                         m, n);
-  return cudaMemset3DAsync(p, 0, make_cudaExtent(m * es, m, m), s);
-}
 
 // ---------------------------------------------------------------- level ops
 
@@ -629,6 +620,11 @@ mg_status read_norm(mg_ctx *c, double *out) {
 
 // ---------------------------------------------------------------- ABI
 
+namespace {
+// The norm scale of a new context: four FP32 ones (no host upload).
+__global__ void k_ones4(float *p) { p[threadIdx.x] = 1.0f; }
+}  // namespace
+
 extern "C" {
 
 void mg_default_options(mg_options *o) {
@@ -742,11 +738,12 @@ mg_status mg_create(int dim, int n, const mg_const_stencil *stencil, const doubl
     c->launches++;
     CKC(cudaMemcpyAsync(U.u[1], U.u[0], (size_t)U.count * 8, cudaMemcpyDeviceToDevice, c->stream));
   }
-  {
-    static const float one[4] = {1.0f, 1.0f, 1.0f, 1.0f};
-    CKC(cudaMemcpyAsync(c->dc_scale, one, sizeof one, cudaMemcpyHostToDevice, c->stream));
-  }
-  CKC(cudaStreamSynchronize(c->stream));
+  k_ones4<<<1, 4, 0, c->stream>>>(c->dc_scale);
+  CKC(cudaGetLastError());
+  // The caller's k and boundary arrays are borrowed for this call only: wait
+  // until their copies have run. Without them nothing needs waiting for; the
+  // set-up stays queued on the stream ahead of the context's later work.
+  if (k || (bc && bc->dirichlet_values)) CKC(cudaStreamSynchronize(c->stream));
 #undef CKC
   *out = c;
   return MG_OK;
@@ -795,7 +792,10 @@ mg_status mg_set_solution(mg_ctx *c, const double *u0) {
   Level &U = user_level(c);
   void *dst = user_u(c);
   if (!u0) {
-    CK(zero_interior_box(U, dst, c->stream));
+    // one kernel: a 2D/3D memset of the interior box cost ~0.6 ms of host
+    // time per call (the serving loop sets up thousands of solves a second)
+    CK(DISPATCH(U, zero_interior, U, dst, c->stream));
+    c->launches++;
   } else {
     CK(copy_dense_interior(U, u0, dst, c->stream));
   }

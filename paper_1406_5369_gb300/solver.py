@@ -49,7 +49,7 @@ class Solver:
     def __init__(self, dim, n, *, stencil=(1.0, 1.0, 1.0), k=None, dirichlet=None,
                  smoother="rbgs", omega=1.0, nu1=2, nu2=1, maxit=50, precision="fp64",
                  fuse=True, use_graph=True, inner_cycles=1, exact_outer=True, tile_rows=0, tile_max_n=0,
-                 fuse_depth=0, join_cycles=True, coarsest_n=3, stream=None, device="cuda"):
+                 fuse_depth=0, join_cycles=True, coarsest_n=3, stream=None, device="cuda", arena=None):
         import torch
         self._lib = C.load()
         self.dim, self.n = dim, n
@@ -76,7 +76,14 @@ class Solver:
         if nbytes == 0:
             raise C.MGError(C.MG_EINVAL, self._lib.mg_last_error().decode())
         self.workspace_bytes = nbytes
-        self.arena = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        if arena is None:
+            self.arena = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        else:
+            # the caller's device memory (a uint8 tensor of at least nbytes,
+            # 256-byte aligned), e.g. a slice of a pool it manages itself
+            if arena.numel() < nbytes or arena.data_ptr() % 256:
+                raise ValueError("arena must hold workspace_bytes and start 256-byte aligned")
+            self.arena = arena
         st = C.mg_const_stencil(*[float(x) for x in (list(stencil) + [1.0] * 3)[:3]])
         kp, self._k_keep = _ptr(k, dim, n)
         bc = None

@@ -193,10 +193,18 @@ def _t_shr(z, k):
     return (z >> k) & ((1 << (64 - k)) - 1)
 
 
-def torch_splitmix64(seed: int, count: int, start: int = 0, device="cpu"):
+def torch_seed(seed: int) -> int:
+    """A seed as the signed 64-bit integer the torch generators add: the value
+    to store in a 0-dim int64 tensor passed as `seed` (e.g. one a CUDA graph
+    of a generator reads)."""
+    return _t_const(seed & 0xFFFFFFFFFFFFFFFF)
+
+
+def torch_splitmix64(seed, count: int, start: int = 0, device="cpu"):
+    """seed: an int, or a 0-dim int64 tensor holding torch_seed(seed)."""
     import torch
     idx = torch.arange(start + 1, start + count + 1, dtype=torch.int64, device=device)
-    z = idx * _T_GAMMA + _t_const(seed & 0xFFFFFFFFFFFFFFFF)
+    z = idx * _T_GAMMA + (seed if isinstance(seed, torch.Tensor) else torch_seed(seed))
     z = (z ^ _t_shr(z, 30)) * _T_M1
     z = (z ^ _t_shr(z, 27)) * _T_M2
     return z ^ _t_shr(z, 31)

@@ -215,3 +215,55 @@ def test_batch_kernel_timing_counts_groups_and_bytes_without_changing_results():
             B.reset_timing()
             assert B.timing("pre") == (0.0, 0, 0.0)
     assert outs[0][0] == outs[1][0] and np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_async_steps_on_two_streams_equal_synchronous_steps():
+    """mg_batch_step_async / mg_batch_step_wait on a 2D and a 3D batch, each
+    on a stream of its own and both in flight at once, give the same ratios
+    and solutions, bit for bit, as mg_batch_step; a problem added while a step
+    is in flight joins the next step; misuse is refused."""
+    torch = need_gpu()
+    from paper_1406_5369_gb300 import BatchSolver, MGError
+    kw3 = dict(prec="bf16_dc", smoother="jacobi", omega=6 / 7, nu=(2, 2), inner=2)
+
+    def make_all():
+        p2 = [make_problem(2, m, 800 + i, inner=3) for i, m in enumerate([6, 8, 7])]
+        p3 = [make_problem(3, m, 850 + i, **kw3) for i, m in enumerate([5, 4])]
+        return p2, p3
+
+    # synchronous reference
+    p2, p3 = make_all()
+    B2, B3 = BatchSolver(4), BatchSolver(4)
+    i2 = [B2.add(p[0]) for p in p2]
+    i3 = [B3.add(p[0]) for p in p3]
+    ref = [(B2.step(i2), B3.step(i3)) for _ in range(4)]
+    ref_u = [p[0].get_solution() for p in p2 + p3]
+    # asynchronous, two streams
+    q2, q3 = make_all()
+    s2, s3 = torch.cuda.Stream(), torch.cuda.Stream()
+    A2, A3 = BatchSolver(4, stream=s2.cuda_stream), BatchSolver(4, stream=s3.cuda_stream)
+    j2 = [A2.add(p[0]) for p in q2]
+    j3 = [A3.add(p[0]) for p in q3]
+    for k in range(4):
+        A2.step_async(j2)
+        A3.step_async(j3)
+        with pytest.raises(MGError):
+            A2.step_async(j2)  # one step in flight per batch
+        r3 = A3.step_wait()
+        r2 = A2.step_wait()
+        assert np.array_equal(r2, ref[k][0]) and np.array_equal(r3, ref[k][1]), k
+    with pytest.raises(MGError):
+        A2.step_wait()  # nothing in flight
+    for p, u in zip(q2 + q3, ref_u):
+        assert np.array_equal(p[0].get_solution(), u)
+    # a problem added while a step runs takes its first step with the next one
+    late, f_late, _ = make_problem(2, 6, 800, inner=3)
+    A2.step_async(j2)
+    jl = A2.add(late)
+    A2.step_wait()
+    A2.step_async([jl])
+    rl = A2.step_wait()
+    fresh, _, _ = make_problem(2, 6, 800, inner=3)
+    B1 = BatchSolver(1)
+    B1.add(fresh)
+    assert np.array_equal(rl, B1.step([0]))

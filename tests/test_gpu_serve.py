@@ -26,7 +26,7 @@ def test_server_mix_equals_alone_and_meets_tolerance():
     from paper_1406_5369_gb300.serve import Server
     reqs = requests()
     srv = Server(budget_bytes=4e9, max_active=16)
-    done, stats = srv.run(reqs, keep_solutions=True)
+    done, stats = srv.run(reqs, keep_solutions=True, max_wall=120.0)
     assert stats["completed"] == len(reqs) and stats["unfinished"] == 0
     by_id = {d["id"]: d for d in done}
     for r in reqs:
@@ -37,7 +37,7 @@ def test_server_mix_equals_alone_and_meets_tolerance():
         assert res <= 1.01 * r["tol"], (r, res)
     for r in (reqs[2], reqs[8], reqs[6]):
         alone = Server(budget_bytes=4e9, max_active=2)
-        d1, _ = alone.run([dict(r, t=0.0)], keep_solutions=True)
+        d1, _ = alone.run([dict(r, t=0.0)], keep_solutions=True, max_wall=60.0)
         assert d1[0]["steps"] == by_id[r["id"]]["steps"]
         assert np.array_equal(d1[0]["u"], by_id[r["id"]]["u"])
 
@@ -46,10 +46,9 @@ def test_server_admission_respects_budget():
     need_gpu()
     from paper_1406_5369_gb300.serve import Server
     reqs = [{"id": i, "t": 0.0, "dim": 2, "n": 257, "tol": 1e-6, "seed": 7 + i} for i in range(6)]
-    srv = Server(budget_bytes=1.0, max_active=8)
-    one = srv._bytes(2, 257)
-    srv.budget = 2.5 * one  # room for two hierarchies at a time
-    done, stats = srv.run(reqs)
+    one = Server(budget_bytes=1.0, max_active=1, device="cpu")._bytes(2, 257)
+    srv = Server(budget_bytes=2.5 * one, max_active=8)  # room for two hierarchies at a time
+    done, stats = srv.run(reqs, max_wall=120.0)
     assert stats["completed"] == 6
     assert srv.peak_used <= srv.budget
     assert stats["max_queue_depth"] >= 3

@@ -506,6 +506,10 @@ def test_torch_generator_matches_numpy_bitwise():
         a = synth.uniform_rhs(dim, n, 99)
         b = synth.torch_uniform_rhs(dim, n, 99).numpy()
         assert np.array_equal(a, b)
+    # a seed held in a tensor (as a captured generator reads it) draws the same values
+    for seed in (99, 0xFFFFFFFF, 0x5EED0005 ^ 12345):
+        t = torch.tensor(synth.torch_seed(seed), dtype=torch.int64)
+        assert np.array_equal(synth.uniform_rhs(2, 33, seed), synth.torch_uniform_rhs(2, 33, t).numpy())
 
 
 def test_coarse_faces_conserve_parallel_conductance():
