@@ -182,7 +182,7 @@ KERNEL_TRAFFIC = {
     "k_dcx2d": 2185.6e6,   # algorithmic 32 B/node = 2148 MB
     "k_pre2d_x2": 875.7e6,  # a launch that reads u: algorithmic 13 B/node = 872.6 MB
     "k_post2d_x2": 877.8e6,  # algorithmic 13 B/node = 872.6 MB
-    "k_postpre2d_x2": None,  # not captured yet
+    "k_postpre2d_x2": 942.3e6,  # algorithmic 14 B/node = 939.8 MB
 }
 TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of this kernel build at 8193^2, "
                   "captured separately (not in this run)")
