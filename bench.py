@@ -275,7 +275,10 @@ def run_gpu(args):
     coarse_ms = sum(s.timing("coarse", l)[0] for l in range(s.levels)) / 2 * args.steps
     pre_all = sum(s.timing("pre", l)[0] for l in range(s.levels)) / 2 * args.steps
     post_all = sum(s.timing("post", l)[0] for l in range(s.levels)) / 2 * args.steps
+    postpre_all = sum(s.timing("postpre", l)[0] for l in range(s.levels)) / 2 * args.steps
     norm_all = sum(s.timing("norm", l)[0] for l in range(s.levels)) / 2 * args.steps
+    # smoothing-pass time per level and solve (pre + post + joined passes)
+    per_level = [sum(s.timing(k, l)[0] for k in ("pre", "post", "postpre")) / 2 for l in range(s.levels)]
     s.set_timing(False)
 
     # plain FP64 V-cycle solve of the same problem (beside the headline)
@@ -443,8 +446,11 @@ def run_gpu(args):
         "roofline": roofline,
         "roofline_kernels": lines,
         "time_split_ms": {"outer": t_outer / args.steps, "pre_all_levels": pre_all / args.steps,
-                          "post_all_levels": post_all / args.steps, "coarse": coarse_ms / args.steps,
-                          "norm": norm_all / args.steps,
+                          "post_all_levels": post_all / args.steps,
+                          "joined_post_pre_all_levels": postpre_all / args.steps,
+                          "coarse": coarse_ms / args.steps, "norm": norm_all / args.steps,
+                          "smoothing_passes_per_level": [{"n": (n - 1) // (1 << l) + 1, "ms": v}
+                                                         for l, v in enumerate(per_level) if v > 0],
                           "source": "outer: timed region; the all-level sums: two solves after it with every "
                                     "kernel timed"},
         "clocks": clk_sum,

@@ -87,8 +87,8 @@ fz::Args2D make_args(const Level &L, const Level &Cl, double omega, int R_overri
 template <typename T, int NU, bool ZERO, bool VAR = false>
 cudaError_t launch_pre(fz::Args2D a, int R_override, const Level &L, cudaStream_t s, const fz::Args2D *list = nullptr,
                        int count = 1) {
-  constexpr int W = fz::Warps<T>::value;
-  constexpr size_t smem = (size_t)W * (fz::kRing * 32 * fz::Lane<T>::bytes * 2 +
+  constexpr int W = fz::Warps<T, VAR>::value;
+  constexpr size_t smem = (size_t)W * (fz::kRing * 32 * fz::Lane<T>::bytes * (ZERO ? 1 : 2) +
                                        (VAR ? (size_t)fz::kFaceRing * 32 * fz::Lane<T>::bytes * 2 : 0));
   static bool ready = false;
   static int bps = 1;
@@ -112,7 +112,7 @@ cudaError_t launch_pre(fz::Args2D a, int R_override, const Level &L, cudaStream_
 template <typename T, int NU, bool VAR = false>
 cudaError_t launch_post(fz::Args2D a, int R_override, const Level &L, cudaStream_t s, const fz::Args2D *list = nullptr,
                         int count = 1) {
-  constexpr int W = fz::Warps<T>::value;
+  constexpr int W = fz::Warps<T, VAR>::value;
   constexpr size_t smem = (size_t)W * (fz::kRing * 32 * (2 * fz::Lane<T>::bytes + 2 * sizeof(T)) +
                                        (VAR ? (size_t)fz::kFaceRing * 32 * fz::Lane<T>::bytes * 2 : 0));
   static bool ready = false;

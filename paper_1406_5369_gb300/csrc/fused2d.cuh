@@ -48,12 +48,20 @@ constexpr int kOut = kCols - 2 * kHalo;  // columns written per strip
 constexpr int kSlots = 8;                // row window in registers
 constexpr int kGroup = 4;                // rows per cp.async commit group
 constexpr int kRing = 2 * kGroup;        // row ring in shared memory: two groups in flight
-// Warps per block: the shared-memory ring of FP64 rows is twice as large.
-template <typename T> struct Warps { static constexpr int value = sizeof(T) == 8 ? 2 : 4; };
+// Warps per block: the shared-memory ring of FP64 rows is twice as large;
+// variable-stencil warps carry 16 face rows besides and run in blocks of 2,
+// so that the per-SM residency is set by the per-warp footprint alone.
+template <typename T, bool VAR = false> struct Warps {
+  static constexpr int value = (sizeof(T) == 8 || VAR) ? 2 : 4;
+};
 // Resident blocks asked of the register allocator: 5 blocks of 4 FP32 warps
 // (at most 96 registers per thread); FP64 kernels are bound by the FP64 pipe
-// and keep their natural register count.
-template <typename T> struct MinBlocks { static constexpr int value = sizeof(T) == 8 ? 1 : 5; };
+// and keep their natural register count. FP32 variable-stencil blocks of 2
+// warps: as many as their shared memory admits (20 KB per warp starting from
+// zero, 24 KB otherwise, 26 KB for post-smoothing: 5, 4 and 4 blocks).
+template <typename T, bool VAR = false, int VBLOCKS = 4> struct MinBlocks {
+  static constexpr int value = sizeof(T) == 8 ? 1 : (VAR ? VBLOCKS : 5);
+};
 
 struct Args2D {
   const void *uin;  // level solution (ignored when starting from zero)
@@ -330,7 +338,8 @@ __device__ __forceinline__ void residual_row_var(C (&rr)[kVec], const C (&uc)[kV
 // ------------------------------------------------------------------------
 // Pre-smoothing + residual + restriction.
 template <typename T, int NU, bool ZERO, bool VAR = false>
-__global__ void __launch_bounds__(32 * Warps<T>::value, VAR ? 2 : MinBlocks<T>::value) k_pre2d(Args2D a, const Args2D *__restrict__ list) {
+__global__ void __launch_bounds__(32 * Warps<T, VAR>::value, MinBlocks<T, VAR, ZERO ? 5 : 4>::value)
+    k_pre2d(Args2D a, const Args2D *__restrict__ list) {
   typedef typename CT<T>::type C;
   extern __shared__ __align__(16) unsigned char smem[];
   if (list) {
@@ -338,7 +347,7 @@ __global__ void __launch_bounds__(32 * Warps<T>::value, VAR ? 2 : MinBlocks<T>::
     take_problem(a, list[blockIdx.y]);
   }
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const long long gw = (long long)blockIdx.x * Warps<T>::value + wib;
+  const long long gw = (long long)blockIdx.x * Warps<T, VAR>::value + wib;
   if (gw >= (long long)a.nstrips * a.nchunks) return;
   const int s = (int)(gw % a.nstrips), ch = (int)(gw / a.nstrips);
   const int n = a.n;
@@ -354,9 +363,11 @@ __global__ void __launch_bounds__(32 * Warps<T>::value, VAR ? 2 : MinBlocks<T>::
   T *uout = (T *)a.uout;
   T *fc = (T *)a.fc;
   constexpr int LB = Lane<T>::bytes;
-  constexpr size_t WB = (size_t)kRing * 32 * LB * 2 + (VAR ? (size_t)kFaceRing * 32 * LB * 2 : 0);
+  // per-warp rings: u (absent when starting from zero), f, then the faces
+  constexpr size_t UB = ZERO ? 0 : (size_t)kRing * 32 * LB;
+  constexpr size_t WB = UB + (size_t)kRing * 32 * LB + (VAR ? (size_t)kFaceRing * 32 * LB * 2 : 0);
   unsigned char *su = smem + (size_t)wib * WB;
-  unsigned char *sf = su + kRing * 32 * LB;
+  unsigned char *sf = su + UB;
   unsigned char *skx = sf + kRing * 32 * LB;          // VAR: face rings
   unsigned char *sky = skx + kFaceRing * 32 * LB;
   const T *kxg = (const T *)a.kx;
@@ -499,7 +510,8 @@ __global__ void __launch_bounds__(32 * Warps<T>::value, VAR ? 2 : MinBlocks<T>::
 // ------------------------------------------------------------------------
 // Interpolation + correction + post-smoothing.
 template <typename T, int NU, bool VAR = false>
-__global__ void __launch_bounds__(32 * Warps<T>::value, VAR ? 2 : MinBlocks<T>::value) k_post2d(Args2D a, const Args2D *__restrict__ list) {
+__global__ void __launch_bounds__(32 * Warps<T, VAR>::value, MinBlocks<T, VAR, 4>::value)
+    k_post2d(Args2D a, const Args2D *__restrict__ list) {
   typedef typename CT<T>::type C;
   extern __shared__ __align__(16) unsigned char smem[];
   if (list) {
@@ -507,7 +519,7 @@ __global__ void __launch_bounds__(32 * Warps<T>::value, VAR ? 2 : MinBlocks<T>::
     take_problem(a, list[blockIdx.y]);
   }
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const long long gw = (long long)blockIdx.x * Warps<T>::value + wib;
+  const long long gw = (long long)blockIdx.x * Warps<T, VAR>::value + wib;
   if (gw >= (long long)a.nstrips * a.nchunks) return;
   const int s = (int)(gw % a.nstrips), ch = (int)(gw / a.nstrips);
   const int n = a.n;
