@@ -46,7 +46,7 @@ WORKLOAD = {
 # kernels (0 = one wave), largest level on the block-tile kernels (0 = 257)
 # and the sweeps fused per pass (0 = all).
 TUNE_KNOBS = {"inner_cycles": [1, 2, 3, 4], "tile_rows": [0, 64, 128, 256, 512],
-              "tile_max_n": [0, 129, 513, 1025], "fuse_depth": [0, 1]}
+              "cluster_max_n": [0, 129, 1], "tile_max_n": [0, 129, 513, 1025], "fuse_depth": [0, 1]}
 
 
 def peaks():

@@ -120,7 +120,14 @@ typedef struct { int kind; const double *dirichlet_values; } mg_boundary;
  *                         pass and the next cycle's pre-smoothing pass run as
  *                         one pass (packed FP32 2D streaming levels,
  *                         nu1 + nu2 <= 3; the same operations in the same
- *                         order, so the same results), 0 = two passes */
+ *                         order, so the same results), 0 = two passes
+ * cluster_max_n         : *_DC, 2D constant stencil, RBGS only: the largest
+ *                         inner level (129 or 257) from which the V-cycle of
+ *                         every coarser level runs as one kernel on a cluster
+ *                         of 8 thread blocks holding the levels in their
+ *                         shared memory (levels 33 and below in one of them);
+ *                         0 = 257, values below 129 = never (per-level
+ *                         kernels and the single-block cycle below 65) */
 typedef struct {
   mg_smoother smoother;
   double omega;
@@ -137,13 +144,14 @@ typedef struct {
   int tile_max_n;
   int fuse_depth;
   int join_cycles;
+  int cluster_max_n;
 } mg_options;
 
 typedef struct mg_ctx mg_ctx;
 
 /* Fills *opt with RBGS, omega 1, V(2,1), coarsest 3, maxit 50, FP64,
  * default stream, fuse 1, use_graph 1, inner_cycles 1, exact_outer 1,
- * tile_rows 0, tile_max_n 0, fuse_depth 0, join_cycles 1 (the Layer-3
+ * tile_rows 0, tile_max_n 0, fuse_depth 0, join_cycles 1, cluster_max_n 0 (the Layer-3
  * defaults of Sec. 2.3 and automatic tiling). */
 void mg_default_options(mg_options *opt);
 

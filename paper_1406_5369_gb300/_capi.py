@@ -36,7 +36,7 @@ class mg_options(ctypes.Structure):
                 ("precision", ctypes.c_int), ("stream", ctypes.c_void_p), ("fuse", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("inner_cycles", ctypes.c_int), ("exact_outer", ctypes.c_int),
                 ("tile_rows", ctypes.c_int), ("tile_max_n", ctypes.c_int), ("fuse_depth", ctypes.c_int),
-                ("join_cycles", ctypes.c_int)]
+                ("join_cycles", ctypes.c_int), ("cluster_max_n", ctypes.c_int)]
 
 
 class mg_cc_params(ctypes.Structure):

@@ -189,13 +189,12 @@ __device__ void smooth(const Lev<C> &L, C *tmp, const C (&c)[3], int smoother, C
   }
 }
 
+template <int DIM, bool VAR, typename C> __device__ void cycle_in_smem(const CoarseArgs &a, C *sm);
+
 template <int DIM, bool VAR, typename C>
 __device__ __forceinline__ void coarse_cycle_body(const CoarseArgs &a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *sm = (C *)smem_raw;
-  const C c[3] = {pick<C>(a.c[0], a.cf[0]), pick<C>(a.c[1], a.cf[1]), pick<C>(a.c[2], a.cf[2])};
-  const C omega = pick<C>(a.omega, a.omegaf);
-  C *tmp = sm + a.off_tmp;
   for (int p = threadIdx.x; p < a.total; p += kThreads) sm[p] = (C)0;
   __syncthreads();
   // load the top level (and the faces of every level)
@@ -223,6 +222,25 @@ __device__ __forceinline__ void coarse_cycle_body(const CoarseArgs &a) {
     }
   }
   __syncthreads();
+  cycle_in_smem<DIM, VAR, C>(a, sm);
+  // write back the top level's solution
+  {
+    Lev<C> T = level<DIM, VAR, C>(a, sm, 0);
+    for_interior<DIM>(a.n[0], [&](int p, int i, int j, int k) {
+      long long g = (long long)k * a.plane[0] + (long long)j * a.pitch[0] + i;
+      stg_as<C>(a.u_top, g, a.top_dtype, T.u[p]);
+    });
+  }
+}
+
+// The V-cycle of levels 0 .. a.nlev-1 held in shared memory at sm (offsets
+// in a): level 0's right-hand side and solution are in place, every coarser
+// solution is zero. Ends with level 0's solution in place (after a block
+// barrier).
+template <int DIM, bool VAR, typename C> __device__ void cycle_in_smem(const CoarseArgs &a, C *sm) {
+  const C c[3] = {pick<C>(a.c[0], a.cf[0]), pick<C>(a.c[1], a.cf[1]), pick<C>(a.c[2], a.cf[2])};
+  const C omega = pick<C>(a.omega, a.omegaf);
+  C *tmp = sm + a.off_tmp;
   // descend
   for (int l = 0; l + 1 < a.nlev; l++) {
     const Lev<C> F = level<DIM, VAR, C>(a, sm, l);
@@ -327,14 +345,7 @@ __device__ __forceinline__ void coarse_cycle_body(const CoarseArgs &a) {
     __syncthreads();
     smooth<DIM, VAR, C>(F, tmp, c, a.smoother, omega, a.nu2);
   }
-  // write back the top level's solution
-  {
-    Lev<C> T = level<DIM, VAR, C>(a, sm, 0);
-    for_interior<DIM>(a.n[0], [&](int p, int i, int j, int k) {
-      long long g = (long long)k * a.plane[0] + (long long)j * a.pitch[0] + i;
-      stg_as<C>(a.u_top, g, a.top_dtype, T.u[p]);
-    });
-  }
+  __syncthreads();
 }
 
 template <int DIM, bool VAR, typename C>

@@ -18,7 +18,9 @@
 // SM. Rows are processed 8 at a time by straight-line code (the register
 // window), which lets the compiler overlap consecutive rows. Warps whose
 // rows and columns are all interior run a copy of that code without the
-// boundary predicates. Half-sweep h of the stack runs
+// boundary predicates (constant stencil only: the variable-stencil body is
+// large enough that a second copy costs more in instruction-fetch stalls
+// than the predicates it saves). Half-sweep h of the stack runs
 // on row t - h when row t arrives (red = i+j even first, as in the paper's
 // "order rb"), so every update sees exactly the neighbour values a
 // sequential red-then-black sweep would; the x-neighbours of a lane's edge
@@ -502,8 +504,13 @@ __global__ void __launch_bounds__(32 * Warps<T, VAR>::value, MinBlocks<T, VAR, Z
     });
   }
   };
-  if (interior_warp) body(std::false_type{});
-  else body(std::true_type{});
+  if constexpr (VAR) {
+    (void)interior_warp;
+    body(std::true_type{});
+  } else {
+    if (interior_warp) body(std::false_type{});
+    else body(std::true_type{});
+  }
   cp_async_wait<0>();
 }
 
@@ -680,8 +687,13 @@ __global__ void __launch_bounds__(32 * Warps<T, VAR>::value, MinBlocks<T, VAR, 4
     });
   }
   };
-  if (interior_warp) body(std::false_type{});
-  else body(std::true_type{});
+  if constexpr (VAR) {
+    (void)interior_warp;
+    body(std::true_type{});
+  } else {
+    if (interior_warp) body(std::false_type{});
+    else body(std::true_type{});
+  }
   cp_async_wait<0>();
 }
 

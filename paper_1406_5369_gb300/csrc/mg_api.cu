@@ -338,6 +338,12 @@ bool level_fused(mg_ctx *c, int l) {
 // of a defect-correction step), which lets the fused kernels skip reading it.
 mg_status vcycle_rec(mg_ctx *c, int l, bool zero, cudaStream_t s) {
   mg_status st;
+  if (c->opt.fuse && c->dim == 2 && c->lv[l].n > mg::coarse_top_n(c->dim, !c->dc) &&
+      mg::cluster_ok(c->lv, l, c->nl, (int)c->opt.smoother, !c->dc, c->opt.cluster_max_n)) {
+    TLAUNCH(c, MG_KERNEL_COARSE, l, s,
+            mg::cluster_cycle(c->lv, l, c->nl, zero, c->opt.omega, c->opt.nu1, c->opt.nu2, s));
+    return MG_OK;
+  }
   if (c->opt.fuse && c->lv[l].n <= mg::coarse_top_n(c->dim, !c->dc)) {
     TLAUNCH(c, MG_KERNEL_COARSE, l, s,
             mg::coarse_cycle(c->lv, l, c->nl, zero, c->opt.smoother, c->opt.omega, c->opt.nu1, c->opt.nu2, !c->dc, s));
@@ -643,6 +649,7 @@ void mg_default_options(mg_options *o) {
   o->inner_cycles = 1;
   o->exact_outer = 1;
   o->join_cycles = 1;
+  o->cluster_max_n = 0;
 }
 
 size_t mg_workspace_bytes(int dim, int n, int variable_k, const mg_options *opt) {
@@ -688,6 +695,8 @@ mg_status mg_create(int dim, int n, const mg_const_stencil *stencil, const doubl
   c->dc = opt->precision != MG_FP64;
   c->stream = (cudaStream_t)opt->stream;
   c->capturing_slot = -1;
+  // the device check of the cluster cycle runs here, never inside a capture
+  if (dim == 2 && c->dc && opt->fuse && opt->smoother == MG_RBGS) mg::cluster_probe();
   for (int d = 0; d < 3; d++) c->lv[0].c[d] = c3[d];
   size_t need = layout(c, nullptr);
   if (arena_bytes < need) {

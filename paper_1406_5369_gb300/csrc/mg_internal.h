@@ -162,6 +162,16 @@ cudaError_t coarse_cycle(const Level *lv, int first, int nl, bool zero_top, int 
 size_t coarse_args(const Level *lv, int first, int nl, bool zero_top, int smoother, double omega, int nu1, int nu2,
                    bool fp64, void *args_out);
 size_t coarse_args_bytes();
+// V-cycle of levels first..nl-1 on one cluster of thread blocks (2D,
+// constant stencil, RBGS, FP32 arithmetic; cluster.cuh). cluster_ok: level
+// l takes it (size within cluster_max_n, the hierarchy's shape, and a
+// cluster of that size fits the device).
+bool cluster_ok(const Level *lv, int l, int nl, int smoother, bool fp64, int cluster_max_n);
+// Asks the device once whether the cluster fits (outside any stream capture:
+// mg_create calls it); cluster_ok answers no until it has run.
+void cluster_probe();
+cudaError_t cluster_cycle(const Level *lv, int first, int nl, bool zero_top, double omega, int nu1, int nu2,
+                          cudaStream_t s);
 // Points a filled argument record at its problem's live flag (captured batch steps).
 void coarse_args_set_live(void *args, const int *live);
 cudaError_t coarse_cycle_batched(const void *list_dev, int count, int dim, bool var, bool fp64, size_t smem,

@@ -49,7 +49,7 @@ class Solver:
     def __init__(self, dim, n, *, stencil=(1.0, 1.0, 1.0), k=None, dirichlet=None,
                  smoother="rbgs", omega=1.0, nu1=2, nu2=1, maxit=50, precision="fp64",
                  fuse=True, use_graph=True, inner_cycles=1, exact_outer=True, tile_rows=0, tile_max_n=0,
-                 fuse_depth=0, join_cycles=True, coarsest_n=3, stream=None, device="cuda", arena=None):
+                 fuse_depth=0, join_cycles=True, cluster_max_n=0, coarsest_n=3, stream=None, device="cuda", arena=None):
         import torch
         self._lib = C.load()
         self.dim, self.n = dim, n
@@ -69,6 +69,7 @@ class Solver:
         opt.tile_max_n = int(tile_max_n)
         opt.fuse_depth = int(fuse_depth)
         opt.join_cycles = int(bool(join_cycles))
+        opt.cluster_max_n = int(cluster_max_n)
         opt.stream = default_stream_handle() if stream is None else stream
         self._tstream = torch.cuda.current_stream() if stream is None else torch.cuda.ExternalStream(stream)
         self.opt = opt

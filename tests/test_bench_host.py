@@ -58,7 +58,8 @@ def test_autotuner_coordinate_search_and_cache(monkeypatch, tmp_path):
             pass
 
     # time = (a - 2)^2 + (b - 3)^2 + 1: the search should land on a = 2, b = 3
-    def fake_time(solver, f, tol, reps=2):
+    def fake_time(solver, f, tol, reps=3, stat="median"):
+        assert stat == "min" and reps >= 3  # one disturbed timing must not decide
         kw = solver.kw
         return (kw["a"] - 2) ** 2 + (kw["b"] - 3) ** 2 + 1.0, 4
 
