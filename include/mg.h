@@ -294,8 +294,8 @@ typedef enum {
  * captured graphs too; graphs are recaptured when the setting changes);
  * mg_set_timing(ctx, 2) only the kernels of level 0 (and the outer step and
  * finest norms), which keeps the event nodes' own cost (a few microseconds
- * each) off the other levels; 0 switches timing off; other values give
- * MG_EINVAL.
+ * each) off the other levels; mg_set_timing(ctx, 3) only the outer step of
+ * defect correction; 0 switches timing off; other values give MG_EINVAL.
  * Durations are added up at synchronising calls (mg_solve,
  * mg_residual_norm, mg_get_timing); a graph replayed twice between two of
  * them contributes its last replay only. mg_get_timing returns the total

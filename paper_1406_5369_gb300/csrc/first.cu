@@ -8,23 +8,55 @@ namespace mg {
 namespace {
 
 // Blocks walk the interior rows (and planes) in a fixed order; each writes
-// one partial sum. d: inner defect (interior rows, zeros in the boundary
-// columns), skipped when Ti is void.
+// one partial sum. Thread t takes the groups of 4 consecutive nodes t,
+// t + 256, ... of each row, two groups per iteration so that four 16-byte
+// loads of f are in flight (rows start 128-byte aligned and every row pitch
+// is a multiple of 4 elements at least n, so the last group stays inside
+// its row). d: inner defect (interior rows, zeros in the boundary columns),
+// skipped when Ti is void.
+__device__ __forceinline__ void store4(float *p, const float (&v)[4]) {
+  *(float4 *)p = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void store4(bf16 *p, const float (&v)[4]) {
+  *(uint2 *)p = make_uint2(bf16_rne_bits(v[0]) | (bf16_rne_bits(v[1]) << 16),
+                           bf16_rne_bits(v[2]) | (bf16_rne_bits(v[3]) << 16));
+}
+
 template <int DIM, typename Ti>
 __global__ void __launch_bounds__(256) k_first_defect(const double *__restrict__ f, Geo go, Ti *__restrict__ d,
                                                       Geo gi, double *__restrict__ partials) {
-  const int n = go.n, m = n - 2;
+  const int n = go.n, m = n - 2, ng = (n + 3) >> 2;
   const long long rows = (long long)m * (DIM == 3 ? m : 1);
   double acc = 0.0;
   for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
     const int j = 1 + (int)(r % m), k = DIM == 3 ? 1 + (int)(r / m) : 0;
     const double *fr = f + (long long)k * go.sz + (long long)j * go.sy;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const bool in = i >= 1 && i <= n - 2;
-      const double v = in ? fr[i] : 0.0;
-      acc = fma(v, v, acc);
-      if constexpr (!std::is_void<Ti>::value) {
-        st(d + (long long)k * gi.sz + (long long)j * gi.sy + i, oz::d2f_bits(v));
+    for (int g0 = threadIdx.x; g0 < ng; g0 += 2 * blockDim.x) {
+      double v[2][4];
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const int g = g0 + h * (int)blockDim.x;
+        if (g < ng) {
+          const double2 a = __ldg((const double2 *)(fr + 4 * g)), b = __ldg((const double2 *)(fr + 4 * g + 2));
+          v[h][0] = a.x; v[h][1] = a.y; v[h][2] = b.x; v[h][3] = b.y;
+        } else {
+          v[h][0] = v[h][1] = v[h][2] = v[h][3] = 0.0;
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const int g = g0 + h * (int)blockDim.x;
+        float out[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const int i = 4 * g + q;
+          const double x = (i >= 1 && i <= n - 2) ? v[h][q] : 0.0;
+          acc = fma(x, x, acc);
+          out[q] = oz::d2f_bits(x);
+        }
+        if constexpr (!std::is_void<Ti>::value) {
+          if (g < ng) store4(d + (long long)k * gi.sz + (long long)j * gi.sy + 4 * g, out);
+        }
       }
     }
   }

@@ -69,7 +69,7 @@ int alloc_pair(mg_ctx *c) {
 
 // Records the start event of a timed launch; returns the pair or -1.
 int timing_begin(mg_ctx *c, int kind, int level, cudaStream_t s) {
-  if (!c->timing || (c->timing == 2 && level != 0)) return -1;
+  if (!c->timing || (c->timing >= 2 && level != 0) || (c->timing == 3 && kind != MG_KERNEL_OUTER)) return -1;
   int slot = c->capturing_slot;
   if (slot >= 0 && c->graphs[slot].npairs >= kSlotPairs) return -1;
   int i = alloc_pair(c);
@@ -1074,7 +1074,7 @@ mg_status mg_set_timing(mg_ctx *c, int on) {
       return fail(MG_ENOMEM, "host allocation of timing events failed");
     }
   }
-  if (on < 0 || on > 2) return fail(MG_EINVAL, "timing mode must be 0, 1 or 2");
+  if (on < 0 || on > 3) return fail(MG_EINVAL, "timing mode must be 0, 1, 2 or 3");
   if (on != c->timing) {
     CK(cudaStreamSynchronize(c->stream));
     if (c->timing) timing_harvest(c);

@@ -114,10 +114,11 @@ class Solver:
     def kernel_launches(self):
         return self._lib.mg_kernel_launches(self.ctx)
 
-    def set_timing(self, on=True, level0_only=False):
+    def set_timing(self, on=True, level0_only=False, outer_only=False):
         """CUDA-event timing of every kernel (on=True), of level-0 kernels only
-        (level0_only=True), or off."""
-        C.check(self._lib.mg_set_timing(self.ctx, (2 if level0_only else 1) if on else 0))
+        (level0_only=True), of the outer step of defect correction only
+        (outer_only=True), or off."""
+        C.check(self._lib.mg_set_timing(self.ctx, (3 if outer_only else 2 if level0_only else 1) if on else 0))
 
     def reset_timing(self):
         C.check(self._lib.mg_reset_timing(self.ctx))
