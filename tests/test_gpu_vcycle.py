@@ -260,6 +260,13 @@ def test_kernel_timing_instrumentation():
     it2, _, _ = s.solve(1e-10)
     assert s.timing("pre", 0)[1] == it2 and s.timing("postpre", 0)[1] == it2 and s.timing("outer", 0)[1] == it2
     assert s.timing("pre", 1) == (0.0, 0) and s.timing("coarse", s.levels - 1) == (0.0, 0)
+    # outer-only mode: the outer step alone
+    s.set_timing(True, outer_only=True)
+    s.reset_timing()
+    s.set_solution(None)
+    it3, _, _ = s.solve(1e-10)
+    assert s.timing("outer", 0)[1] == it3 and s.timing("outer", 0)[0] > 0
+    assert s.timing("pre", 0) == (0.0, 0) and s.timing("postpre", 0) == (0.0, 0) and s.timing("post", 0) == (0.0, 0)
     s.set_timing(False)
     s.reset_timing()
     s.set_solution(None)
