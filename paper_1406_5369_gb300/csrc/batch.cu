@@ -1006,16 +1006,32 @@ mg_status batched_outer(mg_batch *b, const std::vector<mg_ctx *> &ps, bool updat
   BCK("clear partials", cudaMemsetAsync(b->partials, 0, sizeof(double) * (size_t)P * kSlots, b->stream));
   std::vector<BOuter> gen;
   std::map<int, std::vector<std::pair<int, mg_ctx *>>> fast;  // outer size -> (position, problem)
+  std::vector<FirstRec> first;  // zero start, homogeneous Dirichlet data: the residual is f
+  double first_nodes = 0.0;
+  int ti = ps[0]->lv[0].dtype;
   for (int i = 0; i < P; i++) {
     mg_ctx *c = ps[i];
-    if (fast_outer(c)) fast[c->outer.n].push_back({i, c});
-    else {
+    if (!update && c->u_zero && c->bc_zero && (ti == F32 || ti == BF16)) {
+      first.push_back(first_record(c->outer, c->lv[0], b->partials + (size_t)i * kSlots, live_of(b, c)));
+      first_nodes += nodes_of(c->outer);
+    } else if (fast_outer(c)) {
+      fast[c->outer.n].push_back({i, c});
+    } else {
       gen.push_back(make_outer(c, true, update, b->partials + (size_t)i * kSlots));
       gen.back().live = live_of(b, c);
     }
+    // the update makes u non-zero: a later single-context solve must not
+    // take the zero-start residual
+    if (update) c->u_zero = false;
   }
   cudaStream_t s = b->stream;
-  int ti = ps[0]->lv[0].dtype;
+  if (!first.empty()) {
+    const FirstRec *dev = push_list(b, first);
+    if (!dev) return bfail(MG_ENOMEM, "batch descriptor area exhausted");
+    BTimer tm(b, MG_BATCH_OUTER, first_nodes * (8.0 + dtype_size(ti)));  // read f (FP64), write the defect
+    BCK("batched first defect", first_defect_list(dim, ti, dev, (int)first.size(), kPartBlocks, s));
+    b->launches++;
+  }
   if (!gen.empty()) {
     const BOuter *dev = (const BOuter *)push(b, gen.data(), sizeof(BOuter) * gen.size());
     if (!dev) return bfail(MG_ENOMEM, "batch descriptor area exhausted");

@@ -22,9 +22,11 @@ __device__ __forceinline__ void store4(bf16 *p, const float (&v)[4]) {
                            bf16_rne_bits(v[2]) | (bf16_rne_bits(v[3]) << 16));
 }
 
+// This block's share (rows blockIdx.x, blockIdx.x + gridDim.x, ...) of one
+// problem: defect written, sum of squares returned (per thread).
 template <int DIM, typename Ti>
-__global__ void __launch_bounds__(256) k_first_defect(const double *__restrict__ f, Geo go, Ti *__restrict__ d,
-                                                      Geo gi, double *__restrict__ partials) {
+__device__ __forceinline__ double first_rows(const double *__restrict__ f, const Geo &go, Ti *__restrict__ d,
+                                             const Geo &gi) {
   const int n = go.n, m = n - 2, ng = (n + 3) >> 2;
   const long long rows = (long long)m * (DIM == 3 ? m : 1);
   double acc = 0.0;
@@ -60,8 +62,30 @@ __global__ void __launch_bounds__(256) k_first_defect(const double *__restrict__
       }
     }
   }
-  acc = block_sum(acc);
+  return acc;
+}
+
+template <int DIM, typename Ti>
+__global__ void __launch_bounds__(256) k_first_defect(const double *__restrict__ f, Geo go, Ti *__restrict__ d,
+                                                      Geo gi, double *__restrict__ partials) {
+  const double acc = block_sum(first_rows<DIM, Ti>(f, go, d, gi));
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+// Problem blockIdx.y of a list (the batch engine); a problem no longer live
+// is skipped by the whole block.
+template <int DIM, typename Ti>
+__global__ void __launch_bounds__(256) k_first_defect_list(const FirstRec *__restrict__ list) {
+  const FirstRec &rc = list[blockIdx.y];
+  if (rc.live && !*rc.live) return;
+  Geo go, gi;
+  go.n = gi.n = rc.n;
+  go.sy = rc.sy;
+  go.sz = rc.sz;
+  gi.sy = rc.syi;
+  gi.sz = rc.szi;
+  const double acc = block_sum(first_rows<DIM, Ti>(rc.f, go, (Ti *)rc.d, gi));
+  if (threadIdx.x == 0) rc.partials[blockIdx.x] = acc;
 }
 
 template <int DIM> cudaError_t launch(const Level &O, const Level *I, double *partials, cudaStream_t s) {
@@ -81,6 +105,36 @@ template <int DIM> cudaError_t launch(const Level &O, const Level *I, double *pa
 cudaError_t first_defect(const Level &O, const Level *I, double *partials, cudaStream_t s) {
   if (O.dtype != F64 || (I && I->dtype != F32 && I->dtype != BF16)) return cudaErrorInvalidValue;
   return O.dim == 2 ? launch<2>(O, I, partials, s) : launch<3>(O, I, partials, s);
+}
+
+FirstRec first_record(const Level &O, const Level &I, double *partials, const int *live) {
+  FirstRec r;
+  r.f = (const double *)O.f;
+  r.d = I.f;
+  r.n = O.n;
+  r.sy = O.pitch;
+  r.sz = O.plane;
+  r.syi = I.pitch;
+  r.szi = I.plane;
+  r.partials = partials;
+  r.live = live;
+  return r;
+}
+
+cudaError_t first_defect_list(int dim, int inner_dtype, const FirstRec *list, int count, int blocks,
+                              cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const dim3 g((unsigned)blocks, (unsigned)count);
+  if (inner_dtype == F32) {
+    if (dim == 2) k_first_defect_list<2, float><<<g, 256, 0, s>>>(list);
+    else k_first_defect_list<3, float><<<g, 256, 0, s>>>(list);
+  } else if (inner_dtype == BF16) {
+    if (dim == 2) k_first_defect_list<2, bf16><<<g, 256, 0, s>>>(list);
+    else k_first_defect_list<3, bf16><<<g, 256, 0, s>>>(list);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace mg

@@ -143,6 +143,20 @@ cudaError_t norm_stream(const Level &L, const void *u, const void *f, double *pa
 // FP64 level O: kNormBlocks partial sums of f^2 over the interior and, when
 // I is given (defect correction), f written as I's right-hand side.
 cudaError_t first_defect(const Level &O, const Level *I, double *partials, cudaStream_t s);
+// The same over a list of problems in device memory (the batch engine): the
+// FP64 outer level's f, the inner level-0 defect, `blocks` partial sums per
+// problem into its own slots; grid (blocks, count).
+struct FirstRec {
+  const double *f;
+  void *d;
+  int n;
+  long long sy, sz, syi, szi;  // outer and inner row / plane strides (elements)
+  double *partials;
+  const int *live;             // NULL: always live
+};
+FirstRec first_record(const Level &O, const Level &I, double *partials, const int *live);
+cudaError_t first_defect_list(int dim, int inner_dtype, const FirstRec *list, int count, int blocks,
+                              cudaStream_t s);
 
 // Deterministic sum of nb partials (any nb): out[0] = sqrt(sum) / *scale_in
 // (scale_in may be NULL), out[1] = sum; scale_out (may be NULL) receives the

@@ -267,3 +267,38 @@ def test_async_steps_on_two_streams_equal_synchronous_steps():
     B1 = BatchSolver(1)
     B1.add(fresh)
     assert np.array_equal(rl, B1.step([0]))
+
+
+def test_zero_start_first_defect_in_batches():
+    """A problem that starts from u = 0 under homogeneous Dirichlet data gets
+    the residual f itself as its first defect (no stencil pass), a problem
+    with a non-zero start the full residual; both first norms are the
+    oracle's (the first step's ratio uses them). After a batch step the
+    solution is no longer zero, so a single-context solve that follows forms
+    the full residual of it."""
+    need_gpu()
+    from paper_1406_5369_gb300 import BatchSolver
+    for dim, m, prec in ((2, 7, "fp32_dc"), (3, 5, "bf16_dc")):
+        kw = dict(prec=prec, smoother="rbgs" if dim == 2 else "jacobi", omega=1.0 if dim == 2 else 6 / 7,
+                  nu=(2, 1) if dim == 2 else (2, 2), inner=2)
+        sz, fz_, _ = make_problem(dim, m, 900 + dim, **kw)
+        sn, fn, _ = make_problem(dim, m, 910 + dim, **kw)
+        rng = np.random.default_rng(7 + dim)
+        u0 = np.zeros(fn.shape)
+        u0[(slice(1, -1),) * dim] = rng.uniform(-1, 1, (fn.shape[0] - 2,) * dim)
+        sn.set_solution(u0)
+        B = BatchSolver(4)
+        pz, pn = B.add(sz), B.add(sn)
+        rho = B.step([pz, pn])
+        r0 = [oracle.norm(oracle.residual(np.zeros_like(fz_), fz_)), oracle.norm(oracle.residual(u0, fn))]
+        for k, (s, f) in enumerate(((sz, fz_), (sn, fn))):
+            r1 = oracle.norm(oracle.residual(s.get_solution(), f))
+            assert abs(rho[k] - r1 / r0[k]) <= 1e-5 * r1 / r0[k], (dim, k, rho[k], r1 / r0[k])
+        # a single-context solve after the batch step starts from the stepped u
+        B.remove(pz)
+        u1 = sz.get_solution()
+        r_start = oracle.norm(oracle.residual(u1, fz_))
+        it, rr, _ = sz.solve(1e-10)
+        u2 = sz.get_solution()
+        assert oracle.norm(oracle.residual(u2, fz_)) <= 1.01e-10 * r_start
+        B.close()
