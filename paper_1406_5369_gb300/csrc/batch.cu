@@ -219,19 +219,14 @@ __global__ void kb_dc_residual(const BOuter *__restrict__ os) {
   const BOuter &o = os[blockIdx.y];
   if (gone(o)) return;
   const Sten<double> s = o.sd;
-  int m = o.go.n - 2;
-  long long total = (long long)m * m * (DIM == 3 ? m : 1);
   double acc = 0.0;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    long long p = interior_node<DIM>(t, m, o.go);
-    long long q = interior_node<DIM>(t, m, o.gi);
+  for_interior_rows<DIM>(o.go.n - 2, o.go, o.gi, [&](long long p, long long q) {
     double Au, dg;
     apply_at<DIM, VAR>(o.u, p, o.go, s, Au, dg);
     double r = o.f[p] - Au;
     acc += r * r;
     if (o.d) st((Ti *)o.d + q, oz::d2f_bits(r));  // truncation to FP32 without the FP64 pipe
-  }
+  });
   acc = block_sum(acc);
   if (threadIdx.x == 0) o.partials[blockIdx.x] = acc;
 }
@@ -240,14 +235,8 @@ template <int DIM, typename Ti>
 __global__ void kb_dc_update(const BOuter *__restrict__ os) {
   const BOuter &o = os[blockIdx.y];
   if (gone(o)) return;
-  int m = o.go.n - 2;
-  long long total = (long long)m * m * (DIM == 3 ? m : 1);
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    long long p = interior_node<DIM>(t, m, o.go);
-    long long q = interior_node<DIM>(t, m, o.gi);
-    o.u[p] += oz::f2d_bits(ld((const Ti *)o.e + q));
-  }
+  for_interior_rows<DIM>(o.go.n - 2, o.go, o.gi,
+                         [&](long long p, long long q) { o.u[p] += oz::f2d_bits(ld((const Ti *)o.e + q)); });
 }
 
 // Norm partials of level 0 for plain FP64 problems.
@@ -258,17 +247,13 @@ __global__ void kb_norm(const BOp *__restrict__ ops, double *__restrict__ partia
   const Sten<double> s = o.sd;
   const double *u = (const double *)o.u[o.cur];
   const double *f = (const double *)o.f;
-  int m = o.g.n - 2;
-  long long total = (long long)m * m * (DIM == 3 ? m : 1);
   double acc = 0.0;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    long long p = interior_node<DIM>(t, m, o.g);
+  for_interior_rows<DIM>(o.g.n - 2, o.g, o.g, [&](long long p, long long) {
     double Au, dg;
     apply_at<DIM, VAR>(u, p, o.g, s, Au, dg);
     double r = f[p] - Au;
     acc += r * r;
-  }
+  });
   acc = block_sum(acc);
   if (threadIdx.x == 0) partials[(long long)blockIdx.y * kSlots + blockIdx.x] = acc;
 }

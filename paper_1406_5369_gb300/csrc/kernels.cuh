@@ -267,32 +267,37 @@ __device__ __forceinline__ double block_sum(double v) {
 }
 
 // Interior node t of a level with m = n-2 interior nodes per dimension.
-template <int DIM>
-__device__ __forceinline__ long long interior_node(long long t, int m, const Geo &g) {
-  long long i = 1 + t % m;
-  long long rest = t / m;
-  long long j = 1 + rest % m;
-  long long k = DIM == 3 ? 1 + rest / m : 0;
-  return k * g.sz + j * g.sy + i;
+// Calls body(po, pi) for the interior nodes of block blockIdx.x's share of
+// an n^DIM level (m = n - 2 interior nodes per dimension), in a fixed order
+// that depends only on the grid size: rows (y, or y and z) blockIdx.x,
+// blockIdx.x + gridDim.x, ...; within a row, columns 1 + threadIdx.x,
+// 1 + threadIdx.x + blockDim.x, ... po and pi index the same node in the two
+// geometries go and gi (an outer level and its inner level). One integer
+// division per row, none per node.
+template <int DIM, typename Fn>
+__device__ __forceinline__ void for_interior_rows(int m, const Geo &go, const Geo &gi, Fn &&body) {
+  const int rows = DIM == 3 ? m * m : m;
+  for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+    const int j = 1 + (DIM == 3 ? r % m : r), k = DIM == 3 ? 1 + r / m : 0;
+    const long long ro = (long long)k * go.sz + (long long)j * go.sy;
+    const long long ri = (long long)k * gi.sz + (long long)j * gi.sy;
+    for (int i = 1 + (int)threadIdx.x; i <= m; i += (int)blockDim.x) body(ro + i, ri + i);
+  }
 }
 
-// Per-block partial sums of (f - A u)^2 in FP64 over a fixed grid-stride
-// partition, so the summation order depends only on the grid size.
+// Per-block partial sums of (f - A u)^2 in FP64 over a fixed partition of
+// the rows, so the summation order depends only on the grid size.
 template <int DIM, typename T, bool VAR>
 __global__ void k_norm_partials(const T *__restrict__ u, const T *__restrict__ f, Geo g,
                                 Sten<typename CT<T>::type> s, double *__restrict__ partials) {
   typedef typename CT<T>::type C;
-  int m = g.n - 2;
-  long long total = (long long)m * m * (DIM == 3 ? m : 1);
   double acc = 0.0;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    long long p = interior_node<DIM>(t, m, g);
+  for_interior_rows<DIM>(g.n - 2, g, g, [&](long long p, long long) {
     C Au, dg;
     apply_at<DIM, VAR>(u, p, g, s, Au, dg);
     double r = (double)(ld(f + p) - Au);
     acc += r * r;
-  }
+  });
   acc = block_sum(acc);
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
@@ -398,19 +403,14 @@ __global__ void __launch_bounds__(352) k_coarse_dense(double *u, const double *f
 template <int DIM, typename Ti, bool VAR>
 __global__ void k_dc_residual(const double *__restrict__ u, const double *__restrict__ f, Geo go,
                               Sten<double> s, Ti *__restrict__ d, Geo gi, double *__restrict__ partials) {
-  int m = go.n - 2;
-  long long total = (long long)m * m * (DIM == 3 ? m : 1);
   double acc = 0.0;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    long long p = interior_node<DIM>(t, m, go);
-    long long q = interior_node<DIM>(t, m, gi);
+  for_interior_rows<DIM>(go.n - 2, go, gi, [&](long long p, long long q) {
     double Au, dg;
     apply_at<DIM, VAR>(u, p, go, s, Au, dg);
     double r = f[p] - Au;
     acc += r * r;
     st(d + q, (float)r);
-  }
+  });
   acc = block_sum(acc);
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
