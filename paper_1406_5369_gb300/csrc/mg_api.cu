@@ -785,14 +785,62 @@ int mg_level_size(const mg_ctx *c, int level) {
   return c->lv[level].n;
 }
 
+// Rows of a dense FP64 array that the device reaches directly (pinned host
+// memory) written into a pitched field: the interior box (interior != 0) or
+// every node. Each block takes rows in turn, its threads stream one row with
+// 8-byte loads (rows of an odd n start only 8-byte aligned), four in flight
+// per thread: host reads cross the chip-to-chip link with microseconds of
+// latency.
+__global__ void __launch_bounds__(1024) k_rows_in(const double *__restrict__ src, double *__restrict__ dst,
+                                                  long long pitch, long long plane, int n, int dim, int interior) {
+  const int lo = interior ? 1 : 0, m = n - 2 * lo;
+  const long long rows = (long long)m * (dim == 3 ? m : 1);
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+    const int j = lo + (int)(r % m), k = dim == 3 ? lo + (int)(r / m) : 0;
+    const double *a = src + ((long long)k * n + j) * n + lo;
+    double *b = dst + (long long)k * plane + (long long)j * pitch + lo;
+    const int B = (int)blockDim.x;
+    for (int i = threadIdx.x; i < m; i += 4 * B) {
+      double v[4];
+#pragma unroll
+      for (int h = 0; h < 4; h++) v[h] = i + h * B < m ? __ldg(a + i + h * B) : 0.0;
+#pragma unroll
+      for (int h = 0; h < 4; h++)
+        if (i + h * B < m) b[i + h * B] = v[h];
+    }
+  }
+}
+
+// Copies a dense FP64 host or device array into the user level's pitched
+// field dst (the interior box, or every node). Pinned host memory is read by
+// a small kernel through its device mapping: the copy engines' host reads
+// measured slow while the other context of a solve sequence kept HBM busy.
+static cudaError_t copy_field_in(mg_ctx *c, const double *src, void *dst, bool interior, cudaStream_t s) {
+  Level &U = user_level(c);
+  cudaPointerAttributes at;
+  bool pinned = false;
+  if (cudaPointerGetAttributes(&at, src) == cudaSuccess) {
+    pinned = at.type == cudaMemoryTypeHost && at.devicePointer != nullptr;
+  } else {
+    cudaGetLastError();  // an unknown host pointer: clear the error
+  }
+  if (pinned) {
+    // 16 blocks of 1024 threads, as for the solution's way back
+    k_rows_in<<<16, 1024, 0, s>>>((const double *)at.devicePointer, (double *)dst, U.pitch, U.plane, U.n, U.dim,
+                                  interior ? 1 : 0);
+    c->launches++;
+    return cudaGetLastError();
+  }
+  return interior ? copy_dense_interior(U, src, dst, s) : copy_dense_to_pitched(U, src, dst, s);
+}
+
 mg_status mg_set_rhs(mg_ctx *c, const double *f) {
   if (!c || !f) return fail(MG_EINVAL, "NULL argument");
   Level &U = user_level(c);
   // Defect correction: interior only, so the outer right-hand side stays
   // zero on the boundary (the exact outer step takes every value of a row
   // into its exponent).
-  if (c->dc) CK(copy_dense_interior(U, f, U.f, c->stream));
-  else CK(copy_dense_to_pitched(U, f, U.f, c->stream));
+  CK(copy_field_in(c, f, U.f, c->dc, c->stream));
   return MG_OK;
 }
 
@@ -812,7 +860,7 @@ mg_status mg_set_solution(mg_ctx *c, const double *u0) {
       c->launches++;
     }
   } else {
-    CK(copy_dense_interior(U, u0, dst, c->stream));
+    CK(copy_field_in(c, u0, dst, true, c->stream));
   }
   c->u_zero = u0 == nullptr;
   return MG_OK;
