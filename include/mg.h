@@ -49,7 +49,8 @@ typedef enum {
   MG_ENOMEM = 2,   /* arena smaller than mg_workspace_bytes() */
   MG_ECUDA = 3,    /* a CUDA runtime call failed (message in mg_last_error) */
   MG_ENOCONV = 4,  /* residual became NaN/Inf or maxit reached above tol */
-  MG_ETIMEOUT = 5  /* a bounded device-side wait gave up */
+  MG_ETIMEOUT = 5  /* reserved for a bounded device-side wait that gives up; no kernel of
+                      this library waits on a flag, so no call returns it */
 } mg_status;
 
 /* Smoothers of the feature model (Table 1): omega red-black Gauss-Seidel

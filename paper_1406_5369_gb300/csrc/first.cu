@@ -30,6 +30,47 @@ __device__ __forceinline__ double first_rows(const double *__restrict__ f, const
   const int n = go.n, m = n - 2, ng = (n + 3) >> 2;
   const long long rows = (long long)m * (DIM == 3 ? m : 1);
   double acc = 0.0;
+  if (DIM == 3 && ng <= (int)blockDim.x) {
+    // short rows (3D levels; the 2D kernels keep their registers without this
+    // branch): rows r, r + G, r + 2G, r + 3G (G = gridDim.x) per
+    // iteration, one group of each per thread, so that eight loads are in
+    // flight per thread instead of two
+    const int g = threadIdx.x;
+    for (long long r0 = blockIdx.x; r0 < rows; r0 += 4LL * gridDim.x) {
+      double v[4][4];
+#pragma unroll
+      for (int h = 0; h < 4; h++) {
+        const long long r = r0 + (long long)h * gridDim.x;
+        if (r < rows && g < ng) {
+          const int j = 1 + (int)(r % m), k = DIM == 3 ? 1 + (int)(r / m) : 0;
+          const double *fr = f + (long long)k * go.sz + (long long)j * go.sy + 4 * g;
+          const double2 a = __ldg((const double2 *)fr), b = __ldg((const double2 *)(fr + 2));
+          v[h][0] = a.x; v[h][1] = a.y; v[h][2] = b.x; v[h][3] = b.y;
+        } else {
+          v[h][0] = v[h][1] = v[h][2] = v[h][3] = 0.0;
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < 4; h++) {
+        const long long r = r0 + (long long)h * gridDim.x;
+        float out[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const int i = 4 * g + q;
+          const double x = (i >= 1 && i <= n - 2) ? v[h][q] : 0.0;
+          acc = fma(x, x, acc);
+          out[q] = oz::d2f_bits(x);
+        }
+        if constexpr (!std::is_void<Ti>::value) {
+          if (r < rows && g < ng) {
+            const int j = 1 + (int)(r % m), k = DIM == 3 ? 1 + (int)(r / m) : 0;
+            store4(d + (long long)k * gi.sz + (long long)j * gi.sy + 4 * g, out);
+          }
+        }
+      }
+    }
+    return acc;
+  }
   for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
     const int j = 1 + (int)(r % m), k = DIM == 3 ? 1 + (int)(r / m) : 0;
     const double *fr = f + (long long)k * go.sz + (long long)j * go.sy;
