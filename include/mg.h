@@ -326,8 +326,9 @@ mg_status mg_reset_timing(mg_ctx *ctx);
  * MG_NOALLOC_MAX_PARTIALS + 32 doubles (about 256 KB) that every GPU which
  * loads the library keeps until the process exits; nothing is allocated.
  * The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress) - make that first call before any stream capture.
- * All calls share the array and it keeps the last call's contents (every
+ * (cudaGetSymbolAddress). The call cannot be made on a stream that is being
+ * captured into a graph: it ends by synchronising the stream, which a
+ * capturing stream refuses. All calls share the array and it keeps the last call's contents (every
  * call overwrites the slots it reads), so calls that overlap on the GPU -
  * on different streams, or from several host threads - race and must be
  * serialised by the caller. The call runs on `stream` (a cudaStream_t,
