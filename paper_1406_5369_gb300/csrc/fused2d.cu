@@ -3,6 +3,7 @@
 
 #include "fused2d.cuh"
 #include "fused2d_x2.cuh"
+#include "fused2d_x2v.cuh"
 #include "tile2d.cuh"
 
 namespace mg {
@@ -273,6 +274,35 @@ cudaError_t postpre_x2(const fz::Args2D &a, int R, const Level &L, cudaStream_t 
   return a.has_gamma ? launch_postpre_x2<NUA, NUB, true>(a, R, L, s) : launch_postpre_x2<NUA, NUB, false>(a, R, L, s);
 }
 
+// The packed FP32 variable-stencil pre-smoothing pass (fused2d_x2v.cuh).
+template <int NU, bool ZERO>
+cudaError_t launch_pre_x2v(fz::Args2D a, int R_override, const Level &L, cudaStream_t s, const fz::Args2D *list,
+                           int count) {
+  constexpr int W = 2;
+  constexpr size_t smem = (size_t)W * fz::X2VSmem<ZERO>::WB;
+  static bool ready = false;
+  static int bps = 1;
+  if (!ready) {
+    cudaError_t e = prepare(fz::k_pre2d_x2v<NU, ZERO, false>, smem);
+    if (e == cudaSuccess) e = prepare(fz::k_pre2d_x2v<NU, ZERO, true>, smem);
+    if (e != cudaSuccess) return e;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fz::k_pre2d_x2v<NU, ZERO, false>, 32 * W, smem);
+    if (bps < 1) bps = 1;
+    ready = true;
+  }
+  if (R_override <= 0) {
+    a.R = pick_rows(L.n, a.nstrips, bps, W, list ? kListRows : 0);
+    a.nchunks = (L.n + a.R - 1) / a.R;
+  }
+  long long warps = (long long)a.nstrips * a.nchunks;
+  unsigned blocks = (unsigned)((warps + W - 1) / W);
+  if (list)
+    fz::k_pre2d_x2v<NU, ZERO, true><<<dim3(blocks, (unsigned)count), 32 * W, smem, s>>>(a, list);
+  else
+    fz::k_pre2d_x2v<NU, ZERO, false><<<blocks, 32 * W, smem, s>>>(a, nullptr);
+  return cudaGetLastError();
+}
+
 template <int NU, bool ZERO>
 cudaError_t pre_x2(const fz::Args2D &a, int R, const Level &L, cudaStream_t s, const fz::Args2D *list, int count) {
   return a.has_gamma ? launch_pre_x2<NU, ZERO, true>(a, R, L, s, list, count)
@@ -295,8 +325,9 @@ cudaError_t dispatch_pre(fz::Args2D a, int R, const Level &L, cudaStream_t s, co
     return zero ? pre_x2<2, true>(a, R, L, s, list, count) : pre_x2<2, false>(a, R, L, s, list, count);
   }
   if (L.dtype == F32) {
-    if (nu == 1) { if (zero) { MG_PRE(float, 1, true); } else { MG_PRE(float, 1, false); } }
-    if (zero) { MG_PRE(float, 2, true); } else { MG_PRE(float, 2, false); }
+    // variable stencil: the packed instance
+    if (nu == 1) return zero ? launch_pre_x2v<1, true>(a, R, L, s, list, count) : launch_pre_x2v<1, false>(a, R, L, s, list, count);
+    return zero ? launch_pre_x2v<2, true>(a, R, L, s, list, count) : launch_pre_x2v<2, false>(a, R, L, s, list, count);
   }
 #undef MG_PRE
   if (nu == 1) return zero ? launch_pre<double, 1, true>(a, R, L, s, list, count) : launch_pre<double, 1, false>(a, R, L, s, list, count);
