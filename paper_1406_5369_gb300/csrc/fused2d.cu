@@ -303,6 +303,35 @@ cudaError_t launch_pre_x2v(fz::Args2D a, int R_override, const Level &L, cudaStr
   return cudaGetLastError();
 }
 
+// The packed FP32 variable-stencil post-smoothing pass (fused2d_x2v.cuh).
+template <int NU>
+cudaError_t launch_post_x2v(fz::Args2D a, int R_override, const Level &L, cudaStream_t s, const fz::Args2D *list,
+                            int count) {
+  constexpr int W = 2;
+  constexpr size_t smem = (size_t)W * fz::kX2VPostWB;
+  static bool ready = false;
+  static int bps = 1;
+  if (!ready) {
+    cudaError_t e = prepare(fz::k_post2d_x2v<NU, false>, smem);
+    if (e == cudaSuccess) e = prepare(fz::k_post2d_x2v<NU, true>, smem);
+    if (e != cudaSuccess) return e;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fz::k_post2d_x2v<NU, false>, 32 * W, smem);
+    if (bps < 1) bps = 1;
+    ready = true;
+  }
+  if (R_override <= 0) {
+    a.R = pick_rows(L.n, a.nstrips, bps, W, list ? kListRows : 0);
+    a.nchunks = (L.n + a.R - 1) / a.R;
+  }
+  long long warps = (long long)a.nstrips * a.nchunks;
+  unsigned blocks = (unsigned)((warps + W - 1) / W);
+  if (list)
+    fz::k_post2d_x2v<NU, true><<<dim3(blocks, (unsigned)count), 32 * W, smem, s>>>(a, list);
+  else
+    fz::k_post2d_x2v<NU, false><<<blocks, 32 * W, smem, s>>>(a, nullptr);
+  return cudaGetLastError();
+}
+
 template <int NU, bool ZERO>
 cudaError_t pre_x2(const fz::Args2D &a, int R, const Level &L, cudaStream_t s, const fz::Args2D *list, int count) {
   return a.has_gamma ? launch_pre_x2<NU, ZERO, true>(a, R, L, s, list, count)
@@ -342,8 +371,8 @@ cudaError_t dispatch_post(fz::Args2D a, int R, const Level &L, cudaStream_t s, c
   if (L.dtype == F32 && !var)
     return nu == 1 ? post_x2<1>(a, R, L, s, list, count) : post_x2<2>(a, R, L, s, list, count);
   if (L.dtype == F32) {
-    if (nu == 1) { MG_POST(float, 1); }
-    MG_POST(float, 2);
+    // variable stencil: the packed instance
+    return nu == 1 ? launch_post_x2v<1>(a, R, L, s, list, count) : launch_post_x2v<2>(a, R, L, s, list, count);
   }
 #undef MG_POST
   return nu == 1 ? launch_post<double, 1>(a, R, L, s, list, count) : launch_post<double, 2>(a, R, L, s, list, count);

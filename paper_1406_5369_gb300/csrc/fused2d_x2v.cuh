@@ -250,5 +250,161 @@ __global__ void __launch_bounds__(64, 4) k_pre2d_x2v(Args2D a, const Args2D *__r
   cp_async_wait<0>();
 }
 
+// Interpolation + correction + NU RBGS sweeps with the variable stencil
+// (k_post2d, FP32) in the pair layout: the coarse correction as in
+// k_post2d_x2 (a lane's coarse values at J0 = c0 / 2 and J0 + 1 form one
+// pair), the sweeps as in k_pre2d_x2v. Per warp: rings of u, f and the
+// coarse rows (8 rows) and of the faces (16 rows).
+constexpr size_t kX2VPostWB = (size_t)kRing * 32 * (16 + 16 + 8) + (size_t)kFaceRing * 32 * 16 * 2;
+
+template <int NU, bool LIST>
+__global__ void __launch_bounds__(64, 4) k_post2d_x2v(Args2D a, const Args2D *__restrict__ list) {
+  static_assert(2 * NU + 1 + 2 * kGroup <= kFaceRing, "face ring too short for NU");
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (LIST) {
+    if (retired(list[blockIdx.y])) return;
+    take_problem(a, list[blockIdx.y]);
+  }
+  constexpr int W = 2;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const long long gw = (long long)blockIdx.x * W + wib;
+  if (gw >= (long long)a.nstrips * a.nchunks) return;
+  const int s = (int)(gw % a.nstrips), ch = (int)(gw / a.nstrips);
+  const int n = a.n;
+  const int x0 = s * kOut - kHalo;
+  const int c0 = x0 + kVec * lane;
+  const bool col_ok = c0 >= 0 && c0 < a.pitch;
+  const int J0 = c0 >> 1;
+  const bool ccol_ok = c0 >= 0 && J0 + 1 < a.pitchc;
+  const bool out_lane = lane >= kHalo / kVec && lane < 32 - kHalo / kVec && col_ok;
+  const int r0 = ch * a.R, r1 = min(r0 + a.R, n);
+  const int tstart = max(r0 - 8, 0);  // a multiple of 8
+  const int tend = r1 - 1 + 2 * NU;   // inclusive: final u of row r1 - 1 is ready at t = r1 - 1 + 2 NU
+  const int rlim = min(n, tend + 1);
+  const long long pitch = a.pitch, pitchc = a.pitchc;
+  const float *uin = (const float *)a.uin;
+  const float *f = (const float *)a.f;
+  const float *ec = (const float *)a.ec;
+  const float *kxg = (const float *)a.kx;
+  const float *kyg = (const float *)a.ky;
+  float *uout = (float *)a.uout;
+  constexpr int CB = 8;  // two coarse values per lane
+  unsigned char *su = smem + (size_t)wib * kX2VPostWB;
+  unsigned char *sf = su + kRing * 32 * 16;
+  unsigned char *se = sf + kRing * 32 * 16;
+  unsigned char *skx = se + kRing * 32 * CB;
+  unsigned char *sky = skx + kFaceRing * 32 * 16;
+  const float omega = a.omegaf;
+  const float2 h2 = splat2(a.h2f), gam = splat2(a.gammaf), half2 = splat2(0.5f);
+  const bool has_gamma = a.has_gamma != 0;
+  bool mE[2], mO[2];
+  mE[0] = c0 >= 1 && c0 <= n - 2;
+  mO[0] = c0 + 1 >= 1 && c0 + 1 <= n - 2;
+  mE[1] = c0 + 2 >= 1 && c0 + 2 <= n - 2;
+  mO[1] = c0 + 3 >= 1 && c0 + 3 <= n - 2;
+
+  float2 UE[kSlots], UO[kSlots], FE[kSlots], FO[kSlots], WE[kSlots], WO[kSlots];
+#pragma unroll
+  for (int i = 0; i < kSlots; i++) UE[i] = UO[i] = FE[i] = FO[i] = WE[i] = WO[i] = make_float2(0.0f, 0.0f);
+  // coarse rows by parity of the coarse row index (values at J0, J0 + 1)
+  float2 EC[2] = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
+
+  const long long lane_off = col_ok ? c0 : 0;
+  auto stage_faces = [&](int row) {
+    const bool ok = col_ok && row >= 0 && row < rlim;
+    const int fs = row & (kFaceRing - 1);
+    const long long off = (long long)(ok ? row : 0) * pitch + lane_off;
+    cp_async16(skx + (fs * 32 + lane) * 16, ok ? (const void *)(kxg + off) : (const void *)kxg, ok);
+    cp_async16(sky + (fs * 32 + lane) * 16, ok ? (const void *)(kyg + off) : (const void *)kyg, ok);
+  };
+  auto face_row = [&](const unsigned char *ring, int row) {
+    return ring + ((row & (kFaceRing - 1)) * 32 + lane) * 16;
+  };
+  int tnext = tstart;
+  // With fine row `row` also stage coarse row (row + 1) / 2 when row is odd,
+  // and coarse row 0 with fine row 0.
+  auto issue_group = [&](auto sb) {
+    constexpr int SB = decltype(sb)::value;
+#pragma unroll
+    for (int j = 0; j < kGroup; j++) {
+      const int row = tnext + j;
+      const bool ok = col_ok && row < rlim;
+      const long long off = (long long)(ok ? row : 0) * pitch + lane_off;
+      const int slot = (SB + j) & (kRing - 1);
+      cp_async16(su + (slot * 32 + lane) * 16, ok ? (const void *)(uin + off) : (const void *)uin, ok);
+      cp_async16(sf + (slot * 32 + lane) * 16, ok ? (const void *)(f + off) : (const void *)f, ok);
+      const int I = (j & 1) ? (row + 1) >> 1 : (row == 0 ? 0 : -1);  // row has the parity of j
+      const bool cok = ccol_ok && row <= tend && I >= 0 && I < a.nc;
+      cp_async8(se + (slot * 32 + lane) * CB, cok ? (const void *)(ec + (long long)I * pitchc + J0) : (const void *)ec, cok);
+      stage_faces(row);
+    }
+    cp_async_commit();
+    tnext += kGroup;
+  };
+
+  // coarse row tstart / 2 (even index) precedes the window when the chunk starts inside the grid
+  if (tstart > 0) {
+    const int I = tstart >> 1;
+    if (ccol_ok && I < a.nc) EC[0] = *(const float2 *)(ec + (long long)I * pitchc + J0);
+  }
+#pragma unroll
+  for (int j = kGroup; j >= 1; j--) stage_faces(tstart - j);
+  cp_async_commit();
+  issue_group(std::integral_constant<int, 0>{});
+  for (int tb = tstart; tb <= tend; tb += kSlots) {
+    static_for<0, kSlots>([&](auto kc) {
+      constexpr int K = decltype(kc)::value;
+      const int t = tb + K;
+      if constexpr (K % kGroup == 0) {
+        issue_group(std::integral_constant<int, (K + kGroup) & (kRing - 1)>{});
+        cp_async_wait<1>();
+      }
+      pairs_of(su + (K * 32 + lane) * 16, UE[K], UO[K]);
+      {
+        float2 fe, fo;
+        pairs_of(sf + (K * 32 + lane) * 16, fe, fo);
+        FE[K] = mul2(h2, fe);
+        FO[K] = mul2(h2, fo);
+        const FacesX2 q = faces_x2(face_row(skx, t), face_row(sky, t), face_row(sky, t - 1));
+        const float2 dE = add2(add2(q.KE, q.KWE), add2(q.YE, q.SE));
+        const float2 dO = add2(add2(q.KO, q.KE), add2(q.YO, q.SO));
+        WE[K] = make_float2(__fdividef(omega, dE.x), __fdividef(omega, dE.y));
+        WO[K] = make_float2(__fdividef(omega, dO.x), __fdividef(omega, dO.y));
+      }
+      constexpr int PI = ((K + 1) >> 1) & 1;  // parity of I = (t + 1) / 2
+      if ((K & 1) || t == 0) EC[PI] = *(const float2 *)(se + (K * 32 + lane) * CB);
+      // interpolation and correction of row t
+      {
+        constexpr int PA = (K >> 1) & 1, PB = PA ^ 1;  // parities of t / 2 and t / 2 + 1
+        const float2 ce = (K & 1) ? mul2(half2, add2(EC[PA], EC[PB])) : EC[PA];  // (e0, e1)
+        const float2 co = mul2(half2, add2(ce, make_float2(ce.y, shdn(ce.x))));   // (e0+e1, e1+e2) / 2
+        const bool rowok = t >= 1 && t <= n - 2;
+        const float2 vE = add2(UE[K], ce), vO = add2(UO[K], co);
+        UE[K].x = rowok && mE[0] ? vE.x : UE[K].x;
+        UE[K].y = rowok && mE[1] ? vE.y : UE[K].y;
+        UO[K].x = rowok && mO[0] ? vO.x : UO[K].x;
+        UO[K].y = rowok && mO[1] ? vO.y : UO[K].y;
+      }
+      static_for<1, 2 * NU + 1>([&](auto hc) {
+        constexpr int h = decltype(hc)::value;
+        constexpr int sc = (K - h) & (kSlots - 1), sa = (K - h - 1) & (kSlots - 1), sb = (K - h + 1) & (kSlots - 1);
+        constexpr int PAR = ((h - 1) ^ (K - h)) & 1;
+        const int r = t - h;
+        const bool rowok = r >= 1 && r <= n - 2;
+        const FacesX2 q = faces_x2(face_row(skx, r), face_row(sky, r), face_row(sky, r - 1));
+        half_x2v<PAR>(UE[sc], UO[sc], UE[sa], UO[sa], UE[sb], UO[sb], FE[sc], FO[sc], WE[sc], WO[sc], q, rowok, mE,
+                      mO, gam, has_gamma);
+      });
+      {
+        const int r = t - 2 * NU;
+        constexpr int sc = (K - 2 * NU) & (kSlots - 1);
+        if (r >= r0 && r < r1 && out_lane)
+          *(float4 *)(uout + (long long)r * pitch + c0) = make_float4(UE[sc].x, UO[sc].x, UE[sc].y, UO[sc].y);
+      }
+    });
+  }
+  cp_async_wait<0>();
+}
+
 }  // namespace fz
 }  // namespace mg
