@@ -85,18 +85,17 @@ fz::Args2D make_args(const Level &L, const Level &Cl, double omega, int R_overri
   return a;
 }
 
-template <typename T, int NU, bool ZERO, bool VAR = false>
+template <typename T, int NU, bool ZERO>
 cudaError_t launch_pre(fz::Args2D a, int R_override, const Level &L, cudaStream_t s, const fz::Args2D *list = nullptr,
                        int count = 1) {
-  constexpr int W = fz::Warps<T, VAR>::value;
-  constexpr size_t smem = (size_t)W * (fz::kRing * 32 * fz::Lane<T>::bytes * (ZERO ? 1 : 2) +
-                                       (VAR ? (size_t)fz::kFaceRing * 32 * fz::Lane<T>::bytes * 2 : 0));
+  constexpr int W = fz::Warps<T>::value;
+  constexpr size_t smem = (size_t)W * fz::kRing * 32 * fz::Lane<T>::bytes * (ZERO ? 1 : 2);
   static bool ready = false;
   static int bps = 1;
   if (!ready) {
-    cudaError_t e = prepare(fz::k_pre2d<T, NU, ZERO, VAR>, smem);
+    cudaError_t e = prepare(fz::k_pre2d<T, NU, ZERO>, smem);
     if (e != cudaSuccess) return e;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fz::k_pre2d<T, NU, ZERO, VAR>, 32 * W, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fz::k_pre2d<T, NU, ZERO>, 32 * W, smem);
     if (bps < 1) bps = 1;
     ready = true;
   }
@@ -106,22 +105,21 @@ cudaError_t launch_pre(fz::Args2D a, int R_override, const Level &L, cudaStream_
   }
   long long warps = (long long)a.nstrips * a.nchunks;
   unsigned blocks = (unsigned)((warps + W - 1) / W);
-  fz::k_pre2d<T, NU, ZERO, VAR><<<dim3(blocks, (unsigned)count), 32 * W, smem, s>>>(a, list);
+  fz::k_pre2d<T, NU, ZERO><<<dim3(blocks, (unsigned)count), 32 * W, smem, s>>>(a, list);
   return cudaGetLastError();
 }
 
-template <typename T, int NU, bool VAR = false>
+template <typename T, int NU>
 cudaError_t launch_post(fz::Args2D a, int R_override, const Level &L, cudaStream_t s, const fz::Args2D *list = nullptr,
                         int count = 1) {
-  constexpr int W = fz::Warps<T, VAR>::value;
-  constexpr size_t smem = (size_t)W * (fz::kRing * 32 * (2 * fz::Lane<T>::bytes + 2 * sizeof(T)) +
-                                       (VAR ? (size_t)fz::kFaceRing * 32 * fz::Lane<T>::bytes * 2 : 0));
+  constexpr int W = fz::Warps<T>::value;
+  constexpr size_t smem = (size_t)W * fz::kRing * 32 * (2 * fz::Lane<T>::bytes + 2 * sizeof(T));
   static bool ready = false;
   static int bps = 1;
   if (!ready) {
-    cudaError_t e = prepare(fz::k_post2d<T, NU, VAR>, smem);
+    cudaError_t e = prepare(fz::k_post2d<T, NU>, smem);
     if (e != cudaSuccess) return e;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fz::k_post2d<T, NU, VAR>, 32 * W, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fz::k_post2d<T, NU>, 32 * W, smem);
     if (bps < 1) bps = 1;
     ready = true;
   }
@@ -131,7 +129,7 @@ cudaError_t launch_post(fz::Args2D a, int R_override, const Level &L, cudaStream
   }
   long long warps = (long long)a.nstrips * a.nchunks;
   unsigned blocks = (unsigned)((warps + W - 1) / W);
-  fz::k_post2d<T, NU, VAR><<<dim3(blocks, (unsigned)count), 32 * W, smem, s>>>(a, list);
+  fz::k_post2d<T, NU><<<dim3(blocks, (unsigned)count), 32 * W, smem, s>>>(a, list);
   return cudaGetLastError();
 }
 
@@ -347,8 +345,6 @@ cudaError_t post_x2(const fz::Args2D &a, int R, const Level &L, cudaStream_t s, 
 cudaError_t dispatch_pre(fz::Args2D a, int R, const Level &L, cudaStream_t s, const fz::Args2D *list, int count,
                          bool zero, int nu) {
   const bool var = L.kf[0] != nullptr;
-#define MG_PRE(T, NUv, Z)                                                                      \
-  return var ? launch_pre<T, NUv, Z, true>(a, R, L, s, list, count) : launch_pre<T, NUv, Z, false>(a, R, L, s, list, count)
   if (L.dtype == F32 && !var) {
     if (nu == 1) return zero ? pre_x2<1, true>(a, R, L, s, list, count) : pre_x2<1, false>(a, R, L, s, list, count);
     return zero ? pre_x2<2, true>(a, R, L, s, list, count) : pre_x2<2, false>(a, R, L, s, list, count);
@@ -358,7 +354,6 @@ cudaError_t dispatch_pre(fz::Args2D a, int R, const Level &L, cudaStream_t s, co
     if (nu == 1) return zero ? launch_pre_x2v<1, true>(a, R, L, s, list, count) : launch_pre_x2v<1, false>(a, R, L, s, list, count);
     return zero ? launch_pre_x2v<2, true>(a, R, L, s, list, count) : launch_pre_x2v<2, false>(a, R, L, s, list, count);
   }
-#undef MG_PRE
   if (nu == 1) return zero ? launch_pre<double, 1, true>(a, R, L, s, list, count) : launch_pre<double, 1, false>(a, R, L, s, list, count);
   return zero ? launch_pre<double, 2, true>(a, R, L, s, list, count) : launch_pre<double, 2, false>(a, R, L, s, list, count);
 }
@@ -366,23 +361,20 @@ cudaError_t dispatch_pre(fz::Args2D a, int R, const Level &L, cudaStream_t s, co
 cudaError_t dispatch_post(fz::Args2D a, int R, const Level &L, cudaStream_t s, const fz::Args2D *list, int count,
                           int nu) {
   const bool var = L.kf[0] != nullptr;
-#define MG_POST(T, NUv) \
-  return var ? launch_post<T, NUv, true>(a, R, L, s, list, count) : launch_post<T, NUv, false>(a, R, L, s, list, count)
   if (L.dtype == F32 && !var)
     return nu == 1 ? post_x2<1>(a, R, L, s, list, count) : post_x2<2>(a, R, L, s, list, count);
   if (L.dtype == F32) {
     // variable stencil: the packed instance
     return nu == 1 ? launch_post_x2v<1>(a, R, L, s, list, count) : launch_post_x2v<2>(a, R, L, s, list, count);
   }
-#undef MG_POST
   return nu == 1 ? launch_post<double, 1>(a, R, L, s, list, count) : launch_post<double, 2>(a, R, L, s, list, count);
 }
 
 }  // namespace
 
-// Constant stencil in FP64 or FP32; variable stencil in FP32 (faces stored in
-// the level's type; the FP64 variable-stencil instance would not fit in the
-// register file without spilling, so those levels keep the generic kernels).
+// Constant stencil in FP64 or FP32; variable stencil in FP32 (the packed
+// kernels of fused2d_x2v.cuh, faces stored in FP32); FP64 variable-stencil
+// levels keep the generic kernels.
 bool fused_ok(const Level &L, const Level &Cl, int nu) {
   return L.dim == 2 && (L.dtype == F64 || L.dtype == F32) && (!L.kf[0] || L.dtype == F32) && Cl.dtype == L.dtype &&
          (nu == 1 || nu == 2) && L.n >= 33;

@@ -1,5 +1,8 @@
 // Fused, temporally blocked 2D kernels for the fine levels of the V-cycle
-// (Algorithm 1), constant stencil, red-black Gauss-Seidel.
+// (Algorithm 1), constant stencil, red-black Gauss-Seidel. These scalar
+// instances run the FP64 levels; FP32 levels run the packed FP32x2 instances
+// of the same design (fused2d_x2.cuh, and fused2d_x2v.cuh for the variable
+// stencil).
 //
 //   k_pre2d : nu1 RBGS sweeps + residual + full-weighting restriction in one
 //             pass: reads f (and u unless the level starts from zero), writes
@@ -18,9 +21,7 @@
 // SM. Rows are processed 8 at a time by straight-line code (the register
 // window), which lets the compiler overlap consecutive rows. Warps whose
 // rows and columns are all interior run a copy of that code without the
-// boundary predicates (constant stencil only: the variable-stencil body is
-// large enough that a second copy costs more in instruction-fetch stalls
-// than the predicates it saves). Half-sweep h of the stack runs
+// boundary predicates. Half-sweep h of the stack runs
 // on row t - h when row t arrives (red = i+j even first, as in the paper's
 // "order rb"), so every update sees exactly the neighbour values a
 // sequential red-then-black sweep would; the x-neighbours of a lane's edge
@@ -50,20 +51,12 @@ constexpr int kOut = kCols - 2 * kHalo;  // columns written per strip
 constexpr int kSlots = 8;                // row window in registers
 constexpr int kGroup = 4;                // rows per cp.async commit group
 constexpr int kRing = 2 * kGroup;        // row ring in shared memory: two groups in flight
-// Warps per block: the shared-memory ring of FP64 rows is twice as large;
-// variable-stencil warps carry 16 face rows besides and run in blocks of 2,
-// so that the per-SM residency is set by the per-warp footprint alone.
-template <typename T, bool VAR = false> struct Warps {
-  static constexpr int value = (sizeof(T) == 8 || VAR) ? 2 : 4;
-};
+// Warps per block: the shared-memory ring of FP64 rows is twice as large.
+template <typename T> struct Warps { static constexpr int value = sizeof(T) == 8 ? 2 : 4; };
 // Resident blocks asked of the register allocator: 5 blocks of 4 FP32 warps
 // (at most 96 registers per thread); FP64 kernels are bound by the FP64 pipe
-// and keep their natural register count. FP32 variable-stencil blocks of 2
-// warps: as many as their shared memory admits (20 KB per warp starting from
-// zero, 24 KB otherwise, 26 KB for post-smoothing: 5, 4 and 4 blocks).
-template <typename T, bool VAR = false, int VBLOCKS = 4> struct MinBlocks {
-  static constexpr int value = sizeof(T) == 8 ? 1 : (VAR ? VBLOCKS : 5);
-};
+// and keep their natural register count.
+template <typename T> struct MinBlocks { static constexpr int value = sizeof(T) == 8 ? 1 : 5; };
 
 struct Args2D {
   const void *uin;  // level solution (ignored when starting from zero)
@@ -243,104 +236,14 @@ __device__ __forceinline__ void residual_row(C (&rr)[kVec], const C (&uc)[kVec],
   }
 }
 
-// Variable stencil (conservative form, faces from the harmonic rule): with
-// S = kx[c] u_e + kx[c-1] u_w + ky[r] u_below + ky[r-1] u_above and D the sum
-// of those four faces, the RBGS update is u' = (1 - omega) u + W (F' + S)
-// with W = omega / D (one division per node and pass, kept in the register
-// window) and F' = h^2 f; the residual is (F' + S - D u) / h^2.
-constexpr int kFaceRing = 16;  // face rows stay staged until the residual 2 NU + 2 rows behind has used them
-
-template <typename C> struct VarCoef {
-  C omega, h2, ih2, gamma;
-  bool has_gamma;
-};
-template <typename C> __device__ __forceinline__ VarCoef<C> var_coef_of(const Args2D &a) {
-  VarCoef<C> k;
-  k.omega = pick<C>(a.omega, a.omegaf);
-  k.h2 = pick<C>(a.h2, a.h2f);
-  k.ih2 = pick<C>(a.ih2, a.ih2f);
-  k.gamma = pick<C>(a.gamma, a.gammaf);
-  k.has_gamma = a.has_gamma != 0;
-  return k;
-}
-
-// W = omega / D of the lane's 4 nodes of a row, from its face rows. FP32
-// (the inner cycles of defect correction, whose rounding the FP64 outer loop
-// corrects) uses the fast single-precision division intrinsic (within 2 ulp).
-__device__ __forceinline__ float var_div(float a, float b) { return __fdividef(a, b); }
-__device__ __forceinline__ double var_div(double a, double b) { return a / b; }
-template <typename C>
-__device__ __forceinline__ void var_weight(C (&w)[kVec], const C (&kx)[kVec], const C (&kyr)[kVec],
-                                           const C (&kys)[kVec], C omega) {
-  C kxw = shup(kx[3]);
-#pragma unroll
-  for (int q = 0; q < kVec; q++) {
-    C d = (kx[q] + (q == 0 ? kxw : kx[q - 1])) + (kyr[q] + kys[q]);
-    w[q] = var_div(omega, d);
-  }
-}
-
-template <bool CHECK, typename C>
-__device__ __forceinline__ void half_sweep_var(C (&uc)[kVec], const C (&ua)[kVec], const C (&ub)[kVec],
-                                               const C (&fr)[kVec], const C (&wr)[kVec], const C (&kx)[kVec],
-                                               const C (&kyr)[kVec], const C (&kys)[kVec], int r, int color,
-                                               int c0, int n, const VarCoef<C> &k) {
-  bool rowok = !CHECK || (r >= 1 && r <= n - 2);
-  int par = (color ^ r) & 1;
-  C kxw = shup(kx[3]);
-  if (par == 0) {
-    C left = shup(uc[3]);
-    C s0 = kx[0] * uc[1] + kxw * left + kyr[0] * ub[0] + kys[0] * ua[0];
-    C s2 = kx[2] * uc[3] + kx[1] * uc[1] + kyr[2] * ub[2] + kys[2] * ua[2];
-    C n0 = wr[0] * (fr[0] + s0), n2 = wr[2] * (fr[2] + s2);
-    if (k.has_gamma) { n0 += k.gamma * uc[0]; n2 += k.gamma * uc[2]; }
-    if (!CHECK) {
-      uc[0] = n0;
-      uc[2] = n2;
-    } else {
-      if (rowok && c0 >= 1 && c0 <= n - 2) uc[0] = n0;
-      if (rowok && c0 + 2 >= 1 && c0 + 2 <= n - 2) uc[2] = n2;
-    }
-  } else {
-    C right = shdn(uc[0]);
-    C s1 = kx[1] * uc[2] + kx[0] * uc[0] + kyr[1] * ub[1] + kys[1] * ua[1];
-    C s3 = kx[3] * right + kx[2] * uc[2] + kyr[3] * ub[3] + kys[3] * ua[3];
-    C n1 = wr[1] * (fr[1] + s1), n3 = wr[3] * (fr[3] + s3);
-    if (k.has_gamma) { n1 += k.gamma * uc[1]; n3 += k.gamma * uc[3]; }
-    if (!CHECK) {
-      uc[1] = n1;
-      uc[3] = n3;
-    } else {
-      if (rowok && c0 + 1 >= 1 && c0 + 1 <= n - 2) uc[1] = n1;
-      if (rowok && c0 + 3 >= 1 && c0 + 3 <= n - 2) uc[3] = n3;
-    }
-  }
-}
-
-template <bool CHECK, typename C>
-__device__ __forceinline__ void residual_row_var(C (&rr)[kVec], const C (&uc)[kVec], const C (&ua)[kVec],
-                                                 const C (&ub)[kVec], const C (&fr)[kVec], const C (&kx)[kVec],
-                                                 const C (&kyr)[kVec], const C (&kys)[kVec], int r, int c0, int n,
-                                                 const VarCoef<C> &k) {
-  C left = shup(uc[3]), right = shdn(uc[0]), kxw = shup(kx[3]);
-  bool rowok = !CHECK || (r >= 1 && r <= n - 2);
-#pragma unroll
-  for (int q = 0; q < kVec; q++) {
-    C uw = q == 0 ? left : uc[q - 1];
-    C ue = q == kVec - 1 ? right : uc[q + 1];
-    C kw = q == 0 ? kxw : kx[q - 1];
-    // (F' + sum_faces k (u_nbr - u)) / h^2, the difference form of A u
-    C t = kx[q] * (ue - uc[q]) + kw * (uw - uc[q]) + kyr[q] * (ub[q] - uc[q]) + kys[q] * (ua[q] - uc[q]);
-    C res = (fr[q] + t) * k.ih2;
-    int c = c0 + q;
-    rr[q] = (!CHECK || (rowok && c >= 1 && c <= n - 2)) ? res : (C)0;
-  }
-}
+// Face rows of the variable-stencil kernels (fused2d_x2v.cuh) stay staged
+// until the residual 2 NU + 2 rows behind has used them.
+constexpr int kFaceRing = 16;
 
 // ------------------------------------------------------------------------
 // Pre-smoothing + residual + restriction.
-template <typename T, int NU, bool ZERO, bool VAR = false>
-__global__ void __launch_bounds__(32 * Warps<T, VAR>::value, MinBlocks<T, VAR, ZERO ? 5 : 4>::value)
+template <typename T, int NU, bool ZERO>
+__global__ void __launch_bounds__(32 * Warps<T>::value, MinBlocks<T>::value)
     k_pre2d(Args2D a, const Args2D *__restrict__ list) {
   typedef typename CT<T>::type C;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -349,7 +252,7 @@ __global__ void __launch_bounds__(32 * Warps<T, VAR>::value, MinBlocks<T, VAR, Z
     take_problem(a, list[blockIdx.y]);
   }
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const long long gw = (long long)blockIdx.x * Warps<T, VAR>::value + wib;
+  const long long gw = (long long)blockIdx.x * Warps<T>::value + wib;
   if (gw >= (long long)a.nstrips * a.nchunks) return;
   const int s = (int)(gw % a.nstrips), ch = (int)(gw / a.nstrips);
   const int n = a.n;
@@ -365,46 +268,29 @@ __global__ void __launch_bounds__(32 * Warps<T, VAR>::value, MinBlocks<T, VAR, Z
   T *uout = (T *)a.uout;
   T *fc = (T *)a.fc;
   constexpr int LB = Lane<T>::bytes;
-  // per-warp rings: u (absent when starting from zero), f, then the faces
+  // per-warp rings: u (absent when starting from zero), f
   constexpr size_t UB = ZERO ? 0 : (size_t)kRing * 32 * LB;
-  constexpr size_t WB = UB + (size_t)kRing * 32 * LB + (VAR ? (size_t)kFaceRing * 32 * LB * 2 : 0);
+  constexpr size_t WB = UB + (size_t)kRing * 32 * LB;
   unsigned char *su = smem + (size_t)wib * WB;
   unsigned char *sf = su + UB;
-  unsigned char *skx = sf + kRing * 32 * LB;          // VAR: face rings
-  unsigned char *sky = skx + kFaceRing * 32 * LB;
-  const T *kxg = (const T *)a.kx;
-  const T *kyg = (const T *)a.ky;
   const Coef<C> k = coef_of<C>(a);
-  const VarCoef<C> kv = var_coef_of<C>(a);
 
-  C U[kSlots][kVec], F[kSlots][kVec], Rr[kSlots][kVec], W[VAR ? kSlots : 1][kVec];
+  C U[kSlots][kVec], F[kSlots][kVec], Rr[kSlots][kVec];
 #pragma unroll
   for (int i = 0; i < kSlots; i++)
 #pragma unroll
     for (int q = 0; q < kVec; q++) { U[i][q] = 0; F[i][q] = 0; Rr[i][q] = 0; }
-  auto face = [&](const unsigned char *ring, int row, C (&v)[kVec]) {
-    load_lane<T, C>(ring + ((row & (kFaceRing - 1)) * 32 + lane) * LB, v);
-  };
 
-  // Stages the kGroup rows starting at tg (one commit group); faces_only:
-  // the face rows alone (the rows above the first one, whose u/f ring slots
-  // the first in-loop group refills while this group may still be in flight).
-  auto issue_group = [&](int tg, bool faces_only = false) {
+  // Stages the kGroup rows starting at tg (one commit group).
+  auto issue_group = [&](int tg) {
 #pragma unroll
     for (int K = 0; K < kGroup; K++) {
       int row = tg + K;
       int slot = row & (kRing - 1);
       bool ok = col_ok && row >= 0 && row < n && row <= tend;
       long long off = (long long)row * a.pitch + c0;
-      if (!faces_only) {
-        if (!ZERO) stage_row<T>(su + (slot * 32 + lane) * LB, uin, off, ok);
-        stage_row<T>(sf + (slot * 32 + lane) * LB, f, off, ok);
-      }
-      if (VAR) {
-        int fs = row & (kFaceRing - 1);
-        stage_row<T>(skx + (fs * 32 + lane) * LB, kxg, off, ok);
-        stage_row<T>(sky + (fs * 32 + lane) * LB, kyg, off, ok);
-      }
+      if (!ZERO) stage_row<T>(su + (slot * 32 + lane) * LB, uin, off, ok);
+      stage_row<T>(sf + (slot * 32 + lane) * LB, f, off, ok);
     }
     cp_async_commit();
   };
@@ -419,7 +305,6 @@ __global__ void __launch_bounds__(32 * Warps<T, VAR>::value, MinBlocks<T, VAR, Z
   // already in registers.
   auto body = [&](auto chk) {
   constexpr bool CHECK = decltype(chk)::value;
-  if (VAR) issue_group(tstart - kGroup, true);  // the face row above the first row
   issue_group(tstart);
   for (int tb = tstart; tb <= tend; tb += kSlots) {
     static_for<0, kSlots>([&](auto kc) {
@@ -438,28 +323,11 @@ __global__ void __launch_bounds__(32 * Warps<T, VAR>::value, MinBlocks<T, VAR, Z
           for (int q = 0; q < kVec; q++) U[K][q] = (C)0;
         }
         load_lane<T, C>(sf + (slot * 32 + lane) * LB, F[K]);
-        if constexpr (VAR) {
-          C kx[kVec], kyr[kVec], kys[kVec];
-          face(skx, t, kx);
-          face(sky, t, kyr);
-          face(sky, t - 1, kys);
-          var_weight<C>(W[K], kx, kyr, kys, kv.omega);
-#pragma unroll
-          for (int q = 0; q < kVec; q++) F[K][q] *= kv.h2;
-        }
         // half-sweeps h = 1 .. 2 NU on rows t - h (odd h red, even h black)
 #pragma unroll
         for (int h = 1; h <= 2 * NU; h++) {
           const int sc = (K - h) & (kSlots - 1), sa = (K - h - 1) & (kSlots - 1), sb = (K - h + 1) & (kSlots - 1);
-          if constexpr (VAR) {
-            C kx[kVec], kyr[kVec], kys[kVec];
-            face(skx, t - h, kx);
-            face(sky, t - h, kyr);
-            face(sky, t - h - 1, kys);
-            half_sweep_var<CHECK, C>(U[sc], U[sa], U[sb], F[sc], W[sc], kx, kyr, kys, t - h, (h - 1) & 1, c0, n, kv);
-          } else {
-            half_sweep<CHECK, C>(U[sc], U[sa], U[sb], F[sc], t - h, (h - 1) & 1, c0, n, k);
-          }
+          half_sweep<CHECK, C>(U[sc], U[sa], U[sb], F[sc], t - h, (h - 1) & 1, c0, n, k);
         }
         // final u of row t - 2 NU
         {
@@ -472,15 +340,7 @@ __global__ void __launch_bounds__(32 * Warps<T, VAR>::value, MinBlocks<T, VAR, Z
           const int r = t - 2 * NU - 1;
           const int sc = (K - 2 * NU - 1) & (kSlots - 1), sa = (K - 2 * NU - 2) & (kSlots - 1),
                     sb = (K - 2 * NU) & (kSlots - 1);
-          if constexpr (VAR) {
-            C kx[kVec], kyr[kVec], kys[kVec];
-            face(skx, r, kx);
-            face(sky, r, kyr);
-            face(sky, r - 1, kys);
-            residual_row_var<CHECK, C>(Rr[sc], U[sc], U[sa], U[sb], F[sc], kx, kyr, kys, r, c0, n, kv);
-          } else {
-            residual_row<CHECK, C>(Rr[sc], U[sc], U[sa], U[sb], F[sc], r, c0, n, k);
-          }
+          residual_row<CHECK, C>(Rr[sc], U[sc], U[sa], U[sb], F[sc], r, c0, n, k);
           // restriction once the row below the coarse row is ready (r = 2I + 1);
           // tb is a multiple of 8, so r's parity is known at compile time
           if constexpr (((K - 2 * NU - 1) & 1) != 0) {
@@ -504,20 +364,15 @@ __global__ void __launch_bounds__(32 * Warps<T, VAR>::value, MinBlocks<T, VAR, Z
     });
   }
   };
-  if constexpr (VAR) {
-    (void)interior_warp;
-    body(std::true_type{});
-  } else {
-    if (interior_warp) body(std::false_type{});
-    else body(std::true_type{});
-  }
+  if (interior_warp) body(std::false_type{});
+  else body(std::true_type{});
   cp_async_wait<0>();
 }
 
 // ------------------------------------------------------------------------
 // Interpolation + correction + post-smoothing.
-template <typename T, int NU, bool VAR = false>
-__global__ void __launch_bounds__(32 * Warps<T, VAR>::value, MinBlocks<T, VAR, 4>::value)
+template <typename T, int NU>
+__global__ void __launch_bounds__(32 * Warps<T>::value, MinBlocks<T>::value)
     k_post2d(Args2D a, const Args2D *__restrict__ list) {
   typedef typename CT<T>::type C;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -526,7 +381,7 @@ __global__ void __launch_bounds__(32 * Warps<T, VAR>::value, MinBlocks<T, VAR, 4
     take_problem(a, list[blockIdx.y]);
   }
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const long long gw = (long long)blockIdx.x * Warps<T, VAR>::value + wib;
+  const long long gw = (long long)blockIdx.x * Warps<T>::value + wib;
   if (gw >= (long long)a.nstrips * a.nchunks) return;
   const int s = (int)(gw % a.nstrips), ch = (int)(gw / a.nstrips);
   const int n = a.n;
@@ -545,21 +400,13 @@ __global__ void __launch_bounds__(32 * Warps<T, VAR>::value, MinBlocks<T, VAR, 4
   T *uout = (T *)a.uout;
   constexpr int LB = Lane<T>::bytes;
   constexpr int CB = 2 * (int)sizeof(T);  // two coarse values per lane
-  constexpr size_t WB = (size_t)kRing * 32 * (2 * LB + CB) + (VAR ? (size_t)kFaceRing * 32 * LB * 2 : 0);
+  constexpr size_t WB = (size_t)kRing * 32 * (2 * LB + CB);
   unsigned char *su = smem + (size_t)wib * WB;
   unsigned char *sf = su + kRing * 32 * LB;
   unsigned char *se = sf + kRing * 32 * LB;  // CB bytes per lane and slot
-  unsigned char *skx = se + kRing * 32 * CB;  // VAR: face rings
-  unsigned char *sky = skx + kFaceRing * 32 * LB;
-  const T *kxg = (const T *)a.kx;
-  const T *kyg = (const T *)a.ky;
   const Coef<C> k = coef_of<C>(a);
-  const VarCoef<C> kv = var_coef_of<C>(a);
-  auto face = [&](const unsigned char *ring, int row, C (&v)[kVec]) {
-    load_lane<T, C>(ring + ((row & (kFaceRing - 1)) * 32 + lane) * LB, v);
-  };
 
-  C U[kSlots][kVec], F[kSlots][kVec], W[VAR ? kSlots : 1][kVec];
+  C U[kSlots][kVec], F[kSlots][kVec];
   // Coarse rows by parity of the coarse row index (values at J0, J0+1). Chunks
   // start at multiples of 8, so every parity below is a compile-time constant.
   C E[2][2];
@@ -571,28 +418,21 @@ __global__ void __launch_bounds__(32 * Warps<T, VAR>::value, MinBlocks<T, VAR, 4
 
   // With fine row `row` also stage coarse row I = (row + 1) / 2 when row is
   // odd, and coarse row 0 with fine row 0.
-  auto issue_group = [&](int tg, bool faces_only = false) {
+  auto issue_group = [&](int tg) {
 #pragma unroll
     for (int K = 0; K < kGroup; K++) {
       int row = tg + K;
       int slot = row & (kRing - 1);
       bool ok = col_ok && row >= 0 && row < n && row <= tend;
       long long off = (long long)row * a.pitch + c0;
-      if (!faces_only) {
-        stage_row<T>(su + (slot * 32 + lane) * LB, uin, off, ok);
-        stage_row<T>(sf + (slot * 32 + lane) * LB, f, off, ok);
-        int I = (row & 1) ? (row + 1) >> 1 : (row == 0 ? 0 : -1);
-        bool cok = ccol_ok && row >= 0 && row <= tend && I >= 0 && I < a.nc;
-        const T *csrc = cok ? ec + (long long)I * a.pitchc + J0 : ec;
-        unsigned char *cdst = se + (slot * 32 + lane) * CB;
-        if (CB == 16) cp_async16(cdst, csrc, cok);
-        else cp_async8(cdst, csrc, cok);
-      }
-      if (VAR) {
-        int fs = row & (kFaceRing - 1);
-        stage_row<T>(skx + (fs * 32 + lane) * LB, kxg, off, ok);
-        stage_row<T>(sky + (fs * 32 + lane) * LB, kyg, off, ok);
-      }
+      stage_row<T>(su + (slot * 32 + lane) * LB, uin, off, ok);
+      stage_row<T>(sf + (slot * 32 + lane) * LB, f, off, ok);
+      int I = (row & 1) ? (row + 1) >> 1 : (row == 0 ? 0 : -1);
+      bool cok = ccol_ok && row >= 0 && row <= tend && I >= 0 && I < a.nc;
+      const T *csrc = cok ? ec + (long long)I * a.pitchc + J0 : ec;
+      unsigned char *cdst = se + (slot * 32 + lane) * CB;
+      if (CB == 16) cp_async16(cdst, csrc, cok);
+      else cp_async8(cdst, csrc, cok);
     }
     cp_async_commit();
   };
@@ -611,7 +451,6 @@ __global__ void __launch_bounds__(32 * Warps<T, VAR>::value, MinBlocks<T, VAR, 4
 
   auto body = [&](auto chk) {
   constexpr bool CHECK = decltype(chk)::value;
-  if (VAR) issue_group(tstart - kGroup, true);  // the face row above the first row
   issue_group(tstart);
   for (int tb = tstart; tb <= tend; tb += kSlots) {
     static_for<0, kSlots>([&](auto kc) {
@@ -625,15 +464,6 @@ __global__ void __launch_bounds__(32 * Warps<T, VAR>::value, MinBlocks<T, VAR, 4
         constexpr int slot = K % kRing;
         load_lane<T, C>(su + (slot * 32 + lane) * LB, U[K]);
         load_lane<T, C>(sf + (slot * 32 + lane) * LB, F[K]);
-        if constexpr (VAR) {
-          C kx[kVec], kyr[kVec], kys[kVec];
-          face(skx, t, kx);
-          face(sky, t, kyr);
-          face(sky, t - 1, kys);
-          var_weight<C>(W[K], kx, kyr, kys, kv.omega);
-#pragma unroll
-          for (int q = 0; q < kVec; q++) F[K][q] *= kv.h2;
-        }
         if ((K & 1) || (CHECK && t == 0)) {
           constexpr int PI = ((K + 1) >> 1) & 1;  // parity of I = (t + 1) / 2
           const unsigned char *cs = se + (slot * 32 + lane) * CB;
@@ -668,15 +498,7 @@ __global__ void __launch_bounds__(32 * Warps<T, VAR>::value, MinBlocks<T, VAR, 4
 #pragma unroll
         for (int h = 1; h <= 2 * NU; h++) {
           const int sc = (K - h) & (kSlots - 1), sa = (K - h - 1) & (kSlots - 1), sb = (K - h + 1) & (kSlots - 1);
-          if constexpr (VAR) {
-            C kx[kVec], kyr[kVec], kys[kVec];
-            face(skx, t - h, kx);
-            face(sky, t - h, kyr);
-            face(sky, t - h - 1, kys);
-            half_sweep_var<CHECK, C>(U[sc], U[sa], U[sb], F[sc], W[sc], kx, kyr, kys, t - h, (h - 1) & 1, c0, n, kv);
-          } else {
-            half_sweep<CHECK, C>(U[sc], U[sa], U[sb], F[sc], t - h, (h - 1) & 1, c0, n, k);
-          }
+          half_sweep<CHECK, C>(U[sc], U[sa], U[sb], F[sc], t - h, (h - 1) & 1, c0, n, k);
         }
         {
           const int r = t - 2 * NU;
@@ -687,13 +509,8 @@ __global__ void __launch_bounds__(32 * Warps<T, VAR>::value, MinBlocks<T, VAR, 4
     });
   }
   };
-  if constexpr (VAR) {
-    (void)interior_warp;
-    body(std::true_type{});
-  } else {
-    if (interior_warp) body(std::false_type{});
-    else body(std::true_type{});
-  }
+  if (interior_warp) body(std::false_type{});
+  else body(std::true_type{});
   cp_async_wait<0>();
 }
 
