@@ -850,8 +850,14 @@ def run_c4(args):
         dt, timings[inner] = run_batch(inner, True)
         if best_ms is None or dt < best_ms:
             best_inner, best_ms = inner, dt
-    # the same batch stepped from the host (mg_batch_step per step, norms read back every step)
+    # the same batch stepped from the host (mg_batch_step per step, norms read
+    # back every step), twice (the second is timed); the faster of the two
+    # modes is the tuned choice the line reports (a captured solve pays its
+    # set-up and capture, ~45 ms here, on every one-shot batch solve)
+    run_batch(best_inner, False)
     _, stepped = run_batch(best_inner, False)
+    mode = "captured" if best_ms <= stepped["total_s"] else "host-stepped"
+    best_s = min(best_ms, stepped["total_s"])
     # per-kernel-kind CUDA-event times and algorithmic bytes: one more stepped
     # solve with its launch groups timed (outside the timed runs above)
     _, timed = run_batch(best_inner, False, timing=True)
@@ -883,19 +889,19 @@ def run_c4(args):
     if rank != 0:
         return
     extra = {} if args.no_cpu_baseline else {"cpu_baseline": cpu_baseline_c4(ms_, seed)}
-    _line(METRIC, P / best_ms, "problems/s (batch of 4096 solved to 1e-8)", True, best_ms * 1e3, args,
+    _line(METRIC, P / best_s, "problems/s (batch of 4096 solved to 1e-8)", True, best_s * 1e3, args,
           {"workload": f"{P} independent 2D variable-coefficient problems -div(k grad u) = f, sizes (2^m+1)^2, "
                        "m ~ U{5..10} (seed 0x5EED0004), k lognormal(0,1) per node, harmonic faces, f ~ U[-1,1]; "
                        "FP32 inner / FP64 outer defect correction to 1e-8; RBGS V(2,1); one mg_batch",
            "total_nodes_rank0": nodes, "setup_s": t_setup,
            "parallelism": f"{world} rank(s), problems split by size, no collective on the data path"},
-          "f32 inner / f64 outer", tuned_inner_cycles=best_inner, default_vs_tuned=timings,
+          "f32 inner / f64 outer", tuned_inner_cycles=best_inner, tuned_mode=mode, default_vs_tuned=timings,
           host_stepped=stepped, roofline=roofline, roofline_kernels=klines,
           kernel_timed_solve_s=timed["total_s"],
-          note="one captured CUDA graph of two solve steps replayed, the stopping test on the device (converged "
-               "problems skipped by every later launch); inner_cycles is chosen by timing candidates 1..3 "
-               "(autotuned vs default = 1); host_stepped: the same batch with one host-synchronised "
-               "mg_batch_step per step", **extra)
+          note="two modes of one mg_batch solve, the faster reported (tuned_mode): captured = one CUDA graph of "
+               "two solve steps replayed, the stopping test on the device (converged problems skipped by every "
+               "later launch), set-up and capture included; host-stepped = one host-synchronised mg_batch_step "
+               "per step; inner_cycles is chosen by timing candidates 1..3 captured (default_vs_tuned)", **extra)
 
 
 def serve_step_bytes(dim, n, inner=3):
