@@ -23,16 +23,18 @@ __device__ __forceinline__ void store4(bf16 *p, const float (&v)[4]) {
 }
 
 // This block's share (rows blockIdx.x, blockIdx.x + gridDim.x, ...) of one
-// problem: defect written, sum of squares returned (per thread).
-template <int DIM, typename Ti>
+// problem: defect written, sum of squares returned (per thread). SHORT: rows
+// of at most blockDim.x groups take the short-row path (3D levels, and the
+// batch engine's problems of every size; the single-problem 2D kernel keeps
+// its registers without it).
+template <int DIM, typename Ti, bool SHORT = (DIM == 3)>
 __device__ __forceinline__ double first_rows(const double *__restrict__ f, const Geo &go, Ti *__restrict__ d,
                                              const Geo &gi) {
   const int n = go.n, m = n - 2, ng = (n + 3) >> 2;
   const long long rows = (long long)m * (DIM == 3 ? m : 1);
   double acc = 0.0;
-  if (DIM == 3 && ng <= (int)blockDim.x) {
-    // short rows (3D levels; the 2D kernels keep their registers without this
-    // branch): rows r, r + G, r + 2G, r + 3G (G = gridDim.x) per
+  if (SHORT && ng <= (int)blockDim.x) {
+    // short rows: rows r, r + G, r + 2G, r + 3G (G = gridDim.x) per
     // iteration, one group of each per thread, so that eight loads are in
     // flight per thread instead of two
     const int g = threadIdx.x;
@@ -125,7 +127,7 @@ __global__ void __launch_bounds__(256) k_first_defect_list(const FirstRec *__res
   go.sz = rc.sz;
   gi.sy = rc.syi;
   gi.sz = rc.szi;
-  const double acc = block_sum(first_rows<DIM, Ti>(rc.f, go, (Ti *)rc.d, gi));
+  const double acc = block_sum(first_rows<DIM, Ti, true>(rc.f, go, (Ti *)rc.d, gi));
   if (threadIdx.x == 0) rc.partials[blockIdx.x] = acc;
 }
 
