@@ -821,12 +821,13 @@ def run_c4(args):
     best_inner, best_ms = None, None
     Pm = len(mine)
 
-    def run_batch(inner, capture, timing=False):
+    def run_batch(inner, capture, timing=False, rows=0):
         B = BatchSolver(Pm)
         for s in solvers:
             s.set_solution(None)
             B.add(s)
         B.set_inner_cycles(inner)
+        B.set_tile_rows(rows)
         B.set_capture(capture)
         B.set_timing(timing)
         if world > 1:
@@ -850,17 +851,23 @@ def run_c4(args):
         dt, timings[inner] = run_batch(inner, True)
         if best_ms is None or dt < best_ms:
             best_inner, best_ms = inner, dt
+    # rows per chunk of the fused list launches (tile shape; 0 = 256), at the best inner cycles
+    best_rows, rows_t = 0, {}
+    for rows in (64, 128, 512):
+        dt, rows_t[rows] = run_batch(best_inner, True, rows=rows)
+        if dt < best_ms:
+            best_rows, best_ms = rows, dt
     # the same batch stepped from the host (mg_batch_step per step, norms read
     # back every step), twice (the second is timed); the faster of the two
     # modes is the tuned choice the line reports (a captured solve pays its
     # set-up and capture, ~45 ms here, on every one-shot batch solve)
-    run_batch(best_inner, False)
-    _, stepped = run_batch(best_inner, False)
+    run_batch(best_inner, False, rows=best_rows)
+    _, stepped = run_batch(best_inner, False, rows=best_rows)
     mode = "captured" if best_ms <= stepped["total_s"] else "host-stepped"
     best_s = min(best_ms, stepped["total_s"])
     # per-kernel-kind CUDA-event times and algorithmic bytes: one more stepped
     # solve with its launch groups timed (outside the timed runs above)
-    _, timed = run_batch(best_inner, False, timing=True)
+    _, timed = run_batch(best_inner, False, timing=True, rows=best_rows)
     hbm_peak, peak_kind = peaks()
     kinds = timed.pop("kinds")
     total_k = sum(v[0] for v in kinds.values())
@@ -895,13 +902,15 @@ def run_c4(args):
                        "FP32 inner / FP64 outer defect correction to 1e-8; RBGS V(2,1); one mg_batch",
            "total_nodes_rank0": nodes, "setup_s": t_setup,
            "parallelism": f"{world} rank(s), problems split by size, no collective on the data path"},
-          "f32 inner / f64 outer", tuned_inner_cycles=best_inner, tuned_mode=mode, default_vs_tuned=timings,
+          "f32 inner / f64 outer", tuned_inner_cycles=best_inner, tuned_tile_rows=best_rows, tuned_mode=mode,
+          default_vs_tuned=timings, tile_rows_candidates={str(k): v["total_s"] for k, v in rows_t.items()},
           host_stepped=stepped, roofline=roofline, roofline_kernels=klines,
           kernel_timed_solve_s=timed["total_s"],
           note="two modes of one mg_batch solve, the faster reported (tuned_mode): captured = one CUDA graph of "
                "two solve steps replayed, the stopping test on the device (converged problems skipped by every "
                "later launch), set-up and capture included; host-stepped = one host-synchronised mg_batch_step "
-               "per step; inner_cycles is chosen by timing candidates 1..3 captured (default_vs_tuned)", **extra)
+               "per step; inner_cycles is chosen by timing candidates 1..3 captured (default_vs_tuned), then the list "
+               "launches' rows per chunk among 256 (default), 64, 128, 512 (tile_rows_candidates)", **extra)
 
 
 def serve_step_bytes(dim, n, inner=3):

@@ -415,6 +415,13 @@ mg_status mg_batch_set_capture(mg_batch *batch, int on);
  * (1..8), overriding the value taken from its first problem. */
 mg_status mg_batch_set_inner_cycles(mg_batch *batch, int inner_cycles);
 
+/* Rows each warp of the batch's fused 2D list launches walks per chunk
+ * (rounded up to a multiple of 8; 0 = 256, the default): a tile-shape knob
+ * for the autotuner. The chunking depends on this value and the level size
+ * only, so a problem's results do not depend on the rest of the batch.
+ * Any time, before or after problems are added; MG_EINVAL outside 0..65536. */
+mg_status mg_batch_set_tile_rows(mg_batch *batch, int rows);
+
 /* Kernels the batch has launched so far (diagnostic). */
 unsigned long long mg_batch_launches(const mg_batch *batch);
 

@@ -101,6 +101,7 @@ SIGNATURES = {
     "mg_batch_solve": (_I, [_P, ctypes.POINTER(_D), _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "mg_batch_launches": (ctypes.c_ulonglong, [_P]),
     "mg_batch_set_inner_cycles": (_I, [_P, _I]),
+    "mg_batch_set_tile_rows": (_I, [_P, _I]),
     "mg_batch_set_capture": (_I, [_P, _I]),
     "mg_batch_solve_profile": (_I, [_P, ctypes.POINTER(_D)]),
     "mg_batch_set_timing": (_I, [_P, _I]),

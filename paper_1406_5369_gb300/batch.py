@@ -76,6 +76,10 @@ class BatchSolver:
     def set_inner_cycles(self, n):
         C.check(self._lib.mg_batch_set_inner_cycles(self.h, int(n)))
 
+    def set_tile_rows(self, rows):
+        """Rows per warp chunk of the fused 2D list launches (0 = 256)."""
+        C.check(self._lib.mg_batch_set_tile_rows(self.h, int(rows)))
+
     def set_capture(self, on):
         """True (default): solve() replays captured steps with the stopping
         test on the device; False: one mg_batch_step per step."""

@@ -350,6 +350,7 @@ struct mg_batch {
   cudaStream_t stream;
   bool have_opts;
   mg_options opt;
+  int list_rows;  // rows per chunk of the fused 2D list launches (0 = 256), mg_batch_set_tile_rows
   int dim;
   bool dc, fp64;
   // descriptors: staged in pinned host memory, copied right before the
@@ -669,7 +670,8 @@ mg_status fast_descend(mg_batch *b, std::vector<Item *> &F, bool zero0) {
       // read f (and u), write u and the coarse f; faces (FP32) when variable
       const double w = dtype_size(L0.dtype);
       BTimer tm(b, MG_BATCH_PRE, recs.size() * nodes_of(L0) * ((zero ? 2.25 : 3.25) * w + (L0.kf[0] ? 8.0 : 0.0)));
-      BLAUNCH("batched fused pre-smoothing", d2::pre_fused_list(L0, C0, dev, (int)recs.size(), zero != 0, o.nu1, s));
+      BLAUNCH("batched fused pre-smoothing",
+              d2::pre_fused_list(L0, C0, dev, (int)recs.size(), zero != 0, o.nu1, b->list_rows, s));
       b->launches++;
     }
     for (Item *it : F) it->flip ^= 1;
@@ -777,7 +779,7 @@ mg_status fast_ascend(mg_batch *b, std::vector<Item *> &F, const std::function<i
     if (!dev) return bfail(MG_ENOMEM, "batch descriptor area exhausted");
     // read u, f and the coarse e, write u; faces (FP32) when variable
     BTimer tm(b, MG_BATCH_POST, recs.size() * nodes_of(L0) * (3.25 * dtype_size(L0.dtype) + (L0.kf[0] ? 8.0 : 0.0)));
-    BLAUNCH("batched fused post-smoothing", d2::post_fused_list(L0, C0, dev, (int)recs.size(), o.nu2, s));
+    BLAUNCH("batched fused post-smoothing", d2::post_fused_list(L0, C0, dev, (int)recs.size(), o.nu2, b->list_rows, s));
     b->launches++;
     for (Item *it : F) it->flip ^= 1;
     return MG_OK;
@@ -1364,6 +1366,7 @@ mg_status mg_batch_create(int max_problems, void *workspace, size_t bytes, void 
   b->capture = 1;
   b->stream = (cudaStream_t)stream;
   b->have_opts = false;
+  b->list_rows = 0;
   b->launches = 0;
   b->dev_off = 0;
   b->pinned = nullptr;
@@ -1603,6 +1606,12 @@ mg_status mg_batch_solve_profile(const mg_batch *b, double *out) {
 mg_status mg_batch_set_capture(mg_batch *b, int on) {
   if (!b || (on != 0 && on != 1)) return bfail(MG_EINVAL, "capture must be 0 or 1");
   b->capture = on;
+  return MG_OK;
+}
+
+mg_status mg_batch_set_tile_rows(mg_batch *b, int rows) {
+  if (!b || rows < 0 || rows > 65536) return bfail(MG_EINVAL, "rows must lie in 0..65536");
+  b->list_rows = rows;
   return MG_OK;
 }
 

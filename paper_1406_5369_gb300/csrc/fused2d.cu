@@ -439,15 +439,15 @@ fz::Args2D fused_record(const Level &L, const Level &Cl, double omega, const voi
 }
 
 cudaError_t pre_fused_list(const Level &L, const Level &Cl, const fz::Args2D *list, int count, bool zero, int nu,
-                           cudaStream_t s) {
-  fz::Args2D a = make_args(L, Cl, 1.0, 0, 1);
-  return dispatch_pre(a, 0, L, s, list, count, zero, nu);
+                           int rows, cudaStream_t s) {
+  fz::Args2D a = make_args(L, Cl, 1.0, rows, 1);
+  return dispatch_pre(a, rows, L, s, list, count, zero, nu);
 }
 
-cudaError_t post_fused_list(const Level &L, const Level &Cl, const fz::Args2D *list, int count, int nu,
+cudaError_t post_fused_list(const Level &L, const Level &Cl, const fz::Args2D *list, int count, int nu, int rows,
                             cudaStream_t s) {
-  fz::Args2D a = make_args(L, Cl, 1.0, 0, 1);
-  return dispatch_post(a, 0, L, s, list, count, nu);
+  fz::Args2D a = make_args(L, Cl, 1.0, rows, 1);
+  return dispatch_post(a, rows, L, s, list, count, nu);
 }
 
 }  // namespace d2

@@ -520,11 +520,13 @@ namespace d2 {
 // One problem's record for the list launches (pointers and coefficients).
 fz::Args2D fused_record(const Level &L, const Level &Cl, double omega, const void *uin, void *uout, const void *ec,
                         void *fc);
-// k_pre2d / k_post2d over `count` problems of level size L.n (coarse Cl.n),
-// records in device memory; the grid's y index is the problem.
+// The fused passes over `count` problems of level size L.n (coarse Cl.n),
+// records in device memory; the grid's y index is the problem. rows: rows per
+// warp chunk (0 = 256), the same for every problem of the size whatever else
+// is in the batch.
 cudaError_t pre_fused_list(const Level &L, const Level &Cl, const fz::Args2D *list, int count, bool zero, int nu,
-                           cudaStream_t s);
-cudaError_t post_fused_list(const Level &L, const Level &Cl, const fz::Args2D *list, int count, int nu,
+                           int rows, cudaStream_t s);
+cudaError_t post_fused_list(const Level &L, const Level &Cl, const fz::Args2D *list, int count, int nu, int rows,
                             cudaStream_t s);
 }  // namespace d2
 }  // namespace mg

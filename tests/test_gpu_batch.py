@@ -302,3 +302,36 @@ def test_zero_start_first_defect_in_batches():
         u2 = sz.get_solution()
         assert oracle.norm(oracle.residual(u2, fz_)) <= 1.01e-10 * r_start
         B.close()
+
+
+def test_batch_tile_rows_knob():
+    """The list launches' rows per chunk (mg_batch_set_tile_rows) is a tuning
+    knob: every problem still reaches its tolerance by the oracle's residual,
+    a problem gives bit for bit the same solution alone and in a mix under the
+    same setting, and invalid values are refused."""
+    need_gpu()
+    from paper_1406_5369_gb300 import BatchSolver
+    import paper_1406_5369_gb300._capi as C
+    ms = [7, 9, 8, 10]
+    probs = [make_problem(2, m, 500 + i, var=True, inner=2) for i, m in enumerate(ms)]
+    B = BatchSolver(8)
+    B.set_tile_rows(64)  # before the problems are added: kept
+    for p in probs:
+        B.add(p[0])
+    iters, rel = B.solve(1e-8, maxit=60)
+    for i, (s, f, k) in enumerate(probs):
+        assert rel[i] <= 1e-8
+        faces = oracle.node_faces(k)
+        u = s.get_solution()
+        assert oracle.norm(oracle.residual(u, f, faces=faces)) / oracle.norm(f) <= 1.01e-8
+    s, f, k = make_problem(2, ms[3], 503, var=True, inner=2)
+    B1 = BatchSolver(1)
+    B1.add(s)
+    B1.set_tile_rows(64)
+    it1, _ = B1.solve(1e-8, maxit=60)
+    assert it1[0] == iters[3]
+    assert np.array_equal(s.get_solution(), probs[3][0].get_solution())
+    with pytest.raises(C.MGError):
+        B1.set_tile_rows(-1)
+    B.close()
+    B1.close()
