@@ -5,12 +5,11 @@
 // A cluster of 16 blocks (8 where the device cannot place 16) of 1024
 // threads, one per SM, keeps every level from the top one (129^2 or 257^2)
 // down to 65^2 in distributed shared memory: block r owns a band of interior
-// rows of each level plus one halo
-// row above and below. The bands of consecutive levels are nested (the fine
-// band of block r starts at twice the first coarse row of its coarse band),
-// so that full weighting and bilinear interpolation read only the block's
-// own rows and halo rows, apart from one residual row that the block above
-// supplies. A red-black half-sweep of colour c updates colour-c nodes from
+// rows of each level plus one halo row above and below. The bands of
+// consecutive levels are nested (the fine band of block r starts at twice
+// the first coarse row of its coarse band), so that full weighting and
+// bilinear interpolation read only the block's own rows and halo rows,
+// apart from one residual row that the block above supplies. A red-black half-sweep of colour c updates colour-c nodes from
 // colour-(1-c) neighbours only; the thread that updates a node in a band's
 // first or last row also stores the new value into the halo row of the
 // neighbouring block (a store into that block's shared memory through the
