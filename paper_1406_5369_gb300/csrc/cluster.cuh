@@ -2,26 +2,25 @@
 // below a size threshold, constant stencil, red-black Gauss-Seidel, FP32
 // arithmetic: the inner levels of defect correction).
 //
-// A cluster of 16 blocks (8 where the device cannot place 16) of 1024
-// threads, one per SM, keeps every level from the top one (129^2 or 257^2)
-// down to 65^2 in distributed shared memory: block r owns a band of interior
-// rows of each level plus one halo row above and below. The bands of
-// consecutive levels are nested (the fine band of block r starts at twice
-// the first coarse row of its coarse band), so that full weighting and
-// bilinear interpolation read only the block's own rows and halo rows,
-// apart from one residual row that the block above supplies. A red-black half-sweep of colour c updates colour-c nodes from
-// colour-(1-c) neighbours only; the thread that updates a node in a band's
-// first or last row also stores the new value into the halo row of the
+// A cluster of 16 blocks (8 where the device cannot place 16) of 1024 threads,
+// one per SM, keeps every level from the top one (129^2 or 257^2) down to 65^2
+// in distributed shared memory: block r owns a band of interior rows of each
+// level plus one halo row above and below. The bands of consecutive levels are
+// nested (the fine band of block r starts at twice the first coarse row of its
+// coarse band), so that full weighting and bilinear interpolation read only
+// the block's own rows and halo rows, apart from one residual row that the
+// block above supplies. A red-black half-sweep of colour c updates colour-c
+// nodes from colour-(1-c) neighbours only; the thread that updates a node in a
+// band's first or last row also stores the new value into the halo row of the
 // neighbouring block (a store into that block's shared memory through the
 // cluster mapping), and one cluster barrier (release / acquire) ends the
-// half-sweep. The neighbour may still be running the same half-sweep while
-// the store lands, but it reads only colour-(1-c) values of its halo row and
-// the store writes only colour-c values, so the two never touch the same
-// word. Levels 33^2 and below run in block 0 alone with the single-block
-// cycle (coarse.cuh), between two cluster barriers: the blocks restrict
-// their bands of the 65^2 residual straight into block 0's copy of the
-// 33^2 right-hand side and later read its 33^2 solution back for the
-// interpolation.
+// half-sweep. The neighbour may still be running the same half-sweep while the
+// store lands, but it reads only colour-(1-c) values of its halo row and the
+// store writes only colour-c values, so the two never touch the same word.
+// Levels 33^2 and below run in block 0 alone with the single-block cycle
+// (coarse.cuh), between two cluster barriers: the blocks restrict their bands
+// of the 65^2 residual straight into block 0's copy of the 33^2 right-hand
+// side and later read its 33^2 solution back for the interpolation.
 //
 // Per V-cycle: 2 nu1 + 1 + 1 + 2 nu2 cluster barriers per distributed level
 // and two around block 0's levels, against two kernel launches per level
