@@ -125,10 +125,17 @@ typedef struct { int kind; const double *dirichlet_values; } mg_boundary;
  * cluster_max_n         : *_DC, 2D constant stencil, RBGS only: the largest
  *                         inner level (129 or 257) from which the V-cycle of
  *                         every coarser level runs as one kernel on a cluster
- *                         of 8 thread blocks holding the levels in their
- *                         shared memory (levels 33 and below in one of them);
- *                         0 = 257, values below 129 = never (per-level
- *                         kernels and the single-block cycle below 65) */
+ *                         of 16 thread blocks (8 where 16 cannot be placed)
+ *                         holding the levels in their shared memory (levels
+ *                         33 and below in one of them); 0 = 257, values
+ *                         below 129 = never (per-level kernels and the
+ *                         single-block cycle below 65)
+ * canary                : 1 = debug layout: every buffer the context lays out
+ *                         in the arena is followed by a 256-byte guard zone
+ *                         filled with the byte 0xA5 at mg_create and checked
+ *                         by mg_check_canaries (a write past the end of a
+ *                         buffer changes it); mg_workspace_bytes counts the
+ *                         zones; 0 = no guard zones (the packed layout) */
 typedef struct {
   mg_smoother smoother;
   double omega;
@@ -146,14 +153,15 @@ typedef struct {
   int fuse_depth;
   int join_cycles;
   int cluster_max_n;
+  int canary;
 } mg_options;
 
 typedef struct mg_ctx mg_ctx;
 
 /* Fills *opt with RBGS, omega 1, V(2,1), coarsest 3, maxit 50, FP64,
  * default stream, fuse 1, use_graph 1, inner_cycles 1, exact_outer 1,
- * tile_rows 0, tile_max_n 0, fuse_depth 0, join_cycles 1, cluster_max_n 0 (the Layer-3
- * defaults of Sec. 2.3 and automatic tiling). */
+ * tile_rows 0, tile_max_n 0, fuse_depth 0, join_cycles 1, cluster_max_n 0,
+ * canary 0 (the Layer-3 defaults of Sec. 2.3 and automatic tiling). */
 void mg_default_options(mg_options *opt);
 
 /* Bytes of device arena mg_create needs for this problem (0 if the
@@ -179,6 +187,17 @@ mg_status mg_create(int dim, int n, const mg_const_stencil *stencil, const doubl
 
 /* Releases the host context (the arena stays the caller's). NULL is a no-op. */
 mg_status mg_destroy(mg_ctx *ctx);
+
+/* Debug check of the arena of a context created with options.canary = 1:
+ * waits for the context's stream, copies every guard zone to the host and
+ * sets *damaged to the number of zones holding a byte other than 0xA5 (a
+ * kernel or copy wrote past the end of the buffer before that zone). When
+ * *damaged > 0, mg_last_error names the first damaged zone's buffer and the
+ * offset of its first changed byte. Buffers keep their 256-byte alignment
+ * with zones between them, so every kernel runs its normal code. Returns MG_EINVAL for a NULL argument or a context created
+ * with canary = 0, MG_ECUDA if a copy fails; MG_OK otherwise, damaged or
+ * not. Not for a stream under capture (it synchronizes). */
+mg_status mg_check_canaries(mg_ctx *ctx, int *damaged);
 
 /* Number of levels L (level 0 finest, L-1 coarsest) and nodes per dimension
  * of a level (-1 if out of range). */

@@ -36,7 +36,7 @@ class mg_options(ctypes.Structure):
                 ("precision", ctypes.c_int), ("stream", ctypes.c_void_p), ("fuse", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("inner_cycles", ctypes.c_int), ("exact_outer", ctypes.c_int),
                 ("tile_rows", ctypes.c_int), ("tile_max_n", ctypes.c_int), ("fuse_depth", ctypes.c_int),
-                ("join_cycles", ctypes.c_int), ("cluster_max_n", ctypes.c_int)]
+                ("join_cycles", ctypes.c_int), ("cluster_max_n", ctypes.c_int), ("canary", ctypes.c_int)]
 
 
 class mg_cc_params(ctypes.Structure):
@@ -67,6 +67,7 @@ SIGNATURES = {
     "mg_create": (_I, [_I, _I, ctypes.POINTER(mg_const_stencil), _P, ctypes.POINTER(mg_boundary),
                        ctypes.POINTER(mg_options), _P, ctypes.c_size_t, ctypes.POINTER(_P)]),
     "mg_destroy": (_I, [_P]),
+    "mg_check_canaries": (_I, [_P, ctypes.POINTER(_I)]),
     "mg_num_levels": (_I, [_P]),
     "mg_level_size": (_I, [_P, _I]),
     "mg_set_rhs": (_I, [_P, _P]),

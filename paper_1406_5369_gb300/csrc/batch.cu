@@ -1454,6 +1454,7 @@ mg_status mg_batch_remove(mg_batch *b, int id) {
 // stream: the initial norms of new problems, the step, copies of both into
 // pinned host memory and an event after them. step_finish completes it.
 static mg_status step_enqueue(mg_batch *b, const int *ids, int count) {
+  NvtxRange range("mg_batch step");
   std::vector<mg_ctx *> ps, fresh;
   std::vector<int> fresh_ids;
   for (int i = 0; i < count; i++) {
@@ -1491,6 +1492,7 @@ static mg_status step_enqueue(mg_batch *b, const int *ids, int count) {
 
 // Waits for the step in flight and forms each problem's rho = ||r|| / ||r_0||.
 static mg_status step_finish(mg_batch *b, double *rho) {
+  NvtxRange range("mg_batch step wait");
   b->step_pending = false;
   BCK("synchronize", cudaEventSynchronize(b->step_ev));
   for (size_t i = 0; i < b->step_fresh.size(); i++) b->r0[b->step_fresh[i]] = b->hstep[b->maxp + i];
@@ -1538,6 +1540,7 @@ mg_status mg_batch_step_wait(mg_batch *b, double *rho) {
 
 mg_status mg_batch_solve(mg_batch *b, const double *tol, int maxit, int *iters, double *relres) {
   if (!b || !tol) return bfail(MG_EINVAL, "NULL argument");
+  NvtxRange range("mg_batch_solve");
   if (b->step_pending) return bfail(MG_EINVAL, "a step started by mg_batch_step_async is still in flight");
   std::vector<int> active;
   for (int i = 0; i < b->maxp; i++)

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "mg.h"
 #include "mg_internal.h"
@@ -14,6 +15,21 @@ constexpr int kGraphSlots = 4;
 constexpr int kMaxPairs = 2048;       // event pairs for kernel timing
 constexpr int kSlotPairs = 256;       // timed kernels per captured graph
 constexpr int kKinds = 7;             // mg_kernel_kind values
+constexpr int kMaxGuards = 256;       // guard zones of a canary layout (31 levels x 7 buffers + 11)
+constexpr size_t kGuardBytes = 256;   // bytes per guard zone
+constexpr unsigned char kGuardByte = 0xA5;  // finite as FP64, FP32 and BF16 if a kernel ever reads it
+
+// An NVTX range open for the lifetime of the object: per entry point, V-cycle
+// or solve step and level, so that a profiler can group kernels by them
+// (ncu --nvtx --nvtx-include). Without a tool that reads NVTX attached the
+// push and pop return at once. Inside a stream capture the ranges mark the
+// capture, not the later replays of the graph.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 struct TimingPair {
   cudaEvent_t a, b;
@@ -61,5 +77,12 @@ struct mg_ctx {
   int nfree;
   double t_ms[kKinds][kMaxLevels];
   unsigned long long t_n[kKinds][kMaxLevels];
+  // canary layout (options.canary): the zone after each buffer, its owner's name
+  char *arena;
+  int nguards;
+  size_t guard_off[kMaxGuards];
+  char guard_tag[kMaxGuards][16];
+  // NVTX range names of the levels ("level 3 n=513")
+  char level_name[kMaxLevels][24];
 };
 

@@ -118,13 +118,26 @@ void timing_harvest(mg_ctx *c) {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Hands out 256-byte aligned slices of the arena. With a guard context
+// (options.canary) each slice is followed by kGuardBytes bytes whose offset
+// and owner are recorded there when laying out for real (base != NULL).
 struct Bump {
   char *base;
   size_t off;
-  void *take(size_t bytes) {
+  mg_ctx *guards;
+  void *take(size_t bytes, const char *tag = "buffer", int level = -1) {
     off = align_up(off, 256);
     void *p = base ? base + off : nullptr;
     off += bytes;
+    if (guards) {
+      if (base && guards->nguards < kMaxGuards) {
+        int g = guards->nguards++;
+        guards->guard_off[g] = off;
+        if (level >= 0) snprintf(guards->guard_tag[g], sizeof guards->guard_tag[g], "l%d.%s", level, tag);
+        else snprintf(guards->guard_tag[g], sizeof guards->guard_tag[g], "%s", tag);
+      }
+      off += kGuardBytes;
+    }
     return p;
   }
 };
@@ -160,6 +173,7 @@ mg_status check_args(int dim, int n, const mg_options *opt) {
   if (opt->tile_max_n < 0) return fail(MG_EINVAL, "tile_max_n must be >= 0");
   if (opt->fuse_depth < 0 || opt->fuse_depth > 8) return fail(MG_EINVAL, "fuse_depth must lie in 0..8");
   if (opt->join_cycles != 0 && opt->join_cycles != 1) return fail(MG_EINVAL, "join_cycles must be 0 or 1");
+  if (opt->canary != 0 && opt->canary != 1) return fail(MG_EINVAL, "canary must be 0 or 1");
   return MG_OK;
 }
 
@@ -187,50 +201,52 @@ void init_level(Level &L, int dim, int n, int dtype, const double c[3]) {
   L.inv_h2 = 1.0 / (h * h);
 }
 
-void take_level(Level &L, Bump &b, bool variable) {
+void take_level(Level &L, Bump &b, bool variable, int l) {
+  static const char *face[3] = {"kx", "ky", "kz"};
   size_t bytes = (size_t)L.count * mg::dtype_size(L.dtype);
-  L.u[0] = b.take(bytes);
-  L.u[1] = b.take(bytes);
-  L.f = b.take(bytes);
-  L.r = b.take(bytes);
+  L.u[0] = b.take(bytes, "u0", l);
+  L.u[1] = b.take(bytes, "u1", l);
+  L.f = b.take(bytes, "f", l);
+  L.r = b.take(bytes, "r", l);
   if (variable) {
     size_t fb = (size_t)L.count * mg::face_size(L.dtype);
-    for (int d = 0; d < L.dim; d++) L.kf[d] = b.take(fb);
+    for (int d = 0; d < L.dim; d++) L.kf[d] = b.take(fb, face[d], l);
   }
 }
 
 // Lays out every buffer of the context in the arena (base == NULL: sizing).
 size_t layout(mg_ctx *c, char *base) {
-  Bump b{base, 0};
+  Bump b{base, 0, c->opt.canary ? c : nullptr};
+  c->nguards = 0;
   int inner = c->opt.precision == MG_FP32_DC ? mg::F32 : (c->opt.precision == MG_BF16_DC ? mg::BF16 : mg::F64);
   double cc[3] = {c->lv[0].c[0], c->lv[0].c[1], c->lv[0].c[2]};
   int nn = c->n;
   for (int l = 0; l < c->nl; l++) {
     int dt = (l == c->nl - 1) ? mg::F64 : inner;
     init_level(c->lv[l], c->dim, nn, dt, cc);
-    take_level(c->lv[l], b, c->variable);
+    take_level(c->lv[l], b, c->variable, l);
     nn = (nn - 1) / 2 + 1;
   }
   {
     Level &Z = c->lv[c->nl - 1];
     if (Z.n > 3) {
       size_t m = (size_t)Z.n - 2, N = c->dim == 3 ? m * m * m : m * m;
-      Z.dense = (double *)b.take(N * N * sizeof(double));
+      Z.dense = (double *)b.take(N * N * sizeof(double), "dense");
     }
   }
   if (c->dc) {
     init_level(c->outer, c->dim, c->n, mg::F64, cc);
     size_t bytes = (size_t)c->outer.count * 8;
-    c->outer.u[0] = b.take(bytes);
-    c->outer.u[1] = b.take(bytes);
-    c->outer.f = b.take(bytes);
-    c->outer.r = b.take(bytes);
+    c->outer.u[0] = b.take(bytes, "outer.u0");
+    c->outer.u[1] = b.take(bytes, "outer.u1");
+    c->outer.f = b.take(bytes, "outer.f");
+    c->outer.r = b.take(bytes, "outer.r");
     if (c->variable)
-      for (int d = 0; d < c->dim; d++) c->outer.kf[d] = b.take(bytes);
+      for (int d = 0; d < c->dim; d++) c->outer.kf[d] = b.take(bytes, d == 0 ? "outer.kx" : d == 1 ? "outer.ky" : "outer.kz");
   }
-  c->partials = (double *)b.take(sizeof(double) * mg::kMaxPartials);
-  c->norm_out = (double *)b.take(sizeof(double) * 4);
-  c->dc_scale = (float *)b.take(sizeof(float) * 4);
+  c->partials = (double *)b.take(sizeof(double) * mg::kMaxPartials, "partials");
+  c->norm_out = (double *)b.take(sizeof(double) * 4, "norm_out");
+  c->dc_scale = (float *)b.take(sizeof(float) * 4, "dc_scale");
   return align_up(b.off, 256);
 }
 
@@ -337,6 +353,7 @@ bool level_fused(mg_ctx *c, int l) {
 // says that u_l is zero on entry (every coarse level, and the finest level
 // of a defect-correction step), which lets the fused kernels skip reading it.
 mg_status vcycle_rec(mg_ctx *c, int l, bool zero, cudaStream_t s) {
+  NvtxRange range(c->level_name[l]);
   mg_status st;
   if (c->opt.fuse && c->dim == 2 && c->lv[l].n > mg::coarse_top_n(c->dim, !c->dc) &&
       mg::cluster_ok(c->lv, l, c->nl, (int)c->opt.smoother, !c->dc, c->opt.cluster_max_n)) {
@@ -558,6 +575,7 @@ void drop_graphs(mg_ctx *c) {
 // A graph is keyed by the live-buffer state it was captured in and stores
 // the state it leaves behind (Jacobi sweeps flip a level's live buffer).
 mg_status run(mg_ctx *c, int kind) {
+  NvtxRange range(kind ? "mg solve step" : "mg V-cycle");
   if (!c->opt.use_graph) return record(c, kind, c->stream);
   unsigned key = cur_key(c);
   for (int i = 0; i < kGraphSlots; i++) {
@@ -650,6 +668,7 @@ void mg_default_options(mg_options *o) {
   o->exact_outer = 1;
   o->join_cycles = 1;
   o->cluster_max_n = 0;
+  o->canary = 0;
 }
 
 size_t mg_workspace_bytes(int dim, int n, int variable_k, const mg_options *opt) {
@@ -704,6 +723,9 @@ mg_status mg_create(int dim, int n, const mg_const_stencil *stencil, const doubl
     return fail(MG_ENOMEM, "arena has %zu bytes, %zu needed", arena_bytes, need);
   }
   layout(c, (char *)arena);
+  c->arena = (char *)arena;
+  for (int l = 0; l < c->nl; l++)
+    snprintf(c->level_name[l], sizeof c->level_name[l], "level %d n=%d", l, c->lv[l].n);
   c->used_bytes = need;
   cudaError_t e;
 #define CKC(call)                                                                  \
@@ -715,6 +737,8 @@ mg_status mg_create(int dim, int n, const mg_const_stencil *stencil, const doubl
     }                                                                              \
   } while (0)
   CKC(cudaMemsetAsync(arena, 0, need, c->stream));
+  for (int g = 0; g < c->nguards; g++)
+    CKC(cudaMemsetAsync(c->arena + c->guard_off[g], kGuardByte, kGuardBytes, c->stream));
   if (c->variable) {
     // Node coefficients -> FP64 staging with the finest FP64 layout -> faces.
     Level &K = c->dc ? c->outer : c->lv[0];
@@ -775,6 +799,42 @@ mg_status mg_destroy(mg_ctx *c) {
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->host_norm) cudaFreeHost(c->host_norm);
   free(c);
+  return MG_OK;
+}
+
+mg_status mg_check_canaries(mg_ctx *c, int *damaged) {
+  g_err[0] = 0;
+  if (!c || !damaged) return fail(MG_EINVAL, "NULL argument");
+  *damaged = 0;
+  if (!c->opt.canary) return fail(MG_EINVAL, "the context was created with canary = 0");
+  size_t bytes = (size_t)c->nguards * kGuardBytes;
+  unsigned char *h = (unsigned char *)malloc(bytes ? bytes : 1);
+  if (!h) return fail(MG_ENOMEM, "host buffer for the guard zones");
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  for (int g = 0; g < c->nguards && e == cudaSuccess; g++)
+    e = cudaMemcpy(h + (size_t)g * kGuardBytes, c->arena + c->guard_off[g], kGuardBytes, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    free(h);
+    return fail(MG_ECUDA, "reading the guard zones: %s", cudaGetErrorString(e));
+  }
+  int first = -1, first_byte = 0;
+  for (int g = 0; g < c->nguards; g++) {
+    const unsigned char *z = h + (size_t)g * kGuardBytes;
+    for (size_t i = 0; i < kGuardBytes; i++) {
+      if (z[i] != kGuardByte) {
+        if (first < 0) {
+          first = g;
+          first_byte = (int)i;
+        }
+        ++*damaged;
+        break;
+      }
+    }
+  }
+  free(h);
+  if (first >= 0)
+    snprintf(g_err, sizeof g_err, "%d guard zone(s) damaged; first: after %s, byte %d past its end",
+             *damaged, c->guard_tag[first], first_byte);
   return MG_OK;
 }
 
@@ -1007,6 +1067,7 @@ mg_status mg_residual_norm(mg_ctx *c, int level, double *out) {
 
 mg_status mg_solve(mg_ctx *c, double tol, int *iters, double *relres, double *history) {
   if (!c) return fail(MG_EINVAL, "NULL context");
+  NvtxRange range("mg_solve");
   if (!(tol >= 0.0)) return fail(MG_EINVAL, "tol must be >= 0");
   double r0;
   mg_status st = c->u_zero && c->bc_zero ? op_first_norm(c, c->stream) : op_norm(c, 0, c->stream);
@@ -1049,6 +1110,7 @@ mg_status mg_solve_sequence(mg_ctx *a, mg_ctx *b, void *copy_stream, int count, 
   for (int i = 0; i < count; i++)
     if (!f[i] || !u[i]) return fail(MG_EINVAL, "NULL right-hand side or solution %d", i);
   if (count == 0) return MG_OK;
+  NvtxRange range("mg_solve_sequence");
   cudaStream_t cs = (cudaStream_t)copy_stream;
   mg_ctx *cx[2] = {a, b};
   cudaEvent_t solved[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr};

@@ -49,7 +49,8 @@ class Solver:
     def __init__(self, dim, n, *, stencil=(1.0, 1.0, 1.0), k=None, dirichlet=None,
                  smoother="rbgs", omega=1.0, nu1=2, nu2=1, maxit=50, precision="fp64",
                  fuse=True, use_graph=True, inner_cycles=1, exact_outer=True, tile_rows=0, tile_max_n=0,
-                 fuse_depth=0, join_cycles=True, cluster_max_n=0, coarsest_n=3, stream=None, device="cuda", arena=None):
+                 fuse_depth=0, join_cycles=True, cluster_max_n=0, coarsest_n=3, stream=None, device="cuda", arena=None,
+                 canary=False):
         import torch
         self._lib = C.load()
         self.dim, self.n = dim, n
@@ -70,6 +71,7 @@ class Solver:
         opt.fuse_depth = int(fuse_depth)
         opt.join_cycles = int(bool(join_cycles))
         opt.cluster_max_n = int(cluster_max_n)
+        opt.canary = int(bool(canary))
         opt.stream = default_stream_handle() if stream is None else stream
         self._tstream = torch.cuda.current_stream() if stream is None else torch.cuda.ExternalStream(stream)
         self.opt = opt
@@ -110,6 +112,14 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+    def check_canaries(self):
+        """Debug check of a solver built with canary=True: (number of damaged
+        guard zones, message naming the first). A zone is damaged when a
+        kernel or copy wrote past the end of the arena buffer before it."""
+        bad = ctypes.c_int()
+        C.check(self._lib.mg_check_canaries(self.ctx, ctypes.byref(bad)))
+        return bad.value, (self._lib.mg_last_error().decode() if bad.value else "")
 
     def kernel_launches(self):
         return self._lib.mg_kernel_launches(self.ctx)

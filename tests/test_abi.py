@@ -61,6 +61,39 @@ def test_default_options_and_workspace(lib):
     assert fp < dc < 2 * fp
 
 
+@pytest.mark.parametrize("dim,n,variable,precision,coarsest", [
+    (2, 129, 0, "MG_FP64", 3), (2, 129, 1, "MG_FP32_DC", 5), (3, 33, 1, "MG_BF16_DC", 9), (3, 65, 0, "MG_FP64", 3)])
+def test_canary_layout_adds_one_guard_zone_per_buffer(lib, dim, n, variable, precision, coarsest):
+    """options.canary = 1 puts a 256-byte guard zone after every arena buffer:
+    four fields per level (plus dim face arrays with variable k), the dense
+    coarsest inverse when the coarsest grid is above 3, the outer FP64 level of
+    defect correction (four fields plus faces), and the norm partials, the norm
+    result and the scale words. Each zone adds exactly 256 bytes, since every
+    buffer starts 256-byte aligned."""
+    from paper_1406_5369_gb300 import _capi as C
+    o = C.mg_options()
+    lib.mg_default_options(ctypes.byref(o))
+    assert o.canary == 0
+    o.precision = getattr(C, precision)
+    o.coarsest_n = coarsest
+    plain = lib.mg_workspace_bytes(dim, n, variable, ctypes.byref(o))
+    o.canary = 1
+    guarded = lib.mg_workspace_bytes(dim, n, variable, ctypes.byref(o))
+    levels, m = 0, n
+    while m >= coarsest:
+        levels += 1
+        if m == coarsest:
+            break
+        m = (m - 1) // 2 + 1
+    per_level = 4 + (dim if variable else 0)
+    zones = levels * per_level + (1 if coarsest > 3 else 0) + 3
+    if precision != "MG_FP64":
+        zones += 4 + (dim if variable else 0)
+    assert plain > 0 and guarded - plain == 256 * zones
+    o.canary = 2
+    assert lib.mg_workspace_bytes(dim, n, variable, ctypes.byref(o)) == 0
+
+
 def test_invalid_arguments_are_rejected_before_any_device_work(lib):
     from paper_1406_5369_gb300 import _capi as C
     o = C.mg_options()
